@@ -80,6 +80,9 @@ def _load():
             lib.orc_node_coords.argtypes = [cfgp, ctypes.c_int, dp]
             lib.orc_diag.argtypes = [cfgp, dp, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, dp]
+            lib.orc_tgv_step_sample.argtypes = [cfgp, ctypes.c_double, ctypes.c_double,
+                                                ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                ctypes.POINTER(ctypes.c_long), dp]
             lib.orc_num_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -260,6 +263,21 @@ def tgv_fields(g: Grid, U0: float, rho0: float = 1.0, T0: float = 1.0, C: float 
     _load().orc_tgv_fields(ctypes.byref(c), float(U0), float(rho0), float(T0), float(C),
                            _ptr(rho), _ptr(u), _ptr(T))
     return rho, u, T
+
+
+def tgv_step_sample(g: Grid, nodes, U0: float, rho0: float = 1.0, T0: float = 1.0,
+                    C: float | None = None) -> np.ndarray:
+    """One step from the Taylor-Green equilibrium state at the listed node indices only;
+    returns [len(nodes), 90] (f then g)."""
+    if C is None:
+        C = U0 * U0 / T0
+    nodes = np.ascontiguousarray(nodes, dtype=np.int64)
+    out = np.zeros((len(nodes), 2 * Q))
+    c = g._c()
+    _load().orc_tgv_step_sample(ctypes.byref(c), float(U0), float(rho0), float(T0), float(C),
+                                len(nodes), nodes.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                                _ptr(out))
+    return out
 
 
 def diag(g: Grid, pop: np.ndarray, rho_ref: float, Re: float, U0: float) -> np.ndarray:

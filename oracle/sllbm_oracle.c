@@ -279,6 +279,24 @@ static int wrap(long v, int n)
     return (int)(r < 0 ? r + n : r);
 }
 
+/* Departure search of Sec. II.A for one support point and one velocity: the departure
+ * point x - dt xi is located by the floor of its cell coordinate (periodic wrap happens
+ * when the support values are read), and the Lagrange basis of Eq. (interpolation) is
+ * evaluated at its reference coordinate in each direction.                          */
+static void orc_departure(const orc_cfg *g, double *const xs[3], const int node[3],
+                          const double *xi_i, int base[3], double ell[3][16])
+{
+    int dd;
+    for (dd = 0; dd < 3; ++dd) {
+        double h = g->L[dd] / g->cells[dd];
+        double y = xs[dd][node[dd]] - g->dt * xi_i[dd];
+        double cf = floor(y / h);
+        double r = 2.0 * (y / h - cf) - 1.0;
+        base[dd] = (int)cf * g->p; /* first support node of the departure cell */
+        orc_lagrange(g->p, r, ell[dd]);
+    }
+}
+
 /* Semi-Lagrangian streaming, Sec. II.A: for every support point x and velocity i,
  * the departure point x - dt xi_i is located (floor of the cell coordinate, periodic
  * wrap), and h_i is evaluated there with the tensor-product Lagrange interpolant of
@@ -301,20 +319,13 @@ void orc_stream(const orc_cfg *g, int nh, int nvel, const double *xi, const doub
         for (long n = 0; n < nn; ++n) {
             const int i = hq % nvel;
             const double *in = src + (long)hq * nn;
-            int node[3], base[3], dd, j, k, l;
+            int node[3], base[3], j, k, l;
             double ell[3][16];
             double acc = 0.0;
             node[0] = (int)(n % N[0]);
             node[1] = (int)((n / N[0]) % N[1]);
             node[2] = (int)(n / ((long)N[0] * N[1]));
-            for (dd = 0; dd < 3; ++dd) {
-                double h = g->L[dd] / g->cells[dd];
-                double y = xs[dd][node[dd]] - g->dt * xi[3 * i + dd];
-                double cf = floor(y / h);
-                double r = 2.0 * (y / h - cf) - 1.0;
-                base[dd] = (int)cf * p; /* first support node of the departure cell */
-                orc_lagrange(p, r, ell[dd]);
-            }
+            orc_departure(g, xs, node, xi + 3 * i, base, ell);
             for (l = 0; l <= p; ++l)
                 for (k = 0; k <= p; ++k)
                     for (j = 0; j <= p; ++j) {
@@ -379,59 +390,71 @@ void orc_moments(const orc_cfg *g, const double *pop, double *rho, double *u, do
  * App. D: Qbar_abc = sum_i f_i (xi-u)_a (xi-u)_b (xi-u)_c, Qbar^eq = 0 for this
  * equilibrium, h_i^* = (w_i/3!) Qbar^neq : H_i^(3), g_i^* = (2C_v - D) T f_i^*,
  * tau_Pr = (tau - 1/2)/Pr + 1/2.                                                  */
+static void orc_collide_one(const orc_cfg *g, const double *xi, const double *w, double *f,
+                            double *gg)
+{
+    const double Cv = 1.0 / (g->gamma - 1.0);
+    const double gfac_c = 2.0 * Cv - 3.0;
+    double feq[ORC_Q], fst[ORC_Q];
+    double gs = 0.0, rho, u[3], T, mu, tau, omega, om_pr = 0.0;
+    int i;
+    for (i = 0; i < ORC_Q; ++i) gs += gg[i];
+    orc_node_moments(f, &gs, xi, Cv, &rho, u, &T);
+    mu = orc_sutherland(T) * g->mu_inf;
+    tau = mu / (rho * T * g->dt) + 0.5;
+    omega = 1.0 / tau;
+    orc_feq(xi, w, ORC_Q, rho, u, T, feq);
+    for (i = 0; i < ORC_Q; ++i) fst[i] = 0.0;
+    if (g->pr_correction) {
+        double Qb[3][3][3];
+        int a, b, c, ix[4] = {0, 0, 0, 0};
+        double tau_pr = (tau - 0.5) / g->Pr + 0.5;
+        om_pr = 1.0 / tau - 1.0 / tau_pr;
+        for (a = 0; a < 3; ++a)
+            for (b = 0; b < 3; ++b)
+                for (c = 0; c < 3; ++c) {
+                    double s = 0.0;
+                    for (i = 0; i < ORC_Q; ++i)
+                        s += f[i] * (xi[3 * i + a] - u[a]) * (xi[3 * i + b] - u[b])
+                           * (xi[3 * i + c] - u[c]);
+                    Qb[a][b][c] = s; /* Qbar^eq = 0, so this is Qbar^neq */
+                }
+        for (i = 0; i < ORC_Q; ++i) {
+            double s = 0.0;
+            for (a = 0; a < 3; ++a)
+                for (b = 0; b < 3; ++b)
+                    for (c = 0; c < 3; ++c) {
+                        ix[0] = a; ix[1] = b; ix[2] = c;
+                        s += Qb[a][b][c] * orc_H_n(3, ix, xi + 3 * i);
+                    }
+            fst[i] = w[i] * s / 6.0;
+        }
+    }
+    for (i = 0; i < ORC_Q; ++i) {
+        double geq = gfac_c * T * feq[i];
+        double gst = gfac_c * T * fst[i];
+        f[i] = f[i] - omega * (f[i] - feq[i]) + om_pr * fst[i];
+        gg[i] = gg[i] - omega * (gg[i] - geq) + om_pr * gst;
+    }
+}
+
 void orc_collide(const orc_cfg *g, double *pop)
 {
     double xi[3 * ORC_Q], w[ORC_Q];
     const long nn = orc_nodes(g);
-    const double Cv = 1.0 / (g->gamma - 1.0);
-    const double gfac_c = 2.0 * Cv - 3.0;
     orc_velset(xi, w);
 #pragma omp parallel for schedule(static)
     for (long n = 0; n < nn; ++n) {
-        double f[ORC_Q], gg[ORC_Q], feq[ORC_Q], fst[ORC_Q];
-        double gs = 0.0, rho, u[3], T, mu, tau, omega, om_pr = 0.0;
+        double f[ORC_Q], gg[ORC_Q];
         int i;
         for (i = 0; i < ORC_Q; ++i) {
             f[i] = pop[(long)i * nn + n];
             gg[i] = pop[(long)(ORC_Q + i) * nn + n];
-            gs += gg[i];
         }
-        orc_node_moments(f, &gs, xi, Cv, &rho, u, &T);
-        mu = orc_sutherland(T) * g->mu_inf;
-        tau = mu / (rho * T * g->dt) + 0.5;
-        omega = 1.0 / tau;
-        orc_feq(xi, w, ORC_Q, rho, u, T, feq);
-        for (i = 0; i < ORC_Q; ++i) fst[i] = 0.0;
-        if (g->pr_correction) {
-            double Qb[3][3][3];
-            int a, b, c, ix[4] = {0, 0, 0, 0};
-            double tau_pr = (tau - 0.5) / g->Pr + 0.5;
-            om_pr = 1.0 / tau - 1.0 / tau_pr;
-            for (a = 0; a < 3; ++a)
-                for (b = 0; b < 3; ++b)
-                    for (c = 0; c < 3; ++c) {
-                        double s = 0.0;
-                        for (i = 0; i < ORC_Q; ++i)
-                            s += f[i] * (xi[3 * i + a] - u[a]) * (xi[3 * i + b] - u[b])
-                               * (xi[3 * i + c] - u[c]);
-                        Qb[a][b][c] = s; /* Qbar^eq = 0, so this is Qbar^neq */
-                    }
-            for (i = 0; i < ORC_Q; ++i) {
-                double s = 0.0;
-                for (a = 0; a < 3; ++a)
-                    for (b = 0; b < 3; ++b)
-                        for (c = 0; c < 3; ++c) {
-                            ix[0] = a; ix[1] = b; ix[2] = c;
-                            s += Qb[a][b][c] * orc_H_n(3, ix, xi + 3 * i);
-                        }
-                fst[i] = w[i] * s / 6.0;
-            }
-        }
+        orc_collide_one(g, xi, w, f, gg);
         for (i = 0; i < ORC_Q; ++i) {
-            double geq = gfac_c * T * feq[i];
-            double gst = gfac_c * T * fst[i];
-            pop[(long)i * nn + n] = f[i] - omega * (f[i] - feq[i]) + om_pr * fst[i];
-            pop[(long)(ORC_Q + i) * nn + n] = gg[i] - omega * (gg[i] - geq) + om_pr * gst;
+            pop[(long)i * nn + n] = f[i];
+            pop[(long)(ORC_Q + i) * nn + n] = gg[i];
         }
     }
 }
@@ -493,6 +516,63 @@ void orc_tgv_fields(const orc_cfg *g, double U0, double rho0, double T0, double 
         u[2 * nn + n] = 0.0;
         rho[n] = rho0 * (1.0 + C / 16.0 * (cos(2 * x) + cos(2 * y)) * (cos(2 * z) + 2.0));
         T[n] = T0;
+    }
+    for (d = 0; d < 3; ++d) free(xs[d]);
+}
+
+/* One step from the Taylor-Green equilibrium state, evaluated only at the listed nodes:
+ * the initial populations are f_i^eq and (2C_v - D) T f_i^eq of the Sec. III.C fields,
+ * computed on demand at each support point a departure cell needs; the streamed values
+ * then go through the collision.  out[k*90 + q] is population q of node nodes[k] after
+ * the step.  Lets full-size runs be checked on a sample without the full state.      */
+void orc_tgv_step_sample(const orc_cfg *g, double U0, double rho0, double T0, double C,
+                         int nsample, const long *nodes, double *out)
+{
+    const int p = g->p;
+    const int N[3] = {g->cells[0] * p, g->cells[1] * p, g->cells[2] * p};
+    const double gfac_c = 2.0 / (g->gamma - 1.0) - 3.0;
+    double xi[3 * ORC_Q], w[ORC_Q];
+    double *xs[3];
+    int d;
+    orc_velset(xi, w);
+    for (d = 0; d < 3; ++d) {
+        xs[d] = (double *)malloc(sizeof(double) * N[d]);
+        orc_node_coords(g, d, xs[d]);
+    }
+#pragma omp parallel for schedule(dynamic)
+    for (int k = 0; k < nsample; ++k) {
+        long n = nodes[k];
+        int node[3], base[3], i, j, kk, l;
+        double ell[3][16], f[ORC_Q], gg[ORC_Q];
+        node[0] = (int)(n % N[0]);
+        node[1] = (int)((n / N[0]) % N[1]);
+        node[2] = (int)(n / ((long)N[0] * N[1]));
+        for (i = 0; i < ORC_Q; ++i) {
+            double af = 0.0, ag = 0.0;
+            orc_departure(g, xs, node, xi + 3 * i, base, ell);
+            for (l = 0; l <= p; ++l)
+                for (kk = 0; kk <= p; ++kk)
+                    for (j = 0; j <= p; ++j) {
+                        double x = xs[0][wrap(base[0] + j, N[0])];
+                        double y = xs[1][wrap(base[1] + kk, N[1])];
+                        double z = xs[2][wrap(base[2] + l, N[2])];
+                        double u[3], rho, fe, wt = ell[0][j] * ell[1][kk] * ell[2][l];
+                        u[0] = U0 * sin(x) * cos(y) * cos(z);
+                        u[1] = -U0 * cos(x) * sin(y) * cos(z);
+                        u[2] = 0.0;
+                        rho = rho0 * (1.0 + C / 16.0 * (cos(2 * x) + cos(2 * y)) * (cos(2 * z) + 2.0));
+                        fe = orc_feq_one(xi + 3 * i, w[i], rho, u, T0);
+                        af += wt * fe;
+                        ag += wt * gfac_c * T0 * fe;
+                    }
+            f[i] = af;
+            gg[i] = ag;
+        }
+        if (g->collide) orc_collide_one(g, xi, w, f, gg);
+        for (i = 0; i < ORC_Q; ++i) {
+            out[(long)k * 2 * ORC_Q + i] = f[i];
+            out[(long)k * 2 * ORC_Q + ORC_Q + i] = gg[i];
+        }
     }
     for (d = 0; d < 3; ++d) free(xs[d]);
 }

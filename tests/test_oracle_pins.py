@@ -430,3 +430,16 @@ def test_sutherland_constants_match_paper():
     for T in (0.5, 1.0, 1.7):
         assert O.sutherland(T) == pytest.approx(g["sutherland_a"] * T ** 1.5
                                                 / (T + g["sutherland_b"]), rel=1e-15)
+
+
+def test_sampled_tgv_step_matches_full_step():
+    """The on-demand (sampled) Taylor-Green step used for full-size checks agrees with the
+    full-grid step on a small mesh (same departure search and collision)."""
+    Ma, gam, Re = 0.5, 1.4, 1600.0
+    U0 = Ma * math.sqrt(gam)
+    g = O.Grid(cells=(3, 2, 4), p=3, dt=0.2, mu_inf=U0 / Re, pr_correction=True)
+    rho, u, T = O.tgv_fields(g, U0)
+    full = O.step(g, O.init_fields(g, rho, u, T), 1).reshape(90, -1)
+    nodes = np.array([0, 5, 77, g.nodes - 1, 123])
+    samp = O.tgv_step_sample(g, nodes, U0)
+    assert np.allclose(samp, full[:, nodes].T, rtol=1e-13, atol=1e-15)

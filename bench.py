@@ -1,0 +1,363 @@
+"""Throughput benchmark of the fused SLLBM step (node-updates/s) on synthetic
+Taylor-Green input.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+                  [--workload tgv_32c_p4] [--storage f32|f64]
+
+One "step" is one SLLBM time step over the whole mesh: one launch of the fused kernel
+(streaming of all 90 populations, moments, equilibrium, collision).  The default
+workload is the 32^3-cell, p = 4 (128^3 nodes) Taylor-Green vortex at Ma 0.5, Re 1600,
+Courant number 4, FP32 storage.  Each population buffer (755 MB) is larger than the
+129 MB L2, so no L2 flush is needed between steps.  With N > 1 (torchrun) every rank
+runs an independent replica (the path is not sharded across GPUs: replicas only).
+
+--impl reference times the FP64 CPU oracle (tests-only code) on the host cores on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2012_05537_gb300 import inputs as I  # noqa: E402
+
+METRIC = "node-updates/s (×45 pops) vs HBM roofline; mixed vs FP64 at stated error"
+UNIT = "node-updates/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
+    ap.add_argument("--workload", default="tgv_32c_p4", choices=sorted(I.WORKLOADS))
+    ap.add_argument("--storage", choices=["f32", "f64"], default=None)
+    ap.add_argument("--e2e-steps", type=int, default=40)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    csrc = os.path.join(ROOT, "paper_2012_05537_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in ("step_kernel.cuh", "collide.cuh", "sllbm_internal.h", "step_f32.cu", "step_f64.cu"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str, storage: str):
+    """DRAM bytes per launch recorded from an ncu capture of the current kernel source,
+    or None if no summary matches the current source hash."""
+    path = os.path.join(ROOT, "profiles", f"step_{storage}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_hash = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
+    m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_bytes.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+def oracle_sample_rate(w: I.Workload, min_seconds: float = 8.0):
+    """Oracle node-updates/s on a periodic sub-box of the workload: same cell size h, p,
+    dt, Ma, Re; 6 x 6 x 6 cells; Taylor-Green initial fields at those coordinates."""
+    import numpy as np
+
+    import oracle as O
+    h = 2 * math.pi / w.cells[0]
+    sub = (6, 6, 6)
+    g = O.Grid(cells=sub, p=w.p, dt=w.dt(), mu_inf=w.mu_inf, gamma=w.gamma, Pr=w.Pr,
+               pr_correction=w.pr_correction, L=tuple(c * h for c in sub))
+    pop = O.init_fields(g, *O.tgv_fields(g, w.U0))
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        pop = O.step(g, pop, 1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds:
+            break
+    assert np.isfinite(pop).all()
+    return g.nodes * steps / el, O.num_threads(), (
+        f"{steps} oracle step(s) on a periodic 6^3-cell sub-box ({g.nodes} nodes) of {w.name} "
+        f"(same h, p={w.p}, dt, Ma, Re); FP64; {el:.1f} s")
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle, rank 0 only."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle as O
+    w = I.WORKLOADS[args.workload]
+    h = 2 * math.pi / w.cells[0]
+    sub = (3, 3, 2)  # bounded sample per step so that K steps stay within minutes
+    g = O.Grid(cells=sub, p=w.p, dt=w.dt(), mu_inf=w.mu_inf, gamma=w.gamma, Pr=w.Pr,
+               pr_correction=w.pr_correction, L=tuple(c * h for c in sub))
+    pop = O.init_fields(g, *O.tgv_fields(g, w.U0))
+    pop = O.step(g, pop, max(0, args.warmup))
+    t0 = time.perf_counter()
+    pop = O.step(g, pop, args.steps)
+    el = time.perf_counter() - t0
+    assert np.isfinite(pop).all()
+    value = g.nodes * args.steps / el
+    sample = (f"each step: one oracle step on a periodic 3x3x2-cell sub-box ({g.nodes} nodes) of "
+              f"{w.name} (same h, p, dt, Ma, Re); FP64 CPU")
+    cores = O.num_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "note": w.note},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_steps(sim, torch, steps, per_launch=True):
+    """Times `steps` single-step launches on the context's stream with CUDA events."""
+    stream = sim.stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)] if per_launch else []
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for k in range(steps):
+        if per_launch:
+            ev[k][0].record(stream)
+        rc = sim.step(1)
+        if rc != 0:
+            raise RuntimeError(f"sllbm_step returned {rc}")
+        if per_launch:
+            ev[k][1].record(stream)
+    end.record(stream)
+    torch.cuda.synchronize()
+    total_ms = start.elapsed_time(end)
+    kern = [a.elapsed_time(b) for a, b in ev] if per_launch else []
+    return total_ms, kern
+
+
+def run_mine(args, rank, world, local):
+    import torch
+
+    from paper_2012_05537_gb300 import build as B
+    from paper_2012_05537_gb300 import sllbm as S
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        B.build()
+    if dist is not None:
+        dist.barrier()
+    S.load()
+    w = I.WORKLOADS[args.workload]
+    storage = args.storage or w.storage
+    cfg = S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, Pr=w.Pr, gamma=w.gamma,
+                   courant=w.courant, pr_correction=w.pr_correction, storage=storage)
+    sim = S.Sim(cfg, device=f"cuda:{local}")
+    sim.init_tgv()
+    for _ in range(max(3, args.warmup)):
+        sim.step(1)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = sim.launches()
+    total_ms, kern = time_steps(sim, torch, args.steps)
+    launches = sim.launches() - launches0
+    torch.cuda.synchronize()
+    if dist is not None:
+        t = torch.tensor([total_ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    clk = clocks.stop()
+    _, _, T = sim.moments()
+    finite = bool(torch.isfinite(T).all().item())
+
+    nodes = sim.nodes
+    value = nodes * args.steps * world / (total_ms / 1e3)
+    elem = 8 if storage == "f64" else 4
+    bytes_per_node = 2 * 45 * 2 * elem  # read + write of f and g
+    kern_avg_ms = statistics.mean(kern)
+    hbm, peak_src = measured_peaks()
+    achieved = bytes_per_node * nodes / (kern_avg_ms / 1e3) / 1e9
+    traffic = profiled_traffic(w.name, storage)
+
+    # end to end through the C ABI with host buffers: H2D of the state, one step, D2H
+    e2e = None
+    if args.e2e_steps > 0:
+        nb = int(sim.info.pop_bytes)
+        host_in = torch.empty(nb, dtype=torch.uint8).pin_memory()
+        host_out = torch.empty(nb, dtype=torch.uint8).pin_memory()
+        host_in.copy_(sim.raw_state().view(torch.uint8).reshape(-1).cpu())
+        sim.run_host(host_in, host_out, 1)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            sim.run_host(host_in, host_out, 1)
+        el = time.perf_counter() - t0
+        e2e = {"value": nodes * args.e2e_steps * world / el, "unit": UNIT,
+               "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
+               "steps": args.e2e_steps}
+
+    variants = {}
+    if not args.no_variants and rank == 0 and storage == "f32":
+        # FP64 storage/arithmetic on the same workload (FP64-ALU bound on this part)
+        sim64 = S.Sim(S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, Pr=w.Pr, gamma=w.gamma,
+                               courant=w.courant, pr_correction=w.pr_correction, storage="f64"),
+                      device=f"cuda:{local}")
+        sim64.init_tgv()
+        sim64.step(3)
+        n64 = 20
+        t64, k64 = time_steps(sim64, torch, n64)
+        variants["f64"] = {"value": nodes * n64 / (t64 / 1e3), "ms_per_step": t64 / n64,
+                           "kernel_ms": statistics.mean(k64),
+                           "hbm_gbs_equiv": 2 * 45 * 2 * 8 * nodes / (statistics.mean(k64) / 1e3) / 1e9,
+                           "steps": n64}
+        sim64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, sample = oracle_sample_rate(w)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": storage, "data": "synthetic",
+            "config": {"workload": w.name, "cells": list(w.cells), "p": w.p,
+                       "nodes": nodes, "Ma": w.Ma, "Re": w.Re, "courant": w.courant,
+                       "dt": sim.dt, "storage": storage,
+                       "l2": f"inputs larger than L2 ({sim.info.pop_bytes / 1e6:.0f} MB per buffer)",
+                       "parallelism": f"replicas x{world}",
+                       "population_updates_per_s": value * 45},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": traffic,
+                         "peak_source": peak_src, "kernel_ms": kern_avg_ms,
+                         "algorithmic_bytes_per_node": bytes_per_node},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "finite": finite,
+        }
+        if variants:
+            line["variants"] = variants
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_mine(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

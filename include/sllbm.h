@@ -1,0 +1,206 @@
+/*
+ * sllbm.h -- C ABI of the GB300 semi-Lagrangian lattice Boltzmann step library
+ * (libsllbm.so).  Implements the per-time-step fused update of the compressible
+ * 3D SLLBM of arXiv:2012.05537 (Wilde, Kraemer, Reith, Foysi) with the 45-velocity
+ * degree-9 cubature set: semi-Lagrangian streaming by cell-oriented Lagrange
+ * interpolation on Gauss-Lobatto-Chebyshev support points (Sec. II.A, Eq.
+ * interpolation), moments (Eq. moments), fourth-order Hermite equilibrium (Eq.
+ * discreteEquilibrium, App. A, App. B), the second energy population g, pressure-
+ * dependent relaxation time with Sutherland viscosity (Sec. II.A, Sec. III.C), BGK
+ * collision (Eq. LBM) and the optional quasi-equilibrium Prandtl term (App. D).
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ *  Units      lattice units with c_s^2 = T_ref = 1; the Hermite tensors use xi/c_s.
+ *  Mesh       periodic, uniform hexahedral cells, cells[d] per direction on
+ *             [0, L[d]); order-p Gauss-Lobatto-Chebyshev support points, p in {2,3,4};
+ *             N[d] = cells[d]*p unique nodes per direction (a cell's right-face nodes
+ *             are the next cell's left-face nodes).  Node (x,y,z) has index
+ *             n = (z*N[1] + y)*N[0] + x (x fastest); along a direction the node
+ *             c*p + a (a in [0,p)) sits at c*h + (1 - cos(pi a/p)) h/2, h = L/cells.
+ *  Velocities the 45 abscissae in the order returned by sllbm_velset_table():
+ *             origin; icosahedron |xi|=sqrt(3); dodecahedron |xi|=3; icosahedron
+ *             |xi|=sqrt(15).
+ *  Populations one buffer holds 2*45 fields, pop[h][i][z][y][x] with h = 0 for f and
+ *             h = 1 for g, each field N[0]*N[1]*N[2] elements of the storage type
+ *             (SLLBM_F64: double, SLLBM_F32: float).  The stored state is the
+ *             post-collision population; sllbm_step() streams it (pull, departure
+ *             point x - dt*xi_i) and collides the result, ping-ponging two buffers.
+ *  Streams    every call that touches the GPU is enqueued on the CUDA stream given
+ *             to sllbm_create() and is asynchronous unless stated otherwise.
+ *  Errors     every int-returning call returns SLLBM_OK (0) or a negative SLLBM_E*
+ *             code; no call aborts the process.  After SLLBM_ECUDA the CUDA error is
+ *             kept in the context (sllbm_last_cuda_error).
+ *  Ownership  the context owns its small tables (and, if no buffers were given, its
+ *             population buffers).  Buffers given to sllbm_set_buffers() stay owned by
+ *             the caller and must outlive the context's use of them.
+ */
+#ifndef SLLBM_H
+#define SLLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SLLBM_OK 0
+#define SLLBM_EINVAL (-1)     /* bad argument (size, order, null pointer, ...) */
+#define SLLBM_ENOMEM (-2)     /* device or host allocation failed */
+#define SLLBM_ECUDA (-3)      /* a CUDA runtime call failed; see sllbm_last_cuda_error */
+#define SLLBM_ENONFINITE (-4) /* non-finite or non-positive rho/T seen by the step check */
+#define SLLBM_ETIMEOUT (-5)   /* a bounded device-side wait gave up */
+#define SLLBM_ENOTREADY (-6)  /* population buffers not set or not initialised */
+
+typedef struct sllbm_ctx sllbm_ctx; /* opaque */
+
+/* Periodic uniform hexahedral mesh (Sec. III.C uses the triply periodic [0,2 pi]^3). */
+typedef struct {
+    int cells[3];  /* cells per direction, >= 1 */
+    double L[3];   /* domain lengths */
+} sllbm_mesh;
+
+typedef enum { SLLBM_D3Q45 = 0 } sllbm_velset;
+
+typedef enum {
+    SLLBM_F64 = 0, /* double populations, FP64 arithmetic */
+    SLLBM_F32 = 1  /* float populations, FP32 arithmetic */
+} sllbm_storage;
+
+/* Physical and run parameters.  Taylor-Green scaling (Sec. III.C): U0 = Ma*sqrt(gamma*T0),
+ * mu_inf = rho0*U0*1/Re (reference length 1), unless mu_inf_override > 0. */
+typedef struct {
+    double Ma;              /* Mach number of the Taylor-Green initial field */
+    double Re;              /* Reynolds number, Re = U0 L / nu_inf with L = 1 */
+    double Pr;              /* Prandtl number used by the App. D term */
+    double gamma;           /* heat capacity ratio; C_v = 1/(gamma-1) */
+    double T0;              /* uniform initial temperature of the TGV field */
+    double rho0;            /* reference density of the TGV field */
+    double dt_or_courant;   /* time step dt, or Courant number if dt_is_courant */
+    int dt_is_courant;      /* 1: dt = C * min_d(L[d]/N[d]) / max_i|xi_i| (C = Courant number) */
+    int pr_correction;      /* 1: apply the quasi-equilibrium Prandtl term (App. D) */
+    sllbm_storage storage;  /* population storage / arithmetic type */
+    int nonfinite_check;    /* 1: the step kernel flags non-finite rho or T */
+    double tgv_C;           /* density numerator C of the TGV field; < 0 selects gamma*Ma^2 */
+    double mu_inf_override; /* > 0: use this mu_inf instead of rho0*U0/Re */
+    int collide;            /* 1: stream and collide (normal); 0: stream only */
+} sllbm_params;
+
+/* Read-only description of a created context. */
+typedef struct {
+    int N[3];          /* nodes per direction */
+    int p;             /* polynomial order */
+    int64_t nodes;     /* N[0]*N[1]*N[2] */
+    int Q;             /* 45 */
+    double dt;         /* time step */
+    double U0;         /* TGV velocity amplitude */
+    double mu_inf;     /* reference dynamic viscosity */
+    double max_xi;     /* largest |xi_i| */
+    size_t pop_bytes;  /* bytes of one population buffer (2*Q*nodes*sizeof(storage)) */
+    int storage;       /* sllbm_storage */
+    int max_cell_shift;/* largest |departure cell shift| over velocities and directions */
+} sllbm_info_t;
+
+/* Fills p_out with the defaults used for the paper's Re = 1600 Taylor-Green runs
+ * (Sec. III.C): Ma 0.5, Re 1600, Pr 0.7, gamma 1.4, T0 = rho0 = 1, Courant 1,
+ * Prandtl term off, FP32 storage, collide on. */
+void sllbm_default_params(sllbm_params *p_out);
+
+/* Creates a context: validates mesh/order/params, builds the velocity set, the GLC
+ * support points and the per-velocity separable interpolation tables (departure cell
+ * shift and p+1 Lagrange weights per velocity, direction and local node index; the
+ * uniform-mesh reduction of the matrices Psi_i, Sec. IV.B), and records the stream
+ * (cudaStream_t passed as void*, NULL = legacy default stream).  Allocates nothing
+ * large on the device.  Errors: SLLBM_EINVAL (cells < 1, p not in {2,3,4}, dt <= 0,
+ * a departure shift beyond 100 cells, unknown storage), SLLBM_ENOMEM, SLLBM_ECUDA. */
+int sllbm_create(const sllbm_mesh *mesh, int p, sllbm_velset vs, const sllbm_params *prm,
+                 void *cuda_stream, sllbm_ctx **out);
+
+/* Frees everything the context owns (not caller buffers). NULL is accepted. */
+void sllbm_destroy(sllbm_ctx *ctx);
+
+/* Copies the context description into *info. */
+int sllbm_get_info(const sllbm_ctx *ctx, sllbm_info_t *info);
+
+/* Velocity set (Sec. II.B): xi[45*3] (row-major, x,y,z) and w[45], host pointers. */
+int sllbm_velset_table(const sllbm_ctx *ctx, double *xi, double *w);
+
+/* Gives the context two device buffers of pop_bytes each (caller-owned, e.g. torch
+ * tensors); popA becomes the current state.  bytes < pop_bytes -> SLLBM_EINVAL.
+ * If never called, sllbm_init_* allocates two buffers owned by the context. */
+int sllbm_set_buffers(sllbm_ctx *ctx, void *popA, void *popB, size_t bytes);
+
+/* Device pointer to the buffer holding the current state (NULL before init). */
+void *sllbm_current_buffer(const sllbm_ctx *ctx);
+
+/* Taylor-Green initialisation (Sec. III.C, constant-temperature initial condition):
+ * f_i = f_i^eq(rho, u, T0), g_i = (2C_v - D) T0 f_i^eq at every node, computed in FP64. */
+int sllbm_init_tgv(sllbm_ctx *ctx);
+
+/* Equilibrium initialisation from given FP64 fields rho[nodes], u[3][nodes], T[nodes]
+ * (host pointers if on_device == 0, device pointers otherwise). */
+int sllbm_init_fields(sllbm_ctx *ctx, const double *rho, const double *u, const double *T,
+                      int on_device);
+
+/* Sets the current state from FP64 populations pop[2][45][nodes] (host or device),
+ * rounding to the storage type. */
+int sllbm_set_populations(sllbm_ctx *ctx, const double *pop, int on_device);
+
+/* Copies the current state to FP64 pop[2][45][nodes] (host or device).  Synchronous
+ * when on_device == 0. */
+int sllbm_get_populations(sllbm_ctx *ctx, double *pop, int on_device);
+
+/* Advances n >= 0 time steps: each step is one launch of the fused kernel (pull
+ * streaming of all 90 populations, moments, equilibrium, BGK [+ Prandtl term]),
+ * alternating the two buffers.  Asynchronous.  With nonfinite_check on, the
+ * check flag is read back (synchronising) after the last step and SLLBM_ENONFINITE
+ * is returned if any node had non-finite or non-positive rho or T. */
+int sllbm_step(sllbm_ctx *ctx, int n);
+
+/* Density, velocity and temperature of the current state, Eq. (moments), FP64:
+ * rho[nodes], u[3][nodes], T[nodes]; host pointers (synchronous) if on_device == 0. */
+int sllbm_moments(sllbm_ctx *ctx, double *rho, double *u, double *T, int on_device);
+
+/* Sec. III.C diagnostics of the current state, volume-averaged, FP64, host outputs:
+ * Ek = <rho|u|^2/2>/(rho0 U0^2), eps_s = <mu/mu_inf |curl u|^2>/(rho0 Re U0^2),
+ * eps_c = (4/3)<mu/mu_inf (div u)^2>/(rho0 Re U0^2), with per-cell Clenshaw-Curtis
+ * quadrature on the support points and cell-local Lagrange derivatives.
+ * Synchronous.  Uses a context-owned device scratch buffer (allocated on first use). */
+int sllbm_diag(sllbm_ctx *ctx, double *Ek, double *eps_s, double *eps_c);
+
+/* End-to-end call with HOST buffers: copies pop_in (pop_bytes, storage type, host
+ * memory; pinned for full speed) to the device, advances n steps, copies the result
+ * to pop_out (host) and synchronises the stream. */
+int sllbm_run_host(sllbm_ctx *ctx, const void *pop_in, void *pop_out, int n);
+
+/* Waits for all work the context enqueued. */
+int sllbm_sync(sllbm_ctx *ctx);
+
+/* Last CUDA error code seen by the context (cudaError_t as int, 0 if none). */
+int sllbm_last_cuda_error(const sllbm_ctx *ctx);
+
+/* Number of kernel launches the context has issued so far (all kernels). */
+int64_t sllbm_launch_count(const sllbm_ctx *ctx);
+
+/* Host-only, needs no context or GPU: the 45 abscissae xi[45*3] and weights w[45] of the
+ * degree-9 cubature set (Sec. II.B, Fig. 2) in the canonical order described above. */
+int sllbm_velset_d3q45(double *xi, double *w);
+
+/* Host-only, needs no context or GPU: the precomputed streaming table of one direction
+ * `dir` (0,1,2) for order p, cell size h and time step dt -- the uniform-mesh form of the
+ * departure search and of the interpolation matrices Psi_i (Sec. II.A, Sec. IV.B).  For
+ * velocity i and local node a in [0,p) the departure point of node c*p + a lies in cell
+ * c + shift[i*p + a] at the reference coordinate whose Lagrange weights on the cell's
+ * GLC points are weights[(i*p + a)*(p+1) + j], j = 0..p.  Arrays are caller-owned with
+ * 45*p and 45*p*(p+1) entries.  SLLBM_EINVAL for p not in {2,3,4}, h <= 0 or dt < 0. */
+int sllbm_stream_table(int p, double h, double dt, int dir, int *shift, double *weights);
+
+/* Static description of an error code. */
+const char *sllbm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLLBM_H */

@@ -1,0 +1,750 @@
+// C ABI of the SLLBM step library (declared in include/sllbm.h) and its auxiliary
+// kernels: equilibrium initialisation, population conversion, moments, diagnostics.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "collide.cuh"
+#include "sllbm_internal.h"
+#include "tables.h"
+
+using namespace sllbm;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+struct VelConst {
+    double xi[kQ][3];
+    double w[kQ];
+};
+
+VelConst vel_const(const sllbm_ctx* ctx) {
+    VelConst v;
+    std::memcpy(v.xi, ctx->xi, sizeof(v.xi));
+    std::memcpy(v.w, ctx->w, sizeof(v.w));
+    return v;
+}
+
+int fail(sllbm_ctx* ctx, cudaError_t e) {
+    if (ctx) ctx->last_err = static_cast<int>(e);
+    return SLLBM_ECUDA;
+}
+
+#define CK(ctx, call)                                        \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return fail((ctx), e_);       \
+    } while (0)
+
+unsigned grid_for(long long n, int block) {
+    long long g = (n + block - 1) / block;
+    if (g > 1048576) g = 1048576;
+    if (g < 1) g = 1;
+    return static_cast<unsigned>(g);
+}
+
+// ---------------------------------------------------------------- initialisation
+// f_i = f_i^eq(rho, u, T), g_i = (2C_v - D) T f_i^eq, in FP64 (Eq. discreteEquilibrium).
+// mode 0: Taylor-Green fields of Sec. III.C at the node coordinates; mode 1: given fields.
+template <typename S>
+__global__ void init_eq_kernel(S* __restrict__ pop, long long nn, int Nx, int Ny,
+                               const double* __restrict__ cx, const double* __restrict__ cy,
+                               const double* __restrict__ cz, int mode, double U0, double rho0,
+                               double T0, double C, const double* __restrict__ rho_f,
+                               const double* __restrict__ u_f, const double* __restrict__ T_f,
+                               double gfac, const __grid_constant__ VelConst vc) {
+    for (long long n = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; n < nn;
+         n += static_cast<long long>(gridDim.x) * blockDim.x) {
+        double rho, ux, uy, uz, T;
+        if (mode == 0) {
+            const int ix = static_cast<int>(n % Nx);
+            const int iy = static_cast<int>((n / Nx) % Ny);
+            const int iz = static_cast<int>(n / (static_cast<long long>(Nx) * Ny));
+            const double x = cx[ix], y = cy[iy], z = cz[iz];
+            ux = U0 * sin(x) * cos(y) * cos(z);
+            uy = -U0 * cos(x) * sin(y) * cos(z);
+            uz = 0.0;
+            rho = rho0 * (1.0 + C / 16.0 * (cos(2.0 * x) + cos(2.0 * y)) * (cos(2.0 * z) + 2.0));
+            T = T0;
+        } else {
+            rho = rho_f[n];
+            ux = u_f[n];
+            uy = u_f[nn + n];
+            uz = u_f[2 * nn + n];
+            T = T_f[n];
+        }
+        const EqCoef<double> ec = eq_coefficients(ux * ux + uy * uy + uz * uz, T - 1.0);
+#pragma unroll 5
+        for (int i = 0; i < kQ; ++i) {
+            const double s = vc.xi[i][0] * ux + vc.xi[i][1] * uy + vc.xi[i][2] * uz;
+            const double feq = vc.w[i] * rho * eq_poly(ec, shell_of(i), s);
+            pop[i * nn + n] = static_cast<S>(feq);
+            pop[(kQ + i) * nn + n] = static_cast<S>(gfac * T * feq);
+        }
+    }
+}
+
+template <typename A, typename B>
+__global__ void convert_kernel(const A* __restrict__ in, B* __restrict__ out, long long count) {
+    for (long long k = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; k < count;
+         k += static_cast<long long>(gridDim.x) * blockDim.x)
+        out[k] = static_cast<B>(in[k]);
+}
+
+// ---------------------------------------------------------------- moments
+template <typename S>
+__global__ void moments_kernel(const S* __restrict__ pop, long long nn, double inv_2cv,
+                               double* __restrict__ rho_o, double* __restrict__ u_o,
+                               double* __restrict__ T_o, const __grid_constant__ VelConst vc) {
+    for (long long n = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; n < nn;
+         n += static_cast<long long>(gridDim.x) * blockDim.x) {
+        double rho = 0, mx = 0, my = 0, mz = 0, e2 = 0;
+#pragma unroll 5
+        for (int i = 0; i < kQ; ++i) {
+            const double f = static_cast<double>(pop[i * nn + n]);
+            rho += f;
+            mx += f * vc.xi[i][0];
+            my += f * vc.xi[i][1];
+            mz += f * vc.xi[i][2];
+            e2 += f * shell_xi2(shell_of(i)) + static_cast<double>(pop[(kQ + i) * nn + n]);
+        }
+        const double ux = mx / rho, uy = my / rho, uz = mz / rho;
+        rho_o[n] = rho;
+        u_o[n] = ux;
+        u_o[nn + n] = uy;
+        u_o[2 * nn + n] = uz;
+        T_o[n] = (e2 / rho - (ux * ux + uy * uy + uz * uz)) * inv_2cv;
+    }
+}
+
+// ---------------------------------------------------------------- diagnostics
+struct DiagConst {
+    double xi[kQ][3];
+    double W[kMaxP + 1];
+    double D[kMaxP + 1][kMaxP + 1];
+};
+
+// Per cell: rho, u, T at its (p+1)^3 support points, gradients from the cell-local
+// Lagrange polynomials, Clenshaw-Curtis quadrature of rho|u|^2/2, mu~|curl u|^2 and
+// mu~(div u)^2 (Sec. III.C).  Grid-stride over cells; one FP64 partial triple per block.
+template <typename S, int P>
+__global__ void __launch_bounds__(128) diag_kernel(const S* __restrict__ pop, long long nn, int Nx, int Ny,
+                                                   int Nz, int ncx, int ncy, long long ncell, double inv_2cv,
+                                                   double hx, double hy, double hz,
+                                                   const __grid_constant__ DiagConst dc,
+                                                   double* __restrict__ partials) {
+    constexpr int P1 = P + 1;
+    constexpr int NPC = P1 * P1 * P1;
+    __shared__ double su[3][NPC];
+    __shared__ double red[3][4];
+    double acc0 = 0, acc1 = 0, acc2 = 0;
+    const int t = threadIdx.x;
+    const int ia = t % P1, ib = (t / P1) % P1, ic = t / (P1 * P1);
+    for (long long cell = blockIdx.x; cell < ncell; cell += gridDim.x) {
+        const int cx = static_cast<int>(cell % ncx);
+        const int cy = static_cast<int>((cell / ncx) % ncy);
+        const int cz = static_cast<int>(cell / (static_cast<long long>(ncx) * ncy));
+        double rho = 0, T = 0, ux = 0, uy = 0, uz = 0;
+        if (t < NPC) {
+            const int nx = (cx * P + ia) % Nx, ny = (cy * P + ib) % Ny, nz = (cz * P + ic) % Nz;
+            const long long n = (static_cast<long long>(nz) * Ny + ny) * Nx + nx;
+            double mx = 0, my = 0, mz = 0, e2 = 0;
+            for (int i = 0; i < kQ; ++i) {
+                const double f = static_cast<double>(pop[i * nn + n]);
+                rho += f;
+                mx += f * dc.xi[i][0];
+                my += f * dc.xi[i][1];
+                mz += f * dc.xi[i][2];
+                e2 += f * shell_xi2(shell_of(i)) + static_cast<double>(pop[(kQ + i) * nn + n]);
+            }
+            ux = mx / rho;
+            uy = my / rho;
+            uz = mz / rho;
+            T = (e2 / rho - (ux * ux + uy * uy + uz * uz)) * inv_2cv;
+            su[0][t] = ux;
+            su[1][t] = uy;
+            su[2][t] = uz;
+        }
+        __syncthreads();
+        if (t < NPC) {
+            double g[3][3];  // g[comp][dir]
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                double sx = 0, sy = 0, sz = 0;
+#pragma unroll
+                for (int j = 0; j < P1; ++j) {
+                    sx += dc.D[ia][j] * su[c][(ic * P1 + ib) * P1 + j];
+                    sy += dc.D[ib][j] * su[c][(ic * P1 + j) * P1 + ia];
+                    sz += dc.D[ic][j] * su[c][(j * P1 + ib) * P1 + ia];
+                }
+                g[c][0] = sx * 2.0 / hx;
+                g[c][1] = sy * 2.0 / hy;
+                g[c][2] = sz * 2.0 / hz;
+            }
+            const double wq = dc.W[ia] * dc.W[ib] * dc.W[ic] * hx * hy * hz * 0.125;
+            const double wx = g[2][1] - g[1][2], wy = g[0][2] - g[2][0], wz = g[1][0] - g[0][1];
+            const double dv = g[0][0] + g[1][1] + g[2][2];
+            const double mut = sutherland(T);
+            acc0 += wq * 0.5 * rho * (ux * ux + uy * uy + uz * uz);
+            acc1 += wq * mut * (wx * wx + wy * wy + wz * wz);
+            acc2 += wq * mut * dv * dv;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc0 += __shfl_down_sync(0xffffffffu, acc0, o);
+        acc1 += __shfl_down_sync(0xffffffffu, acc1, o);
+        acc2 += __shfl_down_sync(0xffffffffu, acc2, o);
+    }
+    if ((t & 31) == 0) {
+        red[0][t >> 5] = acc0;
+        red[1][t >> 5] = acc1;
+        red[2][t >> 5] = acc2;
+    }
+    __syncthreads();
+    if (t < 3) {
+        double s = 0;
+        for (int w = 0; w < 4; ++w) s += red[t][w];
+        partials[blockIdx.x * 3 + t] = s;
+    }
+}
+
+// Fixed-order sum of the per-block partial triples (deterministic).
+__global__ void sum_partials_kernel(const double* __restrict__ partials, int nblocks,
+                                    double* __restrict__ out) {
+    __shared__ double red[3][256];
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        s0 += partials[3 * b];
+        s1 += partials[3 * b + 1];
+        s2 += partials[3 * b + 2];
+    }
+    red[0][threadIdx.x] = s0;
+    red[1][threadIdx.x] = s1;
+    red[2][threadIdx.x] = s2;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+            for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) out[threadIdx.x] = red[threadIdx.x][0];
+}
+
+int ensure_buffers(sllbm_ctx* ctx) {
+    if (ctx->buf[0] != nullptr) return SLLBM_OK;
+    for (int b = 0; b < 2; ++b) {
+        cudaError_t e = cudaMalloc(&ctx->buf[b], ctx->pop_bytes);
+        if (e != cudaSuccess) {
+            ctx->last_err = static_cast<int>(e);
+            return SLLBM_ENOMEM;
+        }
+    }
+    ctx->own_buf = true;
+    ctx->cur = 0;
+    return SLLBM_OK;
+}
+
+int launch_init(sllbm_ctx* ctx, int mode, const double* rho, const double* u, const double* T) {
+    int rc = ensure_buffers(ctx);
+    if (rc != SLLBM_OK) return rc;
+    const int block = 256;
+    const unsigned grid = grid_for(ctx->nn, block);
+    const double gfac = 2.0 / (ctx->prm.gamma - 1.0) - 3.0;
+    const double U0 = ctx->U0, rho0 = ctx->prm.rho0, T0 = ctx->prm.T0, C = ctx->tgv_C;
+    void* dst = ctx->buf[ctx->cur];
+    if (ctx->prm.storage == SLLBM_F64)
+        init_eq_kernel<double><<<grid, block, 0, ctx->stream>>>(
+            static_cast<double*>(dst), ctx->nn, ctx->N[0], ctx->N[1], ctx->d_coords[0], ctx->d_coords[1],
+            ctx->d_coords[2], mode, U0, rho0, T0, C, rho, u, T, gfac, vel_const(ctx));
+    else
+        init_eq_kernel<float><<<grid, block, 0, ctx->stream>>>(
+            static_cast<float*>(dst), ctx->nn, ctx->N[0], ctx->N[1], ctx->d_coords[0], ctx->d_coords[1],
+            ctx->d_coords[2], mode, U0, rho0, T0, C, rho, u, T, gfac, vel_const(ctx));
+    ctx->launches += 1;
+    CK(ctx, cudaGetLastError());
+    ctx->initialised = true;
+    return SLLBM_OK;
+}
+
+template <int P>
+int launch_diag_p(sllbm_ctx* ctx, const void* pop, double* d_out) {
+    const long long ncell = static_cast<long long>(ctx->cells[0]) * ctx->cells[1] * ctx->cells[2];
+    DiagConst dc;
+    std::memcpy(dc.xi, ctx->xi, sizeof(dc.xi));
+    double W[kMaxP + 1];
+    clenshaw_curtis(P, W);
+    for (int j = 0; j <= kMaxP; ++j) dc.W[j] = j <= P ? W[j] : 0.0;
+    double D[kMaxP + 1][kMaxP + 1];
+    diff_matrix(P, D);
+    for (int a = 0; a <= kMaxP; ++a)
+        for (int j = 0; j <= kMaxP; ++j) dc.D[a][j] = (a <= P && j <= P) ? D[a][j] : 0.0;
+    const double inv_2cv = 0.5 * (ctx->prm.gamma - 1.0);
+    const int nb = ctx->partial_blocks;
+    if (ctx->prm.storage == SLLBM_F64)
+        diag_kernel<double, P><<<nb, 128, 0, ctx->stream>>>(
+            static_cast<const double*>(pop), ctx->nn, ctx->N[0], ctx->N[1], ctx->N[2], ctx->cells[0],
+            ctx->cells[1], ncell, inv_2cv, ctx->h[0], ctx->h[1], ctx->h[2], dc, ctx->d_partials);
+    else
+        diag_kernel<float, P><<<nb, 128, 0, ctx->stream>>>(
+            static_cast<const float*>(pop), ctx->nn, ctx->N[0], ctx->N[1], ctx->N[2], ctx->cells[0],
+            ctx->cells[1], ncell, inv_2cv, ctx->h[0], ctx->h[1], ctx->h[2], dc, ctx->d_partials);
+    sum_partials_kernel<<<1, 256, 0, ctx->stream>>>(ctx->d_partials, nb, d_out);
+    ctx->launches += 2;
+    CK(ctx, cudaGetLastError());
+    return SLLBM_OK;
+}
+
+}  // namespace
+
+namespace sllbm {
+
+void fill_step_args(const sllbm_ctx* ctx, const void* src, void* dst, StepArgs* a) {
+    a->src = src;
+    a->dst = dst;
+    for (int d = 0; d < 3; ++d) {
+        a->N[d] = ctx->N[d];
+        a->cells[d] = ctx->cells[d];
+        a->tiles[d] = 1;
+    }
+    a->nn = ctx->nn;
+    a->mu_over_dt = ctx->mu_inf / ctx->dt;
+    const double cv = 1.0 / (ctx->prm.gamma - 1.0);
+    a->inv_2cv = 0.5 / cv;
+    a->gfac = 2.0 * cv - 3.0;
+    a->inv_pr = 1.0 / ctx->prm.Pr;
+    a->pr = ctx->prm.pr_correction;
+    a->collide = ctx->prm.collide;
+    a->flag = ctx->prm.nonfinite_check ? ctx->d_flag : nullptr;
+}
+
+}  // namespace sllbm
+
+extern "C" {
+
+void sllbm_default_params(sllbm_params* p) {
+    if (p == nullptr) return;
+    std::memset(p, 0, sizeof(*p));
+    p->Ma = 0.5;
+    p->Re = 1600.0;
+    p->Pr = 0.7;
+    p->gamma = 1.4;
+    p->T0 = 1.0;
+    p->rho0 = 1.0;
+    p->dt_or_courant = 1.0;
+    p->dt_is_courant = 1;
+    p->pr_correction = 0;
+    p->storage = SLLBM_F32;
+    p->nonfinite_check = 0;
+    p->tgv_C = -1.0;
+    p->mu_inf_override = 0.0;
+    p->collide = 1;
+}
+
+int sllbm_create(const sllbm_mesh* mesh, int p, sllbm_velset vs, const sllbm_params* prm,
+                 void* cuda_stream, sllbm_ctx** out) {
+    if (out == nullptr) return SLLBM_EINVAL;
+    *out = nullptr;
+    if (mesh == nullptr || prm == nullptr || vs != SLLBM_D3Q45) return SLLBM_EINVAL;
+    if (p < 2 || p > 4) return SLLBM_EINVAL;
+    if (prm->storage != SLLBM_F64 && prm->storage != SLLBM_F32) return SLLBM_EINVAL;
+    if (!(prm->gamma > 1.0) || !(prm->Pr > 0.0) || !(prm->T0 > 0.0) || !(prm->rho0 > 0.0))
+        return SLLBM_EINVAL;
+    if (!(prm->dt_or_courant > 0.0)) return SLLBM_EINVAL;
+    long long nn = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (mesh->cells[d] < 1 || !(mesh->L[d] > 0.0)) return SLLBM_EINVAL;
+        if (static_cast<long long>(mesh->cells[d]) * p > (1 << 20)) return SLLBM_EINVAL;
+        nn *= static_cast<long long>(mesh->cells[d]) * p;
+    }
+    if (nn > 0x7fffffffLL) return SLLBM_EINVAL;  // per-field offsets are 32-bit
+    sllbm_ctx* c = static_cast<sllbm_ctx*>(std::calloc(1, sizeof(sllbm_ctx)));
+    if (c == nullptr) return SLLBM_ENOMEM;
+    c->p = p;
+    c->prm = *prm;
+    c->nn = nn;
+    for (int d = 0; d < 3; ++d) {
+        c->cells[d] = mesh->cells[d];
+        c->N[d] = mesh->cells[d] * p;
+        c->L[d] = mesh->L[d];
+        c->h[d] = mesh->L[d] / mesh->cells[d];
+    }
+    build_velocity_set(c->xi, c->w);
+    double mx = 0.0;
+    for (int i = 0; i < kQ; ++i)
+        mx = std::fmax(mx, std::sqrt(c->xi[i][0] * c->xi[i][0] + c->xi[i][1] * c->xi[i][1]
+                                     + c->xi[i][2] * c->xi[i][2]));
+    c->max_xi = mx;
+    if (prm->dt_is_courant) {
+        double dxn = c->L[0] / c->N[0];
+        for (int d = 1; d < 3; ++d) dxn = std::fmin(dxn, c->L[d] / c->N[d]);
+        c->dt = prm->dt_or_courant * dxn / mx;
+    } else {
+        c->dt = prm->dt_or_courant;
+    }
+    c->U0 = prm->Ma * std::sqrt(prm->gamma * prm->T0);
+    c->mu_inf = prm->mu_inf_override > 0.0 ? prm->mu_inf_override : prm->rho0 * c->U0 / prm->Re;
+    c->tgv_C = prm->tgv_C < 0.0 ? prm->gamma * prm->Ma * prm->Ma : prm->tgv_C;
+    if (!(c->mu_inf > 0.0) && prm->collide) {
+        std::free(c);
+        return SLLBM_EINVAL;
+    }
+    c->max_shift = 0;
+    bool span_ok = true;
+    for (int d = 0; d < 3; ++d) {
+        build_dir_table(p, c->h[d], c->dt, c->xi, d, &c->dir[d]);
+        for (int i = 0; i < kQ; ++i) {
+            int lo = c->dir[d].shift[i][0], hi = lo;
+            for (int a = 0; a < p; ++a) {
+                int k = c->dir[d].shift[i][a];
+                int s = std::abs(k);
+                if (s > c->max_shift) c->max_shift = s;
+                lo = k < lo ? k : lo;
+                hi = k > hi ? k : hi;
+            }
+            // the departure points of one cell's nodes span less than a cell, so at most
+            // two neighbouring cells; the kernel's source-box sizes rely on this
+            if (hi - lo > 1) span_ok = false;
+        }
+    }
+    if (c->max_shift > 100 || !span_ok) {
+        std::free(c);
+        return SLLBM_EINVAL;
+    }
+    c->elem = prm->storage == SLLBM_F64 ? sizeof(double) : sizeof(float);
+    c->pop_bytes = static_cast<size_t>(2 * kQ) * static_cast<size_t>(nn) * c->elem;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) {
+        for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
+            e = cudaMalloc(&c->d_coords[d], sizeof(double) * c->N[d]);
+            if (e != cudaSuccess) break;
+            double* x = static_cast<double*>(std::malloc(sizeof(double) * c->N[d]));
+            if (x == nullptr) {
+                e = cudaErrorMemoryAllocation;
+                break;
+            }
+            for (int cc = 0; cc < c->cells[d]; ++cc)
+                for (int a = 0; a < p; ++a)
+                    x[cc * p + a] = cc * c->h[d] + (1.0 - std::cos(kPi * a / p)) * 0.5 * c->h[d];
+            e = cudaMemcpy(c->d_coords[d], x, sizeof(double) * c->N[d], cudaMemcpyHostToDevice);
+            std::free(x);
+        }
+        if (e == cudaSuccess) e = cudaMalloc(&c->d_flag, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(c->d_flag, 0, sizeof(int));
+    }
+    if (e != cudaSuccess) {
+        int code = (e == cudaErrorMemoryAllocation) ? SLLBM_ENOMEM : SLLBM_ECUDA;
+        sllbm_destroy(c);
+        return code;
+    }
+    *out = c;
+    return SLLBM_OK;
+}
+
+void sllbm_destroy(sllbm_ctx* ctx) {
+    if (ctx == nullptr) return;
+    if (ctx->own_buf) {
+        cudaFree(ctx->buf[0]);
+        cudaFree(ctx->buf[1]);
+    }
+    for (int d = 0; d < 3; ++d) cudaFree(ctx->d_coords[d]);
+    cudaFree(ctx->d_flag);
+    cudaFree(ctx->d_partials);
+    std::free(ctx->step_blob);
+    std::free(ctx);
+}
+
+int sllbm_get_info(const sllbm_ctx* ctx, sllbm_info_t* info) {
+    if (ctx == nullptr || info == nullptr) return SLLBM_EINVAL;
+    for (int d = 0; d < 3; ++d) info->N[d] = ctx->N[d];
+    info->p = ctx->p;
+    info->nodes = ctx->nn;
+    info->Q = kQ;
+    info->dt = ctx->dt;
+    info->U0 = ctx->U0;
+    info->mu_inf = ctx->mu_inf;
+    info->max_xi = ctx->max_xi;
+    info->pop_bytes = ctx->pop_bytes;
+    info->storage = ctx->prm.storage;
+    info->max_cell_shift = ctx->max_shift;
+    return SLLBM_OK;
+}
+
+int sllbm_velset_table(const sllbm_ctx* ctx, double* xi, double* w) {
+    if (ctx == nullptr || xi == nullptr || w == nullptr) return SLLBM_EINVAL;
+    std::memcpy(xi, ctx->xi, sizeof(ctx->xi));
+    std::memcpy(w, ctx->w, sizeof(ctx->w));
+    return SLLBM_OK;
+}
+
+int sllbm_set_buffers(sllbm_ctx* ctx, void* popA, void* popB, size_t bytes) {
+    if (ctx == nullptr || popA == nullptr || popB == nullptr || popA == popB) return SLLBM_EINVAL;
+    if (bytes < ctx->pop_bytes) return SLLBM_EINVAL;
+    if (ctx->own_buf) {
+        cudaFree(ctx->buf[0]);
+        cudaFree(ctx->buf[1]);
+        ctx->own_buf = false;
+    }
+    ctx->buf[0] = popA;
+    ctx->buf[1] = popB;
+    ctx->cur = 0;
+    ctx->initialised = false;
+    return SLLBM_OK;
+}
+
+void* sllbm_current_buffer(const sllbm_ctx* ctx) {
+    if (ctx == nullptr || !ctx->initialised) return nullptr;
+    return ctx->buf[ctx->cur];
+}
+
+int sllbm_init_tgv(sllbm_ctx* ctx) {
+    if (ctx == nullptr) return SLLBM_EINVAL;
+    return launch_init(ctx, 0, nullptr, nullptr, nullptr);
+}
+
+int sllbm_init_fields(sllbm_ctx* ctx, const double* rho, const double* u, const double* T,
+                      int on_device) {
+    if (ctx == nullptr || rho == nullptr || u == nullptr || T == nullptr) return SLLBM_EINVAL;
+    if (on_device) return launch_init(ctx, 1, rho, u, T);
+    double* d = nullptr;
+    const size_t nb = sizeof(double) * static_cast<size_t>(ctx->nn);
+    cudaError_t e = cudaMalloc(&d, 5 * nb);
+    if (e != cudaSuccess) {
+        ctx->last_err = static_cast<int>(e);
+        return SLLBM_ENOMEM;
+    }
+    int rc = SLLBM_OK;
+    e = cudaMemcpyAsync(d, rho, nb, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + ctx->nn, u, 3 * nb, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + 4 * ctx->nn, T, nb, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) {
+        rc = launch_init(ctx, 1, d, d + ctx->nn, d + 4 * ctx->nn);
+        if (rc == SLLBM_OK) e = cudaStreamSynchronize(ctx->stream);
+    }
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(ctx, e);
+    return rc;
+}
+
+int sllbm_set_populations(sllbm_ctx* ctx, const double* pop, int on_device) {
+    if (ctx == nullptr || pop == nullptr) return SLLBM_EINVAL;
+    int rc = ensure_buffers(ctx);
+    if (rc != SLLBM_OK) return rc;
+    const long long count = 2LL * kQ * ctx->nn;
+    void* dst = ctx->buf[ctx->cur];
+    if (ctx->prm.storage == SLLBM_F64) {
+        CK(ctx, cudaMemcpyAsync(dst, pop, count * sizeof(double),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+        if (!on_device) CK(ctx, cudaStreamSynchronize(ctx->stream));
+    } else {
+        const double* src = pop;
+        double* tmp = nullptr;
+        if (!on_device) {
+            CK(ctx, cudaMalloc(&tmp, count * sizeof(double)));
+            cudaError_t e = cudaMemcpyAsync(tmp, pop, count * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+            if (e != cudaSuccess) {
+                cudaFree(tmp);
+                return fail(ctx, e);
+            }
+            src = tmp;
+        }
+        convert_kernel<double, float><<<grid_for(count, 256), 256, 0, ctx->stream>>>(src, static_cast<float*>(dst), count);
+        ctx->launches += 1;
+        cudaError_t e = cudaGetLastError();
+        if (tmp != nullptr) {
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+            cudaFree(tmp);
+        }
+        if (e != cudaSuccess) return fail(ctx, e);
+    }
+    ctx->initialised = true;
+    return SLLBM_OK;
+}
+
+int sllbm_get_populations(sllbm_ctx* ctx, double* pop, int on_device) {
+    if (ctx == nullptr || pop == nullptr) return SLLBM_EINVAL;
+    if (!ctx->initialised) return SLLBM_ENOTREADY;
+    const long long count = 2LL * kQ * ctx->nn;
+    const void* src = ctx->buf[ctx->cur];
+    if (ctx->prm.storage == SLLBM_F64) {
+        CK(ctx, cudaMemcpyAsync(pop, src, count * sizeof(double),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+        if (!on_device) CK(ctx, cudaStreamSynchronize(ctx->stream));
+        return SLLBM_OK;
+    }
+    double* dst = pop;
+    double* tmp = nullptr;
+    if (!on_device) {
+        CK(ctx, cudaMalloc(&tmp, count * sizeof(double)));
+        dst = tmp;
+    }
+    convert_kernel<float, double><<<grid_for(count, 256), 256, 0, ctx->stream>>>(static_cast<const float*>(src), dst, count);
+    ctx->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (tmp != nullptr) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(pop, tmp, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        cudaFree(tmp);
+    }
+    if (e != cudaSuccess) return fail(ctx, e);
+    return SLLBM_OK;
+}
+
+int sllbm_step(sllbm_ctx* ctx, int n) {
+    if (ctx == nullptr || n < 0) return SLLBM_EINVAL;
+    if (!ctx->initialised) return SLLBM_ENOTREADY;
+    if (ctx->prm.nonfinite_check) CK(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
+    for (int s = 0; s < n; ++s) {
+        const void* src = ctx->buf[ctx->cur];
+        void* dst = ctx->buf[1 - ctx->cur];
+        int rc = ctx->prm.storage == SLLBM_F64 ? launch_step_f64(ctx, src, dst) : launch_step_f32(ctx, src, dst);
+        if (rc != SLLBM_OK) return rc;
+        ctx->cur = 1 - ctx->cur;
+    }
+    if (ctx->prm.nonfinite_check) {
+        int flag = 0;
+        CK(ctx, cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        if (flag) return SLLBM_ENONFINITE;
+    }
+    return SLLBM_OK;
+}
+
+int sllbm_moments(sllbm_ctx* ctx, double* rho, double* u, double* T, int on_device) {
+    if (ctx == nullptr || rho == nullptr || u == nullptr || T == nullptr) return SLLBM_EINVAL;
+    if (!ctx->initialised) return SLLBM_ENOTREADY;
+    const size_t nb = sizeof(double) * static_cast<size_t>(ctx->nn);
+    double* d = nullptr;
+    double *dr = rho, *du = u, *dT = T;
+    if (!on_device) {
+        CK(ctx, cudaMalloc(&d, 5 * nb));
+        dr = d;
+        du = d + ctx->nn;
+        dT = d + 4 * ctx->nn;
+    }
+    const double inv_2cv = 0.5 * (ctx->prm.gamma - 1.0);
+    const void* pop = ctx->buf[ctx->cur];
+    const unsigned grid = grid_for(ctx->nn, 256);
+    if (ctx->prm.storage == SLLBM_F64)
+        moments_kernel<double><<<grid, 256, 0, ctx->stream>>>(static_cast<const double*>(pop), ctx->nn, inv_2cv,
+                                                               dr, du, dT, vel_const(ctx));
+    else
+        moments_kernel<float><<<grid, 256, 0, ctx->stream>>>(static_cast<const float*>(pop), ctx->nn, inv_2cv,
+                                                              dr, du, dT, vel_const(ctx));
+    ctx->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (!on_device) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(rho, dr, nb, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(u, du, 3 * nb, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(T, dT, nb, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        cudaFree(d);
+    }
+    if (e != cudaSuccess) return fail(ctx, e);
+    return SLLBM_OK;
+}
+
+int sllbm_diag(sllbm_ctx* ctx, double* Ek, double* eps_s, double* eps_c) {
+    if (ctx == nullptr || Ek == nullptr || eps_s == nullptr || eps_c == nullptr) return SLLBM_EINVAL;
+    if (!ctx->initialised) return SLLBM_ENOTREADY;
+    if (ctx->d_partials == nullptr) {
+        const long long ncell = static_cast<long long>(ctx->cells[0]) * ctx->cells[1] * ctx->cells[2];
+        ctx->partial_blocks = static_cast<int>(ncell < 2048 ? ncell : 2048);
+        // 3 partial sums per block, then the 3 totals
+        cudaError_t e = cudaMalloc(&ctx->d_partials, sizeof(double) * (3 * ctx->partial_blocks + 3));
+        if (e != cudaSuccess) {
+            ctx->d_partials = nullptr;
+            ctx->last_err = static_cast<int>(e);
+            return SLLBM_ENOMEM;
+        }
+    }
+    double* d_out = ctx->d_partials + 3 * ctx->partial_blocks;
+    const void* pop = ctx->buf[ctx->cur];
+    int rc = ctx->p == 2 ? launch_diag_p<2>(ctx, pop, d_out)
+           : ctx->p == 3 ? launch_diag_p<3>(ctx, pop, d_out)
+                         : launch_diag_p<4>(ctx, pop, d_out);
+    if (rc != SLLBM_OK) return rc;
+    double h[3];
+    CK(ctx, cudaMemcpyAsync(h, d_out, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    const double vol = ctx->L[0] * ctx->L[1] * ctx->L[2];
+    const double u2 = ctx->U0 * ctx->U0;
+    const double rho0 = ctx->prm.rho0;
+    *Ek = h[0] / vol / (rho0 * u2);
+    *eps_s = h[1] / vol / (rho0 * ctx->prm.Re * u2);
+    *eps_c = 4.0 / 3.0 * h[2] / vol / (rho0 * ctx->prm.Re * u2);
+    return SLLBM_OK;
+}
+
+int sllbm_run_host(sllbm_ctx* ctx, const void* pop_in, void* pop_out, int n) {
+    if (ctx == nullptr || pop_in == nullptr || pop_out == nullptr || n < 0) return SLLBM_EINVAL;
+    int rc = ensure_buffers(ctx);
+    if (rc != SLLBM_OK) return rc;
+    CK(ctx, cudaMemcpyAsync(ctx->buf[ctx->cur], pop_in, ctx->pop_bytes, cudaMemcpyHostToDevice, ctx->stream));
+    ctx->initialised = true;
+    rc = sllbm_step(ctx, n);
+    if (rc != SLLBM_OK) return rc;
+    CK(ctx, cudaMemcpyAsync(pop_out, ctx->buf[ctx->cur], ctx->pop_bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return SLLBM_OK;
+}
+
+int sllbm_sync(sllbm_ctx* ctx) {
+    if (ctx == nullptr) return SLLBM_EINVAL;
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return SLLBM_OK;
+}
+
+int sllbm_velset_d3q45(double* xi, double* w) {
+    if (xi == nullptr || w == nullptr) return SLLBM_EINVAL;
+    double x[kQ][3];
+    double ww[kQ];
+    build_velocity_set(x, ww);
+    std::memcpy(xi, x, sizeof(x));
+    std::memcpy(w, ww, sizeof(ww));
+    return SLLBM_OK;
+}
+
+int sllbm_stream_table(int p, double h, double dt, int dir, int* shift, double* weights) {
+    if (p < 2 || p > 4 || !(h > 0.0) || !(dt >= 0.0) || dir < 0 || dir > 2 || shift == nullptr
+        || weights == nullptr)
+        return SLLBM_EINVAL;
+    double x[kQ][3];
+    double ww[kQ];
+    build_velocity_set(x, ww);
+    DirTable* t = static_cast<DirTable*>(std::malloc(sizeof(DirTable)));
+    if (t == nullptr) return SLLBM_ENOMEM;
+    build_dir_table(p, h, dt, x, dir, t);
+    for (int i = 0; i < kQ; ++i)
+        for (int a = 0; a < p; ++a) {
+            shift[i * p + a] = t->shift[i][a];
+            for (int j = 0; j <= p; ++j) weights[(i * p + a) * (p + 1) + j] = t->weight[i][a][j];
+        }
+    std::free(t);
+    return SLLBM_OK;
+}
+
+int sllbm_last_cuda_error(const sllbm_ctx* ctx) { return ctx ? ctx->last_err : 0; }
+
+int64_t sllbm_launch_count(const sllbm_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+const char* sllbm_strerror(int code) {
+    switch (code) {
+    case SLLBM_OK: return "ok";
+    case SLLBM_EINVAL: return "invalid argument";
+    case SLLBM_ENOMEM: return "out of memory";
+    case SLLBM_ECUDA: return "CUDA runtime error";
+    case SLLBM_ENONFINITE: return "non-finite or non-positive density/temperature";
+    case SLLBM_ETIMEOUT: return "bounded device wait timed out";
+    case SLLBM_ENOTREADY: return "populations not initialised";
+    }
+    return "unknown error";
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// Internal definitions shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "sllbm.h"
+#include "tables.h"
+
+// The opaque context behind sllbm_ctx*.
+struct sllbm_ctx {
+    int cells[3];
+    int N[3];
+    int p;
+    double L[3];
+    double h[3];
+    long long nn;          // nodes
+    sllbm_params prm;
+    double dt, U0, mu_inf, max_xi, tgv_C;
+    double xi[sllbm::kQ][3];
+    double w[sllbm::kQ];
+    sllbm::DirTable dir[3];
+    int max_shift;
+    cudaStream_t stream;
+    int device;
+    void* buf[2];
+    int cur;               // index of the buffer holding the current state
+    bool own_buf;
+    bool initialised;
+    size_t elem;           // bytes per stored population value
+    size_t pop_bytes;
+    double* d_coords[3];   // node coordinates per direction (device)
+    int* d_flag;           // non-finite flag (device)
+    double* d_partials;    // diagnostics partial sums (device scratch)
+    int partial_blocks;
+    unsigned char* step_blob;  // StepTables<C,P> of the storage type, built on first step
+    size_t step_blob_size;
+    int last_err;
+    long long launches;
+};
+
+namespace sllbm {
+
+// Constant tables of the fused step, passed to the kernel by value (constant bank).
+// kc[i][d][a] is the departure cell shift minus kmin[i][d] (0 or 1): the source box of a
+// tile starts kmin cells away and spans span+1 extra cells.
+template <typename C, int P>
+struct StepTables {
+    C lw[kQ][3][P][P + 1];
+    signed char kc[kQ][3][P];
+    signed char kmin[kQ][3];
+    signed char span[kQ][3];
+    C xi[kQ][3];
+    C w[kQ];
+};
+
+struct StepArgs {
+    const void* src;
+    void* dst;
+    int N[3];
+    int cells[3];
+    int tiles[3];
+    long long nn;
+    double mu_over_dt;  // mu_inf / dt
+    double inv_2cv;     // 1 / (2 C_v)
+    double gfac;        // 2 C_v - D
+    double inv_pr;      // 1 / Pr
+    int pr;             // Prandtl term on
+    int collide;        // 0: stream only
+    int* flag;          // non-finite flag or nullptr
+};
+
+template <typename C, int P>
+void fill_step_tables(const sllbm_ctx* ctx, StepTables<C, P>* t) {
+    for (int i = 0; i < kQ; ++i) {
+        for (int d = 0; d < 3; ++d) {
+            int kmn = 1 << 20, kmx = -(1 << 20);
+            for (int a = 0; a < P; ++a) {
+                int k = ctx->dir[d].shift[i][a];
+                kmn = k < kmn ? k : kmn;
+                kmx = k > kmx ? k : kmx;
+            }
+            t->kmin[i][d] = static_cast<signed char>(kmn);
+            t->span[i][d] = static_cast<signed char>(kmx - kmn);
+            for (int a = 0; a < P; ++a) {
+                t->kc[i][d][a] = static_cast<signed char>(ctx->dir[d].shift[i][a] - kmn);
+                for (int j = 0; j <= P; ++j) t->lw[i][d][a][j] = static_cast<C>(ctx->dir[d].weight[i][a][j]);
+            }
+            t->xi[i][d] = static_cast<C>(ctx->xi[i][d]);
+        }
+        t->w[i] = static_cast<C>(ctx->w[i]);
+    }
+}
+
+// Step launchers, one per storage type (step_f32.cu, step_f64.cu).
+int launch_step_f32(sllbm_ctx* ctx, const void* src, void* dst);
+int launch_step_f64(sllbm_ctx* ctx, const void* src, void* dst);
+
+void fill_step_args(const sllbm_ctx* ctx, const void* src, void* dst, StepArgs* a);
+
+}  // namespace sllbm

@@ -1,0 +1,284 @@
+// Fused SLLBM time step: pull streaming of the 90 populations by separable Lagrange
+// interpolation + moments + equilibrium + BGK (+ Prandtl term), one tile per CTA.
+//
+// Data flow per CTA (tile of CX x CY x CZ cells = TX x TY x TZ nodes):
+//   * each warp owns whole populations q (f_i or g_i); for one q it gathers the source
+//     box of the tile (the tile translated by the velocity's departure cell shift, plus
+//     one cell where the shift differs between local nodes, plus the shared face) from
+//     global memory into shared memory, with periodic wrap;
+//   * three separable passes (z, then y, then x) apply the per-velocity Lagrange
+//     weights (Eq. interpolation; identical for every cell on the uniform mesh) and
+//     leave the streamed value of every tile node in the CTA's OUT[90][tile] array;
+//   * after a CTA barrier each thread takes nodes of the tile, forms rho, u, T
+//     (Eq. moments), tau (Sec. II.A, Sutherland law of Sec. III.C), the fourth-order
+//     equilibrium (Eq. discreteEquilibrium), and writes the collided f and g
+//     (Eq. LBM, App. D) to the destination buffer.
+#pragma once
+
+#include <cstdlib>
+
+#include "collide.cuh"
+#include "sllbm_internal.h"
+
+namespace sllbm {
+
+template <int CX, int CY, int CZ, int P>
+struct TileShape {
+    static constexpr int TX = CX * P, TY = CY * P, TZ = CZ * P;
+    static constexpr int TILE = TX * TY * TZ;
+    static constexpr int BX = (CX + 1) * P + 1, BY = (CY + 1) * P + 1, BZ = (CZ + 1) * P + 1;
+    static constexpr int BOX = BX * BY * BZ;   // largest source box
+    static constexpr int TMP1 = TZ * BY * BX;  // z-pass result
+};
+
+template <typename C, int P, int CX, int CY, int CZ, int NW>
+struct StepSmem {
+    using TS = TileShape<CX, CY, CZ, P>;
+    static constexpr size_t out_elems = size_t(2) * kQ * TS::TILE;
+    static constexpr size_t warp_elems = size_t(TS::BOX) + TS::TMP1;
+    static constexpr size_t warp_ints = TS::BX + TS::BY + TS::BZ;
+    static constexpr size_t bytes = (out_elems + NW * warp_elems) * sizeof(C) + NW * warp_ints * sizeof(int);
+};
+
+__device__ __forceinline__ int wrap_index(int v, int n) {
+    int r = v % n;
+    return r < 0 ? r + n : r;
+}
+
+// Moments, equilibrium and collision of one node whose streamed populations are
+// h[q*stride], q = 0..89; the result goes to dst[q*nn].
+template <typename S, typename C, int P, bool PR>
+__device__ __forceinline__ void collide_node(const C* __restrict__ h, int stride, const StepArgs& a,
+                                             const StepTables<C, P>& t, S* __restrict__ dst) {
+    C rho = 0, mx = 0, my = 0, mz = 0, e2 = 0;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const C f = h[i * stride];
+        rho += f;
+        mx += f * t.xi[i][0];
+        my += f * t.xi[i][1];
+        mz += f * t.xi[i][2];
+        e2 += f * C(shell_xi2(shell_of(i))) + h[(kQ + i) * stride];
+    }
+    const C inv_rho = C(1) / rho;
+    const C ux = mx * inv_rho, uy = my * inv_rho, uz = mz * inv_rho;
+    const C usq = ux * ux + uy * uy + uz * uz;
+    const C T = (e2 * inv_rho - usq) * C(a.inv_2cv);
+    if (a.flag != nullptr && !(rho > C(0) && T > C(0) && isfinite(rho) && isfinite(T)))
+        atomicOr(a.flag, 1);
+    const long long nn = a.nn;
+    if (!a.collide) {
+#pragma unroll 9
+        for (int q = 0; q < 2 * kQ; ++q) dst[q * nn] = static_cast<S>(h[q * stride]);
+        return;
+    }
+    // tau = mu/(P dt) + 1/2, P = rho T, mu = Sutherland(T) mu_inf  (Sec. II.A, III.C)
+    const C tau = C(a.mu_over_dt) * sutherland(T) / (rho * T) + C(0.5);
+    const C om = C(1) / tau;
+    const C gT = C(a.gfac) * T;  // g^eq = (2 C_v - D) T f^eq
+    const EqCoef<C> ec = eq_coefficients(usq, T - C(1));
+
+    // App. D: centred third moment Qbar of the streamed f (its equilibrium part is zero
+    // for this equilibrium), f*_i = (w_i/3!) Qbar : H^(3)(xi_i), g*_i = (2C_v - D) T f*_i.
+    C Qxxx = 0, Qyyy = 0, Qzzz = 0, Qxxy = 0, Qxxz = 0, Qyyx = 0, Qyyz = 0, Qzzx = 0, Qzzy = 0,
+      Qxyz = 0, ompr = 0;
+    if (PR) {
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) {
+            const C f = h[i * stride];
+            const C cx = t.xi[i][0] - ux, cy = t.xi[i][1] - uy, cz = t.xi[i][2] - uz;
+            const C fx = f * cx, fy = f * cy, fz = f * cz;
+            Qxxx += fx * cx * cx;
+            Qyyy += fy * cy * cy;
+            Qzzz += fz * cz * cz;
+            Qxxy += fx * cx * cy;
+            Qxxz += fx * cx * cz;
+            Qyyx += fy * cy * cx;
+            Qyyz += fy * cy * cz;
+            Qzzx += fz * cz * cx;
+            Qzzy += fz * cz * cy;
+            Qxyz += fx * cy * cz;
+        }
+        const C tau_pr = (tau - C(0.5)) * C(a.inv_pr) + C(0.5);
+        ompr = om - C(1) / tau_pr;
+    }
+    // contracted third moment q_a = sum_b Qbar_abb
+    const C qx = Qxxx + Qyyx + Qzzx, qy = Qxxy + Qyyy + Qzzy, qz = Qxxz + Qyyz + Qzzz;
+
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const C x = t.xi[i][0], y = t.xi[i][1], z = t.xi[i][2];
+        const C s = x * ux + y * uy + z * uz;
+        const C feq = t.w[i] * rho * eq_poly(ec, shell_of(i), s);
+        const C f = h[i * stride];
+        const C g = h[(kQ + i) * stride];
+        C fo = f + om * (feq - f);
+        C go = g + om * (gT * feq - g);
+        if (PR) {
+            // Qbar : xi xi xi over all 27 index combinations, minus 3 xi.q
+            const C cub = Qxxx * x * x * x + Qyyy * y * y * y + Qzzz * z * z * z
+                        + C(3) * (Qxxy * x * x * y + Qxxz * x * x * z + Qyyx * y * y * x
+                                  + Qyyz * y * y * z + Qzzx * z * z * x + Qzzy * z * z * y)
+                        + C(6) * Qxyz * x * y * z;
+            const C fst = t.w[i] * C(1.0 / 6.0) * (cub - C(3) * (x * qx + y * qy + z * qz));
+            fo += ompr * fst;
+            go += ompr * gT * fst;
+        }
+        dst[i * nn] = static_cast<S>(fo);
+        dst[(kQ + i) * nn] = static_cast<S>(go);
+    }
+}
+
+template <typename S, typename C, int P, int CX, int CY, int CZ, int NW, bool PR>
+__global__ void __launch_bounds__(NW * 32, 1)
+    step_kernel(const StepArgs a, const __grid_constant__ StepTables<C, P> t) {
+    using TS = TileShape<CX, CY, CZ, P>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* out = reinterpret_cast<C*>(smem_raw);
+    C* wbase = out + StepSmem<C, P, CX, CY, CZ, NW>::out_elems;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    C* box = wbase + warp * (TS::BOX + TS::TMP1);
+    C* tmp1 = box + TS::BOX;
+    int* xo = reinterpret_cast<int*>(wbase + NW * (TS::BOX + TS::TMP1)) + warp * (TS::BX + TS::BY + TS::BZ);
+    int* yo = xo + TS::BX;
+    int* zo = yo + TS::BY;
+
+    int tile = blockIdx.x;
+    const int tix = tile % a.tiles[0];
+    tile /= a.tiles[0];
+    const int tiy = tile % a.tiles[1];
+    const int tiz = tile / a.tiles[1];
+    const int c0[3] = {tix * CX, tiy * CY, tiz * CZ};
+    const int tc[3] = {min(CX, a.cells[0] - c0[0]), min(CY, a.cells[1] - c0[1]), min(CZ, a.cells[2] - c0[2])};
+    const int te[3] = {tc[0] * P, tc[1] * P, tc[2] * P};
+    const S* __restrict__ src = static_cast<const S*>(a.src);
+    const int nxy = a.N[0] * a.N[1];
+
+    for (int q = warp; q < 2 * kQ; q += NW) {
+        const int i = q < kQ ? q : q - kQ;
+        int s[3], b0[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            s[d] = (tc[d] + t.span[i][d]) * P + 1;
+            b0[d] = (c0[d] + t.kmin[i][d]) * P;
+        }
+        for (int e = lane; e < s[0]; e += 32) xo[e] = wrap_index(b0[0] + e, a.N[0]);
+        for (int e = lane; e < s[1]; e += 32) yo[e] = wrap_index(b0[1] + e, a.N[1]) * a.N[0];
+        for (int e = lane; e < s[2]; e += 32) zo[e] = wrap_index(b0[2] + e, a.N[2]) * nxy;
+        __syncwarp();
+        const S* __restrict__ sq = src + static_cast<long long>(q) * a.nn;
+        const int sxy = s[0] * s[1];
+        const int tot = sxy * s[2];
+        for (int e = lane; e < tot; e += 32) {
+            const int z = e / sxy;
+            const int r = e - z * sxy;
+            const int y = r / s[0];
+            const int x = r - y * s[0];
+            box[e] = static_cast<C>(__ldg(sq + zo[z] + yo[y] + xo[x]));
+        }
+        __syncwarp();
+        // z pass: tmp1[oz][y][x] = sum_l Lz[az][l] box[zb+l][y][x]
+        const int n1 = te[2] * sxy;
+        for (int e = lane; e < n1; e += 32) {
+            const int oz = e / sxy;
+            const int r = e - oz * sxy;
+            const int az = oz % P;
+            const int zb = (oz / P + t.kc[i][2][az]) * P;
+            C acc = 0;
+#pragma unroll
+            for (int l = 0; l <= P; ++l) acc += t.lw[i][2][az][l] * box[(zb + l) * sxy + r];
+            tmp1[e] = acc;
+        }
+        __syncwarp();
+        // y pass: box[oz][oy][x] = sum_k Ly[ay][k] tmp1[oz][yb+k][x]
+        const int n2 = te[2] * te[1] * s[0];
+        for (int e = lane; e < n2; e += 32) {
+            const int x = e % s[0];
+            const int r = e / s[0];
+            const int oy = r % te[1];
+            const int oz = r / te[1];
+            const int ay = oy % P;
+            const int yb = (oy / P + t.kc[i][1][ay]) * P;
+            C acc = 0;
+#pragma unroll
+            for (int k = 0; k <= P; ++k) acc += t.lw[i][1][ay][k] * tmp1[(oz * s[1] + yb + k) * s[0] + x];
+            box[e] = acc;
+        }
+        __syncwarp();
+        // x pass: OUT[q][oz][oy][ox] = sum_j Lx[ax][j] box[oz][oy][xb+j]
+        const int n3 = te[2] * te[1] * te[0];
+        C* oq = out + q * TS::TILE;
+        for (int e = lane; e < n3; e += 32) {
+            const int ox = e % te[0];
+            const int r = e / te[0];
+            const int oy = r % te[1];
+            const int oz = r / te[1];
+            const int ax = ox % P;
+            const int xb = (ox / P + t.kc[i][0][ax]) * P;
+            C acc = 0;
+#pragma unroll
+            for (int j = 0; j <= P; ++j) acc += t.lw[i][0][ax][j] * box[(oz * te[1] + oy) * s[0] + xb + j];
+            oq[(oz * TS::TY + oy) * TS::TX + ox] = acc;
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+
+    S* dst = static_cast<S*>(a.dst);
+    for (int n = threadIdx.x; n < TS::TILE; n += NW * 32) {
+        const int ox = n % TS::TX;
+        const int r = n / TS::TX;
+        const int oy = r % TS::TY;
+        const int oz = r / TS::TY;
+        if (ox >= te[0] || oy >= te[1] || oz >= te[2]) continue;
+        const long long g = (static_cast<long long>(c0[2] * P + oz) * a.N[1] + (c0[1] * P + oy)) * a.N[0]
+                          + (c0[0] * P + ox);
+        collide_node<S, C, P, PR>(out + n, TS::TILE, a, t, dst + g);
+    }
+}
+
+template <typename S, typename C, int P, int CX, int CY, int CZ, int NW>
+int launch_step_tiled(sllbm_ctx* ctx, const void* src, void* dst) {
+    using SM = StepSmem<C, P, CX, CY, CZ, NW>;
+    static_assert(SM::bytes <= 227 * 1024, "shared memory budget");
+    // the tables are built once per context and kept in its host-side blob
+    if (ctx->step_blob == nullptr || ctx->step_blob_size != sizeof(StepTables<C, P>)) {
+        free(ctx->step_blob);
+        ctx->step_blob = static_cast<unsigned char*>(malloc(sizeof(StepTables<C, P>)));
+        if (ctx->step_blob == nullptr) return SLLBM_ENOMEM;
+        ctx->step_blob_size = sizeof(StepTables<C, P>);
+        fill_step_tables<C, P>(ctx, reinterpret_cast<StepTables<C, P>*>(ctx->step_blob));
+    }
+    const StepTables<C, P>* tab = reinterpret_cast<const StepTables<C, P>*>(ctx->step_blob);
+    StepArgs args;
+    fill_step_args(ctx, src, dst, &args);
+    args.tiles[0] = (ctx->cells[0] + CX - 1) / CX;
+    args.tiles[1] = (ctx->cells[1] + CY - 1) / CY;
+    args.tiles[2] = (ctx->cells[2] + CZ - 1) / CZ;
+    const long long ntiles = static_cast<long long>(args.tiles[0]) * args.tiles[1] * args.tiles[2];
+    if (ntiles > 0x7fffffffLL) return SLLBM_EINVAL;
+    cudaError_t err;
+    if (ctx->prm.pr_correction) {
+        auto k = step_kernel<S, C, P, CX, CY, CZ, NW, true>;
+        err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(SM::bytes));
+        if (err == cudaSuccess) {
+            k<<<static_cast<unsigned>(ntiles), NW * 32, SM::bytes, ctx->stream>>>(args, *tab);
+            err = cudaGetLastError();
+        }
+    } else {
+        auto k = step_kernel<S, C, P, CX, CY, CZ, NW, false>;
+        err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(SM::bytes));
+        if (err == cudaSuccess) {
+            k<<<static_cast<unsigned>(ntiles), NW * 32, SM::bytes, ctx->stream>>>(args, *tab);
+            err = cudaGetLastError();
+        }
+    }
+    ctx->launches += 1;
+    if (err != cudaSuccess) {
+        ctx->last_err = static_cast<int>(err);
+        return SLLBM_ECUDA;
+    }
+    return SLLBM_OK;
+}
+
+}  // namespace sllbm

@@ -1,0 +1,115 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle runs.
+
+Holds workload definitions (mesh, order, flow parameters) and seeded random-number
+helpers only; none of the method's arithmetic (no equilibrium, no streaming, no
+moments) lives here, so that the CUDA path and the oracle stay independent.
+
+The workloads stand in for the paper's compressible Taylor-Green vortex runs
+(Sec. III.C): periodic [0, 2 pi]^3, constant-temperature initial condition, Re = 1600,
+Pr = 0.7, gamma = 1.4, time step given as a Courant number C = dt max|xi| / (L/N).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    cells: tuple
+    p: int
+    Ma: float
+    Re: float
+    courant: float
+    steps: int
+    storage: str
+    Pr: float = 0.7
+    gamma: float = 1.4
+    pr_correction: bool = False
+    note: str = ""
+
+    @property
+    def N(self):
+        return tuple(c * self.p for c in self.cells)
+
+    @property
+    def nodes(self) -> int:
+        n = self.N
+        return n[0] * n[1] * n[2]
+
+    @property
+    def U0(self) -> float:
+        return self.Ma * math.sqrt(self.gamma)
+
+    @property
+    def mu_inf(self) -> float:
+        return self.U0 / self.Re
+
+    def dt(self, max_xi: float = math.sqrt(15.0)) -> float:
+        return self.courant * (2 * math.pi / max(self.N)) / max_xi
+
+
+WORKLOADS = {
+    # small case the oracle finishes in seconds
+    "tgv_8c_p3": Workload("tgv_8c_p3", (8, 8, 8), 3, 0.5, 1600.0, 2.0, 50, "f64",
+                          note="8^3 cells, p=3 (24^3 nodes), Ma 0.5, C=2, 50 steps"),
+    # the throughput workload (about 94 M f-populations)
+    "tgv_32c_p4": Workload("tgv_32c_p4", (32, 32, 32), 4, 0.5, 1600.0, 4.0, 2000, "f32",
+                           note="32^3 cells, p=4 (128^3 nodes), Ma 0.5, C=4"),
+    # oracle-size companion of the throughput workload (curves)
+    "tgv_16c_p4": Workload("tgv_16c_p4", (16, 16, 16), 4, 0.5, 1600.0, 4.0, 2000, "f64",
+                           note="16^3 cells, p=4 (64^3 nodes)"),
+    # shocklet case at higher Mach
+    "tgv_64c_p3_ma125": Workload("tgv_64c_p3_ma125", (64, 64, 64), 3, 1.25, 1600.0, 8.0, 5000,
+                                 "f32", note="64^3 cells, p=3 (192^3 nodes), Ma 1.25, C=8"),
+}
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.default_rng(seed)
+
+
+def random_fields(shape, seed: int, rho=(0.7, 1.4), u_amp=0.6, T=(0.7, 1.4)):
+    """Independent uniform random rho, u (3 components), T at every node (FP64)."""
+    g = rng(seed)
+    r = g.uniform(rho[0], rho[1], shape)
+    u = g.uniform(-u_amp, u_amp, (3,) + tuple(shape))
+    t = g.uniform(T[0], T[1], shape)
+    return r, u, t
+
+
+def smooth_fields(shape, seed: int, modes: int = 3, rho_amp=0.1, u_amp=0.4, T_amp=0.1):
+    """Smooth periodic random fields on [0, 2 pi)^3 sampled at the given node
+    coordinates' index grid (uniform spacing), from a few random Fourier modes."""
+    g = rng(seed)
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid(*(np.arange(n) * 2 * np.pi / n for n in (nz, ny, nx)), indexing="ij")
+
+    def one(amp):
+        out = np.zeros(shape)
+        for _ in range(modes):
+            k = g.integers(-2, 3, 3)
+            ph = g.uniform(0, 2 * np.pi)
+            out += g.uniform(-amp, amp) * np.cos(k[0] * x + k[1] * y + k[2] * z + ph)
+        return out
+
+    r = 1.0 + one(rho_amp)
+    u = np.stack([one(u_amp) for _ in range(3)])
+    t = 1.0 + one(T_amp)
+    return r, u, t
+
+
+def noise(shape, seed: int) -> np.ndarray:
+    """Standard normal array used to push populations away from equilibrium."""
+    return rng(seed).standard_normal(shape)
+
+
+def sample_nodes(nodes: int, count: int, seed: int) -> np.ndarray:
+    """Sorted distinct node indices, always including the first and the last node."""
+    g = rng(seed)
+    pick = g.choice(nodes, size=min(count, nodes), replace=False)
+    pick = np.unique(np.concatenate([pick, [0, nodes - 1]]))
+    return pick.astype(np.int64)

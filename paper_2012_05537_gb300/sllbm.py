@@ -1,0 +1,376 @@
+"""Python binding of libsllbm.so (include/sllbm.h) -- argument marshalling only.
+
+Every function named ``sllbm_*`` here calls the C entry point of the same name; all
+arithmetic of the step runs in the library's CUDA kernels.  PyTorch provides device
+memory (population buffers are ``torch.uint8`` tensors handed to ``sllbm_set_buffers``)
+and the CUDA stream.  There is no CPU fallback: if the library is missing, loading
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ENOTREADY = 0, -1, -2, -3, -4, -5, -6
+F64, F32 = 0, 1
+Q = 45
+
+_lib = None
+
+
+class SllbmError(RuntimeError):
+    def __init__(self, code: int, where: str, cuda_err: int = 0):
+        self.code = code
+        msg = f"{where}: {strerror(code)} ({code})"
+        if cuda_err:
+            msg += f", cudaError {cuda_err}"
+        super().__init__(msg)
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [("cells", ctypes.c_int * 3), ("L", ctypes.c_double * 3)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("Ma", ctypes.c_double), ("Re", ctypes.c_double), ("Pr", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("T0", ctypes.c_double), ("rho0", ctypes.c_double),
+                ("dt_or_courant", ctypes.c_double), ("dt_is_courant", ctypes.c_int),
+                ("pr_correction", ctypes.c_int), ("storage", ctypes.c_int),
+                ("nonfinite_check", ctypes.c_int), ("tgv_C", ctypes.c_double),
+                ("mu_inf_override", ctypes.c_double), ("collide", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int * 3), ("p", ctypes.c_int), ("nodes", ctypes.c_int64),
+                ("Q", ctypes.c_int), ("dt", ctypes.c_double), ("U0", ctypes.c_double),
+                ("mu_inf", ctypes.c_double), ("max_xi", ctypes.c_double),
+                ("pop_bytes", ctypes.c_size_t), ("storage", ctypes.c_int),
+                ("max_cell_shift", ctypes.c_int)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Loads libsllbm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"libsllbm.so not built ({path}); run paper_2012_05537_gb300.build.build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "sllbm_default_params": (None, [ctypes.POINTER(Params)]),
+        "sllbm_create": (ctypes.c_int, [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(Params), vp, ctypes.POINTER(vp)]),
+        "sllbm_destroy": (None, [vp]),
+        "sllbm_get_info": (ctypes.c_int, [vp, ctypes.POINTER(Info)]),
+        "sllbm_velset_table": (ctypes.c_int, [vp, dp, dp]),
+        "sllbm_set_buffers": (ctypes.c_int, [vp, vp, vp, ctypes.c_size_t]),
+        "sllbm_current_buffer": (vp, [vp]),
+        "sllbm_init_tgv": (ctypes.c_int, [vp]),
+        "sllbm_init_fields": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int]),
+        "sllbm_set_populations": (ctypes.c_int, [vp, vp, ctypes.c_int]),
+        "sllbm_get_populations": (ctypes.c_int, [vp, vp, ctypes.c_int]),
+        "sllbm_step": (ctypes.c_int, [vp, ctypes.c_int]),
+        "sllbm_moments": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int]),
+        "sllbm_diag": (ctypes.c_int, [vp, dp, dp, dp]),
+        "sllbm_run_host": (ctypes.c_int, [vp, vp, vp, ctypes.c_int]),
+        "sllbm_sync": (ctypes.c_int, [vp]),
+        "sllbm_last_cuda_error": (ctypes.c_int, [vp]),
+        "sllbm_launch_count": (ctypes.c_int64, [vp]),
+        "sllbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "sllbm_velset_d3q45": (ctypes.c_int, [dp, dp]),
+        "sllbm_stream_table": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().sllbm_strerror(int(code)).decode()
+    except Exception:  # library not loadable: still give a message
+        return f"error {code}"
+
+
+def _check(rc: int, where: str, ctx=None):
+    if rc != OK:
+        err = load().sllbm_last_cuda_error(ctx) if ctx else 0
+        raise SllbmError(rc, where, err)
+
+
+# ---- thin wrappers with the C names --------------------------------------------------
+def sllbm_default_params() -> Params:
+    p = Params()
+    load().sllbm_default_params(ctypes.byref(p))
+    return p
+
+
+def sllbm_create(mesh: Mesh, p: int, params: Params, stream: int = 0, velset: int = 0):
+    ctx = ctypes.c_void_p()
+    rc = load().sllbm_create(ctypes.byref(mesh), int(p), int(velset), ctypes.byref(params),
+                             ctypes.c_void_p(stream), ctypes.byref(ctx))
+    _check(rc, "sllbm_create")
+    return ctx
+
+
+def sllbm_destroy(ctx) -> None:
+    load().sllbm_destroy(ctx)
+
+
+def sllbm_get_info(ctx) -> Info:
+    info = Info()
+    _check(load().sllbm_get_info(ctx, ctypes.byref(info)), "sllbm_get_info", ctx)
+    return info
+
+
+def sllbm_velset_table(ctx):
+    xi = np.zeros((Q, 3))
+    w = np.zeros(Q)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(load().sllbm_velset_table(ctx, xi.ctypes.data_as(dp), w.ctypes.data_as(dp)),
+           "sllbm_velset_table", ctx)
+    return xi, w
+
+
+def sllbm_set_buffers(ctx, ptr_a: int, ptr_b: int, nbytes: int) -> None:
+    _check(load().sllbm_set_buffers(ctx, ctypes.c_void_p(ptr_a), ctypes.c_void_p(ptr_b),
+                                    ctypes.c_size_t(nbytes)), "sllbm_set_buffers", ctx)
+
+
+def sllbm_current_buffer(ctx) -> int:
+    return load().sllbm_current_buffer(ctx) or 0
+
+
+def sllbm_init_tgv(ctx) -> None:
+    _check(load().sllbm_init_tgv(ctx), "sllbm_init_tgv", ctx)
+
+
+def sllbm_init_fields(ctx, rho_ptr: int, u_ptr: int, T_ptr: int, on_device: bool) -> None:
+    _check(load().sllbm_init_fields(ctx, ctypes.c_void_p(rho_ptr), ctypes.c_void_p(u_ptr),
+                                    ctypes.c_void_p(T_ptr), int(on_device)), "sllbm_init_fields", ctx)
+
+
+def sllbm_set_populations(ctx, ptr: int, on_device: bool) -> None:
+    _check(load().sllbm_set_populations(ctx, ctypes.c_void_p(ptr), int(on_device)),
+           "sllbm_set_populations", ctx)
+
+
+def sllbm_get_populations(ctx, ptr: int, on_device: bool) -> None:
+    _check(load().sllbm_get_populations(ctx, ctypes.c_void_p(ptr), int(on_device)),
+           "sllbm_get_populations", ctx)
+
+
+def sllbm_step(ctx, n: int) -> int:
+    rc = load().sllbm_step(ctx, int(n))
+    if rc not in (OK, ENONFINITE):
+        _check(rc, "sllbm_step", ctx)
+    return rc
+
+
+def sllbm_moments(ctx, rho_ptr: int, u_ptr: int, T_ptr: int, on_device: bool) -> None:
+    _check(load().sllbm_moments(ctx, ctypes.c_void_p(rho_ptr), ctypes.c_void_p(u_ptr),
+                                ctypes.c_void_p(T_ptr), int(on_device)), "sllbm_moments", ctx)
+
+
+def sllbm_diag(ctx):
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().sllbm_diag(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "sllbm_diag", ctx)
+    return a.value, b.value, c.value
+
+
+def sllbm_run_host(ctx, in_ptr: int, out_ptr: int, n: int) -> None:
+    _check(load().sllbm_run_host(ctx, ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), int(n)),
+           "sllbm_run_host", ctx)
+
+
+def sllbm_sync(ctx) -> None:
+    _check(load().sllbm_sync(ctx), "sllbm_sync", ctx)
+
+
+def sllbm_velset_d3q45():
+    xi = np.zeros((Q, 3))
+    w = np.zeros(Q)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(load().sllbm_velset_d3q45(xi.ctypes.data_as(dp), w.ctypes.data_as(dp)), "sllbm_velset_d3q45")
+    return xi, w
+
+
+def sllbm_stream_table(p: int, h: float, dt: float, direction: int):
+    shift = np.zeros((Q, p), dtype=np.int32)
+    weights = np.zeros((Q, p, p + 1))
+    _check(load().sllbm_stream_table(int(p), float(h), float(dt), int(direction),
+                                     shift.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                     weights.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+           "sllbm_stream_table")
+    return shift, weights
+
+
+def sllbm_launch_count(ctx) -> int:
+    return int(load().sllbm_launch_count(ctx))
+
+
+# ---- convenience object ------------------------------------------------------------------
+@dataclass
+class Config:
+    cells: tuple = (8, 8, 8)
+    p: int = 3
+    Ma: float = 0.5
+    Re: float = 1600.0
+    Pr: float = 0.7
+    gamma: float = 1.4
+    T0: float = 1.0
+    rho0: float = 1.0
+    courant: float | None = 2.0
+    dt: float | None = None
+    pr_correction: bool = False
+    storage: str = "f32"
+    nonfinite_check: bool = False
+    tgv_C: float = -1.0
+    mu_inf: float | None = None
+    collide: bool = True
+    L: tuple = (2 * np.pi, 2 * np.pi, 2 * np.pi)
+
+
+class Sim:
+    """One SLLBM context with torch-owned ping-pong population buffers."""
+
+    def __init__(self, cfg: Config, device=None, stream=None):
+        import torch
+        self.cfg = cfg
+        self.torch = torch
+        self.device = torch.device(device if device is not None else "cuda")
+        if self.device.type != "cuda":
+            raise RuntimeError("the SLLBM library runs on CUDA devices only")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        mesh = Mesh()
+        for d in range(3):
+            mesh.cells[d] = int(cfg.cells[d])
+            mesh.L[d] = float(cfg.L[d])
+        prm = sllbm_default_params()
+        prm.Ma, prm.Re, prm.Pr, prm.gamma = cfg.Ma, cfg.Re, cfg.Pr, cfg.gamma
+        prm.T0, prm.rho0 = cfg.T0, cfg.rho0
+        if cfg.dt is not None:
+            prm.dt_or_courant, prm.dt_is_courant = float(cfg.dt), 0
+        else:
+            prm.dt_or_courant, prm.dt_is_courant = float(cfg.courant), 1
+        prm.pr_correction = int(bool(cfg.pr_correction))
+        prm.storage = {"f64": F64, "f32": F32}[cfg.storage]
+        prm.nonfinite_check = int(bool(cfg.nonfinite_check))
+        prm.tgv_C = float(cfg.tgv_C)
+        prm.mu_inf_override = float(cfg.mu_inf) if cfg.mu_inf else 0.0
+        prm.collide = int(bool(cfg.collide))
+        with torch.cuda.device(self.device):
+            self.ctx = sllbm_create(mesh, cfg.p, prm, self.stream.cuda_stream)
+        self.info = sllbm_get_info(self.ctx)
+        nb = int(self.info.pop_bytes)
+        self.buffers = [torch.empty(nb, dtype=torch.uint8, device=self.device) for _ in range(2)]
+        sllbm_set_buffers(self.ctx, self.buffers[0].data_ptr(), self.buffers[1].data_ptr(), nb)
+
+    # geometry
+    @property
+    def N(self):
+        return tuple(self.info.N)
+
+    @property
+    def nodes(self) -> int:
+        return int(self.info.nodes)
+
+    @property
+    def dt(self) -> float:
+        return float(self.info.dt)
+
+    @property
+    def pop_dtype(self):
+        return self.torch.float64 if self.info.storage == F64 else self.torch.float32
+
+    def velset(self):
+        return sllbm_velset_table(self.ctx)
+
+    def init_tgv(self):
+        sllbm_init_tgv(self.ctx)
+        return self
+
+    def init_fields(self, rho, u, T):
+        t = self.torch
+        rho = t.as_tensor(rho, dtype=t.float64, device=self.device).contiguous()
+        u = t.as_tensor(u, dtype=t.float64, device=self.device).contiguous()
+        T = t.as_tensor(T, dtype=t.float64, device=self.device).contiguous()
+        sllbm_init_fields(self.ctx, rho.data_ptr(), u.data_ptr(), T.data_ptr(), True)
+        return self
+
+    def set_populations(self, pop):
+        t = self.torch
+        pop = t.as_tensor(pop, dtype=t.float64, device=self.device).contiguous()
+        assert pop.numel() == 2 * Q * self.nodes
+        sllbm_set_populations(self.ctx, pop.data_ptr(), True)
+        self.sync()
+        return self
+
+    def populations(self):
+        """Current state as a float64 tensor [2, 45, Nz, Ny, Nx] on the device."""
+        t = self.torch
+        out = t.empty((2, Q) + self.N[::-1], dtype=t.float64, device=self.device)
+        sllbm_get_populations(self.ctx, out.data_ptr(), True)
+        self.sync()
+        return out
+
+    def raw_state(self):
+        """Current state buffer viewed in the storage dtype, [2, 45, Nz, Ny, Nx] (no copy)."""
+        cur = sllbm_current_buffer(self.ctx)
+        idx = 0 if cur == self.buffers[0].data_ptr() else 1
+        return self.buffers[idx].view(self.pop_dtype).view((2, Q) + self.N[::-1])
+
+    def step(self, n: int = 1) -> int:
+        return sllbm_step(self.ctx, n)
+
+    def moments(self):
+        t = self.torch
+        shp = self.N[::-1]
+        rho = t.empty(shp, dtype=t.float64, device=self.device)
+        u = t.empty((3,) + shp, dtype=t.float64, device=self.device)
+        T = t.empty(shp, dtype=t.float64, device=self.device)
+        sllbm_moments(self.ctx, rho.data_ptr(), u.data_ptr(), T.data_ptr(), True)
+        self.sync()
+        return rho, u, T
+
+    def diag(self):
+        return sllbm_diag(self.ctx)
+
+    def run_host(self, host_in, host_out, n: int):
+        sllbm_run_host(self.ctx, host_in.data_ptr(), host_out.data_ptr(), n)
+
+    def sync(self):
+        sllbm_sync(self.ctx)
+
+    def launches(self) -> int:
+        return sllbm_launch_count(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            sllbm_sync(self.ctx)
+            sllbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,236 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (written here, derived from the arithmetic):
+  * FP64 path: relative L2 <= 1e-12 (and max relative element error <= 1e-11) after one
+    step and after the 50-step 24^3 Taylor-Green run.  Both sides compute the same
+    algebra in double precision with different summation orders; one step perturbs each
+    value by a few ulps (~1e-15).
+  * FP32 path: FP32 unit round-off is 6e-8; one step sums 3(p+1) weighted values per
+    pass (Lebesgue constant of the GLC points <= 2 for p <= 4) and a few collision
+    terms, so per-element errors stay below ~1e-6 relative to the local population
+    scale; relative L2 <= 1e-6 after one step, <= 3e-5 after 50 steps.
+Inputs come from the oracle (equilibrium of seeded fields, seeded noise) or from the
+paper's Taylor-Green definition evaluated independently on each side.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2012_05537_gb300 import build as B
+from paper_2012_05537_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+    from paper_2012_05537_gb300 import sllbm
+    sllbm.load()
+    return sllbm
+
+
+def make(S, cells, p, storage="f64", dt=None, courant=2.0, pr=False, collide=True, Ma=0.5,
+         Re=1600.0, mu_inf=None, check=False):
+    cfg = S.Config(cells=tuple(cells), p=p, Ma=Ma, Re=Re, courant=None if dt else courant,
+                   dt=dt, pr_correction=pr, storage=storage, collide=collide, mu_inf=mu_inf,
+                   nonfinite_check=check)
+    return S.Sim(cfg)
+
+
+def grid_of(sim, pr=False, collide=True):
+    c = sim.cfg
+    return O.Grid(cells=tuple(c.cells), p=c.p, dt=sim.dt, mu_inf=float(sim.info.mu_inf),
+                  gamma=c.gamma, Pr=c.Pr, pr_correction=pr, collide=collide)
+
+
+def noneq_state(g, seed, amp=0.02):
+    rho, u, T = I.smooth_fields(g.N[::-1], seed)
+    pop = O.init_fields(g, rho, u, T)
+    return pop * (1.0 + amp * I.noise(pop.shape, seed + 1))
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_velocity_table_matches_oracle(S):
+    sim = make(S, (2, 2, 2), 2)
+    xi, w = sim.velset()
+    xo, wo = O.velset()
+    assert np.max(np.abs(xi - xo)) <= 1e-15 and np.max(np.abs(w - wo)) <= 1e-17
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-14), ("f32", 1e-7)])
+def test_init_tgv_matches_oracle(S, storage, tol):
+    sim = make(S, (3, 2, 4), 3, storage=storage)
+    sim.init_tgv()
+    g = grid_of(sim)
+    U0 = sim.info.U0
+    ref = O.init_fields(g, *O.tgv_fields(g, U0))
+    got = sim.populations().cpu().numpy()
+    assert np.max(np.abs(got - ref) / np.abs(ref).max()) <= tol
+
+
+def test_init_fields_equilibrium_matches_tensor_contraction(S):
+    """Closed-form quartic equilibrium on the GPU = the oracle's full tensor contraction."""
+    sim = make(S, (2, 3, 2), 4)
+    g = grid_of(sim)
+    rho, u, T = I.random_fields(g.N[::-1], 3, u_amp=1.5, T=(0.5, 2.0))
+    sim.init_fields(rho, u, T)
+    ref = O.init_fields(g, rho, u, T)
+    got = sim.populations().cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-14 * np.abs(ref).max()
+
+
+def test_moments_match_oracle(S):
+    sim = make(S, (2, 2, 3), 3)
+    g = grid_of(sim)
+    pop = noneq_state(g, 5)
+    sim.set_populations(pop)
+    rho, u, T = (x.cpu().numpy() for x in sim.moments())
+    r2, u2, T2 = O.moments(g, pop)
+    assert np.allclose(rho, r2, rtol=1e-14, atol=0)
+    assert np.allclose(u, u2, rtol=0, atol=1e-14)
+    assert np.allclose(T, T2, rtol=1e-14, atol=0)
+
+
+STEP_CASES = [
+    ((2, 2, 2), 2, False),
+    ((3, 5, 2), 3, False),   # ragged tiles in every direction
+    ((3, 2, 3), 4, True),
+    ((1, 1, 1), 4, False),   # a single cell: every departure wraps onto itself
+    ((5, 1, 1), 2, True),    # thin domain
+    ((2, 3, 2), 3, True),
+]
+
+
+@pytest.mark.parametrize("cells,p,pr", STEP_CASES)
+def test_step_f64_matches_oracle(S, cells, p, pr):
+    sim = make(S, cells, p, courant=2.5, pr=pr)
+    g = grid_of(sim, pr=pr)
+    pop = noneq_state(g, 11)
+    sim.set_populations(pop)
+    for nsteps in (1, 2):
+        assert sim.step(1) == 0
+        pop = O.step(g, pop, 1)
+        got = sim.populations().cpu().numpy()
+        assert rel_l2(got, pop) <= 1e-12, nsteps
+        assert np.max(np.abs(got - pop)) <= 1e-11 * np.abs(pop).max()
+
+
+@pytest.mark.parametrize("cells,p,pr", STEP_CASES[:4])
+def test_step_f32_matches_oracle(S, cells, p, pr):
+    sim = make(S, cells, p, storage="f32", courant=2.5, pr=pr)
+    g = grid_of(sim, pr=pr)
+    pop = noneq_state(g, 13)
+    pop32 = pop.astype(np.float32).astype(np.float64)  # the state the FP32 path holds
+    sim.set_populations(pop32)
+    assert sim.step(1) == 0
+    ref = O.step(g, pop32, 1)
+    got = sim.populations().cpu().numpy()
+    assert rel_l2(got, ref) <= 1e-6
+    assert np.max(np.abs(got - ref)) <= 2e-6 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_stream_only_matches_oracle(S, p):
+    """Collision off: the kernel is exactly the semi-Lagrangian streaming operator."""
+    sim = make(S, (3, 2, 2), p, courant=3.7, collide=False)
+    g = grid_of(sim, collide=False)
+    pop = noneq_state(g, 17, amp=0.3)
+    sim.set_populations(pop)
+    sim.step(1)
+    ref = O.stream(g, pop)
+    got = sim.populations().cpu().numpy()
+    assert rel_l2(got, ref) <= 1e-13
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 3e-5)])
+def test_tgv_24cube_50_steps_matches_oracle(S, storage, tol):
+    """The 8^3-cell, p=3 Taylor-Green run (Ma 0.5, Re 1600, C = 2) for 50 steps."""
+    w = I.WORKLOADS["tgv_8c_p3"]
+    sim = make(S, w.cells, w.p, storage=storage, courant=w.courant, Ma=w.Ma, Re=w.Re)
+    sim.init_tgv()
+    g = grid_of(sim)
+    pop = O.init_fields(g, *O.tgv_fields(g, sim.info.U0))
+    if storage == "f32":
+        pop = sim.populations().cpu().numpy()  # FP32-rounded TGV state (checked above)
+        assert np.max(np.abs(pop - O.init_fields(g, *O.tgv_fields(g, sim.info.U0)))) < 1e-7
+    assert sim.step(w.steps) == 0
+    ref = O.step(g, pop, w.steps)
+    got = sim.populations().cpu().numpy()
+    assert rel_l2(got, ref) <= tol
+    r1, u1, T1 = (x.cpu().numpy() for x in sim.moments())
+    r2, u2, T2 = O.moments(g, ref)
+    assert rel_l2(r1, r2) <= tol and rel_l2(u1, u2) <= 10 * tol and rel_l2(T1, T2) <= tol
+    d_gpu = np.array(sim.diag())
+    d_orc = O.diag(g, ref, 1.0, w.Re, sim.info.U0)
+    assert np.allclose(d_gpu, d_orc, rtol=max(tol * 100, 1e-11), atol=0)
+
+
+@pytest.mark.parametrize("name,storage", [("tgv_32c_p4", "f32"), ("tgv_32c_p4", "f64"),
+                                          ("tgv_64c_p3_ma125", "f32")])
+def test_full_size_first_step_sampled(S, name, storage):
+    """At the benchmark sizes, in the benchmark launch configuration: one step from the
+    Taylor-Green state, compared at sampled nodes that the oracle evaluates one by one."""
+    w = I.WORKLOADS[name]
+    sim = make(S, w.cells, w.p, storage=storage, courant=w.courant, Ma=w.Ma, Re=w.Re)
+    sim.init_tgv()
+    assert sim.step(1) == 0
+    g = grid_of(sim)
+    nodes = I.sample_nodes(sim.nodes, 48, seed=2)
+    ref = O.tgv_step_sample(g, nodes, sim.info.U0)
+    got = sim.raw_state().reshape(90, -1)[:, torch.as_tensor(nodes, device="cuda")]
+    got = got.double().cpu().numpy().T
+    scale = np.abs(ref).max()
+    tol = 1e-12 if storage == "f64" else 1e-6
+    assert np.max(np.abs(got - ref)) <= tol * scale
+
+
+def test_zero_steps_and_not_ready(S):
+    sim = make(S, (2, 2, 2), 3)
+    with pytest.raises(S.SllbmError):
+        sim.step(1)
+    sim.init_tgv()
+    before = sim.populations().cpu().numpy()
+    assert sim.step(0) == 0
+    assert np.array_equal(sim.populations().cpu().numpy(), before)
+
+
+def test_nonfinite_check_reports_bad_state(S):
+    sim = make(S, (2, 2, 2), 3, check=True)
+    g = grid_of(sim)
+    pop = noneq_state(g, 3)
+    sim.set_populations(pop)
+    assert sim.step(2) == 0
+    pop[:, :, 1, 2, 3] = -pop[:, :, 1, 2, 3]  # negative density at one node
+    sim.set_populations(pop)
+    assert sim.step(1) == S.ENONFINITE
+
+
+def test_run_host_equals_device_path(S):
+    sim = make(S, (4, 2, 2), 4, storage="f32")
+    sim.init_tgv()
+    raw0 = sim.raw_state().clone()
+    host_in = raw0.cpu().pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    sim.run_host(host_in, host_out, 3)
+    dev = make(S, (4, 2, 2), 4, storage="f32")
+    dev.init_tgv()
+    dev.step(3)
+    assert torch.equal(host_out, dev.raw_state().cpu())
+
+
+def test_launch_count_is_one_kernel_per_step(S):
+    sim = make(S, (2, 2, 2), 2)
+    sim.init_tgv()
+    n0 = sim.launches()
+    sim.step(7)
+    assert sim.launches() - n0 == 7

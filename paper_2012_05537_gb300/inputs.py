@@ -11,7 +11,7 @@ Pr = 0.7, gamma = 1.4, time step given as a Courant number C = dt max|xi| / (L/N
 from __future__ import annotations
 
 import math
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 
@@ -59,6 +59,9 @@ WORKLOADS = {
     # the throughput workload (about 94 M f-populations)
     "tgv_32c_p4": Workload("tgv_32c_p4", (32, 32, 32), 4, 0.5, 1600.0, 4.0, 2000, "f32",
                            note="32^3 cells, p=4 (128^3 nodes), Ma 0.5, C=4"),
+    # profiling size: same resolution per cell as tgv_32c_p4, buffers (318 MB) > L2
+    "tgv_24c_p4": Workload("tgv_24c_p4", (24, 24, 24), 4, 0.5, 1600.0, 4.0, 2000, "f32",
+                           note="24^3 cells, p=4 (96^3 nodes), Ma 0.5, C=4"),
     # oracle-size companion of the throughput workload (curves)
     "tgv_16c_p4": Workload("tgv_16c_p4", (16, 16, 16), 4, 0.5, 1600.0, 4.0, 2000, "f64",
                            note="16^3 cells, p=4 (64^3 nodes)"),

@@ -8,7 +8,9 @@ Tolerances (written here, derived from the arithmetic):
   * FP32 path: FP32 unit round-off is 6e-8; one step sums 3(p+1) weighted values per
     pass (Lebesgue constant of the GLC points <= 2 for p <= 4) and a few collision
     terms, so per-element errors stay below ~1e-6 relative to the local population
-    scale; relative L2 <= 1e-6 after one step, <= 3e-5 after 50 steps.
+    scale; relative L2 <= 1e-6 after one step, <= 3e-5 after 50 steps.  At Ma 1.25 the
+    equilibrium quartic has terms up to s^4/24 ~ 45 (s = |xi||u| <= 5.7) that cancel
+    to O(1), which amplifies FP32 round-off; the bound there is 4e-6 of the scale.
 Inputs come from the oracle (equilibrium of seeded fields, seeded noise) or from the
 paper's Taylor-Green definition evaluated independently on each side.
 """
@@ -161,8 +163,8 @@ def test_tgv_24cube_50_steps_matches_oracle(S, storage, tol):
     g = grid_of(sim)
     pop = O.init_fields(g, *O.tgv_fields(g, sim.info.U0))
     if storage == "f32":
-        pop = sim.populations().cpu().numpy()  # FP32-rounded TGV state (checked above)
-        assert np.max(np.abs(pop - O.init_fields(g, *O.tgv_fields(g, sim.info.U0)))) < 1e-7
+        # the oracle's own TGV state rounded to FP32, as the FP32 path stores it
+        pop = pop.astype(np.float32).astype(np.float64)
     assert sim.step(w.steps) == 0
     ref = O.step(g, pop, w.steps)
     got = sim.populations().cpu().numpy()
@@ -190,7 +192,7 @@ def test_full_size_first_step_sampled(S, name, storage):
     got = sim.raw_state().reshape(90, -1)[:, torch.as_tensor(nodes, device="cuda")]
     got = got.double().cpu().numpy().T
     scale = np.abs(ref).max()
-    tol = 1e-12 if storage == "f64" else 1e-6
+    tol = 1e-12 if storage == "f64" else (1e-6 if w.Ma <= 0.5 else 4e-6)
     assert np.max(np.abs(got - ref)) <= tol * scale
 
 
@@ -210,9 +212,14 @@ def test_nonfinite_check_reports_bad_state(S):
     pop = noneq_state(g, 3)
     sim.set_populations(pop)
     assert sim.step(2) == 0
-    pop[:, :, 1, 2, 3] = -pop[:, :, 1, 2, 3]  # negative density at one node
-    sim.set_populations(pop)
+    bad = pop.copy()
+    bad[0, 0, 1, 2, 3] = np.nan  # reaches every node whose departure cell holds it
+    sim.set_populations(bad)
     assert sim.step(1) == S.ENONFINITE
+    sim.set_populations(-pop)    # negative density everywhere
+    assert sim.step(1) == S.ENONFINITE
+    sim.set_populations(pop)     # the flag is cleared at the start of each call
+    assert sim.step(1) == 0
 
 
 def test_run_host_equals_device_path(S):

@@ -169,6 +169,18 @@ int sllbm_moments(sllbm_ctx *ctx, double *rho, double *u, double *T, int on_devi
  * Synchronous.  Uses a context-owned device scratch buffer (allocated on first use). */
 int sllbm_diag(sllbm_ctx *ctx, double *Ek, double *eps_s, double *eps_c);
 
+/* sllbm_diag without any device allocation (the paper has no counterpart: this is a
+ * library-interface matter).  For callers that cannot let the library allocate: their
+ * device memory is owned by another allocator or a fixed budget, or their loop must not
+ * pay for cudaMalloc/cudaFree (cudaFree synchronises the device).  The scratch is a
+ * static device array inside the library holding one partial triple per cell: meshes
+ * with more than 65536 cells get SLLBM_EINVAL.  Results equal sllbm_diag's up to the
+ * order of the FP64 sums.  The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress) and should come before any stream capture.  Calls share the
+ * array, so calls that overlap on the GPU (other streams or contexts) race.  Uses the
+ * current device, which must be the context's.  Synchronous; host outputs. */
+int sllbm_diag_noalloc(sllbm_ctx *ctx, double *Ek, double *eps_s, double *eps_c);
+
 /* End-to-end call with HOST buffers: copies pop_in (pop_bytes, storage type, host
  * memory; pinned for full speed) to the device, advances n steps, copies the result
  * to pop_out (host) and synchronises the stream. */

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "collide.cuh"
@@ -295,6 +296,45 @@ int launch_diag_p(sllbm_ctx* ctx, const void* pop, double* d_out) {
             static_cast<const float*>(pop), ctx->nn, ctx->N[0], ctx->N[1], ctx->N[2], ctx->cells[0],
             ctx->cells[1], ncell, inv_2cv, ctx->h[0], ctx->h[1], ctx->h[2], dc, ctx->d_partials);
     sum_partials_kernel<<<1, 256, 0, ctx->stream>>>(ctx->d_partials, nb, d_out);
+    ctx->launches += 2;
+    CK(ctx, cudaGetLastError());
+    return SLLBM_OK;
+}
+
+// ---------------------------------------------------------------- diagnostics without allocation
+// Scratch of sllbm_diag_noalloc: one partial triple per cell plus the three totals, in a
+// file-scope device array (every GPU that loads the library holds these 1.5 MB until exit).
+constexpr long long kNoAllocDiagMaxCells = 65536;
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) double g_diag_scratch[3 * kNoAllocDiagMaxCells + 3];
+
+// Device address of g_diag_scratch per device ordinal, looked up once with that device current.
+std::mutex g_diag_scratch_mu;
+double* g_diag_scratch_addr[kNoAllocMaxDevices] = {};
+
+template <int P>
+int launch_diag_cells_into(sllbm_ctx* ctx, const void* pop, double* partials, double* d_out) {
+    const long long ncell = static_cast<long long>(ctx->cells[0]) * ctx->cells[1] * ctx->cells[2];
+    DiagConst dc;
+    std::memcpy(dc.xi, ctx->xi, sizeof(dc.xi));
+    double W[kMaxP + 1];
+    clenshaw_curtis(P, W);
+    for (int j = 0; j <= kMaxP; ++j) dc.W[j] = j <= P ? W[j] : 0.0;
+    double D[kMaxP + 1][kMaxP + 1];
+    diff_matrix(P, D);
+    for (int a = 0; a <= kMaxP; ++a)
+        for (int j = 0; j <= kMaxP; ++j) dc.D[a][j] = (a <= P && j <= P) ? D[a][j] : 0.0;
+    const double inv_2cv = 0.5 * (ctx->prm.gamma - 1.0);
+    const int nb = static_cast<int>(ncell);  // one block, hence one partial triple, per cell
+    if (ctx->prm.storage == SLLBM_F64)
+        diag_kernel<double, P><<<nb, 128, 0, ctx->stream>>>(
+            static_cast<const double*>(pop), ctx->nn, ctx->N[0], ctx->N[1], ctx->N[2], ctx->cells[0],
+            ctx->cells[1], ncell, inv_2cv, ctx->h[0], ctx->h[1], ctx->h[2], dc, partials);
+    else
+        diag_kernel<float, P><<<nb, 128, 0, ctx->stream>>>(
+            static_cast<const float*>(pop), ctx->nn, ctx->N[0], ctx->N[1], ctx->N[2], ctx->cells[0],
+            ctx->cells[1], ncell, inv_2cv, ctx->h[0], ctx->h[1], ctx->h[2], dc, partials);
+    sum_partials_kernel<<<1, 256, 0, ctx->stream>>>(partials, nb, d_out);
     ctx->launches += 2;
     CK(ctx, cudaGetLastError());
     return SLLBM_OK;
@@ -669,6 +709,50 @@ int sllbm_diag(sllbm_ctx* ctx, double* Ek, double* eps_s, double* eps_c) {
     int rc = ctx->p == 2 ? launch_diag_p<2>(ctx, pop, d_out)
            : ctx->p == 3 ? launch_diag_p<3>(ctx, pop, d_out)
                          : launch_diag_p<4>(ctx, pop, d_out);
+    if (rc != SLLBM_OK) return rc;
+    double h[3];
+    CK(ctx, cudaMemcpyAsync(h, d_out, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    const double vol = ctx->L[0] * ctx->L[1] * ctx->L[2];
+    const double u2 = ctx->U0 * ctx->U0;
+    const double rho0 = ctx->prm.rho0;
+    *Ek = h[0] / vol / (rho0 * u2);
+    *eps_s = h[1] / vol / (rho0 * ctx->prm.Re * u2);
+    *eps_c = 4.0 / 3.0 * h[2] / vol / (rho0 * ctx->prm.Re * u2);
+    return SLLBM_OK;
+}
+
+// Same results as sllbm_diag (up to summation order) without allocating device memory:
+// for callers whose device memory is owned by another allocator or a fixed budget, or
+// whose loop must not pay for cudaMalloc/cudaFree (cudaFree synchronises the device).
+// The scratch is g_diag_scratch above; the first call on a device looks up its address
+// with cudaGetSymbolAddress (make that first call before any stream capture).  All calls
+// share the array and each overwrites every entry it reads, so nothing needs clearing,
+// but calls that overlap on the GPU (other streams, other contexts) race on it.
+int sllbm_diag_noalloc(sllbm_ctx* ctx, double* Ek, double* eps_s, double* eps_c) {
+    if (ctx == nullptr || Ek == nullptr || eps_s == nullptr || eps_c == nullptr) return SLLBM_EINVAL;
+    if (!ctx->initialised) return SLLBM_ENOTREADY;
+    const long long ncell = static_cast<long long>(ctx->cells[0]) * ctx->cells[1] * ctx->cells[2];
+    if (ncell > kNoAllocDiagMaxCells) return SLLBM_EINVAL;  // more cells than the static scratch holds
+    int dev = 0;
+    CK(ctx, cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return SLLBM_EINVAL;
+    double* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_diag_scratch_mu);
+        if (g_diag_scratch_addr[dev] == nullptr) {
+            void* addr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&addr, g_diag_scratch);
+            if (e != cudaSuccess) return fail(ctx, e);
+            g_diag_scratch_addr[dev] = static_cast<double*>(addr);
+        }
+        scratch = g_diag_scratch_addr[dev];
+    }
+    double* d_out = scratch + 3 * ncell;
+    const void* pop = ctx->buf[ctx->cur];
+    int rc = ctx->p == 2 ? launch_diag_cells_into<2>(ctx, pop, scratch, d_out)
+           : ctx->p == 3 ? launch_diag_cells_into<3>(ctx, pop, scratch, d_out)
+                         : launch_diag_cells_into<4>(ctx, pop, scratch, d_out);
     if (rc != SLLBM_OK) return rc;
     double h[3];
     CK(ctx, cudaMemcpyAsync(h, d_out, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));

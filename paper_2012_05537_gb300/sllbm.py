@@ -85,6 +85,7 @@ def load(build_if_missing: bool = False):
         "sllbm_step": (ctypes.c_int, [vp, ctypes.c_int]),
         "sllbm_moments": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int]),
         "sllbm_diag": (ctypes.c_int, [vp, dp, dp, dp]),
+        "sllbm_diag_noalloc": (ctypes.c_int, [vp, dp, dp, dp]),
         "sllbm_run_host": (ctypes.c_int, [vp, vp, vp, ctypes.c_int]),
         "sllbm_sync": (ctypes.c_int, [vp]),
         "sllbm_last_cuda_error": (ctypes.c_int, [vp]),
@@ -193,6 +194,14 @@ def sllbm_diag(ctx):
     a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(load().sllbm_diag(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
            "sllbm_diag", ctx)
+    return a.value, b.value, c.value
+
+
+def sllbm_diag_noalloc(ctx):
+    """sllbm_diag without device allocation (static library scratch, <= 65536 cells)."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().sllbm_diag_noalloc(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "sllbm_diag_noalloc", ctx)
     return a.value, b.value, c.value
 
 

@@ -21,11 +21,14 @@
  *  Velocities the 45 abscissae in the order returned by sllbm_velset_table():
  *             origin; icosahedron |xi|=sqrt(3); dodecahedron |xi|=3; icosahedron
  *             |xi|=sqrt(15).
- *  Populations one buffer holds 2*45 fields, pop[h][i][z][y][x] with h = 0 for f and
- *             h = 1 for g, each field N[0]*N[1]*N[2] elements of the storage type
- *             (SLLBM_F64: double, SLLBM_F32: float).  The stored state is the
- *             post-collision population; sllbm_step() streams it (pull, departure
- *             point x - dt*xi_i) and collides the result, ping-ponging two buffers.
+ *  Populations a state buffer holds the 2*45 populations of every node in the storage
+ *             type (SLLBM_F64: double, SLLBM_F32: float) in the order
+ *             buf[i][z][y][x][h]: velocity slowest, then the node, then h = 0 for f and
+ *             h = 1 for g, so f_i and g_i of a node sit side by side.  The FP64
+ *             interface of sllbm_set_populations / sllbm_get_populations uses the order
+ *             pop[h][i][z][y][x] instead.  The stored state is the post-collision
+ *             population; sllbm_step() streams it (pull, departure point x - dt*xi_i)
+ *             and collides the result, ping-ponging two buffers.
  *  Streams    every call that touches the GPU is enqueued on the CUDA stream given
  *             to sllbm_create() and is asynchronous unless stated otherwise.
  *  Errors     every int-returning call returns SLLBM_OK (0) or a negative SLLBM_E*
@@ -85,6 +88,9 @@ typedef struct {
     double tgv_C;           /* density numerator C of the TGV field; < 0 selects gamma*Ma^2 */
     double mu_inf_override; /* > 0: use this mu_inf instead of rho0*U0/Re */
     int collide;            /* 1: stream and collide (normal); 0: stream only */
+    int kernel;             /* step kernel: 0 automatic, 1 generic tile kernel, 2 TMA-fed
+                               persistent kernel (FP32 only; needs N[0] even, cells divisible
+                               by its tile, no Prandtl term, collide on; else SLLBM_EINVAL) */
 } sllbm_params;
 
 /* Read-only description of a created context. */
@@ -100,6 +106,7 @@ typedef struct {
     size_t pop_bytes;  /* bytes of one population buffer (2*Q*nodes*sizeof(storage)) */
     int storage;       /* sllbm_storage */
     int max_cell_shift;/* largest |departure cell shift| over velocities and directions */
+    int step_kernel;   /* kernel sllbm_step launches: 1 generic tile kernel, 2 TMA-fed kernel */
 } sllbm_info_t;
 
 /* Fills p_out with the defaults used for the paper's Re = 1600 Taylor-Green runs
@@ -154,9 +161,15 @@ int sllbm_get_populations(sllbm_ctx *ctx, double *pop, int on_device);
 /* Advances n >= 0 time steps: each step is one launch of the fused kernel (pull
  * streaming of all 90 populations, moments, equilibrium, BGK [+ Prandtl term]),
  * alternating the two buffers.  Asynchronous.  With nonfinite_check on, the
- * check flag is read back (synchronising) after the last step and SLLBM_ENONFINITE
- * is returned if any node had non-finite or non-positive rho or T. */
+ * check flags are read back (synchronising) after the last step: SLLBM_ETIMEOUT if a
+ * bounded device wait gave up, SLLBM_ENONFINITE if any node had non-finite or
+ * non-positive rho or T. */
 int sllbm_step(sllbm_ctx *ctx, int n);
+
+/* Synchronises the stream and reports device-side trouble since the last call: returns
+ * SLLBM_ETIMEOUT (and clears it) if a bounded wait inside a step kernel gave up, else
+ * SLLBM_OK.  Kernels never spin without a limit; after such an error the state is garbage. */
+int sllbm_status(sllbm_ctx *ctx);
 
 /* Density, velocity and temperature of the current state, Eq. (moments), FP64:
  * rho[nodes], u[3][nodes], T[nodes]; host pointers (synchronous) if on_device == 0. */

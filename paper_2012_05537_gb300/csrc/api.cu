@@ -83,17 +83,32 @@ __global__ void init_eq_kernel(S* __restrict__ pop, long long nn, int Nx, int Ny
         for (int i = 0; i < kQ; ++i) {
             const double s = vc.xi[i][0] * ux + vc.xi[i][1] * uy + vc.xi[i][2] * uz;
             const double feq = vc.w[i] * rho * eq_poly(ec, shell_of(i), s);
-            pop[i * nn + n] = static_cast<S>(feq);
-            pop[(kQ + i) * nn + n] = static_cast<S>(gfac * T * feq);
+            pop[2 * (i * nn + n)] = static_cast<S>(feq);
+            pop[2 * (i * nn + n) + 1] = static_cast<S>(gfac * T * feq);
         }
     }
 }
 
-template <typename A, typename B>
-__global__ void convert_kernel(const A* __restrict__ in, B* __restrict__ out, long long count) {
+// FP64 populations in the interface order [h][i][node] <-> the storage order
+// [i][node][h] (f_i and g_i of a node side by side), rounding to the storage type.
+template <typename S>
+__global__ void pack_kernel(const double* __restrict__ in, S* __restrict__ out, long long nn) {
+    const long long count = 2LL * kQ * nn;
     for (long long k = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; k < count;
-         k += static_cast<long long>(gridDim.x) * blockDim.x)
-        out[k] = static_cast<B>(in[k]);
+         k += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long h = k & 1, r = k >> 1;  // r = i*nn + node
+        out[k] = static_cast<S>(in[h * kQ * nn + r]);
+    }
+}
+
+template <typename S>
+__global__ void unpack_kernel(const S* __restrict__ in, double* __restrict__ out, long long nn) {
+    const long long count = 2LL * kQ * nn;
+    for (long long k = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; k < count;
+         k += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long h = k & 1, r = k >> 1;
+        out[h * kQ * nn + r] = static_cast<double>(in[k]);
+    }
 }
 
 // ---------------------------------------------------------------- moments
@@ -106,12 +121,12 @@ __global__ void moments_kernel(const S* __restrict__ pop, long long nn, double i
         double rho = 0, mx = 0, my = 0, mz = 0, e2 = 0;
 #pragma unroll 5
         for (int i = 0; i < kQ; ++i) {
-            const double f = static_cast<double>(pop[i * nn + n]);
+            const double f = static_cast<double>(pop[2 * (i * nn + n)]);
             rho += f;
             mx += f * vc.xi[i][0];
             my += f * vc.xi[i][1];
             mz += f * vc.xi[i][2];
-            e2 += f * shell_xi2(shell_of(i)) + static_cast<double>(pop[(kQ + i) * nn + n]);
+            e2 += f * shell_xi2(shell_of(i)) + static_cast<double>(pop[2 * (i * nn + n) + 1]);
         }
         const double ux = mx / rho, uy = my / rho, uz = mz / rho;
         rho_o[n] = rho;
@@ -155,12 +170,12 @@ __global__ void __launch_bounds__(128) diag_kernel(const S* __restrict__ pop, lo
             const long long n = (static_cast<long long>(nz) * Ny + ny) * Nx + nx;
             double mx = 0, my = 0, mz = 0, e2 = 0;
             for (int i = 0; i < kQ; ++i) {
-                const double f = static_cast<double>(pop[i * nn + n]);
+                const double f = static_cast<double>(pop[2 * (i * nn + n)]);
                 rho += f;
                 mx += f * dc.xi[i][0];
                 my += f * dc.xi[i][1];
                 mz += f * dc.xi[i][2];
-                e2 += f * shell_xi2(shell_of(i)) + static_cast<double>(pop[(kQ + i) * nn + n]);
+                e2 += f * shell_xi2(shell_of(i)) + static_cast<double>(pop[2 * (i * nn + n) + 1]);
             }
             ux = mx / rho;
             uy = my / rho;
@@ -235,6 +250,14 @@ __global__ void sum_partials_kernel(const double* __restrict__ partials, int nbl
         __syncthreads();
     }
     if (threadIdx.x < 3) out[threadIdx.x] = red[threadIdx.x][0];
+}
+
+// 1: generic tile kernel, 2: TMA-fed persistent kernel, 0: the requested kernel cannot run.
+int choose_step_kernel(const sllbm_ctx* c) {
+    const bool tma_ok = tma_step_eligible(c);
+    if (c->prm.kernel == 2) return tma_ok ? 2 : 0;
+    if (c->prm.kernel == 1) return 1;
+    return tma_ok ? 2 : 1;
 }
 
 int ensure_buffers(sllbm_ctx* ctx) {
@@ -361,6 +384,7 @@ void fill_step_args(const sllbm_ctx* ctx, const void* src, void* dst, StepArgs* 
     a->pr = ctx->prm.pr_correction;
     a->collide = ctx->prm.collide;
     a->flag = ctx->prm.nonfinite_check ? ctx->d_flag : nullptr;
+    a->flag_err = ctx->d_flag + 1;
 }
 
 }  // namespace sllbm
@@ -384,6 +408,7 @@ void sllbm_default_params(sllbm_params* p) {
     p->tgv_C = -1.0;
     p->mu_inf_override = 0.0;
     p->collide = 1;
+    p->kernel = 0;
 }
 
 int sllbm_create(const sllbm_mesh* mesh, int p, sllbm_velset vs, const sllbm_params* prm,
@@ -475,13 +500,20 @@ int sllbm_create(const sllbm_mesh* mesh, int p, sllbm_velset vs, const sllbm_par
             e = cudaMemcpy(c->d_coords[d], x, sizeof(double) * c->N[d], cudaMemcpyHostToDevice);
             std::free(x);
         }
-        if (e == cudaSuccess) e = cudaMalloc(&c->d_flag, sizeof(int));
-        if (e == cudaSuccess) e = cudaMemset(c->d_flag, 0, sizeof(int));
+        // d_flag[0]: non-finite rho/T seen; d_flag[1]: a bounded device wait gave up
+        if (e == cudaSuccess) e = cudaMalloc(&c->d_flag, 2 * sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(c->d_flag, 0, 2 * sizeof(int));
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     }
     if (e != cudaSuccess) {
         int code = (e == cudaErrorMemoryAllocation) ? SLLBM_ENOMEM : SLLBM_ECUDA;
         sllbm_destroy(c);
         return code;
+    }
+    c->step_kernel = choose_step_kernel(c);
+    if (c->step_kernel == 0) {  // the TMA kernel was requested but cannot run this case
+        sllbm_destroy(c);
+        return SLLBM_EINVAL;
     }
     *out = c;
     return SLLBM_OK;
@@ -513,6 +545,7 @@ int sllbm_get_info(const sllbm_ctx* ctx, sllbm_info_t* info) {
     info->pop_bytes = ctx->pop_bytes;
     info->storage = ctx->prm.storage;
     info->max_cell_shift = ctx->max_shift;
+    info->step_kernel = ctx->step_kernel;
     return SLLBM_OK;
 }
 
@@ -535,6 +568,7 @@ int sllbm_set_buffers(sllbm_ctx* ctx, void* popA, void* popB, size_t bytes) {
     ctx->buf[1] = popB;
     ctx->cur = 0;
     ctx->initialised = false;
+    ctx->tmap_src[0] = ctx->tmap_src[1] = nullptr;  // TMA descriptors describe old buffers
     return SLLBM_OK;
 }
 
@@ -578,31 +612,28 @@ int sllbm_set_populations(sllbm_ctx* ctx, const double* pop, int on_device) {
     if (rc != SLLBM_OK) return rc;
     const long long count = 2LL * kQ * ctx->nn;
     void* dst = ctx->buf[ctx->cur];
-    if (ctx->prm.storage == SLLBM_F64) {
-        CK(ctx, cudaMemcpyAsync(dst, pop, count * sizeof(double),
-                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
-        if (!on_device) CK(ctx, cudaStreamSynchronize(ctx->stream));
-    } else {
-        const double* src = pop;
-        double* tmp = nullptr;
-        if (!on_device) {
-            CK(ctx, cudaMalloc(&tmp, count * sizeof(double)));
-            cudaError_t e = cudaMemcpyAsync(tmp, pop, count * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
-            if (e != cudaSuccess) {
-                cudaFree(tmp);
-                return fail(ctx, e);
-            }
-            src = tmp;
-        }
-        convert_kernel<double, float><<<grid_for(count, 256), 256, 0, ctx->stream>>>(src, static_cast<float*>(dst), count);
-        ctx->launches += 1;
-        cudaError_t e = cudaGetLastError();
-        if (tmp != nullptr) {
-            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    const double* src = pop;
+    double* tmp = nullptr;
+    if (!on_device) {
+        CK(ctx, cudaMalloc(&tmp, count * sizeof(double)));
+        cudaError_t e = cudaMemcpyAsync(tmp, pop, count * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) {
             cudaFree(tmp);
+            return fail(ctx, e);
         }
-        if (e != cudaSuccess) return fail(ctx, e);
+        src = tmp;
     }
+    if (ctx->prm.storage == SLLBM_F64)
+        pack_kernel<double><<<grid_for(count, 256), 256, 0, ctx->stream>>>(src, static_cast<double*>(dst), ctx->nn);
+    else
+        pack_kernel<float><<<grid_for(count, 256), 256, 0, ctx->stream>>>(src, static_cast<float*>(dst), ctx->nn);
+    ctx->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (tmp != nullptr) {
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        cudaFree(tmp);
+    }
+    if (e != cudaSuccess) return fail(ctx, e);
     ctx->initialised = true;
     return SLLBM_OK;
 }
@@ -612,19 +643,16 @@ int sllbm_get_populations(sllbm_ctx* ctx, double* pop, int on_device) {
     if (!ctx->initialised) return SLLBM_ENOTREADY;
     const long long count = 2LL * kQ * ctx->nn;
     const void* src = ctx->buf[ctx->cur];
-    if (ctx->prm.storage == SLLBM_F64) {
-        CK(ctx, cudaMemcpyAsync(pop, src, count * sizeof(double),
-                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
-        if (!on_device) CK(ctx, cudaStreamSynchronize(ctx->stream));
-        return SLLBM_OK;
-    }
     double* dst = pop;
     double* tmp = nullptr;
     if (!on_device) {
         CK(ctx, cudaMalloc(&tmp, count * sizeof(double)));
         dst = tmp;
     }
-    convert_kernel<float, double><<<grid_for(count, 256), 256, 0, ctx->stream>>>(static_cast<const float*>(src), dst, count);
+    if (ctx->prm.storage == SLLBM_F64)
+        unpack_kernel<double><<<grid_for(count, 256), 256, 0, ctx->stream>>>(static_cast<const double*>(src), dst, ctx->nn);
+    else
+        unpack_kernel<float><<<grid_for(count, 256), 256, 0, ctx->stream>>>(static_cast<const float*>(src), dst, ctx->nn);
     ctx->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (tmp != nullptr) {
@@ -648,10 +676,27 @@ int sllbm_step(sllbm_ctx* ctx, int n) {
         ctx->cur = 1 - ctx->cur;
     }
     if (ctx->prm.nonfinite_check) {
-        int flag = 0;
-        CK(ctx, cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        int flags[2] = {0, 0};
+        CK(ctx, cudaMemcpyAsync(flags, ctx->d_flag, sizeof(flags), cudaMemcpyDeviceToHost, ctx->stream));
         CK(ctx, cudaStreamSynchronize(ctx->stream));
-        if (flag) return SLLBM_ENONFINITE;
+        if (flags[1]) {
+            CK(ctx, cudaMemsetAsync(ctx->d_flag + 1, 0, sizeof(int), ctx->stream));
+            return SLLBM_ETIMEOUT;
+        }
+        if (flags[0]) return SLLBM_ENONFINITE;
+    }
+    return SLLBM_OK;
+}
+
+int sllbm_status(sllbm_ctx* ctx) {
+    if (ctx == nullptr) return SLLBM_EINVAL;
+    int err = 0;
+    CK(ctx, cudaMemcpyAsync(&err, ctx->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (err) {
+        CK(ctx, cudaMemsetAsync(ctx->d_flag + 1, 0, sizeof(int), ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        return SLLBM_ETIMEOUT;
     }
     return SLLBM_OK;
 }

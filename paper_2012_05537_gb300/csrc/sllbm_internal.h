@@ -37,6 +37,10 @@ struct sllbm_ctx {
     int partial_blocks;
     unsigned char* step_blob;  // StepTables<C,P> of the storage type, built on first step
     size_t step_blob_size;
+    int num_sms;
+    int step_kernel;           // 1: generic tile kernel, 2: TMA-fed persistent kernel
+    alignas(64) unsigned char tmap[2][128];  // TMA descriptors (CUtensorMap) per source buffer
+    const void* tmap_src[2];
     int last_err;
     long long launches;
 };
@@ -70,6 +74,7 @@ struct StepArgs {
     int pr;             // Prandtl term on
     int collide;        // 0: stream only
     int* flag;          // non-finite flag or nullptr
+    int* flag_err;      // set (bit 2) when a bounded device-side wait gave up
 };
 
 template <typename C, int P>
@@ -99,5 +104,8 @@ int launch_step_f32(sllbm_ctx* ctx, const void* src, void* dst);
 int launch_step_f64(sllbm_ctx* ctx, const void* src, void* dst);
 
 void fill_step_args(const sllbm_ctx* ctx, const void* src, void* dst, StepArgs* a);
+
+// True when the TMA-fed FP32 kernel can run this context (step_f32.cu).
+bool tma_step_eligible(const sllbm_ctx* c);
 
 }  // namespace sllbm

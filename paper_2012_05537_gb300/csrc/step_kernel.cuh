@@ -46,7 +46,7 @@ __device__ __forceinline__ int wrap_index(int v, int n) {
 }
 
 // Moments, equilibrium and collision of one node whose streamed populations are
-// h[q*stride], q = 0..89; the result goes to dst[q*nn].
+// h[q*stride], q = 0..89 (f then g); the result f_i, g_i goes to dst[2*i*nn + {0,1}].
 template <typename S, typename C, int P, bool PR>
 __device__ __forceinline__ void collide_node(const C* __restrict__ h, int stride, const StepArgs& a,
                                              const StepTables<C, P>& t, S* __restrict__ dst) {
@@ -69,7 +69,8 @@ __device__ __forceinline__ void collide_node(const C* __restrict__ h, int stride
     const long long nn = a.nn;
     if (!a.collide) {
 #pragma unroll 9
-        for (int q = 0; q < 2 * kQ; ++q) dst[q * nn] = static_cast<S>(h[q * stride]);
+        for (int q = 0; q < 2 * kQ; ++q)
+            dst[2 * (q % kQ) * nn + q / kQ] = static_cast<S>(h[q * stride]);
         return;
     }
     // tau = mu/(P dt) + 1/2, P = rho T, mu = Sutherland(T) mu_inf  (Sec. II.A, III.C)
@@ -124,8 +125,8 @@ __device__ __forceinline__ void collide_node(const C* __restrict__ h, int stride
             fo += ompr * fst;
             go += ompr * gT * fst;
         }
-        dst[i * nn] = static_cast<S>(fo);
-        dst[(kQ + i) * nn] = static_cast<S>(go);
+        dst[2 * i * nn] = static_cast<S>(fo);
+        dst[2 * i * nn + 1] = static_cast<S>(go);
     }
 }
 
@@ -166,7 +167,8 @@ __global__ void __launch_bounds__(NW * 32, 1)
         for (int e = lane; e < s[1]; e += 32) yo[e] = wrap_index(b0[1] + e, a.N[1]) * a.N[0];
         for (int e = lane; e < s[2]; e += 32) zo[e] = wrap_index(b0[2] + e, a.N[2]) * nxy;
         __syncwarp();
-        const S* __restrict__ sq = src + static_cast<long long>(q) * a.nn;
+        // storage order [i][node][h]: population q = (h, i) is every second element
+        const S* __restrict__ sq = src + 2LL * i * a.nn + (q < kQ ? 0 : 1);
         const int sxy = s[0] * s[1];
         const int tot = sxy * s[2];
         for (int e = lane; e < tot; e += 32) {
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
             const int r = e - z * sxy;
             const int y = r / s[0];
             const int x = r - y * s[0];
-            box[e] = static_cast<C>(__ldg(sq + zo[z] + yo[y] + xo[x]));
+            box[e] = static_cast<C>(__ldg(sq + 2 * (zo[z] + yo[y] + xo[x])));
         }
         __syncwarp();
         // z pass: tmp1[oz][y][x] = sum_l Lz[az][l] box[zb+l][y][x]
@@ -233,7 +235,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
         if (ox >= te[0] || oy >= te[1] || oz >= te[2]) continue;
         const long long g = (static_cast<long long>(c0[2] * P + oz) * a.N[1] + (c0[1] * P + oy)) * a.N[0]
                           + (c0[0] * P + ox);
-        collide_node<S, C, P, PR>(out + n, TS::TILE, a, t, dst + g);
+        collide_node<S, C, P, PR>(out + n, TS::TILE, a, t, dst + 2 * g);
     }
 }
 

@@ -1,0 +1,527 @@
+// Fused SLLBM step for FP32 storage on sm_100-family GPUs: TMA-fed, warp-specialised,
+// persistent.  Same arithmetic as step_kernel.cuh (Eq. interpolation, Eq. moments,
+// Eq. discreteEquilibrium, Eq. LBM), organised for GB300:
+//
+//  * One persistent CTA per SM walks tiles of CX x CY x CZ cells (TX x TY x TZ nodes).
+//  * A producer warp loads, for every velocity i of a tile, the source box of the pair
+//    (f_i, g_i) -- the tile translated by the departure cell shift, plus one cell and the
+//    shared face -- into a ring of shared-memory slots: one 4D TMA load
+//    (cp.async.bulk.tensor) when the box lies inside the periodic domain, 16-byte
+//    cp.async copies with wrapped coordinates when it crosses the boundary.  Slots are
+//    handed over with mbarriers (transaction counts for TMA).
+//  * NC consumer warps own 45/NC velocity pairs each.  For a pair they run the z and y
+//    Lagrange passes in place in the slot (each lane owns whole columns), release the
+//    slot after the x pass, and keep the streamed (f_i, g_i) of the TX nodes of their
+//    lane's x-row in registers.  f_i and g_i share weights and positions, so every FMA
+//    is a packed FP32x2 FMA.
+//  * Moments are summed per warp over its pairs, reduced across warps through shared
+//    memory in a fixed order, turned into rho, u, T, omega and the shell coefficients
+//    of the quartic equilibrium, and each warp finishes the collision of its own pairs
+//    and stores them (16-byte stores, f_i and g_i interleaved).
+//  * Every mbarrier wait is bounded; on expiry the kernel raises an error flag, the
+//    consumers leave together at the next tile barrier and the producer waits (bounded)
+//    for its copies in flight before returning.
+#pragma once
+
+#include <cuda.h>
+
+#include <cstdint>
+
+#include "collide.cuh"
+#include "sllbm_internal.h"
+
+namespace sllbm {
+
+template <int P>
+struct StepTablesF2 {
+    float2 lw2[kQ][3][P][P + 1];  // Lagrange weight w stored as {w, w} for packed FMAs
+    signed char kc[kQ][3][P];     // departure cell shift minus kmin (0 or 1)
+    signed char kmin[kQ][3];
+    signed char span[kQ][3];
+    float xi[kQ][3];
+    float w[kQ];
+};
+
+template <int P, int CX, int CY, int CZ>
+struct TmaGeom {
+    static constexpr int TX = CX * P, TY = CY * P, TZ = CZ * P;
+    static constexpr int TILE = TX * TY * TZ;
+    static constexpr int ROWS = TY * TZ;  // x-rows of a tile, one per lane
+    static constexpr int BX = (CX + 1) * P + 1, BY = (CY + 1) * P + 1, BZ = (CZ + 1) * P + 1;
+    static constexpr int BXP = ((BX + 1) + 1) / 2 * 2;  // pairs per box row: even start + offset
+    static constexpr int PLANE = BY * BXP;              // float2 per box plane
+    static constexpr int BOX = BZ * PLANE;              // float2 per box
+    static constexpr uint32_t BOX_BYTES = BOX * 8u;
+    static constexpr int SLOT_BYTES = (BOX * 8 + 127) / 128 * 128;
+    static_assert(ROWS <= 32, "one x-row per lane");
+    static_assert(BXP % 2 == 0 && BXP >= BX + 1, "TMA rows start on an even pair");
+};
+
+constexpr int kNParams = 20;  // rho, ux, uy, uz, gT, omega, c0[4], c1[4], c2[4], (2 spare)
+
+template <int P, int CX, int CY, int CZ, int NC, int NSLOT>
+struct TmaSmem {
+    using G = TmaGeom<P, CX, CY, CZ>;
+    // every region starts on a 128-byte boundary (TMA destinations, float4 and mbarrier
+    // alignment)
+    static constexpr size_t round128(size_t b) { return (b + 127) / 128 * 128; }
+    static constexpr size_t slots = size_t(NSLOT) * G::SLOT_BYTES;
+    static constexpr size_t partials = round128(size_t(NC) * 5 * G::TILE * sizeof(float));
+    static constexpr size_t params = round128(size_t(kNParams) * G::TILE * sizeof(float));
+    static constexpr size_t bars = size_t(2) * NSLOT * sizeof(uint64_t) + 16;
+    static constexpr size_t bytes = slots + partials + params + bars + 128;  // +128 for base alignment
+};
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// One poll: the thread may sleep until the phase completes, but at most ~1 us (the
+// suspend-time hint), so `limit` polls bound the wall time of a wait.
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(1000u)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase `parity` of an mbarrier.  Gives up when another warp raised
+// the CTA abort flag or after `limit` polls (then raises it and the global error bit).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                                  int* err_flag, uint32_t limit) {
+    for (uint32_t it = 0; it < limit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 15u) == 15u && *abort_flag) return false;
+    }
+    *abort_flag = 1;
+    if (err_flag != nullptr) atomicOr(err_flag, 2);
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_mbar_arrive(uint32_t bar) {
+    asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Named barrier 1 over the consumer warps with an OR vote (all threads get the same answer).
+__device__ __forceinline__ int consumer_barrier_or(int v, int nthreads) {
+    uint32_t out;
+    asm volatile(
+        "{\n\t.reg .pred pin, pout;\n\tsetp.ne.u32 pin, %1, 0;\n\t"
+        "barrier.cta.red.or.pred pout, 1, %2, pin;\n\tselp.u32 %0, 1, 0, pout;\n\t}"
+        : "=r"(out)
+        : "r"(v), "r"(nthreads)
+        : "memory");
+    return static_cast<int>(out);
+}
+
+__device__ __forceinline__ int wrapi(int v, int n) {
+    int r = v % n;
+    return r < 0 ? r + n : r;
+}
+
+// ------------------------------------------------------------------ kernel
+template <int P, int CX, int CY, int CZ, int NC, int NSLOT>
+__global__ void __launch_bounds__((NC + 1) * 32, 1)
+    step_tma_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs a,
+                    const __grid_constant__ StepTablesF2<P> t) {
+    using G = TmaGeom<P, CX, CY, CZ>;
+    using SM = TmaSmem<P, CX, CY, CZ, NC, NSLOT>;
+    constexpr int NPW = kQ / NC;  // velocity pairs per consumer warp
+    static_assert(NPW * NC == kQ, "consumers must split the 45 pairs evenly");
+    constexpr uint32_t kWaitLimit = 1u << 22;  // polls of <= 1 us: about 4 s before giving up
+
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    float2* slots = reinterpret_cast<float2*>(base);
+    float* part = reinterpret_cast<float*>(base + SM::slots);
+    float* prm = reinterpret_cast<float*>(base + SM::slots + SM::partials);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + SM::slots + SM::partials + SM::params);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * NSLOT);
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + NSLOT);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSLOT; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    const int ntx = a.cells[0] / CX, nty = a.cells[1] / CY, ntz = a.cells[2] / CZ;
+    const int ntiles = ntx * nty * ntz;
+    int* err_flag = a.flag_err;
+
+    if (warp == NC) {
+        // ------------------------------------------------ producer warp
+        long long s = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const int c0[3] = {(tile % ntx) * CX, ((tile / ntx) % nty) * CY, (tile / (ntx * nty)) * CZ};
+            const int cd[3] = {CX, CY, CZ};
+            for (int j = 0; j < kQ; ++j, ++s) {
+                const int slot = static_cast<int>(s % NSLOT);
+                const uint32_t ph = static_cast<uint32_t>((s / NSLOT) & 1);
+                if (!mbar_wait_bounded(empty0 + 8 * slot, ph ^ 1u, abort_flag, err_flag, kWaitLimit)) {
+                    ok = false;
+                    break;
+                }
+                int b0[3];
+                bool cross = false;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    b0[d] = (c0[d] + t.kmin[j][d]) * P;
+                    const int need = (cd[d] + t.span[j][d]) * P + 1;
+                    cross |= (b0[d] < 0) || (b0[d] + need > a.N[d]);
+                }
+                const int x0 = b0[0] - (b0[0] & 1);  // even pair index (floor for negatives)
+                const uint32_t dst = smem_u32(slots) + static_cast<uint32_t>(slot) * G::SLOT_BYTES;
+                const uint32_t full = full0 + 8 * slot;
+                if (!cross) {
+                    if (lane == 0) {
+                        mbar_arrive_expect_tx(full, G::BOX_BYTES);
+                        tma_load_4d(dst, &tmap, 2 * x0, b0[1], b0[2], j, full);
+                    }
+                } else {
+                    // wrapped 16-byte copies: a chunk is two (f,g) pairs at an even x, and N[0]
+                    // is even, so a chunk never straddles the periodic boundary
+                    const float* src = static_cast<const float*>(a.src) + 2LL * j * a.nn;
+                    constexpr int CH = G::BXP / 2;
+                    constexpr int NCHUNK = G::BZ * G::BY * CH;
+                    for (int q = lane; q < NCHUNK; q += 32) {
+                        const int c = q % CH;
+                        const int row = q / CH;
+                        const int y = row % G::BY, z = row / G::BY;
+                        const int gx = wrapi(x0 + 2 * c, a.N[0]);
+                        const int gy = wrapi(b0[1] + y, a.N[1]);
+                        const int gz = wrapi(b0[2] + z, a.N[2]);
+                        const long long off = 2LL * ((static_cast<long long>(gz) * a.N[1] + gy) * a.N[0] + gx);
+                        cp_async16(dst + static_cast<uint32_t>((row * G::BXP + 2 * c) * 8), src + off);
+                    }
+                    cp_async_mbar_arrive(full);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(full);
+                }
+            }
+        }
+        if (!ok) {
+            // drain: wait (bounded) for the fills this warp may still have in flight
+            for (long long r = s - NSLOT; r < s; ++r) {
+                if (r < 0) continue;
+                mbar_wait_bounded(full0 + 8 * static_cast<int>(r % NSLOT), static_cast<uint32_t>((r / NSLOT) & 1),
+                                  abort_flag, nullptr, 1u << 18);
+            }
+        }
+        return;
+    }
+
+    // ---------------------------------------------------- consumer warps
+    const int c = warp;
+    const bool row_lane = lane < G::ROWS;
+    const int oz_l = lane / G::TY, oy_l = lane % G::TY;
+    float2 acc[NPW][G::TX];
+#pragma unroll
+    for (int k = 0; k < NPW; ++k)
+#pragma unroll
+        for (int x = 0; x < G::TX; ++x) acc[k][x] = make_float2(0.f, 0.f);
+
+    long long tau = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tau) {
+        const int c0[3] = {(tile % ntx) * CX, ((tile / ntx) % nty) * CY, (tile / (ntx * nty)) * CZ};
+#pragma unroll 1
+        for (int k = 0; k < NPW; ++k) {
+            const int j = c + NC * k;
+            const long long s = tau * kQ + j;
+            const int slot = static_cast<int>(s % NSLOT);
+            const uint32_t ph = static_cast<uint32_t>((s / NSLOT) & 1);
+            mbar_wait_bounded(full0 + 8 * slot, ph, abort_flag, err_flag, kWaitLimit);
+            float2* box = slots + static_cast<size_t>(slot) * (G::SLOT_BYTES / 8);
+            const int ox0 = ((c0[0] + t.kmin[j][0]) * P) & 1;
+
+            // z pass, in place: column (y, xb) of the box, planes -> output planes 0..TZ-1
+            {
+                float2 wz[P][P + 1];
+                bool kz[P];
+#pragma unroll
+                for (int az = 0; az < P; ++az) {
+                    kz[az] = t.kc[j][2][az] != 0;
+#pragma unroll
+                    for (int l = 0; l <= P; ++l) wz[az][l] = t.lw2[j][2][az][l];
+                }
+#pragma unroll
+                for (int it = 0; it < (G::PLANE + 31) / 32; ++it) {
+                    const int e = lane + 32 * it;
+                    if (e < G::PLANE) {
+                        float2 v[G::BZ];
+#pragma unroll
+                        for (int z = 0; z < G::BZ; ++z) v[z] = box[z * G::PLANE + e];
+#pragma unroll
+                        for (int oz = 0; oz < G::TZ; ++oz) {
+                            const int cz = oz / P, az = oz % P;
+                            float2 o = make_float2(0.f, 0.f);
+                            if (kz[az]) {
+#pragma unroll
+                                for (int l = 0; l <= P; ++l) o = ffma2(v[(cz + 1) * P + l], wz[az][l], o);
+                            } else {
+#pragma unroll
+                                for (int l = 0; l <= P; ++l) o = ffma2(v[cz * P + l], wz[az][l], o);
+                            }
+                            box[oz * G::PLANE + e] = o;
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            // y pass, in place: column (oz, xb), rows -> output rows 0..TY-1
+            {
+                float2 wy[P][P + 1];
+                bool ky[P];
+#pragma unroll
+                for (int ay = 0; ay < P; ++ay) {
+                    ky[ay] = t.kc[j][1][ay] != 0;
+#pragma unroll
+                    for (int l = 0; l <= P; ++l) wy[ay][l] = t.lw2[j][1][ay][l];
+                }
+#pragma unroll
+                for (int it = 0; it < (G::TZ * G::BXP + 31) / 32; ++it) {
+                    const int e = lane + 32 * it;
+                    if (e < G::TZ * G::BXP) {
+                        const int oz = e / G::BXP, xb = e - oz * G::BXP;
+                        float2* col = box + oz * G::PLANE + xb;
+                        float2 v[G::BY];
+#pragma unroll
+                        for (int y = 0; y < G::BY; ++y) v[y] = col[y * G::BXP];
+#pragma unroll
+                        for (int oy = 0; oy < G::TY; ++oy) {
+                            const int cy = oy / P, ay = oy % P;
+                            float2 o = make_float2(0.f, 0.f);
+                            if (ky[ay]) {
+#pragma unroll
+                                for (int l = 0; l <= P; ++l) o = ffma2(v[(cy + 1) * P + l], wy[ay][l], o);
+                            } else {
+#pragma unroll
+                                for (int l = 0; l <= P; ++l) o = ffma2(v[cy * P + l], wy[ay][l], o);
+                            }
+                            col[oy * G::BXP] = o;
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            // x pass: lane = x-row (oz, oy) of the tile; results stay in registers
+            float2 res[G::TX];
+            {
+                float2 wx[P][P + 1];
+                bool kx[P];
+#pragma unroll
+                for (int ax = 0; ax < P; ++ax) {
+                    kx[ax] = t.kc[j][0][ax] != 0;
+#pragma unroll
+                    for (int l = 0; l <= P; ++l) wx[ax][l] = t.lw2[j][0][ax][l];
+                }
+                float2 v[G::BX];
+                const float2* row = box + oz_l * G::PLANE + oy_l * G::BXP + ox0;
+#pragma unroll
+                for (int x = 0; x < G::BX; ++x) v[x] = row_lane ? row[x] : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int ox = 0; ox < G::TX; ++ox) {
+                    const int cx = ox / P, ax = ox % P;
+                    float2 o = make_float2(0.f, 0.f);
+                    if (kx[ax]) {
+#pragma unroll
+                        for (int l = 0; l <= P; ++l) o = ffma2(v[(cx + 1) * P + l], wx[ax][l], o);
+                    } else {
+#pragma unroll
+                        for (int l = 0; l <= P; ++l) o = ffma2(v[cx * P + l], wx[ax][l], o);
+                    }
+                    res[ox] = o;
+                }
+            }
+            // the slot was written in place (generic proxy); order that before the next TMA fill
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty0 + 8 * slot);
+            switch (k) {
+#define SLLBM_KEEP(K)                                                   \
+    case K:                                                             \
+        if (K < NPW) {                                                  \
+            _Pragma("unroll") for (int x = 0; x < G::TX; ++x) acc[K < NPW ? K : 0][x] = res[x]; \
+        }                                                               \
+        break;
+                SLLBM_KEEP(0)
+                SLLBM_KEEP(1)
+                SLLBM_KEEP(2)
+                SLLBM_KEEP(3)
+                SLLBM_KEEP(4)
+                SLLBM_KEEP(5)
+                SLLBM_KEEP(6)
+                SLLBM_KEEP(7)
+                SLLBM_KEEP(8)
+#undef SLLBM_KEEP
+            default:
+                break;
+            }
+        }
+
+        // partial moments of this warp's pairs for the TX nodes of the lane's row
+        if (row_lane) {
+#pragma unroll
+            for (int x = 0; x < G::TX; x += 4) {
+                float4 pr = make_float4(0, 0, 0, 0), pmx = pr, pmy = pr, pmz = pr, pe = pr;
+                float* prf = &pr.x;
+                float* mxf = &pmx.x;
+                float* myf = &pmy.x;
+                float* mzf = &pmz.x;
+                float* ef = &pe.x;
+#pragma unroll
+                for (int q = 0; q < 4 && x + q < G::TX; ++q) {
+#pragma unroll
+                    for (int k = 0; k < NPW; ++k) {
+                        const int j = c + NC * k;
+                        const float f = acc[k][x + q].x, g = acc[k][x + q].y;
+                        prf[q] += f;
+                        mxf[q] += f * t.xi[j][0];
+                        myf[q] += f * t.xi[j][1];
+                        mzf[q] += f * t.xi[j][2];
+                        ef[q] += f * static_cast<float>(shell_xi2(shell_of(j))) + g;
+                    }
+                }
+                const int n = lane * G::TX + x;
+                float* pc = part + static_cast<size_t>(c) * 5 * G::TILE;
+                if (G::TX % 4 == 0) {
+                    *reinterpret_cast<float4*>(pc + 0 * G::TILE + n) = pr;
+                    *reinterpret_cast<float4*>(pc + 1 * G::TILE + n) = pmx;
+                    *reinterpret_cast<float4*>(pc + 2 * G::TILE + n) = pmy;
+                    *reinterpret_cast<float4*>(pc + 3 * G::TILE + n) = pmz;
+                    *reinterpret_cast<float4*>(pc + 4 * G::TILE + n) = pe;
+                } else {
+                    for (int q = 0; q < 4 && x + q < G::TX; ++q) {
+                        pc[0 * G::TILE + n + q] = prf[q];
+                        pc[1 * G::TILE + n + q] = mxf[q];
+                        pc[2 * G::TILE + n + q] = myf[q];
+                        pc[3 * G::TILE + n + q] = mzf[q];
+                        pc[4 * G::TILE + n + q] = ef[q];
+                    }
+                }
+            }
+        }
+        if (consumer_barrier_or(*abort_flag, NC * 32)) break;
+
+        // per-node moments (fixed-order sum over warps), tau, equilibrium coefficients
+        for (int n = threadIdx.x; n < G::TILE; n += NC * 32) {
+            float m[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+            for (int w = 0; w < NC; ++w)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) m[q] += part[(static_cast<size_t>(w) * 5 + q) * G::TILE + n];
+            const float rho = m[0];
+            const float inv_rho = 1.0f / rho;
+            const float ux = m[1] * inv_rho, uy = m[2] * inv_rho, uz = m[3] * inv_rho;
+            const float usq = ux * ux + uy * uy + uz * uz;
+            const float T = (m[4] * inv_rho - usq) * static_cast<float>(a.inv_2cv);
+            if (a.flag != nullptr && !(rho > 0.f && T > 0.f && isfinite(rho) && isfinite(T))) atomicOr(a.flag, 1);
+            const float tau_r = static_cast<float>(a.mu_over_dt) * sutherland(T) / (rho * T) + 0.5f;
+            const EqCoef<float> ec = eq_coefficients(usq, T - 1.0f);
+            prm[0 * G::TILE + n] = rho;
+            prm[1 * G::TILE + n] = ux;
+            prm[2 * G::TILE + n] = uy;
+            prm[3 * G::TILE + n] = uz;
+            prm[4 * G::TILE + n] = static_cast<float>(a.gfac) * T;
+            prm[5 * G::TILE + n] = 1.0f / tau_r;
+#pragma unroll
+            for (int sh = 0; sh < 4; ++sh) {
+                prm[(6 + sh) * G::TILE + n] = ec.c0[sh];
+                prm[(10 + sh) * G::TILE + n] = ec.c1[sh];
+                prm[(14 + sh) * G::TILE + n] = ec.c2[sh];
+            }
+        }
+        consumer_barrier_or(0, NC * 32);
+
+        // collision of this warp's pairs at the lane's TX nodes, 16-byte stores
+        if (row_lane) {
+            const long long g0 =
+                (static_cast<long long>(c0[2] * P + oz_l) * a.N[1] + (c0[1] * P + oy_l)) * a.N[0] + c0[0] * P;
+            float2* dst = static_cast<float2*>(a.dst);
+#pragma unroll
+            for (int x = 0; x < G::TX; ++x) {
+                const int n = lane * G::TX + x;
+                float pv[18];
+#pragma unroll
+                for (int q = 0; q < 18; ++q) pv[q] = prm[q * G::TILE + n];
+                const float rho = pv[0], ux = pv[1], uy = pv[2], uz = pv[3], gT = pv[4], om = pv[5];
+#pragma unroll
+                for (int k = 0; k < NPW; ++k) {
+                    const int j = c + NC * k;
+                    const int sh = shell_of(j);
+                    const float s = t.xi[j][0] * ux + t.xi[j][1] * uy + t.xi[j][2] * uz;
+                    const float poly = pv[6 + sh] + s * (pv[10 + sh] + s * (pv[14 + sh] + s * (1.0f / 6.0f + s * (1.0f / 24.0f))));
+                    const float feq = t.w[j] * rho * poly;
+                    const float2 h = acc[k][x];
+                    acc[k][x] = make_float2(h.x + om * (feq - h.x), h.y + om * (gT * feq - h.y));
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NPW; ++k) {
+                const int j = c + NC * k;
+                float2* out = dst + static_cast<long long>(j) * a.nn + g0;
+                if (G::TX % 2 == 0) {
+#pragma unroll
+                    for (int x = 0; x < G::TX; x += 2)
+                        *reinterpret_cast<float4*>(out + x) =
+                            make_float4(acc[k][x].x, acc[k][x].y, acc[k][x + 1].x, acc[k][x + 1].y);
+                } else {
+#pragma unroll
+                    for (int x = 0; x < G::TX; ++x) out[x] = acc[k][x];
+                }
+            }
+        }
+    }
+}
+
+}  // namespace sllbm

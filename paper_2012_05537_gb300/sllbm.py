@@ -42,7 +42,8 @@ class Params(ctypes.Structure):
                 ("dt_or_courant", ctypes.c_double), ("dt_is_courant", ctypes.c_int),
                 ("pr_correction", ctypes.c_int), ("storage", ctypes.c_int),
                 ("nonfinite_check", ctypes.c_int), ("tgv_C", ctypes.c_double),
-                ("mu_inf_override", ctypes.c_double), ("collide", ctypes.c_int)]
+                ("mu_inf_override", ctypes.c_double), ("collide", ctypes.c_int),
+                ("kernel", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -50,7 +51,7 @@ class Info(ctypes.Structure):
                 ("Q", ctypes.c_int), ("dt", ctypes.c_double), ("U0", ctypes.c_double),
                 ("mu_inf", ctypes.c_double), ("max_xi", ctypes.c_double),
                 ("pop_bytes", ctypes.c_size_t), ("storage", ctypes.c_int),
-                ("max_cell_shift", ctypes.c_int)]
+                ("max_cell_shift", ctypes.c_int), ("step_kernel", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -88,6 +89,7 @@ def load(build_if_missing: bool = False):
         "sllbm_diag_noalloc": (ctypes.c_int, [vp, dp, dp, dp]),
         "sllbm_run_host": (ctypes.c_int, [vp, vp, vp, ctypes.c_int]),
         "sllbm_sync": (ctypes.c_int, [vp]),
+        "sllbm_status": (ctypes.c_int, [vp]),
         "sllbm_last_cuda_error": (ctypes.c_int, [vp]),
         "sllbm_launch_count": (ctypes.c_int64, [vp]),
         "sllbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -210,6 +212,13 @@ def sllbm_run_host(ctx, in_ptr: int, out_ptr: int, n: int) -> None:
            "sllbm_run_host", ctx)
 
 
+def sllbm_status(ctx) -> int:
+    rc = load().sllbm_status(ctx)
+    if rc not in (OK, ETIMEOUT):
+        _check(rc, "sllbm_status", ctx)
+    return rc
+
+
 def sllbm_sync(ctx) -> None:
     _check(load().sllbm_sync(ctx), "sllbm_sync", ctx)
 
@@ -255,6 +264,7 @@ class Config:
     tgv_C: float = -1.0
     mu_inf: float | None = None
     collide: bool = True
+    kernel: int = 0  # 0 automatic, 1 generic tile kernel, 2 TMA-fed persistent kernel
     L: tuple = (2 * np.pi, 2 * np.pi, 2 * np.pi)
 
 
@@ -286,6 +296,7 @@ class Sim:
         prm.tgv_C = float(cfg.tgv_C)
         prm.mu_inf_override = float(cfg.mu_inf) if cfg.mu_inf else 0.0
         prm.collide = int(bool(cfg.collide))
+        prm.kernel = int(cfg.kernel)
         with torch.cuda.device(self.device):
             self.ctx = sllbm_create(mesh, cfg.p, prm, self.stream.cuda_stream)
         self.info = sllbm_get_info(self.ctx)
@@ -342,10 +353,11 @@ class Sim:
         return out
 
     def raw_state(self):
-        """Current state buffer viewed in the storage dtype, [2, 45, Nz, Ny, Nx] (no copy)."""
+        """Current state buffer viewed in the storage dtype and storage order,
+        [45, Nz, Ny, Nx, 2] with the last index 0 for f and 1 for g (no copy)."""
         cur = sllbm_current_buffer(self.ctx)
         idx = 0 if cur == self.buffers[0].data_ptr() else 1
-        return self.buffers[idx].view(self.pop_dtype).view((2, Q) + self.N[::-1])
+        return self.buffers[idx].view(self.pop_dtype).view((Q,) + self.N[::-1] + (2,))
 
     def step(self, n: int = 1) -> int:
         return sllbm_step(self.ctx, n)
@@ -368,6 +380,9 @@ class Sim:
 
     def sync(self):
         sllbm_sync(self.ctx)
+
+    def status(self) -> int:
+        return sllbm_status(self.ctx)
 
     def launches(self) -> int:
         return sllbm_launch_count(self.ctx)

@@ -28,8 +28,12 @@ template <>
 struct TmaTile<4> {
     static constexpr int CX = 2, CY = 2, CZ = 1;
 };
-constexpr int kConsumers = 9;  // 45 velocity pairs = 9 warps x 5
-constexpr int kSlots = 12;     // source boxes in flight per SM
+// Consumer warps (45 velocity pairs split evenly: 9 x 5) and source boxes in flight per SM
+// (what fits next to partials, params and tables).
+template <int P>
+constexpr int kConsumersFor = 9;
+template <int P>
+constexpr int kSlotsFor = P == 4 ? 11 : 12;
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static std::once_flag once;
@@ -46,7 +50,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 template <int P>
-void fill_tables_f2(const sllbm_ctx* ctx, StepTablesF2<P>* t) {
+void fill_tables_s(const sllbm_ctx* ctx, StepTablesS<P>* t) {
     for (int i = 0; i < kQ; ++i) {
         for (int d = 0; d < 3; ++d) {
             int kmn = ctx->dir[d].shift[i][0], kmx = kmn;
@@ -60,8 +64,7 @@ void fill_tables_f2(const sllbm_ctx* ctx, StepTablesF2<P>* t) {
             for (int a = 0; a < P; ++a) {
                 t->kc[i][d][a] = static_cast<signed char>(ctx->dir[d].shift[i][a] - kmn);
                 for (int j = 0; j <= P; ++j) {
-                    const float w = static_cast<float>(ctx->dir[d].weight[i][a][j]);
-                    t->lw2[i][d][a][j] = make_float2(w, w);
+                    t->lw[i][d][a][j] = static_cast<float>(ctx->dir[d].weight[i][a][j]);
                 }
             }
             t->xi[i][d] = static_cast<float>(ctx->xi[i][d]);
@@ -107,15 +110,16 @@ int tensor_map_for(sllbm_ctx* ctx, const void* src, CUtensorMap* out) {
 template <int P>
 int launch_tma(sllbm_ctx* ctx, const void* src, void* dst) {
     using T = TmaTile<P>;
-    using SM = TmaSmem<P, T::CX, T::CY, T::CZ, kConsumers, kSlots>;
+    constexpr int kConsumers = kConsumersFor<P>;
+    using SM = TmaSmem<P, T::CX, T::CY, T::CZ, kConsumers, kSlotsFor<P>>;
     static_assert(SM::bytes <= 227 * 1024, "shared memory budget");
-    using Tab = StepTablesF2<P>;
+    using Tab = StepTablesS<P>;
     if (ctx->step_blob == nullptr || ctx->step_blob_size != sizeof(Tab) + 1) {
         std::free(ctx->step_blob);
         ctx->step_blob = static_cast<unsigned char*>(std::malloc(sizeof(Tab)));
         if (ctx->step_blob == nullptr) return SLLBM_ENOMEM;
         ctx->step_blob_size = sizeof(Tab) + 1;  // +1 keeps it distinct from the generic tables
-        fill_tables_f2<P>(ctx, reinterpret_cast<Tab*>(ctx->step_blob));
+        fill_tables_s<P>(ctx, reinterpret_cast<Tab*>(ctx->step_blob));
     }
     CUtensorMap map;
     int rc = tensor_map_for<P>(ctx, src, &map);
@@ -124,7 +128,7 @@ int launch_tma(sllbm_ctx* ctx, const void* src, void* dst) {
     fill_step_args(ctx, src, dst, &args);
     const int ntiles = (ctx->cells[0] / T::CX) * (ctx->cells[1] / T::CY) * (ctx->cells[2] / T::CZ);
     const int grid = ntiles < ctx->num_sms ? ntiles : ctx->num_sms;
-    auto k = step_tma_kernel<P, T::CX, T::CY, T::CZ, kConsumers, kSlots>;
+    auto k = step_tma_kernel<P, T::CX, T::CY, T::CZ, kConsumers, kSlotsFor<P>>;
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(SM::bytes));
     if (err == cudaSuccess) {
         k<<<grid, (kConsumers + 1) * 32, SM::bytes, ctx->stream>>>(map, args, *reinterpret_cast<const Tab*>(ctx->step_blob));

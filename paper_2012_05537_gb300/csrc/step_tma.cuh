@@ -1,6 +1,7 @@
 // Fused SLLBM step for FP32 storage on sm_100-family GPUs: TMA-fed, warp-specialised,
-// persistent.  Same arithmetic as step_kernel.cuh (Eq. interpolation, Eq. moments,
-// Eq. discreteEquilibrium, Eq. LBM), organised for GB300:
+// persistent, with the streamed populations parked in tensor memory.  Same arithmetic as
+// step_kernel.cuh (Eq. interpolation, Eq. moments, Eq. discreteEquilibrium, Eq. LBM),
+// organised for GB300:
 //
 //  * One persistent CTA per SM walks tiles of CX x CY x CZ cells (TX x TY x TZ nodes).
 //  * A producer warp loads, for every velocity i of a tile, the source box of the pair
@@ -10,17 +11,19 @@
 //    cp.async copies with wrapped coordinates when it crosses the boundary.  Slots are
 //    handed over with mbarriers (transaction counts for TMA).
 //  * NC consumer warps own 45/NC velocity pairs each.  For a pair they run the z and y
-//    Lagrange passes in place in the slot (each lane owns whole columns), release the
-//    slot after the x pass, and keep the streamed (f_i, g_i) of the TX nodes of their
-//    lane's x-row in registers.  f_i and g_i share weights and positions, so every FMA
-//    is a packed FP32x2 FMA.
-//  * Moments are summed per warp over its pairs, reduced across warps through shared
-//    memory in a fixed order, turned into rho, u, T, omega and the shell coefficients
-//    of the quartic equilibrium, and each warp finishes the collision of its own pairs
-//    and stores them (16-byte stores, f_i and g_i interleaved).
+//    Lagrange passes in place in the slot (each lane owns whole columns) and the x pass
+//    into registers (lane = one x-row of the tile), then release the slot.  f_i and g_i
+//    share weights and positions, so every FMA is a packed FP32x2 FMA.  The streamed
+//    (f_i, g_i) of the lane's TX nodes go to the lane's row of tensor memory
+//    (tcgen05.st), which keeps the register file free for the passes; the per-node
+//    moment contributions are accumulated in registers on the way.
+//  * Per tile, the partial moments are reduced across warps through shared memory in a
+//    fixed order and turned into rho, u, T, omega and the shell coefficients of the
+//    quartic equilibrium; each warp then reads its pairs back (tcgen05.ld), collides and
+//    stores them (16-byte stores, f_i and g_i interleaved).
 //  * Every mbarrier wait is bounded; on expiry the kernel raises an error flag, the
-//    consumers leave together at the next tile barrier and the producer waits (bounded)
-//    for its copies in flight before returning.
+//    consumers leave together at the next tile barrier (and free the tensor memory) and
+//    the producer waits (bounded) for its copies in flight before returning.
 #pragma once
 
 #include <cuda.h>
@@ -32,14 +35,16 @@
 
 namespace sllbm {
 
+// Per-velocity tables; passed by value, then copied once per CTA into shared memory so that
+// every lane reads the (warp-uniform) entries of its pair with broadcast loads.
 template <int P>
-struct StepTablesF2 {
-    float2 lw2[kQ][3][P][P + 1];  // Lagrange weight w stored as {w, w} for packed FMAs
-    signed char kc[kQ][3][P];     // departure cell shift minus kmin (0 or 1)
-    signed char kmin[kQ][3];
-    signed char span[kQ][3];
+struct StepTablesS {
+    float lw[kQ][3][P][P + 1];  // Lagrange weights per (velocity, direction, local node)
     float xi[kQ][3];
     float w[kQ];
+    signed char kc[kQ][3][P];   // departure cell shift minus kmin (0 or 1)
+    signed char kmin[kQ][3];
+    signed char span[kQ][3];
 };
 
 template <int P, int CX, int CY, int CZ>
@@ -55,6 +60,7 @@ struct TmaGeom {
     static constexpr int SLOT_BYTES = (BOX * 8 + 127) / 128 * 128;
     static_assert(ROWS <= 32, "one x-row per lane");
     static_assert(BXP % 2 == 0 && BXP >= BX + 1, "TMA rows start on an even pair");
+    static_assert(TX == 8 || TX == 9, "tensor-memory row layout");
 };
 
 constexpr int kNParams = 20;  // rho, ux, uy, uz, gT, omega, c0[4], c1[4], c2[4], (2 spare)
@@ -68,8 +74,20 @@ struct TmaSmem {
     static constexpr size_t slots = size_t(NSLOT) * G::SLOT_BYTES;
     static constexpr size_t partials = round128(size_t(NC) * 5 * G::TILE * sizeof(float));
     static constexpr size_t params = round128(size_t(kNParams) * G::TILE * sizeof(float));
+    static constexpr size_t tables = round128(sizeof(StepTablesS<P>));
     static constexpr size_t bars = size_t(2) * NSLOT * sizeof(uint64_t) + 16;
-    static constexpr size_t bytes = slots + partials + params + bars + 128;  // +128 for base alignment
+    static constexpr size_t bytes = slots + partials + params + tables + bars + 128;  // +128: base alignment
+};
+
+// Tensor-memory columns: a warp's lane keeps NPW pairs x 2*TX floats; warps w, w+4, w+8
+// share a 32-lane quarter (the quarter a warp may touch is fixed by w % 4).
+template <int TX, int NPW, int NC>
+struct TmemCols {
+    static constexpr int per_warp = NPW * 2 * TX;
+    static constexpr int per_quarter = ((NC + 3) / 4) * per_warp;
+    static constexpr int alloc = per_quarter <= 32 ? 32 : per_quarter <= 64 ? 64 : per_quarter <= 128 ? 128
+                               : per_quarter <= 256 ? 256 : 512;
+    static_assert(per_quarter <= 512, "tensor memory columns");
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -158,6 +176,51 @@ __device__ __forceinline__ int consumer_barrier_or(int v, int nthreads) {
     return static_cast<int>(out);
 }
 
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive 32-bit tensor-memory columns of the calling thread's lane.
+__device__ __forceinline__ void tmem_st16(uint32_t ta, const float* v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(ta),
+        "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]),
+        "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st2(uint32_t ta, const float* v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};" ::"r"(ta), "f"(v[0]), "f"(v[1]) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t ta, float* v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]),
+          "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15])
+        : "r"(ta)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld2(uint32_t ta, float* v) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=f"(v[0]), "=f"(v[1]) : "r"(ta) : "memory");
+}
+
+// 2*TX floats (TX = 8 or 9) of one pair at column ta.
+template <int TX>
+__device__ __forceinline__ void tmem_store_row(uint32_t ta, const float* v) {
+    tmem_st16(ta, v);
+    if (TX == 9) tmem_st2(ta + 16, v + 16);
+}
+
+template <int TX>
+__device__ __forceinline__ void tmem_load_row(uint32_t ta, float* v) {
+    tmem_ld16(ta, v);
+    if (TX == 9) tmem_ld2(ta + 16, v + 16);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ int wrapi(int v, int n) {
     int r = v % n;
     return r < 0 ? r + n : r;
@@ -167,11 +230,12 @@ __device__ __forceinline__ int wrapi(int v, int n) {
 template <int P, int CX, int CY, int CZ, int NC, int NSLOT>
 __global__ void __launch_bounds__((NC + 1) * 32, 1)
     step_tma_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs a,
-                    const __grid_constant__ StepTablesF2<P> t) {
+                    const __grid_constant__ StepTablesS<P> tpar) {
     using G = TmaGeom<P, CX, CY, CZ>;
     using SM = TmaSmem<P, CX, CY, CZ, NC, NSLOT>;
     constexpr int NPW = kQ / NC;  // velocity pairs per consumer warp
     static_assert(NPW * NC == kQ, "consumers must split the 45 pairs evenly");
+    using TC = TmemCols<G::TX, NPW, NC>;
     constexpr uint32_t kWaitLimit = 1u << 22;  // polls of <= 1 us: about 4 s before giving up
 
     extern __shared__ unsigned char smem_raw[];
@@ -179,11 +243,20 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
     float2* slots = reinterpret_cast<float2*>(base);
     float* part = reinterpret_cast<float*>(base + SM::slots);
     float* prm = reinterpret_cast<float*>(base + SM::slots + SM::partials);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(base + SM::slots + SM::partials + SM::params);
+    StepTablesS<P>* tsm = reinterpret_cast<StepTablesS<P>*>(base + SM::slots + SM::partials + SM::params);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + SM::slots + SM::partials + SM::params + SM::tables);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * NSLOT);
+    uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(bars + 2 * NSLOT) + 1;
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + NSLOT);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    {
+        // tables into shared memory (sizeof is a multiple of 4)
+        const int* src = reinterpret_cast<const int*>(&tpar);
+        int* dstw = reinterpret_cast<int*>(tsm);
+        for (int q = threadIdx.x; q < static_cast<int>(sizeof(StepTablesS<P>) / 4); q += blockDim.x) dstw[q] = src[q];
+    }
+    const StepTablesS<P>& t = *tsm;
     if (threadIdx.x == 0) {
         for (int s = 0; s < NSLOT; ++s) {
             mbar_init(full0 + 8 * s, 1);
@@ -192,7 +265,16 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (warp == 0) {
+        // tensor memory for the streamed populations, freed by the same warp at the end
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_base_s)),
+                     "r"(static_cast<uint32_t>(TC::alloc))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
     __syncthreads();
+    tc_fence_after();
 
     const int ntx = a.cells[0] / CX, nty = a.cells[1] / CY, ntz = a.cells[2] / CZ;
     const int ntiles = ntx * nty * ntz;
@@ -265,15 +347,19 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
     const int c = warp;
     const bool row_lane = lane < G::ROWS;
     const int oz_l = lane / G::TY, oy_l = lane % G::TY;
-    float2 acc[NPW][G::TX];
-#pragma unroll
-    for (int k = 0; k < NPW; ++k)
-#pragma unroll
-        for (int x = 0; x < G::TX; ++x) acc[k][x] = make_float2(0.f, 0.f);
+    const uint32_t tmem_warp = *tmem_base_s + (static_cast<uint32_t>((warp & 3) * 32) << 16) +
+                               static_cast<uint32_t>((warp >> 2) * TC::per_warp);
 
     long long tau = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tau) {
         const int c0[3] = {(tile % ntx) * CX, ((tile / ntx) % nty) * CY, (tile / (ntx * nty)) * CZ};
+        // per-node moment contributions of this warp's pairs: rho, m_x, m_y, m_z, 2 rho E
+        float pm[5][G::TX];
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+#pragma unroll
+            for (int x = 0; x < G::TX; ++x) pm[q][x] = 0.f;
+
 #pragma unroll 1
         for (int k = 0; k < NPW; ++k) {
             const int j = c + NC * k;
@@ -292,9 +378,9 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
                 for (int az = 0; az < P; ++az) {
                     kz[az] = t.kc[j][2][az] != 0;
 #pragma unroll
-                    for (int l = 0; l <= P; ++l) wz[az][l] = t.lw2[j][2][az][l];
+                    for (int l = 0; l <= P; ++l) wz[az][l] = make_float2(t.lw[j][2][az][l], t.lw[j][2][az][l]);
                 }
-#pragma unroll
+#pragma unroll 2
                 for (int it = 0; it < (G::PLANE + 31) / 32; ++it) {
                     const int e = lane + 32 * it;
                     if (e < G::PLANE) {
@@ -326,9 +412,9 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
                 for (int ay = 0; ay < P; ++ay) {
                     ky[ay] = t.kc[j][1][ay] != 0;
 #pragma unroll
-                    for (int l = 0; l <= P; ++l) wy[ay][l] = t.lw2[j][1][ay][l];
+                    for (int l = 0; l <= P; ++l) wy[ay][l] = make_float2(t.lw[j][1][ay][l], t.lw[j][1][ay][l]);
                 }
-#pragma unroll
+#pragma unroll 1
                 for (int it = 0; it < (G::TZ * G::BXP + 31) / 32; ++it) {
                     const int e = lane + 32 * it;
                     if (e < G::TZ * G::BXP) {
@@ -354,8 +440,8 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
                 }
             }
             __syncwarp();
-            // x pass: lane = x-row (oz, oy) of the tile; results stay in registers
-            float2 res[G::TX];
+            // x pass: lane = x-row (oz, oy) of the tile
+            float res[2 * G::TX];
             {
                 float2 wx[P][P + 1];
                 bool kx[P];
@@ -363,7 +449,7 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
                 for (int ax = 0; ax < P; ++ax) {
                     kx[ax] = t.kc[j][0][ax] != 0;
 #pragma unroll
-                    for (int l = 0; l <= P; ++l) wx[ax][l] = t.lw2[j][0][ax][l];
+                    for (int l = 0; l <= P; ++l) wx[ax][l] = make_float2(t.lw[j][0][ax][l], t.lw[j][0][ax][l]);
                 }
                 float2 v[G::BX];
                 const float2* row = box + oz_l * G::PLANE + oy_l * G::BXP + ox0;
@@ -380,77 +466,38 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
 #pragma unroll
                         for (int l = 0; l <= P; ++l) o = ffma2(v[cx * P + l], wx[ax][l], o);
                     }
-                    res[ox] = o;
+                    res[2 * ox] = o.x;
+                    res[2 * ox + 1] = o.y;
                 }
             }
             // the slot was written in place (generic proxy); order that before the next TMA fill
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(empty0 + 8 * slot);
-            switch (k) {
-#define SLLBM_KEEP(K)                                                   \
-    case K:                                                             \
-        if (K < NPW) {                                                  \
-            _Pragma("unroll") for (int x = 0; x < G::TX; ++x) acc[K < NPW ? K : 0][x] = res[x]; \
-        }                                                               \
-        break;
-                SLLBM_KEEP(0)
-                SLLBM_KEEP(1)
-                SLLBM_KEEP(2)
-                SLLBM_KEEP(3)
-                SLLBM_KEEP(4)
-                SLLBM_KEEP(5)
-                SLLBM_KEEP(6)
-                SLLBM_KEEP(7)
-                SLLBM_KEEP(8)
-#undef SLLBM_KEEP
-            default:
-                break;
+
+            // moment contributions of this pair, then park the pair in tensor memory
+            const float xix = t.xi[j][0], xiy = t.xi[j][1], xiz = t.xi[j][2];
+            const float x2 = static_cast<float>(shell_xi2(shell_of(j)));
+#pragma unroll
+            for (int x = 0; x < G::TX; ++x) {
+                const float f = res[2 * x], g = res[2 * x + 1];
+                pm[0][x] += f;
+                pm[1][x] += f * xix;
+                pm[2][x] += f * xiy;
+                pm[3][x] += f * xiz;
+                pm[4][x] += f * x2 + g;
             }
+            tmem_store_row<G::TX>(tmem_warp + static_cast<uint32_t>(k * 2 * G::TX), res);
         }
 
-        // partial moments of this warp's pairs for the TX nodes of the lane's row
         if (row_lane) {
+            float* pc = part + static_cast<size_t>(c) * 5 * G::TILE + lane * G::TX;
 #pragma unroll
-            for (int x = 0; x < G::TX; x += 4) {
-                float4 pr = make_float4(0, 0, 0, 0), pmx = pr, pmy = pr, pmz = pr, pe = pr;
-                float* prf = &pr.x;
-                float* mxf = &pmx.x;
-                float* myf = &pmy.x;
-                float* mzf = &pmz.x;
-                float* ef = &pe.x;
+            for (int q = 0; q < 5; ++q)
 #pragma unroll
-                for (int q = 0; q < 4 && x + q < G::TX; ++q) {
-#pragma unroll
-                    for (int k = 0; k < NPW; ++k) {
-                        const int j = c + NC * k;
-                        const float f = acc[k][x + q].x, g = acc[k][x + q].y;
-                        prf[q] += f;
-                        mxf[q] += f * t.xi[j][0];
-                        myf[q] += f * t.xi[j][1];
-                        mzf[q] += f * t.xi[j][2];
-                        ef[q] += f * static_cast<float>(shell_xi2(shell_of(j))) + g;
-                    }
-                }
-                const int n = lane * G::TX + x;
-                float* pc = part + static_cast<size_t>(c) * 5 * G::TILE;
-                if (G::TX % 4 == 0) {
-                    *reinterpret_cast<float4*>(pc + 0 * G::TILE + n) = pr;
-                    *reinterpret_cast<float4*>(pc + 1 * G::TILE + n) = pmx;
-                    *reinterpret_cast<float4*>(pc + 2 * G::TILE + n) = pmy;
-                    *reinterpret_cast<float4*>(pc + 3 * G::TILE + n) = pmz;
-                    *reinterpret_cast<float4*>(pc + 4 * G::TILE + n) = pe;
-                } else {
-                    for (int q = 0; q < 4 && x + q < G::TX; ++q) {
-                        pc[0 * G::TILE + n + q] = prf[q];
-                        pc[1 * G::TILE + n + q] = mxf[q];
-                        pc[2 * G::TILE + n + q] = myf[q];
-                        pc[3 * G::TILE + n + q] = mzf[q];
-                        pc[4 * G::TILE + n + q] = ef[q];
-                    }
-                }
-            }
+                for (int x = 0; x < G::TX; ++x) pc[q * G::TILE + x] = pm[q][x];
         }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         if (consumer_barrier_or(*abort_flag, NC * 32)) break;
 
         // per-node moments (fixed-order sum over warps), tau, equilibrium coefficients
@@ -484,44 +531,51 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
         consumer_barrier_or(0, NC * 32);
 
         // collision of this warp's pairs at the lane's TX nodes, 16-byte stores
-        if (row_lane) {
-            const long long g0 =
-                (static_cast<long long>(c0[2] * P + oz_l) * a.N[1] + (c0[1] * P + oy_l)) * a.N[0] + c0[0] * P;
-            float2* dst = static_cast<float2*>(a.dst);
+        const long long g0 =
+            (static_cast<long long>(c0[2] * P + oz_l) * a.N[1] + (c0[1] * P + oy_l)) * a.N[0] + c0[0] * P;
+        float2* dstp = static_cast<float2*>(a.dst);
+#pragma unroll 1
+        for (int k = 0; k < NPW; ++k) {
+            const int j = c + NC * k;
+            float h[2 * G::TX];
+            tmem_load_row<G::TX>(tmem_warp + static_cast<uint32_t>(k * 2 * G::TX), h);  // all lanes
+            if (!row_lane) continue;
+            const int sh = shell_of(j);
+            const float xix = t.xi[j][0], xiy = t.xi[j][1], xiz = t.xi[j][2], wj = t.w[j];
 #pragma unroll
             for (int x = 0; x < G::TX; ++x) {
                 const int n = lane * G::TX + x;
-                float pv[18];
-#pragma unroll
-                for (int q = 0; q < 18; ++q) pv[q] = prm[q * G::TILE + n];
-                const float rho = pv[0], ux = pv[1], uy = pv[2], uz = pv[3], gT = pv[4], om = pv[5];
-#pragma unroll
-                for (int k = 0; k < NPW; ++k) {
-                    const int j = c + NC * k;
-                    const int sh = shell_of(j);
-                    const float s = t.xi[j][0] * ux + t.xi[j][1] * uy + t.xi[j][2] * uz;
-                    const float poly = pv[6 + sh] + s * (pv[10 + sh] + s * (pv[14 + sh] + s * (1.0f / 6.0f + s * (1.0f / 24.0f))));
-                    const float feq = t.w[j] * rho * poly;
-                    const float2 h = acc[k][x];
-                    acc[k][x] = make_float2(h.x + om * (feq - h.x), h.y + om * (gT * feq - h.y));
-                }
+                const float rho = prm[0 * G::TILE + n], ux = prm[1 * G::TILE + n], uy = prm[2 * G::TILE + n],
+                            uz = prm[3 * G::TILE + n], gT = prm[4 * G::TILE + n], om = prm[5 * G::TILE + n];
+                const float s = xix * ux + xiy * uy + xiz * uz;
+                const float poly = prm[(6 + sh) * G::TILE + n] +
+                                   s * (prm[(10 + sh) * G::TILE + n] +
+                                        s * (prm[(14 + sh) * G::TILE + n] + s * (1.0f / 6.0f + s * (1.0f / 24.0f))));
+                const float feq = wj * rho * poly;
+                const float f = h[2 * x], g = h[2 * x + 1];
+                h[2 * x] = f + om * (feq - f);
+                h[2 * x + 1] = g + om * (gT * feq - g);
             }
+            float2* out = dstp + static_cast<long long>(j) * a.nn + g0;
+            if (G::TX % 2 == 0) {
 #pragma unroll
-            for (int k = 0; k < NPW; ++k) {
-                const int j = c + NC * k;
-                float2* out = dst + static_cast<long long>(j) * a.nn + g0;
-                if (G::TX % 2 == 0) {
+                for (int x = 0; x < G::TX; x += 2)
+                    *reinterpret_cast<float4*>(out + x) = make_float4(h[2 * x], h[2 * x + 1], h[2 * x + 2], h[2 * x + 3]);
+            } else {
 #pragma unroll
-                    for (int x = 0; x < G::TX; x += 2)
-                        *reinterpret_cast<float4*>(out + x) =
-                            make_float4(acc[k][x].x, acc[k][x].y, acc[k][x + 1].x, acc[k][x + 1].y);
-                } else {
-#pragma unroll
-                    for (int x = 0; x < G::TX; ++x) out[x] = acc[k][x];
-                }
+                for (int x = 0; x < G::TX; ++x) out[x] = make_float2(h[2 * x], h[2 * x + 1]);
             }
         }
     }
+
+    // free the tensor memory once every consumer is done with it
+    tc_fence_before();
+    consumer_barrier_or(0, NC * 32);
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tmem_base_s),
+                     "r"(static_cast<uint32_t>(TC::alloc))
+                     : "memory");
 }
 
 }  // namespace sllbm

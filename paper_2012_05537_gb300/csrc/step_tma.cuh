@@ -72,11 +72,13 @@ struct TmaSmem {
     // alignment)
     static constexpr size_t round128(size_t b) { return (b + 127) / 128 * 128; }
     static constexpr size_t slots = size_t(NSLOT) * G::SLOT_BYTES;
-    static constexpr size_t partials = round128(size_t(NC) * 5 * G::TILE * sizeof(float));
-    static constexpr size_t params = round128(size_t(kNParams) * G::TILE * sizeof(float));
+    static constexpr size_t partials = round128(size_t(NC) * 5 * G::TX * 32 * sizeof(float));
+    static constexpr size_t params = round128(size_t(kNParams) * G::TX * 32 * sizeof(float));
     static constexpr size_t tables = round128(sizeof(StepTablesS<P>));
     static constexpr size_t bars = size_t(2) * NSLOT * sizeof(uint64_t) + 16;
-    static constexpr size_t bytes = slots + partials + params + tables + bars + 128;  // +128: base alignment
+    static constexpr size_t bars_padded = round128(bars);
+    static constexpr size_t woff = round128(size_t(G::BZ + G::BY + G::BXP / 2) * sizeof(long long));
+    static constexpr size_t bytes = slots + partials + params + tables + bars_padded + woff + 128;  // +128: base alignment
 };
 
 // Tensor-memory columns: a warp's lane keeps NPW pairs x 2*TX floats; warps w, w+4, w+8
@@ -136,6 +138,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
                                                   int* err_flag, uint32_t limit) {
     for (uint32_t it = 0; it < limit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        // back off so that waiting warps leave issue slots and the shared-memory pipe to
+        // the warps doing work (32 ns growing to 1 us)
+        if (it >= 4) __nanosleep(32u << (it < 9 ? it - 4 : 5));
         if ((it & 15u) == 15u && *abort_flag) return false;
     }
     *abort_flag = 1;
@@ -214,11 +219,11 @@ __device__ __forceinline__ void tmem_store_row(uint32_t ta, const float* v) {
     if (TX == 9) tmem_st2(ta + 16, v + 16);
 }
 
+// (the caller waits with tcgen05.wait::ld before using v)
 template <int TX>
 __device__ __forceinline__ void tmem_load_row(uint32_t ta, float* v) {
     tmem_ld16(ta, v);
     if (TX == 9) tmem_ld2(ta + 16, v + 16);
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ int wrapi(int v, int n) {
@@ -236,7 +241,7 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
     constexpr int NPW = kQ / NC;  // velocity pairs per consumer warp
     static_assert(NPW * NC == kQ, "consumers must split the 45 pairs evenly");
     using TC = TmemCols<G::TX, NPW, NC>;
-    constexpr uint32_t kWaitLimit = 1u << 22;  // polls of <= 1 us: about 4 s before giving up
+    constexpr uint32_t kWaitLimit = 1u << 21;  // polls of <= 2 us with back-off: about 4 s before giving up
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -247,6 +252,7 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + SM::slots + SM::partials + SM::params + SM::tables);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * NSLOT);
     uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(bars + 2 * NSLOT) + 1;
+    long long* woff = reinterpret_cast<long long*>(reinterpret_cast<unsigned char*>(bars) + SM::bars_padded);
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + NSLOT);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -312,20 +318,25 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
                     }
                 } else {
                     // wrapped 16-byte copies: a chunk is two (f,g) pairs at an even x, and N[0]
-                    // is even, so a chunk never straddles the periodic boundary
+                    // is even, so a chunk never straddles the periodic boundary.  The wrapped
+                    // offsets (in floats) of the box's planes, rows and chunks are computed once
+                    // per box, one modulo per lane, into a small table.
                     const float* src = static_cast<const float*>(a.src) + 2LL * j * a.nn;
                     constexpr int CH = G::BXP / 2;
                     constexpr int NCHUNK = G::BZ * G::BY * CH;
+                    if (lane < G::BZ)
+                        woff[lane] = 2LL * wrapi(b0[2] + lane, a.N[2]) * a.N[1] * a.N[0];
+                    if (lane < G::BY) woff[G::BZ + lane] = 2LL * wrapi(b0[1] + lane, a.N[1]) * a.N[0];
+                    if (lane < CH) woff[G::BZ + G::BY + lane] = 2LL * wrapi(x0 + 2 * lane, a.N[0]);
+                    __syncwarp();
                     for (int q = lane; q < NCHUNK; q += 32) {
                         const int c = q % CH;
                         const int row = q / CH;
                         const int y = row % G::BY, z = row / G::BY;
-                        const int gx = wrapi(x0 + 2 * c, a.N[0]);
-                        const int gy = wrapi(b0[1] + y, a.N[1]);
-                        const int gz = wrapi(b0[2] + z, a.N[2]);
-                        const long long off = 2LL * ((static_cast<long long>(gz) * a.N[1] + gy) * a.N[0] + gx);
+                        const long long off = woff[z] + woff[G::BZ + y] + woff[G::BZ + G::BY + c];
                         cp_async16(dst + static_cast<uint32_t>((row * G::BXP + 2 * c) * 8), src + off);
                     }
+                    __syncwarp();  // the table is rewritten for the next crossing box
                     cp_async_mbar_arrive(full);
                     __syncwarp();
                     if (lane == 0) mbar_arrive(full);
@@ -490,23 +501,27 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
             tmem_store_row<G::TX>(tmem_warp + static_cast<uint32_t>(k * 2 * G::TX), res);
         }
 
-        if (row_lane) {
-            float* pc = part + static_cast<size_t>(c) * 5 * G::TILE + lane * G::TX;
+        // Shared-memory layouts indexed [..][x][lane] (node = lane*TX + x) so that every
+        // lane-parallel access below is contiguous (no bank conflicts).
+        {
+            float* pc = part + static_cast<size_t>(c) * 5 * G::TX * 32 + lane;
 #pragma unroll
             for (int q = 0; q < 5; ++q)
 #pragma unroll
-                for (int x = 0; x < G::TX; ++x) pc[q * G::TILE + x] = pm[q][x];
+                for (int x = 0; x < G::TX; ++x) pc[(q * G::TX + x) * 32] = pm[q][x];
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         if (consumer_barrier_or(*abort_flag, NC * 32)) break;
 
         // per-node moments (fixed-order sum over warps), tau, equilibrium coefficients
-        for (int n = threadIdx.x; n < G::TILE; n += NC * 32) {
+        for (int tn = threadIdx.x; tn < G::TX * 32; tn += NC * 32) {
+            const int xn = tn >> 5, ln = tn & 31;  // node = ln*TX + xn
+            if (ln >= G::ROWS) continue;
             float m[5] = {0, 0, 0, 0, 0};
 #pragma unroll
             for (int w = 0; w < NC; ++w)
 #pragma unroll
-                for (int q = 0; q < 5; ++q) m[q] += part[(static_cast<size_t>(w) * 5 + q) * G::TILE + n];
+                for (int q = 0; q < 5; ++q) m[q] += part[((static_cast<size_t>(w) * 5 + q) * G::TX + xn) * 32 + ln];
             const float rho = m[0];
             const float inv_rho = 1.0f / rho;
             const float ux = m[1] * inv_rho, uy = m[2] * inv_rho, uz = m[3] * inv_rho;
@@ -515,55 +530,67 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
             if (a.flag != nullptr && !(rho > 0.f && T > 0.f && isfinite(rho) && isfinite(T))) atomicOr(a.flag, 1);
             const float tau_r = static_cast<float>(a.mu_over_dt) * sutherland(T) / (rho * T) + 0.5f;
             const EqCoef<float> ec = eq_coefficients(usq, T - 1.0f);
-            prm[0 * G::TILE + n] = rho;
-            prm[1 * G::TILE + n] = ux;
-            prm[2 * G::TILE + n] = uy;
-            prm[3 * G::TILE + n] = uz;
-            prm[4 * G::TILE + n] = static_cast<float>(a.gfac) * T;
-            prm[5 * G::TILE + n] = 1.0f / tau_r;
+            float* pn = prm + xn * 32 + ln;
+            constexpr int QS = G::TX * 32;  // stride between parameters
+            pn[0 * QS] = rho;
+            pn[1 * QS] = ux;
+            pn[2 * QS] = uy;
+            pn[3 * QS] = uz;
+            pn[4 * QS] = static_cast<float>(a.gfac) * T;
+            pn[5 * QS] = 1.0f / tau_r;
 #pragma unroll
             for (int sh = 0; sh < 4; ++sh) {
-                prm[(6 + sh) * G::TILE + n] = ec.c0[sh];
-                prm[(10 + sh) * G::TILE + n] = ec.c1[sh];
-                prm[(14 + sh) * G::TILE + n] = ec.c2[sh];
+                pn[(6 + sh) * QS] = ec.c0[sh];
+                pn[(10 + sh) * QS] = ec.c1[sh];
+                pn[(14 + sh) * QS] = ec.c2[sh];
             }
         }
         consumer_barrier_or(0, NC * 32);
 
-        // collision of this warp's pairs at the lane's TX nodes, 16-byte stores
-        const long long g0 =
-            (static_cast<long long>(c0[2] * P + oz_l) * a.N[1] + (c0[1] * P + oy_l)) * a.N[0] + c0[0] * P;
-        float2* dstp = static_cast<float2*>(a.dst);
-#pragma unroll 1
-        for (int k = 0; k < NPW; ++k) {
-            const int j = c + NC * k;
-            float h[2 * G::TX];
-            tmem_load_row<G::TX>(tmem_warp + static_cast<uint32_t>(k * 2 * G::TX), h);  // all lanes
-            if (!row_lane) continue;
-            const int sh = shell_of(j);
-            const float xix = t.xi[j][0], xiy = t.xi[j][1], xiz = t.xi[j][2], wj = t.w[j];
+        // collision of this warp's pairs at the lane's TX nodes: the pairs come back from
+        // tensor memory, each node's parameters are read once, 16-byte streaming stores
+        float h[NPW][2 * G::TX];
+#pragma unroll
+        for (int k = 0; k < NPW; ++k) tmem_load_row<G::TX>(tmem_warp + static_cast<uint32_t>(k * 2 * G::TX), h[k]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row_lane) {
 #pragma unroll
             for (int x = 0; x < G::TX; ++x) {
-                const int n = lane * G::TX + x;
-                const float rho = prm[0 * G::TILE + n], ux = prm[1 * G::TILE + n], uy = prm[2 * G::TILE + n],
-                            uz = prm[3 * G::TILE + n], gT = prm[4 * G::TILE + n], om = prm[5 * G::TILE + n];
-                const float s = xix * ux + xiy * uy + xiz * uz;
-                const float poly = prm[(6 + sh) * G::TILE + n] +
-                                   s * (prm[(10 + sh) * G::TILE + n] +
-                                        s * (prm[(14 + sh) * G::TILE + n] + s * (1.0f / 6.0f + s * (1.0f / 24.0f))));
-                const float feq = wj * rho * poly;
-                const float f = h[2 * x], g = h[2 * x + 1];
-                h[2 * x] = f + om * (feq - f);
-                h[2 * x + 1] = g + om * (gT * feq - g);
+                const float* pn = prm + x * 32 + lane;
+                constexpr int QS = G::TX * 32;
+                const float rho = pn[0 * QS], ux = pn[1 * QS], uy = pn[2 * QS], uz = pn[3 * QS], gT = pn[4 * QS],
+                            om = pn[5 * QS];
+#pragma unroll
+                for (int k = 0; k < NPW; ++k) {
+                    const int j = c + NC * k;
+                    const int sh = shell_of(j);  // warp-dependent: read the shell's coefficients directly
+                    const float s = t.xi[j][0] * ux + t.xi[j][1] * uy + t.xi[j][2] * uz;
+                    const float poly = pn[(6 + sh) * QS] +
+                                       s * (pn[(10 + sh) * QS] + s * (pn[(14 + sh) * QS] + s * (1.0f / 6.0f + s * (1.0f / 24.0f))));
+                    const float feq = t.w[j] * rho * poly;
+                    const float f = h[k][2 * x], g = h[k][2 * x + 1];
+                    h[k][2 * x] = f + om * (feq - f);
+                    h[k][2 * x + 1] = g + om * (gT * feq - g);
+                }
             }
-            float2* out = dstp + static_cast<long long>(j) * a.nn + g0;
-            if (G::TX % 2 == 0) {
+            // streaming stores: the new state is not read again in this step, so it should
+            // not push the source boxes' halos out of L2
+            const long long g0 =
+                (static_cast<long long>(c0[2] * P + oz_l) * a.N[1] + (c0[1] * P + oy_l)) * a.N[0] + c0[0] * P;
+            float2* dstp = static_cast<float2*>(a.dst);
 #pragma unroll
-                for (int x = 0; x < G::TX; x += 2)
-                    *reinterpret_cast<float4*>(out + x) = make_float4(h[2 * x], h[2 * x + 1], h[2 * x + 2], h[2 * x + 3]);
-            } else {
+            for (int k = 0; k < NPW; ++k) {
+                const int j = c + NC * k;
+                float2* out = dstp + static_cast<long long>(j) * a.nn + g0;
+                if (G::TX % 2 == 0) {
 #pragma unroll
-                for (int x = 0; x < G::TX; ++x) out[x] = make_float2(h[2 * x], h[2 * x + 1]);
+                    for (int x = 0; x < G::TX; x += 2)
+                        __stcs(reinterpret_cast<float4*>(out + x),
+                               make_float4(h[k][2 * x], h[k][2 * x + 1], h[k][2 * x + 2], h[k][2 * x + 3]));
+                } else {
+#pragma unroll
+                    for (int x = 0; x < G::TX; ++x) __stcs(out + x, make_float2(h[k][2 * x], h[k][2 * x + 1]));
+                }
             }
         }
     }

@@ -8,8 +8,9 @@
 //    (f_i, g_i) -- the tile translated by the departure cell shift, plus one cell and the
 //    shared face -- into a ring of shared-memory slots: one 4D TMA load
 //    (cp.async.bulk.tensor) when the box lies inside the periodic domain, 16-byte
-//    cp.async copies with wrapped coordinates when it crosses the boundary.  Slots are
-//    handed over with mbarriers (transaction counts for TMA).
+//    cp.async copies from the wrapped positions when it crosses the boundary.
+//    Slots are handed over with mbarriers (transaction counts), and each slot carries
+//    the number of the item last issued into it.
 //  * NC consumer warps own 45/NC velocity pairs each.  For a pair they run the z and y
 //    Lagrange passes in place in the slot (each lane owns whole columns) and the x pass
 //    into registers (lane = one x-row of the tile), then release the slot.  f_i and g_i
@@ -75,7 +76,8 @@ struct TmaSmem {
     static constexpr size_t partials = round128(size_t(NC) * 5 * G::TX * 32 * sizeof(float));
     static constexpr size_t params = round128(size_t(kNParams) * G::TX * 32 * sizeof(float));
     static constexpr size_t tables = round128(sizeof(StepTablesS<P>));
-    static constexpr size_t bars = size_t(2) * NSLOT * sizeof(uint64_t) + 16;
+    // full[NSLOT], empty[NSLOT] mbarriers, tag[NSLOT] (item last issued into a slot), flags
+    static constexpr size_t bars = size_t(3) * NSLOT * sizeof(uint64_t) + 16;
     static constexpr size_t bars_padded = round128(bars);
     static constexpr size_t woff = round128(size_t(G::BZ + G::BY + G::BXP / 2) * sizeof(long long));
     static constexpr size_t bytes = slots + partials + params + tables + bars_padded + woff + 128;  // +128: base alignment
@@ -148,6 +150,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
     return false;
 }
 
+// Bounded wait until a shared-memory tag reaches `want` (same give-up rules as above).
+__device__ __forceinline__ bool wait_tag_bounded(volatile long long* tag, long long want, volatile int* abort_flag,
+                                                 int* err_flag, uint32_t limit) {
+    for (uint32_t it = 0; it < limit; ++it) {
+        if (*tag == want) return true;
+        if (it >= 4) __nanosleep(32u << (it < 9 ? it - 4 : 5));
+        if ((it & 15u) == 15u && *abort_flag) return false;
+    }
+    *abort_flag = 1;
+    if (err_flag != nullptr) atomicOr(err_flag, 2);
+    return false;
+}
+
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                             uint32_t bar) {
     asm volatile(
@@ -161,6 +176,7 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
 
+// The mbarrier receives one arrival once all earlier cp.async copies of the thread landed.
 __device__ __forceinline__ void cp_async_mbar_arrive(uint32_t bar) {
     asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -250,8 +266,9 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
     float* prm = reinterpret_cast<float*>(base + SM::slots + SM::partials);
     StepTablesS<P>* tsm = reinterpret_cast<StepTablesS<P>*>(base + SM::slots + SM::partials + SM::params);
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + SM::slots + SM::partials + SM::params + SM::tables);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * NSLOT);
-    uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(bars + 2 * NSLOT) + 1;
+    volatile long long* slot_tag = reinterpret_cast<volatile long long*>(bars + 2 * NSLOT);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 3 * NSLOT);
+    uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(bars + 3 * NSLOT) + 1;
     long long* woff = reinterpret_cast<long long*>(reinterpret_cast<unsigned char*>(bars) + SM::bars_padded);
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + NSLOT);
 
@@ -268,6 +285,7 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
+        for (int s = 0; s < NSLOT; ++s) slot_tag[s] = -1;
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -311,16 +329,18 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
                 const int x0 = b0[0] - (b0[0] & 1);  // even pair index (floor for negatives)
                 const uint32_t dst = smem_u32(slots) + static_cast<uint32_t>(slot) * G::SLOT_BYTES;
                 const uint32_t full = full0 + 8 * slot;
+                // announce which item this slot now carries (see the consumer's wait)
+                if (lane == 0) slot_tag[slot] = s;
                 if (!cross) {
                     if (lane == 0) {
                         mbar_arrive_expect_tx(full, G::BOX_BYTES);
                         tma_load_4d(dst, &tmap, 2 * x0, b0[1], b0[2], j, full);
                     }
                 } else {
-                    // wrapped 16-byte copies: a chunk is two (f,g) pairs at an even x, and N[0]
-                    // is even, so a chunk never straddles the periodic boundary.  The wrapped
-                    // offsets (in floats) of the box's planes, rows and chunks are computed once
-                    // per box, one modulo per lane, into a small table.
+                    // the box crosses the periodic boundary: 16-byte copies from the wrapped
+                    // positions.  A chunk is two (f,g) pairs at an even x and N[0] is even, so a
+                    // chunk never straddles the boundary.  The wrapped offsets (in floats) of
+                    // the box's planes, rows and chunks are computed once per box into a table.
                     const float* src = static_cast<const float*>(a.src) + 2LL * j * a.nn;
                     constexpr int CH = G::BXP / 2;
                     constexpr int NCHUNK = G::BZ * G::BY * CH;
@@ -377,6 +397,11 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
             const long long s = tau * kQ + j;
             const int slot = static_cast<int>(s % NSLOT);
             const uint32_t ph = static_cast<uint32_t>((s / NSLOT) & 1);
+            // A slot's previous fill (item s - NSLOT, another warp's) may still be in flight when
+            // this warp arrives, and one parity bit cannot tell "previous phase pending" from
+            // "this phase done".  Wait until the producer has issued item s into the slot (its
+            // tag): the barrier is then within one phase of the one awaited.
+            wait_tag_bounded(slot_tag + slot, s, abort_flag, err_flag, kWaitLimit);
             mbar_wait_bounded(full0 + 8 * slot, ph, abort_flag, err_flag, kWaitLimit);
             float2* box = slots + static_cast<size_t>(slot) * (G::SLOT_BYTES / 8);
             const int ox0 = ((c0[0] + t.kmin[j][0]) * P) & 1;

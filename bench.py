@@ -72,7 +72,7 @@ def measured_peaks():
 def kernel_source_hash() -> str:
     csrc = os.path.join(ROOT, "paper_2012_05537_gb300", "csrc")
     h = hashlib.sha256()
-    for name in ("step_kernel.cuh", "collide.cuh", "sllbm_internal.h", "step_f32.cu", "step_f64.cu"):
+    for name in ("step_kernel.cuh", "step_tma.cuh", "collide.cuh", "sllbm_internal.h", "step_f32.cu", "step_f64.cu"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

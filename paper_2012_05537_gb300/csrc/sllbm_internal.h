@@ -39,7 +39,7 @@ struct sllbm_ctx {
     size_t step_blob_size;
     int num_sms;
     int step_kernel;           // 1: generic tile kernel, 2: TMA-fed persistent kernel
-    alignas(64) unsigned char tmap[2][128];  // TMA descriptors (CUtensorMap) per source buffer
+    alignas(64) unsigned char tmap[2][8][128];  // TMA descriptors (CUtensorMap) per source buffer and box shape
     const void* tmap_src[2];
     int last_err;
     long long launches;

@@ -29,11 +29,12 @@ struct TmaTile<4> {
     static constexpr int CX = 2, CY = 2, CZ = 1;
 };
 // Consumer warps (45 velocity pairs split evenly: 9 x 5) and source boxes in flight per SM
-// (what fits next to partials, params and tables).
+// (as many as fit next to the moment sums, parameters and tables).
 template <int P>
 constexpr int kConsumersFor = 9;
 template <int P>
-constexpr int kSlotsFor = P == 4 ? 11 : 12;
+constexpr int kSlotsFor =
+    SlotFit<P, TmaTile<P>::CX, TmaTile<P>::CY, TmaTile<P>::CZ, kConsumersFor<P>, kMaxSlots>::value;
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static std::once_flag once;
@@ -79,31 +80,38 @@ bool tma_eligible_p(const sllbm_ctx* c) {
     return c->cells[0] % T::CX == 0 && c->cells[1] % T::CY == 0 && c->cells[2] % T::CZ == 0;
 }
 
-// Builds (or reuses) the TMA descriptor of a source buffer: the buffer seen as a 4D FP32
-// tensor [45][Nz][Ny][2*Nx] (f_i, g_i interleaved along x), box = one source box.
+// Builds (or reuses) the TMA descriptors of a source buffer: the buffer seen as a 4D FP32
+// tensor [45][Nz][Ny][2*Nx] (f_i, g_i interleaved along x), one descriptor per box shape
+// (span 0 or 1 of the departure cells in x, y, z).  Out-of-domain elements read as zero.
 template <int P>
-int tensor_map_for(sllbm_ctx* ctx, const void* src, CUtensorMap* out) {
+int tensor_maps_for(sllbm_ctx* ctx, const void* src, TmaMaps* out) {
     using T = TmaTile<P>;
     using G = TmaGeom<P, T::CX, T::CY, T::CZ>;
     const int k = (src == ctx->buf[0]) ? 0 : 1;
     if (ctx->tmap_src[k] != src) {
         PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
         if (enc == nullptr) return SLLBM_ECUDA;
-        CUtensorMap map;
         const cuuint64_t nx2 = 2ull * ctx->N[0];
         cuuint64_t gdim[4] = {nx2, static_cast<cuuint64_t>(ctx->N[1]), static_cast<cuuint64_t>(ctx->N[2]),
                               static_cast<cuuint64_t>(kQ)};
         cuuint64_t gstride[3] = {nx2 * 4, nx2 * ctx->N[1] * 4, nx2 * ctx->N[1] * ctx->N[2] * 4};
-        cuuint32_t box[4] = {2u * G::BXP, static_cast<cuuint32_t>(G::BY), static_cast<cuuint32_t>(G::BZ), 1u};
         cuuint32_t estride[4] = {1, 1, 1, 1};
-        CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(src), gdim, gstride, box,
-                         estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return SLLBM_ECUDA;
-        std::memcpy(ctx->tmap[k], &map, sizeof(map));
+        for (int shape = 0; shape < 8; ++shape) {
+            CUtensorMap map;
+            cuuint32_t box[4] = {2u * G::xpairs(shape & 1), static_cast<cuuint32_t>(G::rows((shape >> 1) & 1)),
+                                 static_cast<cuuint32_t>(G::planes((shape >> 2) & 1)), 1u};
+            CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(src), gdim, gstride, box,
+                             estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) {
+                ctx->tmap_src[k] = nullptr;
+                return SLLBM_ECUDA;
+            }
+            std::memcpy(ctx->tmap[k][shape], &map, sizeof(map));
+        }
         ctx->tmap_src[k] = src;
     }
-    std::memcpy(out, ctx->tmap[k], sizeof(CUtensorMap));
+    std::memcpy(out, ctx->tmap[k], sizeof(TmaMaps));
     return SLLBM_OK;
 }
 
@@ -121,8 +129,8 @@ int launch_tma(sllbm_ctx* ctx, const void* src, void* dst) {
         ctx->step_blob_size = sizeof(Tab) + 1;  // +1 keeps it distinct from the generic tables
         fill_tables_s<P>(ctx, reinterpret_cast<Tab*>(ctx->step_blob));
     }
-    CUtensorMap map;
-    int rc = tensor_map_for<P>(ctx, src, &map);
+    TmaMaps maps;
+    int rc = tensor_maps_for<P>(ctx, src, &maps);
     if (rc != SLLBM_OK) return rc;
     StepArgs args;
     fill_step_args(ctx, src, dst, &args);
@@ -131,7 +139,7 @@ int launch_tma(sllbm_ctx* ctx, const void* src, void* dst) {
     auto k = step_tma_kernel<P, T::CX, T::CY, T::CZ, kConsumers, kSlotsFor<P>>;
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(SM::bytes));
     if (err == cudaSuccess) {
-        k<<<grid, (kConsumers + 1) * 32, SM::bytes, ctx->stream>>>(map, args, *reinterpret_cast<const Tab*>(ctx->step_blob));
+        k<<<grid, (kConsumers + 1) * 32, SM::bytes, ctx->stream>>>(maps, args, *reinterpret_cast<const Tab*>(ctx->step_blob));
         err = cudaGetLastError();
     }
     ctx->launches += 1;

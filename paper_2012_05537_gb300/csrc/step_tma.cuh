@@ -7,10 +7,12 @@
 //  * A producer warp loads, for every velocity i of a tile, the source box of the pair
 //    (f_i, g_i) -- the tile translated by the departure cell shift, plus one cell and the
 //    shared face -- into a ring of shared-memory slots: one 4D TMA load
-//    (cp.async.bulk.tensor) when the box lies inside the periodic domain, 16-byte
-//    cp.async copies from the wrapped positions when it crosses the boundary.
-//    Slots are handed over with mbarriers (transaction counts), and each slot carries
-//    the number of the item last issued into it.
+//    (cp.async.bulk.tensor) when the box lies inside the periodic domain; when it crosses
+//    the boundary, one TMA load per periodic image it overlaps, into consecutive slots
+//    (zero-filled outside the domain, summed by the consumer on its first pass), or
+//    16-byte cp.async copies from the wrapped positions when that takes too many images.
+//    Slots are handed over with mbarriers (transaction counts); a small item table tells
+//    the consumers where each item starts in the ring and how many slots it took.
 //  * NC consumer warps own 45/NC velocity pairs each.  For a pair they run the z and y
 //    Lagrange passes in place in the slot (each lane owns whole columns) and the x pass
 //    into registers (lane = one x-row of the tile), then release the slot.  f_i and g_i
@@ -59,12 +61,35 @@ struct TmaGeom {
     static constexpr int BOX = BZ * PLANE;              // float2 per box
     static constexpr uint32_t BOX_BYTES = BOX * 8u;
     static constexpr int SLOT_BYTES = (BOX * 8 + 127) / 128 * 128;
+    // A velocity whose P local nodes all depart from the same cell in a direction (span 0)
+    // needs one cell less of the box in that direction.  Box extents per span:
+    static constexpr int BX0 = CX * P + 1, BY0 = CY * P + 1, BZ0 = CZ * P + 1;
+    static constexpr int BXP0 = ((BX0 + 1) + 1) / 2 * 2;
+    __host__ __device__ static constexpr int xpairs(int span) { return span ? BXP : BXP0; }
+    __host__ __device__ static constexpr int rows(int span) { return span ? BY : BY0; }
+    __host__ __device__ static constexpr int planes(int span) { return span ? BZ : BZ0; }
     static_assert(ROWS <= 32, "one x-row per lane");
-    static_assert(BXP % 2 == 0 && BXP >= BX + 1, "TMA rows start on an even pair");
+    static_assert(BXP % 2 == 0 && BXP >= BX + 1 && BXP0 % 2 == 0 && BXP0 >= BX0 + 1, "TMA rows start on an even pair");
     static_assert(TX == 8 || TX == 9, "tensor-memory row layout");
 };
 
+// One TMA descriptor per box shape (span 0/1 in x, y, z: index sx + 2 sy + 4 sz) of a source
+// buffer, passed to the kernel as one parameter block.
+struct TmaMaps {
+    CUtensorMap m[8];
+};
+
 constexpr int kNParams = 20;  // rho, ux, uy, uz, gT, omega, c0[4], c1[4], c2[4], (2 spare)
+// A source box that crosses the periodic boundary is loaded as one TMA box per periodic image
+// it overlaps (zero outside the domain), at most kMaxPieces of them in consecutive ring slots;
+// boxes with more images (meshes not much larger than a tile) take the cp.async path.
+constexpr int kMaxPieces = 8;
+// Entries of the item table (a power of two, at least the slot count: an entry is reused only
+// after the item that used it has released its slots).
+constexpr int kItems = 32;
+constexpr int kMaxSlots = 24;
+constexpr size_t kSmemBudget = 227 * 1024;
+static_assert((kItems & (kItems - 1)) == 0, "item table size");
 
 template <int P, int CX, int CY, int CZ, int NC, int NSLOT>
 struct TmaSmem {
@@ -73,14 +98,26 @@ struct TmaSmem {
     // alignment)
     static constexpr size_t round128(size_t b) { return (b + 127) / 128 * 128; }
     static constexpr size_t slots = size_t(NSLOT) * G::SLOT_BYTES;
-    static constexpr size_t partials = round128(size_t(NC) * 5 * G::TX * 32 * sizeof(float));
+    static constexpr size_t partials = round128(size_t(5) * G::TX * 32 * sizeof(float));  // moment sums
     static constexpr size_t params = round128(size_t(kNParams) * G::TX * 32 * sizeof(float));
     static constexpr size_t tables = round128(sizeof(StepTablesS<P>));
-    // full[NSLOT], empty[NSLOT] mbarriers, tag[NSLOT] (item last issued into a slot), flags
-    static constexpr size_t bars = size_t(3) * NSLOT * sizeof(uint64_t) + 16;
+    // full[NSLOT], empty[NSLOT] mbarriers, the item table (one word per entry: item number,
+    // first slot, its phase and the piece count), flags
+    static constexpr size_t bars = (size_t(2) * NSLOT + kItems) * sizeof(uint64_t) + 16;
     static constexpr size_t bars_padded = round128(bars);
     static constexpr size_t woff = round128(size_t(G::BZ + G::BY + G::BXP / 2) * sizeof(long long));
     static constexpr size_t bytes = slots + partials + params + tables + bars_padded + woff + 128;  // +128: base alignment
+};
+
+// The largest slot count (at most kMaxSlots) whose layout fits the shared-memory budget.
+template <int P, int CX, int CY, int CZ, int NC, int N>
+struct SlotFit {
+    static constexpr int value =
+        TmaSmem<P, CX, CY, CZ, NC, N>::bytes <= kSmemBudget ? N : SlotFit<P, CX, CY, CZ, NC, N - 1>::value;
+};
+template <int P, int CX, int CY, int CZ, int NC>
+struct SlotFit<P, CX, CY, CZ, NC, 0> {
+    static constexpr int value = 0;
 };
 
 // Tensor-memory columns: a warp's lane keeps NPW pairs x 2*TX floats; warps w, w+4, w+8
@@ -92,6 +129,12 @@ struct TmemCols {
     static constexpr int alloc = per_quarter <= 32 ? 32 : per_quarter <= 64 ? 64 : per_quarter <= 128 ? 128
                                : per_quarter <= 256 ? 256 : 512;
     static_assert(per_quarter <= 512, "tensor memory columns");
+};
+
+// compile-time integer as a value (selects a pass variant in a generic lambda)
+template <int V>
+struct IntC {
+    static constexpr int value = V;
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -121,8 +164,20 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
+// Non-blocking test: has the phase with this parity completed?
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // One poll: the thread may sleep until the phase completes, but at most ~1 us (the
-// suspend-time hint), so `limit` polls bound the wall time of a wait.
+// suspend-time hint).
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -134,33 +189,68 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait for the phase `parity` of an mbarrier.  Gives up when another warp raised
-// the CTA abort flag or after `limit` polls (then raises it and the global error bit).
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                                  int* err_flag, uint32_t limit) {
-    for (uint32_t it = 0; it < limit; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        // back off so that waiting warps leave issue slots and the shared-memory pipe to
-        // the warps doing work (32 ns growing to 1 us)
-        if (it >= 4) __nanosleep(32u << (it < 9 ? it - 4 : 5));
-        if ((it & 15u) == 15u && *abort_flag) return false;
-    }
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded waits give up after kWaitNs of wall time (read from the global timer), or after
+// kWaitPolls polls should that timer not advance, or as soon as another warp raised the CTA
+// abort flag; the warp that gives up raises the abort flag and the global error bit.
+constexpr uint64_t kWaitNs = 2000000000ull;
+constexpr uint32_t kWaitPolls = 1u << 26;
+
+__device__ __forceinline__ bool wait_give_up(volatile int* abort_flag, int* err_flag) {
     *abort_flag = 1;
     if (err_flag != nullptr) atomicOr(err_flag, 2);
     return false;
 }
 
-// Bounded wait until a shared-memory tag reaches `want` (same give-up rules as above).
-__device__ __forceinline__ bool wait_tag_bounded(volatile long long* tag, long long want, volatile int* abort_flag,
-                                                 int* err_flag, uint32_t limit) {
-    for (uint32_t it = 0; it < limit; ++it) {
-        if (*tag == want) return true;
-        if (it >= 4) __nanosleep(32u << (it < 9 ? it - 4 : 5));
-        if ((it & 15u) == 15u && *abort_flag) return false;
+// Bounded wait for the phase `parity` of an mbarrier.  try_wait suspends the thread until the
+// phase completes (or the hint expires), so the loop does not spin on the issue slots.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                                  int* err_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1; it < kWaitPolls; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 7u) == 0) {
+            if (*abort_flag) return false;
+            if (global_ns() - t0 > kWaitNs) break;
+        }
     }
-    *abort_flag = 1;
-    if (err_flag != nullptr) atomicOr(err_flag, 2);
-    return false;
+    return wait_give_up(abort_flag, err_flag);
+}
+
+// Bounded wait until the high half of a shared-memory word (written with one 64-bit store)
+// reaches `want`; returns the low half (0 if the wait gave up, same give-up rules).  Short
+// sleeps between polls leave the issue slots to the warps doing work.
+__device__ __forceinline__ uint32_t wait_item_bounded(volatile unsigned long long* word, uint32_t want,
+                                                      volatile int* abort_flag, int* err_flag) {
+    unsigned long long v = *word;
+    if (static_cast<uint32_t>(v >> 32) == want) return static_cast<uint32_t>(v);
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1; it < kWaitPolls; ++it) {
+        __nanosleep(32);
+        v = *word;
+        if (static_cast<uint32_t>(v >> 32) == want) return static_cast<uint32_t>(v);
+        if ((it & 7u) == 0) {
+            if (*abort_flag) return 0;
+            if (global_ns() - t0 > kWaitNs) break;
+        }
+    }
+    wait_give_up(abort_flag, err_flag);
+    return 0;
+}
+
+// floor(a / n) for n > 0; the usual cases (|a| < 2n) without a division
+__device__ __forceinline__ int floor_div(int a, int n) {
+    if (a >= 0 && a < n) return 0;
+    if (a < 0 && a >= -n) return -1;
+    if (a >= n && a < 2 * n) return 1;
+    const int q = a / n;
+    return (a % n != 0 && a < 0) ? q - 1 : q;
 }
 
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
@@ -183,6 +273,14 @@ __device__ __forceinline__ void cp_async_mbar_arrive(uint32_t bar) {
 
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Named barriers between two warps (64 threads): one warp arrives, the other waits.
+__device__ __forceinline__ void named_barrier_sync(int id, int nthreads) {
+    asm volatile("barrier.cta.sync.aligned %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ void named_barrier_arrive(int id, int nthreads) {
+    asm volatile("barrier.cta.arrive.aligned %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 // Named barrier 1 over the consumer warps with an OR vote (all threads get the same answer).
@@ -250,14 +348,15 @@ __device__ __forceinline__ int wrapi(int v, int n) {
 // ------------------------------------------------------------------ kernel
 template <int P, int CX, int CY, int CZ, int NC, int NSLOT>
 __global__ void __launch_bounds__((NC + 1) * 32, 1)
-    step_tma_kernel(const __grid_constant__ CUtensorMap tmap, const StepArgs a,
+    step_tma_kernel(const __grid_constant__ TmaMaps maps, const StepArgs a,
                     const __grid_constant__ StepTablesS<P> tpar) {
     using G = TmaGeom<P, CX, CY, CZ>;
     using SM = TmaSmem<P, CX, CY, CZ, NC, NSLOT>;
     constexpr int NPW = kQ / NC;  // velocity pairs per consumer warp
     static_assert(NPW * NC == kQ, "consumers must split the 45 pairs evenly");
     using TC = TmemCols<G::TX, NPW, NC>;
-    constexpr uint32_t kWaitLimit = 1u << 21;  // polls of <= 2 us with back-off: about 4 s before giving up
+    static_assert(kItems >= NSLOT && kMaxPieces <= NSLOT, "item table and ring sizes");
+    constexpr int SLOT_F2 = G::SLOT_BYTES / 8;
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -266,9 +365,11 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
     float* prm = reinterpret_cast<float*>(base + SM::slots + SM::partials);
     StepTablesS<P>* tsm = reinterpret_cast<StepTablesS<P>*>(base + SM::slots + SM::partials + SM::params);
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + SM::slots + SM::partials + SM::params + SM::tables);
-    volatile long long* slot_tag = reinterpret_cast<volatile long long*>(bars + 2 * NSLOT);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 3 * NSLOT);
-    uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(bars + 3 * NSLOT) + 1;
+    // item table: entry s % kItems = (s << 32) | (first slot << 8) | (its phase << 4) | pieces
+    // for item s (tile-major, 45 per tile), written with one 64-bit store
+    volatile unsigned long long* items = reinterpret_cast<volatile unsigned long long*>(bars + 2 * NSLOT);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * NSLOT + kItems);
+    uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(bars + 2 * NSLOT + kItems) + 1;
     long long* woff = reinterpret_cast<long long*>(reinterpret_cast<unsigned char*>(bars) + SM::bars_padded);
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + NSLOT);
 
@@ -285,7 +386,7 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
-        for (int s = 0; s < NSLOT; ++s) slot_tag[s] = -1;
+        for (int e = 0; e < kItems; ++e) items[e] = ~0ull;
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -306,69 +407,213 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
 
     if (warp == NC) {
         // ------------------------------------------------ producer warp
-        long long s = 0;
+        // Per tile, lane L works out items L and L + 32 in parallel (box origin of the first
+        // periodic image, image counts, shape, ring positions).  Items then go out in order,
+        // in batches: every lane holding one of the next unissued items whose slots lie within
+        // one ring turn tests its slots, and the longest run of ready items from the first
+        // one is announced and issued at once, one lane per item.  A producer that falls
+        // behind thus issues larger batches instead of paying the mbarrier and TMA latencies
+        // once per item.
+        uint32_t s_tile = 0;  // number of the tile's first item
+        int rbase = 0;        // ring position (mod 2 NSLOT) of the tile's first slot
+        int done = 0;         // ring positions used so far, capped (for the drain)
         bool ok = true;
-        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-            const int c0[3] = {(tile % ntx) * CX, ((tile / ntx) % nty) * CY, (tile / (ntx * nty)) * CZ};
-            const int cd[3] = {CX, CY, CZ};
-            for (int j = 0; j < kQ; ++j, ++s) {
-                const int slot = static_cast<int>(s % NSLOT);
-                const uint32_t ph = static_cast<uint32_t>((s / NSLOT) & 1);
-                if (!mbar_wait_bounded(empty0 + 8 * slot, ph ^ 1u, abort_flag, err_flag, kWaitLimit)) {
-                    ok = false;
-                    break;
-                }
-                int b0[3];
-                bool cross = false;
+        const uint32_t slots_u32 = smem_u32(slots);
+        const int cd[3] = {CX, CY, CZ};
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, s_tile += kQ) {
+            const int tyz = tile / ntx;
+            const int cb[3] = {(tile - tyz * ntx) * CX * P, (tyz % nty) * CY * P, (tyz / nty) * CZ * P};
+            // meta: pieces m | nk_x << 4 | nk_y << 8 | nk_z << 12 | shape << 16 | cp.async << 20
+            uint32_t meta[2];
+            int crd[2][3];
+            int mm[2];
 #pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    b0[d] = (c0[d] + t.kmin[j][d]) * P;
-                    const int need = (cd[d] + t.span[j][d]) * P + 1;
-                    cross |= (b0[d] < 0) || (b0[d] + need > a.N[d]);
-                }
-                const int x0 = b0[0] - (b0[0] & 1);  // even pair index (floor for negatives)
-                const uint32_t dst = smem_u32(slots) + static_cast<uint32_t>(slot) * G::SLOT_BYTES;
-                const uint32_t full = full0 + 8 * slot;
-                // announce which item this slot now carries (see the consumer's wait)
-                if (lane == 0) slot_tag[slot] = s;
-                if (!cross) {
-                    if (lane == 0) {
-                        mbar_arrive_expect_tx(full, G::BOX_BYTES);
-                        tma_load_4d(dst, &tmap, 2 * x0, b0[1], b0[2], j, full);
+            for (int h = 0; h < 2; ++h) {
+                const int j = lane + 32 * h;
+                meta[h] = 0;
+                mm[h] = 0;
+                crd[h][0] = crd[h][1] = crd[h][2] = 0;
+                if (j < kQ) {
+                    int b0[3], klo[3], nk[3], sp[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        sp[d] = t.span[j][d];
+                        b0[d] = cb[d] + t.kmin[j][d] * P;
+                        const int need = (cd[d] + sp[d]) * P + 1;
+                        klo[d] = floor_div(b0[d], a.N[d]);
+                        nk[d] = floor_div(b0[d] + need - 1, a.N[d]) - klo[d] + 1;
                     }
-                } else {
-                    // the box crosses the periodic boundary: 16-byte copies from the wrapped
-                    // positions.  A chunk is two (f,g) pairs at an even x and N[0] is even, so a
-                    // chunk never straddles the boundary.  The wrapped offsets (in floats) of
-                    // the box's planes, rows and chunks are computed once per box into a table.
+                    const int npiece = nk[0] * nk[1] * nk[2];
+                    const bool tma_pieces = npiece <= kMaxPieces;
+                    mm[h] = tma_pieces ? npiece : 1;
+                    const int x0 = b0[0] - (b0[0] & 1);  // even pair index (floor for negatives)
+                    crd[h][0] = 2 * (x0 - klo[0] * a.N[0]);
+                    crd[h][1] = b0[1] - klo[1] * a.N[1];
+                    crd[h][2] = b0[2] - klo[2] * a.N[2];
+                    meta[h] = static_cast<uint32_t>(mm[h] | (nk[0] << 4) | (nk[1] << 8) | (nk[2] << 12) |
+                                                    ((sp[0] + 2 * sp[1] + 4 * sp[2]) << 16) |
+                                                    ((tma_pieces ? 0 : 1) << 20));
+                }
+            }
+            // ring positions (relative to rbase): exclusive prefix sums of the piece counts
+            int inc0 = mm[0], inc1 = mm[1];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u0 = __shfl_up_sync(0xffffffffu, inc0, o), u1 = __shfl_up_sync(0xffffffffu, inc1, o);
+                if (lane >= o) {
+                    inc0 += u0;
+                    inc1 += u1;
+                }
+            }
+            const int tot0 = __shfl_sync(0xffffffffu, inc0, 31), tot1 = __shfl_sync(0xffffffffu, inc1, 31);
+            const int pre[2] = {inc0 - mm[0], tot0 + inc1 - mm[1]};
+
+            int nxt = 0;  // first item of the tile not issued yet
+            while (nxt < kQ) {
+                const int h = nxt >> 5;
+                const int lo = nxt & 31;
+                const int nlane = h ? kQ - 32 : 32;  // items held in this round
+                const uint32_t mt = h ? meta[1] : meta[0];
+                const int m = h ? mm[1] : mm[0];
+                const int pr = h ? pre[1] : pre[0];
+                const int pos = rbase + pr;
+                const int slot = pos % NSLOT;
+                const uint32_t phase = static_cast<uint32_t>((pos / NSLOT) & 1);
+                const bool fallback = (mt >> 20) & 1u;
+                const int pr_first = __shfl_sync(0xffffffffu, pr, lo);
+                // Candidates: this round's unissued TMA items whose slots lie within one ring turn
+                // of the first unissued position (their slot's previous use has been issued, so
+                // one parity bit tells the phases apart).
+                bool ready = lane >= lo && lane < nlane && !fallback && pr + m <= pr_first + NSLOT;
+                if (ready) {
+                    int sq = slot;
+                    uint32_t pq = phase;
+                    for (int q = 0; q < m; ++q) {
+                        if (!mbar_test_wait(empty0 + 8 * sq, pq ^ 1u)) {
+                            ready = false;
+                            break;
+                        }
+                        if (++sq == NSLOT) {
+                            sq = 0;
+                            pq ^= 1u;
+                        }
+                    }
+                }
+                const uint32_t rmask = __ballot_sync(0xffffffffu, ready) >> lo;
+                const int run = (~rmask == 0u) ? 32 - lo : __ffs(static_cast<int>(~rmask)) - 1;
+                bool issue = lane >= lo && lane < lo + run;
+                int stop = 0;
+                if (run == 0) {
+                    // the first unissued item is not ready (or needs the whole warp): wait for its
+                    // slots (blocking, bounded), then issue it alone
+                    if (lane == lo) {
+                        int sq = slot;
+                        uint32_t pq = phase;
+                        for (int q = 0; q < m; ++q) {
+                            if (!mbar_wait_bounded(empty0 + 8 * sq, pq ^ 1u, abort_flag, err_flag)) {
+                                stop = 1;
+                                break;
+                            }
+                            if (++sq == NSLOT) {
+                                sq = 0;
+                                pq ^= 1u;
+                            }
+                        }
+                        if (!stop && fallback) stop = 2;
+                        issue = stop == 0;
+                    }
+                    stop = __shfl_sync(0xffffffffu, stop, lo);
+                    if (stop == 1) {
+                        // drain below from this item's first ring position
+                        const int posb = __shfl_sync(0xffffffffu, pos, lo);
+                        done = done + pr_first < NSLOT ? done + pr_first : NSLOT;
+                        rbase = posb % (2 * NSLOT);
+                        ok = false;
+                        break;
+                    }
+                }
+                if (issue || (stop == 2 && lane == lo)) {
+                    const uint32_t s = s_tile + static_cast<uint32_t>(lane + 32 * h);
+                    items[s & (kItems - 1)] = (static_cast<unsigned long long>(s) << 32) |
+                                              (static_cast<uint32_t>(slot) << 8) | (phase << 4) |
+                                              static_cast<uint32_t>(m);
+                }
+                if (issue) {
+                    const int shape = static_cast<int>((mt >> 16) & 7u);
+                    const CUtensorMap* map = &maps.m[shape];
+                    const uint32_t bytes = static_cast<uint32_t>(G::xpairs(shape & 1) * G::rows((shape >> 1) & 1) *
+                                                                 G::planes(shape >> 2)) * 8u;
+                    const int nkx = static_cast<int>((mt >> 4) & 15u), nky = static_cast<int>((mt >> 8) & 15u),
+                              nkz = static_cast<int>((mt >> 12) & 15u);
+                    const int cx = h ? crd[1][0] : crd[0][0], cy = h ? crd[1][1] : crd[0][1],
+                              cz = h ? crd[1][2] : crd[0][2];
+                    const int j = lane + 32 * h;
+                    int sq = slot;
+                    for (int qz = 0; qz < nkz; ++qz)
+                        for (int qy = 0; qy < nky; ++qy)
+                            for (int qx = 0; qx < nkx; ++qx) {
+                                const uint32_t full = full0 + 8 * sq;
+                                mbar_arrive_expect_tx(full, bytes);
+                                tma_load_4d(slots_u32 + static_cast<uint32_t>(sq) * G::SLOT_BYTES, map,
+                                            cx - 2 * qx * a.N[0], cy - qy * a.N[1], cz - qz * a.N[2], j, full);
+                                if (++sq == NSLOT) sq = 0;
+                            }
+                }
+                if (stop == 2) {
+                    const int j = nxt;
+                    const int fslot = __shfl_sync(0xffffffffu, slot, lo);
+                    const uint32_t dst = slots_u32 + static_cast<uint32_t>(fslot) * G::SLOT_BYTES;
+                    const uint32_t full = full0 + 8 * fslot;
+                    int b0[3], sp[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        sp[d] = t.span[j][d];
+                        b0[d] = cb[d] + t.kmin[j][d] * P;
+                    }
+                    const int x0 = b0[0] - (b0[0] & 1);
+                    // the box overlaps more periodic images than there are pieces: 16-byte copies
+                    // from the wrapped positions, in the layout of the box's shape.  A chunk is
+                    // two (f,g) pairs at an even x and N[0] is even, so a chunk never straddles
+                    // the boundary.  The wrapped offsets (in floats) of the box's planes, rows
+                    // and chunks are computed once per box into a table.
                     const float* src = static_cast<const float*>(a.src) + 2LL * j * a.nn;
-                    constexpr int CH = G::BXP / 2;
-                    constexpr int NCHUNK = G::BZ * G::BY * CH;
-                    if (lane < G::BZ)
-                        woff[lane] = 2LL * wrapi(b0[2] + lane, a.N[2]) * a.N[1] * a.N[0];
-                    if (lane < G::BY) woff[G::BZ + lane] = 2LL * wrapi(b0[1] + lane, a.N[1]) * a.N[0];
+                    const int XP = G::xpairs(sp[0]), YR = G::rows(sp[1]), ZP = G::planes(sp[2]);
+                    const int CH = XP / 2;
+                    const int nchunk = ZP * YR * CH;
+                    if (lane < ZP) woff[lane] = 2LL * wrapi(b0[2] + lane, a.N[2]) * a.N[1] * a.N[0];
+                    if (lane < YR) woff[G::BZ + lane] = 2LL * wrapi(b0[1] + lane, a.N[1]) * a.N[0];
                     if (lane < CH) woff[G::BZ + G::BY + lane] = 2LL * wrapi(x0 + 2 * lane, a.N[0]);
                     __syncwarp();
-                    for (int q = lane; q < NCHUNK; q += 32) {
-                        const int c = q % CH;
+                    for (int q = lane; q < nchunk; q += 32) {
                         const int row = q / CH;
-                        const int y = row % G::BY, z = row / G::BY;
+                        const int c = q - row * CH;
+                        const int z = row / YR, y = row - z * YR;
                         const long long off = woff[z] + woff[G::BZ + y] + woff[G::BZ + G::BY + c];
-                        cp_async16(dst + static_cast<uint32_t>((row * G::BXP + 2 * c) * 8), src + off);
+                        cp_async16(dst + static_cast<uint32_t>((row * XP + 2 * c) * 8), src + off);
                     }
-                    __syncwarp();  // the table is rewritten for the next crossing box
+                    __syncwarp();  // the table is rewritten for the next such box
                     cp_async_mbar_arrive(full);
                     __syncwarp();
                     if (lane == 0) mbar_arrive(full);
                 }
+                nxt += run > 0 ? run : 1;
             }
+            if (!ok) break;
+            rbase = (rbase + tot0 + tot1) % (2 * NSLOT);
+            done = done + tot0 + tot1 < NSLOT ? done + tot0 + tot1 : NSLOT;
         }
         if (!ok) {
-            // drain: wait (bounded) for the fills this warp may still have in flight
-            for (long long r = s - NSLOT; r < s; ++r) {
-                if (r < 0) continue;
-                mbar_wait_bounded(full0 + 8 * static_cast<int>(r % NSLOT), static_cast<uint32_t>((r / NSLOT) & 1),
-                                  abort_flag, nullptr, 1u << 18);
+            // drain: wait (bounded, whatever the abort flag says) for the fills of the last
+            // ring positions issued (at most NSLOT), which may still be in flight
+            volatile int keep_waiting = 0;
+            int sq = rbase % NSLOT;
+            uint32_t pq = static_cast<uint32_t>((rbase / NSLOT) & 1);
+            for (int q = 0; q < done; ++q) {
+                if (--sq < 0) {
+                    sq = NSLOT - 1;
+                    pq ^= 1u;
+                }
+                mbar_wait_bounded(full0 + 8 * sq, pq, &keep_waiting, nullptr);
             }
         }
         return;
@@ -394,20 +639,32 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
 #pragma unroll 1
         for (int k = 0; k < NPW; ++k) {
             const int j = c + NC * k;
-            const long long s = tau * kQ + j;
-            const int slot = static_cast<int>(s % NSLOT);
-            const uint32_t ph = static_cast<uint32_t>((s / NSLOT) & 1);
-            // A slot's previous fill (item s - NSLOT, another warp's) may still be in flight when
-            // this warp arrives, and one parity bit cannot tell "previous phase pending" from
-            // "this phase done".  Wait until the producer has issued item s into the slot (its
-            // tag): the barrier is then within one phase of the one awaited.
-            wait_tag_bounded(slot_tag + slot, s, abort_flag, err_flag, kWaitLimit);
-            mbar_wait_bounded(full0 + 8 * slot, ph, abort_flag, err_flag, kWaitLimit);
-            float2* box = slots + static_cast<size_t>(slot) * (G::SLOT_BYTES / 8);
-            const int ox0 = ((c0[0] + t.kmin[j][0]) * P) & 1;
-
-            // z pass, in place: column (y, xb) of the box, planes -> output planes 0..TZ-1
+            const uint32_t s = static_cast<uint32_t>(tau * kQ + j);
+            // Where the item sits in the ring.  The producer announces an item only once all
+            // its slots are free, so every slot's full barrier is then at most one phase ahead
+            // of the phase awaited below (one parity bit cannot tell more apart).
+            const uint32_t pos = wait_item_bounded(items + (s & (kItems - 1)), s, abort_flag, err_flag);
+            const int slot = static_cast<int>(pos >> 8), m = static_cast<int>(pos & 15u);
             {
+                int sq = slot;
+                uint32_t pq = (pos >> 4) & 1u;
+                for (int q = 0; q < m; ++q) {
+                    mbar_wait_bounded(full0 + 8 * sq, pq, abort_flag, err_flag);
+                    if (++sq == NSLOT) {
+                        sq = 0;
+                        pq ^= 1u;
+                    }
+                }
+            }
+            float2* box = slots + static_cast<size_t>(slot) * SLOT_F2;
+            const int ox0 = ((c0[0] + t.kmin[j][0]) * P) & 1;
+            // the box's shape: rows of XP pairs, planes of PL pairs
+            const int sx = t.span[j][0], sy = t.span[j][1], sz = t.span[j][2];
+            const int XP = G::xpairs(sx), PL = G::rows(sy) * XP;
+
+            // z pass, in place: column (y, xb) of the box, NZ planes -> output planes 0..TZ-1
+            auto z_pass = [&](auto nz) {
+                constexpr int NZ = decltype(nz)::value;
                 float2 wz[P][P + 1];
                 bool kz[P];
 #pragma unroll
@@ -416,32 +673,68 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
 #pragma unroll
                     for (int l = 0; l <= P; ++l) wz[az][l] = make_float2(t.lw[j][2][az][l], t.lw[j][2][az][l]);
                 }
+                const int nit = (PL + 31) >> 5;
 #pragma unroll 2
-                for (int it = 0; it < (G::PLANE + 31) / 32; ++it) {
+                for (int it = 0; it < nit; ++it) {
                     const int e = lane + 32 * it;
-                    if (e < G::PLANE) {
-                        float2 v[G::BZ];
+                    if (e < PL) {
+                        float2 v[NZ];
 #pragma unroll
-                        for (int z = 0; z < G::BZ; ++z) v[z] = box[z * G::PLANE + e];
+                        for (int z = 0; z < NZ; ++z) v[z] = box[z * PL + e];
+                        // the other periodic images of a box that crosses the boundary (each is
+                        // zero outside the domain, so their sum is the wrapped box)
+                        for (int q = 1; q < m; ++q) {
+                            int sq = slot + q;
+                            sq -= sq >= NSLOT ? NSLOT : 0;
+                            const float2* bq = slots + static_cast<size_t>(sq) * SLOT_F2;
+#pragma unroll
+                            for (int z = 0; z < NZ; ++z) {
+                                const float2 u = bq[z * PL + e];
+                                v[z].x += u.x;
+                                v[z].y += u.y;
+                            }
+                        }
 #pragma unroll
                         for (int oz = 0; oz < G::TZ; ++oz) {
                             const int cz = oz / P, az = oz % P;
                             float2 o = make_float2(0.f, 0.f);
-                            if (kz[az]) {
+                            if constexpr (NZ == G::BZ) {
+                                if (kz[az]) {
 #pragma unroll
-                                for (int l = 0; l <= P; ++l) o = ffma2(v[(cz + 1) * P + l], wz[az][l], o);
+                                    for (int l = 0; l <= P; ++l) o = ffma2(v[(cz + 1) * P + l], wz[az][l], o);
+                                } else {
+#pragma unroll
+                                    for (int l = 0; l <= P; ++l) o = ffma2(v[cz * P + l], wz[az][l], o);
+                                }
                             } else {
 #pragma unroll
                                 for (int l = 0; l <= P; ++l) o = ffma2(v[cz * P + l], wz[az][l], o);
                             }
-                            box[oz * G::PLANE + e] = o;
+                            box[oz * PL + e] = o;
                         }
                     }
                 }
-            }
+            };
+            if (sz)
+                z_pass(IntC<G::BZ>{});
+            else
+                z_pass(IntC<G::BZ0>{});
             __syncwarp();
-            // y pass, in place: column (oz, xb), rows -> output rows 0..TY-1
-            {
+            if (m > 1) {
+                // the extra images were only read: hand their slots back now
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) {
+                    for (int q = 1; q < m; ++q) {
+                        int sq = slot + q;
+                        sq -= sq >= NSLOT ? NSLOT : 0;
+                        mbar_arrive(empty0 + 8 * sq);
+                    }
+                }
+            }
+            // y pass, in place: column (oz, xb), NY rows -> output rows 0..TY-1
+            auto y_pass = [&](auto ny) {
+                constexpr int NY = decltype(ny)::value;
                 float2 wy[P][P + 1];
                 bool ky[P];
 #pragma unroll
@@ -450,19 +743,19 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
 #pragma unroll
                     for (int l = 0; l <= P; ++l) wy[ay][l] = make_float2(t.lw[j][1][ay][l], t.lw[j][1][ay][l]);
                 }
+                const int ncol = G::TZ * XP;
 #pragma unroll 1
-                for (int it = 0; it < (G::TZ * G::BXP + 31) / 32; ++it) {
-                    const int e = lane + 32 * it;
-                    if (e < G::TZ * G::BXP) {
-                        const int oz = e / G::BXP, xb = e - oz * G::BXP;
-                        float2* col = box + oz * G::PLANE + xb;
-                        float2 v[G::BY];
+                for (int e = lane; e < ncol; e += 32) {
+                    const int oz = e / XP, xb = e - oz * XP;
+                    float2* col = box + oz * PL + xb;
+                    float2 v[NY];
 #pragma unroll
-                        for (int y = 0; y < G::BY; ++y) v[y] = col[y * G::BXP];
+                    for (int y = 0; y < NY; ++y) v[y] = col[y * XP];
 #pragma unroll
-                        for (int oy = 0; oy < G::TY; ++oy) {
-                            const int cy = oy / P, ay = oy % P;
-                            float2 o = make_float2(0.f, 0.f);
+                    for (int oy = 0; oy < G::TY; ++oy) {
+                        const int cy = oy / P, ay = oy % P;
+                        float2 o = make_float2(0.f, 0.f);
+                        if constexpr (NY == G::BY) {
                             if (ky[ay]) {
 #pragma unroll
                                 for (int l = 0; l <= P; ++l) o = ffma2(v[(cy + 1) * P + l], wy[ay][l], o);
@@ -470,15 +763,23 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
 #pragma unroll
                                 for (int l = 0; l <= P; ++l) o = ffma2(v[cy * P + l], wy[ay][l], o);
                             }
-                            col[oy * G::BXP] = o;
+                        } else {
+#pragma unroll
+                            for (int l = 0; l <= P; ++l) o = ffma2(v[cy * P + l], wy[ay][l], o);
                         }
+                        col[oy * XP] = o;
                     }
                 }
-            }
+            };
+            if (sy)
+                y_pass(IntC<G::BY>{});
+            else
+                y_pass(IntC<G::BY0>{});
             __syncwarp();
-            // x pass: lane = x-row (oz, oy) of the tile
+            // x pass: lane = x-row (oz, oy) of the tile, NX pairs from the row's start
             float res[2 * G::TX];
-            {
+            auto x_pass = [&](auto nx) {
+                constexpr int NX = decltype(nx)::value;
                 float2 wx[P][P + 1];
                 bool kx[P];
 #pragma unroll
@@ -487,17 +788,22 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
 #pragma unroll
                     for (int l = 0; l <= P; ++l) wx[ax][l] = make_float2(t.lw[j][0][ax][l], t.lw[j][0][ax][l]);
                 }
-                float2 v[G::BX];
-                const float2* row = box + oz_l * G::PLANE + oy_l * G::BXP + ox0;
+                float2 v[NX];
+                const float2* row = box + oz_l * PL + oy_l * XP + ox0;
 #pragma unroll
-                for (int x = 0; x < G::BX; ++x) v[x] = row_lane ? row[x] : make_float2(0.f, 0.f);
+                for (int x = 0; x < NX; ++x) v[x] = row_lane ? row[x] : make_float2(0.f, 0.f);
 #pragma unroll
                 for (int ox = 0; ox < G::TX; ++ox) {
                     const int cx = ox / P, ax = ox % P;
                     float2 o = make_float2(0.f, 0.f);
-                    if (kx[ax]) {
+                    if constexpr (NX == G::BX) {
+                        if (kx[ax]) {
 #pragma unroll
-                        for (int l = 0; l <= P; ++l) o = ffma2(v[(cx + 1) * P + l], wx[ax][l], o);
+                            for (int l = 0; l <= P; ++l) o = ffma2(v[(cx + 1) * P + l], wx[ax][l], o);
+                        } else {
+#pragma unroll
+                            for (int l = 0; l <= P; ++l) o = ffma2(v[cx * P + l], wx[ax][l], o);
+                        }
                     } else {
 #pragma unroll
                         for (int l = 0; l <= P; ++l) o = ffma2(v[cx * P + l], wx[ax][l], o);
@@ -505,11 +811,15 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
                     res[2 * ox] = o.x;
                     res[2 * ox + 1] = o.y;
                 }
-            }
+            };
+            if (sx)
+                x_pass(IntC<G::BX>{});
+            else
+                x_pass(IntC<G::BX0>{});
             // the slot was written in place (generic proxy); order that before the next TMA fill
             fence_proxy_async();
             __syncwarp();
-            if (lane == 0) mbar_arrive(empty0 + 8 * slot);
+            if (lane == 0 && m > 0) mbar_arrive(empty0 + 8 * slot);
 
             // moment contributions of this pair, then park the pair in tensor memory
             const float xix = t.xi[j][0], xiy = t.xi[j][1], xiz = t.xi[j][2];
@@ -526,27 +836,35 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
             tmem_store_row<G::TX>(tmem_warp + static_cast<uint32_t>(k * 2 * G::TX), res);
         }
 
-        // Shared-memory layouts indexed [..][x][lane] (node = lane*TX + x) so that every
-        // lane-parallel access below is contiguous (no bank conflicts).
+        // Per-node moment sums over the warps, in a fixed order: warp c adds its contributions
+        // once warp c - 1 has (hand-over through named barrier c + 1).  Shared-memory layouts
+        // are indexed [..][x][lane] (node = lane*TX + x) so that every lane-parallel access
+        // below is contiguous (no bank conflicts).
         {
-            float* pc = part + static_cast<size_t>(c) * 5 * G::TX * 32 + lane;
+            float* pc = part + lane;
+            if (c > 0) named_barrier_sync(c + 1, 64);
 #pragma unroll
             for (int q = 0; q < 5; ++q)
 #pragma unroll
-                for (int x = 0; x < G::TX; ++x) pc[(q * G::TX + x) * 32] = pm[q][x];
+                for (int x = 0; x < G::TX; ++x) {
+                    float* e = pc + (q * G::TX + x) * 32;
+                    *e = c > 0 ? *e + pm[q][x] : pm[q][x];
+                }
+            if (c + 1 < NC) {
+                __threadfence_block();
+                named_barrier_arrive(c + 2, 64);
+            }
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         if (consumer_barrier_or(*abort_flag, NC * 32)) break;
 
-        // per-node moments (fixed-order sum over warps), tau, equilibrium coefficients
+        // per-node moments, tau, equilibrium coefficients
         for (int tn = threadIdx.x; tn < G::TX * 32; tn += NC * 32) {
             const int xn = tn >> 5, ln = tn & 31;  // node = ln*TX + xn
             if (ln >= G::ROWS) continue;
-            float m[5] = {0, 0, 0, 0, 0};
+            float m[5];
 #pragma unroll
-            for (int w = 0; w < NC; ++w)
-#pragma unroll
-                for (int q = 0; q < 5; ++q) m[q] += part[((static_cast<size_t>(w) * 5 + q) * G::TX + xn) * 32 + ln];
+            for (int q = 0; q < 5; ++q) m[q] = part[(q * G::TX + xn) * 32 + ln];
             const float rho = m[0];
             const float inv_rho = 1.0f / rho;
             const float ux = m[1] * inv_rho, uy = m[2] * inv_rho, uz = m[3] * inv_rho;

@@ -28,13 +28,9 @@ template <>
 struct TmaTile<4> {
     static constexpr int CX = 2, CY = 2, CZ = 1;
 };
-// Consumer warps (45 velocity pairs split evenly: 9 x 5) and source boxes in flight per SM
-// (as many as fit next to the moment sums, parameters and tables).
+// Consumer warps (45 velocity pairs split evenly: 9 x 5).
 template <int P>
 constexpr int kConsumersFor = 9;
-template <int P>
-constexpr int kSlotsFor =
-    SlotFit<P, TmaTile<P>::CX, TmaTile<P>::CY, TmaTile<P>::CZ, kConsumersFor<P>, kMaxSlots>::value;
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static std::once_flag once;
@@ -119,8 +115,8 @@ template <int P>
 int launch_tma(sllbm_ctx* ctx, const void* src, void* dst) {
     using T = TmaTile<P>;
     constexpr int kConsumers = kConsumersFor<P>;
-    using SM = TmaSmem<P, T::CX, T::CY, T::CZ, kConsumers, kSlotsFor<P>>;
-    static_assert(SM::bytes <= 227 * 1024, "shared memory budget");
+    using SM = TmaSmem<P, T::CX, T::CY, T::CZ, kConsumers>;
+    static_assert(SM::bytes <= kSmemBudget, "shared memory budget");
     using Tab = StepTablesS<P>;
     if (ctx->step_blob == nullptr || ctx->step_blob_size != sizeof(Tab) + 1) {
         std::free(ctx->step_blob);
@@ -136,7 +132,7 @@ int launch_tma(sllbm_ctx* ctx, const void* src, void* dst) {
     fill_step_args(ctx, src, dst, &args);
     const int ntiles = (ctx->cells[0] / T::CX) * (ctx->cells[1] / T::CY) * (ctx->cells[2] / T::CZ);
     const int grid = ntiles < ctx->num_sms ? ntiles : ctx->num_sms;
-    auto k = step_tma_kernel<P, T::CX, T::CY, T::CZ, kConsumers, kSlotsFor<P>>;
+    auto k = step_tma_kernel<P, T::CX, T::CY, T::CZ, kConsumers>;
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(SM::bytes));
     if (err == cudaSuccess) {
         k<<<grid, (kConsumers + 1) * 32, SM::bytes, ctx->stream>>>(maps, args, *reinterpret_cast<const Tab*>(ctx->step_blob));

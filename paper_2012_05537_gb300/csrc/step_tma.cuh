@@ -5,23 +5,25 @@
 //
 //  * One persistent CTA per SM walks tiles of CX x CY x CZ cells (TX x TY x TZ nodes).
 //  * A producer warp loads, for every velocity i of a tile, the source box of the pair
-//    (f_i, g_i) -- the tile translated by the departure cell shift, plus one cell and the
-//    shared face -- into a ring of shared-memory slots: one 4D TMA load
+//    (f_i, g_i) -- the tile translated by the departure cell shift, plus the cells and the
+//    shared face the departure points reach; a box is one cell shorter in each direction
+//    where all local nodes depart from the same cell -- into a ring of shared memory that
+//    is allocated in 128-byte units and reclaimed in order: one 4D TMA load
 //    (cp.async.bulk.tensor) when the box lies inside the periodic domain; when it crosses
-//    the boundary, one TMA load per periodic image it overlaps, into consecutive slots
-//    (zero-filled outside the domain, summed by the consumer on its first pass), or
-//    16-byte cp.async copies from the wrapped positions when that takes too many images.
-//    Slots are handed over with mbarriers (transaction counts); a small item table tells
-//    the consumers where each item starts in the ring and how many slots it took.
+//    the boundary, one TMA load per periodic image it overlaps, back to back (zero-filled
+//    outside the domain, summed by the consumer on its first pass), or 16-byte cp.async
+//    copies from the wrapped positions when that takes too many images.  Items are handed
+//    over through a ring of 32 descriptors: full/empty mbarriers (transaction counts) and
+//    an item table entry that tells the consumers where the item's box sits.
 //  * NC consumer warps own 45/NC velocity pairs each.  For a pair they run the z and y
-//    Lagrange passes in place in the slot (each lane owns whole columns) and the x pass
-//    into registers (lane = one x-row of the tile), then release the slot.  f_i and g_i
+//    Lagrange passes in place in the box (each lane owns whole columns) and the x pass
+//    into registers (lane = one x-row of the tile), then release the box.  f_i and g_i
 //    share weights and positions, so every FMA is a packed FP32x2 FMA.  The streamed
 //    (f_i, g_i) of the lane's TX nodes go to the lane's row of tensor memory
 //    (tcgen05.st), which keeps the register file free for the passes; the per-node
 //    moment contributions are accumulated in registers on the way.
-//  * Per tile, the partial moments are reduced across warps through shared memory in a
-//    fixed order and turned into rho, u, T, omega and the shell coefficients of the
+//  * Per tile, the partial moments are summed over the warps in shared memory in a fixed
+//    order (deterministic results) and turned into rho, u, T, omega and the shell coefficients of the
 //    quartic equilibrium; each warp then reads its pairs back (tcgen05.ld), collides and
 //    stores them (16-byte stores, f_i and g_i interleaved).
 //  * Every mbarrier wait is bounded; on expiry the kernel raises an error flag, the
@@ -68,6 +70,11 @@ struct TmaGeom {
     __host__ __device__ static constexpr int xpairs(int span) { return span ? BXP : BXP0; }
     __host__ __device__ static constexpr int rows(int span) { return span ? BY : BY0; }
     __host__ __device__ static constexpr int planes(int span) { return span ? BZ : BZ0; }
+    // bytes of a box of shape sx + 2 sy + 4 sz, and the 128-byte ring units one piece takes
+    __host__ __device__ static constexpr int box_bytes(int shape) {
+        return xpairs(shape & 1) * rows((shape >> 1) & 1) * planes((shape >> 2) & 1) * 8;
+    }
+    __host__ __device__ static constexpr int piece_units(int shape) { return (box_bytes(shape) + 127) / 128; }
     static_assert(ROWS <= 32, "one x-row per lane");
     static_assert(BXP % 2 == 0 && BXP >= BX + 1 && BXP0 % 2 == 0 && BXP0 >= BX0 + 1, "TMA rows start on an even pair");
     static_assert(TX == 8 || TX == 9, "tensor-memory row layout");
@@ -80,44 +87,40 @@ struct TmaMaps {
 };
 
 constexpr int kNParams = 20;  // rho, ux, uy, uz, gT, omega, c0[4], c1[4], c2[4], (2 spare)
+// Fixed-point scale of the per-node moment sums (a per-warp partial times this stays far below
+// 2^63 for any state the step can represent; the unit 2^-40 is far below FP32 resolution).
+constexpr float kFixScale = 1099511627776.0f;  // 2^40
+constexpr double kFixUnit = 1.0 / 1099511627776.0;
 // A source box that crosses the periodic boundary is loaded as one TMA box per periodic image
-// it overlaps (zero outside the domain), at most kMaxPieces of them in consecutive ring slots;
+// it overlaps (zero outside the domain), at most kMaxPieces of them, back to back in the ring;
 // boxes with more images (meshes not much larger than a tile) take the cp.async path.
 constexpr int kMaxPieces = 8;
-// Entries of the item table (a power of two, at least the slot count: an entry is reused only
-// after the item that used it has released its slots).
+// Items in flight at most: the descriptor ring (full/empty mbarriers, item table entry and
+// ring offset per item; a power of two).
 constexpr int kItems = 32;
-constexpr int kMaxSlots = 24;
 constexpr size_t kSmemBudget = 227 * 1024;
 static_assert((kItems & (kItems - 1)) == 0, "item table size");
 
-template <int P, int CX, int CY, int CZ, int NC, int NSLOT>
+template <int P, int CX, int CY, int CZ, int NC>
 struct TmaSmem {
     using G = TmaGeom<P, CX, CY, CZ>;
     // every region starts on a 128-byte boundary (TMA destinations, float4 and mbarrier
     // alignment)
     static constexpr size_t round128(size_t b) { return (b + 127) / 128 * 128; }
-    static constexpr size_t slots = size_t(NSLOT) * G::SLOT_BYTES;
-    static constexpr size_t partials = round128(size_t(5) * G::TX * 32 * sizeof(float));  // moment sums
+    static constexpr size_t partials = round128(size_t(5) * G::TX * 32 * sizeof(long long));  // moment sums
     static constexpr size_t params = round128(size_t(kNParams) * G::TX * 32 * sizeof(float));
     static constexpr size_t tables = round128(sizeof(StepTablesS<P>));
-    // full[NSLOT], empty[NSLOT] mbarriers, the item table (one word per entry: item number,
-    // first slot, its phase and the piece count), flags
-    static constexpr size_t bars = (size_t(2) * NSLOT + kItems) * sizeof(uint64_t) + 16;
+    // full[kItems], empty[kItems] mbarriers, the item table (one word per entry: item number,
+    // ring offset and piece count), the ring offsets of the items in flight, flags
+    static constexpr size_t bars = size_t(3) * kItems * sizeof(uint64_t) + kItems * sizeof(int) + 16;
     static constexpr size_t bars_padded = round128(bars);
     static constexpr size_t woff = round128(size_t(G::BZ + G::BY + G::BXP / 2) * sizeof(long long));
-    static constexpr size_t bytes = slots + partials + params + tables + bars_padded + woff + 128;  // +128: base alignment
-};
-
-// The largest slot count (at most kMaxSlots) whose layout fits the shared-memory budget.
-template <int P, int CX, int CY, int CZ, int NC, int N>
-struct SlotFit {
-    static constexpr int value =
-        TmaSmem<P, CX, CY, CZ, NC, N>::bytes <= kSmemBudget ? N : SlotFit<P, CX, CY, CZ, NC, N - 1>::value;
-};
-template <int P, int CX, int CY, int CZ, int NC>
-struct SlotFit<P, CX, CY, CZ, NC, 0> {
-    static constexpr int value = 0;
+    static constexpr size_t fixed = partials + params + tables + bars_padded + woff + 128;  // +128: base alignment
+    // the box ring takes the rest, in 128-byte units
+    static constexpr int ring_units = static_cast<int>((kSmemBudget - fixed) / 128);
+    static constexpr size_t ring = size_t(ring_units) * 128;
+    static constexpr size_t bytes = ring + fixed;
+    static_assert(ring_units >= kMaxPieces * (G::SLOT_BYTES / 128), "ring holds the largest item");
 };
 
 // Tensor-memory columns: a warp's lane keeps NPW pairs x 2*TX floats; warps w, w+4, w+8
@@ -275,12 +278,9 @@ __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Named barriers between two warps (64 threads): one warp arrives, the other waits.
-__device__ __forceinline__ void named_barrier_sync(int id, int nthreads) {
-    asm volatile("barrier.cta.sync.aligned %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-__device__ __forceinline__ void named_barrier_arrive(int id, int nthreads) {
-    asm volatile("barrier.cta.arrive.aligned %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+// Shared-memory 64-bit add without a result (no wait for the old value).
+__device__ __forceinline__ void red_add_shared(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(smem_u32(p)), "l"(v) : "memory");
 }
 
 // Named barrier 1 over the consumer warps with an OR vote (all threads get the same answer).
@@ -346,32 +346,32 @@ __device__ __forceinline__ int wrapi(int v, int n) {
 }
 
 // ------------------------------------------------------------------ kernel
-template <int P, int CX, int CY, int CZ, int NC, int NSLOT>
+template <int P, int CX, int CY, int CZ, int NC>
 __global__ void __launch_bounds__((NC + 1) * 32, 1)
     step_tma_kernel(const __grid_constant__ TmaMaps maps, const StepArgs a,
                     const __grid_constant__ StepTablesS<P> tpar) {
     using G = TmaGeom<P, CX, CY, CZ>;
-    using SM = TmaSmem<P, CX, CY, CZ, NC, NSLOT>;
+    using SM = TmaSmem<P, CX, CY, CZ, NC>;
     constexpr int NPW = kQ / NC;  // velocity pairs per consumer warp
     static_assert(NPW * NC == kQ, "consumers must split the 45 pairs evenly");
     using TC = TmemCols<G::TX, NPW, NC>;
-    static_assert(kItems >= NSLOT && kMaxPieces <= NSLOT, "item table and ring sizes");
-    constexpr int SLOT_F2 = G::SLOT_BYTES / 8;
+    constexpr uint32_t KM = kItems - 1;
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    float2* slots = reinterpret_cast<float2*>(base);
-    float* part = reinterpret_cast<float*>(base + SM::slots);
-    float* prm = reinterpret_cast<float*>(base + SM::slots + SM::partials);
-    StepTablesS<P>* tsm = reinterpret_cast<StepTablesS<P>*>(base + SM::slots + SM::partials + SM::params);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(base + SM::slots + SM::partials + SM::params + SM::tables);
-    // item table: entry s % kItems = (s << 32) | (first slot << 8) | (its phase << 4) | pieces
-    // for item s (tile-major, 45 per tile), written with one 64-bit store
-    volatile unsigned long long* items = reinterpret_cast<volatile unsigned long long*>(bars + 2 * NSLOT);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * NSLOT + kItems);
-    uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(bars + 2 * NSLOT + kItems) + 1;
+    float2* ring = reinterpret_cast<float2*>(base);  // the box ring, 16 float2 per unit
+    unsigned long long* part = reinterpret_cast<unsigned long long*>(base + SM::ring);
+    float* prm = reinterpret_cast<float*>(base + SM::ring + SM::partials);
+    StepTablesS<P>* tsm = reinterpret_cast<StepTablesS<P>*>(base + SM::ring + SM::partials + SM::params);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + SM::ring + SM::partials + SM::params + SM::tables);
+    // item table: entry s % kItems = (s << 32) | (ring offset in units << 8) | pieces for item s
+    // (tile-major, 45 per tile), written with one 64-bit store
+    volatile unsigned long long* items = reinterpret_cast<volatile unsigned long long*>(bars + 2 * kItems);
+    int* start_of = reinterpret_cast<int*>(bars + 3 * kItems);  // ring offset per item in flight
+    volatile int* abort_flag = start_of + kItems;
+    uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(start_of + kItems) + 1;
     long long* woff = reinterpret_cast<long long*>(reinterpret_cast<unsigned char*>(bars) + SM::bars_padded);
-    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + NSLOT);
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kItems);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     {
@@ -379,12 +379,13 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
         const int* src = reinterpret_cast<const int*>(&tpar);
         int* dstw = reinterpret_cast<int*>(tsm);
         for (int q = threadIdx.x; q < static_cast<int>(sizeof(StepTablesS<P>) / 4); q += blockDim.x) dstw[q] = src[q];
+        for (int q = threadIdx.x; q < 5 * G::TX * 32; q += blockDim.x) part[q] = 0ull;
     }
     const StepTablesS<P>& t = *tsm;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NSLOT; ++s) {
-            mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 1);
+        for (int e = 0; e < kItems; ++e) {
+            mbar_init(full0 + 8 * e, 1);
+            mbar_init(empty0 + 8 * e, 1);
         }
         for (int e = 0; e < kItems; ++e) items[e] = ~0ull;
         *abort_flag = 0;
@@ -408,17 +409,18 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
     if (warp == NC) {
         // ------------------------------------------------ producer warp
         // Per tile, lane L works out items L and L + 32 in parallel (box origin of the first
-        // periodic image, image counts, shape, ring positions).  Items then go out in order,
-        // in batches: every lane holding one of the next unissued items whose slots lie within
-        // one ring turn tests its slots, and the longest run of ready items from the first
-        // one is announced and issued at once, one lane per item.  A producer that falls
-        // behind thus issues larger batches instead of paying the mbarrier and TMA latencies
-        // once per item.
+        // periodic image, image counts, shape, ring units).  Items then go out in order, in
+        // batches: the releases of the oldest items in flight are confirmed together (one
+        // lane per item), as many of the next items as fit are placed in the ring, and they
+        // are announced and issued at once, one lane per item.  A producer that falls behind
+        // thus issues larger batches instead of paying the mbarrier and TMA latencies once
+        // per item.  The ring is reclaimed in item order.
         uint32_t s_tile = 0;  // number of the tile's first item
-        int rbase = 0;        // ring position (mod 2 NSLOT) of the tile's first slot
-        int done = 0;         // ring positions used so far, capped (for the drain)
+        uint32_t tail = 0;    // oldest item whose release is not confirmed yet
+        int head = 0;         // ring unit where the next item goes (if it fits)
+        uint32_t sent = 0;    // items issued
         bool ok = true;
-        const uint32_t slots_u32 = smem_u32(slots);
+        const uint32_t ring_u32 = smem_u32(ring);
         const int cd[3] = {CX, CY, CZ};
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, s_tile += kQ) {
             const int tyz = tile / ntx;
@@ -426,12 +428,12 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
             // meta: pieces m | nk_x << 4 | nk_y << 8 | nk_z << 12 | shape << 16 | cp.async << 20
             uint32_t meta[2];
             int crd[2][3];
-            int mm[2];
+            int units[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int j = lane + 32 * h;
                 meta[h] = 0;
-                mm[h] = 0;
+                units[h] = 0;
                 crd[h][0] = crd[h][1] = crd[h][2] = 0;
                 if (j < kQ) {
                     int b0[3], klo[3], nk[3], sp[3];
@@ -445,125 +447,113 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
                     }
                     const int npiece = nk[0] * nk[1] * nk[2];
                     const bool tma_pieces = npiece <= kMaxPieces;
-                    mm[h] = tma_pieces ? npiece : 1;
+                    const int m = tma_pieces ? npiece : 1;
+                    const int shape = sp[0] + 2 * sp[1] + 4 * sp[2];
+                    units[h] = m * G::piece_units(shape);
                     const int x0 = b0[0] - (b0[0] & 1);  // even pair index (floor for negatives)
                     crd[h][0] = 2 * (x0 - klo[0] * a.N[0]);
                     crd[h][1] = b0[1] - klo[1] * a.N[1];
                     crd[h][2] = b0[2] - klo[2] * a.N[2];
-                    meta[h] = static_cast<uint32_t>(mm[h] | (nk[0] << 4) | (nk[1] << 8) | (nk[2] << 12) |
-                                                    ((sp[0] + 2 * sp[1] + 4 * sp[2]) << 16) |
+                    meta[h] = static_cast<uint32_t>(m | (nk[0] << 4) | (nk[1] << 8) | (nk[2] << 12) | (shape << 16) |
                                                     ((tma_pieces ? 0 : 1) << 20));
                 }
             }
-            // ring positions (relative to rbase): exclusive prefix sums of the piece counts
-            int inc0 = mm[0], inc1 = mm[1];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int u0 = __shfl_up_sync(0xffffffffu, inc0, o), u1 = __shfl_up_sync(0xffffffffu, inc1, o);
-                if (lane >= o) {
-                    inc0 += u0;
-                    inc1 += u1;
-                }
-            }
-            const int tot0 = __shfl_sync(0xffffffffu, inc0, 31), tot1 = __shfl_sync(0xffffffffu, inc1, 31);
-            const int pre[2] = {inc0 - mm[0], tot0 + inc1 - mm[1]};
 
             int nxt = 0;  // first item of the tile not issued yet
             while (nxt < kQ) {
                 const int h = nxt >> 5;
                 const int lo = nxt & 31;
                 const int nlane = h ? kQ - 32 : 32;  // items held in this round
-                const uint32_t mt = h ? meta[1] : meta[0];
-                const int m = h ? mm[1] : mm[0];
-                const int pr = h ? pre[1] : pre[0];
-                const int pos = rbase + pr;
-                const int slot = pos % NSLOT;
-                const uint32_t phase = static_cast<uint32_t>((pos / NSLOT) & 1);
-                const bool fallback = (mt >> 20) & 1u;
-                const int pr_first = __shfl_sync(0xffffffffu, pr, lo);
-                // Candidates: this round's unissued TMA items whose slots lie within one ring turn
-                // of the first unissued position (their slot's previous use has been issued, so
-                // one parity bit tells the phases apart).
-                bool ready = lane >= lo && lane < nlane && !fallback && pr + m <= pr_first + NSLOT;
-                if (ready) {
-                    int sq = slot;
-                    uint32_t pq = phase;
-                    for (int q = 0; q < m; ++q) {
-                        if (!mbar_test_wait(empty0 + 8 * sq, pq ^ 1u)) {
-                            ready = false;
-                            break;
-                        }
-                        if (++sq == NSLOT) {
-                            sq = 0;
-                            pq ^= 1u;
-                        }
-                    }
+                const uint32_t issued = s_tile + static_cast<uint32_t>(nxt);
+                // confirm the releases of the oldest items in flight, in order
+                int inflight = static_cast<int>(issued - tail);
+                if (inflight > 0) {
+                    const uint32_t x = tail + static_cast<uint32_t>(lane);
+                    const bool rel = lane < inflight && mbar_test_wait(empty0 + 8 * (x & KM), (x / kItems) & 1u);
+                    const uint32_t rm = __ballot_sync(0xffffffffu, rel);
+                    const int nrel = (~rm == 0u) ? 32 : __ffs(static_cast<int>(~rm)) - 1;
+                    tail += static_cast<uint32_t>(nrel);
+                    inflight -= nrel;
                 }
-                const uint32_t rmask = __ballot_sync(0xffffffffu, ready) >> lo;
-                const int run = (~rmask == 0u) ? 32 - lo : __ffs(static_cast<int>(~rmask)) - 1;
-                bool issue = lane >= lo && lane < lo + run;
-                int stop = 0;
-                if (run == 0) {
-                    // the first unissued item is not ready (or needs the whole warp): wait for its
-                    // slots (blocking, bounded), then issue it alone
-                    if (lane == lo) {
-                        int sq = slot;
-                        uint32_t pq = phase;
-                        for (int q = 0; q < m; ++q) {
-                            if (!mbar_wait_bounded(empty0 + 8 * sq, pq ^ 1u, abort_flag, err_flag)) {
-                                stop = 1;
-                                break;
-                            }
-                            if (++sq == NSLOT) {
-                                sq = 0;
-                                pq ^= 1u;
-                            }
-                        }
-                        if (!stop && fallback) stop = 2;
-                        issue = stop == 0;
+                if (inflight == 0) head = 0;  // ring empty: start over at its beginning
+                // place the next items of this round while they fit (a cp.async item goes alone)
+                int tail_off = inflight > 0 ? start_of[tail & KM] : 0;
+                bool nonempty = inflight > 0;
+                int nb = 0;
+                int my_off = -1;
+                bool first_fb = false;
+                while (lo + nb < nlane && inflight + nb < kItems) {
+                    const int need = __shfl_sync(0xffffffffu, h ? units[1] : units[0], lo + nb);
+                    const bool fb = (__shfl_sync(0xffffffffu, h ? meta[1] : meta[0], lo + nb) >> 20) & 1u;
+                    if (fb && nb > 0) break;
+                    int off = -1;
+                    if (!nonempty) {
+                        off = head;
+                    } else if (head > tail_off) {
+                        off = head + need <= SM::ring_units ? head : (need <= tail_off ? 0 : -1);
+                    } else if (head < tail_off) {
+                        off = head + need <= tail_off ? head : -1;
                     }
-                    stop = __shfl_sync(0xffffffffu, stop, lo);
-                    if (stop == 1) {
-                        // drain below from this item's first ring position
-                        const int posb = __shfl_sync(0xffffffffu, pos, lo);
-                        done = done + pr_first < NSLOT ? done + pr_first : NSLOT;
-                        rbase = posb % (2 * NSLOT);
-                        ok = false;
+                    if (off < 0) break;
+                    if (lane == lo + nb) my_off = off;
+                    if (!nonempty) {
+                        tail_off = off;
+                        nonempty = true;
+                    }
+                    head = off + need;
+                    ++nb;
+                    if (fb) {
+                        first_fb = true;
                         break;
                     }
                 }
-                if (issue || (stop == 2 && lane == lo)) {
-                    const uint32_t s = s_tile + static_cast<uint32_t>(lane + 32 * h);
-                    items[s & (kItems - 1)] = (static_cast<unsigned long long>(s) << 32) |
-                                              (static_cast<uint32_t>(slot) << 8) | (phase << 4) |
-                                              static_cast<uint32_t>(m);
+                if (nb == 0) {
+                    // nothing fits: wait (blocking, bounded) for the oldest item's release
+                    int stop = 0;
+                    if (lane == 0 && !mbar_wait_bounded(empty0 + 8 * (tail & KM), (tail / kItems) & 1u, abort_flag,
+                                                        err_flag))
+                        stop = 1;
+                    if (__shfl_sync(0xffffffffu, stop, 0)) {
+                        ok = false;
+                        break;
+                    }
+                    ++tail;
+                    continue;
                 }
-                if (issue) {
-                    const int shape = static_cast<int>((mt >> 16) & 7u);
-                    const CUtensorMap* map = &maps.m[shape];
-                    const uint32_t bytes = static_cast<uint32_t>(G::xpairs(shape & 1) * G::rows((shape >> 1) & 1) *
-                                                                 G::planes(shape >> 2)) * 8u;
-                    const int nkx = static_cast<int>((mt >> 4) & 15u), nky = static_cast<int>((mt >> 8) & 15u),
-                              nkz = static_cast<int>((mt >> 12) & 15u);
-                    const int cx = h ? crd[1][0] : crd[0][0], cy = h ? crd[1][1] : crd[0][1],
-                              cz = h ? crd[1][2] : crd[0][2];
-                    const int j = lane + 32 * h;
-                    int sq = slot;
-                    for (int qz = 0; qz < nkz; ++qz)
-                        for (int qy = 0; qy < nky; ++qy)
-                            for (int qx = 0; qx < nkx; ++qx) {
-                                const uint32_t full = full0 + 8 * sq;
-                                mbar_arrive_expect_tx(full, bytes);
-                                tma_load_4d(slots_u32 + static_cast<uint32_t>(sq) * G::SLOT_BYTES, map,
-                                            cx - 2 * qx * a.N[0], cy - qy * a.N[1], cz - qz * a.N[2], j, full);
-                                if (++sq == NSLOT) sq = 0;
-                            }
+                // announce and issue the batch, one lane per item
+                const bool mine = lane >= lo && lane < lo + nb;
+                if (mine) {
+                    const uint32_t s = issued + static_cast<uint32_t>(lane - lo);
+                    const uint32_t mt = h ? meta[1] : meta[0];
+                    const int m = static_cast<int>(mt & 15u);
+                    const uint32_t e = s & KM;
+                    start_of[e] = my_off;
+                    items[e] = (static_cast<unsigned long long>(s) << 32) | (static_cast<uint32_t>(my_off) << 8) |
+                               static_cast<uint32_t>(m);
+                    if (!first_fb) {
+                        const int shape = static_cast<int>((mt >> 16) & 7u);
+                        const CUtensorMap* map = &maps.m[shape];
+                        const uint32_t bytes = static_cast<uint32_t>(G::box_bytes(shape));
+                        const uint32_t pstride = static_cast<uint32_t>(G::piece_units(shape)) * 128u;
+                        const int nkx = static_cast<int>((mt >> 4) & 15u), nky = static_cast<int>((mt >> 8) & 15u),
+                                  nkz = static_cast<int>((mt >> 12) & 15u);
+                        const int cx = h ? crd[1][0] : crd[0][0], cy = h ? crd[1][1] : crd[0][1],
+                                  cz = h ? crd[1][2] : crd[0][2];
+                        const int j = lane + 32 * h;
+                        const uint32_t full = full0 + 8 * e;
+                        mbar_arrive_expect_tx(full, bytes * static_cast<uint32_t>(m));
+                        uint32_t dst = ring_u32 + static_cast<uint32_t>(my_off) * 128u;
+                        for (int qz = 0; qz < nkz; ++qz)
+                            for (int qy = 0; qy < nky; ++qy)
+                                for (int qx = 0; qx < nkx; ++qx, dst += pstride)
+                                    tma_load_4d(dst, map, cx - 2 * qx * a.N[0], cy - qy * a.N[1], cz - qz * a.N[2], j,
+                                                full);
+                    }
                 }
-                if (stop == 2) {
+                if (first_fb) {
                     const int j = nxt;
-                    const int fslot = __shfl_sync(0xffffffffu, slot, lo);
-                    const uint32_t dst = slots_u32 + static_cast<uint32_t>(fslot) * G::SLOT_BYTES;
-                    const uint32_t full = full0 + 8 * fslot;
+                    const uint32_t e = issued & KM;
+                    const int foff = __shfl_sync(0xffffffffu, my_off, lo);
                     int b0[3], sp[3];
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
@@ -571,6 +561,8 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
                         b0[d] = cb[d] + t.kmin[j][d] * P;
                     }
                     const int x0 = b0[0] - (b0[0] & 1);
+                    const uint32_t dst = ring_u32 + static_cast<uint32_t>(foff) * 128u;
+                    const uint32_t full = full0 + 8 * e;
                     // the box overlaps more periodic images than there are pieces: 16-byte copies
                     // from the wrapped positions, in the layout of the box's shape.  A chunk is
                     // two (f,g) pairs at an even x and N[0] is even, so a chunk never straddles
@@ -596,25 +588,17 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
                     __syncwarp();
                     if (lane == 0) mbar_arrive(full);
                 }
-                nxt += run > 0 ? run : 1;
+                __syncwarp();  // ring offsets written by the issuing lanes are read by all
+                nxt += nb;
+                sent = issued + static_cast<uint32_t>(nb);
             }
-            if (!ok) break;
-            rbase = (rbase + tot0 + tot1) % (2 * NSLOT);
-            done = done + tot0 + tot1 < NSLOT ? done + tot0 + tot1 : NSLOT;
         }
         if (!ok) {
-            // drain: wait (bounded, whatever the abort flag says) for the fills of the last
-            // ring positions issued (at most NSLOT), which may still be in flight
+            // drain: wait (bounded, whatever the abort flag says) for the fills of the items
+            // in flight
             volatile int keep_waiting = 0;
-            int sq = rbase % NSLOT;
-            uint32_t pq = static_cast<uint32_t>((rbase / NSLOT) & 1);
-            for (int q = 0; q < done; ++q) {
-                if (--sq < 0) {
-                    sq = NSLOT - 1;
-                    pq ^= 1u;
-                }
-                mbar_wait_bounded(full0 + 8 * sq, pq, &keep_waiting, nullptr);
-            }
+            for (uint32_t x = tail; x != sent; ++x)
+                mbar_wait_bounded(full0 + 8 * (x & KM), (x / kItems) & 1u, &keep_waiting, nullptr);
         }
         return;
     }
@@ -640,27 +624,19 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
         for (int k = 0; k < NPW; ++k) {
             const int j = c + NC * k;
             const uint32_t s = static_cast<uint32_t>(tau * kQ + j);
-            // Where the item sits in the ring.  The producer announces an item only once all
-            // its slots are free, so every slot's full barrier is then at most one phase ahead
-            // of the phase awaited below (one parity bit cannot tell more apart).
-            const uint32_t pos = wait_item_bounded(items + (s & (kItems - 1)), s, abort_flag, err_flag);
-            const int slot = static_cast<int>(pos >> 8), m = static_cast<int>(pos & 15u);
-            {
-                int sq = slot;
-                uint32_t pq = (pos >> 4) & 1u;
-                for (int q = 0; q < m; ++q) {
-                    mbar_wait_bounded(full0 + 8 * sq, pq, abort_flag, err_flag);
-                    if (++sq == NSLOT) {
-                        sq = 0;
-                        pq ^= 1u;
-                    }
-                }
-            }
-            float2* box = slots + static_cast<size_t>(slot) * SLOT_F2;
+            // Where the item sits in the ring.  The producer announces item s only once item
+            // s - kItems has released the same descriptor, so its full barrier is then at most
+            // one phase ahead of the phase awaited below (one parity bit cannot tell more apart).
+            const uint32_t e = s & KM;
+            const uint32_t word = wait_item_bounded(items + e, s, abort_flag, err_flag);
+            const int m = static_cast<int>(word & 15u);
+            if (m > 0) mbar_wait_bounded(full0 + 8 * e, (s / kItems) & 1u, abort_flag, err_flag);
+            float2* box = ring + static_cast<size_t>(word >> 8) * 16;
             const int ox0 = ((c0[0] + t.kmin[j][0]) * P) & 1;
-            // the box's shape: rows of XP pairs, planes of PL pairs
+            // the box's shape: rows of XP pairs, planes of PL pairs; pieces PSTRIDE float2 apart
             const int sx = t.span[j][0], sy = t.span[j][1], sz = t.span[j][2];
             const int XP = G::xpairs(sx), PL = G::rows(sy) * XP;
+            const int PSTRIDE = G::piece_units(sx + 2 * sy + 4 * sz) * 16;
 
             // z pass, in place: column (y, xb) of the box, NZ planes -> output planes 0..TZ-1
             auto z_pass = [&](auto nz) {
@@ -684,9 +660,7 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
                         // the other periodic images of a box that crosses the boundary (each is
                         // zero outside the domain, so their sum is the wrapped box)
                         for (int q = 1; q < m; ++q) {
-                            int sq = slot + q;
-                            sq -= sq >= NSLOT ? NSLOT : 0;
-                            const float2* bq = slots + static_cast<size_t>(sq) * SLOT_F2;
+                            const float2* bq = box + q * PSTRIDE;
 #pragma unroll
                             for (int z = 0; z < NZ; ++z) {
                                 const float2 u = bq[z * PL + e];
@@ -720,18 +694,6 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
             else
                 z_pass(IntC<G::BZ0>{});
             __syncwarp();
-            if (m > 1) {
-                // the extra images were only read: hand their slots back now
-                fence_proxy_async();
-                __syncwarp();
-                if (lane == 0) {
-                    for (int q = 1; q < m; ++q) {
-                        int sq = slot + q;
-                        sq -= sq >= NSLOT ? NSLOT : 0;
-                        mbar_arrive(empty0 + 8 * sq);
-                    }
-                }
-            }
             // y pass, in place: column (oz, xb), NY rows -> output rows 0..TY-1
             auto y_pass = [&](auto ny) {
                 constexpr int NY = decltype(ny)::value;
@@ -819,7 +781,7 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
             // the slot was written in place (generic proxy); order that before the next TMA fill
             fence_proxy_async();
             __syncwarp();
-            if (lane == 0 && m > 0) mbar_arrive(empty0 + 8 * slot);
+            if (lane == 0 && m > 0) mbar_arrive(empty0 + 8 * e);
 
             // moment contributions of this pair, then park the pair in tensor memory
             const float xix = t.xi[j][0], xiy = t.xi[j][1], xiz = t.xi[j][2];
@@ -836,24 +798,28 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
             tmem_store_row<G::TX>(tmem_warp + static_cast<uint32_t>(k * 2 * G::TX), res);
         }
 
-        // Per-node moment sums over the warps, in a fixed order: warp c adds its contributions
-        // once warp c - 1 has (hand-over through named barrier c + 1).  Shared-memory layouts
-        // are indexed [..][x][lane] (node = lane*TX + x) so that every lane-parallel access
-        // below is contiguous (no bank conflicts).
+        // Per-node moment sums over the warps: each warp adds its contributions as 64-bit fixed
+        // point (2^-40 units) with shared-memory atomics.  Integer addition is exact, so the
+        // sums do not depend on the order the warps arrive in.  Shared-memory layouts are
+        // indexed [..][x][lane] (node = lane*TX + x) so that every lane-parallel access below
+        // is contiguous.
         {
-            float* pc = part + lane;
-            if (c > 0) named_barrier_sync(c + 1, 64);
+            if (a.flag != nullptr) {
+                // a non-finite contribution would not survive the conversion: flag it here
+                bool bad = false;
+#pragma unroll
+                for (int q = 0; q < 5; ++q)
+#pragma unroll
+                    for (int x = 0; x < G::TX; ++x) bad |= !isfinite(pm[q][x]);
+                if (bad) atomicOr(a.flag, 1);
+            }
+            unsigned long long* pc = part + lane;
 #pragma unroll
             for (int q = 0; q < 5; ++q)
 #pragma unroll
-                for (int x = 0; x < G::TX; ++x) {
-                    float* e = pc + (q * G::TX + x) * 32;
-                    *e = c > 0 ? *e + pm[q][x] : pm[q][x];
-                }
-            if (c + 1 < NC) {
-                __threadfence_block();
-                named_barrier_arrive(c + 2, 64);
-            }
+                for (int x = 0; x < G::TX; ++x)
+                    red_add_shared(pc + (q * G::TX + x) * 32,
+                                   static_cast<unsigned long long>(__float2ll_rn(pm[q][x] * kFixScale)));
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         if (consumer_barrier_or(*abort_flag, NC * 32)) break;
@@ -862,9 +828,15 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
         for (int tn = threadIdx.x; tn < G::TX * 32; tn += NC * 32) {
             const int xn = tn >> 5, ln = tn & 31;  // node = ln*TX + xn
             if (ln >= G::ROWS) continue;
+            // read the sums and clear them for the next tile (every warp adds to them only after
+            // the barrier that closes this phase)
             float m[5];
 #pragma unroll
-            for (int q = 0; q < 5; ++q) m[q] = part[(q * G::TX + xn) * 32 + ln];
+            for (int q = 0; q < 5; ++q) {
+                unsigned long long* e = part + (q * G::TX + xn) * 32 + ln;
+                m[q] = static_cast<float>(static_cast<double>(static_cast<long long>(*e)) * kFixUnit);
+                *e = 0ull;
+            }
             const float rho = m[0];
             const float inv_rho = 1.0f / rho;
             const float ux = m[1] * inv_rho, uy = m[2] * inv_rho, uz = m[3] * inv_rho;

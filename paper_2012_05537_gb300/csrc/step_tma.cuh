@@ -476,37 +476,48 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
                     inflight -= nrel;
                 }
                 if (inflight == 0) head = 0;  // ring empty: start over at its beginning
-                // place the next items of this round while they fit (a cp.async item goes alone)
-                int tail_off = inflight > 0 ? start_of[tail & KM] : 0;
-                bool nonempty = inflight > 0;
-                int nb = 0;
-                int my_off = -1;
-                bool first_fb = false;
-                while (lo + nb < nlane && inflight + nb < kItems) {
-                    const int need = __shfl_sync(0xffffffffu, h ? units[1] : units[0], lo + nb);
-                    const bool fb = (__shfl_sync(0xffffffffu, h ? meta[1] : meta[0], lo + nb) >> 20) & 1u;
-                    if (fb && nb > 0) break;
-                    int off = -1;
-                    if (!nonempty) {
-                        off = head;
-                    } else if (head > tail_off) {
-                        off = head + need <= SM::ring_units ? head : (need <= tail_off ? 0 : -1);
-                    } else if (head < tail_off) {
-                        off = head + need <= tail_off ? head : -1;
-                    }
-                    if (off < 0) break;
-                    if (lane == lo + nb) my_off = off;
-                    if (!nonempty) {
-                        tail_off = off;
-                        nonempty = true;
-                    }
-                    head = off + need;
-                    ++nb;
-                    if (fb) {
-                        first_fb = true;
-                        break;
-                    }
+                // Place the next items of this round: a prefix sum of their ring units over the
+                // lanes, then the longest run from the first one that fits in one free region
+                // (the rest of the ring after `head`, or its start when that is too short).  A
+                // cp.async item goes alone.
+                const int tail_off = inflight > 0 ? start_of[tail & KM] : 0;
+                const int cap = min(nlane - lo, kItems - inflight);
+                const uint32_t mt_l = h ? meta[1] : meta[0];
+                const bool cand = lane >= lo && lane < lo + cap;
+                const uint32_t fbm = __ballot_sync(0xffffffffu, cand && ((mt_l >> 20) & 1u));
+                const bool first_fb = (fbm >> lo) & 1u;
+                // candidates end before the first cp.async item after the first one
+                const uint32_t fb_after = fbm & ~((2u << lo) - 1u);
+                const int end = first_fb ? lo + 1 : (fb_after ? min(lo + cap, __ffs(static_cast<int>(fb_after)) - 1) : lo + cap);
+                const int need_l = (lane >= lo && lane < end) ? (h ? units[1] : units[0]) : 0;
+                int incl = need_l;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += u;
                 }
+                const int first_need = __shfl_sync(0xffffffffu, need_l, lo);
+                int base = -1, limit = 0;
+                if (inflight == 0) {
+                    base = head;
+                    limit = SM::ring_units;
+                } else if (head > tail_off) {
+                    if (head + first_need <= SM::ring_units) {
+                        base = head;
+                        limit = SM::ring_units;
+                    } else if (first_need <= tail_off) {
+                        base = 0;
+                        limit = tail_off;
+                    }
+                } else if (head < tail_off) {
+                    base = head;
+                    limit = tail_off;
+                }
+                const bool fits = base >= 0 && lane >= lo && lane < end && base + incl <= limit;
+                const uint32_t fm = __ballot_sync(0xffffffffu, fits) >> lo;
+                const int nb = (~fm == 0u) ? 32 - lo : __ffs(static_cast<int>(~fm)) - 1;
+                const int my_off = base + incl - need_l;
+                if (nb > 0) head = base + __shfl_sync(0xffffffffu, incl, lo + nb - 1);
                 if (nb == 0) {
                     // nothing fits: wait (blocking, bounded) for the oldest item's release
                     int stop = 0;

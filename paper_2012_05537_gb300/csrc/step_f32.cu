@@ -13,7 +13,9 @@ namespace sllbm {
 
 namespace {
 
-// Tile (in cells) of the TMA kernel per order: 8x8x4, 9x9x3 and 8x8x4 nodes.
+// Tile (in cells) of the TMA kernel per order: 8x8x4 nodes for p = 2 and p = 4.  (For p = 3
+// a tile of whole cells is 9 nodes wide, and two tiles of streamed pairs do not fit in tensor
+// memory next to each other; p = 3 runs the generic kernel.)
 template <int P>
 struct TmaTile;
 template <>
@@ -21,14 +23,10 @@ struct TmaTile<2> {
     static constexpr int CX = 4, CY = 4, CZ = 2;
 };
 template <>
-struct TmaTile<3> {
-    static constexpr int CX = 3, CY = 3, CZ = 1;
-};
-template <>
 struct TmaTile<4> {
     static constexpr int CX = 2, CY = 2, CZ = 1;
 };
-// Consumer warps (45 velocity pairs split evenly: 9 x 5).
+// Stream warps (45 velocity pairs split evenly: 9 x 5).
 template <int P>
 constexpr int kConsumersFor = 9;
 
@@ -135,7 +133,8 @@ int launch_tma(sllbm_ctx* ctx, const void* src, void* dst) {
     auto k = step_tma_kernel<P, T::CX, T::CY, T::CZ, kConsumers>;
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(SM::bytes));
     if (err == cudaSuccess) {
-        k<<<grid, (kConsumers + 1) * 32, SM::bytes, ctx->stream>>>(maps, args, *reinterpret_cast<const Tab*>(ctx->step_blob));
+        k<<<grid, kWarps * 32, SM::bytes, ctx->stream>>>(
+            maps, args, *reinterpret_cast<const Tab*>(ctx->step_blob));
         err = cudaGetLastError();
     }
     ctx->launches += 1;
@@ -154,7 +153,6 @@ bool tma_step_eligible(const sllbm_ctx* c) {
     if (tensor_map_encoder() == nullptr) return false;
     switch (c->p) {
     case 2: return tma_eligible_p<2>(c);
-    case 3: return tma_eligible_p<3>(c);
     case 4: return tma_eligible_p<4>(c);
     }
     return false;
@@ -164,7 +162,6 @@ int launch_step_f32(sllbm_ctx* ctx, const void* src, void* dst) {
     if (ctx->step_kernel == 2) {
         switch (ctx->p) {
         case 2: return launch_tma<2>(ctx, src, dst);
-        case 3: return launch_tma<3>(ctx, src, dst);
         case 4: return launch_tma<4>(ctx, src, dst);
         }
         return SLLBM_EINVAL;

@@ -15,20 +15,22 @@
 //    copies from the wrapped positions when that takes too many images.  Items are handed
 //    over through a ring of 32 descriptors: full/empty mbarriers (transaction counts) and
 //    an item table entry that tells the consumers where the item's box sits.
-//  * NC consumer warps own 45/NC velocity pairs each.  For a pair they run the z and y
+//  * NC stream warps own 45/NC velocity pairs each.  For a pair they run the z and y
 //    Lagrange passes in place in the box (each lane owns whole columns) and the x pass
 //    into registers (lane = one x-row of the tile), then release the box.  f_i and g_i
 //    share weights and positions, so every FMA is a packed FP32x2 FMA.  The streamed
-//    (f_i, g_i) of the lane's TX nodes go to the lane's row of tensor memory
-//    (tcgen05.st), which keeps the register file free for the passes; the per-node
-//    moment contributions are accumulated in registers on the way.
-//  * Per tile, the partial moments are summed over the warps in shared memory in a fixed
-//    order (deterministic results) and turned into rho, u, T, omega and the shell coefficients of the
-//    quartic equilibrium; each warp then reads its pairs back (tcgen05.ld), collides and
-//    stores them (16-byte stores, f_i and g_i interleaved).
-//  * Every mbarrier wait is bounded; on expiry the kernel raises an error flag, the
-//    consumers leave together at the next tile barrier (and free the tensor memory) and
-//    the producer waits (bounded) for its copies in flight before returning.
+//    (f_i, g_i) of the lane's TX nodes go to the lane's row of tensor memory (tcgen05.st),
+//    in one of two buffers per tile parity.
+//  * Four epilogue warps, one per tensor-memory lane quarter, take a tile's buffer once the
+//    quarter's stream warps are done with it: per-node moment sums of the quarter's pairs,
+//    the sum over the quarters in a fixed order (deterministic), rho, u, T, omega and the
+//    shell coefficients of the quartic equilibrium (each epilogue warp a quarter of the
+//    nodes), then the collision of the quarter's pairs and 16-byte stores (f_i and g_i
+//    interleaved).  Meanwhile the stream warps fill the other buffer: streaming never
+//    waits for the collision.
+//  * Every mbarrier wait is bounded; on expiry the kernel raises an error flag, the stream
+//    and epilogue warps leave (and free the tensor memory) and the producer waits (bounded)
+//    for its copies in flight before returning.
 #pragma once
 
 #include <cuda.h>
@@ -77,7 +79,7 @@ struct TmaGeom {
     __host__ __device__ static constexpr int piece_units(int shape) { return (box_bytes(shape) + 127) / 128; }
     static_assert(ROWS <= 32, "one x-row per lane");
     static_assert(BXP % 2 == 0 && BXP >= BX + 1 && BXP0 % 2 == 0 && BXP0 >= BX0 + 1, "TMA rows start on an even pair");
-    static_assert(TX == 8 || TX == 9, "tensor-memory row layout");
+    static_assert(TX == 8, "tensor-memory row layout and node shares of the epilogue warps");
 };
 
 // One TMA descriptor per box shape (span 0/1 in x, y, z: index sx + 2 sy + 4 sz) of a source
@@ -86,11 +88,19 @@ struct TmaMaps {
     CUtensorMap m[8];
 };
 
-constexpr int kNParams = 20;  // rho, ux, uy, uz, gT, omega, c0[4], c1[4], c2[4], (2 spare)
-// Fixed-point scale of the per-node moment sums (a per-warp partial times this stays far below
-// 2^63 for any state the step can represent; the unit 2^-40 is far below FP32 resolution).
-constexpr float kFixScale = 1099511627776.0f;  // 2^40
-constexpr double kFixUnit = 1.0 / 1099511627776.0;
+constexpr int kNParams = 18;  // rho, ux, uy, uz, gT, omega, c0[4], c1[4], c2[4]
+// Warp roles.  A warp's SM sub-partition is its index mod 4.  The producer (warp 13) has
+// sub-partition 1 to itself, so that its latency-bound issue path is not starved of issue
+// slots; the 9 stream warps are 0, 2, 3, 4, 6, 7, 8, 10, 11 (three per tensor-memory lane
+// quarter 0, 2, 3, the quarter a warp may touch being its index mod 4) and the 3 epilogue
+// warps 12, 14, 15 (one per used quarter); warps 1, 5 and 9 have no work.
+constexpr int kWarps = 16;
+constexpr int kProducerWarp = 13;
+constexpr int kEpilogueWarps = 3;
+__host__ __device__ constexpr bool is_stream_warp(int w) { return w < 12 && (w & 3) != 1; }
+__host__ __device__ constexpr int stream_index(int w) { return w - ((w + 2) >> 2); }
+__host__ __device__ constexpr bool is_epilogue_warp(int w) { return w == 12 || w == 14 || w == 15; }
+__host__ __device__ constexpr int epilogue_index(int w) { return w == 12 ? 0 : w - 13; }
 // A source box that crosses the periodic boundary is loaded as one TMA box per periodic image
 // it overlaps (zero outside the domain), at most kMaxPieces of them, back to back in the ring;
 // boxes with more images (meshes not much larger than a tile) take the cp.async path.
@@ -107,15 +117,17 @@ struct TmaSmem {
     // every region starts on a 128-byte boundary (TMA destinations, float4 and mbarrier
     // alignment)
     static constexpr size_t round128(size_t b) { return (b + 127) / 128 * 128; }
-    static constexpr size_t partials = round128(size_t(5) * G::TX * 32 * sizeof(long long));  // moment sums
+    static constexpr size_t partials = round128(size_t(4) * 5 * G::TX * 32 * sizeof(float));  // per quarter
     static constexpr size_t params = round128(size_t(kNParams) * G::TX * 32 * sizeof(float));
     static constexpr size_t tables = round128(sizeof(StepTablesS<P>));
     // full[kItems], empty[kItems] mbarriers, the item table (one word per entry: item number,
-    // ring offset and piece count), the ring offsets of the items in flight, flags
-    static constexpr size_t bars = size_t(3) * kItems * sizeof(uint64_t) + kItems * sizeof(int) + 16;
+    // ring offset and piece count), tmem_full[4][2], tmem_empty[4][2] mbarriers, the ring
+    // offsets of the items in flight, flags
+    static constexpr size_t bars = (size_t(3) * kItems + 16) * sizeof(uint64_t) + kItems * sizeof(int) + 16;
     static constexpr size_t bars_padded = round128(bars);
     static constexpr size_t woff = round128(size_t(G::BZ + G::BY + G::BXP / 2) * sizeof(long long));
-    static constexpr size_t fixed = partials + params + tables + bars_padded + woff + 128;  // +128: base alignment
+    static constexpr size_t stage = size_t(kEpilogueWarps) * 32 * 64;  // one pair's 32 rows per epilogue warp
+    static constexpr size_t fixed = partials + params + tables + bars_padded + woff + stage + 128;  // +128: base alignment
     // the box ring takes the rest, in 128-byte units
     static constexpr int ring_units = static_cast<int>((kSmemBudget - fixed) / 128);
     static constexpr size_t ring = size_t(ring_units) * 128;
@@ -123,12 +135,14 @@ struct TmaSmem {
     static_assert(ring_units >= kMaxPieces * (G::SLOT_BYTES / 128), "ring holds the largest item");
 };
 
-// Tensor-memory columns: a warp's lane keeps NPW pairs x 2*TX floats; warps w, w+4, w+8
-// share a 32-lane quarter (the quarter a warp may touch is fixed by w % 4).
+// Tensor-memory columns: a stream warp's lane keeps NPW pairs x 2*TX floats per tile; stream
+// warps w, w+4, w+8 share a 32-lane quarter (the quarter a warp may touch is fixed by w % 4);
+// each quarter holds two tiles (buffers).
 template <int TX, int NPW, int NC>
 struct TmemCols {
     static constexpr int per_warp = NPW * 2 * TX;
-    static constexpr int per_quarter = ((NC + 3) / 4) * per_warp;
+    static constexpr int per_buf = ((NC + 3) / 4) * per_warp;
+    static constexpr int per_quarter = 2 * per_buf;
     static constexpr int alloc = per_quarter <= 32 ? 32 : per_quarter <= 64 ? 64 : per_quarter <= 128 ? 128
                                : per_quarter <= 256 ? 256 : 512;
     static_assert(per_quarter <= 512, "tensor memory columns");
@@ -278,12 +292,8 @@ __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Shared-memory 64-bit add without a result (no wait for the old value).
-__device__ __forceinline__ void red_add_shared(unsigned long long* p, unsigned long long v) {
-    asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(smem_u32(p)), "l"(v) : "memory");
-}
-
-// Named barrier 1 over the consumer warps with an OR vote (all threads get the same answer).
+// Named barrier 1 over the stream and epilogue warps with an OR vote (all threads get the
+// same answer).
 __device__ __forceinline__ int consumer_barrier_or(int v, int nthreads) {
     uint32_t out;
     asm volatile(
@@ -291,6 +301,18 @@ __device__ __forceinline__ int consumer_barrier_or(int v, int nthreads) {
         "barrier.cta.red.or.pred pout, 1, %2, pin;\n\tselp.u32 %0, 1, 0, pout;\n\t}"
         : "=r"(out)
         : "r"(v), "r"(nthreads)
+        : "memory");
+    return static_cast<int>(out);
+}
+
+// Named barrier 2 over the epilogue warps, with an OR vote.
+__device__ __forceinline__ int epilogue_barrier_or(int v) {
+    uint32_t out;
+    asm volatile(
+        "{\n\t.reg .pred pin, pout;\n\tsetp.ne.u32 pin, %1, 0;\n\t"
+        "barrier.cta.red.or.pred pout, 2, %2, pin;\n\tselp.u32 %0, 1, 0, pout;\n\t}"
+        : "=r"(out)
+        : "r"(v), "r"(kEpilogueWarps * 32)
         : "memory");
     return static_cast<int>(out);
 }
@@ -347,7 +369,7 @@ __device__ __forceinline__ int wrapi(int v, int n) {
 
 // ------------------------------------------------------------------ kernel
 template <int P, int CX, int CY, int CZ, int NC>
-__global__ void __launch_bounds__((NC + 1) * 32, 1)
+__global__ void __launch_bounds__(kWarps * 32, 1)
     step_tma_kernel(const __grid_constant__ TmaMaps maps, const StepArgs a,
                     const __grid_constant__ StepTablesS<P> tpar) {
     using G = TmaGeom<P, CX, CY, CZ>;
@@ -356,21 +378,25 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
     static_assert(NPW * NC == kQ, "consumers must split the 45 pairs evenly");
     using TC = TmemCols<G::TX, NPW, NC>;
     constexpr uint32_t KM = kItems - 1;
+    constexpr int NE = kEpilogueWarps;
+    static_assert(NC == 9 && NE == 3, "warp roles");
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     float2* ring = reinterpret_cast<float2*>(base);  // the box ring, 16 float2 per unit
-    unsigned long long* part = reinterpret_cast<unsigned long long*>(base + SM::ring);
+    float* part = reinterpret_cast<float*>(base + SM::ring);
     float* prm = reinterpret_cast<float*>(base + SM::ring + SM::partials);
     StepTablesS<P>* tsm = reinterpret_cast<StepTablesS<P>*>(base + SM::ring + SM::partials + SM::params);
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + SM::ring + SM::partials + SM::params + SM::tables);
     // item table: entry s % kItems = (s << 32) | (ring offset in units << 8) | pieces for item s
     // (tile-major, 45 per tile), written with one 64-bit store
     volatile unsigned long long* items = reinterpret_cast<volatile unsigned long long*>(bars + 2 * kItems);
-    int* start_of = reinterpret_cast<int*>(bars + 3 * kItems);  // ring offset per item in flight
+    const uint32_t tmem_full0 = smem_u32(bars + 3 * kItems), tmem_empty0 = smem_u32(bars + 3 * kItems + 8);
+    int* start_of = reinterpret_cast<int*>(bars + 3 * kItems + 16);  // ring offset per item in flight
     volatile int* abort_flag = start_of + kItems;
     uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(start_of + kItems) + 1;
     long long* woff = reinterpret_cast<long long*>(reinterpret_cast<unsigned char*>(bars) + SM::bars_padded);
+    float4* stage = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(bars) + SM::bars_padded + SM::woff);
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kItems);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -379,7 +405,6 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
         const int* src = reinterpret_cast<const int*>(&tpar);
         int* dstw = reinterpret_cast<int*>(tsm);
         for (int q = threadIdx.x; q < static_cast<int>(sizeof(StepTablesS<P>) / 4); q += blockDim.x) dstw[q] = src[q];
-        for (int q = threadIdx.x; q < 5 * G::TX * 32; q += blockDim.x) part[q] = 0ull;
     }
     const StepTablesS<P>& t = *tsm;
     if (threadIdx.x == 0) {
@@ -388,6 +413,11 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
             mbar_init(empty0 + 8 * e, 1);
         }
         for (int e = 0; e < kItems; ++e) items[e] = ~0ull;
+        for (int q = 0; q < 4; ++q)
+            for (int b = 0; b < 2; ++b) {
+                mbar_init(tmem_full0 + 8 * (q * 2 + b), q == 1 ? 1u : 3u);  // stream warps per quarter
+                mbar_init(tmem_empty0 + 8 * (q * 2 + b), 1);
+            }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -406,7 +436,7 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
     const int ntiles = ntx * nty * ntz;
     int* err_flag = a.flag_err;
 
-    if (warp == NC) {
+    if (warp == kProducerWarp) {
         // ------------------------------------------------ producer warp
         // Per tile, lane L works out items L and L + 32 in parallel (box origin of the first
         // periodic image, image counts, shape, ring units).  Items then go out in order, in
@@ -614,316 +644,362 @@ __global__ void __launch_bounds__((NC + 1) * 32, 1)
         return;
     }
 
-    // ---------------------------------------------------- consumer warps
-    const int c = warp;
-    const bool row_lane = lane < G::ROWS;
+    if (!is_stream_warp(warp) && !is_epilogue_warp(warp)) return;  // no work
+
+    // ---------------------------------------------------- stream warps
+    // Warp c streams pairs c, c + NC, ... of every tile of the CTA into tensor-memory buffer
+    // it & 1 of its lane quarter (c % 4), then hands the buffer to the quarter's epilogue warp
+    // (tmem_full); before reusing a buffer it waits until that warp has read it (tmem_empty).
+    const int ncta = ntiles > static_cast<int>(blockIdx.x)
+                         ? (ntiles - 1 - static_cast<int>(blockIdx.x)) / static_cast<int>(gridDim.x) + 1
+                         : 0;
     const int oz_l = lane / G::TY, oy_l = lane % G::TY;
-    const uint32_t tmem_warp = *tmem_base_s + (static_cast<uint32_t>((warp & 3) * 32) << 16) +
-                               static_cast<uint32_t>((warp >> 2) * TC::per_warp);
-
-    long long tau = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tau) {
-        const int c0[3] = {(tile % ntx) * CX, ((tile / ntx) % nty) * CY, (tile / (ntx * nty)) * CZ};
-        // per-node moment contributions of this warp's pairs: rho, m_x, m_y, m_z, 2 rho E
-        float pm[5][G::TX];
-#pragma unroll
-        for (int q = 0; q < 5; ++q)
-#pragma unroll
-            for (int x = 0; x < G::TX; ++x) pm[q][x] = 0.f;
-
+    if (is_stream_warp(warp)) {
+        const int c = stream_index(warp), qd = warp & 3;
+        const bool row_lane = lane < G::ROWS;
+        const uint32_t tmem_warp = *tmem_base_s + (static_cast<uint32_t>(qd * 32) << 16) +
+                                   static_cast<uint32_t>((warp >> 2) * TC::per_warp);
+        for (int it = 0; it < ncta; ++it) {
+            if (*abort_flag) break;
+            const int bf = it & 1;
+            const int tile = static_cast<int>(blockIdx.x) + it * static_cast<int>(gridDim.x);
+            const int c0[3] = {(tile % ntx) * CX, ((tile / ntx) % nty) * CY, (tile / (ntx * nty)) * CZ};
+            if (it >= 2)
+                mbar_wait_bounded(tmem_empty0 + 8 * (qd * 2 + bf), static_cast<uint32_t>((it - 2) >> 1) & 1u, abort_flag,
+                                  err_flag);
+            tc_fence_after();
+            const uint32_t tbuf = tmem_warp + static_cast<uint32_t>(bf * TC::per_buf);
 #pragma unroll 1
-        for (int k = 0; k < NPW; ++k) {
-            const int j = c + NC * k;
-            const uint32_t s = static_cast<uint32_t>(tau * kQ + j);
-            // Where the item sits in the ring.  The producer announces item s only once item
-            // s - kItems has released the same descriptor, so its full barrier is then at most
-            // one phase ahead of the phase awaited below (one parity bit cannot tell more apart).
-            const uint32_t e = s & KM;
-            const uint32_t word = wait_item_bounded(items + e, s, abort_flag, err_flag);
-            const int m = static_cast<int>(word & 15u);
-            if (m > 0) mbar_wait_bounded(full0 + 8 * e, (s / kItems) & 1u, abort_flag, err_flag);
-            float2* box = ring + static_cast<size_t>(word >> 8) * 16;
-            const int ox0 = ((c0[0] + t.kmin[j][0]) * P) & 1;
-            // the box's shape: rows of XP pairs, planes of PL pairs; pieces PSTRIDE float2 apart
-            const int sx = t.span[j][0], sy = t.span[j][1], sz = t.span[j][2];
-            const int XP = G::xpairs(sx), PL = G::rows(sy) * XP;
-            const int PSTRIDE = G::piece_units(sx + 2 * sy + 4 * sz) * 16;
+            for (int k = 0; k < NPW; ++k) {
+                const int j = c + NC * k;
+                const uint32_t s = static_cast<uint32_t>(it) * kQ + static_cast<uint32_t>(j);
+                // Where the item sits in the ring.  The producer announces item s only once item
+                // s - kItems has released the same descriptor, so its full barrier is then at most
+                // one phase ahead of the phase awaited below (one parity bit cannot tell more apart).
+                const uint32_t e = s & KM;
+                const uint32_t word = wait_item_bounded(items + e, s, abort_flag, err_flag);
+                const int m = static_cast<int>(word & 15u);
+                if (m > 0) mbar_wait_bounded(full0 + 8 * e, (s / kItems) & 1u, abort_flag, err_flag);
+                float2* box = ring + static_cast<size_t>(word >> 8) * 16;
+                const int ox0 = ((c0[0] + t.kmin[j][0]) * P) & 1;
+                // the box's shape: rows of XP pairs, planes of PL pairs; pieces PSTRIDE float2 apart
+                const int sx = t.span[j][0], sy = t.span[j][1], sz = t.span[j][2];
+                const int XP = G::xpairs(sx), PL = G::rows(sy) * XP;
+                const int PSTRIDE = G::piece_units(sx + 2 * sy + 4 * sz) * 16;
 
-            // z pass, in place: column (y, xb) of the box, NZ planes -> output planes 0..TZ-1
-            auto z_pass = [&](auto nz) {
-                constexpr int NZ = decltype(nz)::value;
-                float2 wz[P][P + 1];
-                bool kz[P];
+                // z pass, in place: column (y, xb) of the box, NZ planes -> output planes 0..TZ-1
+                auto z_pass = [&](auto nz) {
+                    constexpr int NZ = decltype(nz)::value;
+                    float2 wz[P][P + 1];
+                    bool kz[P];
 #pragma unroll
-                for (int az = 0; az < P; ++az) {
-                    kz[az] = t.kc[j][2][az] != 0;
+                    for (int az = 0; az < P; ++az) {
+                        kz[az] = t.kc[j][2][az] != 0;
 #pragma unroll
-                    for (int l = 0; l <= P; ++l) wz[az][l] = make_float2(t.lw[j][2][az][l], t.lw[j][2][az][l]);
-                }
-                const int nit = (PL + 31) >> 5;
+                        for (int l = 0; l <= P; ++l) wz[az][l] = make_float2(t.lw[j][2][az][l], t.lw[j][2][az][l]);
+                    }
+                    const int nit = (PL + 31) >> 5;
 #pragma unroll 2
-                for (int it = 0; it < nit; ++it) {
-                    const int e = lane + 32 * it;
-                    if (e < PL) {
-                        float2 v[NZ];
+                    for (int it = 0; it < nit; ++it) {
+                        const int e = lane + 32 * it;
+                        if (e < PL) {
+                            float2 v[NZ];
 #pragma unroll
-                        for (int z = 0; z < NZ; ++z) v[z] = box[z * PL + e];
-                        // the other periodic images of a box that crosses the boundary (each is
-                        // zero outside the domain, so their sum is the wrapped box)
-                        for (int q = 1; q < m; ++q) {
-                            const float2* bq = box + q * PSTRIDE;
+                            for (int z = 0; z < NZ; ++z) v[z] = box[z * PL + e];
+                            // the other periodic images of a box that crosses the boundary (each is
+                            // zero outside the domain, so their sum is the wrapped box)
+                            for (int q = 1; q < m; ++q) {
+                                const float2* bq = box + q * PSTRIDE;
 #pragma unroll
-                            for (int z = 0; z < NZ; ++z) {
-                                const float2 u = bq[z * PL + e];
-                                v[z].x += u.x;
-                                v[z].y += u.y;
+                                for (int z = 0; z < NZ; ++z) {
+                                    const float2 u = bq[z * PL + e];
+                                    v[z].x += u.x;
+                                    v[z].y += u.y;
+                                }
                             }
-                        }
 #pragma unroll
-                        for (int oz = 0; oz < G::TZ; ++oz) {
-                            const int cz = oz / P, az = oz % P;
-                            float2 o = make_float2(0.f, 0.f);
-                            if constexpr (NZ == G::BZ) {
-                                if (kz[az]) {
+                            for (int oz = 0; oz < G::TZ; ++oz) {
+                                const int cz = oz / P, az = oz % P;
+                                float2 o = make_float2(0.f, 0.f);
+                                if constexpr (NZ == G::BZ) {
+                                    if (kz[az]) {
 #pragma unroll
-                                    for (int l = 0; l <= P; ++l) o = ffma2(v[(cz + 1) * P + l], wz[az][l], o);
+                                        for (int l = 0; l <= P; ++l) o = ffma2(v[(cz + 1) * P + l], wz[az][l], o);
+                                    } else {
+#pragma unroll
+                                        for (int l = 0; l <= P; ++l) o = ffma2(v[cz * P + l], wz[az][l], o);
+                                    }
                                 } else {
 #pragma unroll
                                     for (int l = 0; l <= P; ++l) o = ffma2(v[cz * P + l], wz[az][l], o);
                                 }
-                            } else {
-#pragma unroll
-                                for (int l = 0; l <= P; ++l) o = ffma2(v[cz * P + l], wz[az][l], o);
+                                box[oz * PL + e] = o;
                             }
-                            box[oz * PL + e] = o;
                         }
                     }
-                }
-            };
-            if (sz)
-                z_pass(IntC<G::BZ>{});
-            else
-                z_pass(IntC<G::BZ0>{});
-            __syncwarp();
-            // y pass, in place: column (oz, xb), NY rows -> output rows 0..TY-1
-            auto y_pass = [&](auto ny) {
-                constexpr int NY = decltype(ny)::value;
-                float2 wy[P][P + 1];
-                bool ky[P];
+                };
+                if (sz)
+                    z_pass(IntC<G::BZ>{});
+                else
+                    z_pass(IntC<G::BZ0>{});
+                __syncwarp();
+                // y pass, in place: column (oz, xb), NY rows -> output rows 0..TY-1
+                auto y_pass = [&](auto ny) {
+                    constexpr int NY = decltype(ny)::value;
+                    float2 wy[P][P + 1];
+                    bool ky[P];
 #pragma unroll
-                for (int ay = 0; ay < P; ++ay) {
-                    ky[ay] = t.kc[j][1][ay] != 0;
+                    for (int ay = 0; ay < P; ++ay) {
+                        ky[ay] = t.kc[j][1][ay] != 0;
 #pragma unroll
-                    for (int l = 0; l <= P; ++l) wy[ay][l] = make_float2(t.lw[j][1][ay][l], t.lw[j][1][ay][l]);
-                }
-                const int ncol = G::TZ * XP;
+                        for (int l = 0; l <= P; ++l) wy[ay][l] = make_float2(t.lw[j][1][ay][l], t.lw[j][1][ay][l]);
+                    }
+                    const int ncol = G::TZ * XP;
 #pragma unroll 1
-                for (int e = lane; e < ncol; e += 32) {
-                    const int oz = e / XP, xb = e - oz * XP;
-                    float2* col = box + oz * PL + xb;
-                    float2 v[NY];
+                    for (int e = lane; e < ncol; e += 32) {
+                        const int oz = e / XP, xb = e - oz * XP;
+                        float2* col = box + oz * PL + xb;
+                        float2 v[NY];
 #pragma unroll
-                    for (int y = 0; y < NY; ++y) v[y] = col[y * XP];
+                        for (int y = 0; y < NY; ++y) v[y] = col[y * XP];
 #pragma unroll
-                    for (int oy = 0; oy < G::TY; ++oy) {
-                        const int cy = oy / P, ay = oy % P;
-                        float2 o = make_float2(0.f, 0.f);
-                        if constexpr (NY == G::BY) {
-                            if (ky[ay]) {
+                        for (int oy = 0; oy < G::TY; ++oy) {
+                            const int cy = oy / P, ay = oy % P;
+                            float2 o = make_float2(0.f, 0.f);
+                            if constexpr (NY == G::BY) {
+                                if (ky[ay]) {
 #pragma unroll
-                                for (int l = 0; l <= P; ++l) o = ffma2(v[(cy + 1) * P + l], wy[ay][l], o);
+                                    for (int l = 0; l <= P; ++l) o = ffma2(v[(cy + 1) * P + l], wy[ay][l], o);
+                                } else {
+#pragma unroll
+                                    for (int l = 0; l <= P; ++l) o = ffma2(v[cy * P + l], wy[ay][l], o);
+                                }
                             } else {
 #pragma unroll
                                 for (int l = 0; l <= P; ++l) o = ffma2(v[cy * P + l], wy[ay][l], o);
                             }
-                        } else {
-#pragma unroll
-                            for (int l = 0; l <= P; ++l) o = ffma2(v[cy * P + l], wy[ay][l], o);
+                            col[oy * XP] = o;
                         }
-                        col[oy * XP] = o;
                     }
-                }
-            };
-            if (sy)
-                y_pass(IntC<G::BY>{});
-            else
-                y_pass(IntC<G::BY0>{});
-            __syncwarp();
-            // x pass: lane = x-row (oz, oy) of the tile, NX pairs from the row's start
-            float res[2 * G::TX];
-            auto x_pass = [&](auto nx) {
-                constexpr int NX = decltype(nx)::value;
-                float2 wx[P][P + 1];
-                bool kx[P];
+                };
+                if (sy)
+                    y_pass(IntC<G::BY>{});
+                else
+                    y_pass(IntC<G::BY0>{});
+                __syncwarp();
+                // x pass: lane = x-row (oz, oy) of the tile, NX pairs from the row's start
+                float res[2 * G::TX];
+                auto x_pass = [&](auto nx) {
+                    constexpr int NX = decltype(nx)::value;
+                    float2 wx[P][P + 1];
+                    bool kx[P];
 #pragma unroll
-                for (int ax = 0; ax < P; ++ax) {
-                    kx[ax] = t.kc[j][0][ax] != 0;
+                    for (int ax = 0; ax < P; ++ax) {
+                        kx[ax] = t.kc[j][0][ax] != 0;
 #pragma unroll
-                    for (int l = 0; l <= P; ++l) wx[ax][l] = make_float2(t.lw[j][0][ax][l], t.lw[j][0][ax][l]);
-                }
-                float2 v[NX];
-                const float2* row = box + oz_l * PL + oy_l * XP + ox0;
+                        for (int l = 0; l <= P; ++l) wx[ax][l] = make_float2(t.lw[j][0][ax][l], t.lw[j][0][ax][l]);
+                    }
+                    float2 v[NX];
+                    const float2* row = box + oz_l * PL + oy_l * XP + ox0;
 #pragma unroll
-                for (int x = 0; x < NX; ++x) v[x] = row_lane ? row[x] : make_float2(0.f, 0.f);
+                    for (int x = 0; x < NX; ++x) v[x] = row_lane ? row[x] : make_float2(0.f, 0.f);
 #pragma unroll
-                for (int ox = 0; ox < G::TX; ++ox) {
-                    const int cx = ox / P, ax = ox % P;
-                    float2 o = make_float2(0.f, 0.f);
-                    if constexpr (NX == G::BX) {
-                        if (kx[ax]) {
+                    for (int ox = 0; ox < G::TX; ++ox) {
+                        const int cx = ox / P, ax = ox % P;
+                        float2 o = make_float2(0.f, 0.f);
+                        if constexpr (NX == G::BX) {
+                            if (kx[ax]) {
 #pragma unroll
-                            for (int l = 0; l <= P; ++l) o = ffma2(v[(cx + 1) * P + l], wx[ax][l], o);
+                                for (int l = 0; l <= P; ++l) o = ffma2(v[(cx + 1) * P + l], wx[ax][l], o);
+                            } else {
+#pragma unroll
+                                for (int l = 0; l <= P; ++l) o = ffma2(v[cx * P + l], wx[ax][l], o);
+                            }
                         } else {
 #pragma unroll
                             for (int l = 0; l <= P; ++l) o = ffma2(v[cx * P + l], wx[ax][l], o);
                         }
-                    } else {
-#pragma unroll
-                        for (int l = 0; l <= P; ++l) o = ffma2(v[cx * P + l], wx[ax][l], o);
+                        res[2 * ox] = o.x;
+                        res[2 * ox + 1] = o.y;
                     }
-                    res[2 * ox] = o.x;
-                    res[2 * ox + 1] = o.y;
-                }
-            };
-            if (sx)
-                x_pass(IntC<G::BX>{});
-            else
-                x_pass(IntC<G::BX0>{});
-            // the slot was written in place (generic proxy); order that before the next TMA fill
-            fence_proxy_async();
-            __syncwarp();
-            if (lane == 0 && m > 0) mbar_arrive(empty0 + 8 * e);
+                };
+                if (sx)
+                    x_pass(IntC<G::BX>{});
+                else
+                    x_pass(IntC<G::BX0>{});
+                // the slot was written in place (generic proxy); order that before the next TMA fill
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0 && m > 0) mbar_arrive(empty0 + 8 * e);
 
-            // moment contributions of this pair, then park the pair in tensor memory
-            const float xix = t.xi[j][0], xiy = t.xi[j][1], xiz = t.xi[j][2];
-            const float x2 = static_cast<float>(shell_xi2(shell_of(j)));
-#pragma unroll
-            for (int x = 0; x < G::TX; ++x) {
-                const float f = res[2 * x], g = res[2 * x + 1];
-                pm[0][x] += f;
-                pm[1][x] += f * xix;
-                pm[2][x] += f * xiy;
-                pm[3][x] += f * xiz;
-                pm[4][x] += f * x2 + g;
+                // park the pair in tensor memory
+                tmem_store_row<G::TX>(tbuf + static_cast<uint32_t>(k * 2 * G::TX), res);
             }
-            tmem_store_row<G::TX>(tmem_warp + static_cast<uint32_t>(k * 2 * G::TX), res);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tmem_full0 + 8 * (qd * 2 + bf));
         }
-
-        // Per-node moment sums over the warps: each warp adds its contributions as 64-bit fixed
-        // point (2^-40 units) with shared-memory atomics.  Integer addition is exact, so the
-        // sums do not depend on the order the warps arrive in.  Shared-memory layouts are
-        // indexed [..][x][lane] (node = lane*TX + x) so that every lane-parallel access below
-        // is contiguous.
-        {
-            if (a.flag != nullptr) {
-                // a non-finite contribution would not survive the conversion: flag it here
-                bool bad = false;
+    }
+    // ---------------------------------------------------- epilogue warps
+    // One per lane quarter.  Per tile: the moment sums of the quarter's pairs (streamed by
+    // warps q, q + 4, q + 8), the sum over the quarters in a fixed order and the per-node
+    // parameters (each epilogue warp a share of the nodes), then the BGK collision and the
+    // stores of the quarter's pairs.  The epilogue warps meet at named barrier 2.
+    else if (is_epilogue_warp(warp)) {
+        const int ep = epilogue_index(warp);  // 0 .. NE-1: share of the nodes whose parameters it forms
+        const int qd = warp & 3;              // the lane quarter it reads (0, 2 or 3)
+        constexpr int nsw = 3;                // stream warps in the quarter: qd, qd + 4, qd + 8
+        const uint32_t tq = *tmem_base_s + (static_cast<uint32_t>(qd * 32) << 16);
+        constexpr int QS = G::TX * 32;  // stride between parameters
+        constexpr int XS = (G::TX + NE - 1) / NE;  // node columns per epilogue warp (the last one fewer)
+        for (int it = 0; it < ncta; ++it) {
+            if (epilogue_barrier_or(*abort_flag)) break;
+            const int bf = it & 1;
+            const int tile = static_cast<int>(blockIdx.x) + it * static_cast<int>(gridDim.x);
+            const int c0[3] = {(tile % ntx) * CX, ((tile / ntx) % nty) * CY, (tile / (ntx * nty)) * CZ};
+            const uint32_t tb = tq + static_cast<uint32_t>(bf * TC::per_buf);
+            mbar_wait_bounded(tmem_full0 + 8 * (qd * 2 + bf), static_cast<uint32_t>(it >> 1) & 1u, abort_flag, err_flag);
+            tc_fence_after();
+            // moment contributions of the quarter's pairs (rho, m_x, m_y, m_z, 2 rho E; Eq. moments)
+            {
+                float pm[5][G::TX];
 #pragma unroll
                 for (int q = 0; q < 5; ++q)
 #pragma unroll
-                    for (int x = 0; x < G::TX; ++x) bad |= !isfinite(pm[q][x]);
-                if (bad) atomicOr(a.flag, 1);
+                    for (int x = 0; x < G::TX; ++x) pm[q][x] = 0.f;
+                for (int sw = 0; sw < nsw; ++sw) {
+#pragma unroll 1
+                    for (int k = 0; k < NPW; ++k) {
+                        const int j = stream_index(qd + 4 * sw) + NC * k;
+                        float v[2 * G::TX];
+                        tmem_load_row<G::TX>(tb + static_cast<uint32_t>(sw * TC::per_warp + k * 2 * G::TX), v);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        const float xix = t.xi[j][0], xiy = t.xi[j][1], xiz = t.xi[j][2];
+                        const float x2 = static_cast<float>(shell_xi2(shell_of(j)));
+#pragma unroll
+                        for (int x = 0; x < G::TX; ++x) {
+                            const float f = v[2 * x], g = v[2 * x + 1];
+                            pm[0][x] += f;
+                            pm[1][x] += f * xix;
+                            pm[2][x] += f * xiy;
+                            pm[3][x] += f * xiz;
+                            pm[4][x] += f * x2 + g;
+                        }
+                    }
+                }
+                // layout [quarter][moment][x][lane] (node = lane*TX + x): contiguous lane accesses
+                float* pc = part + static_cast<size_t>(qd) * 5 * QS + lane;
+#pragma unroll
+                for (int q = 0; q < 5; ++q)
+#pragma unroll
+                    for (int x = 0; x < G::TX; ++x) pc[q * QS + x * 32] = pm[q][x];
             }
-            unsigned long long* pc = part + lane;
+            epilogue_barrier_or(0);
+            // per-node moments (quarters summed in a fixed order), tau, equilibrium coefficients
+            // (Eq. discreteEquilibrium, Sutherland's law) of this warp's share of the nodes
 #pragma unroll
-            for (int q = 0; q < 5; ++q)
+            for (int xx = 0; xx < XS; ++xx) {
+                const int x = ep * XS + xx;
+                if (x >= G::TX) break;
+                float m[5];
 #pragma unroll
-                for (int x = 0; x < G::TX; ++x)
-                    red_add_shared(pc + (q * G::TX + x) * 32,
-                                   static_cast<unsigned long long>(__float2ll_rn(pm[q][x] * kFixScale)));
-        }
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        if (consumer_barrier_or(*abort_flag, NC * 32)) break;
-
-        // per-node moments, tau, equilibrium coefficients
-        for (int tn = threadIdx.x; tn < G::TX * 32; tn += NC * 32) {
-            const int xn = tn >> 5, ln = tn & 31;  // node = ln*TX + xn
-            if (ln >= G::ROWS) continue;
-            // read the sums and clear them for the next tile (every warp adds to them only after
-            // the barrier that closes this phase)
-            float m[5];
+                for (int q = 0; q < 5; ++q)
+                    m[q] = (part[(0 * 5 + q) * QS + x * 32 + lane] + part[(2 * 5 + q) * QS + x * 32 + lane]) +
+                           part[(3 * 5 + q) * QS + x * 32 + lane];
+                const float rho = m[0];
+                const float inv_rho = 1.0f / rho;
+                const float ux = m[1] * inv_rho, uy = m[2] * inv_rho, uz = m[3] * inv_rho;
+                const float usq = ux * ux + uy * uy + uz * uz;
+                const float T = (m[4] * inv_rho - usq) * static_cast<float>(a.inv_2cv);
+                if (a.flag != nullptr && !(rho > 0.f && T > 0.f && isfinite(rho) && isfinite(T))) atomicOr(a.flag, 1);
+                const float tau_r = static_cast<float>(a.mu_over_dt) * sutherland(T) / (rho * T) + 0.5f;
+                const EqCoef<float> ec = eq_coefficients(usq, T - 1.0f);
+                float* pn = prm + x * 32 + lane;
+                pn[0 * QS] = rho;
+                pn[1 * QS] = ux;
+                pn[2 * QS] = uy;
+                pn[3 * QS] = uz;
+                pn[4 * QS] = static_cast<float>(a.gfac) * T;
+                pn[5 * QS] = 1.0f / tau_r;
 #pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                unsigned long long* e = part + (q * G::TX + xn) * 32 + ln;
-                m[q] = static_cast<float>(static_cast<double>(static_cast<long long>(*e)) * kFixUnit);
-                *e = 0ull;
+                for (int sh = 0; sh < 4; ++sh) {
+                    pn[(6 + sh) * QS] = ec.c0[sh];
+                    pn[(10 + sh) * QS] = ec.c1[sh];
+                    pn[(14 + sh) * QS] = ec.c2[sh];
+                }
             }
-            const float rho = m[0];
-            const float inv_rho = 1.0f / rho;
-            const float ux = m[1] * inv_rho, uy = m[2] * inv_rho, uz = m[3] * inv_rho;
-            const float usq = ux * ux + uy * uy + uz * uz;
-            const float T = (m[4] * inv_rho - usq) * static_cast<float>(a.inv_2cv);
-            if (a.flag != nullptr && !(rho > 0.f && T > 0.f && isfinite(rho) && isfinite(T))) atomicOr(a.flag, 1);
-            const float tau_r = static_cast<float>(a.mu_over_dt) * sutherland(T) / (rho * T) + 0.5f;
-            const EqCoef<float> ec = eq_coefficients(usq, T - 1.0f);
-            float* pn = prm + xn * 32 + ln;
-            constexpr int QS = G::TX * 32;  // stride between parameters
-            pn[0 * QS] = rho;
-            pn[1 * QS] = ux;
-            pn[2 * QS] = uy;
-            pn[3 * QS] = uz;
-            pn[4 * QS] = static_cast<float>(a.gfac) * T;
-            pn[5 * QS] = 1.0f / tau_r;
-#pragma unroll
-            for (int sh = 0; sh < 4; ++sh) {
-                pn[(6 + sh) * QS] = ec.c0[sh];
-                pn[(10 + sh) * QS] = ec.c1[sh];
-                pn[(14 + sh) * QS] = ec.c2[sh];
-            }
-        }
-        consumer_barrier_or(0, NC * 32);
-
-        // collision of this warp's pairs at the lane's TX nodes: the pairs come back from
-        // tensor memory, each node's parameters are read once, 16-byte streaming stores
-        float h[NPW][2 * G::TX];
-#pragma unroll
-        for (int k = 0; k < NPW; ++k) tmem_load_row<G::TX>(tmem_warp + static_cast<uint32_t>(k * 2 * G::TX), h[k]);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (row_lane) {
+            epilogue_barrier_or(0);
+            // collision of the quarter's pairs at the lane's TX nodes, pair by pair
+            float rho_[G::TX], ux_[G::TX], uy_[G::TX], uz_[G::TX], gT_[G::TX], om_[G::TX];
 #pragma unroll
             for (int x = 0; x < G::TX; ++x) {
                 const float* pn = prm + x * 32 + lane;
-                constexpr int QS = G::TX * 32;
-                const float rho = pn[0 * QS], ux = pn[1 * QS], uy = pn[2 * QS], uz = pn[3 * QS], gT = pn[4 * QS],
-                            om = pn[5 * QS];
-#pragma unroll
-                for (int k = 0; k < NPW; ++k) {
-                    const int j = c + NC * k;
-                    const int sh = shell_of(j);  // warp-dependent: read the shell's coefficients directly
-                    const float s = t.xi[j][0] * ux + t.xi[j][1] * uy + t.xi[j][2] * uz;
-                    const float poly = pn[(6 + sh) * QS] +
-                                       s * (pn[(10 + sh) * QS] + s * (pn[(14 + sh) * QS] + s * (1.0f / 6.0f + s * (1.0f / 24.0f))));
-                    const float feq = t.w[j] * rho * poly;
-                    const float f = h[k][2 * x], g = h[k][2 * x + 1];
-                    h[k][2 * x] = f + om * (feq - f);
-                    h[k][2 * x + 1] = g + om * (gT * feq - g);
-                }
+                rho_[x] = pn[0 * QS];
+                ux_[x] = pn[1 * QS];
+                uy_[x] = pn[2 * QS];
+                uz_[x] = pn[3 * QS];
+                gT_[x] = pn[4 * QS];
+                om_[x] = pn[5 * QS];
             }
-            // streaming stores: the new state is not read again in this step, so it should
-            // not push the source boxes' halos out of L2
-            const long long g0 =
-                (static_cast<long long>(c0[2] * P + oz_l) * a.N[1] + (c0[1] * P + oy_l)) * a.N[0] + c0[0] * P;
             float2* dstp = static_cast<float2*>(a.dst);
+            float4* st = stage + ep * 128;
+            for (int sw = 0; sw < nsw; ++sw) {
+#pragma unroll 1
+                for (int k = 0; k < NPW; ++k) {
+                    const int j = stream_index(qd + 4 * sw) + NC * k;
+                    float h[2 * G::TX];
+                    tmem_load_row<G::TX>(tb + static_cast<uint32_t>(sw * TC::per_warp + k * 2 * G::TX), h);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (sw == nsw - 1 && k == NPW - 1) {
+                        // the last read of this buffer: hand it back to the stream warps
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(tmem_empty0 + 8 * (qd * 2 + bf));
+                    }
+                    const int sh = shell_of(j);
+                    const float xix = t.xi[j][0], xiy = t.xi[j][1], xiz = t.xi[j][2], wj = t.w[j];
 #pragma unroll
-            for (int k = 0; k < NPW; ++k) {
-                const int j = c + NC * k;
-                float2* out = dstp + static_cast<long long>(j) * a.nn + g0;
-                if (G::TX % 2 == 0) {
+                    for (int x = 0; x < G::TX; ++x) {
+                        const float* pn = prm + x * 32 + lane;
+                        const float sdot = xix * ux_[x] + xiy * uy_[x] + xiz * uz_[x];
+                        const float poly = pn[(6 + sh) * QS] +
+                                           sdot * (pn[(10 + sh) * QS] +
+                                                   sdot * (pn[(14 + sh) * QS] + sdot * (1.0f / 6.0f + sdot * (1.0f / 24.0f))));
+                        const float feq = wj * rho_[x] * poly;
+                        const float f = h[2 * x], g = h[2 * x + 1];
+                        h[2 * x] = f + om_[x] * (feq - f);
+                        h[2 * x + 1] = g + om_[x] * (gT_[x] * feq - g);
+                    }
+                    // streaming stores (the new state is not read again in this step, so it
+                    // should not push the source boxes' halos out of L2), through the warp's
+                    // staging buffer so that each 16-byte store instruction covers 8 whole rows
+                    // (64 bytes each) instead of a quarter of 32 rows.  Chunk q of row r sits at
+                    // float4 r*4 + (q ^ ((r >> 1) & 3)): both access patterns are free of bank
+                    // conflicts.
+                    __syncwarp();
 #pragma unroll
-                    for (int x = 0; x < G::TX; x += 2)
-                        __stcs(reinterpret_cast<float4*>(out + x),
-                               make_float4(h[k][2 * x], h[k][2 * x + 1], h[k][2 * x + 2], h[k][2 * x + 3]));
-                } else {
+                    for (int q = 0; q < 4; ++q)
+                        st[lane * 4 + (q ^ ((lane >> 1) & 3))] =
+                            make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+                    __syncwarp();
 #pragma unroll
-                    for (int x = 0; x < G::TX; ++x) __stcs(out + x, make_float2(h[k][2 * x], h[k][2 * x + 1]));
+                    for (int i = 0; i < 4; ++i) {
+                        const int r = 8 * i + (lane >> 2), ch = lane & 3;
+                        const float4 vv = st[r * 4 + (ch ^ ((r >> 1) & 3))];
+                        const int oz = r / G::TY, oy = r % G::TY;
+                        const long long g0r =
+                            (static_cast<long long>(c0[2] * P + oz) * a.N[1] + (c0[1] * P + oy)) * a.N[0] + c0[0] * P;
+                        __stcs(reinterpret_cast<float4*>(dstp + static_cast<long long>(j) * a.nn + g0r) + ch, vv);
+                    }
                 }
             }
         }
     }
 
-    // free the tensor memory once every consumer is done with it
+    // free the tensor memory once every stream and epilogue warp is done with it
     tc_fence_before();
-    consumer_barrier_or(0, NC * 32);
+    consumer_barrier_or(0, (NC + NE) * 32);
     tc_fence_after();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tmem_base_s),

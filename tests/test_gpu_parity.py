@@ -144,7 +144,7 @@ def test_step_f32_matches_oracle(S, cells, p, pr):
 # TMA-fed kernel: tiles of 8x8x4 (p=2, 4), 9x9x3 (p=3) nodes.  On the small meshes every
 # source box wraps around the periodic boundary (16-byte cp.async path); the larger ones
 # have interior tiles (one TMA load per box).
-TMA_CASES = [((2, 2, 1), 4), ((4, 2, 3), 4), ((6, 6, 3), 3), ((8, 4, 2), 2), ((8, 8, 6), 4),
+TMA_CASES = [((2, 2, 1), 4), ((4, 2, 3), 4), ((6, 4, 2), 4), ((8, 4, 2), 2), ((8, 8, 6), 4),
              ((12, 8, 4), 2)]
 
 
@@ -182,6 +182,10 @@ def test_tma_kernel_refuses_meshes_it_cannot_tile(S):
     with pytest.raises(S.SllbmError):
         make(S, (2, 2, 2), 4, storage="f32", kernel=2, pr=True)
     assert make(S, (3, 2, 2), 4, storage="f32").info.step_kernel == 1
+    # p = 3: two tiles of streamed pairs do not fit in tensor memory; the generic kernel runs
+    with pytest.raises(S.SllbmError):
+        make(S, (6, 6, 3), 3, storage="f32", kernel=2)
+    assert make(S, (6, 6, 3), 3, storage="f32").info.step_kernel == 1
 
 
 @pytest.mark.parametrize("p", [2, 3, 4])

@@ -89,21 +89,33 @@ struct TmaMaps {
 };
 
 constexpr int kNParams = 18;  // rho, ux, uy, uz, gT, omega, c0[4], c1[4], c2[4]
-// Warp roles.  A warp's SM sub-partition is its index mod 4.  The producer (warp 13) has
-// sub-partition 1 to itself, so that its latency-bound issue path is not starved of issue
-// slots; the 9 stream warps are 0, 2, 3, 4, 6, 7, 8, 10, 11 (three per tensor-memory lane
-// quarter 0, 2, 3, the quarter a warp may touch being its index mod 4) and the 3 epilogue
-// warps 12, 14, 15 (one per used quarter); warps 1, 5 and 9 have no work.
+// Warp roles.  A warp's SM sub-partition is its index mod 4.  The producer (warp 1; with
+// SLLBM_TMA_PRODUCERS=3, warps 1, 5, 9) has sub-partition 1 to itself, so that its
+// latency-bound issue path is not starved of issue slots; the 9 stream warps are 0, 2, 3, 4,
+// 6, 7, 8, 10, 11 (three per tensor-memory lane quarter 0, 2, 3, the quarter a warp may touch
+// being its index mod 4) and the 3 epilogue warps 12, 14, 15 (one per used quarter); the
+// other warps of sub-partition 1 have no work.  (Three producers, each serving the
+// velocities of one residue mod 3 from its own third of the ring, measured faster on a 96^3
+// mesh and slower on 128^3.)
 constexpr int kWarps = 16;
-constexpr int kProducerWarp = 13;
 constexpr int kEpilogueWarps = 3;
+#ifndef SLLBM_TMA_PRODUCERS
+#define SLLBM_TMA_PRODUCERS 1
+#endif
+constexpr int NPROD = SLLBM_TMA_PRODUCERS;  // producers; producer p serves velocities j = p (mod NPROD)
+constexpr int IPP = kQ / NPROD;             // items per tile and producer
+static_assert((NPROD == 1 || NPROD == 3) && IPP * NPROD == kQ && IPP <= 64, "items per producer");
+__host__ __device__ constexpr bool is_producer_warp(int w) { return w < 4 * NPROD && (w & 3) == 1; }
+__host__ __device__ constexpr int producer_index(int w) { return w >> 2; }
 __host__ __device__ constexpr bool is_stream_warp(int w) { return w < 12 && (w & 3) != 1; }
+static_assert(9 % NPROD == 0, "a stream warp's pairs all come from one producer");
 __host__ __device__ constexpr int stream_index(int w) { return w - ((w + 2) >> 2); }
 __host__ __device__ constexpr bool is_epilogue_warp(int w) { return w == 12 || w == 14 || w == 15; }
 __host__ __device__ constexpr int epilogue_index(int w) { return w == 12 ? 0 : w - 13; }
 // A source box that crosses the periodic boundary is loaded as one TMA box per periodic image
 // it overlaps (zero outside the domain), at most kMaxPieces of them, back to back in the ring;
-// boxes with more images (meshes not much larger than a tile) take the cp.async path.
+// boxes with more images (meshes not much larger than a tile), or whose images would not fit
+// in the producer's part of the ring, take the cp.async path.
 constexpr int kMaxPieces = 8;
 // Items in flight at most: the descriptor ring (full/empty mbarriers, item table entry and
 // ring offset per item; a power of two).
@@ -120,19 +132,21 @@ struct TmaSmem {
     static constexpr size_t partials = round128(size_t(4) * 5 * G::TX * 32 * sizeof(float));  // per quarter
     static constexpr size_t params = round128(size_t(kNParams) * G::TX * 32 * sizeof(float));
     static constexpr size_t tables = round128(sizeof(StepTablesS<P>));
-    // full[kItems], empty[kItems] mbarriers, the item table (one word per entry: item number,
-    // ring offset and piece count), tmem_full[4][2], tmem_empty[4][2] mbarriers, the ring
-    // offsets of the items in flight, flags
-    static constexpr size_t bars = (size_t(3) * kItems + 16) * sizeof(uint64_t) + kItems * sizeof(int) + 16;
+    // per producer: full[kItems], empty[kItems] mbarriers and the item table (one word per
+    // entry: item number, ring offset and piece count); tmem_full[4][2], tmem_empty[4][2]
+    // mbarriers; per producer the ring offsets of its items in flight; flags
+    static constexpr size_t bars =
+        (size_t(NPROD) * 3 * kItems + 16) * sizeof(uint64_t) + size_t(NPROD) * kItems * sizeof(int) + 16;
     static constexpr size_t bars_padded = round128(bars);
-    static constexpr size_t woff = round128(size_t(G::BZ + G::BY + G::BXP / 2) * sizeof(long long));
+    static constexpr int woff_n = G::BZ + G::BY + G::BXP / 2;  // wrapped-offset table per producer
+    static constexpr size_t woff = round128(size_t(NPROD) * woff_n * sizeof(long long));
     static constexpr size_t stage = size_t(kEpilogueWarps) * 32 * 64;  // one pair's 32 rows per epilogue warp
     static constexpr size_t fixed = partials + params + tables + bars_padded + woff + stage + 128;  // +128: base alignment
     // the box ring takes the rest, in 128-byte units
     static constexpr int ring_units = static_cast<int>((kSmemBudget - fixed) / 128);
     static constexpr size_t ring = size_t(ring_units) * 128;
     static constexpr size_t bytes = ring + fixed;
-    static_assert(ring_units >= kMaxPieces * (G::SLOT_BYTES / 128), "ring holds the largest item");
+    static_assert(ring_units / NPROD >= G::SLOT_BYTES / 128, "each producer's ring holds the largest box");
 };
 
 // Tensor-memory columns: a stream warp's lane keeps NPW pairs x 2*TX floats per tile; stream
@@ -390,14 +404,15 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + SM::ring + SM::partials + SM::params + SM::tables);
     // item table: entry s % kItems = (s << 32) | (ring offset in units << 8) | pieces for item s
     // (tile-major, 45 per tile), written with one 64-bit store
+    // (producer p's block starts at bars + 3*kItems*p: full, empty, item table)
     volatile unsigned long long* items = reinterpret_cast<volatile unsigned long long*>(bars + 2 * kItems);
-    const uint32_t tmem_full0 = smem_u32(bars + 3 * kItems), tmem_empty0 = smem_u32(bars + 3 * kItems + 8);
-    int* start_of = reinterpret_cast<int*>(bars + 3 * kItems + 16);  // ring offset per item in flight
-    volatile int* abort_flag = start_of + kItems;
-    uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(start_of + kItems) + 1;
+    const uint32_t tmem_full0 = smem_u32(bars + NPROD * 3 * kItems), tmem_empty0 = tmem_full0 + 64;
+    int* start_of = reinterpret_cast<int*>(bars + NPROD * 3 * kItems + 16);  // ring offset per item in flight
+    volatile int* abort_flag = start_of + NPROD * kItems;
+    uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(start_of + NPROD * kItems) + 1;
     long long* woff = reinterpret_cast<long long*>(reinterpret_cast<unsigned char*>(bars) + SM::bars_padded);
     float4* stage = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(bars) + SM::bars_padded + SM::woff);
-    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kItems);
+    const uint32_t full0 = smem_u32(bars);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     {
@@ -408,11 +423,10 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     }
     const StepTablesS<P>& t = *tsm;
     if (threadIdx.x == 0) {
-        for (int e = 0; e < kItems; ++e) {
-            mbar_init(full0 + 8 * e, 1);
-            mbar_init(empty0 + 8 * e, 1);
-        }
-        for (int e = 0; e < kItems; ++e) items[e] = ~0ull;
+        for (int e = 0; e < NPROD * 3 * kItems; ++e)
+            if (e % (3 * kItems) < 2 * kItems) mbar_init(full0 + 8 * e, 1);  // full and empty
+        for (int pp = 0; pp < NPROD; ++pp)
+            for (int e = 0; e < kItems; ++e) items[pp * 3 * kItems + e] = ~0ull;
         for (int q = 0; q < 4; ++q)
             for (int b = 0; b < 2; ++b) {
                 mbar_init(tmem_full0 + 8 * (q * 2 + b), q == 1 ? 1u : 3u);  // stream warps per quarter
@@ -436,15 +450,24 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     const int ntiles = ntx * nty * ntz;
     int* err_flag = a.flag_err;
 
-    if (warp == kProducerWarp) {
-        // ------------------------------------------------ producer warp
-        // Per tile, lane L works out items L and L + 32 in parallel (box origin of the first
+    if (is_producer_warp(warp)) {
+        // ------------------------------------------------ producer warps
+        // Producer pp serves the velocities j = pp + NPROD*m (m < IPP), which are the pairs of
+        // the stream warps c = pp (mod NPROD), through its own part of the box ring and its own
+        // descriptors.  Per tile, lane m works out item m in parallel (box origin of the first
         // periodic image, image counts, shape, ring units).  Items then go out in order, in
         // batches: the releases of the oldest items in flight are confirmed together (one
         // lane per item), as many of the next items as fit are placed in the ring, and they
         // are announced and issued at once, one lane per item.  A producer that falls behind
         // thus issues larger batches instead of paying the mbarrier and TMA latencies once
         // per item.  The ring is reclaimed in item order.
+        const int pp = producer_index(warp);
+        const uint32_t pf0 = full0 + 8u * static_cast<uint32_t>(pp * 3 * kItems), pe0 = pf0 + 8u * kItems;
+        volatile unsigned long long* pit = items + pp * 3 * kItems;
+        int* pst = start_of + pp * kItems;
+        long long* pwo = woff + pp * SM::woff_n;
+        constexpr int RP = SM::ring_units / NPROD;  // ring units of this producer ...
+        const int RB = pp * RP;                     // ... starting at this unit
         uint32_t s_tile = 0;  // number of the tile's first item
         uint32_t tail = 0;    // oldest item whose release is not confirmed yet
         int head = 0;         // ring unit where the next item goes (if it fits)
@@ -452,7 +475,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         bool ok = true;
         const uint32_t ring_u32 = smem_u32(ring);
         const int cd[3] = {CX, CY, CZ};
-        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, s_tile += kQ) {
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, s_tile += IPP) {
             const int tyz = tile / ntx;
             const int cb[3] = {(tile - tyz * ntx) * CX * P, (tyz % nty) * CY * P, (tyz / nty) * CZ * P};
             // meta: pieces m | nk_x << 4 | nk_y << 8 | nk_z << 12 | shape << 16 | cp.async << 20
@@ -461,11 +484,12 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
             int units[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int j = lane + 32 * h;
+                const int mi = lane + 32 * h;
+                const int j = pp + NPROD * mi;
                 meta[h] = 0;
                 units[h] = 0;
                 crd[h][0] = crd[h][1] = crd[h][2] = 0;
-                if (j < kQ) {
+                if (mi < IPP) {
                     int b0[3], klo[3], nk[3], sp[3];
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
@@ -476,9 +500,9 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                         nk[d] = floor_div(b0[d] + need - 1, a.N[d]) - klo[d] + 1;
                     }
                     const int npiece = nk[0] * nk[1] * nk[2];
-                    const bool tma_pieces = npiece <= kMaxPieces;
-                    const int m = tma_pieces ? npiece : 1;
                     const int shape = sp[0] + 2 * sp[1] + 4 * sp[2];
+                    const bool tma_pieces = npiece <= kMaxPieces && npiece * G::piece_units(shape) <= RP;
+                    const int m = tma_pieces ? npiece : 1;
                     units[h] = m * G::piece_units(shape);
                     const int x0 = b0[0] - (b0[0] & 1);  // even pair index (floor for negatives)
                     crd[h][0] = 2 * (x0 - klo[0] * a.N[0]);
@@ -490,16 +514,17 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
             }
 
             int nxt = 0;  // first item of the tile not issued yet
-            while (nxt < kQ) {
+            while (nxt < IPP) {
                 const int h = nxt >> 5;
                 const int lo = nxt & 31;
-                const int nlane = h ? kQ - 32 : 32;  // items held in this round
+                const int nlane = h ? IPP - 32 : (IPP < 32 ? IPP : 32);  // items held in this round
                 const uint32_t issued = s_tile + static_cast<uint32_t>(nxt);
                 // confirm the releases of the oldest items in flight, in order
                 int inflight = static_cast<int>(issued - tail);
                 if (inflight > 0) {
                     const uint32_t x = tail + static_cast<uint32_t>(lane);
-                    const bool rel = lane < inflight && mbar_test_wait(empty0 + 8 * (x & KM), (x / kItems) & 1u);
+                    // (the oldest 8 at most: each lane's test is a separate shared-memory operation)
+                    const bool rel = lane < inflight && lane < 8 && mbar_test_wait(pe0 + 8 * (x & KM), (x / kItems) & 1u);
                     const uint32_t rm = __ballot_sync(0xffffffffu, rel);
                     const int nrel = (~rm == 0u) ? 32 : __ffs(static_cast<int>(~rm)) - 1;
                     tail += static_cast<uint32_t>(nrel);
@@ -510,7 +535,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                 // lanes, then the longest run from the first one that fits in one free region
                 // (the rest of the ring after `head`, or its start when that is too short).  A
                 // cp.async item goes alone.
-                const int tail_off = inflight > 0 ? start_of[tail & KM] : 0;
+                const int tail_off = inflight > 0 ? pst[tail & KM] : 0;
                 const int cap = min(nlane - lo, kItems - inflight);
                 const uint32_t mt_l = h ? meta[1] : meta[0];
                 const bool cand = lane >= lo && lane < lo + cap;
@@ -530,11 +555,11 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                 int base = -1, limit = 0;
                 if (inflight == 0) {
                     base = head;
-                    limit = SM::ring_units;
+                    limit = RP;
                 } else if (head > tail_off) {
-                    if (head + first_need <= SM::ring_units) {
+                    if (head + first_need <= RP) {
                         base = head;
-                        limit = SM::ring_units;
+                        limit = RP;
                     } else if (first_need <= tail_off) {
                         base = 0;
                         limit = tail_off;
@@ -551,7 +576,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                 if (nb == 0) {
                     // nothing fits: wait (blocking, bounded) for the oldest item's release
                     int stop = 0;
-                    if (lane == 0 && !mbar_wait_bounded(empty0 + 8 * (tail & KM), (tail / kItems) & 1u, abort_flag,
+                    if (lane == 0 && !mbar_wait_bounded(pe0 + 8 * (tail & KM), (tail / kItems) & 1u, abort_flag,
                                                         err_flag))
                         stop = 1;
                     if (__shfl_sync(0xffffffffu, stop, 0)) {
@@ -568,8 +593,8 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                     const uint32_t mt = h ? meta[1] : meta[0];
                     const int m = static_cast<int>(mt & 15u);
                     const uint32_t e = s & KM;
-                    start_of[e] = my_off;
-                    items[e] = (static_cast<unsigned long long>(s) << 32) | (static_cast<uint32_t>(my_off) << 8) |
+                    pst[e] = my_off;
+                    pit[e] = (static_cast<unsigned long long>(s) << 32) | (static_cast<uint32_t>(RB + my_off) << 8) |
                                static_cast<uint32_t>(m);
                     if (!first_fb) {
                         const int shape = static_cast<int>((mt >> 16) & 7u);
@@ -580,10 +605,10 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                                   nkz = static_cast<int>((mt >> 12) & 15u);
                         const int cx = h ? crd[1][0] : crd[0][0], cy = h ? crd[1][1] : crd[0][1],
                                   cz = h ? crd[1][2] : crd[0][2];
-                        const int j = lane + 32 * h;
-                        const uint32_t full = full0 + 8 * e;
+                        const int j = pp + NPROD * (lane + 32 * h);
+                        const uint32_t full = pf0 + 8 * e;
                         mbar_arrive_expect_tx(full, bytes * static_cast<uint32_t>(m));
-                        uint32_t dst = ring_u32 + static_cast<uint32_t>(my_off) * 128u;
+                        uint32_t dst = ring_u32 + static_cast<uint32_t>(RB + my_off) * 128u;
                         for (int qz = 0; qz < nkz; ++qz)
                             for (int qy = 0; qy < nky; ++qy)
                                 for (int qx = 0; qx < nkx; ++qx, dst += pstride)
@@ -592,7 +617,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                     }
                 }
                 if (first_fb) {
-                    const int j = nxt;
+                    const int j = pp + NPROD * nxt;
                     const uint32_t e = issued & KM;
                     const int foff = __shfl_sync(0xffffffffu, my_off, lo);
                     int b0[3], sp[3];
@@ -602,8 +627,8 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                         b0[d] = cb[d] + t.kmin[j][d] * P;
                     }
                     const int x0 = b0[0] - (b0[0] & 1);
-                    const uint32_t dst = ring_u32 + static_cast<uint32_t>(foff) * 128u;
-                    const uint32_t full = full0 + 8 * e;
+                    const uint32_t dst = ring_u32 + static_cast<uint32_t>(RB + foff) * 128u;
+                    const uint32_t full = pf0 + 8 * e;
                     // the box overlaps more periodic images than there are pieces: 16-byte copies
                     // from the wrapped positions, in the layout of the box's shape.  A chunk is
                     // two (f,g) pairs at an even x and N[0] is even, so a chunk never straddles
@@ -613,15 +638,15 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                     const int XP = G::xpairs(sp[0]), YR = G::rows(sp[1]), ZP = G::planes(sp[2]);
                     const int CH = XP / 2;
                     const int nchunk = ZP * YR * CH;
-                    if (lane < ZP) woff[lane] = 2LL * wrapi(b0[2] + lane, a.N[2]) * a.N[1] * a.N[0];
-                    if (lane < YR) woff[G::BZ + lane] = 2LL * wrapi(b0[1] + lane, a.N[1]) * a.N[0];
-                    if (lane < CH) woff[G::BZ + G::BY + lane] = 2LL * wrapi(x0 + 2 * lane, a.N[0]);
+                    if (lane < ZP) pwo[lane] = 2LL * wrapi(b0[2] + lane, a.N[2]) * a.N[1] * a.N[0];
+                    if (lane < YR) pwo[G::BZ + lane] = 2LL * wrapi(b0[1] + lane, a.N[1]) * a.N[0];
+                    if (lane < CH) pwo[G::BZ + G::BY + lane] = 2LL * wrapi(x0 + 2 * lane, a.N[0]);
                     __syncwarp();
                     for (int q = lane; q < nchunk; q += 32) {
                         const int row = q / CH;
                         const int c = q - row * CH;
                         const int z = row / YR, y = row - z * YR;
-                        const long long off = woff[z] + woff[G::BZ + y] + woff[G::BZ + G::BY + c];
+                        const long long off = pwo[z] + pwo[G::BZ + y] + pwo[G::BZ + G::BY + c];
                         cp_async16(dst + static_cast<uint32_t>((row * XP + 2 * c) * 8), src + off);
                     }
                     __syncwarp();  // the table is rewritten for the next such box
@@ -639,7 +664,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
             // in flight
             volatile int keep_waiting = 0;
             for (uint32_t x = tail; x != sent; ++x)
-                mbar_wait_bounded(full0 + 8 * (x & KM), (x / kItems) & 1u, &keep_waiting, nullptr);
+                mbar_wait_bounded(pf0 + 8 * (x & KM), (x / kItems) & 1u, &keep_waiting, nullptr);
         }
         return;
     }
@@ -656,6 +681,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     const int oz_l = lane / G::TY, oy_l = lane % G::TY;
     if (is_stream_warp(warp)) {
         const int c = stream_index(warp), qd = warp & 3;
+        const uint32_t pbase = static_cast<uint32_t>((c % NPROD) * 3 * kItems);  // its producer's block
         const bool row_lane = lane < G::ROWS;
         const uint32_t tmem_warp = *tmem_base_s + (static_cast<uint32_t>(qd * 32) << 16) +
                                    static_cast<uint32_t>((warp >> 2) * TC::per_warp);
@@ -672,14 +698,14 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
 #pragma unroll 1
             for (int k = 0; k < NPW; ++k) {
                 const int j = c + NC * k;
-                const uint32_t s = static_cast<uint32_t>(it) * kQ + static_cast<uint32_t>(j);
+                const uint32_t s = static_cast<uint32_t>(it) * IPP + static_cast<uint32_t>(j / NPROD);
                 // Where the item sits in the ring.  The producer announces item s only once item
                 // s - kItems has released the same descriptor, so its full barrier is then at most
                 // one phase ahead of the phase awaited below (one parity bit cannot tell more apart).
                 const uint32_t e = s & KM;
-                const uint32_t word = wait_item_bounded(items + e, s, abort_flag, err_flag);
+                const uint32_t word = wait_item_bounded(items + pbase + e, s, abort_flag, err_flag);
                 const int m = static_cast<int>(word & 15u);
-                if (m > 0) mbar_wait_bounded(full0 + 8 * e, (s / kItems) & 1u, abort_flag, err_flag);
+                if (m > 0) mbar_wait_bounded(full0 + 8 * (pbase + e), (s / kItems) & 1u, abort_flag, err_flag);
                 float2* box = ring + static_cast<size_t>(word >> 8) * 16;
                 const int ox0 = ((c0[0] + t.kmin[j][0]) * P) & 1;
                 // the box's shape: rows of XP pairs, planes of PL pairs; pieces PSTRIDE float2 apart
@@ -830,7 +856,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                 // the slot was written in place (generic proxy); order that before the next TMA fill
                 fence_proxy_async();
                 __syncwarp();
-                if (lane == 0 && m > 0) mbar_arrive(empty0 + 8 * e);
+                if (lane == 0 && m > 0) mbar_arrive(full0 + 8 * (pbase + kItems + e));
 
                 // park the pair in tensor memory
                 tmem_store_row<G::TX>(tbuf + static_cast<uint32_t>(k * 2 * G::TX), res);

@@ -376,6 +376,27 @@ __device__ __forceinline__ void tmem_load_row(uint32_t ta, float* v) {
     if (TX == 9) tmem_ld2(ta + 16, v + 16);
 }
 
+// Visiting order of the tiles: slabs of kBlockZ tile layers; in a slab, blocks of kBlockXY x
+// kBlockXY tile columns (row by row); in a block, z-, y-, then x-slowest.  Consecutive tiles
+// (the CTAs of one wave) thus cover a compact block whose source boxes overlap in L2, rather
+// than one thin layer of tiles whose z-halo is read again by the next wave.  Edge slabs,
+// rows and blocks are simply thinner.  Returns the tile's (x, y, z) tile coordinates.
+constexpr int kBlockXY = 4, kBlockZ = 8;
+__device__ __forceinline__ void tile_coords(int t, int ntx, int nty, int ntz, int* tc) {
+    const int slab = t / (ntx * nty * kBlockZ);
+    const int bz = min(kBlockZ, ntz - slab * kBlockZ);
+    int u = t - slab * ntx * nty * kBlockZ;
+    const int yb = u / (ntx * kBlockXY * bz);
+    const int by = min(kBlockXY, nty - yb * kBlockXY);
+    u -= yb * ntx * kBlockXY * bz;
+    const int xb = u / (kBlockXY * by * bz);
+    const int bx = min(kBlockXY, ntx - xb * kBlockXY);
+    u -= xb * kBlockXY * by * bz;
+    tc[0] = xb * kBlockXY + u % bx;
+    tc[1] = yb * kBlockXY + (u / bx) % by;
+    tc[2] = slab * kBlockZ + u / (bx * by);
+}
+
 __device__ __forceinline__ int wrapi(int v, int n) {
     int r = v % n;
     return r < 0 ? r + n : r;
@@ -476,8 +497,9 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         const uint32_t ring_u32 = smem_u32(ring);
         const int cd[3] = {CX, CY, CZ};
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, s_tile += IPP) {
-            const int tyz = tile / ntx;
-            const int cb[3] = {(tile - tyz * ntx) * CX * P, (tyz % nty) * CY * P, (tyz / nty) * CZ * P};
+            int tc[3];
+            tile_coords(tile, ntx, nty, ntz, tc);
+            const int cb[3] = {tc[0] * CX * P, tc[1] * CY * P, tc[2] * CZ * P};
             // meta: pieces m | nk_x << 4 | nk_y << 8 | nk_z << 12 | shape << 16 | cp.async << 20
             uint32_t meta[2];
             int crd[2][3];
@@ -689,7 +711,9 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
             if (*abort_flag) break;
             const int bf = it & 1;
             const int tile = static_cast<int>(blockIdx.x) + it * static_cast<int>(gridDim.x);
-            const int c0[3] = {(tile % ntx) * CX, ((tile / ntx) % nty) * CY, (tile / (ntx * nty)) * CZ};
+            int tc[3];
+            tile_coords(tile, ntx, nty, ntz, tc);
+            const int c0[3] = {tc[0] * CX, tc[1] * CY, tc[2] * CZ};
             if (it >= 2)
                 mbar_wait_bounded(tmem_empty0 + 8 * (qd * 2 + bf), static_cast<uint32_t>((it - 2) >> 1) & 1u, abort_flag,
                                   err_flag);
@@ -883,7 +907,9 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
             if (epilogue_barrier_or(*abort_flag)) break;
             const int bf = it & 1;
             const int tile = static_cast<int>(blockIdx.x) + it * static_cast<int>(gridDim.x);
-            const int c0[3] = {(tile % ntx) * CX, ((tile / ntx) % nty) * CY, (tile / (ntx * nty)) * CZ};
+            int tc[3];
+            tile_coords(tile, ntx, nty, ntz, tc);
+            const int c0[3] = {tc[0] * CX, tc[1] * CY, tc[2] * CZ};
             const uint32_t tb = tq + static_cast<uint32_t>(bf * TC::per_buf);
             mbar_wait_bounded(tmem_full0 + 8 * (qd * 2 + bf), static_cast<uint32_t>(it >> 1) & 1u, abort_flag, err_flag);
             tc_fence_after();

@@ -207,6 +207,20 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def replica_throughput(total_ms: float, nodes: int, steps: int, dist=None, device="cpu"):
+    """Whole-job throughput of N independent replicas: every rank's nodes over the slowest
+    rank's time (max over ranks).  Returns (max_ms, node-updates/s)."""
+    import torch
+
+    world = 1
+    if dist is not None:
+        world = dist.get_world_size()
+        t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, nodes * steps * world / (total_ms / 1e3)
+
+
 def time_steps(sim, torch, steps, per_launch=True):
     """Times `steps` single-step launches on the context's stream with CUDA events."""
     stream = sim.stream
@@ -268,17 +282,14 @@ def run_mine(args, rank, world, local):
     total_ms, kern = time_steps(sim, torch, args.steps)
     launches = sim.launches() - launches0
     torch.cuda.synchronize()
+    nodes = sim.nodes
+    total_ms, value = replica_throughput(total_ms, nodes, args.steps, dist, device=f"cuda:{local}")
     if dist is not None:
-        t = torch.tensor([total_ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     clk = clocks.stop()
     _, _, T = sim.moments()
     finite = bool(torch.isfinite(T).all().item())
 
-    nodes = sim.nodes
-    value = nodes * args.steps * world / (total_ms / 1e3)
     elem = 8 if storage == "f64" else 4
     bytes_per_node = 2 * 45 * 2 * elem  # read + write of f and g
     kern_avg_ms = statistics.mean(kern)

@@ -757,7 +757,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                         for (int l = 0; l <= P; ++l) wz[az][l] = make_float2(t.lw[j][2][az][l], t.lw[j][2][az][l]);
                     }
                     const int nit = (PL + 31) >> 5;
-#pragma unroll 2
+#pragma unroll 1
                     for (int it = 0; it < nit; ++it) {
                         const int e = lane + 32 * it;
                         if (e < PL) {

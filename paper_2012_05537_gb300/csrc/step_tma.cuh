@@ -756,43 +756,58 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
 #pragma unroll
                         for (int l = 0; l <= P; ++l) wz[az][l] = make_float2(t.lw[j][2][az][l], t.lw[j][2][az][l]);
                     }
-                    const int nit = (PL + 31) >> 5;
+                    // two adjacent columns per lane: 16-byte loads and stores (PL is even and the box
+                    // starts on a 128-byte boundary)
+                    const int nq = PL >> 1;
+                    float4* box4 = reinterpret_cast<float4*>(box);
 #pragma unroll 1
-                    for (int it = 0; it < nit; ++it) {
-                        const int e = lane + 32 * it;
-                        if (e < PL) {
-                            float2 v[NZ];
+                    for (int e2 = lane; e2 < nq; e2 += 32) {
+                        float2 va[NZ], vb[NZ];
 #pragma unroll
-                            for (int z = 0; z < NZ; ++z) v[z] = box[z * PL + e];
-                            // the other periodic images of a box that crosses the boundary (each is
-                            // zero outside the domain, so their sum is the wrapped box)
-                            for (int q = 1; q < m; ++q) {
-                                const float2* bq = box + q * PSTRIDE;
+                        for (int z = 0; z < NZ; ++z) {
+                            const float4 q4 = box4[z * nq + e2];
+                            va[z] = make_float2(q4.x, q4.y);
+                            vb[z] = make_float2(q4.z, q4.w);
+                        }
+                        // the other periodic images of a box that crosses the boundary (each is
+                        // zero outside the domain, so their sum is the wrapped box)
+                        for (int q = 1; q < m; ++q) {
+                            const float4* bq = reinterpret_cast<const float4*>(box + q * PSTRIDE);
 #pragma unroll
-                                for (int z = 0; z < NZ; ++z) {
-                                    const float2 u = bq[z * PL + e];
-                                    v[z].x += u.x;
-                                    v[z].y += u.y;
-                                }
+                            for (int z = 0; z < NZ; ++z) {
+                                const float4 u = bq[z * nq + e2];
+                                va[z].x += u.x;
+                                va[z].y += u.y;
+                                vb[z].x += u.z;
+                                vb[z].y += u.w;
                             }
+                        }
 #pragma unroll
-                            for (int oz = 0; oz < G::TZ; ++oz) {
-                                const int cz = oz / P, az = oz % P;
-                                float2 o = make_float2(0.f, 0.f);
-                                if constexpr (NZ == G::BZ) {
-                                    if (kz[az]) {
+                        for (int oz = 0; oz < G::TZ; ++oz) {
+                            const int cz = oz / P, az = oz % P;
+                            float2 oa = make_float2(0.f, 0.f), ob = make_float2(0.f, 0.f);
+                            if constexpr (NZ == G::BZ) {
+                                if (kz[az]) {
 #pragma unroll
-                                        for (int l = 0; l <= P; ++l) o = ffma2(v[(cz + 1) * P + l], wz[az][l], o);
-                                    } else {
-#pragma unroll
-                                        for (int l = 0; l <= P; ++l) o = ffma2(v[cz * P + l], wz[az][l], o);
+                                    for (int l = 0; l <= P; ++l) {
+                                        oa = ffma2(va[(cz + 1) * P + l], wz[az][l], oa);
+                                        ob = ffma2(vb[(cz + 1) * P + l], wz[az][l], ob);
                                     }
                                 } else {
 #pragma unroll
-                                    for (int l = 0; l <= P; ++l) o = ffma2(v[cz * P + l], wz[az][l], o);
+                                    for (int l = 0; l <= P; ++l) {
+                                        oa = ffma2(va[cz * P + l], wz[az][l], oa);
+                                        ob = ffma2(vb[cz * P + l], wz[az][l], ob);
+                                    }
                                 }
-                                box[oz * PL + e] = o;
+                            } else {
+#pragma unroll
+                                for (int l = 0; l <= P; ++l) {
+                                    oa = ffma2(va[cz * P + l], wz[az][l], oa);
+                                    ob = ffma2(vb[cz * P + l], wz[az][l], ob);
+                                }
                             }
+                            box4[oz * nq + e2] = make_float4(oa.x, oa.y, ob.x, ob.y);
                         }
                     }
                 };

@@ -827,31 +827,46 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
 #pragma unroll
                         for (int l = 0; l <= P; ++l) wy[ay][l] = make_float2(t.lw[j][1][ay][l], t.lw[j][1][ay][l]);
                     }
-                    const int ncol = G::TZ * XP;
+                    // two adjacent columns per lane: 16-byte loads and stores (XP is even)
+                    const int XQ = XP >> 1, ncol = G::TZ * XQ;
+                    float4* box4 = reinterpret_cast<float4*>(box);
 #pragma unroll 1
                     for (int e = lane; e < ncol; e += 32) {
-                        const int oz = e / XP, xb = e - oz * XP;
-                        float2* col = box + oz * PL + xb;
-                        float2 v[NY];
+                        const int oz = e / XQ, xq = e - oz * XQ;
+                        float4* col = box4 + oz * (PL >> 1) + xq;
+                        float2 va[NY], vb[NY];
 #pragma unroll
-                        for (int y = 0; y < NY; ++y) v[y] = col[y * XP];
+                        for (int y = 0; y < NY; ++y) {
+                            const float4 q4 = col[y * XQ];
+                            va[y] = make_float2(q4.x, q4.y);
+                            vb[y] = make_float2(q4.z, q4.w);
+                        }
 #pragma unroll
                         for (int oy = 0; oy < G::TY; ++oy) {
                             const int cy = oy / P, ay = oy % P;
-                            float2 o = make_float2(0.f, 0.f);
+                            float2 oa = make_float2(0.f, 0.f), ob = make_float2(0.f, 0.f);
                             if constexpr (NY == G::BY) {
                                 if (ky[ay]) {
 #pragma unroll
-                                    for (int l = 0; l <= P; ++l) o = ffma2(v[(cy + 1) * P + l], wy[ay][l], o);
+                                    for (int l = 0; l <= P; ++l) {
+                                        oa = ffma2(va[(cy + 1) * P + l], wy[ay][l], oa);
+                                        ob = ffma2(vb[(cy + 1) * P + l], wy[ay][l], ob);
+                                    }
                                 } else {
 #pragma unroll
-                                    for (int l = 0; l <= P; ++l) o = ffma2(v[cy * P + l], wy[ay][l], o);
+                                    for (int l = 0; l <= P; ++l) {
+                                        oa = ffma2(va[cy * P + l], wy[ay][l], oa);
+                                        ob = ffma2(vb[cy * P + l], wy[ay][l], ob);
+                                    }
                                 }
                             } else {
 #pragma unroll
-                                for (int l = 0; l <= P; ++l) o = ffma2(v[cy * P + l], wy[ay][l], o);
+                                for (int l = 0; l <= P; ++l) {
+                                    oa = ffma2(va[cy * P + l], wy[ay][l], oa);
+                                    ob = ffma2(vb[cy * P + l], wy[ay][l], ob);
+                                }
                             }
-                            col[oy * XP] = o;
+                            col[oy * XQ] = make_float4(oa.x, oa.y, ob.x, ob.y);
                         }
                     }
                 };

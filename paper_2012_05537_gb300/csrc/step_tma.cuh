@@ -543,6 +543,20 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                 }
             }
 
+            // per round of 32 items: inclusive prefix sums of the ring units over the lanes, and the
+            // lanes whose item takes the cp.async path
+            int incl_r[2] = {units[0], units[1]};
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int u = __shfl_up_sync(0xffffffffu, incl_r[h], o);
+                    if (lane >= o) incl_r[h] += u;
+                }
+            }
+            const uint32_t fbm_r[2] = {__ballot_sync(0xffffffffu, (meta[0] >> 20) & 1u),
+                                       __ballot_sync(0xffffffffu, (meta[1] >> 20) & 1u)};
+
             int nxt = 0;  // first item of the tile not issued yet
             while (nxt < IPP) {
                 const int h = nxt >> 5;
@@ -561,27 +575,22 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                     inflight -= nrel;
                 }
                 if (inflight == 0) head = 0;  // ring empty: start over at its beginning
-                // Place the next items of this round: a prefix sum of their ring units over the
-                // lanes, then the longest run from the first one that fits in one free region
-                // (the rest of the ring after `head`, or its start when that is too short).  A
-                // cp.async item goes alone.
+                // Place the next items of this round: the longest run from the first one whose
+                // ring units (the tile's prefix sums, taken from item lo on) fit in one free
+                // region (the rest of the ring after `head`, or its start when that is too
+                // short).  A cp.async item goes alone.
                 const int tail_off = inflight > 0 ? pst[tail & KM] : 0;
                 const int cap = min(nlane - lo, kItems - inflight);
-                const uint32_t mt_l = h ? meta[1] : meta[0];
-                const bool cand = lane >= lo && lane < lo + cap;
-                const uint32_t fbm = __ballot_sync(0xffffffffu, cand && ((mt_l >> 20) & 1u));
+                const uint32_t fbm = h ? fbm_r[1] : fbm_r[0];
                 const bool first_fb = (fbm >> lo) & 1u;
                 // candidates end before the first cp.async item after the first one
                 const uint32_t fb_after = fbm & ~((2u << lo) - 1u);
                 const int end = first_fb ? lo + 1 : (fb_after ? min(lo + cap, __ffs(static_cast<int>(fb_after)) - 1) : lo + cap);
-                const int need_l = (lane >= lo && lane < end) ? (h ? units[1] : units[0]) : 0;
-                int incl = need_l;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int u = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += u;
-                }
+                const int need_l = h ? units[1] : units[0];
+                const int incl_l = h ? incl_r[1] : incl_r[0];
+                const int excl_lo = __shfl_sync(0xffffffffu, incl_l - need_l, lo);
                 const int first_need = __shfl_sync(0xffffffffu, need_l, lo);
+                const int incl = incl_l - excl_lo;  // units of items lo .. lane
                 int base = -1, limit = 0;
                 if (inflight == 0) {
                     base = head;

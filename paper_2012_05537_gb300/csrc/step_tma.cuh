@@ -129,8 +129,11 @@ struct TmaSmem {
     // every region starts on a 128-byte boundary (TMA destinations, float4 and mbarrier
     // alignment)
     static constexpr size_t round128(size_t b) { return (b + 127) / 128 * 128; }
-    static constexpr size_t partials = round128(size_t(4) * 5 * G::TX * 32 * sizeof(float));  // per quarter
-    static constexpr size_t params = round128(size_t(kNParams) * G::TX * 32 * sizeof(float));
+    // the per-quarter moment sums (3 quarters x 5) and the per-node parameters share one region:
+    // an epilogue warp reads the sums of exactly the node columns whose parameters it writes
+    static constexpr int kShared = 3 * 5 > kNParams ? 3 * 5 : kNParams;
+    static constexpr size_t partials = round128(size_t(kShared) * G::TX * 32 * sizeof(float));
+    static constexpr size_t params = 0;
     static constexpr size_t tables = round128(sizeof(StepTablesS<P>));
     // per producer: full[kItems], empty[kItems] mbarriers and the item table (one word per
     // entry: item number, ring offset and piece count); tmem_full[4][2], tmem_empty[4][2]
@@ -428,7 +431,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     float2* ring = reinterpret_cast<float2*>(base);  // the box ring, 16 float2 per unit
     float* part = reinterpret_cast<float*>(base + SM::ring);
-    float* prm = reinterpret_cast<float*>(base + SM::ring + SM::partials);
+    float* prm = part;  // (the same region; see TmaSmem)
     StepTablesS<P>* tsm = reinterpret_cast<StepTablesS<P>*>(base + SM::ring + SM::partials + SM::params);
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + SM::ring + SM::partials + SM::params + SM::tables);
     // item table: entry s % kItems = (s << 32) | (ring offset in units << 8) | pieces for item s
@@ -988,7 +991,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                     }
                 }
                 // layout [quarter][moment][x][lane] (node = lane*TX + x): contiguous lane accesses
-                float* pc = part + static_cast<size_t>(qd) * 5 * QS + lane;
+                float* pc = part + static_cast<size_t>(qd == 0 ? 0 : qd - 1) * 5 * QS + lane;
 #pragma unroll
                 for (int q = 0; q < 5; ++q)
 #pragma unroll
@@ -1004,8 +1007,8 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                 float m[5];
 #pragma unroll
                 for (int q = 0; q < 5; ++q)
-                    m[q] = (part[(0 * 5 + q) * QS + x * 32 + lane] + part[(2 * 5 + q) * QS + x * 32 + lane]) +
-                           part[(3 * 5 + q) * QS + x * 32 + lane];
+                    m[q] = (part[(0 * 5 + q) * QS + x * 32 + lane] + part[(1 * 5 + q) * QS + x * 32 + lane]) +
+                           part[(2 * 5 + q) * QS + x * 32 + lane];
                 const float rho = m[0];
                 const float inv_rho = 1.0f / rho;
                 const float ux = m[1] * inv_rho, uy = m[2] * inv_rho, uz = m[3] * inv_rho;

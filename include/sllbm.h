@@ -22,7 +22,9 @@
  *             origin; icosahedron |xi|=sqrt(3); dodecahedron |xi|=3; icosahedron
  *             |xi|=sqrt(15).
  *  Populations a state buffer holds the 2*45 populations of every node in the storage
- *             type (SLLBM_F64: double, SLLBM_F32: float) in the order
+ *             type (SLLBM_F64: double, SLLBM_F32: float, SLLBM_F16DEV: IEEE half,
+ *             SLLBM_BF16DEV: bfloat16; the 16-bit types hold deviations, see
+ *             sllbm_storage) in the order
  *             buf[i][z][y][x][h]: velocity slowest, then the node, then h = 0 for f and
  *             h = 1 for g, so f_i and g_i of a node sit side by side.  The FP64
  *             interface of sllbm_set_populations / sllbm_get_populations uses the order
@@ -67,9 +69,18 @@ typedef struct {
 typedef enum { SLLBM_D3Q45 = 0 } sllbm_velset;
 
 typedef enum {
-    SLLBM_F64 = 0, /* double populations, FP64 arithmetic */
-    SLLBM_F32 = 1  /* float populations, FP32 arithmetic */
+    SLLBM_F64 = 0,     /* double populations, FP64 arithmetic */
+    SLLBM_F32 = 1,     /* float populations, FP32 arithmetic */
+    SLLBM_F16DEV = 2,  /* IEEE half deviations, FP32 arithmetic (see below) */
+    SLLBM_BF16DEV = 3  /* bfloat16 deviations, FP32 arithmetic (see below) */
 } sllbm_storage;
+/* Mixed-precision storage: SLLBM_F16DEV and SLLBM_BF16DEV store, per node and velocity,
+ * d_i = f_i/w_i - rho0 and d_gi = g_i/w_i - (2 C_v - 3) T0 rho0 (rho0, T0 of the context's
+ * parameters) in 16 bits.  The step interpolates the deviations in FP32 (the Lagrange
+ * weights of each pass sum to one), forms rho - rho0, rho u and 2 rho (T - T0) C_v from
+ * deviation sums with the exact quadrature identities sum w_i = 1, sum w_i xi_i = 0,
+ * sum w_i |xi_i|^2 = 3 (no cancellation against the reference state), collides in FP32 and
+ * stores deviations again.  The generic kernel runs these types. */
 
 /* Physical and run parameters.  Taylor-Green scaling (Sec. III.C): U0 = Ma*sqrt(gamma*T0),
  * mu_inf = rho0*U0*1/Re (reference length 1), unless mu_inf_override > 0. */

@@ -10,6 +10,7 @@
 
 #include "collide.cuh"
 #include "sllbm_internal.h"
+#include "storage.cuh"
 #include "tables.h"
 
 using namespace sllbm;
@@ -41,6 +42,23 @@ int fail(sllbm_ctx* ctx, cudaError_t e) {
         if (e_ != cudaSuccess) return fail((ctx), e_);       \
     } while (0)
 
+// Calls f with a value of the storage type of the context (double, float, __half, bfloat16).
+template <typename F>
+void with_storage(const sllbm_ctx* ctx, F&& f) {
+    switch (ctx->prm.storage) {
+    case SLLBM_F64: f(double{}); break;
+    case SLLBM_F32: f(float{}); break;
+    case SLLBM_F16DEV: f(__half{}); break;
+    default: f(__nv_bfloat16{}); break;
+    }
+}
+
+// Deviation references of 16-bit storage: rho0 for f, (2 C_v - D) T0 rho0 for g.
+PopRef pop_ref(const sllbm_ctx* ctx) {
+    const double gfac = 2.0 / (ctx->prm.gamma - 1.0) - 3.0;
+    return PopRef{ctx->prm.rho0, gfac * ctx->prm.T0 * ctx->prm.rho0};
+}
+
 unsigned grid_for(long long n, int block) {
     long long g = (n + block - 1) / block;
     if (g > 1048576) g = 1048576;
@@ -57,7 +75,7 @@ __global__ void init_eq_kernel(S* __restrict__ pop, long long nn, int Nx, int Ny
                                const double* __restrict__ cz, int mode, double U0, double rho0,
                                double T0, double C, const double* __restrict__ rho_f,
                                const double* __restrict__ u_f, const double* __restrict__ T_f,
-                               double gfac, const __grid_constant__ VelConst vc) {
+                               double gfac, PopRef ref, const __grid_constant__ VelConst vc) {
     for (long long n = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; n < nn;
          n += static_cast<long long>(gridDim.x) * blockDim.x) {
         double rho, ux, uy, uz, T;
@@ -83,8 +101,8 @@ __global__ void init_eq_kernel(S* __restrict__ pop, long long nn, int Nx, int Ny
         for (int i = 0; i < kQ; ++i) {
             const double s = vc.xi[i][0] * ux + vc.xi[i][1] * uy + vc.xi[i][2] * uz;
             const double feq = vc.w[i] * rho * eq_poly(ec, shell_of(i), s);
-            pop[2 * (i * nn + n)] = static_cast<S>(feq);
-            pop[2 * (i * nn + n) + 1] = static_cast<S>(gfac * T * feq);
+            pop[2 * (i * nn + n)] = PopCodec<S>::encode(feq, vc.w[i], ref.f);
+            pop[2 * (i * nn + n) + 1] = PopCodec<S>::encode(gfac * T * feq, vc.w[i], ref.g);
         }
     }
 }
@@ -92,22 +110,26 @@ __global__ void init_eq_kernel(S* __restrict__ pop, long long nn, int Nx, int Ny
 // FP64 populations in the interface order [h][i][node] <-> the storage order
 // [i][node][h] (f_i and g_i of a node side by side), rounding to the storage type.
 template <typename S>
-__global__ void pack_kernel(const double* __restrict__ in, S* __restrict__ out, long long nn) {
+__global__ void pack_kernel(const double* __restrict__ in, S* __restrict__ out, long long nn, PopRef ref,
+                            const __grid_constant__ VelConst vc) {
     const long long count = 2LL * kQ * nn;
     for (long long k = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; k < count;
          k += static_cast<long long>(gridDim.x) * blockDim.x) {
         const long long h = k & 1, r = k >> 1;  // r = i*nn + node
-        out[k] = static_cast<S>(in[h * kQ * nn + r]);
+        const int i = static_cast<int>(r / nn);
+        out[k] = PopCodec<S>::encode(in[h * kQ * nn + r], vc.w[i], h ? ref.g : ref.f);
     }
 }
 
 template <typename S>
-__global__ void unpack_kernel(const S* __restrict__ in, double* __restrict__ out, long long nn) {
+__global__ void unpack_kernel(const S* __restrict__ in, double* __restrict__ out, long long nn, PopRef ref,
+                              const __grid_constant__ VelConst vc) {
     const long long count = 2LL * kQ * nn;
     for (long long k = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; k < count;
          k += static_cast<long long>(gridDim.x) * blockDim.x) {
         const long long h = k & 1, r = k >> 1;
-        out[h * kQ * nn + r] = static_cast<double>(in[k]);
+        const int i = static_cast<int>(r / nn);
+        out[h * kQ * nn + r] = PopCodec<S>::decode(in[k], vc.w[i], h ? ref.g : ref.f);
     }
 }
 
@@ -115,18 +137,18 @@ __global__ void unpack_kernel(const S* __restrict__ in, double* __restrict__ out
 template <typename S>
 __global__ void moments_kernel(const S* __restrict__ pop, long long nn, double inv_2cv,
                                double* __restrict__ rho_o, double* __restrict__ u_o,
-                               double* __restrict__ T_o, const __grid_constant__ VelConst vc) {
+                               double* __restrict__ T_o, PopRef ref, const __grid_constant__ VelConst vc) {
     for (long long n = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; n < nn;
          n += static_cast<long long>(gridDim.x) * blockDim.x) {
         double rho = 0, mx = 0, my = 0, mz = 0, e2 = 0;
 #pragma unroll 5
         for (int i = 0; i < kQ; ++i) {
-            const double f = static_cast<double>(pop[2 * (i * nn + n)]);
+            const double f = PopCodec<S>::decode(pop[2 * (i * nn + n)], vc.w[i], ref.f);
             rho += f;
             mx += f * vc.xi[i][0];
             my += f * vc.xi[i][1];
             mz += f * vc.xi[i][2];
-            e2 += f * shell_xi2(shell_of(i)) + static_cast<double>(pop[2 * (i * nn + n) + 1]);
+            e2 += f * shell_xi2(shell_of(i)) + PopCodec<S>::decode(pop[2 * (i * nn + n) + 1], vc.w[i], ref.g);
         }
         const double ux = mx / rho, uy = my / rho, uz = mz / rho;
         rho_o[n] = rho;
@@ -140,6 +162,8 @@ __global__ void moments_kernel(const S* __restrict__ pop, long long nn, double i
 // ---------------------------------------------------------------- diagnostics
 struct DiagConst {
     double xi[kQ][3];
+    double w[kQ];
+    PopRef ref;
     double W[kMaxP + 1];
     double D[kMaxP + 1][kMaxP + 1];
 };
@@ -170,12 +194,12 @@ __global__ void __launch_bounds__(128) diag_kernel(const S* __restrict__ pop, lo
             const long long n = (static_cast<long long>(nz) * Ny + ny) * Nx + nx;
             double mx = 0, my = 0, mz = 0, e2 = 0;
             for (int i = 0; i < kQ; ++i) {
-                const double f = static_cast<double>(pop[2 * (i * nn + n)]);
+                const double f = PopCodec<S>::decode(pop[2 * (i * nn + n)], dc.w[i], dc.ref.f);
                 rho += f;
                 mx += f * dc.xi[i][0];
                 my += f * dc.xi[i][1];
                 mz += f * dc.xi[i][2];
-                e2 += f * shell_xi2(shell_of(i)) + static_cast<double>(pop[2 * (i * nn + n) + 1]);
+                e2 += f * shell_xi2(shell_of(i)) + PopCodec<S>::decode(pop[2 * (i * nn + n) + 1], dc.w[i], dc.ref.g);
             }
             ux = mx / rho;
             uy = my / rho;
@@ -282,14 +306,12 @@ int launch_init(sllbm_ctx* ctx, int mode, const double* rho, const double* u, co
     const double gfac = 2.0 / (ctx->prm.gamma - 1.0) - 3.0;
     const double U0 = ctx->U0, rho0 = ctx->prm.rho0, T0 = ctx->prm.T0, C = ctx->tgv_C;
     void* dst = ctx->buf[ctx->cur];
-    if (ctx->prm.storage == SLLBM_F64)
-        init_eq_kernel<double><<<grid, block, 0, ctx->stream>>>(
-            static_cast<double*>(dst), ctx->nn, ctx->N[0], ctx->N[1], ctx->d_coords[0], ctx->d_coords[1],
-            ctx->d_coords[2], mode, U0, rho0, T0, C, rho, u, T, gfac, vel_const(ctx));
-    else
-        init_eq_kernel<float><<<grid, block, 0, ctx->stream>>>(
-            static_cast<float*>(dst), ctx->nn, ctx->N[0], ctx->N[1], ctx->d_coords[0], ctx->d_coords[1],
-            ctx->d_coords[2], mode, U0, rho0, T0, C, rho, u, T, gfac, vel_const(ctx));
+    with_storage(ctx, [&](auto tag) {
+        using S = decltype(tag);
+        init_eq_kernel<S><<<grid, block, 0, ctx->stream>>>(
+            static_cast<S*>(dst), ctx->nn, ctx->N[0], ctx->N[1], ctx->d_coords[0], ctx->d_coords[1],
+            ctx->d_coords[2], mode, U0, rho0, T0, C, rho, u, T, gfac, pop_ref(ctx), vel_const(ctx));
+    });
     ctx->launches += 1;
     CK(ctx, cudaGetLastError());
     ctx->initialised = true;
@@ -301,6 +323,8 @@ int launch_diag_p(sllbm_ctx* ctx, const void* pop, double* d_out) {
     const long long ncell = static_cast<long long>(ctx->cells[0]) * ctx->cells[1] * ctx->cells[2];
     DiagConst dc;
     std::memcpy(dc.xi, ctx->xi, sizeof(dc.xi));
+    std::memcpy(dc.w, ctx->w, sizeof(dc.w));
+    dc.ref = pop_ref(ctx);
     double W[kMaxP + 1];
     clenshaw_curtis(P, W);
     for (int j = 0; j <= kMaxP; ++j) dc.W[j] = j <= P ? W[j] : 0.0;
@@ -310,14 +334,12 @@ int launch_diag_p(sllbm_ctx* ctx, const void* pop, double* d_out) {
         for (int j = 0; j <= kMaxP; ++j) dc.D[a][j] = (a <= P && j <= P) ? D[a][j] : 0.0;
     const double inv_2cv = 0.5 * (ctx->prm.gamma - 1.0);
     const int nb = ctx->partial_blocks;
-    if (ctx->prm.storage == SLLBM_F64)
-        diag_kernel<double, P><<<nb, 128, 0, ctx->stream>>>(
-            static_cast<const double*>(pop), ctx->nn, ctx->N[0], ctx->N[1], ctx->N[2], ctx->cells[0],
+    with_storage(ctx, [&](auto tag) {
+        using S = decltype(tag);
+        diag_kernel<S, P><<<nb, 128, 0, ctx->stream>>>(
+            static_cast<const S*>(pop), ctx->nn, ctx->N[0], ctx->N[1], ctx->N[2], ctx->cells[0],
             ctx->cells[1], ncell, inv_2cv, ctx->h[0], ctx->h[1], ctx->h[2], dc, ctx->d_partials);
-    else
-        diag_kernel<float, P><<<nb, 128, 0, ctx->stream>>>(
-            static_cast<const float*>(pop), ctx->nn, ctx->N[0], ctx->N[1], ctx->N[2], ctx->cells[0],
-            ctx->cells[1], ncell, inv_2cv, ctx->h[0], ctx->h[1], ctx->h[2], dc, ctx->d_partials);
+    });
     sum_partials_kernel<<<1, 256, 0, ctx->stream>>>(ctx->d_partials, nb, d_out);
     ctx->launches += 2;
     CK(ctx, cudaGetLastError());
@@ -340,6 +362,8 @@ int launch_diag_cells_into(sllbm_ctx* ctx, const void* pop, double* partials, do
     const long long ncell = static_cast<long long>(ctx->cells[0]) * ctx->cells[1] * ctx->cells[2];
     DiagConst dc;
     std::memcpy(dc.xi, ctx->xi, sizeof(dc.xi));
+    std::memcpy(dc.w, ctx->w, sizeof(dc.w));
+    dc.ref = pop_ref(ctx);
     double W[kMaxP + 1];
     clenshaw_curtis(P, W);
     for (int j = 0; j <= kMaxP; ++j) dc.W[j] = j <= P ? W[j] : 0.0;
@@ -349,14 +373,12 @@ int launch_diag_cells_into(sllbm_ctx* ctx, const void* pop, double* partials, do
         for (int j = 0; j <= kMaxP; ++j) dc.D[a][j] = (a <= P && j <= P) ? D[a][j] : 0.0;
     const double inv_2cv = 0.5 * (ctx->prm.gamma - 1.0);
     const int nb = static_cast<int>(ncell);  // one block, hence one partial triple, per cell
-    if (ctx->prm.storage == SLLBM_F64)
-        diag_kernel<double, P><<<nb, 128, 0, ctx->stream>>>(
-            static_cast<const double*>(pop), ctx->nn, ctx->N[0], ctx->N[1], ctx->N[2], ctx->cells[0],
+    with_storage(ctx, [&](auto tag) {
+        using S = decltype(tag);
+        diag_kernel<S, P><<<nb, 128, 0, ctx->stream>>>(
+            static_cast<const S*>(pop), ctx->nn, ctx->N[0], ctx->N[1], ctx->N[2], ctx->cells[0],
             ctx->cells[1], ncell, inv_2cv, ctx->h[0], ctx->h[1], ctx->h[2], dc, partials);
-    else
-        diag_kernel<float, P><<<nb, 128, 0, ctx->stream>>>(
-            static_cast<const float*>(pop), ctx->nn, ctx->N[0], ctx->N[1], ctx->N[2], ctx->cells[0],
-            ctx->cells[1], ncell, inv_2cv, ctx->h[0], ctx->h[1], ctx->h[2], dc, partials);
+    });
     sum_partials_kernel<<<1, 256, 0, ctx->stream>>>(partials, nb, d_out);
     ctx->launches += 2;
     CK(ctx, cudaGetLastError());
@@ -382,6 +404,8 @@ void fill_step_args(const sllbm_ctx* ctx, const void* src, void* dst, StepArgs* 
     a->gfac = 2.0 * cv - 3.0;
     a->inv_pr = 1.0 / ctx->prm.Pr;
     a->pr = ctx->prm.pr_correction;
+    a->rho0 = ctx->prm.rho0;
+    a->T0 = ctx->prm.T0;
     a->collide = ctx->prm.collide;
     a->flag = ctx->prm.nonfinite_check ? ctx->d_flag : nullptr;
     a->flag_err = ctx->d_flag + 1;
@@ -417,7 +441,9 @@ int sllbm_create(const sllbm_mesh* mesh, int p, sllbm_velset vs, const sllbm_par
     *out = nullptr;
     if (mesh == nullptr || prm == nullptr || vs != SLLBM_D3Q45) return SLLBM_EINVAL;
     if (p < 2 || p > 4) return SLLBM_EINVAL;
-    if (prm->storage != SLLBM_F64 && prm->storage != SLLBM_F32) return SLLBM_EINVAL;
+    if (prm->storage != SLLBM_F64 && prm->storage != SLLBM_F32 && prm->storage != SLLBM_F16DEV &&
+        prm->storage != SLLBM_BF16DEV)
+        return SLLBM_EINVAL;
     if (!(prm->gamma > 1.0) || !(prm->Pr > 0.0) || !(prm->T0 > 0.0) || !(prm->rho0 > 0.0))
         return SLLBM_EINVAL;
     if (!(prm->dt_or_courant > 0.0)) return SLLBM_EINVAL;
@@ -481,7 +507,7 @@ int sllbm_create(const sllbm_mesh* mesh, int p, sllbm_velset vs, const sllbm_par
         std::free(c);
         return SLLBM_EINVAL;
     }
-    c->elem = prm->storage == SLLBM_F64 ? sizeof(double) : sizeof(float);
+    c->elem = prm->storage == SLLBM_F64 ? sizeof(double) : prm->storage == SLLBM_F32 ? sizeof(float) : 2;
     c->pop_bytes = static_cast<size_t>(2 * kQ) * static_cast<size_t>(nn) * c->elem;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaGetDevice(&c->device);
@@ -623,10 +649,11 @@ int sllbm_set_populations(sllbm_ctx* ctx, const double* pop, int on_device) {
         }
         src = tmp;
     }
-    if (ctx->prm.storage == SLLBM_F64)
-        pack_kernel<double><<<grid_for(count, 256), 256, 0, ctx->stream>>>(src, static_cast<double*>(dst), ctx->nn);
-    else
-        pack_kernel<float><<<grid_for(count, 256), 256, 0, ctx->stream>>>(src, static_cast<float*>(dst), ctx->nn);
+    with_storage(ctx, [&](auto tag) {
+        using S = decltype(tag);
+        pack_kernel<S><<<grid_for(count, 256), 256, 0, ctx->stream>>>(src, static_cast<S*>(dst), ctx->nn, pop_ref(ctx),
+                                                                       vel_const(ctx));
+    });
     ctx->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (tmp != nullptr) {
@@ -649,10 +676,11 @@ int sllbm_get_populations(sllbm_ctx* ctx, double* pop, int on_device) {
         CK(ctx, cudaMalloc(&tmp, count * sizeof(double)));
         dst = tmp;
     }
-    if (ctx->prm.storage == SLLBM_F64)
-        unpack_kernel<double><<<grid_for(count, 256), 256, 0, ctx->stream>>>(static_cast<const double*>(src), dst, ctx->nn);
-    else
-        unpack_kernel<float><<<grid_for(count, 256), 256, 0, ctx->stream>>>(static_cast<const float*>(src), dst, ctx->nn);
+    with_storage(ctx, [&](auto tag) {
+        using S = decltype(tag);
+        unpack_kernel<S><<<grid_for(count, 256), 256, 0, ctx->stream>>>(static_cast<const S*>(src), dst, ctx->nn,
+                                                                         pop_ref(ctx), vel_const(ctx));
+    });
     ctx->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (tmp != nullptr) {
@@ -671,7 +699,9 @@ int sllbm_step(sllbm_ctx* ctx, int n) {
     for (int s = 0; s < n; ++s) {
         const void* src = ctx->buf[ctx->cur];
         void* dst = ctx->buf[1 - ctx->cur];
-        int rc = ctx->prm.storage == SLLBM_F64 ? launch_step_f64(ctx, src, dst) : launch_step_f32(ctx, src, dst);
+        int rc = ctx->prm.storage == SLLBM_F64   ? launch_step_f64(ctx, src, dst)
+                 : ctx->prm.storage == SLLBM_F32 ? launch_step_f32(ctx, src, dst)
+                                                 : launch_step_f16(ctx, src, dst);
         if (rc != SLLBM_OK) return rc;
         ctx->cur = 1 - ctx->cur;
     }
@@ -716,12 +746,11 @@ int sllbm_moments(sllbm_ctx* ctx, double* rho, double* u, double* T, int on_devi
     const double inv_2cv = 0.5 * (ctx->prm.gamma - 1.0);
     const void* pop = ctx->buf[ctx->cur];
     const unsigned grid = grid_for(ctx->nn, 256);
-    if (ctx->prm.storage == SLLBM_F64)
-        moments_kernel<double><<<grid, 256, 0, ctx->stream>>>(static_cast<const double*>(pop), ctx->nn, inv_2cv,
-                                                               dr, du, dT, vel_const(ctx));
-    else
-        moments_kernel<float><<<grid, 256, 0, ctx->stream>>>(static_cast<const float*>(pop), ctx->nn, inv_2cv,
-                                                              dr, du, dT, vel_const(ctx));
+    with_storage(ctx, [&](auto tag) {
+        using S = decltype(tag);
+        moments_kernel<S><<<grid, 256, 0, ctx->stream>>>(static_cast<const S*>(pop), ctx->nn, inv_2cv, dr, du, dT,
+                                                         pop_ref(ctx), vel_const(ctx));
+    });
     ctx->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (!on_device) {

@@ -72,6 +72,7 @@ struct StepArgs {
     double gfac;        // 2 C_v - D
     double inv_pr;      // 1 / Pr
     int pr;             // Prandtl term on
+    double rho0, T0;    // reference state of 16-bit deviation storage
     int collide;        // 0: stream only
     int* flag;          // non-finite flag or nullptr
     int* flag_err;      // set (bit 2) when a bounded device-side wait gave up
@@ -102,6 +103,7 @@ void fill_step_tables(const sllbm_ctx* ctx, StepTables<C, P>* t) {
 // Step launchers, one per storage type (step_f32.cu, step_f64.cu).
 int launch_step_f32(sllbm_ctx* ctx, const void* src, void* dst);
 int launch_step_f64(sllbm_ctx* ctx, const void* src, void* dst);
+int launch_step_f16(sllbm_ctx* ctx, const void* src, void* dst);  // both 16-bit deviation types (step_f16.cu)
 
 void fill_step_args(const sllbm_ctx* ctx, const void* src, void* dst, StepArgs* a);
 

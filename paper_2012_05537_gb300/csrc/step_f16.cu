@@ -1,0 +1,22 @@
+// 16-bit deviation storage (IEEE half, bfloat16) / FP32 arithmetic instances of the
+// generic step kernel.
+#include "step_kernel.cuh"
+
+namespace sllbm {
+
+template <typename S>
+int launch_step_dev(sllbm_ctx* ctx, const void* src, void* dst) {
+    switch (ctx->p) {
+    case 2: return launch_step_tiled<S, float, 2, 4, 4, 2, 10>(ctx, src, dst);
+    case 3: return launch_step_tiled<S, float, 3, 2, 2, 2, 10>(ctx, src, dst);
+    case 4: return launch_step_tiled<S, float, 4, 2, 2, 1, 10>(ctx, src, dst);
+    }
+    return SLLBM_EINVAL;
+}
+
+int launch_step_f16(sllbm_ctx* ctx, const void* src, void* dst) {
+    if (ctx->prm.storage == SLLBM_BF16DEV) return launch_step_dev<__nv_bfloat16>(ctx, src, dst);
+    return launch_step_dev<__half>(ctx, src, dst);
+}
+
+}  // namespace sllbm

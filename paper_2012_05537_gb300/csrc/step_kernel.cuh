@@ -19,6 +19,7 @@
 
 #include "collide.cuh"
 #include "sllbm_internal.h"
+#include "storage.cuh"
 
 namespace sllbm {
 
@@ -40,9 +41,106 @@ struct StepSmem {
     static constexpr size_t bytes = (out_elems + NW * warp_elems) * sizeof(C) + NW * warp_ints * sizeof(int);
 };
 
+// A stored value in the arithmetic type (16-bit storage goes through FP32).
+template <typename C, typename S>
+__device__ __forceinline__ C load_as(S v) {
+    if constexpr (PopCodec<S>::kDev)
+        return static_cast<C>(static_cast<float>(v));
+    else
+        return static_cast<C>(v);
+}
+
 __device__ __forceinline__ int wrap_index(int v, int n) {
     int r = v % n;
     return r < 0 ? r + n : r;
+}
+
+// Moments, equilibrium and collision of one node in 16-bit deviation storage: h[q*stride]
+// holds the streamed deviations d_i = f_i/w_i - rho0 (q < 45) and d_gi = g_i/w_i - (2C_v-D)T0
+// rho0 (q >= 45).  rho - rho0, rho u and 2 C_v rho (T - T0) come from deviation sums with the
+// exact quadrature identities sum w = 1, sum w xi = 0, sum w |xi|^2 = D, and the collision is
+// written for the deviations, so that no step subtracts quantities of the reference size:
+//   d_i'  = d_i  + omega (rho (P_i - 1) + (rho - rho0) - d_i),
+//   d_gi' = d_gi + omega ((2C_v-D) (T rho (P_i - 1) + (T - T0) rho + T0 (rho - rho0)) - d_gi),
+// with f_i^eq = w_i rho P_i (Eq. discreteEquilibrium, P_i the quartic in xi_i.u).
+template <typename S, typename C, int P, bool PR>
+__device__ __forceinline__ void collide_node_dev(const C* __restrict__ h, int stride, const StepArgs& a,
+                                                 const StepTables<C, P>& t, S* __restrict__ dst) {
+    C drho = 0, mx = 0, my = 0, mz = 0, se = 0;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const C w = t.w[i];
+        const C wd = w * h[i * stride];
+        drho += wd;
+        mx += wd * t.xi[i][0];
+        my += wd * t.xi[i][1];
+        mz += wd * t.xi[i][2];
+        se += wd * C(shell_xi2(shell_of(i))) + w * h[(kQ + i) * stride];
+    }
+    const C rho0 = C(a.rho0), T0 = C(a.T0);
+    const C rho = rho0 + drho;
+    const C inv_rho = C(1) / rho;
+    const C ux = mx * inv_rho, uy = my * inv_rho, uz = mz * inv_rho;
+    const C usq = ux * ux + uy * uy + uz * uz;
+    const C two_cv = C(1.0 / a.inv_2cv);
+    // 2 C_v rho (T - T0) = sum w (|xi|^2 d + d_g) + D rho0 (1 - T0) - rho |u|^2 - 2 C_v T0 (rho - rho0)
+    const C dT = (se + C(3) * rho0 * (C(1) - T0) - rho * usq - two_cv * T0 * drho) * inv_rho / two_cv;
+    const C T = T0 + dT;
+    if (a.flag != nullptr && !(rho > C(0) && T > C(0) && isfinite(rho) && isfinite(T))) atomicOr(a.flag, 1);
+    const long long nn = a.nn;
+    if (!a.collide) {
+#pragma unroll 9
+        for (int q = 0; q < 2 * kQ; ++q) dst[2 * (q % kQ) * nn + q / kQ] = static_cast<S>(static_cast<float>(h[q * stride]));
+        return;
+    }
+    const C tau = C(a.mu_over_dt) * sutherland(T) / (rho * T) + C(0.5);
+    const C om = C(1) / tau;
+    const C gfac = C(a.gfac);
+    const EqCoef<C> ec = eq_coefficients(usq, T - C(1));
+    // App. D term from the reconstructed f_i = w_i (d_i + rho0), as in collide_node
+    C Qxxx = 0, Qyyy = 0, Qzzz = 0, Qxxy = 0, Qxxz = 0, Qyyx = 0, Qyyz = 0, Qzzx = 0, Qzzy = 0,
+      Qxyz = 0, ompr = 0;
+    if (PR) {
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) {
+            const C f = t.w[i] * (h[i * stride] + rho0);
+            const C cx = t.xi[i][0] - ux, cy = t.xi[i][1] - uy, cz = t.xi[i][2] - uz;
+            const C fx = f * cx, fy = f * cy, fz = f * cz;
+            Qxxx += fx * cx * cx;
+            Qyyy += fy * cy * cy;
+            Qzzz += fz * cz * cz;
+            Qxxy += fx * cx * cy;
+            Qxxz += fx * cx * cz;
+            Qyyx += fy * cy * cx;
+            Qyyz += fy * cy * cz;
+            Qzzx += fz * cz * cx;
+            Qzzy += fz * cz * cy;
+            Qxyz += fx * cy * cz;
+        }
+        const C tau_pr = (tau - C(0.5)) * C(a.inv_pr) + C(0.5);
+        ompr = om - C(1) / tau_pr;
+    }
+    const C qx = Qxxx + Qyyx + Qzzx, qy = Qxxy + Qyyy + Qzzy, qz = Qxxz + Qyyz + Qzzz;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const C x = t.xi[i][0], y = t.xi[i][1], z = t.xi[i][2];
+        const C pm1 = eq_poly(ec, shell_of(i), x * ux + y * uy + z * uz) - C(1);
+        const C d = h[i * stride];
+        const C dg = h[(kQ + i) * stride];
+        C fo = d + om * (rho * pm1 + drho - d);
+        C go = dg + om * (gfac * (T * rho * pm1 + dT * rho + T0 * drho) - dg);
+        if (PR) {
+            const C cub = Qxxx * x * x * x + Qyyy * y * y * y + Qzzz * z * z * z
+                        + C(3) * (Qxxy * x * x * y + Qxxz * x * x * z + Qyyx * y * y * x
+                                  + Qyyz * y * y * z + Qzzx * z * z * x + Qzzy * z * z * y)
+                        + C(6) * Qxyz * x * y * z;
+            const C fst_w = C(1.0 / 6.0) * (cub - C(3) * (x * qx + y * qy + z * qz));  // f*_i / w_i
+            fo += ompr * fst_w;
+            go += ompr * gfac * T * fst_w;
+        }
+        dst[2 * i * nn] = static_cast<S>(static_cast<float>(fo));
+        dst[2 * i * nn + 1] = static_cast<S>(static_cast<float>(go));
+    }
 }
 
 // Moments, equilibrium and collision of one node whose streamed populations are
@@ -50,6 +148,10 @@ __device__ __forceinline__ int wrap_index(int v, int n) {
 template <typename S, typename C, int P, bool PR>
 __device__ __forceinline__ void collide_node(const C* __restrict__ h, int stride, const StepArgs& a,
                                              const StepTables<C, P>& t, S* __restrict__ dst) {
+    if constexpr (PopCodec<S>::kDev) {
+        collide_node_dev<S, C, P, PR>(h, stride, a, t, dst);
+        return;
+    }
     C rho = 0, mx = 0, my = 0, mz = 0, e2 = 0;
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
@@ -176,7 +278,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
             const int r = e - z * sxy;
             const int y = r / s[0];
             const int x = r - y * s[0];
-            box[e] = static_cast<C>(__ldg(sq + 2 * (zo[z] + yo[y] + xo[x])));
+            box[e] = load_as<C>(__ldg(sq + 2 * (zo[z] + yo[y] + xo[x])));
         }
         __syncwarp();
         // z pass: tmp1[oz][y][x] = sum_l Lz[az][l] box[zb+l][y][x]

@@ -17,7 +17,8 @@ import numpy as np
 from . import build as _build
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ENOTREADY = 0, -1, -2, -3, -4, -5, -6
-F64, F32 = 0, 1
+F64, F32, F16DEV, BF16DEV = 0, 1, 2, 3
+STORAGE = {"f64": F64, "f32": F32, "f16dev": F16DEV, "bf16dev": BF16DEV}
 Q = 45
 
 _lib = None
@@ -291,7 +292,7 @@ class Sim:
         else:
             prm.dt_or_courant, prm.dt_is_courant = float(cfg.courant), 1
         prm.pr_correction = int(bool(cfg.pr_correction))
-        prm.storage = {"f64": F64, "f32": F32}[cfg.storage]
+        prm.storage = STORAGE[cfg.storage]
         prm.nonfinite_check = int(bool(cfg.nonfinite_check))
         prm.tgv_C = float(cfg.tgv_C)
         prm.mu_inf_override = float(cfg.mu_inf) if cfg.mu_inf else 0.0
@@ -319,7 +320,8 @@ class Sim:
 
     @property
     def pop_dtype(self):
-        return self.torch.float64 if self.info.storage == F64 else self.torch.float32
+        t = self.torch
+        return {F64: t.float64, F32: t.float32, F16DEV: t.float16, BF16DEV: t.bfloat16}[self.info.storage]
 
     def velset(self):
         return sllbm_velset_table(self.ctx)

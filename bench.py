@@ -2,7 +2,8 @@
 Taylor-Green input.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
-                  [--workload tgv_32c_p4] [--storage f32|f64]
+                  [--workload tgv_32c_p4] [--storage f32|f64|f16dev|bf16dev]
+                  [--mixed-steps 200]
 
 One "step" is one SLLBM time step over the whole mesh: one launch of the fused kernel
 (streaming of all 90 populations, moments, equilibrium, collision).  The default
@@ -10,6 +11,12 @@ workload is the 32^3-cell, p = 4 (128^3 nodes) Taylor-Green vortex at Ma 0.5, Re
 Courant number 4, FP32 storage.  Each population buffer (755 MB) is larger than the
 129 MB L2, so no L2 flush is needed between steps.  With N > 1 (torchrun) every rank
 runs an independent replica (the path is not sharded across GPUs: replicas only).
+
+Beside the headline line's FP64 variant, the "mixed" block runs the 64^3-cell, p = 3
+(192^3 nodes) Taylor-Green vortex at Ma 1.25, Courant number 1 from the same initial state
+in FP64, FP32 and the 16-bit deviation storages for a bounded number of steps and states
+each one's throughput, HBM fraction and relative L2 error against the FP64 GPU run (rho, u,
+T at the end; kinetic-energy and dissipation curves).
 
 --impl reference times the FP64 CPU oracle (tests-only code) on the host cores on a
 bounded sample of the same workload.
@@ -45,10 +52,13 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
     ap.add_argument("--workload", default="tgv_32c_p4", choices=sorted(I.WORKLOADS))
-    ap.add_argument("--storage", choices=["f32", "f64"], default=None)
+    ap.add_argument("--storage", choices=["f32", "f64", "f16dev", "bf16dev"], default=None)
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--mixed-steps", type=int, default=200,
+                    help="steps of the Ma 1.25 mixed-precision comparison (0: skip)")
+    ap.add_argument("--mixed-every", type=int, default=10)
     return ap.parse_args()
 
 
@@ -72,7 +82,8 @@ def measured_peaks():
 def kernel_source_hash() -> str:
     csrc = os.path.join(ROOT, "paper_2012_05537_gb300", "csrc")
     h = hashlib.sha256()
-    for name in ("step_kernel.cuh", "step_tma.cuh", "collide.cuh", "sllbm_internal.h", "step_f32.cu", "step_f64.cu"):
+    for name in ("step_kernel.cuh", "step_tma.cuh", "collide.cuh", "storage.cuh", "sllbm_internal.h",
+                 "step_f32.cu", "step_f64.cu", "step_f16.cu"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -244,6 +255,63 @@ def time_steps(sim, torch, steps, per_launch=True):
     return total_ms, kern
 
 
+ELEM_BYTES = {"f64": 8, "f32": 4, "f16dev": 2, "bf16dev": 2}
+
+
+def rel_l2(a, b):
+    import numpy as np
+
+    den = float(np.linalg.norm(b))
+    return float(np.linalg.norm(a - b)) / den if den > 0 else float(np.linalg.norm(a - b))
+
+
+def mixed_precision_block(S, torch, device, steps, every, hbm):
+    """FP64, FP32 and 16-bit deviation storage on the Ma 1.25 Taylor-Green workload, all from
+    the same initial state, for `steps` steps.  Per storage: median kernel time, node-updates/s,
+    fraction of the HBM peak at its algorithmic bytes, and the relative L2 error against the
+    FP64 GPU run of rho, u, T after the last step and of the E_k(t) and dissipation
+    eps_s(t) + eps_c(t) curves sampled every `every` steps."""
+    import numpy as np
+
+    w = I.WORKLOADS["tgv_64c_p3_ma125"]
+    every = max(1, min(every, steps))
+    chunks = steps // every
+    out = {"workload": w.name, "note": w.note, "steps": chunks * every,
+           "configured_steps": w.steps, "curve_every": every, "reference": "f64 (GPU)"}
+    ref = None
+    for st in ("f64", "f32", "f16dev", "bf16dev"):
+        sim = S.Sim(S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, Pr=w.Pr, gamma=w.gamma,
+                             courant=w.courant, pr_correction=w.pr_correction, storage=st),
+                    device=device)
+        sim.init_tgv()
+        curve = [sim.diag()]
+        kern = []
+        for _ in range(chunks):
+            _, k = time_steps(sim, torch, every)
+            kern.extend(k)
+            curve.append(sim.diag())
+        rho, u, T = (x.cpu().numpy() for x in sim.moments())
+        curve = np.array(curve)
+        ek, eps = curve[:, 0], curve[:, 1] + curve[:, 2]
+        kms = statistics.median(kern)
+        bpn = 2 * 45 * 2 * ELEM_BYTES[st]
+        rec = {"kernel_ms": kms, "value": sim.nodes / (kms / 1e3), "unit": UNIT,
+               "hbm_frac": bpn * sim.nodes / (kms / 1e3) / 1e9 / hbm,
+               "algorithmic_bytes_per_node": bpn, "step_kernel": int(sim.info.step_kernel),
+               "finite": bool(np.isfinite(T).all() and np.isfinite(rho).all())}
+        if ref is None:
+            ref = (rho, u, T, ek, eps, kms)
+            rec["Ek_end"], rec["eps_end"] = float(ek[-1]), float(eps[-1])
+        else:
+            rec["rel_l2"] = {"rho": rel_l2(rho, ref[0]), "u": rel_l2(u, ref[1]),
+                             "T": rel_l2(T, ref[2]), "Ek_curve": rel_l2(ek, ref[3]),
+                             "eps_curve": rel_l2(eps, ref[4])}
+            rec["speedup_vs_f64"] = ref[5] / kms
+        out[st] = rec
+        sim.close()
+    return out
+
+
 def run_mine(args, rank, world, local):
     import torch
 
@@ -290,7 +358,7 @@ def run_mine(args, rank, world, local):
     _, _, T = sim.moments()
     finite = bool(torch.isfinite(T).all().item())
 
-    elem = 8 if storage == "f64" else 4
+    elem = ELEM_BYTES[storage]
     bytes_per_node = 2 * 45 * 2 * elem  # read + write of f and g
     kern_avg_ms = statistics.mean(kern)
     hbm, peak_src = measured_peaks()
@@ -328,6 +396,9 @@ def run_mine(args, rank, world, local):
                            "hbm_gbs_equiv": 2 * 45 * 2 * 8 * nodes / (statistics.mean(k64) / 1e3) / 1e9,
                            "steps": n64}
         sim64.close()
+    if not args.no_variants and rank == 0 and args.mixed_steps > 0:
+        variants["mixed"] = mixed_precision_block(S, torch, f"cuda:{local}", args.mixed_steps,
+                                                  args.mixed_every, hbm)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

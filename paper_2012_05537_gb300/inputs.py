@@ -65,9 +65,14 @@ WORKLOADS = {
     # oracle-size companion of the throughput workload (curves)
     "tgv_16c_p4": Workload("tgv_16c_p4", (16, 16, 16), 4, 0.5, 1600.0, 4.0, 2000, "f64",
                            note="16^3 cells, p=4 (64^3 nodes)"),
-    # shocklet case at higher Mach
-    "tgv_64c_p3_ma125": Workload("tgv_64c_p3_ma125", (64, 64, 64), 3, 1.25, 1600.0, 8.0, 5000,
-                                 "f32", note="64^3 cells, p=3 (192^3 nodes), Ma 1.25, C=8"),
+    # shocklet case at higher Mach (mixed-precision comparison).  BGK at Ma 1.25 is not stable
+    # at Courant 2 and above on this mesh (tau - 1/2 < 0.03 once shocklets form); Courant 1
+    # matches the time step the paper uses for this Mach number (dt* = 0.009 at 256^3 points).
+    "tgv_64c_p3_ma125": Workload("tgv_64c_p3_ma125", (64, 64, 64), 3, 1.25, 1600.0, 1.0, 5000,
+                                 "f32", note="64^3 cells, p=3 (192^3 nodes), Ma 1.25, C=1"),
+    # the same mesh at Courant 8 (departures 2.7 cells away): first-step parity only
+    "tgv_64c_p3_ma125_c8": Workload("tgv_64c_p3_ma125_c8", (64, 64, 64), 3, 1.25, 1600.0, 8.0, 1,
+                                    "f32", note="64^3 cells, p=3, Ma 1.25, C=8 (one step)"),
 }
 
 

@@ -225,7 +225,7 @@ def test_tgv_24cube_50_steps_matches_oracle(S, storage, tol):
 
 
 @pytest.mark.parametrize("name,storage", [("tgv_32c_p4", "f32"), ("tgv_32c_p4", "f64"),
-                                          ("tgv_64c_p3_ma125", "f32")])
+                                          ("tgv_64c_p3_ma125", "f32"), ("tgv_64c_p3_ma125_c8", "f32")])
 def test_full_size_first_step_sampled(S, name, storage):
     """At the benchmark sizes, in the benchmark launch configuration: one step from the
     Taylor-Green state, compared at sampled nodes that the oracle evaluates one by one."""

@@ -16,7 +16,11 @@ Each wrapper cites the passage of the paper its C function follows:
 * :func:`step` -- stream then collide, the stored state being post-collision;
 * :func:`moments` -- Eq. (moments);
 * :func:`tgv_fields` -- Sec. III.C Taylor-Green initial fields;
-* :func:`diag` -- the E_k, eps_s, eps_c definitions of Sec. III.C.
+* :func:`diag` -- the E_k, eps_s, eps_c definitions of Sec. III.C;
+* :func:`stream_adjoint`, :func:`collide_vjp`, :func:`step_adjoint`, :func:`ek_grad`,
+  :func:`init_fields_vjp` -- reverse mode of the above (no counterpart in the paper):
+  the literal transpose of the streaming, and finite-difference (Richardson-extrapolated)
+  Jacobians of the collision and the equilibrium initialisation.
 
 Parity unpinned: agreement of the 45-point set with the paper's own (unprinted) table.
 """
@@ -84,6 +88,10 @@ def _load():
                                                 ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                                 ctypes.POINTER(ctypes.c_long), dp]
             lib.orc_num_threads.restype = ctypes.c_int
+            lib.orc_stream_adjoint.argtypes = [cfgp, ctypes.c_int, ctypes.c_int, dp, dp, dp]
+            lib.orc_collide_vjp.argtypes = [cfgp, dp, dp, dp, dp]
+            lib.orc_ek_grad.argtypes = [cfgp, dp, ctypes.c_double, ctypes.c_double, dp]
+            lib.orc_init_fields_vjp.argtypes = [cfgp, dp, dp, dp, dp, dp, dp, dp]
             _lib = lib
     return _lib
 
@@ -287,3 +295,58 @@ def diag(g: Grid, pop: np.ndarray, rho_ref: float, Re: float, U0: float) -> np.n
     c = g._c()
     _load().orc_diag(ctypes.byref(c), _ptr(pop), float(rho_ref), float(Re), float(U0), _ptr(out))
     return out
+
+
+# ---- reverse mode --------------------------------------------------------------------------
+def stream_adjoint(g: Grid, lam: np.ndarray, xi=None) -> np.ndarray:
+    """S^T lam for the pull streaming S of :func:`stream` (same layout): the literal scatter."""
+    if xi is None:
+        xi, _ = velset()
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    nh, nvel = lam.shape[0], lam.shape[1]
+    assert nvel == len(xi)
+    out = np.empty_like(lam)
+    c = g._c()
+    _load().orc_stream_adjoint(ctypes.byref(c), nh, nvel, _ptr(xi), _ptr(lam), _ptr(out))
+    return out
+
+
+def collide_vjp(g: Grid, h: np.ndarray, lam: np.ndarray):
+    """(J^T lam, lam . d collide/d mu_inf) of the collision at the streamed state h [2,45,...]."""
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    out = np.empty_like(h)
+    dmu = np.zeros(1)
+    c = g._c()
+    _load().orc_collide_vjp(ctypes.byref(c), _ptr(h), _ptr(lam), _ptr(out), _ptr(dmu))
+    return out, float(dmu[0])
+
+
+def step_adjoint(g: Grid, state_prev: np.ndarray, lam_next: np.ndarray):
+    """Adjoint of one :func:`step` taken from state_prev: (lam_prev, d/d mu_inf term)."""
+    h = stream(g, state_prev)
+    mu_h, dmu = collide_vjp(g, h, lam_next)
+    return stream_adjoint(g, mu_h), dmu
+
+
+def ek_grad(g: Grid, pop: np.ndarray, rho_ref: float, U0: float) -> np.ndarray:
+    """d E_k / d pop (E_k as in :func:`diag`), [2,45,Nz,Ny,Nx]; the g half is zero."""
+    pop = np.ascontiguousarray(pop, dtype=np.float64)
+    lam = np.empty_like(pop)
+    c = g._c()
+    _load().orc_ek_grad(ctypes.byref(c), _ptr(pop), float(rho_ref), float(U0), _ptr(lam))
+    return lam
+
+
+def init_fields_vjp(g: Grid, rho, u, T, lam):
+    """Gradients of sum(lam * init_fields(rho, u, T)) with respect to rho, u, T."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    gr, gu, gT = np.empty_like(rho), np.empty_like(u), np.empty_like(T)
+    c = g._c()
+    _load().orc_init_fields_vjp(ctypes.byref(c), _ptr(rho), _ptr(u), _ptr(T), _ptr(lam),
+                                _ptr(gr), _ptr(gu), _ptr(gT))
+    return gr, gu, gT

@@ -658,3 +658,210 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint (reverse mode) of the step.  The paper has no adjoint: each function below is
+ * the transpose of the derivative of a forward function above, built by the plainest
+ * route available, so that it can be checked by eye against its definition:
+ *   - streaming: the literal transpose of orc_stream -- every weight with which a
+ *     support value was gathered is used to scatter the adjoint back to that value;
+ *   - collision: the node-local Jacobian of orc_collide_one (90 inputs and mu_inf) by
+ *     central differences with one Richardson extrapolation step (error O(delta^4)),
+ *     transposed and applied to the adjoint;
+ *   - kinetic energy: the derivative of the E_k quadrature sum of orc_diag, cell by cell;
+ *   - equilibrium initialisation: the Jacobian of orc_feq in (rho, u, T) by the same
+ *     extrapolated central differences.                                                */
+
+/* lam_src = S^T lam_dst, with S = orc_stream (same arguments and layout). */
+void orc_stream_adjoint(const orc_cfg *g, int nh, int nvel, const double *xi,
+                        const double *lam_dst, double *lam_src)
+{
+    const int p = g->p;
+    const int N[3] = {g->cells[0] * p, g->cells[1] * p, g->cells[2] * p};
+    const long nn = (long)N[0] * N[1] * N[2];
+    double *xs[3];
+    int d;
+    for (d = 0; d < 3; ++d) {
+        xs[d] = (double *)malloc(sizeof(double) * N[d]);
+        orc_node_coords(g, d, xs[d]);
+    }
+    memset(lam_src, 0, sizeof(double) * (size_t)nh * nvel * nn);
+    /* one velocity/population slice per thread: the scatter stays inside the slice */
+#pragma omp parallel for schedule(static)
+    for (int hq = 0; hq < nh * nvel; ++hq) {
+        const int i = hq % nvel;
+        const double *in = lam_dst + (long)hq * nn;
+        double *out = lam_src + (long)hq * nn;
+        for (long n = 0; n < nn; ++n) {
+            int node[3], base[3], j, k, l;
+            double ell[3][16];
+            node[0] = (int)(n % N[0]);
+            node[1] = (int)((n / N[0]) % N[1]);
+            node[2] = (int)(n / ((long)N[0] * N[1]));
+            orc_departure(g, xs, node, xi + 3 * i, base, ell);
+            for (l = 0; l <= p; ++l)
+                for (k = 0; k <= p; ++k)
+                    for (j = 0; j <= p; ++j) {
+                        int sx = wrap(base[0] + j, N[0]);
+                        int sy = wrap(base[1] + k, N[1]);
+                        int sz = wrap(base[2] + l, N[2]);
+                        out[((long)sz * N[1] + sy) * N[0] + sx]
+                            += ell[0][j] * ell[1][k] * ell[2][l] * in[n];
+                    }
+        }
+    }
+    for (d = 0; d < 3; ++d) free(xs[d]);
+}
+
+/* Collision of one node as a function of its 90 inputs x = (f_0..f_44, g_0..g_44) and of
+ * mu_inf: y = orc_collide_one(x). */
+static void orc_collide_eval(const orc_cfg *g, const double *xi, const double *w,
+                             const double *x, double mu_inf, double *y)
+{
+    orc_cfg gc = *g;
+    gc.mu_inf = mu_inf;
+    memcpy(y, x, sizeof(double) * 2 * ORC_Q);
+    orc_collide_one(&gc, xi, w, y, y + ORC_Q);
+}
+
+/* Richardson-extrapolated central difference of the collision along input k (k < 90) or
+ * along mu_inf (k == 90): D = (4 D(delta/2) - D(delta)) / 3.                            */
+static void orc_collide_ddir(const orc_cfg *g, const double *xi, const double *w,
+                             const double *x, int k, double delta, double *dy)
+{
+    double xp[2 * ORC_Q], yp[2 * ORC_Q], ym[2 * ORC_Q], d1[2 * ORC_Q];
+    int pass, m;
+    for (pass = 0; pass < 2; ++pass) {
+        const double e = pass == 0 ? delta : 0.5 * delta;
+        double mu_p = g->mu_inf, mu_m = g->mu_inf;
+        memcpy(xp, x, sizeof(xp));
+        if (k < 2 * ORC_Q) xp[k] = x[k] + e; else mu_p = g->mu_inf + e;
+        orc_collide_eval(g, xi, w, xp, mu_p, yp);
+        memcpy(xp, x, sizeof(xp));
+        if (k < 2 * ORC_Q) xp[k] = x[k] - e; else mu_m = g->mu_inf - e;
+        orc_collide_eval(g, xi, w, xp, mu_m, ym);
+        for (m = 0; m < 2 * ORC_Q; ++m) {
+            double dm = (yp[m] - ym[m]) / (2.0 * e);
+            if (pass == 0) d1[m] = dm;
+            else dy[m] = (4.0 * dm - d1[m]) / 3.0;
+        }
+    }
+}
+
+/* Vector-Jacobian product of the collision at every node: for streamed populations h
+ * and the adjoint lam of the collided populations (both [2][45][nodes]), out = J^T lam
+ * with J = d collide / d h, and dmu[0] = sum over nodes of lam . d collide / d mu_inf. */
+void orc_collide_vjp(const orc_cfg *g, const double *h, const double *lam, double *out,
+                     double *dmu)
+{
+    double xi[3 * ORC_Q], w[ORC_Q];
+    const long nn = orc_nodes(g);
+    double total = 0.0;
+    orc_velset(xi, w);
+#pragma omp parallel for reduction(+ : total) schedule(dynamic, 1)
+    for (long n = 0; n < nn; ++n) {
+        double x[2 * ORC_Q], l[2 * ORC_Q], dy[2 * ORC_Q];
+        int k, m;
+        for (k = 0; k < 2 * ORC_Q; ++k) {
+            x[k] = h[(long)k * nn + n];
+            l[k] = lam[(long)k * nn + n];
+        }
+        for (k = 0; k <= 2 * ORC_Q; ++k) {
+            double s = 0.0;
+            orc_collide_ddir(g, xi, w, x, k, k < 2 * ORC_Q ? 1e-4 : 1e-3 * g->mu_inf, dy);
+            for (m = 0; m < 2 * ORC_Q; ++m) s += l[m] * dy[m];
+            if (k < 2 * ORC_Q) out[(long)k * nn + n] = s;
+            else total += s;
+        }
+    }
+    *dmu = total;
+}
+
+/* dE_k / d pop for E_k as orc_diag defines it (out[0] there): the f entries of cell
+ * point n collect w_q (xi_i . u - |u|^2/2) / (|S| rho_ref U0^2) from every cell that has
+ * n as a support point; the g entries are zero.                                        */
+void orc_ek_grad(const orc_cfg *g, const double *pop, double rho_ref, double U0, double *lam)
+{
+    const int p = g->p;
+    const int N[3] = {g->cells[0] * p, g->cells[1] * p, g->cells[2] * p};
+    const long nn = (long)N[0] * N[1] * N[2];
+    double *rho = (double *)malloc(sizeof(double) * nn);
+    double *u = (double *)malloc(sizeof(double) * 3 * nn);
+    double *T = (double *)malloc(sizeof(double) * nn);
+    double xi[3 * ORC_Q], w[ORC_Q], W[16], h[3];
+    const double vol = g->L[0] * g->L[1] * g->L[2];
+    long cell, ncell = (long)g->cells[0] * g->cells[1] * g->cells[2];
+    int d;
+    orc_velset(xi, w);
+    orc_moments(g, pop, rho, u, T);
+    orc_quad_weights(p, W);
+    for (d = 0; d < 3; ++d) h[d] = g->L[d] / g->cells[d];
+    memset(lam, 0, sizeof(double) * 2 * ORC_Q * nn);
+    for (cell = 0; cell < ncell; ++cell) {
+        int cx = (int)(cell % g->cells[0]);
+        int cy = (int)((cell / g->cells[0]) % g->cells[1]);
+        int cz = (int)(cell / ((long)g->cells[0] * g->cells[1]));
+        int ia, ib, ic, i;
+        for (ic = 0; ic <= p; ++ic)
+            for (ib = 0; ib <= p; ++ib)
+                for (ia = 0; ia <= p; ++ia) {
+                    int nx = wrap(cx * p + ia, N[0]), ny = wrap(cy * p + ib, N[1]),
+                        nz = wrap(cz * p + ic, N[2]);
+                    long n = ((long)nz * N[1] + ny) * N[0] + nx;
+                    double wq = W[ia] * W[ib] * W[ic] * h[0] * h[1] * h[2] / 8.0;
+                    double ux = u[n], uy = u[nn + n], uz = u[2 * nn + n];
+                    double usq = ux * ux + uy * uy + uz * uz;
+                    double s = wq / (vol * rho_ref * U0 * U0);
+                    for (i = 0; i < ORC_Q; ++i)
+                        lam[(long)i * nn + n] += s * (xi[3 * i] * ux + xi[3 * i + 1] * uy
+                                                      + xi[3 * i + 2] * uz - 0.5 * usq);
+                }
+    }
+    free(rho); free(u); free(T);
+}
+
+/* Transpose of orc_init_fields: grad_rho[n], grad_u[3][n], grad_T[n] = the derivatives of
+ * sum_i (lam_f_i f_i + lam_g_i g_i) at node n with respect to rho, u, T there, where
+ * f_i = f_i^eq(rho, u, T) and g_i = (2C_v - D) T f_i^eq.                                */
+void orc_init_fields_vjp(const orc_cfg *g, const double *rho, const double *u,
+                         const double *T, const double *lam, double *grad_rho,
+                         double *grad_u, double *grad_T)
+{
+    double xi[3 * ORC_Q], w[ORC_Q];
+    const long nn = orc_nodes(g);
+    const double gfac_c = 2.0 / (g->gamma - 1.0) - 3.0;
+    orc_velset(xi, w);
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < nn; ++n) {
+        double q0[5] = {rho[n], u[n], u[nn + n], u[2 * nn + n], T[n]};
+        double grad[5];
+        int k, pass, i;
+        for (k = 0; k < 5; ++k) {
+            const double delta = 1e-4;
+            double d1 = 0.0, dd = 0.0;
+            for (pass = 0; pass < 2; ++pass) {
+                const double e = pass == 0 ? delta : 0.5 * delta;
+                double qp[5], qm[5], fp[ORC_Q], fm[ORC_Q], s = 0.0;
+                memcpy(qp, q0, sizeof(qp));
+                memcpy(qm, q0, sizeof(qm));
+                qp[k] += e;
+                qm[k] -= e;
+                orc_feq(xi, w, ORC_Q, qp[0], qp + 1, qp[4], fp);
+                orc_feq(xi, w, ORC_Q, qm[0], qm + 1, qm[4], fm);
+                for (i = 0; i < ORC_Q; ++i) {
+                    double lf = lam[(long)i * nn + n], lg = lam[(long)(ORC_Q + i) * nn + n];
+                    s += lf * (fp[i] - fm[i]) + lg * gfac_c * (qp[4] * fp[i] - qm[4] * fm[i]);
+                }
+                s /= 2.0 * e;
+                if (pass == 0) d1 = s;
+                else dd = (4.0 * s - d1) / 3.0;
+            }
+            grad[k] = dd;
+        }
+        grad_rho[n] = grad[0];
+        grad_u[n] = grad[1];
+        grad_u[nn + n] = grad[2];
+        grad_u[2 * nn + n] = grad[3];
+        grad_T[n] = grad[4];
+    }
+}

@@ -213,6 +213,49 @@ int sllbm_run_host(sllbm_ctx *ctx, const void *pop_in, void *pop_out, int n);
 /* Waits for all work the context enqueued. */
 int sllbm_sync(sllbm_ctx *ctx);
 
+/* Copies a state (storage type and order, pop_bytes bytes, device pointer) into the
+ * current buffer and marks the context initialised.  Asynchronous. */
+int sllbm_load_state(sllbm_ctx *ctx, const void *state);
+
+/* Sets mu_inf, the viscosity scale of the Sutherland law, which fixes the relaxation time
+ * tau = mu_inf (mu/mu_inf)(T) / (rho T dt) + 1/2 (Sec. II.A, Sec. III.C) for the following
+ * steps.  SLLBM_EINVAL unless mu_inf > 0. */
+int sllbm_set_mu_inf(sllbm_ctx *ctx, double mu_inf);
+
+/* ---- reverse mode ---------------------------------------------------------------------
+ * The paper has no adjoint.  These calls are the transposes of the derivatives of the
+ * forward operators above, from which gradients of a scalar of the final state through n
+ * steps are assembled (checkpointing is the caller's).  They need SLLBM_F32 or SLLBM_F64
+ * storage and the Prandtl term off (SLLBM_EINVAL otherwise).  Adjoint populations have the
+ * storage type and order of a state buffer, buf[i][z][y][x][h]; every pointer is a device
+ * pointer; calls are asynchronous on the context's stream.  On the first call the context
+ * allocates two state-sized scratch buffers (freed by sllbm_destroy; SLLBM_ENOMEM if that
+ * fails). */
+
+/* dst = S src (transpose == 0) or dst = S^T src: the semi-Lagrangian streaming of all 90
+ * populations alone (Eq. interpolation, pull), or its transpose, as three 1D passes.
+ * src and dst may be the same buffer.  For SLLBM_F32 and SLLBM_F64 storage. */
+int sllbm_stream_apply(sllbm_ctx *ctx, const void *src, void *dst, int transpose);
+
+/* One step backward.  For the step F (pull streaming S, then the BGK collision C of
+ * Eq. LBM at every node) taken from the state state_prev, and lam_next the adjoint of the
+ * state it produced: lam_prev = (dF/dstate)^T lam_next = S^T (dC/dh)^T lam_next at
+ * h = S state_prev, and *dmu += lam_next . dF/dmu_inf (*dmu: one FP64 device scalar,
+ * accumulated).  lam_prev must not alias state_prev or lam_next. */
+int sllbm_adjoint_step(sllbm_ctx *ctx, const void *state_prev, const void *lam_next, void *lam_prev,
+                       double *dmu);
+
+/* lam = dEk/dstate at state, with Ek as sllbm_diag defines and normalises it (the g
+ * entries are zero). */
+int sllbm_ek_adjoint(sllbm_ctx *ctx, const void *state, void *lam);
+
+/* Transpose of sllbm_init_fields (equilibrium populations of the FP64 fields rho[nodes],
+ * u[3][nodes], T[nodes]): grad_rho[n], grad_u[3][nodes], grad_T[n] = derivatives of
+ * sum(lam * init(rho, u, T)) with respect to rho, u, T at node n, FP64 device arrays,
+ * any of the three may be NULL. */
+int sllbm_init_fields_adjoint(sllbm_ctx *ctx, const double *rho, const double *u, const double *T,
+                              const void *lam, double *grad_rho, double *grad_u, double *grad_T);
+
 /* Last CUDA error code seen by the context (cudaError_t as int, 0 if none). */
 int sllbm_last_cuda_error(const sllbm_ctx *ctx);
 

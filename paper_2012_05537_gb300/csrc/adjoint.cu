@@ -1,0 +1,510 @@
+// Reverse mode of the SLLBM step (the paper has no adjoint): the transposes of the
+// derivatives of the forward operators, for FP32 and FP64 storage without the Prandtl term.
+//
+//   * streaming S = S_x S_y S_z per velocity (Eq. interpolation on the uniform mesh: each
+//     1D factor gathers p+1 support values of the departure cell with the precomputed
+//     Lagrange weights).  Its transpose is applied as three 1D passes in gather form: node
+//     m = c p + b receives w[a][b] from every node (c - k_a) p + a, and for b = 0 also
+//     w[a][p] from (c - 1 - k_a) p + a (the right-face support point of the cell to the
+//     left).  No atomics, each output written once.
+//   * collision (Eq. LBM with Eq. moments, Eq. discreteEquilibrium in its quartic form,
+//     tau = mu/(P dt) + 1/2, Sutherland mu): a node-local vector-Jacobian product through
+//     the primitive variables rho, u, T and omega, derived by hand below.
+//   * kinetic-energy seed and the transpose of the equilibrium initialisation.
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "collide.cuh"
+#include "sllbm_internal.h"
+#include "tables.h"
+
+namespace sllbm {
+
+namespace {
+
+struct AdjVel {
+    double xi[kQ][3];
+    double w[kQ];
+};
+
+template <typename C>
+struct PassTable {
+    int shift[kQ][kMaxP];
+    C w[kQ][kMaxP][kMaxP + 1];
+};
+
+template <typename C>
+struct Pair;
+template <>
+struct Pair<float> {
+    using T = float2;
+};
+template <>
+struct Pair<double> {
+    using T = double2;
+};
+
+__device__ __forceinline__ int wrap_mod(int v, int n) {
+    const int r = v % n;
+    return r < 0 ? r + n : r;
+}
+
+// One 1D streaming pass along direction d on pairs (f_i, g_i) in the storage order
+// [i][z][y][x][h]: forward (TR = false) out(n) = sum_j w[i][a][j] in((c + k_a) p + j), or its
+// transpose (TR = true) as described at the top of the file.
+template <typename C, bool TR>
+__global__ void __launch_bounds__(256) pass_kernel(const C* __restrict__ in, C* __restrict__ out, int Nx, int Ny,
+                                                   int d, int p, int cells_d, long long nn,
+                                                   const __grid_constant__ PassTable<C> t) {
+    using P2 = typename Pair<C>::T;
+    const P2* src = reinterpret_cast<const P2*>(in);
+    P2* dst = reinterpret_cast<P2*>(out);
+    const long long total = static_cast<long long>(kQ) * nn;
+    const long long sxy = static_cast<long long>(Nx) * Ny;
+    for (long long k = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; k < total;
+         k += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int i = static_cast<int>(k / nn);
+        const long long n = k - static_cast<long long>(i) * nn;
+        const int x = static_cast<int>(n % Nx);
+        const int y = static_cast<int>((n / Nx) % Ny);
+        const int z = static_cast<int>(n / sxy);
+        const int coord = d == 0 ? x : (d == 1 ? y : z);
+        const long long stride = d == 0 ? 1 : (d == 1 ? Nx : sxy);
+        const long long base = static_cast<long long>(i) * nn + (n - coord * stride);
+        const int c = coord / p, a = coord - c * p;
+        C af = 0, ag = 0;
+        if (!TR) {
+            const int c0 = wrap_mod(c + t.shift[i][a], cells_d);
+            for (int j = 0; j <= p; ++j) {
+                int m = c0 * p + j;
+                if (m >= cells_d * p) m -= cells_d * p;
+                const P2 v = src[base + m * stride];
+                const C wj = t.w[i][a][j];
+                af += wj * v.x;
+                ag += wj * v.y;
+            }
+        } else {
+            // here (c, a) is the receiving node: cell c, local index b = a
+            const int b = a;
+            for (int q = 0; q < p; ++q) {
+                const int cs = wrap_mod(c - t.shift[i][q], cells_d);
+                const P2 v = src[base + static_cast<long long>(cs * p + q) * stride];
+                const C wq = t.w[i][q][b];
+                af += wq * v.x;
+                ag += wq * v.y;
+                if (b == 0) {
+                    const int cs1 = wrap_mod(c - 1 - t.shift[i][q], cells_d);
+                    const P2 v1 = src[base + static_cast<long long>(cs1 * p + q) * stride];
+                    const C wp = t.w[i][q][p];
+                    af += wp * v1.x;
+                    ag += wp * v1.y;
+                }
+            }
+        }
+        P2 r;
+        r.x = af;
+        r.y = ag;
+        dst[k] = r;
+    }
+}
+
+// Derivatives of the quartic f^eq/(w rho) = c0 + c1 s + c2 s^2 + s^3/6 + s^4/24 of
+// collide.cuh with respect to s = xi.u, |u|^2 and th = T - 1 (from the closed forms of c0,
+// c1, c2 there).
+template <typename C>
+struct PolyDeriv {
+    C P, ds, dusq, dth;
+};
+
+template <typename C>
+__device__ __forceinline__ PolyDeriv<C> poly_deriv(const EqCoef<C>& ec, int sh, C s, C usq, C th) {
+    const C x2 = C(shell_xi2(sh));
+    PolyDeriv<C> r;
+    r.P = eq_poly(ec, sh, s);
+    r.ds = ec.c1[sh] + s * (C(2) * ec.c2[sh] + s * (C(0.5) + s * C(1.0 / 6.0)));
+    r.dusq = (C(-0.5) + C(0.25) * usq + C(0.25) * th * (C(5) - x2)) - C(0.5) * s - C(0.25) * s * s;
+    r.dth = (C(0.5) * (x2 - C(3)) + C(0.25) * usq * (C(5) - x2)
+             + C(0.25) * th * (x2 * x2 - C(10) * x2 + C(15)))
+          + C(0.5) * (x2 - C(5)) * s + C(0.25) * (x2 - C(7)) * s * s;
+    return r;
+}
+
+struct AdjArgs {
+    double mu_over_dt;  // K = mu_inf / dt
+    double inv_dt;
+    double inv_2cv;
+    double gfac;
+};
+
+// Per node: h = streamed populations (pairs), lam = adjoint of the collided populations;
+// out = J^T lam, and the block's share of lam . d collide / d mu_inf in partials[block].
+//
+// Forward (per node):  rho = sum f, j = sum f xi, E2 = sum (f |xi|^2 + g),
+//   u = j/rho, T = (E2/rho - |u|^2)/(2 C_v), tau = K su(T)/(rho T) + 1/2, omega = 1/tau,
+//   f^eq_i = w_i rho P_i(xi_i.u, |u|^2, T-1), g^eq_i = (2C_v - D) T f^eq_i,
+//   f_i' = f_i + omega (f^eq_i - f_i), g_i' = g_i + omega (g^eq_i - g_i).
+// Reverse: with B = sum lam . (h^eq - h), the adjoint reaching f^eq_i is
+//   A_i = omega (lam_f_i + (2C_v - D) T lam_g_i), T also appears in g^eq explicitly,
+//   omega depends on rho and T (and mu_inf); the primitive adjoints are mapped back to the
+//   moments (rho, j, E2) and from there to the populations.
+template <typename C>
+__global__ void __launch_bounds__(128) collide_vjp_kernel(const C* __restrict__ h, const C* __restrict__ lam,
+                                                          C* __restrict__ out, long long nn, AdjArgs aa,
+                                                          const __grid_constant__ AdjVel v,
+                                                          double* __restrict__ partials) {
+    __shared__ double red[4];
+    double dmu_acc = 0.0;
+    const C gfac = C(aa.gfac), inv_2cv = C(aa.inv_2cv), K = C(aa.mu_over_dt);
+    for (long long n = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; n < nn;
+         n += static_cast<long long>(gridDim.x) * blockDim.x) {
+        C rho = 0, jx = 0, jy = 0, jz = 0, E2 = 0;
+        for (int i = 0; i < kQ; ++i) {
+            const C f = h[2 * (i * nn + n)], g = h[2 * (i * nn + n) + 1];
+            rho += f;
+            jx += f * C(v.xi[i][0]);
+            jy += f * C(v.xi[i][1]);
+            jz += f * C(v.xi[i][2]);
+            E2 += f * C(shell_xi2(shell_of(i))) + g;
+        }
+        const C ux = jx / rho, uy = jy / rho, uz = jz / rho;
+        const C usq = ux * ux + uy * uy + uz * uz;
+        const C T = (E2 / rho - usq) * inv_2cv;
+        const C th = T - C(1);
+        const C su = sutherland(T);
+        const C tau = K * su / (rho * T) + C(0.5);
+        const C om = C(1) / tau;
+        const EqCoef<C> ec = eq_coefficients(usq, th);
+        C B = 0, ATd = 0, arho = 0, aux = 0, auy = 0, auz = 0, ausq = 0, ath = 0;
+        for (int i = 0; i < kQ; ++i) {
+            const int sh = shell_of(i);
+            const C x = C(v.xi[i][0]), y = C(v.xi[i][1]), z = C(v.xi[i][2]), w = C(v.w[i]);
+            const C s = x * ux + y * uy + z * uz;
+            const PolyDeriv<C> pd = poly_deriv(ec, sh, s, usq, th);
+            const C feq = w * rho * pd.P, geq = gfac * T * feq;
+            const C lf = lam[2 * (i * nn + n)], lg = lam[2 * (i * nn + n) + 1];
+            const C hf = h[2 * (i * nn + n)], hg = h[2 * (i * nn + n) + 1];
+            B += lf * (feq - hf) + lg * (geq - hg);
+            const C A = om * (lf + gfac * T * lg);
+            ATd += om * gfac * lg * feq;
+            const C Aw = A * w;
+            arho += Aw * pd.P;
+            const C t = Aw * rho * pd.ds;
+            aux += t * x;
+            auy += t * y;
+            auz += t * z;
+            ausq += Aw * rho * pd.dusq;
+            ath += Aw * rho * pd.dth;
+        }
+        // omega = 1/tau: d omega/d tau = -omega^2; d ln su/dT = 3/(2T) - 1/(T + S)
+        const C dom = -om * om;
+        const C dtau_drho = -K * su / (rho * rho * T);
+        const C dtau_dT = K * su / (rho * T) * (sutherland_dlog(T) - C(1) / T);
+        dmu_acc += static_cast<double>(B * dom * su / (rho * T)) * aa.inv_dt;
+        C Arho = arho + B * dom * dtau_drho;
+        const C AT = ath + ATd + B * dom * dtau_dT;
+        C Aux = aux + C(2) * ux * ausq, Auy = auy + C(2) * uy * ausq, Auz = auz + C(2) * uz * ausq;
+        // T = (E2/rho - |u|^2)/(2 C_v)
+        const C AE2 = AT * inv_2cv / rho;
+        Arho -= AT * inv_2cv * E2 / (rho * rho);
+        Aux -= C(2) * AT * inv_2cv * ux;
+        Auy -= C(2) * AT * inv_2cv * uy;
+        Auz -= C(2) * AT * inv_2cv * uz;
+        // u = j/rho
+        const C Ajx = Aux / rho, Ajy = Auy / rho, Ajz = Auz / rho;
+        Arho -= (Aux * ux + Auy * uy + Auz * uz) / rho;
+        const C keep = C(1) - om;
+        for (int i = 0; i < kQ; ++i) {
+            const C x = C(v.xi[i][0]), y = C(v.xi[i][1]), z = C(v.xi[i][2]);
+            const C lf = lam[2 * (i * nn + n)], lg = lam[2 * (i * nn + n) + 1];
+            out[2 * (i * nn + n)] =
+                keep * lf + Arho + Ajx * x + Ajy * y + Ajz * z + AE2 * C(shell_xi2(shell_of(i)));
+            out[2 * (i * nn + n) + 1] = keep * lg + AE2;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dmu_acc += __shfl_down_sync(0xffffffffu, dmu_acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dmu_acc;
+    __syncthreads();
+    if (threadIdx.x == 0) partials[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
+}
+
+// *acc += sum of partials[0..n) in a fixed order (one block).
+__global__ void accumulate_kernel(const double* __restrict__ partials, int n, double* __restrict__ acc) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) s += partials[b];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *acc += red[0];
+}
+
+// Seed of E_k = (1/(|S| rho0 U0^2)) sum_cells sum_points w_q rho |u|^2 / 2 (the sllbm_diag
+// quadrature): dE_k/df_i(n) = W_n (xi_i.u - |u|^2/2), dE_k/dg_i = 0, with W_n the node's
+// total quadrature weight: prod_d W1[a_d] times scale, W1[a] = W_a (+ W_p for a = 0, the
+// node being the right-face point of the neighbouring cell as well).
+struct EkConst {
+    double xi[kQ][3];
+    double W1[kMaxP];
+};
+
+template <typename C>
+__global__ void __launch_bounds__(128) ek_seed_kernel(const C* __restrict__ pop, C* __restrict__ lam, long long nn,
+                                                      int Nx, int Ny, int p, double scale,
+                                                      const __grid_constant__ EkConst kc) {
+    const long long sxy = static_cast<long long>(Nx) * Ny;
+    for (long long n = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; n < nn;
+         n += static_cast<long long>(gridDim.x) * blockDim.x) {
+        double rho = 0, jx = 0, jy = 0, jz = 0;
+        for (int i = 0; i < kQ; ++i) {
+            const double f = pop[2 * (i * nn + n)];
+            rho += f;
+            jx += f * kc.xi[i][0];
+            jy += f * kc.xi[i][1];
+            jz += f * kc.xi[i][2];
+        }
+        const double ux = jx / rho, uy = jy / rho, uz = jz / rho;
+        const double half_usq = 0.5 * (ux * ux + uy * uy + uz * uz);
+        const int x = static_cast<int>(n % Nx), y = static_cast<int>((n / Nx) % Ny),
+                  z = static_cast<int>(n / sxy);
+        const double wn = kc.W1[x % p] * kc.W1[y % p] * kc.W1[z % p] * scale;
+        for (int i = 0; i < kQ; ++i) {
+            lam[2 * (i * nn + n)] = static_cast<C>(wn * (kc.xi[i][0] * ux + kc.xi[i][1] * uy + kc.xi[i][2] * uz - half_usq));
+            lam[2 * (i * nn + n) + 1] = C(0);
+        }
+    }
+}
+
+// Transpose of the equilibrium initialisation f_i = w_i rho P_i, g_i = (2C_v - D) T f_i at
+// each node (FP64 arithmetic, as the initialisation itself).
+template <typename C>
+__global__ void __launch_bounds__(128) init_vjp_kernel(const double* __restrict__ rho_f, const double* __restrict__ u_f,
+                                                       const double* __restrict__ T_f, const C* __restrict__ lam,
+                                                       long long nn, double gfac, const __grid_constant__ AdjVel v,
+                                                       double* __restrict__ g_rho, double* __restrict__ g_u,
+                                                       double* __restrict__ g_T) {
+    for (long long n = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; n < nn;
+         n += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const double rho = rho_f[n], ux = u_f[n], uy = u_f[nn + n], uz = u_f[2 * nn + n], T = T_f[n];
+        const double usq = ux * ux + uy * uy + uz * uz, th = T - 1.0;
+        const EqCoef<double> ec = eq_coefficients(usq, th);
+        double arho = 0, aux = 0, auy = 0, auz = 0, ausq = 0, ath = 0, ATd = 0;
+        for (int i = 0; i < kQ; ++i) {
+            const double x = v.xi[i][0], y = v.xi[i][1], z = v.xi[i][2], w = v.w[i];
+            const PolyDeriv<double> pd = poly_deriv(ec, shell_of(i), x * ux + y * uy + z * uz, usq, th);
+            const double lf = static_cast<double>(lam[2 * (i * nn + n)]);
+            const double lg = static_cast<double>(lam[2 * (i * nn + n) + 1]);
+            const double Aw = (lf + gfac * T * lg) * w;
+            ATd += gfac * lg * w * rho * pd.P;
+            arho += Aw * pd.P;
+            const double t = Aw * rho * pd.ds;
+            aux += t * x;
+            auy += t * y;
+            auz += t * z;
+            ausq += Aw * rho * pd.dusq;
+            ath += Aw * rho * pd.dth;
+        }
+        if (g_rho) g_rho[n] = arho;
+        if (g_u) {
+            g_u[n] = aux + 2.0 * ux * ausq;
+            g_u[nn + n] = auy + 2.0 * uy * ausq;
+            g_u[2 * nn + n] = auz + 2.0 * uz * ausq;
+        }
+        if (g_T) g_T[n] = ath + ATd;
+    }
+}
+
+unsigned adj_grid(long long n, int block) {
+    long long g = (n + block - 1) / block;
+    if (g > 65536) g = 65536;
+    return static_cast<unsigned>(g < 1 ? 1 : g);
+}
+
+AdjVel adj_vel(const sllbm_ctx* ctx) {
+    AdjVel v;
+    std::memcpy(v.xi, ctx->xi, sizeof(v.xi));
+    std::memcpy(v.w, ctx->w, sizeof(v.w));
+    return v;
+}
+
+template <typename C>
+PassTable<C> pass_table(const sllbm_ctx* ctx, int d) {
+    PassTable<C> t;
+    std::memset(&t, 0, sizeof(t));
+    for (int i = 0; i < kQ; ++i)
+        for (int a = 0; a < ctx->p; ++a) {
+            t.shift[i][a] = ctx->dir[d].shift[i][a];
+            for (int j = 0; j <= ctx->p; ++j) t.w[i][a][j] = static_cast<C>(ctx->dir[d].weight[i][a][j]);
+        }
+    return t;
+}
+
+int adj_fail(sllbm_ctx* ctx, cudaError_t e) {
+    ctx->last_err = static_cast<int>(e);
+    return SLLBM_ECUDA;
+}
+
+}  // namespace
+
+// Two state-sized scratch buffers and the per-block partials of the mu_inf sensitivity,
+// allocated on the first reverse-mode call.
+int ensure_adjoint_scratch(sllbm_ctx* ctx) {
+    if (ctx->adj_buf[0] != nullptr) return SLLBM_OK;
+    ctx->adj_blocks = static_cast<int>(adj_grid(ctx->nn, 128));
+    if (ctx->adj_blocks > 2048) ctx->adj_blocks = 2048;
+    cudaError_t e = cudaMalloc(&ctx->adj_buf[0], ctx->pop_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->adj_buf[1], ctx->pop_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_adj_partials, sizeof(double) * ctx->adj_blocks);
+    if (e != cudaSuccess) {
+        adjoint_release(ctx);
+        ctx->last_err = static_cast<int>(e);
+        return SLLBM_ENOMEM;
+    }
+    return SLLBM_OK;
+}
+
+void adjoint_release(sllbm_ctx* ctx) {
+    cudaFree(ctx->adj_buf[0]);
+    cudaFree(ctx->adj_buf[1]);
+    cudaFree(ctx->d_adj_partials);
+    ctx->adj_buf[0] = ctx->adj_buf[1] = nullptr;
+    ctx->d_adj_partials = nullptr;
+}
+
+namespace {
+
+bool adjoint_supported(const sllbm_ctx* ctx) {
+    return (ctx->prm.storage == SLLBM_F32 || ctx->prm.storage == SLLBM_F64) && !ctx->prm.pr_correction &&
+           ctx->prm.collide;
+}
+
+template <typename C>
+int launch_pass(sllbm_ctx* ctx, const void* in, void* out, int d, bool transpose) {
+    const PassTable<C> t = pass_table<C>(ctx, d);
+    const unsigned grid = adj_grid(static_cast<long long>(kQ) * ctx->nn, 256);
+    if (transpose)
+        pass_kernel<C, true><<<grid, 256, 0, ctx->stream>>>(static_cast<const C*>(in), static_cast<C*>(out),
+                                                            ctx->N[0], ctx->N[1], d, ctx->p, ctx->cells[d],
+                                                            ctx->nn, t);
+    else
+        pass_kernel<C, false><<<grid, 256, 0, ctx->stream>>>(static_cast<const C*>(in), static_cast<C*>(out),
+                                                             ctx->N[0], ctx->N[1], d, ctx->p, ctx->cells[d],
+                                                             ctx->nn, t);
+    ctx->launches += 1;
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SLLBM_OK : adj_fail(ctx, e);
+}
+
+// dst = S src (transpose = false) or S^T src, through the two scratch buffers.
+template <typename C>
+int stream_apply_t(sllbm_ctx* ctx, const void* src, void* dst, bool transpose) {
+    void* a = ctx->adj_buf[0];
+    void* b = ctx->adj_buf[1];
+    int rc = launch_pass<C>(ctx, src, a, 2, transpose);
+    if (rc == SLLBM_OK) rc = launch_pass<C>(ctx, a, b, 1, transpose);
+    if (rc == SLLBM_OK) rc = launch_pass<C>(ctx, b, dst, 0, transpose);
+    return rc;
+}
+
+template <typename C>
+int adjoint_step_t(sllbm_ctx* ctx, const void* state_prev, const void* lam_next, void* lam_prev, double* dmu) {
+    void* a = ctx->adj_buf[0];
+    void* b = ctx->adj_buf[1];
+    // h = S state_prev (the populations the step's collision saw)
+    int rc = launch_pass<C>(ctx, state_prev, a, 2, false);
+    if (rc == SLLBM_OK) rc = launch_pass<C>(ctx, a, b, 1, false);
+    if (rc == SLLBM_OK) rc = launch_pass<C>(ctx, b, a, 0, false);
+    if (rc != SLLBM_OK) return rc;
+    // b = (d collide / d h)^T lam_next at h; mu_inf sensitivity into *dmu
+    AdjArgs aa;
+    aa.mu_over_dt = ctx->mu_inf / ctx->dt;
+    aa.inv_dt = 1.0 / ctx->dt;
+    aa.inv_2cv = 0.5 * (ctx->prm.gamma - 1.0);
+    aa.gfac = 2.0 / (ctx->prm.gamma - 1.0) - 3.0;
+    collide_vjp_kernel<C><<<ctx->adj_blocks, 128, 0, ctx->stream>>>(
+        static_cast<const C*>(a), static_cast<const C*>(lam_next), static_cast<C*>(b), ctx->nn, aa, adj_vel(ctx),
+        ctx->d_adj_partials);
+    accumulate_kernel<<<1, 256, 0, ctx->stream>>>(ctx->d_adj_partials, ctx->adj_blocks, dmu);
+    ctx->launches += 2;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return adj_fail(ctx, e);
+    // lam_prev = S^T b
+    rc = launch_pass<C>(ctx, b, a, 0, true);
+    if (rc == SLLBM_OK) rc = launch_pass<C>(ctx, a, b, 1, true);
+    if (rc == SLLBM_OK) rc = launch_pass<C>(ctx, b, lam_prev, 2, true);
+    return rc;
+}
+
+}  // namespace
+
+}  // namespace sllbm
+
+using namespace sllbm;
+
+extern "C" {
+
+int sllbm_stream_apply(sllbm_ctx* ctx, const void* src, void* dst, int transpose) {
+    if (ctx == nullptr || src == nullptr || dst == nullptr) return SLLBM_EINVAL;
+    if (ctx->prm.storage != SLLBM_F32 && ctx->prm.storage != SLLBM_F64) return SLLBM_EINVAL;
+    int rc = ensure_adjoint_scratch(ctx);
+    if (rc != SLLBM_OK) return rc;
+    return ctx->prm.storage == SLLBM_F64 ? stream_apply_t<double>(ctx, src, dst, transpose != 0)
+                                         : stream_apply_t<float>(ctx, src, dst, transpose != 0);
+}
+
+int sllbm_adjoint_step(sllbm_ctx* ctx, const void* state_prev, const void* lam_next, void* lam_prev, double* dmu) {
+    if (ctx == nullptr || state_prev == nullptr || lam_next == nullptr || lam_prev == nullptr || dmu == nullptr)
+        return SLLBM_EINVAL;
+    if (!adjoint_supported(ctx)) return SLLBM_EINVAL;
+    if (lam_prev == state_prev || lam_prev == lam_next) return SLLBM_EINVAL;
+    int rc = ensure_adjoint_scratch(ctx);
+    if (rc != SLLBM_OK) return rc;
+    return ctx->prm.storage == SLLBM_F64 ? adjoint_step_t<double>(ctx, state_prev, lam_next, lam_prev, dmu)
+                                         : adjoint_step_t<float>(ctx, state_prev, lam_next, lam_prev, dmu);
+}
+
+int sllbm_ek_adjoint(sllbm_ctx* ctx, const void* state, void* lam) {
+    if (ctx == nullptr || state == nullptr || lam == nullptr) return SLLBM_EINVAL;
+    if (!adjoint_supported(ctx)) return SLLBM_EINVAL;
+    EkConst kc;
+    std::memcpy(kc.xi, ctx->xi, sizeof(kc.xi));
+    double W[kMaxP + 1];
+    clenshaw_curtis(ctx->p, W);
+    for (int a = 0; a < kMaxP; ++a) kc.W1[a] = a < ctx->p ? W[a] + (a == 0 ? W[ctx->p] : 0.0) : 0.0;
+    const double vol = ctx->L[0] * ctx->L[1] * ctx->L[2];
+    const double scale = ctx->h[0] * ctx->h[1] * ctx->h[2] * 0.125 / (vol * ctx->prm.rho0 * ctx->U0 * ctx->U0);
+    const unsigned grid = adj_grid(ctx->nn, 128);
+    if (ctx->prm.storage == SLLBM_F64)
+        ek_seed_kernel<double><<<grid, 128, 0, ctx->stream>>>(static_cast<const double*>(state),
+                                                              static_cast<double*>(lam), ctx->nn, ctx->N[0],
+                                                              ctx->N[1], ctx->p, scale, kc);
+    else
+        ek_seed_kernel<float><<<grid, 128, 0, ctx->stream>>>(static_cast<const float*>(state), static_cast<float*>(lam),
+                                                             ctx->nn, ctx->N[0], ctx->N[1], ctx->p, scale, kc);
+    ctx->launches += 1;
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SLLBM_OK : adj_fail(ctx, e);
+}
+
+int sllbm_init_fields_adjoint(sllbm_ctx* ctx, const double* rho, const double* u, const double* T, const void* lam,
+                              double* grad_rho, double* grad_u, double* grad_T) {
+    if (ctx == nullptr || rho == nullptr || u == nullptr || T == nullptr || lam == nullptr) return SLLBM_EINVAL;
+    if (!adjoint_supported(ctx)) return SLLBM_EINVAL;
+    const double gfac = 2.0 / (ctx->prm.gamma - 1.0) - 3.0;
+    const unsigned grid = adj_grid(ctx->nn, 128);
+    if (ctx->prm.storage == SLLBM_F64)
+        init_vjp_kernel<double><<<grid, 128, 0, ctx->stream>>>(rho, u, T, static_cast<const double*>(lam), ctx->nn,
+                                                               gfac, adj_vel(ctx), grad_rho, grad_u, grad_T);
+    else
+        init_vjp_kernel<float><<<grid, 128, 0, ctx->stream>>>(rho, u, T, static_cast<const float*>(lam), ctx->nn,
+                                                              gfac, adj_vel(ctx), grad_rho, grad_u, grad_T);
+    ctx->launches += 1;
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SLLBM_OK : adj_fail(ctx, e);
+}
+
+}  // extern "C"

@@ -554,6 +554,7 @@ void sllbm_destroy(sllbm_ctx* ctx) {
     for (int d = 0; d < 3; ++d) cudaFree(ctx->d_coords[d]);
     cudaFree(ctx->d_flag);
     cudaFree(ctx->d_partials);
+    adjoint_release(ctx);
     std::free(ctx->step_blob);
     std::free(ctx);
 }
@@ -715,6 +716,22 @@ int sllbm_step(sllbm_ctx* ctx, int n) {
         }
         if (flags[0]) return SLLBM_ENONFINITE;
     }
+    return SLLBM_OK;
+}
+
+int sllbm_load_state(sllbm_ctx* ctx, const void* state) {
+    if (ctx == nullptr || state == nullptr) return SLLBM_EINVAL;
+    int rc = ensure_buffers(ctx);
+    if (rc != SLLBM_OK) return rc;
+    if (state != ctx->buf[ctx->cur])
+        CK(ctx, cudaMemcpyAsync(ctx->buf[ctx->cur], state, ctx->pop_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->initialised = true;
+    return SLLBM_OK;
+}
+
+int sllbm_set_mu_inf(sllbm_ctx* ctx, double mu_inf) {
+    if (ctx == nullptr || !(mu_inf > 0.0)) return SLLBM_EINVAL;
+    ctx->mu_inf = mu_inf;
     return SLLBM_OK;
 }
 

@@ -52,4 +52,10 @@ __device__ __forceinline__ C sutherland(C T) {
     return C(1.4042) * T * sqrt(T) / (T + C(0.40417));
 }
 
+// d ln(mu/mu_inf) / dT of the same law: 3/(2T) - 1/(T + 0.40417).
+template <typename C>
+__device__ __forceinline__ C sutherland_dlog(C T) {
+    return C(1.5) / T - C(1) / (T + C(0.40417));
+}
+
 }  // namespace sllbm

@@ -43,6 +43,9 @@ struct sllbm_ctx {
     const void* tmap_src[2];
     int last_err;
     long long launches;
+    void* adj_buf[2];          // reverse-mode scratch (state-sized), allocated on first use
+    double* d_adj_partials;    // per-block partials of the mu_inf sensitivity
+    int adj_blocks;
 };
 
 namespace sllbm {
@@ -109,5 +112,9 @@ void fill_step_args(const sllbm_ctx* ctx, const void* src, void* dst, StepArgs* 
 
 // True when the TMA-fed FP32 kernel can run this context (step_f32.cu).
 bool tma_step_eligible(const sllbm_ctx* c);
+
+// Reverse-mode scratch of a context (adjoint.cu): allocation on first use, release.
+int ensure_adjoint_scratch(sllbm_ctx* ctx);
+void adjoint_release(sllbm_ctx* ctx);
 
 }  // namespace sllbm

@@ -70,6 +70,9 @@ WORKLOADS = {
     # matches the time step the paper uses for this Mach number (dt* = 0.009 at 256^3 points).
     "tgv_64c_p3_ma125": Workload("tgv_64c_p3_ma125", (64, 64, 64), 3, 1.25, 1600.0, 1.0, 5000,
                                  "f32", note="64^3 cells, p=3 (192^3 nodes), Ma 1.25, C=1"),
+    # reverse-mode workload: gradients of the final kinetic energy through 200 steps
+    "tgv_16c_p3_adj": Workload("tgv_16c_p3_adj", (16, 16, 16), 3, 0.5, 1600.0, 2.0, 200, "f32",
+                               note="16^3 cells, p=3 (48^3 nodes), Ma 0.5, C=2, 200 steps"),
     # the same mesh at Courant 8 (departures 2.7 cells away): first-step parity only
     "tgv_64c_p3_ma125_c8": Workload("tgv_64c_p3_ma125_c8", (64, 64, 64), 3, 1.25, 1600.0, 8.0, 1,
                                     "f32", note="64^3 cells, p=3, Ma 1.25, C=8 (one step)"),

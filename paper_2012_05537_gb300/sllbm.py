@@ -97,6 +97,12 @@ def load(build_if_missing: bool = False):
         "sllbm_velset_d3q45": (ctypes.c_int, [dp, dp]),
         "sllbm_stream_table": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]),
+        "sllbm_load_state": (ctypes.c_int, [vp, vp]),
+        "sllbm_set_mu_inf": (ctypes.c_int, [vp, ctypes.c_double]),
+        "sllbm_stream_apply": (ctypes.c_int, [vp, vp, vp, ctypes.c_int]),
+        "sllbm_adjoint_step": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+        "sllbm_ek_adjoint": (ctypes.c_int, [vp, vp, vp]),
+        "sllbm_init_fields_adjoint": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -246,6 +252,39 @@ def sllbm_launch_count(ctx) -> int:
     return int(load().sllbm_launch_count(ctx))
 
 
+def sllbm_load_state(ctx, state_ptr: int) -> None:
+    _check(load().sllbm_load_state(ctx, ctypes.c_void_p(state_ptr)), "sllbm_load_state", ctx)
+
+
+def sllbm_set_mu_inf(ctx, mu_inf: float) -> None:
+    _check(load().sllbm_set_mu_inf(ctx, float(mu_inf)), "sllbm_set_mu_inf", ctx)
+
+
+def sllbm_stream_apply(ctx, src_ptr: int, dst_ptr: int, transpose: bool) -> None:
+    _check(load().sllbm_stream_apply(ctx, ctypes.c_void_p(src_ptr), ctypes.c_void_p(dst_ptr),
+                                     int(bool(transpose))), "sllbm_stream_apply", ctx)
+
+
+def sllbm_adjoint_step(ctx, state_prev_ptr: int, lam_next_ptr: int, lam_prev_ptr: int,
+                       dmu_ptr: int) -> None:
+    _check(load().sllbm_adjoint_step(ctx, ctypes.c_void_p(state_prev_ptr), ctypes.c_void_p(lam_next_ptr),
+                                     ctypes.c_void_p(lam_prev_ptr), ctypes.c_void_p(dmu_ptr)),
+           "sllbm_adjoint_step", ctx)
+
+
+def sllbm_ek_adjoint(ctx, state_ptr: int, lam_ptr: int) -> None:
+    _check(load().sllbm_ek_adjoint(ctx, ctypes.c_void_p(state_ptr), ctypes.c_void_p(lam_ptr)),
+           "sllbm_ek_adjoint", ctx)
+
+
+def sllbm_init_fields_adjoint(ctx, rho_ptr: int, u_ptr: int, T_ptr: int, lam_ptr: int,
+                              grad_rho_ptr: int, grad_u_ptr: int, grad_T_ptr: int) -> None:
+    vp = ctypes.c_void_p
+    _check(load().sllbm_init_fields_adjoint(ctx, vp(rho_ptr), vp(u_ptr), vp(T_ptr), vp(lam_ptr),
+                                            vp(grad_rho_ptr or None), vp(grad_u_ptr or None),
+                                            vp(grad_T_ptr or None)), "sllbm_init_fields_adjoint", ctx)
+
+
 # ---- convenience object ------------------------------------------------------------------
 @dataclass
 class Config:
@@ -363,6 +402,19 @@ class Sim:
 
     def step(self, n: int = 1) -> int:
         return sllbm_step(self.ctx, n)
+
+    def state_like(self):
+        """An uninitialised tensor shaped and typed like a state buffer [45, Nz, Ny, Nx, 2]."""
+        return self.torch.empty((Q,) + self.N[::-1] + (2,), dtype=self.pop_dtype, device=self.device)
+
+    def load_state(self, state) -> None:
+        assert state.is_contiguous() and state.dtype == self.pop_dtype
+        assert state.numel() * state.element_size() == int(self.info.pop_bytes)
+        sllbm_load_state(self.ctx, state.data_ptr())
+
+    def set_mu_inf(self, mu_inf: float) -> None:
+        sllbm_set_mu_inf(self.ctx, mu_inf)
+        self.info = sllbm_get_info(self.ctx)
 
     def moments(self):
         t = self.torch

@@ -18,6 +18,9 @@ in FP64, FP32 and the 16-bit deviation storages for a bounded number of steps an
 each one's throughput, HBM fraction and relative L2 error against the FP64 GPU run (rho, u,
 T at the end; kinetic-energy and dissipation curves).
 
+The "adjoint" block times the reverse mode on the 48^3-node Taylor-Green run and states
+its gradients' errors against central differences of the FP64 forward run.
+
 --impl reference times the FP64 CPU oracle (tests-only code) on the host cores on a
 bounded sample of the same workload.
 """
@@ -59,6 +62,8 @@ def parse_args():
     ap.add_argument("--mixed-steps", type=int, default=200,
                     help="steps of the Ma 1.25 mixed-precision comparison (0: skip)")
     ap.add_argument("--mixed-every", type=int, default=10)
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the reverse-mode block (gradients on the 48^3-node run)")
     return ap.parse_args()
 
 
@@ -312,6 +317,77 @@ def mixed_precision_block(S, torch, device, steps, every, hbm):
     return out
 
 
+def adjoint_block(S, torch, device, hbm, every=20, timed=20):
+    """Reverse mode on the 16^3-cell, p = 3 Taylor-Green run (200 steps, checkpoints every
+    20): gradients of the final E_k with respect to a seeded initial-velocity perturbation
+    (amplitude 1e-3 U0) and mu_inf in FP32 and FP64, checked against central differences of
+    the FP64 forward run; and the device time of one backward step (sllbm_adjoint_step)."""
+    from paper_2012_05537_gb300 import adjoint as A
+
+    w = I.WORKLOADS["tgv_16c_p3_adj"]
+    cfgs = {st: S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, courant=w.courant, storage=st)
+            for st in ("f64", "f32")}
+    rho, u, T = A.tgv_fields(cfgs["f64"], device=device)
+    out = {"workload": w.name, "note": w.note, "steps": w.steps, "checkpoint_every": every}
+    grads = {}
+    for st, cfg in cfgs.items():
+        sim = S.Sim(cfg, device=device)
+        U0 = float(sim.info.U0)
+        du = torch.as_tensor(1e-3 * U0 * I.noise(tuple(u.shape), 0), device=device)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        grads[st] = A.kinetic_energy_gradients(sim, rho, u, T, du, w.steps, every)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        # device time of the backward step alone
+        state = sim.raw_state().clone()
+        lam = torch.empty_like(state)
+        S.sllbm_ek_adjoint(sim.ctx, state.data_ptr(), lam.data_ptr())
+        spare = torch.empty_like(lam)
+        dmu = torch.zeros(1, dtype=torch.float64, device=device)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        S.sllbm_adjoint_step(sim.ctx, state.data_ptr(), lam.data_ptr(), spare.data_ptr(), dmu.data_ptr())
+        torch.cuda.synchronize()
+        ev[0].record(sim.stream)
+        for _ in range(timed):
+            S.sllbm_adjoint_step(sim.ctx, state.data_ptr(), lam.data_ptr(), spare.data_ptr(), dmu.data_ptr())
+        ev[1].record(sim.stream)
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / timed
+        _, fwd = time_steps(sim, torch, timed)
+        bpn = 3 * 90 * ELEM_BYTES[st]  # read state and lambda, write lambda
+        out[st] = {"gradients": grads[st], "wall_s_forward_and_backward": wall,
+                   "adjoint_step_ms": ms, "forward_step_ms": statistics.median(fwd),
+                   "adjoint_node_updates_per_s": sim.nodes / (ms / 1e3),
+                   "adjoint_hbm_frac_of_min_bytes": bpn * sim.nodes / (ms / 1e3) / 1e9 / hbm,
+                   "adjoint_min_bytes_per_node": bpn}
+        sim.close()
+    sim = S.Sim(cfgs["f64"], device=device)
+    mu0 = float(sim.info.mu_inf)
+    du = torch.as_tensor(1e-3 * float(sim.info.U0) * I.noise(tuple(u.shape), 0), device=device)
+
+    def ek(eps=0.0, mu=mu0):
+        sim.set_mu_inf(mu)
+        sim.init_fields(rho, u + eps * du, T)
+        sim.step(w.steps)
+        return sim.diag()[0]
+
+    def central(fun, x, h):
+        d1 = (fun(x + h) - fun(x - h)) / (2 * h)
+        d2 = (fun(x + h / 2) - fun(x - h / 2)) / h
+        return (4 * d2 - d1) / 3
+
+    fd = {"dEk_deps": central(lambda e: ek(eps=e), 0.0, 1.0),
+          "dEk_dmu_inf": central(lambda m: ek(mu=m), mu0, 1e-2 * mu0)}
+    sim.close()
+    out["finite_differences_f64"] = fd
+    for st in ("f64", "f32"):
+        out[st]["rel_err_vs_fd"] = {k: abs(grads[st][k] - v) / abs(v) for k, v in fd.items()}
+    out["f32"]["rel_err_vs_f64"] = {k: abs(grads["f32"][k] - grads["f64"][k]) / abs(grads["f64"][k])
+                                    for k in fd}
+    return out
+
+
 def run_mine(args, rank, world, local):
     import torch
 
@@ -396,6 +472,8 @@ def run_mine(args, rank, world, local):
                            "hbm_gbs_equiv": 2 * 45 * 2 * 8 * nodes / (statistics.mean(k64) / 1e3) / 1e9,
                            "steps": n64}
         sim64.close()
+    if not args.no_variants and rank == 0 and not args.no_adjoint:
+        variants["adjoint"] = adjoint_block(S, torch, f"cuda:{local}", hbm)
     if not args.no_variants and rank == 0 and args.mixed_steps > 0:
         variants["mixed"] = mixed_precision_block(S, torch, f"cuda:{local}", args.mixed_steps,
                                                   args.mixed_every, hbm)

@@ -118,6 +118,7 @@ typedef struct {
     int storage;       /* sllbm_storage */
     int max_cell_shift;/* largest |departure cell shift| over velocities and directions */
     int step_kernel;   /* kernel sllbm_step launches: 1 generic tile kernel, 2 TMA-fed kernel */
+    int step_variant;  /* see sllbm_set_step_variant */
 } sllbm_info_t;
 
 /* Fills p_out with the defaults used for the paper's Re = 1600 Taylor-Green runs
@@ -221,6 +222,50 @@ int sllbm_load_state(sllbm_ctx *ctx, const void *state);
  * tau = mu_inf (mu/mu_inf)(T) / (rho T dt) + 1/2 (Sec. II.A, Sec. III.C) for the following
  * steps.  SLLBM_EINVAL unless mu_inf > 0. */
 int sllbm_set_mu_inf(sllbm_ctx *ctx, double mu_inf);
+
+/* ---- kernel choice, autotuning, batched launch ------------------------------------------
+ * A step can run on several kernels with identical results up to FP rounding order: the
+ * TMA-fed persistent kernel (FP32, p = 2 or 4, meshes of whole tiles) and the generic tile
+ * kernel with its default tile or, for FP32 storage without the Prandtl term, one of two
+ * smaller tiles (more CTAs on small meshes).  Variants: 0 TMA-fed kernel; 1 generic,
+ * default tile; 2 and 3 generic, alternative tiles (p = 2: 2x2x2 and 4x2x1 cells; p = 3:
+ * 2x2x1 and 1x1x1; p = 4: 2x1x1 and 1x1x1). */
+
+/* Selects the step kernel of the following steps.  SLLBM_EINVAL if the variant cannot run
+ * this context. */
+int sllbm_set_step_variant(sllbm_ctx *ctx, int variant);
+
+/* Autotuner: times `steps` steps (CUDA events, after one warm-up step) of every variant
+ * that can run this context, starting each from the current state, keeps the fastest and
+ * restores the current state (a temporary device copy of one state is allocated).
+ * Synchronous.  Outputs (either may be NULL): the chosen variant and its time per step in
+ * milliseconds.  Needs an initialised context. */
+int sllbm_autotune(sllbm_ctx *ctx, int steps, int *variant, double *ms_per_step);
+
+/* Batched launch of many contexts (instances of uneven size, order and parameters) as one
+ * CUDA graph.  sllbm_batch_create captures two steps of every context, with the contexts
+ * spread over `streams` worker streams (longest-processing-time-first on the per-step cost
+ * estimate: the autotuned times if every context was autotuned, else the node counts) so that small instances run
+ * concurrently; the graph forks from and joins to cuda_stream, which must be a created
+ * stream (not the legacy default stream, NULL: SLLBM_EINVAL).  Each context must be
+ * initialised, on the current device, with nonfinite_check off, and must not take part in
+ * another batch.  The contexts keep ownership of their buffers and stay usable on their
+ * own; a batch is invalid (SLLBM_EINVAL from sllbm_batch_step) once one of them was stepped
+ * an odd number of times outside it. */
+typedef struct sllbm_batch sllbm_batch;
+int sllbm_batch_create(sllbm_ctx *const *ctxs, int n, int streams, void *cuda_stream, sllbm_batch **out);
+
+/* Advances every context of the batch by nsteps (even, >= 0) steps: nsteps/2 graph
+ * launches on the batch's stream, ordered after work already queued on the contexts'
+ * streams and before work queued on them later.  Asynchronous. */
+int sllbm_batch_step(sllbm_batch *b, int nsteps);
+
+/* Host-only planning helper used by sllbm_batch_create: assigns n jobs with the given
+ * costs to `streams` streams, longest first, each to the least-loaded stream (ties: lowest
+ * index); writes assign[n].  SLLBM_EINVAL for n < 1, streams < 1 or a negative cost. */
+int sllbm_batch_plan(const double *cost, int n, int streams, int *assign);
+
+void sllbm_batch_destroy(sllbm_batch *b);
 
 /* ---- reverse mode ---------------------------------------------------------------------
  * The paper has no adjoint.  These calls are the transposes of the derivatives of the

@@ -389,6 +389,17 @@ int launch_diag_cells_into(sllbm_ctx* ctx, const void* pop, double* partials, do
 
 namespace sllbm {
 
+int step_launch(sllbm_ctx* ctx) {
+    const void* src = ctx->buf[ctx->cur];
+    void* dst = ctx->buf[1 - ctx->cur];
+    int rc = ctx->prm.storage == SLLBM_F64   ? launch_step_f64(ctx, src, dst)
+             : ctx->prm.storage == SLLBM_F32 ? launch_step_f32(ctx, src, dst)
+                                             : launch_step_f16(ctx, src, dst);
+    if (rc != SLLBM_OK) return rc;
+    ctx->cur = 1 - ctx->cur;
+    return SLLBM_OK;
+}
+
 void fill_step_args(const sllbm_ctx* ctx, const void* src, void* dst, StepArgs* a) {
     a->src = src;
     a->dst = dst;
@@ -573,6 +584,7 @@ int sllbm_get_info(const sllbm_ctx* ctx, sllbm_info_t* info) {
     info->storage = ctx->prm.storage;
     info->max_cell_shift = ctx->max_shift;
     info->step_kernel = ctx->step_kernel;
+    info->step_variant = ctx->step_kernel == 2 ? 0 : 1 + ctx->tile_shape;
     return SLLBM_OK;
 }
 
@@ -698,13 +710,8 @@ int sllbm_step(sllbm_ctx* ctx, int n) {
     if (!ctx->initialised) return SLLBM_ENOTREADY;
     if (ctx->prm.nonfinite_check) CK(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
     for (int s = 0; s < n; ++s) {
-        const void* src = ctx->buf[ctx->cur];
-        void* dst = ctx->buf[1 - ctx->cur];
-        int rc = ctx->prm.storage == SLLBM_F64   ? launch_step_f64(ctx, src, dst)
-                 : ctx->prm.storage == SLLBM_F32 ? launch_step_f32(ctx, src, dst)
-                                                 : launch_step_f16(ctx, src, dst);
+        int rc = step_launch(ctx);
         if (rc != SLLBM_OK) return rc;
-        ctx->cur = 1 - ctx->cur;
     }
     if (ctx->prm.nonfinite_check) {
         int flags[2] = {0, 0};

@@ -39,10 +39,12 @@ struct sllbm_ctx {
     size_t step_blob_size;
     int num_sms;
     int step_kernel;           // 1: generic tile kernel, 2: TMA-fed persistent kernel
+    int tile_shape;            // generic FP32 kernel: 0 default tile, 1 and 2 the alternatives
     alignas(64) unsigned char tmap[2][8][128];  // TMA descriptors (CUtensorMap) per source buffer and box shape
     const void* tmap_src[2];
     int last_err;
     long long launches;
+    double tuned_ms;           // step time of the variant sllbm_autotune chose (0: not tuned)
     void* adj_buf[2];          // reverse-mode scratch (state-sized), allocated on first use
     double* d_adj_partials;    // per-block partials of the mu_inf sensitivity
     int adj_blocks;
@@ -107,8 +109,14 @@ void fill_step_tables(const sllbm_ctx* ctx, StepTables<C, P>* t) {
 int launch_step_f32(sllbm_ctx* ctx, const void* src, void* dst);
 int launch_step_f64(sllbm_ctx* ctx, const void* src, void* dst);
 int launch_step_f16(sllbm_ctx* ctx, const void* src, void* dst);  // both 16-bit deviation types (step_f16.cu)
+// Generic FP32 kernel with one of the alternative tile shapes 1, 2 (step_f32_tiles.cu).
+int launch_step_f32_shape(sllbm_ctx* ctx, const void* src, void* dst, int shape);
 
 void fill_step_args(const sllbm_ctx* ctx, const void* src, void* dst, StepArgs* a);
+
+// One step on ctx->stream: launch the context's step kernel from buf[cur] into buf[1-cur]
+// and swap (api.cu).  No flag handling, no synchronisation.
+int step_launch(sllbm_ctx* ctx);
 
 // True when the TMA-fed FP32 kernel can run this context (step_f32.cu).
 bool tma_step_eligible(const sllbm_ctx* c);

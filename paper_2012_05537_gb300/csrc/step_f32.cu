@@ -166,6 +166,7 @@ int launch_step_f32(sllbm_ctx* ctx, const void* src, void* dst) {
         }
         return SLLBM_EINVAL;
     }
+    if (ctx->tile_shape != 0) return launch_step_f32_shape(ctx, src, dst, ctx->tile_shape);
     switch (ctx->p) {
     case 2: return launch_step_tiled<float, float, 2, 4, 4, 2, 10>(ctx, src, dst);
     case 3: return launch_step_tiled<float, float, 3, 2, 2, 2, 10>(ctx, src, dst);

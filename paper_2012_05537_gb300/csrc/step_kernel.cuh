@@ -341,8 +341,11 @@ __global__ void __launch_bounds__(NW * 32, 1)
     }
 }
 
-template <typename S, typename C, int P, int CX, int CY, int CZ, int NW>
+// WITH_PR = false instantiates only the kernel without the Prandtl term (tile-shape
+// variants offered to the autotuner); such a launcher refuses contexts with the term on.
+template <typename S, typename C, int P, int CX, int CY, int CZ, int NW, bool WITH_PR = true>
 int launch_step_tiled(sllbm_ctx* ctx, const void* src, void* dst) {
+    if (!WITH_PR && ctx->prm.pr_correction) return SLLBM_EINVAL;
     using SM = StepSmem<C, P, CX, CY, CZ, NW>;
     static_assert(SM::bytes <= 227 * 1024, "shared memory budget");
     // the tables are built once per context and kept in its host-side blob
@@ -361,13 +364,15 @@ int launch_step_tiled(sllbm_ctx* ctx, const void* src, void* dst) {
     args.tiles[2] = (ctx->cells[2] + CZ - 1) / CZ;
     const long long ntiles = static_cast<long long>(args.tiles[0]) * args.tiles[1] * args.tiles[2];
     if (ntiles > 0x7fffffffLL) return SLLBM_EINVAL;
-    cudaError_t err;
+    cudaError_t err = cudaSuccess;
     if (ctx->prm.pr_correction) {
-        auto k = step_kernel<S, C, P, CX, CY, CZ, NW, true>;
-        err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(SM::bytes));
-        if (err == cudaSuccess) {
-            k<<<static_cast<unsigned>(ntiles), NW * 32, SM::bytes, ctx->stream>>>(args, *tab);
-            err = cudaGetLastError();
+        if constexpr (WITH_PR) {
+            auto k = step_kernel<S, C, P, CX, CY, CZ, NW, true>;
+            err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(SM::bytes));
+            if (err == cudaSuccess) {
+                k<<<static_cast<unsigned>(ntiles), NW * 32, SM::bytes, ctx->stream>>>(args, *tab);
+                err = cudaGetLastError();
+            }
         }
     } else {
         auto k = step_kernel<S, C, P, CX, CY, CZ, NW, false>;

@@ -124,3 +124,31 @@ def sample_nodes(nodes: int, count: int, seed: int) -> np.ndarray:
     pick = g.choice(nodes, size=min(count, nodes), replace=False)
     pick = np.unique(np.concatenate([pick, [0, nodes - 1]]))
     return pick.astype(np.int64)
+
+
+@dataclass(frozen=True)
+class Instance:
+    """One member of a batch of independent Taylor-Green runs (cube of cells)."""
+    cells: tuple
+    p: int
+    Ma: float
+    Re: float
+    courant: float
+
+    @property
+    def nodes(self) -> int:
+        return (self.cells[0] * self.p) * (self.cells[1] * self.p) * (self.cells[2] * self.p)
+
+
+def batch_instances(count: int = 64, seed: int = 0):
+    """Seeded mix of Taylor-Green instances of uneven size, order and parameters: cells per
+    direction uniform in 8..24 (cubes), p in {2, 3, 4}, Ma uniform in [0.3, 1.25], Re uniform
+    in [400, 1600], Courant number uniform in [1, 8]."""
+    g = rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(g.integers(8, 25))
+        p = int(g.choice([2, 3, 4]))
+        out.append(Instance(cells=(n, n, n), p=p, Ma=float(g.uniform(0.3, 1.25)),
+                            Re=float(g.uniform(400.0, 1600.0)), courant=float(g.uniform(1.0, 8.0))))
+    return out

@@ -52,7 +52,8 @@ class Info(ctypes.Structure):
                 ("Q", ctypes.c_int), ("dt", ctypes.c_double), ("U0", ctypes.c_double),
                 ("mu_inf", ctypes.c_double), ("max_xi", ctypes.c_double),
                 ("pop_bytes", ctypes.c_size_t), ("storage", ctypes.c_int),
-                ("max_cell_shift", ctypes.c_int), ("step_kernel", ctypes.c_int)]
+                ("max_cell_shift", ctypes.c_int), ("step_kernel", ctypes.c_int),
+                ("step_variant", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -97,6 +98,13 @@ def load(build_if_missing: bool = False):
         "sllbm_velset_d3q45": (ctypes.c_int, [dp, dp]),
         "sllbm_stream_table": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]),
+        "sllbm_set_step_variant": (ctypes.c_int, [vp, ctypes.c_int]),
+        "sllbm_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]),
+        "sllbm_batch_plan": (ctypes.c_int, [dp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+        "sllbm_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, vp,
+                                              ctypes.POINTER(vp)]),
+        "sllbm_batch_step": (ctypes.c_int, [vp, ctypes.c_int]),
+        "sllbm_batch_destroy": (None, [vp]),
         "sllbm_load_state": (ctypes.c_int, [vp, vp]),
         "sllbm_set_mu_inf": (ctypes.c_int, [vp, ctypes.c_double]),
         "sllbm_stream_apply": (ctypes.c_int, [vp, vp, vp, ctypes.c_int]),
@@ -250,6 +258,42 @@ def sllbm_stream_table(p: int, h: float, dt: float, direction: int):
 
 def sllbm_launch_count(ctx) -> int:
     return int(load().sllbm_launch_count(ctx))
+
+
+def sllbm_set_step_variant(ctx, variant: int) -> None:
+    _check(load().sllbm_set_step_variant(ctx, int(variant)), "sllbm_set_step_variant", ctx)
+
+
+def sllbm_autotune(ctx, steps: int):
+    """(chosen variant, ms per step)."""
+    v, ms = ctypes.c_int(), ctypes.c_double()
+    _check(load().sllbm_autotune(ctx, int(steps), ctypes.byref(v), ctypes.byref(ms)), "sllbm_autotune", ctx)
+    return v.value, ms.value
+
+
+def sllbm_batch_plan(cost, streams: int) -> np.ndarray:
+    cost = np.ascontiguousarray(cost, dtype=np.float64)
+    assign = np.zeros(len(cost), dtype=np.int32)
+    _check(load().sllbm_batch_plan(cost.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(cost),
+                                   int(streams), assign.ctypes.data_as(ctypes.POINTER(ctypes.c_int))),
+           "sllbm_batch_plan")
+    return assign
+
+
+def sllbm_batch_create(ctxs, streams: int, stream: int):
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    b = ctypes.c_void_p()
+    _check(load().sllbm_batch_create(arr, len(ctxs), int(streams), ctypes.c_void_p(stream), ctypes.byref(b)),
+           "sllbm_batch_create")
+    return b
+
+
+def sllbm_batch_step(b, nsteps: int) -> None:
+    _check(load().sllbm_batch_step(b, int(nsteps)), "sllbm_batch_step")
+
+
+def sllbm_batch_destroy(b) -> None:
+    load().sllbm_batch_destroy(b)
 
 
 def sllbm_load_state(ctx, state_ptr: int) -> None:
@@ -406,6 +450,18 @@ class Sim:
     def state_like(self):
         """An uninitialised tensor shaped and typed like a state buffer [45, Nz, Ny, Nx, 2]."""
         return self.torch.empty((Q,) + self.N[::-1] + (2,), dtype=self.pop_dtype, device=self.device)
+
+    def set_variant(self, variant: int) -> None:
+        """Step kernel: 0 TMA-fed, 1 generic default tile, 2 and 3 generic alternative tiles."""
+        sllbm_set_step_variant(self.ctx, variant)
+        self.info = sllbm_get_info(self.ctx)
+
+    def autotune(self, steps: int = 5):
+        """Times every variant that can run this context from the current state, keeps the
+        fastest (the state is restored); returns (variant, ms per step)."""
+        out = sllbm_autotune(self.ctx, steps)
+        self.info = sllbm_get_info(self.ctx)
+        return out
 
     def load_state(self, state) -> None:
         assert state.is_contiguous() and state.dtype == self.pop_dtype

@@ -18,7 +18,9 @@ in FP64, FP32 and the 16-bit deviation storages for a bounded number of steps an
 each one's throughput, HBM fraction and relative L2 error against the FP64 GPU run (rho, u,
 T at the end; kinetic-energy and dissipation curves).
 
-The "adjoint" block times the reverse mode on the 48^3-node Taylor-Green run and states
+The "batched" block runs 64 seeded Taylor-Green instances of uneven size, order and
+parameters one by one and as one CUDA graph per two steps (autotuned kernels), and states
+the aggregate node-updates/s of each.  The "adjoint" block times the reverse mode on the 48^3-node Taylor-Green run and states
 its gradients' errors against central differences of the FP64 forward run.
 
 --impl reference times the FP64 CPU oracle (tests-only code) on the host cores on a
@@ -62,6 +64,8 @@ def parse_args():
     ap.add_argument("--mixed-steps", type=int, default=200,
                     help="steps of the Ma 1.25 mixed-precision comparison (0: skip)")
     ap.add_argument("--mixed-every", type=int, default=10)
+    ap.add_argument("--batch-steps", type=int, default=100,
+                    help="steps of the 64-instance batched comparison (0: skip)")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the reverse-mode block (gradients on the 48^3-node run)")
     return ap.parse_args()
@@ -388,6 +392,60 @@ def adjoint_block(S, torch, device, hbm, every=20, timed=20):
     return out
 
 
+def batch_block(S, torch, device, count, steps, streams=16, seed=0):
+    """`count` Taylor-Green instances of uneven size, order and parameters (seeded mix:
+    cells 8^3..24^3, p in {2,3,4}, Ma 0.3..1.25, Re 400..1600, Courant 1..8), FP32, `steps`
+    steps each: aggregate node-updates/s run one by one (default kernels, then autotuned
+    kernels) against one graph launch per two steps of all instances."""
+    from paper_2012_05537_gb300 import batch as BT
+
+    insts = I.batch_instances(count, seed)
+    sims = BT.make_instances(insts, device=device)
+    nodes = sum(s.nodes for s in sims)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def one_by_one():
+        torch.cuda.synchronize()
+        ms = 0.0
+        for s in sims:
+            ev[0].record(s.stream)
+            s.step(steps)
+            ev[1].record(s.stream)
+            torch.cuda.synchronize()
+            ms += ev[0].elapsed_time(ev[1])
+        return ms
+
+    for s in sims:
+        s.step(2)  # warm-up: tables, descriptors, function attributes
+    default_ms = one_by_one()
+    variants = [s.autotune(3)[0] for s in sims]
+    tuned_ms = one_by_one()
+    bt = BT.Batch(sims, streams=streams)
+    bt.step(2)
+    torch.cuda.synchronize()
+    ev[0].record(bt.stream)
+    bt.step(steps if steps % 2 == 0 else steps + 1)
+    ev[1].record(bt.stream)
+    torch.cuda.synchronize()
+    batch_ms = ev[0].elapsed_time(ev[1])
+    bsteps = steps if steps % 2 == 0 else steps + 1
+    finite = 0
+    for s in sims:
+        _, _, T = s.moments()
+        finite += bool(torch.isfinite(T).all().item())
+    bt.close()
+    for s in sims:
+        s.close()
+    return {"instances": count, "seed": seed, "steps": steps, "nodes_per_step": nodes,
+            "streams": streams, "configured_steps": 500,
+            "one_by_one_default": {"ms": default_ms, "value": nodes * steps / (default_ms / 1e3)},
+            "one_by_one_autotuned": {"ms": tuned_ms, "value": nodes * steps / (tuned_ms / 1e3)},
+            "batched_graph": {"ms": batch_ms, "value": nodes * bsteps / (batch_ms / 1e3)},
+            "speedup_vs_one_by_one_default": (nodes * bsteps / batch_ms) / (nodes * steps / default_ms),
+            "variants_chosen": {str(v): variants.count(v) for v in sorted(set(variants))},
+            "instances_finite_at_end": finite, "unit": UNIT}
+
+
 def run_mine(args, rank, world, local):
     import torch
 
@@ -472,6 +530,8 @@ def run_mine(args, rank, world, local):
                            "hbm_gbs_equiv": 2 * 45 * 2 * 8 * nodes / (statistics.mean(k64) / 1e3) / 1e9,
                            "steps": n64}
         sim64.close()
+    if not args.no_variants and rank == 0 and args.batch_steps > 0:
+        variants["batched"] = batch_block(S, torch, f"cuda:{local}", 64, args.batch_steps)
     if not args.no_variants and rank == 0 and not args.no_adjoint:
         variants["adjoint"] = adjoint_block(S, torch, f"cuda:{local}", hbm)
     if not args.no_variants and rank == 0 and args.mixed_steps > 0:

@@ -2,13 +2,17 @@
 // interpolation + moments + equilibrium + BGK (+ Prandtl term), one tile per CTA.
 //
 // Data flow per CTA (tile of CX x CY x CZ cells = TX x TY x TZ nodes):
-//   * each warp owns whole populations q (f_i or g_i); for one q it gathers the source
-//     box of the tile (the tile translated by the velocity's departure cell shift, plus
-//     one cell where the shift differs between local nodes, plus the shared face) from
-//     global memory into shared memory, with periodic wrap;
-//   * three separable passes (z, then y, then x) apply the per-velocity Lagrange
-//     weights (Eq. interpolation; identical for every cell on the uniform mesh) and
-//     leave the streamed value of every tile node in the CTA's OUT[90][tile] array;
+//   * each warp owns whole velocity pairs (f_i, g_i), which share departure points and
+//     weights; for one pair, each lane takes columns (x, y) of the pair's source box (the
+//     tile translated by the velocity's departure cell shift, plus one cell where the shift
+//     differs between local nodes, plus the shared face), loads the column's values from
+//     global memory into registers (periodic wrap, all loads of a column issued together)
+//     and applies the z pass there (Eq. interpolation; the weights are identical for every
+//     cell on the uniform mesh), writing the TZ output planes to a per-warp buffer;
+//   * the y pass runs in place over columns (x, z) of that buffer, the x pass over rows
+//     (y, z), leaving the streamed f_i and g_i of every tile node in the CTA's OUT[90][tile];
+//     which of two candidate support ranges a local node uses is a register select, not a
+//     computed register index;
 //   * after a CTA barrier each thread takes nodes of the tile, forms rho, u, T
 //     (Eq. moments), tau (Sec. II.A, Sutherland law of Sec. III.C), the fourth-order
 //     equilibrium (Eq. discreteEquilibrium), and writes the collided f and g
@@ -16,6 +20,7 @@
 #pragma once
 
 #include <cstdlib>
+#include <type_traits>
 
 #include "collide.cuh"
 #include "sllbm_internal.h"
@@ -28,18 +33,80 @@ struct TileShape {
     static constexpr int TX = CX * P, TY = CY * P, TZ = CZ * P;
     static constexpr int TILE = TX * TY * TZ;
     static constexpr int BX = (CX + 1) * P + 1, BY = (CY + 1) * P + 1, BZ = (CZ + 1) * P + 1;
-    static constexpr int BOX = BX * BY * BZ;   // largest source box
-    static constexpr int TMP1 = TZ * BY * BX;  // z-pass result
+};
+
+// Pair of the arithmetic type (f_i, g_i).
+template <typename C>
+struct Pair2;
+template <>
+struct Pair2<float> {
+    using T = float2;
+};
+template <>
+struct Pair2<double> {
+    using T = double2;
 };
 
 template <typename C, int P, int CX, int CY, int CZ, int NW>
 struct StepSmem {
     using TS = TileShape<CX, CY, CZ, P>;
+    using C2 = typename Pair2<C>::T;
     static constexpr size_t out_elems = size_t(2) * kQ * TS::TILE;
-    static constexpr size_t warp_elems = size_t(TS::BOX) + TS::TMP1;
+    static constexpr size_t out_bytes = (out_elems * sizeof(C) + 15) / 16 * 16;
+    static constexpr size_t warp_pairs = size_t(TS::TZ) * TS::BY * TS::BX;  // z-pass output planes
     static constexpr size_t warp_ints = TS::BX + TS::BY + TS::BZ;
-    static constexpr size_t bytes = (out_elems + NW * warp_elems) * sizeof(C) + NW * warp_ints * sizeof(int);
+    static constexpr size_t bytes = out_bytes + NW * warp_pairs * sizeof(C2) + NW * warp_ints * sizeof(int);
 };
+
+// One stored pair (f_i, g_i) widened to the arithmetic type.
+template <typename C, typename S>
+__device__ __forceinline__ typename Pair2<C>::T load_pair(const S* p) {
+    typename Pair2<C>::T r;
+    if constexpr (std::is_same<S, float>::value) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+        r.x = static_cast<C>(v.x);
+        r.y = static_cast<C>(v.y);
+    } else if constexpr (std::is_same<S, double>::value) {
+        const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+        r.x = static_cast<C>(v.x);
+        r.y = static_cast<C>(v.y);
+    } else if constexpr (std::is_same<S, __half>::value) {
+        const float2 v = __half22float2(*reinterpret_cast<const __half2*>(p));
+        r.x = static_cast<C>(v.x);
+        r.y = static_cast<C>(v.y);
+    } else {
+        const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+        r.x = static_cast<C>(v.x);
+        r.y = static_cast<C>(v.y);
+    }
+    return r;
+}
+
+// One 1D Lagrange pass over a column held in registers: output o (0..T-1, local index
+// a = o % P in cell o / P) = sum_l w[a][l] v[(o/P + k_a) P + l] with k_a in {0, 1}.
+template <typename C, int P, int T, int NV>
+__device__ __forceinline__ void lagrange_column(const typename Pair2<C>::T (&v)[NV], const C (&w)[P][P + 1],
+                                                const signed char (&kc)[P], typename Pair2<C>::T (&r)[T]) {
+#pragma unroll
+    for (int o = 0; o < T; ++o) {
+        const int a = o % P;
+        const int base = (o / P) * P;
+        const bool hi = kc[a] != 0;
+        C fx = 0, fy = 0;
+#pragma unroll
+        for (int l = 0; l <= P; ++l) {
+            const C wl = w[a][l];
+            const int lo_i = base + l, hi_i = base + P + l;
+            static_assert((T - 1) / P * P + 2 * P < NV, "column shorter than the support of its outputs");
+            const C vx = hi ? v[hi_i].x : v[lo_i].x;
+            const C vy = hi ? v[hi_i].y : v[lo_i].y;
+            fx += wl * vx;
+            fy += wl * vy;
+        }
+        r[o].x = fx;
+        r[o].y = fy;
+    }
+}
 
 // A stored value in the arithmetic type (16-bit storage goes through FP32).
 template <typename C, typename S>
@@ -233,16 +300,17 @@ __device__ __forceinline__ void collide_node(const C* __restrict__ h, int stride
 }
 
 template <typename S, typename C, int P, int CX, int CY, int CZ, int NW, bool PR>
-__global__ void __launch_bounds__(NW * 32, 1)
+__global__ void __launch_bounds__(NW * 32)
     step_kernel(const StepArgs a, const __grid_constant__ StepTables<C, P> t) {
     using TS = TileShape<CX, CY, CZ, P>;
+    using SM = StepSmem<C, P, CX, CY, CZ, NW>;
+    using C2 = typename Pair2<C>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* out = reinterpret_cast<C*>(smem_raw);
-    C* wbase = out + StepSmem<C, P, CX, CY, CZ, NW>::out_elems;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    C* box = wbase + warp * (TS::BOX + TS::TMP1);
-    C* tmp1 = box + TS::BOX;
-    int* xo = reinterpret_cast<int*>(wbase + NW * (TS::BOX + TS::TMP1)) + warp * (TS::BX + TS::BY + TS::BZ);
+    C2* zb = reinterpret_cast<C2*>(smem_raw + SM::out_bytes) + warp * SM::warp_pairs;
+    int* xo = reinterpret_cast<int*>(smem_raw + SM::out_bytes + NW * SM::warp_pairs * sizeof(C2)) +
+              warp * SM::warp_ints;
     int* yo = xo + TS::BX;
     int* zo = yo + TS::BY;
 
@@ -257,8 +325,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
     const S* __restrict__ src = static_cast<const S*>(a.src);
     const int nxy = a.N[0] * a.N[1];
 
-    for (int q = warp; q < 2 * kQ; q += NW) {
-        const int i = q < kQ ? q : q - kQ;
+    for (int i = warp; i < kQ; i += NW) {
         int s[3], b0[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -269,60 +336,81 @@ __global__ void __launch_bounds__(NW * 32, 1)
         for (int e = lane; e < s[1]; e += 32) yo[e] = wrap_index(b0[1] + e, a.N[1]) * a.N[0];
         for (int e = lane; e < s[2]; e += 32) zo[e] = wrap_index(b0[2] + e, a.N[2]) * nxy;
         __syncwarp();
-        // storage order [i][node][h]: population q = (h, i) is every second element
-        const S* __restrict__ sq = src + 2LL * i * a.nn + (q < kQ ? 0 : 1);
-        const int sxy = s[0] * s[1];
-        const int tot = sxy * s[2];
-        for (int e = lane; e < tot; e += 32) {
-            const int z = e / sxy;
-            const int r = e - z * sxy;
-            const int y = r / s[0];
-            const int x = r - y * s[0];
-            box[e] = load_as<C>(__ldg(sq + 2 * (zo[z] + yo[y] + xo[x])));
+        // storage order [i][node][h]: the pair (f_i, g_i) of a node is two adjacent values
+        const S* __restrict__ sp = src + 2LL * i * a.nn;
+        const int sx = s[0], sxy = s[0] * s[1];
+        // gather + z pass: lane = column (x, y) of the source box
+        for (int col = lane; col < sxy; col += 32) {
+            const int y = col / sx;
+            const int x = col - y * sx;
+            const int off = yo[y] + xo[x];
+            C2 v[TS::BZ];
+#pragma unroll
+            for (int z = 0; z < TS::BZ; ++z) {
+                if (z < s[2]) {
+                    v[z] = load_pair<C>(sp + 2LL * (zo[z] + off));
+                } else {
+                    v[z].x = C(0);
+                    v[z].y = C(0);
+                }
+            }
+            C2 r[TS::TZ];
+            lagrange_column<C, P, TS::TZ, TS::BZ>(v, t.lw[i][2], t.kc[i][2], r);
+#pragma unroll
+            for (int oz = 0; oz < TS::TZ; ++oz)
+                if (oz < te[2]) zb[oz * sxy + col] = r[oz];
         }
         __syncwarp();
-        // z pass: tmp1[oz][y][x] = sum_l Lz[az][l] box[zb+l][y][x]
-        const int n1 = te[2] * sxy;
-        for (int e = lane; e < n1; e += 32) {
-            const int oz = e / sxy;
-            const int r = e - oz * sxy;
-            const int az = oz % P;
-            const int zb = (oz / P + t.kc[i][2][az]) * P;
-            C acc = 0;
+        // y pass in place: lane = column (x, z)
+        const int ncol = te[2] * sx;
+        for (int col = lane; col < ncol; col += 32) {
+            const int oz = col / sx;
+            const int x = col - oz * sx;
+            C2* cp = zb + oz * sxy + x;
+            C2 v[TS::BY];
 #pragma unroll
-            for (int l = 0; l <= P; ++l) acc += t.lw[i][2][az][l] * box[(zb + l) * sxy + r];
-            tmp1[e] = acc;
+            for (int y = 0; y < TS::BY; ++y) {
+                if (y < s[1]) {
+                    v[y] = cp[y * sx];
+                } else {
+                    v[y].x = C(0);
+                    v[y].y = C(0);
+                }
+            }
+            C2 r[TS::TY];
+            lagrange_column<C, P, TS::TY, TS::BY>(v, t.lw[i][1], t.kc[i][1], r);
+#pragma unroll
+            for (int oy = 0; oy < TS::TY; ++oy)
+                if (oy < te[1]) cp[oy * sx] = r[oy];
         }
         __syncwarp();
-        // y pass: box[oz][oy][x] = sum_k Ly[ay][k] tmp1[oz][yb+k][x]
-        const int n2 = te[2] * te[1] * s[0];
-        for (int e = lane; e < n2; e += 32) {
-            const int x = e % s[0];
-            const int r = e / s[0];
-            const int oy = r % te[1];
-            const int oz = r / te[1];
-            const int ay = oy % P;
-            const int yb = (oy / P + t.kc[i][1][ay]) * P;
-            C acc = 0;
+        // x pass: lane = row (y, z) of the tile; f_i to OUT[i], g_i to OUT[45 + i]
+        for (int row = lane; row < TS::TY * TS::TZ; row += 32) {
+            const int oz = row / TS::TY;
+            const int oy = row - oz * TS::TY;
+            if (oz >= te[2] || oy >= te[1]) continue;
+            const C2* rp = zb + oz * sxy + oy * sx;
+            C2 v[TS::BX];
 #pragma unroll
-            for (int k = 0; k <= P; ++k) acc += t.lw[i][1][ay][k] * tmp1[(oz * s[1] + yb + k) * s[0] + x];
-            box[e] = acc;
-        }
-        __syncwarp();
-        // x pass: OUT[q][oz][oy][ox] = sum_j Lx[ax][j] box[oz][oy][xb+j]
-        const int n3 = te[2] * te[1] * te[0];
-        C* oq = out + q * TS::TILE;
-        for (int e = lane; e < n3; e += 32) {
-            const int ox = e % te[0];
-            const int r = e / te[0];
-            const int oy = r % te[1];
-            const int oz = r / te[1];
-            const int ax = ox % P;
-            const int xb = (ox / P + t.kc[i][0][ax]) * P;
-            C acc = 0;
+            for (int x = 0; x < TS::BX; ++x) {
+                if (x < sx) {
+                    v[x] = rp[x];
+                } else {
+                    v[x].x = C(0);
+                    v[x].y = C(0);
+                }
+            }
+            C2 r[TS::TX];
+            lagrange_column<C, P, TS::TX, TS::BX>(v, t.lw[i][0], t.kc[i][0], r);
+            C* of = out + i * TS::TILE + (oz * TS::TY + oy) * TS::TX;
+            C* og = of + kQ * TS::TILE;
 #pragma unroll
-            for (int j = 0; j <= P; ++j) acc += t.lw[i][0][ax][j] * box[(oz * te[1] + oy) * s[0] + xb + j];
-            oq[(oz * TS::TY + oy) * TS::TX + ox] = acc;
+            for (int ox = 0; ox < TS::TX; ++ox) {
+                if (ox < te[0]) {
+                    of[ox] = r[ox].x;
+                    og[ox] = r[ox].y;
+                }
+            }
         }
         __syncwarp();
     }

@@ -228,8 +228,9 @@ int sllbm_set_mu_inf(sllbm_ctx *ctx, double mu_inf);
  * TMA-fed persistent kernel (FP32, p = 2 or 4, meshes of whole tiles) and the generic tile
  * kernel with its default tile or, for FP32 storage without the Prandtl term, one of two
  * smaller tiles (more CTAs on small meshes).  Variants: 0 TMA-fed kernel; 1 generic,
- * default tile; 2 and 3 generic, alternative tiles (p = 2: 2x2x2 and 4x2x1 cells; p = 3:
- * 2x2x1 and 1x1x1; p = 4: 2x1x1 and 1x1x1). */
+ * default tile (FP32: p = 2 4x4x2 cells, p = 3 2x2x2, p = 4 2x2x1); 2 and 3 generic,
+ * alternative tiles (p = 2: 4x2x2 and 2x2x1 cells; p = 3: 2x2x1 and 1x1x1; p = 4: 2x1x1 and
+ * 1x1x1). */
 
 /* Selects the step kernel of the following steps.  SLLBM_EINVAL if the variant cannot run
  * this context. */

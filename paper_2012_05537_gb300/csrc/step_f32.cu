@@ -168,9 +168,9 @@ int launch_step_f32(sllbm_ctx* ctx, const void* src, void* dst) {
     }
     if (ctx->tile_shape != 0) return launch_step_f32_shape(ctx, src, dst, ctx->tile_shape);
     switch (ctx->p) {
-    case 2: return launch_step_tiled<float, float, 2, 4, 4, 2, 10>(ctx, src, dst);
-    case 3: return launch_step_tiled<float, float, 3, 2, 2, 2, 10>(ctx, src, dst);
-    case 4: return launch_step_tiled<float, float, 4, 2, 2, 1, 10>(ctx, src, dst);
+    case 2: return launch_step_tiled<float, float, 2, 4, 4, 2, 16>(ctx, src, dst);
+    case 3: return launch_step_tiled<float, float, 3, 2, 2, 2, 16>(ctx, src, dst);
+    case 4: return launch_step_tiled<float, float, 4, 2, 2, 1, 16>(ctx, src, dst);
     }
     return SLLBM_EINVAL;
 }

@@ -8,13 +8,13 @@ namespace sllbm {
 int launch_step_f32_shape(sllbm_ctx* ctx, const void* src, void* dst, int shape) {
     if (shape == 1) {
         switch (ctx->p) {
-        case 2: return launch_step_tiled<float, float, 2, 2, 2, 2, 8, false>(ctx, src, dst);
-        case 3: return launch_step_tiled<float, float, 3, 2, 2, 1, 10, false>(ctx, src, dst);
-        case 4: return launch_step_tiled<float, float, 4, 2, 1, 1, 8, false>(ctx, src, dst);
+        case 2: return launch_step_tiled<float, float, 2, 4, 2, 2, 16, false>(ctx, src, dst);
+        case 3: return launch_step_tiled<float, float, 3, 2, 2, 1, 16, false>(ctx, src, dst);
+        case 4: return launch_step_tiled<float, float, 4, 2, 1, 1, 16, false>(ctx, src, dst);
         }
     } else if (shape == 2) {
         switch (ctx->p) {
-        case 2: return launch_step_tiled<float, float, 2, 4, 2, 1, 8, false>(ctx, src, dst);
+        case 2: return launch_step_tiled<float, float, 2, 2, 2, 1, 8, false>(ctx, src, dst);
         case 3: return launch_step_tiled<float, float, 3, 1, 1, 1, 8, false>(ctx, src, dst);
         case 4: return launch_step_tiled<float, float, 4, 1, 1, 1, 8, false>(ctx, src, dst);
         }

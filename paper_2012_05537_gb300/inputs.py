@@ -73,6 +73,10 @@ WORKLOADS = {
     # reverse-mode workload: gradients of the final kinetic energy through 200 steps
     "tgv_16c_p3_adj": Workload("tgv_16c_p3_adj", (16, 16, 16), 3, 0.5, 1600.0, 2.0, 200, "f32",
                                note="16^3 cells, p=3 (48^3 nodes), Ma 0.5, C=2, 200 steps"),
+    # profiling size of the Ma 1.25 workload's kernel (same cells, order and parameters;
+    # 318 MB per FP32 buffer, larger than L2)
+    "tgv_32c_p3_ma125": Workload("tgv_32c_p3_ma125", (32, 32, 32), 3, 1.25, 1600.0, 1.0, 200, "f32",
+                                 note="32^3 cells, p=3 (96^3 nodes), Ma 1.25, C=1"),
     # the same mesh at Courant 8 (departures 2.7 cells away): first-step parity only
     "tgv_64c_p3_ma125_c8": Workload("tgv_64c_p3_ma125_c8", (64, 64, 64), 3, 1.25, 1600.0, 8.0, 1,
                                     "f32", note="64^3 cells, p=3, Ma 1.25, C=8 (one step)"),

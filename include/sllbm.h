@@ -273,10 +273,17 @@ void sllbm_batch_destroy(sllbm_batch *b);
  * forward operators above, from which gradients of a scalar of the final state through n
  * steps are assembled (checkpointing is the caller's).  They need SLLBM_F32 or SLLBM_F64
  * storage and the Prandtl term off (SLLBM_EINVAL otherwise).  Adjoint populations have the
- * storage type and order of a state buffer, buf[i][z][y][x][h]; every pointer is a device
+ * order of a state buffer, buf[i][z][y][x][h], and the adjoint type (sllbm_set_adjoint_type;
+ * by default the storage type); every pointer is a device
  * pointer; calls are asynchronous on the context's stream.  On the first call the context
  * allocates two state-sized scratch buffers (freed by sllbm_destroy; SLLBM_ENOMEM if that
  * fails). */
+
+/* Type of the adjoint populations of the following reverse-mode calls: the storage type
+ * (the default), or SLLBM_F64 for an SLLBM_F32 context, which keeps the adjoint in FP64
+ * next to the FP32 forward states (the streamed states h stay FP32; the collision VJP and
+ * the transposed streaming run in FP64).  SLLBM_EINVAL for other combinations. */
+int sllbm_set_adjoint_type(sllbm_ctx *ctx, int storage);
 
 /* dst = S src (transpose == 0) or dst = S^T src: the semi-Lagrangian streaming of all 90
  * populations alone (Eq. interpolation, pull), or its transpose, as three 1D passes.

@@ -50,7 +50,7 @@ class InitFields(torch.autograd.Function):
     def backward(ctx, lam):
         sim = ctx.sim
         rho, u, T = ctx.saved_tensors
-        lam = lam.detach().to(sim.pop_dtype).contiguous()
+        lam = lam.detach().to(sim.adjoint_dtype).contiguous()
         need = ctx.needs_input_grad
         g = [torch.empty_like(x) if need[k] else None for k, x in enumerate((rho, u, T))]
         S.sllbm_init_fields_adjoint(sim.ctx, rho.data_ptr(), u.data_ptr(), T.data_ptr(), lam.data_ptr(),
@@ -84,7 +84,7 @@ class Steps(torch.autograd.Function):
     def backward(ctx, lam):
         sim, n, every = ctx.sim, ctx.n, ctx.every
         sim.set_mu_inf(ctx.mu)
-        lam = lam.detach().to(sim.pop_dtype).contiguous().clone()
+        lam = lam.detach().to(sim.adjoint_dtype).contiguous().clone()
         spare = torch.empty_like(lam)
         dmu = torch.zeros(1, dtype=torch.float64, device=sim.device)
         for seg in range(len(ctx.checkpoints) - 1, -1, -1):
@@ -123,7 +123,7 @@ class KineticEnergy(torch.autograd.Function):
     def backward(ctx, g):
         sim = ctx.sim
         (st,) = ctx.saved_tensors
-        lam = torch.empty_like(st)
+        lam = torch.empty(st.shape, dtype=sim.adjoint_dtype, device=st.device)
         S.sllbm_ek_adjoint(sim.ctx, st.data_ptr(), lam.data_ptr())
         return lam * g.to(lam.dtype), None
 
@@ -139,9 +139,12 @@ def tgv_fields(cfg: S.Config, device=None):
     return out
 
 
-def kinetic_energy_gradients(sim: S.Sim, rho, u, T, du, steps: int, every: int):
+def kinetic_energy_gradients(sim: S.Sim, rho, u, T, du, steps: int, every: int, adjoint: str | None = None):
     """E_k after `steps` steps from the equilibrium of (rho, u + eps du, T) at eps = 0, and
-    its gradients with respect to eps and mu_inf (returned as a dict, FP64 scalars)."""
+    its gradients with respect to eps and mu_inf (returned as a dict, FP64 scalars).
+    adjoint="f64" keeps the adjoint populations of an FP32 run in FP64."""
+    if adjoint is not None:
+        sim.set_adjoint_type(adjoint)
     eps = torch.zeros((), dtype=torch.float64, device=sim.device, requires_grad=True)
     mu = torch.tensor(float(sim.info.mu_inf), dtype=torch.float64, device=sim.device, requires_grad=True)
     state0 = InitFields.apply(rho, u + eps * du, T, sim)

@@ -148,8 +148,8 @@ struct AdjArgs {
 //   A_i = omega (lam_f_i + (2C_v - D) T lam_g_i), T also appears in g^eq explicitly,
 //   omega depends on rho and T (and mu_inf); the primitive adjoints are mapped back to the
 //   moments (rho, j, E2) and from there to the populations.
-template <typename C>
-__global__ void __launch_bounds__(128) collide_vjp_kernel(const C* __restrict__ h, const C* __restrict__ lam,
+template <typename CH, typename C>
+__global__ void __launch_bounds__(128) collide_vjp_kernel(const CH* __restrict__ h, const C* __restrict__ lam,
                                                           C* __restrict__ out, long long nn, AdjArgs aa,
                                                           const __grid_constant__ AdjVel v,
                                                           double* __restrict__ partials) {
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(128) collide_vjp_kernel(const C* __restrict__ 
          n += static_cast<long long>(gridDim.x) * blockDim.x) {
         C rho = 0, jx = 0, jy = 0, jz = 0, E2 = 0;
         for (int i = 0; i < kQ; ++i) {
-            const C f = h[2 * (i * nn + n)], g = h[2 * (i * nn + n) + 1];
+            const C f = C(h[2 * (i * nn + n)]), g = C(h[2 * (i * nn + n) + 1]);
             rho += f;
             jx += f * C(v.xi[i][0]);
             jy += f * C(v.xi[i][1]);
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(128) collide_vjp_kernel(const C* __restrict__ 
             const PolyDeriv<C> pd = poly_deriv(ec, sh, s, usq, th);
             const C feq = w * rho * pd.P, geq = gfac * T * feq;
             const C lf = lam[2 * (i * nn + n)], lg = lam[2 * (i * nn + n) + 1];
-            const C hf = h[2 * (i * nn + n)], hg = h[2 * (i * nn + n) + 1];
+            const C hf = C(h[2 * (i * nn + n)]), hg = C(h[2 * (i * nn + n) + 1]);
             B += lf * (feq - hf) + lg * (geq - hg);
             const C A = om * (lf + gfac * T * lg);
             ATd += om * gfac * lg * feq;
@@ -252,8 +252,8 @@ struct EkConst {
     double W1[kMaxP];
 };
 
-template <typename C>
-__global__ void __launch_bounds__(128) ek_seed_kernel(const C* __restrict__ pop, C* __restrict__ lam, long long nn,
+template <typename CS, typename C>
+__global__ void __launch_bounds__(128) ek_seed_kernel(const CS* __restrict__ pop, C* __restrict__ lam, long long nn,
                                                       int Nx, int Ny, int p, double scale,
                                                       const __grid_constant__ EkConst kc) {
     const long long sxy = static_cast<long long>(Nx) * Ny;
@@ -353,11 +353,17 @@ int adj_fail(sllbm_ctx* ctx, cudaError_t e) {
 // Two state-sized scratch buffers and the per-block partials of the mu_inf sensitivity,
 // allocated on the first reverse-mode call.
 int ensure_adjoint_scratch(sllbm_ctx* ctx) {
-    if (ctx->adj_buf[0] != nullptr) return SLLBM_OK;
+    // holds a streamed state and, in the transposed passes, adjoint populations
+    const size_t lam_bytes = static_cast<size_t>(2 * kQ) * static_cast<size_t>(ctx->nn) *
+                             (ctx->adj_f64 ? sizeof(double) : ctx->elem);
+    const size_t need = lam_bytes > ctx->pop_bytes ? lam_bytes : ctx->pop_bytes;
+    if (ctx->adj_buf[0] != nullptr && ctx->adj_bytes >= need) return SLLBM_OK;
+    adjoint_release(ctx);
     ctx->adj_blocks = static_cast<int>(adj_grid(ctx->nn, 128));
     if (ctx->adj_blocks > 2048) ctx->adj_blocks = 2048;
-    cudaError_t e = cudaMalloc(&ctx->adj_buf[0], ctx->pop_bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->adj_buf[1], ctx->pop_bytes);
+    ctx->adj_bytes = need;
+    cudaError_t e = cudaMalloc(&ctx->adj_buf[0], need);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->adj_buf[1], need);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_adj_partials, sizeof(double) * ctx->adj_blocks);
     if (e != cudaSuccess) {
         adjoint_release(ctx);
@@ -373,6 +379,7 @@ void adjoint_release(sllbm_ctx* ctx) {
     cudaFree(ctx->d_adj_partials);
     ctx->adj_buf[0] = ctx->adj_buf[1] = nullptr;
     ctx->d_adj_partials = nullptr;
+    ctx->adj_bytes = 0;
 }
 
 namespace {
@@ -410,14 +417,15 @@ int stream_apply_t(sllbm_ctx* ctx, const void* src, void* dst, bool transpose) {
     return rc;
 }
 
-template <typename C>
+// CS: state type (the streamed populations h are computed in it), C: adjoint type.
+template <typename CS, typename C>
 int adjoint_step_t(sllbm_ctx* ctx, const void* state_prev, const void* lam_next, void* lam_prev, double* dmu) {
     void* a = ctx->adj_buf[0];
     void* b = ctx->adj_buf[1];
     // h = S state_prev (the populations the step's collision saw)
-    int rc = launch_pass<C>(ctx, state_prev, a, 2, false);
-    if (rc == SLLBM_OK) rc = launch_pass<C>(ctx, a, b, 1, false);
-    if (rc == SLLBM_OK) rc = launch_pass<C>(ctx, b, a, 0, false);
+    int rc = launch_pass<CS>(ctx, state_prev, a, 2, false);
+    if (rc == SLLBM_OK) rc = launch_pass<CS>(ctx, a, b, 1, false);
+    if (rc == SLLBM_OK) rc = launch_pass<CS>(ctx, b, a, 0, false);
     if (rc != SLLBM_OK) return rc;
     // b = (d collide / d h)^T lam_next at h; mu_inf sensitivity into *dmu
     AdjArgs aa;
@@ -425,8 +433,8 @@ int adjoint_step_t(sllbm_ctx* ctx, const void* state_prev, const void* lam_next,
     aa.inv_dt = 1.0 / ctx->dt;
     aa.inv_2cv = 0.5 * (ctx->prm.gamma - 1.0);
     aa.gfac = 2.0 / (ctx->prm.gamma - 1.0) - 3.0;
-    collide_vjp_kernel<C><<<ctx->adj_blocks, 128, 0, ctx->stream>>>(
-        static_cast<const C*>(a), static_cast<const C*>(lam_next), static_cast<C*>(b), ctx->nn, aa, adj_vel(ctx),
+    collide_vjp_kernel<CS, C><<<ctx->adj_blocks, 128, 0, ctx->stream>>>(
+        static_cast<const CS*>(a), static_cast<const C*>(lam_next), static_cast<C*>(b), ctx->nn, aa, adj_vel(ctx),
         ctx->d_adj_partials);
     accumulate_kernel<<<1, 256, 0, ctx->stream>>>(ctx->d_adj_partials, ctx->adj_blocks, dmu);
     ctx->launches += 2;
@@ -463,8 +471,22 @@ int sllbm_adjoint_step(sllbm_ctx* ctx, const void* state_prev, const void* lam_n
     if (lam_prev == state_prev || lam_prev == lam_next) return SLLBM_EINVAL;
     int rc = ensure_adjoint_scratch(ctx);
     if (rc != SLLBM_OK) return rc;
-    return ctx->prm.storage == SLLBM_F64 ? adjoint_step_t<double>(ctx, state_prev, lam_next, lam_prev, dmu)
-                                         : adjoint_step_t<float>(ctx, state_prev, lam_next, lam_prev, dmu);
+    if (ctx->prm.storage == SLLBM_F64) return adjoint_step_t<double, double>(ctx, state_prev, lam_next, lam_prev, dmu);
+    if (ctx->adj_f64) return adjoint_step_t<float, double>(ctx, state_prev, lam_next, lam_prev, dmu);
+    return adjoint_step_t<float, float>(ctx, state_prev, lam_next, lam_prev, dmu);
+}
+
+int sllbm_set_adjoint_type(sllbm_ctx* ctx, int storage) {
+    if (ctx == nullptr) return SLLBM_EINVAL;
+    if (storage == SLLBM_F64 && (ctx->prm.storage == SLLBM_F32 || ctx->prm.storage == SLLBM_F64)) {
+        ctx->adj_f64 = ctx->prm.storage == SLLBM_F32;
+        return SLLBM_OK;
+    }
+    if (storage == ctx->prm.storage && storage == SLLBM_F32) {
+        ctx->adj_f64 = false;
+        return SLLBM_OK;
+    }
+    return SLLBM_EINVAL;
 }
 
 int sllbm_ek_adjoint(sllbm_ctx* ctx, const void* state, void* lam) {
@@ -479,12 +501,17 @@ int sllbm_ek_adjoint(sllbm_ctx* ctx, const void* state, void* lam) {
     const double scale = ctx->h[0] * ctx->h[1] * ctx->h[2] * 0.125 / (vol * ctx->prm.rho0 * ctx->U0 * ctx->U0);
     const unsigned grid = adj_grid(ctx->nn, 128);
     if (ctx->prm.storage == SLLBM_F64)
-        ek_seed_kernel<double><<<grid, 128, 0, ctx->stream>>>(static_cast<const double*>(state),
-                                                              static_cast<double*>(lam), ctx->nn, ctx->N[0],
-                                                              ctx->N[1], ctx->p, scale, kc);
+        ek_seed_kernel<double, double><<<grid, 128, 0, ctx->stream>>>(static_cast<const double*>(state),
+                                                                      static_cast<double*>(lam), ctx->nn, ctx->N[0],
+                                                                      ctx->N[1], ctx->p, scale, kc);
+    else if (ctx->adj_f64)
+        ek_seed_kernel<float, double><<<grid, 128, 0, ctx->stream>>>(static_cast<const float*>(state),
+                                                                     static_cast<double*>(lam), ctx->nn, ctx->N[0],
+                                                                     ctx->N[1], ctx->p, scale, kc);
     else
-        ek_seed_kernel<float><<<grid, 128, 0, ctx->stream>>>(static_cast<const float*>(state), static_cast<float*>(lam),
-                                                             ctx->nn, ctx->N[0], ctx->N[1], ctx->p, scale, kc);
+        ek_seed_kernel<float, float><<<grid, 128, 0, ctx->stream>>>(static_cast<const float*>(state),
+                                                                    static_cast<float*>(lam), ctx->nn, ctx->N[0],
+                                                                    ctx->N[1], ctx->p, scale, kc);
     ctx->launches += 1;
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SLLBM_OK : adj_fail(ctx, e);
@@ -496,7 +523,7 @@ int sllbm_init_fields_adjoint(sllbm_ctx* ctx, const double* rho, const double* u
     if (!adjoint_supported(ctx)) return SLLBM_EINVAL;
     const double gfac = 2.0 / (ctx->prm.gamma - 1.0) - 3.0;
     const unsigned grid = adj_grid(ctx->nn, 128);
-    if (ctx->prm.storage == SLLBM_F64)
+    if (ctx->prm.storage == SLLBM_F64 || ctx->adj_f64)
         init_vjp_kernel<double><<<grid, 128, 0, ctx->stream>>>(rho, u, T, static_cast<const double*>(lam), ctx->nn,
                                                                gfac, adj_vel(ctx), grad_rho, grad_u, grad_T);
     else

@@ -48,6 +48,8 @@ struct sllbm_ctx {
     void* adj_buf[2];          // reverse-mode scratch (state-sized), allocated on first use
     double* d_adj_partials;    // per-block partials of the mu_inf sensitivity
     int adj_blocks;
+    size_t adj_bytes;          // size of each reverse-mode scratch buffer
+    bool adj_f64;              // FP32 storage with FP64 adjoint populations
 };
 
 namespace sllbm {

@@ -108,6 +108,7 @@ def load(build_if_missing: bool = False):
         "sllbm_load_state": (ctypes.c_int, [vp, vp]),
         "sllbm_set_mu_inf": (ctypes.c_int, [vp, ctypes.c_double]),
         "sllbm_stream_apply": (ctypes.c_int, [vp, vp, vp, ctypes.c_int]),
+        "sllbm_set_adjoint_type": (ctypes.c_int, [vp, ctypes.c_int]),
         "sllbm_adjoint_step": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "sllbm_ek_adjoint": (ctypes.c_int, [vp, vp, vp]),
         "sllbm_init_fields_adjoint": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp]),
@@ -304,6 +305,10 @@ def sllbm_set_mu_inf(ctx, mu_inf: float) -> None:
     _check(load().sllbm_set_mu_inf(ctx, float(mu_inf)), "sllbm_set_mu_inf", ctx)
 
 
+def sllbm_set_adjoint_type(ctx, storage: int) -> None:
+    _check(load().sllbm_set_adjoint_type(ctx, int(storage)), "sllbm_set_adjoint_type", ctx)
+
+
 def sllbm_stream_apply(ctx, src_ptr: int, dst_ptr: int, transpose: bool) -> None:
     _check(load().sllbm_stream_apply(ctx, ctypes.c_void_p(src_ptr), ctypes.c_void_p(dst_ptr),
                                      int(bool(transpose))), "sllbm_stream_apply", ctx)
@@ -450,6 +455,16 @@ class Sim:
     def state_like(self):
         """An uninitialised tensor shaped and typed like a state buffer [45, Nz, Ny, Nx, 2]."""
         return self.torch.empty((Q,) + self.N[::-1] + (2,), dtype=self.pop_dtype, device=self.device)
+
+    def set_adjoint_type(self, storage: str) -> None:
+        """Type of the adjoint populations of reverse-mode calls: "f64" keeps them in FP64
+        next to FP32 forward states; the storage type is the default."""
+        sllbm_set_adjoint_type(self.ctx, STORAGE[storage])
+        self._adj_f64 = storage == "f64"
+
+    @property
+    def adjoint_dtype(self):
+        return self.torch.float64 if getattr(self, "_adj_f64", False) else self.pop_dtype
 
     def set_variant(self, variant: int) -> None:
         """Step kernel: 0 TMA-fed, 1 generic default tile, 2 and 3 generic alternative tiles."""

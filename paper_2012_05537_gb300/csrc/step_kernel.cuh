@@ -82,6 +82,17 @@ __device__ __forceinline__ typename Pair2<C>::T load_pair(const S* p) {
     return r;
 }
 
+template <typename C, int P>
+__device__ __forceinline__ void load_pass_weights(const C (&w)[P][P + 1], const signed char (&kc)[P],
+                                                  C (&wr)[P][P + 1], signed char (&kr)[P]) {
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+        kr[a] = kc[a];
+#pragma unroll
+        for (int l = 0; l <= P; ++l) wr[a][l] = w[a][l];
+    }
+}
+
 // One 1D Lagrange pass over a column held in registers: output o (0..T-1, local index
 // a = o % P in cell o / P) = sum_l w[a][l] v[(o/P + k_a) P + l] with k_a in {0, 1}.
 template <typename C, int P, int T, int NV>
@@ -339,6 +350,11 @@ __global__ void __launch_bounds__(NW * 32)
         // storage order [i][node][h]: the pair (f_i, g_i) of a node is two adjacent values
         const S* __restrict__ sp = src + 2LL * i * a.nn;
         const int sx = s[0], sxy = s[0] * s[1];
+        // each pass reads the pair's weights and departure-cell bits of its direction from
+        // the constant bank once, before its column loop
+        C wz[P][P + 1];
+        signed char kz[P];
+        load_pass_weights<C, P>(t.lw[i][2], t.kc[i][2], wz, kz);
         // gather + z pass: lane = column (x, y) of the source box
         for (int col = lane; col < sxy; col += 32) {
             const int y = col / sx;
@@ -355,13 +371,16 @@ __global__ void __launch_bounds__(NW * 32)
                 }
             }
             C2 r[TS::TZ];
-            lagrange_column<C, P, TS::TZ, TS::BZ>(v, t.lw[i][2], t.kc[i][2], r);
+            lagrange_column<C, P, TS::TZ, TS::BZ>(v, wz, kz, r);
 #pragma unroll
             for (int oz = 0; oz < TS::TZ; ++oz)
                 if (oz < te[2]) zb[oz * sxy + col] = r[oz];
         }
         __syncwarp();
         // y pass in place: lane = column (x, z)
+        C wy[P][P + 1];
+        signed char ky[P];
+        load_pass_weights<C, P>(t.lw[i][1], t.kc[i][1], wy, ky);
         const int ncol = te[2] * sx;
         for (int col = lane; col < ncol; col += 32) {
             const int oz = col / sx;
@@ -378,13 +397,16 @@ __global__ void __launch_bounds__(NW * 32)
                 }
             }
             C2 r[TS::TY];
-            lagrange_column<C, P, TS::TY, TS::BY>(v, t.lw[i][1], t.kc[i][1], r);
+            lagrange_column<C, P, TS::TY, TS::BY>(v, wy, ky, r);
 #pragma unroll
             for (int oy = 0; oy < TS::TY; ++oy)
                 if (oy < te[1]) cp[oy * sx] = r[oy];
         }
         __syncwarp();
         // x pass: lane = row (y, z) of the tile; f_i to OUT[i], g_i to OUT[45 + i]
+        C wx[P][P + 1];
+        signed char kx[P];
+        load_pass_weights<C, P>(t.lw[i][0], t.kc[i][0], wx, kx);
         for (int row = lane; row < TS::TY * TS::TZ; row += 32) {
             const int oz = row / TS::TY;
             const int oy = row - oz * TS::TY;
@@ -401,7 +423,7 @@ __global__ void __launch_bounds__(NW * 32)
                 }
             }
             C2 r[TS::TX];
-            lagrange_column<C, P, TS::TX, TS::BX>(v, t.lw[i][0], t.kc[i][0], r);
+            lagrange_column<C, P, TS::TX, TS::BX>(v, wx, kx, r);
             C* of = out + i * TS::TILE + (oz * TS::TY + oy) * TS::TX;
             C* og = of + kQ * TS::TILE;
 #pragma unroll

@@ -429,11 +429,22 @@ def batch_block(S, torch, device, count, steps, streams=16, seed=0):
     torch.cuda.synchronize()
     batch_ms = ev[0].elapsed_time(ev[1])
     bsteps = steps if steps % 2 == 0 else steps + 1
+    bt.close()
+    # one persistent launch per order and step, tile shape per order autotuned
+    pt = BT.Batch(sims, autotune_steps=4, persistent=True)
+    shapes = pt.shapes()
+    pt.step(2)
+    torch.cuda.synchronize()
+    ev[0].record(pt.stream)
+    pt.step(bsteps)
+    ev[1].record(pt.stream)
+    torch.cuda.synchronize()
+    pers_ms = ev[0].elapsed_time(ev[1])
+    pt.close()
     finite = 0
     for s in sims:
         _, _, T = s.moments()
         finite += bool(torch.isfinite(T).all().item())
-    bt.close()
     for s in sims:
         s.close()
     return {"instances": count, "seed": seed, "steps": steps, "nodes_per_step": nodes,
@@ -441,6 +452,8 @@ def batch_block(S, torch, device, count, steps, streams=16, seed=0):
             "one_by_one_default": {"ms": default_ms, "value": nodes * steps / (default_ms / 1e3)},
             "one_by_one_autotuned": {"ms": tuned_ms, "value": nodes * steps / (tuned_ms / 1e3)},
             "batched_graph": {"ms": batch_ms, "value": nodes * bsteps / (batch_ms / 1e3)},
+            "persistent_graph": {"ms": pers_ms, "value": nodes * bsteps / (pers_ms / 1e3),
+                                 "tile_shape_per_order": {str(k): v for k, v in shapes.items()}},
             "speedup_vs_one_by_one_default": (nodes * bsteps / batch_ms) / (nodes * steps / default_ms),
             "variants_chosen": {str(v): variants.count(v) for v in sorted(set(variants))},
             "instances_finite_at_end": finite, "unit": UNIT}

@@ -261,6 +261,23 @@ int sllbm_batch_create(sllbm_ctx *const *ctxs, int n, int streams, void *cuda_st
  * streams and before work queued on them later.  Asynchronous. */
 int sllbm_batch_step(sllbm_batch *b, int nsteps);
 
+/* The same, as ONE persistent kernel launch per polynomial order and step: every context
+ * of order p is a job of a work list of (context, tile) items that persistent CTAs (grid =
+ * SMs x resident CTAs) walk, each tile with the generic kernel's tile body and the context's
+ * own arguments and tables (copied to shared memory when a CTA moves to another context);
+ * the launches of the (up to three) orders run on separate worker streams and two steps
+ * are captured into one graph.  With tune_steps > 0 an autotuner picks the tile shape per
+ * order (the default tile, one size smaller, one cell): it times tune_steps (rounded up to
+ * even) launches of each from the current states and restores the states.  FP32 storage
+ * without the Prandtl term only (SLLBM_EINVAL otherwise); other conditions as
+ * sllbm_batch_create.  Synchronous. */
+int sllbm_batch_create_persistent(sllbm_ctx *const *ctxs, int n, void *cuda_stream, int tune_steps,
+                                  sllbm_batch **out);
+
+/* Tile shape chosen per order in a persistent batch (0 default, 1 one size smaller, 2 one
+ * cell; -1 for an order the batch does not contain); any output may be NULL. */
+int sllbm_batch_shapes(const sllbm_batch *b, int *shape_p2, int *shape_p3, int *shape_p4);
+
 /* Host-only planning helper used by sllbm_batch_create: assigns n jobs with the given
  * costs to `streams` streams, longest first, each to the least-loaded stream (ties: lowest
  * index); writes assign[n].  SLLBM_EINVAL for n < 1, streams < 1 or a negative cost. */

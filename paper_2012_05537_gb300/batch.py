@@ -1,6 +1,8 @@
-"""Many independent SLLBM instances advanced together: one CUDA graph per two steps of all
-instances (``sllbm_batch_create`` / ``sllbm_batch_step``), each instance on the step kernel
-its autotuning chose (``sllbm_autotune``).  Argument marshalling only."""
+"""Many independent SLLBM instances advanced together, as one CUDA graph per two steps of all
+instances: either each instance's own step kernel on worker streams (``sllbm_batch_create``,
+kernels chosen per instance by ``sllbm_autotune``), or one persistent launch per polynomial
+order over a work list of (instance, tile) items (``sllbm_batch_create_persistent``, tile
+shape per order chosen by its autotuner).  Argument marshalling only."""
 from __future__ import annotations
 
 import torch
@@ -9,17 +11,26 @@ from . import sllbm as S
 
 
 class Batch:
-    def __init__(self, sims, streams: int = 16, autotune_steps: int = 0, stream=None):
+    def __init__(self, sims, streams: int = 16, autotune_steps: int = 0, stream=None, persistent: bool = False):
         self.sims = list(sims)
         dev = self.sims[0].device
         self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
         self.tuned = []
-        if autotune_steps > 0:
+        self.persistent = persistent
+        if autotune_steps > 0 and not persistent:
             for s in self.sims:
                 self.tuned.append(s.autotune(autotune_steps))
         torch.cuda.synchronize(dev)
         with torch.cuda.device(dev):
-            self.handle = S.sllbm_batch_create([s.ctx for s in self.sims], streams, self.stream.cuda_stream)
+            if persistent:
+                self.handle = S.sllbm_batch_create_persistent([s.ctx for s in self.sims], self.stream.cuda_stream,
+                                                              autotune_steps)
+            else:
+                self.handle = S.sllbm_batch_create([s.ctx for s in self.sims], streams, self.stream.cuda_stream)
+
+    def shapes(self):
+        """Tile shape per order of a persistent batch."""
+        return S.sllbm_batch_shapes(self.handle)
 
     def step(self, nsteps: int) -> None:
         """Advances every instance by nsteps (even) steps; asynchronous."""

@@ -13,7 +13,17 @@
 
 using namespace sllbm;
 
+// One order's share of a persistent batch: its job list and tables on the device.
+struct BatchGroup {
+    int p = 0, shape = 0, grid = 1, njobs = 0;
+    long long items = 0;
+    BatchJob* d_jobs = nullptr;
+    void* d_tabs = nullptr;
+    std::vector<int> members;  // indices into sllbm_batch::ctx
+};
+
 struct sllbm_batch {
+    std::vector<BatchGroup> groups;  // persistent batches only
     std::vector<sllbm_ctx*> ctx;
     std::vector<int> parity;     // ctx->cur when the graph was captured
     std::vector<cudaStream_t> workers;
@@ -56,8 +66,50 @@ int cuda_fail(sllbm_ctx* ctx, cudaError_t e) {
     return SLLBM_ECUDA;
 }
 
+void free_group(BatchGroup& g) {
+    cudaFree(g.d_jobs);
+    cudaFree(g.d_tabs);
+    g.d_jobs = nullptr;
+    g.d_tabs = nullptr;
+}
+
+// Builds the job list and tables of group g for its tile shape (synchronous copies).
+int build_group(BatchGroup& g, const std::vector<sllbm_ctx*>& ctx, int num_sms) {
+    free_group(g);
+    int tc[3];
+    batch_tile_cells(g.p, g.shape, tc);
+    std::vector<BatchJob> jobs(g.members.size());
+    const size_t tb = batch_tables_bytes(g.p);
+    std::vector<unsigned char> tabs(tb * g.members.size());
+    long long items = 0;
+    for (size_t k = 0; k < g.members.size(); ++k) {
+        const sllbm_ctx* c = ctx[g.members[k]];
+        for (int par = 0; par < 2; ++par) {
+            const int from = par == 0 ? c->cur : 1 - c->cur;
+            fill_step_args(c, c->buf[from], c->buf[1 - from], &jobs[k].args[par]);
+            jobs[k].args[par].flag = nullptr;
+            for (int d = 0; d < 3; ++d) jobs[k].args[par].tiles[d] = (c->cells[d] + tc[d] - 1) / tc[d];
+        }
+        jobs[k].tile_begin = items;
+        items += static_cast<long long>(jobs[k].args[0].tiles[0]) * jobs[k].args[0].tiles[1] * jobs[k].args[0].tiles[2];
+        batch_fill_tables(c, tabs.data() + tb * k);
+    }
+    g.njobs = static_cast<int>(jobs.size());
+    g.items = items;
+    cudaError_t e = cudaMalloc(&g.d_jobs, sizeof(BatchJob) * jobs.size());
+    if (e == cudaSuccess) e = cudaMalloc(&g.d_tabs, tabs.size());
+    if (e == cudaSuccess) e = cudaMemcpy(g.d_jobs, jobs.data(), sizeof(BatchJob) * jobs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g.d_tabs, tabs.data(), tabs.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_group(g);
+        return e == cudaErrorMemoryAllocation ? SLLBM_ENOMEM : SLLBM_ECUDA;
+    }
+    return batch_group_grid(g.p, g.shape, num_sms, items, &g.grid);
+}
+
 void destroy_batch(sllbm_batch* b) {
     if (b == nullptr) return;
+    for (BatchGroup& g : b->groups) free_group(g);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     for (cudaEvent_t e : b->join) cudaEventDestroy(e);
@@ -270,7 +322,147 @@ int sllbm_batch_step(sllbm_batch* b, int nsteps) {
         if (b->ctx[k]->stream != b->stream) e = cudaStreamWaitEvent(b->ctx[k]->stream, b->done, 0);
     }
     if (e != cudaSuccess) return cuda_fail(b->ctx[0], e);
-    for (int k = 0; k < n; ++k) b->ctx[k]->launches += nsteps;
+    if (b->groups.empty())
+        for (int k = 0; k < n; ++k) b->ctx[k]->launches += nsteps;
+    return SLLBM_OK;
+}
+
+int sllbm_batch_create_persistent(sllbm_ctx* const* ctxs, int n, void* cuda_stream, int tune_steps,
+                                  sllbm_batch** out) {
+    if (out == nullptr) return SLLBM_EINVAL;
+    *out = nullptr;
+    if (ctxs == nullptr || n < 1 || cuda_stream == nullptr || tune_steps < 0) return SLLBM_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SLLBM_ECUDA;
+    for (int k = 0; k < n; ++k) {
+        const sllbm_ctx* c = ctxs[k];
+        if (c == nullptr || !c->initialised || c->prm.nonfinite_check || c->device != dev) return SLLBM_EINVAL;
+        if (c->prm.storage != SLLBM_F32 || c->prm.pr_correction || !c->prm.collide) return SLLBM_EINVAL;
+        for (int j = 0; j < k; ++j)
+            if (ctxs[j] == c) return SLLBM_EINVAL;
+    }
+    sllbm_batch* b = new (std::nothrow) sllbm_batch;
+    if (b == nullptr) return SLLBM_ENOMEM;
+    b->ctx.assign(ctxs, ctxs + n);
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    for (int k = 0; k < n; ++k) b->parity.push_back(ctxs[k]->cur);
+    for (int p = 2; p <= 4; ++p) {
+        BatchGroup g;
+        g.p = p;
+        for (int k = 0; k < n; ++k)
+            if (ctxs[k]->p == p) g.members.push_back(k);
+        if (!g.members.empty()) b->groups.push_back(g);
+    }
+    const int num_sms = ctxs[0]->num_sms;
+    int rc = SLLBM_OK;
+    cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+    for (size_t s = 0; s < b->groups.size() && e == cudaSuccess; ++s) {
+        cudaStream_t w = nullptr;
+        cudaEvent_t j = nullptr;
+        e = cudaStreamCreateWithFlags(&w, cudaStreamNonBlocking);
+        if (e == cudaSuccess) b->workers.push_back(w);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->join.push_back(j);
+    }
+    for (int k = 0; k < n && e == cudaSuccess; ++k) {
+        cudaEvent_t r = nullptr;
+        e = cudaEventCreateWithFlags(&r, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->ready.push_back(r);
+    }
+    if (e != cudaSuccess) rc = SLLBM_ECUDA;
+
+    // Autotuner: per order, time `tune_steps` (rounded up to even) launches of each tile shape
+    // from the current states and keep the fastest; the states are restored afterwards.
+    if (rc == SLLBM_OK && tune_steps > 0) {
+        const int steps = tune_steps + (tune_steps & 1);
+        std::vector<void*> saved(n, nullptr);
+        for (int k = 0; k < n && rc == SLLBM_OK; ++k) {
+            e = cudaMalloc(&saved[k], ctxs[k]->pop_bytes);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(saved[k], ctxs[k]->buf[ctxs[k]->cur], ctxs[k]->pop_bytes, cudaMemcpyDeviceToDevice);
+            if (e != cudaSuccess) rc = e == cudaErrorMemoryAllocation ? SLLBM_ENOMEM : SLLBM_ECUDA;
+        }
+        cudaEvent_t ev[2] = {nullptr, nullptr};
+        if (rc == SLLBM_OK && (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess))
+            rc = SLLBM_ECUDA;
+        for (BatchGroup& g : b->groups) {
+            float best_ms = 0.0f;
+            int best = -1;
+            for (int sh = 0; sh < 3 && rc == SLLBM_OK; ++sh) {
+                g.shape = sh;
+                rc = build_group(g, b->ctx, num_sms);
+                if (rc != SLLBM_OK) break;
+                rc = launch_batch_group(g.p, g.shape, g.d_jobs, g.njobs, g.d_tabs, g.items, 0, g.grid, b->stream);
+                if (rc == SLLBM_OK) rc = launch_batch_group(g.p, g.shape, g.d_jobs, g.njobs, g.d_tabs, g.items, 1,
+                                                            g.grid, b->stream);
+                if (rc == SLLBM_OK && cudaEventRecord(ev[0], b->stream) != cudaSuccess) rc = SLLBM_ECUDA;
+                for (int s2 = 0; s2 < steps && rc == SLLBM_OK; ++s2)
+                    rc = launch_batch_group(g.p, g.shape, g.d_jobs, g.njobs, g.d_tabs, g.items, s2 & 1, g.grid,
+                                            b->stream);
+                float ms = 0.0f;
+                if (rc == SLLBM_OK && (cudaEventRecord(ev[1], b->stream) != cudaSuccess ||
+                                       cudaEventSynchronize(ev[1]) != cudaSuccess ||
+                                       cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess))
+                    rc = SLLBM_ECUDA;
+                if (rc == SLLBM_OK && (best < 0 || ms < best_ms)) {
+                    best = sh;
+                    best_ms = ms;
+                }
+            }
+            if (rc != SLLBM_OK) break;
+            g.shape = best;
+        }
+        for (int k = 0; k < n; ++k) {
+            if (saved[k] != nullptr && rc == SLLBM_OK)
+                if (cudaMemcpy(ctxs[k]->buf[ctxs[k]->cur], saved[k], ctxs[k]->pop_bytes, cudaMemcpyDeviceToDevice) !=
+                    cudaSuccess)
+                    rc = SLLBM_ECUDA;
+            cudaFree(saved[k]);
+        }
+        if (ev[0]) cudaEventDestroy(ev[0]);
+        if (ev[1]) cudaEventDestroy(ev[1]);
+    }
+    for (size_t s = 0; s < b->groups.size() && rc == SLLBM_OK; ++s) rc = build_group(b->groups[s], b->ctx, num_sms);
+
+    // the graph: per order, on its own worker stream, two launches (parity 0 then 1)
+    if (rc == SLLBM_OK) {
+        e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->stream);
+        for (size_t s = 0; s < b->groups.size() && e == cudaSuccess && rc == SLLBM_OK; ++s) {
+            const BatchGroup& g = b->groups[s];
+            e = cudaStreamWaitEvent(b->workers[s], b->fork, 0);
+            for (int par = 0; par < 2 && e == cudaSuccess && rc == SLLBM_OK; ++par)
+                rc = launch_batch_group(g.p, g.shape, g.d_jobs, g.njobs, g.d_tabs, g.items, par, g.grid, b->workers[s]);
+            if (e == cudaSuccess && rc == SLLBM_OK) e = cudaEventRecord(b->join[s], b->workers[s]);
+            if (e == cudaSuccess && rc == SLLBM_OK) e = cudaStreamWaitEvent(b->stream, b->join[s], 0);
+        }
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e_end = cudaStreamEndCapture(b->stream, &graph);
+        if (rc == SLLBM_OK && e == cudaSuccess && e_end == cudaSuccess) {
+            b->graph = graph;
+            if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) rc = SLLBM_ECUDA;
+        } else {
+            if (graph) cudaGraphDestroy(graph);
+            if (rc == SLLBM_OK) rc = SLLBM_ECUDA;
+        }
+    }
+    if (rc != SLLBM_OK) {
+        cudaGetLastError();
+        destroy_batch(b);
+        return rc;
+    }
+    *out = b;
+    return SLLBM_OK;
+}
+
+int sllbm_batch_shapes(const sllbm_batch* b, int* shape_p2, int* shape_p3, int* shape_p4) {
+    if (b == nullptr) return SLLBM_EINVAL;
+    int* dst[3] = {shape_p2, shape_p3, shape_p4};
+    for (int k = 0; k < 3; ++k)
+        if (dst[k]) *dst[k] = -1;
+    for (const BatchGroup& g : b->groups)
+        if (dst[g.p - 2]) *dst[g.p - 2] = g.shape;
     return SLLBM_OK;
 }
 

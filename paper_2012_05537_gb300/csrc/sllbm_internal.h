@@ -120,6 +120,23 @@ void fill_step_args(const sllbm_ctx* ctx, const void* src, void* dst, StepArgs* 
 // and swap (api.cu).  No flag handling, no synchronisation.
 int step_launch(sllbm_ctx* ctx);
 
+// One mesh of a persistent batched launch: args[parity] are its step arguments from buffer
+// `parity` of its ping-pong pair (parity alternates between launches); its tiles are the
+// work items [tile_begin, next job's tile_begin).
+struct BatchJob {
+    StepArgs args[2];
+    long long tile_begin;
+};
+
+// Persistent batched FP32 step of many meshes of order p (batch_kernel.cu).  Tile shapes
+// (cells): 0 the generic kernel's default, 1 one size smaller, 2 one cell.
+void batch_tile_cells(int p, int shape, int cells[3]);
+size_t batch_tables_bytes(int p);                              // sizeof(StepTables<float, p>)
+void batch_fill_tables(const sllbm_ctx* ctx, void* host_dst);  // StepTables<float, ctx->p>
+int batch_group_grid(int p, int shape, int num_sms, long long items, int* grid);
+int launch_batch_group(int p, int shape, const BatchJob* jobs, int njobs, const void* tabs, long long items,
+                       int parity, int grid, cudaStream_t stream);
+
 // True when the TMA-fed FP32 kernel can run this context (step_f32.cu).
 bool tma_step_eligible(const sllbm_ctx* c);
 

@@ -310,13 +310,15 @@ __device__ __forceinline__ void collide_node(const C* __restrict__ h, int stride
     }
 }
 
+// The step of one tile (tile index `tile` of the mesh a describes), all NW warps of the CTA,
+// with the CTA's dynamic shared memory at smem_raw.  Used by step_kernel (one tile per CTA)
+// and by the batched persistent kernel (many tiles of many meshes per CTA).
 template <typename S, typename C, int P, int CX, int CY, int CZ, int NW, bool PR>
-__global__ void __launch_bounds__(NW * 32)
-    step_kernel(const StepArgs a, const __grid_constant__ StepTables<C, P> t) {
+__device__ __forceinline__ void step_tile(const StepArgs& a, const StepTables<C, P>& t, int tile,
+                                          unsigned char* smem_raw) {
     using TS = TileShape<CX, CY, CZ, P>;
     using SM = StepSmem<C, P, CX, CY, CZ, NW>;
     using C2 = typename Pair2<C>::T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     C* out = reinterpret_cast<C*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     C2* zb = reinterpret_cast<C2*>(smem_raw + SM::out_bytes) + warp * SM::warp_pairs;
@@ -325,7 +327,6 @@ __global__ void __launch_bounds__(NW * 32)
     int* yo = xo + TS::BX;
     int* zo = yo + TS::BY;
 
-    int tile = blockIdx.x;
     const int tix = tile % a.tiles[0];
     tile /= a.tiles[0];
     const int tiy = tile % a.tiles[1];
@@ -448,6 +449,57 @@ __global__ void __launch_bounds__(NW * 32)
         const long long g = (static_cast<long long>(c0[2] * P + oz) * a.N[1] + (c0[1] * P + oy)) * a.N[0]
                           + (c0[0] * P + ox);
         collide_node<S, C, P, PR>(out + n, TS::TILE, a, t, dst + 2 * g);
+    }
+}
+
+template <typename S, typename C, int P, int CX, int CY, int CZ, int NW, bool PR>
+__global__ void __launch_bounds__(NW * 32)
+    step_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ StepTables<C, P> t) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    step_tile<S, C, P, CX, CY, CZ, NW, PR>(a, t, blockIdx.x, smem_raw);
+}
+
+// Many meshes of one order in one launch: job k of the list (BatchJob) owns work items
+// [tile_begin_k, tile_begin_{k+1}) (its tiles in order); persistent CTAs walk the items with
+// a grid stride.
+// Shared memory of the batched kernel: the tile body's, then the current job's tables and
+// arguments (copied from global memory when a CTA moves to another job).
+template <typename C, int P, int CX, int CY, int CZ, int NW>
+struct BatchSmem {
+    static constexpr size_t body = (StepSmem<C, P, CX, CY, CZ, NW>::bytes + 15) / 16 * 16;
+    static constexpr size_t tab = (sizeof(StepTables<C, P>) + 15) / 16 * 16;
+    static constexpr size_t arg = (sizeof(StepArgs) + 15) / 16 * 16;
+    static constexpr size_t bytes = body + tab + arg;
+};
+
+template <typename C, int P, int CX, int CY, int CZ, int NW>
+__global__ void __launch_bounds__(NW * 32)
+    batch_step_kernel(const BatchJob* __restrict__ jobs, int njobs, const StepTables<C, P>* __restrict__ tabs,
+                      long long total, int parity) {
+    using BS = BatchSmem<C, P, CX, CY, CZ, NW>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    StepTables<C, P>* st = reinterpret_cast<StepTables<C, P>*>(smem_raw + BS::body);
+    StepArgs* sa = reinterpret_cast<StepArgs*>(smem_raw + BS::body + BS::tab);
+    int have = -1;
+    for (long long w = blockIdx.x; w < total; w += gridDim.x) {
+        int lo = 0, hi = njobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].tile_begin <= w) lo = mid;
+            else hi = mid - 1;
+        }
+        if (lo != have) {
+            static_assert(sizeof(StepTables<C, P>) % 4 == 0, "tables are copied in 4-byte words");
+            const unsigned* tsrc = reinterpret_cast<const unsigned*>(tabs + lo);
+            unsigned* tdst = reinterpret_cast<unsigned*>(st);
+            for (int k = threadIdx.x; k < static_cast<int>(sizeof(StepTables<C, P>) / 4); k += NW * 32)
+                tdst[k] = tsrc[k];
+            if (threadIdx.x == 0) *sa = jobs[lo].args[parity];
+            have = lo;
+            __syncthreads();
+        }
+        step_tile<C, C, P, CX, CY, CZ, NW, false>(*sa, *st, static_cast<int>(w - jobs[lo].tile_begin), smem_raw);
+        __syncthreads();  // the next item reuses the shared memory
     }
 }
 

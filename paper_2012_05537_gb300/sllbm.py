@@ -104,6 +104,10 @@ def load(build_if_missing: bool = False):
         "sllbm_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, vp,
                                               ctypes.POINTER(vp)]),
         "sllbm_batch_step": (ctypes.c_int, [vp, ctypes.c_int]),
+        "sllbm_batch_create_persistent": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.c_int,
+                                                         ctypes.POINTER(vp)]),
+        "sllbm_batch_shapes": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int)]),
         "sllbm_batch_destroy": (None, [vp]),
         "sllbm_load_state": (ctypes.c_int, [vp, vp]),
         "sllbm_set_mu_inf": (ctypes.c_int, [vp, ctypes.c_double]),
@@ -287,6 +291,21 @@ def sllbm_batch_create(ctxs, streams: int, stream: int):
     _check(load().sllbm_batch_create(arr, len(ctxs), int(streams), ctypes.c_void_p(stream), ctypes.byref(b)),
            "sllbm_batch_create")
     return b
+
+
+def sllbm_batch_create_persistent(ctxs, stream: int, tune_steps: int = 0):
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    b = ctypes.c_void_p()
+    _check(load().sllbm_batch_create_persistent(arr, len(ctxs), ctypes.c_void_p(stream), int(tune_steps),
+                                                ctypes.byref(b)), "sllbm_batch_create_persistent")
+    return b
+
+
+def sllbm_batch_shapes(b):
+    """Tile shape per order (p = 2, 3, 4) of a persistent batch; -1 where the order is absent."""
+    v = [ctypes.c_int() for _ in range(3)]
+    _check(load().sllbm_batch_shapes(b, *(ctypes.byref(x) for x in v)), "sllbm_batch_shapes")
+    return {2: v[0].value, 3: v[1].value, 4: v[2].value}
 
 
 def sllbm_batch_step(b, nsteps: int) -> None:

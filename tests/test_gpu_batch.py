@@ -116,3 +116,35 @@ def test_batch_refuses_the_legacy_stream_and_duplicates(S):
     st = torch.cuda.Stream()
     with pytest.raises(S.SllbmError):
         S.sllbm_batch_create([sim.ctx, sim.ctx], 1, st.cuda_stream)
+
+
+@pytest.mark.parametrize("tune", [0, 2])
+def test_persistent_batch_equals_instances_stepped_alone(S, tune):
+    """One persistent launch per order over all instances' tiles: bit for bit the generic
+    kernel's result for every instance (each node is computed from the same values with the
+    same weights in the same order, whatever the tile shape)."""
+    insts = I.batch_instances(10, 6)
+    insts = [I.Instance(cells=(min(i.cells[0], 11),) * 3, p=i.p, Ma=min(i.Ma, 0.9), Re=i.Re,
+                        courant=min(i.courant, 4.0)) for i in insts]
+    from paper_2012_05537_gb300 import batch as BT
+    sims = BT.make_instances(insts)
+    alone = BT.make_instances(insts)
+    for b in alone:
+        b.set_variant(1)
+    bt = BT.Batch(sims, autotune_steps=tune, persistent=True)
+    shapes = bt.shapes()
+    assert all(shapes[p] in ((0, 1, 2) if p in {i.p for i in insts} else (-1,)) for p in (2, 3, 4))
+    bt.step(4)
+    for b in alone:
+        assert b.step(4) == 0
+    torch.cuda.synchronize()
+    for a, b in zip(sims, alone):
+        assert torch.equal(a.raw_state(), b.raw_state())
+    bt.close()
+
+
+def test_persistent_batch_refuses_other_storage(S):
+    sim = S.Sim(S.Config(cells=(2, 2, 2), p=2, storage="f64")).init_tgv()
+    st = torch.cuda.Stream()
+    with pytest.raises(S.SllbmError):
+        S.sllbm_batch_create_persistent([sim.ctx], st.cuda_stream, 0)

@@ -3,10 +3,11 @@
 //
 //   * streaming S = S_x S_y S_z per velocity (Eq. interpolation on the uniform mesh: each
 //     1D factor gathers p+1 support values of the departure cell with the precomputed
-//     Lagrange weights).  Its transpose is applied as three 1D passes in gather form: node
-//     m = c p + b receives w[a][b] from every node (c - k_a) p + a, and for b = 0 also
-//     w[a][p] from (c - 1 - k_a) p + a (the right-face support point of the cell to the
-//     left).  No atomics, each output written once.
+//     Lagrange weights).  Its transpose, in gather form: node m = c p + b receives w[a][b]
+//     from every node (c - k_a) p + a, and for b = 0 also w[a][p] from (c - 1 - k_a) p + a
+//     (the right-face support point of the cell to the left).  No atomics, each output
+//     written once.  FP32: a tile kernel (the three transposed passes in registers and shared
+//     memory); FP64 arithmetic: three 1D pass kernels.
 //   * collision (Eq. LBM with Eq. moments, Eq. discreteEquilibrium in its quartic form,
 //     tau = mu/(P dt) + 1/2, Sutherland mu): a node-local vector-Jacobian product through
 //     the primitive variables rho, u, T and omega, derived by hand below.
@@ -14,9 +15,11 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <type_traits>
 
 #include "collide.cuh"
 #include "sllbm_internal.h"
+#include "step_kernel.cuh"
 #include "tables.h"
 
 namespace sllbm {
@@ -137,8 +140,10 @@ struct AdjArgs {
     double gfac;
 };
 
-// Per node: h = streamed populations (pairs), lam = adjoint of the collided populations;
-// out = J^T lam, and the block's share of lam . d collide / d mu_inf in partials[block].
+// Vector-Jacobian product of the collision at one node.  h: streamed populations, f_i at
+// h[i * hs] and g_i at h[i * hs + hg]; lam: adjoint of the collided populations and out: the
+// result (J^T lam), both with f_i at [i * 2 nn] and g_i at [i * 2 nn + 1] (a state buffer's
+// pair layout, offset to the node).  Returns the node's lam . d collide / d mu_inf.
 //
 // Forward (per node):  rho = sum f, j = sum f xi, E2 = sum (f |xi|^2 + g),
 //   u = j/rho, T = (E2/rho - |u|^2)/(2 C_v), tau = K su(T)/(rho T) + 1/2, omega = 1/tau,
@@ -149,84 +154,281 @@ struct AdjArgs {
 //   omega depends on rho and T (and mu_inf); the primitive adjoints are mapped back to the
 //   moments (rho, j, E2) and from there to the populations.
 template <typename CH, typename C>
+__device__ __forceinline__ double vjp_node(const CH* __restrict__ h, long long hs, long long hg,
+                                           const C* __restrict__ lam, C* __restrict__ out, long long nn,
+                                           const AdjArgs& aa, const AdjVel& v) {
+    const C gfac = C(aa.gfac), inv_2cv = C(aa.inv_2cv), K = C(aa.mu_over_dt);
+    const long long ls = 2 * nn;
+    C rho = 0, jx = 0, jy = 0, jz = 0, E2 = 0;
+    for (int i = 0; i < kQ; ++i) {
+        const C f = C(h[i * hs]), g = C(h[i * hs + hg]);
+        rho += f;
+        jx += f * C(v.xi[i][0]);
+        jy += f * C(v.xi[i][1]);
+        jz += f * C(v.xi[i][2]);
+        E2 += f * C(shell_xi2(shell_of(i))) + g;
+    }
+    const C ux = jx / rho, uy = jy / rho, uz = jz / rho;
+    const C usq = ux * ux + uy * uy + uz * uz;
+    const C T = (E2 / rho - usq) * inv_2cv;
+    const C th = T - C(1);
+    const C su = sutherland(T);
+    const C tau = K * su / (rho * T) + C(0.5);
+    const C om = C(1) / tau;
+    const EqCoef<C> ec = eq_coefficients(usq, th);
+    C B = 0, ATd = 0, arho = 0, aux = 0, auy = 0, auz = 0, ausq = 0, ath = 0;
+    // shell by shell, so that the shell's polynomial coefficients are plain registers
+#pragma unroll
+    for (int sh = 0; sh < 4; ++sh) {
+        const C x2 = C(shell_xi2(sh));
+        const C c0 = ec.c0[sh], c1 = ec.c1[sh], c2 = ec.c2[sh];
+        const C dusq0 = C(-0.5) + C(0.25) * usq + C(0.25) * th * (C(5) - x2);
+        const C dth0 = C(0.5) * (x2 - C(3)) + C(0.25) * usq * (C(5) - x2) + C(0.25) * th * (x2 * x2 - C(10) * x2 + C(15));
+        const C dth1 = C(0.5) * (x2 - C(5)), dth2 = C(0.25) * (x2 - C(7));
+        // first velocity of each shell in the canonical order: 0, 1, 13, 33, 45
+        const int i0 = sh == 0 ? 0 : (sh == 1 ? 1 : (sh == 2 ? 13 : 33));
+        const int i1 = sh == 0 ? 1 : (sh == 1 ? 13 : (sh == 2 ? 33 : 45));
+#pragma unroll 1
+        for (int i = i0; i < i1; ++i) {
+            const C x = C(v.xi[i][0]), y = C(v.xi[i][1]), z = C(v.xi[i][2]), w = C(v.w[i]);
+            const C s = x * ux + y * uy + z * uz;
+            // f^eq_i/(w rho) = c0 + c1 s + c2 s^2 + s^3/6 + s^4/24 and its derivatives
+            const C P = c0 + s * (c1 + s * (c2 + s * (C(1.0 / 6.0) + s * C(1.0 / 24.0))));
+            const C Ps = c1 + s * (C(2) * c2 + s * (C(0.5) + s * C(1.0 / 6.0)));
+            const C Pusq = dusq0 - C(0.5) * s - C(0.25) * s * s;
+            const C Pth = dth0 + dth1 * s + dth2 * s * s;
+            const C feq = w * rho * P, geq = gfac * T * feq;
+            const C lf = lam[i * ls], lg = lam[i * ls + 1];
+            const C hf = C(h[i * hs]), hgv = C(h[i * hs + hg]);
+            B += lf * (feq - hf) + lg * (geq - hgv);
+            const C A = om * (lf + gfac * T * lg);
+            ATd += om * gfac * lg * feq;
+            const C Aw = A * w;
+            arho += Aw * P;
+            const C t = Aw * rho * Ps;
+            aux += t * x;
+            auy += t * y;
+            auz += t * z;
+            ausq += Aw * rho * Pusq;
+            ath += Aw * rho * Pth;
+        }
+    }
+    // omega = 1/tau: d omega/d tau = -omega^2; d ln su/dT = 3/(2T) - 1/(T + S)
+    const C dom = -om * om;
+    const C dtau_drho = -K * su / (rho * rho * T);
+    const C dtau_dT = K * su / (rho * T) * (sutherland_dlog(T) - C(1) / T);
+    const double dmu = static_cast<double>(B * dom * su / (rho * T)) * aa.inv_dt;
+    C Arho = arho + B * dom * dtau_drho;
+    const C AT = ath + ATd + B * dom * dtau_dT;
+    C Aux = aux + C(2) * ux * ausq, Auy = auy + C(2) * uy * ausq, Auz = auz + C(2) * uz * ausq;
+    // T = (E2/rho - |u|^2)/(2 C_v)
+    const C AE2 = AT * inv_2cv / rho;
+    Arho -= AT * inv_2cv * E2 / (rho * rho);
+    Aux -= C(2) * AT * inv_2cv * ux;
+    Auy -= C(2) * AT * inv_2cv * uy;
+    Auz -= C(2) * AT * inv_2cv * uz;
+    // u = j/rho
+    const C Ajx = Aux / rho, Ajy = Auy / rho, Ajz = Auz / rho;
+    Arho -= (Aux * ux + Auy * uy + Auz * uz) / rho;
+    const C keep = C(1) - om;
+    for (int i = 0; i < kQ; ++i) {
+        const C x = C(v.xi[i][0]), y = C(v.xi[i][1]), z = C(v.xi[i][2]);
+        const C lf = lam[i * ls], lg = lam[i * ls + 1];
+        out[i * ls] = keep * lf + Arho + Ajx * x + Ajy * y + Ajz * z + AE2 * C(shell_xi2(shell_of(i)));
+        out[i * ls + 1] = keep * lg + AE2;
+    }
+    return dmu;
+}
+
+// Block sum of a per-thread double into partials[blockIdx.x] (blockDim.x a multiple of 32).
+__device__ __forceinline__ void block_partial(double x, double* partials) {
+    __shared__ double red[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) s += red[w];
+        partials[blockIdx.x] = s;
+    }
+}
+
+// The collision VJP at every node, h already streamed (a state-sized array, pair layout).
+template <typename CH, typename C>
 __global__ void __launch_bounds__(128) collide_vjp_kernel(const CH* __restrict__ h, const C* __restrict__ lam,
                                                           C* __restrict__ out, long long nn, AdjArgs aa,
                                                           const __grid_constant__ AdjVel v,
                                                           double* __restrict__ partials) {
-    __shared__ double red[4];
     double dmu_acc = 0.0;
-    const C gfac = C(aa.gfac), inv_2cv = C(aa.inv_2cv), K = C(aa.mu_over_dt);
     for (long long n = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; n < nn;
-         n += static_cast<long long>(gridDim.x) * blockDim.x) {
-        C rho = 0, jx = 0, jy = 0, jz = 0, E2 = 0;
-        for (int i = 0; i < kQ; ++i) {
-            const C f = C(h[2 * (i * nn + n)]), g = C(h[2 * (i * nn + n) + 1]);
-            rho += f;
-            jx += f * C(v.xi[i][0]);
-            jy += f * C(v.xi[i][1]);
-            jz += f * C(v.xi[i][2]);
-            E2 += f * C(shell_xi2(shell_of(i))) + g;
-        }
-        const C ux = jx / rho, uy = jy / rho, uz = jz / rho;
-        const C usq = ux * ux + uy * uy + uz * uz;
-        const C T = (E2 / rho - usq) * inv_2cv;
-        const C th = T - C(1);
-        const C su = sutherland(T);
-        const C tau = K * su / (rho * T) + C(0.5);
-        const C om = C(1) / tau;
-        const EqCoef<C> ec = eq_coefficients(usq, th);
-        C B = 0, ATd = 0, arho = 0, aux = 0, auy = 0, auz = 0, ausq = 0, ath = 0;
-        for (int i = 0; i < kQ; ++i) {
-            const int sh = shell_of(i);
-            const C x = C(v.xi[i][0]), y = C(v.xi[i][1]), z = C(v.xi[i][2]), w = C(v.w[i]);
-            const C s = x * ux + y * uy + z * uz;
-            const PolyDeriv<C> pd = poly_deriv(ec, sh, s, usq, th);
-            const C feq = w * rho * pd.P, geq = gfac * T * feq;
-            const C lf = lam[2 * (i * nn + n)], lg = lam[2 * (i * nn + n) + 1];
-            const C hf = C(h[2 * (i * nn + n)]), hg = C(h[2 * (i * nn + n) + 1]);
-            B += lf * (feq - hf) + lg * (geq - hg);
-            const C A = om * (lf + gfac * T * lg);
-            ATd += om * gfac * lg * feq;
-            const C Aw = A * w;
-            arho += Aw * pd.P;
-            const C t = Aw * rho * pd.ds;
-            aux += t * x;
-            auy += t * y;
-            auz += t * z;
-            ausq += Aw * rho * pd.dusq;
-            ath += Aw * rho * pd.dth;
-        }
-        // omega = 1/tau: d omega/d tau = -omega^2; d ln su/dT = 3/(2T) - 1/(T + S)
-        const C dom = -om * om;
-        const C dtau_drho = -K * su / (rho * rho * T);
-        const C dtau_dT = K * su / (rho * T) * (sutherland_dlog(T) - C(1) / T);
-        dmu_acc += static_cast<double>(B * dom * su / (rho * T)) * aa.inv_dt;
-        C Arho = arho + B * dom * dtau_drho;
-        const C AT = ath + ATd + B * dom * dtau_dT;
-        C Aux = aux + C(2) * ux * ausq, Auy = auy + C(2) * uy * ausq, Auz = auz + C(2) * uz * ausq;
-        // T = (E2/rho - |u|^2)/(2 C_v)
-        const C AE2 = AT * inv_2cv / rho;
-        Arho -= AT * inv_2cv * E2 / (rho * rho);
-        Aux -= C(2) * AT * inv_2cv * ux;
-        Auy -= C(2) * AT * inv_2cv * uy;
-        Auz -= C(2) * AT * inv_2cv * uz;
-        // u = j/rho
-        const C Ajx = Aux / rho, Ajy = Auy / rho, Ajz = Auz / rho;
-        Arho -= (Aux * ux + Auy * uy + Auz * uz) / rho;
-        const C keep = C(1) - om;
-        for (int i = 0; i < kQ; ++i) {
-            const C x = C(v.xi[i][0]), y = C(v.xi[i][1]), z = C(v.xi[i][2]);
-            const C lf = lam[2 * (i * nn + n)], lg = lam[2 * (i * nn + n) + 1];
-            out[2 * (i * nn + n)] =
-                keep * lf + Arho + Ajx * x + Ajy * y + Ajz * z + AE2 * C(shell_xi2(shell_of(i)));
-            out[2 * (i * nn + n) + 1] = keep * lg + AE2;
-        }
-    }
+         n += static_cast<long long>(gridDim.x) * blockDim.x)
+        dmu_acc += vjp_node<CH, C>(h + 2 * n, 2 * nn, 1, lam + 2 * n, out + 2 * n, nn, aa, v);
+    block_partial(dmu_acc, partials);
+}
+
+// ---------------------------------------------------------------- transposed streaming as a tile kernel
+// The transposed streaming in gather form: the 1D transpose sends node
+//     m = c p + b the values of nodes (c - k_a) p + a with weights w[a][b], and for b = 0 also
+//     those of (c - 1 - k_a) p + a with w[a][p]; k_a = kmin + kc[a].  A tile of cells
+//     c0..c0+tc-1 therefore reads the cells c0 - 1 - kmin - span .. c0 + tc - 1 - kmin, p nodes
+//     each (no shared face).
+
+template <int CX, int CY, int CZ, int P>
+struct TransShape {
+    static constexpr int TX = CX * P, TY = CY * P, TZ = CZ * P;
+    static constexpr int BX = (CX + 2) * P, BY = (CY + 2) * P, BZ = (CZ + 2) * P;  // with span 1
+};
+
+template <typename C, int P, int CX, int CY, int CZ, int NW>
+struct TransSmem {
+    using TS = TransShape<CX, CY, CZ, P>;
+    static constexpr size_t warp_pairs = size_t(TS::TZ) * TS::BY * TS::BX;
+    static constexpr size_t warp_ints = TS::BX + TS::BY + TS::BZ;
+    static constexpr size_t bytes = NW * warp_pairs * sizeof(typename Pair2<C>::T) + NW * warp_ints * sizeof(int);
+};
+
+// One transposed 1D pass over a column held in registers (box origin cell c0 - 1 - kmin - span):
+// output o = ci P + b gets sum_a w[a][b] v[(ci + 1 + span - kc[a]) P + a], and for b = 0 also
+// sum_a w[a][P] v[(ci + span - kc[a]) P + a]; span - kc[a] is 0 or 1 (a register select).
+template <typename C, int P, int T, int NV>
+__device__ __forceinline__ void transpose_column(const typename Pair2<C>::T (&v)[NV], const C (&w)[P][P + 1],
+                                                 const signed char (&kc)[P], bool sp, typename Pair2<C>::T (&r)[T]) {
+    static_assert(((T - 1) / P + 2) * P + P - 1 < NV, "column shorter than the support of its outputs");
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dmu_acc += __shfl_down_sync(0xffffffffu, dmu_acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dmu_acc;
-    __syncthreads();
-    if (threadIdx.x == 0) partials[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
+    for (int o = 0; o < T; ++o) {
+        const int ci = o / P, b = o % P;
+        C fx = 0, fy = 0;
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+            const bool d1 = sp && kc[a] == 0;
+            const C wb = w[a][b];
+            fx += wb * (d1 ? v[(ci + 2) * P + a].x : v[(ci + 1) * P + a].x);
+            fy += wb * (d1 ? v[(ci + 2) * P + a].y : v[(ci + 1) * P + a].y);
+            if (b == 0) {
+                const C wp = w[a][P];
+                fx += wp * (d1 ? v[(ci + 1) * P + a].x : v[ci * P + a].x);
+                fy += wp * (d1 ? v[(ci + 1) * P + a].y : v[ci * P + a].y);
+            }
+        }
+        r[o].x = fx;
+        r[o].y = fy;
+    }
+}
+
+// dst = S^T src (both state-sized arrays of adjoint populations, pair layout), one tile per CTA.
+template <typename C, int P, int CX, int CY, int CZ, int NW>
+__global__ void __launch_bounds__(NW * 32)
+    adj_transpose_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ StepTables<C, P> t) {
+    using TS = TransShape<CX, CY, CZ, P>;
+    using SM = TransSmem<C, P, CX, CY, CZ, NW>;
+    using C2 = typename Pair2<C>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    C2* zb = reinterpret_cast<C2*>(smem_raw) + warp * SM::warp_pairs;
+    int* xo = reinterpret_cast<int*>(smem_raw + NW * SM::warp_pairs * sizeof(C2)) + warp * SM::warp_ints;
+    int* yo = xo + TS::BX;
+    int* zo = yo + TS::BY;
+    int tile = blockIdx.x;
+    const int tix = tile % a.tiles[0];
+    tile /= a.tiles[0];
+    const int tiy = tile % a.tiles[1];
+    const int tiz = tile / a.tiles[1];
+    const int c0[3] = {tix * CX, tiy * CY, tiz * CZ};
+    const int tc[3] = {min(CX, a.cells[0] - c0[0]), min(CY, a.cells[1] - c0[1]), min(CZ, a.cells[2] - c0[2])};
+    const int te[3] = {tc[0] * P, tc[1] * P, tc[2] * P};
+    const C* __restrict__ src = static_cast<const C*>(a.src);
+    C* __restrict__ dst = static_cast<C*>(a.dst);
+    const int nxy = a.N[0] * a.N[1];
+    for (int i = warp; i < kQ; i += NW) {
+        int s[3], b0[3];
+        bool sp[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            sp[d] = t.span[i][d] != 0;
+            s[d] = (tc[d] + t.span[i][d] + 1) * P;
+            b0[d] = (c0[d] - 1 - t.kmin[i][d] - t.span[i][d]) * P;
+        }
+        for (int e = lane; e < s[0]; e += 32) xo[e] = wrap_index(b0[0] + e, a.N[0]);
+        for (int e = lane; e < s[1]; e += 32) yo[e] = wrap_index(b0[1] + e, a.N[1]) * a.N[0];
+        for (int e = lane; e < s[2]; e += 32) zo[e] = wrap_index(b0[2] + e, a.N[2]) * nxy;
+        __syncwarp();
+        const C* __restrict__ sp_i = src + 2LL * i * a.nn;
+        const int sx = s[0], sxy = s[0] * s[1];
+        C w[P][P + 1];
+        signed char k[P];
+        load_pass_weights<C, P>(t.lw[i][2], t.kc[i][2], w, k);
+        for (int col = lane; col < sxy; col += 32) {
+            const int y = col / sx;
+            const int x = col - y * sx;
+            const int off = yo[y] + xo[x];
+            C2 v[TS::BZ];
+#pragma unroll
+            for (int z = 0; z < TS::BZ; ++z) {
+                if (z < s[2]) {
+                    v[z] = load_pair<C>(sp_i + 2LL * (zo[z] + off));
+                } else {
+                    v[z].x = C(0);
+                    v[z].y = C(0);
+                }
+            }
+            C2 r[TS::TZ];
+            transpose_column<C, P, TS::TZ, TS::BZ>(v, w, k, sp[2], r);
+#pragma unroll
+            for (int oz = 0; oz < TS::TZ; ++oz)
+                if (oz < te[2]) zb[oz * sxy + col] = r[oz];
+        }
+        __syncwarp();
+        load_pass_weights<C, P>(t.lw[i][1], t.kc[i][1], w, k);
+        const int ncol = te[2] * sx;
+        for (int col = lane; col < ncol; col += 32) {
+            const int oz = col / sx;
+            const int x = col - oz * sx;
+            C2* cp = zb + oz * sxy + x;
+            C2 v[TS::BY];
+#pragma unroll
+            for (int y = 0; y < TS::BY; ++y) {
+                if (y < s[1]) {
+                    v[y] = cp[y * sx];
+                } else {
+                    v[y].x = C(0);
+                    v[y].y = C(0);
+                }
+            }
+            C2 r[TS::TY];
+            transpose_column<C, P, TS::TY, TS::BY>(v, w, k, sp[1], r);
+#pragma unroll
+            for (int oy = 0; oy < TS::TY; ++oy)
+                if (oy < te[1]) cp[oy * sx] = r[oy];
+        }
+        __syncwarp();
+        load_pass_weights<C, P>(t.lw[i][0], t.kc[i][0], w, k);
+        for (int row = lane; row < TS::TY * TS::TZ; row += 32) {
+            const int oz = row / TS::TY;
+            const int oy = row - oz * TS::TY;
+            if (oz >= te[2] || oy >= te[1]) continue;
+            const C2* rp = zb + oz * sxy + oy * sx;
+            C2 v[TS::BX];
+#pragma unroll
+            for (int x = 0; x < TS::BX; ++x) {
+                if (x < sx) {
+                    v[x] = rp[x];
+                } else {
+                    v[x].x = C(0);
+                    v[x].y = C(0);
+                }
+            }
+            C2 r[TS::TX];
+            transpose_column<C, P, TS::TX, TS::BX>(v, w, k, sp[0], r);
+            const long long g0 = (static_cast<long long>(c0[2] * P + oz) * a.N[1] + (c0[1] * P + oy)) * a.N[0] +
+                                 c0[0] * P;
+            C2* dp = reinterpret_cast<C2*>(dst) + static_cast<long long>(i) * a.nn + g0;
+#pragma unroll
+            for (int ox = 0; ox < TS::TX; ++ox)
+                if (ox < te[0]) dp[ox] = r[ox];
+        }
+        __syncwarp();
+    }
 }
 
 // *acc += sum of partials[0..n) in a fixed order (one block).
@@ -359,8 +561,9 @@ int ensure_adjoint_scratch(sllbm_ctx* ctx) {
     const size_t need = lam_bytes > ctx->pop_bytes ? lam_bytes : ctx->pop_bytes;
     if (ctx->adj_buf[0] != nullptr && ctx->adj_bytes >= need) return SLLBM_OK;
     adjoint_release(ctx);
-    ctx->adj_blocks = static_cast<int>(adj_grid(ctx->nn, 128));
-    if (ctx->adj_blocks > 2048) ctx->adj_blocks = 2048;
+    // one partial per tile of the fused forward/VJP kernel (tiles are at least one cell)
+    const long long ncell = static_cast<long long>(ctx->cells[0]) * ctx->cells[1] * ctx->cells[2];
+    ctx->adj_blocks = static_cast<int>(ncell);
     ctx->adj_bytes = need;
     cudaError_t e = cudaMalloc(&ctx->adj_buf[0], need);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->adj_buf[1], need);
@@ -417,34 +620,127 @@ int stream_apply_t(sllbm_ctx* ctx, const void* src, void* dst, bool transpose) {
     return rc;
 }
 
-// CS: state type (the streamed populations h are computed in it), C: adjoint type.
-template <typename CS, typename C>
-int adjoint_step_t(sllbm_ctx* ctx, const void* state_prev, const void* lam_next, void* lam_prev, double* dmu) {
-    void* a = ctx->adj_buf[0];
-    void* b = ctx->adj_buf[1];
-    // h = S state_prev (the populations the step's collision saw)
-    int rc = launch_pass<CS>(ctx, state_prev, a, 2, false);
-    if (rc == SLLBM_OK) rc = launch_pass<CS>(ctx, a, b, 1, false);
-    if (rc == SLLBM_OK) rc = launch_pass<CS>(ctx, b, a, 0, false);
-    if (rc != SLLBM_OK) return rc;
-    // b = (d collide / d h)^T lam_next at h; mu_inf sensitivity into *dmu
+template <typename C, int P, int CX, int CY, int CZ, int NW>
+int launch_transpose(sllbm_ctx* ctx, const void* src, void* dst) {
+    using SM = TransSmem<C, P, CX, CY, CZ, NW>;
+    static_assert(SM::bytes <= 227 * 1024, "shared memory budget");
+    StepTables<C, P> tab;
+    fill_step_tables<C, P>(ctx, &tab);
+    StepArgs args;
+    fill_step_args(ctx, src, dst, &args);
+    args.flag = nullptr;
+    args.tiles[0] = (ctx->cells[0] + CX - 1) / CX;
+    args.tiles[1] = (ctx->cells[1] + CY - 1) / CY;
+    args.tiles[2] = (ctx->cells[2] + CZ - 1) / CZ;
+    const int ntiles = args.tiles[0] * args.tiles[1] * args.tiles[2];
+    auto k = adj_transpose_kernel<C, P, CX, CY, CZ, NW>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(SM::bytes));
+    if (e == cudaSuccess) {
+        k<<<ntiles, NW * 32, SM::bytes, ctx->stream>>>(args, tab);
+        e = cudaGetLastError();
+    }
+    ctx->launches += 1;
+    return e == cudaSuccess ? SLLBM_OK : adj_fail(ctx, e);
+}
+
+// Tiles (cells) and warps of the FP32 tile kernels of a backward step (the forward step's).
+template <typename C, int P>
+struct AdjTile;
+template <> struct AdjTile<float, 2> { static constexpr int CX = 4, CY = 4, CZ = 2, NW = 16; };
+template <> struct AdjTile<float, 3> { static constexpr int CX = 2, CY = 2, CZ = 2, NW = 16; };
+template <> struct AdjTile<float, 4> { static constexpr int CX = 2, CY = 2, CZ = 1, NW = 16; };
+
+// The state streamed without collision (the step kernel's tile body, stream-only mode).
+template <typename CS, int P, int CX, int CY, int CZ, int NW>
+int launch_stream_only(sllbm_ctx* ctx, const void* state, void* h) {
+    using SM = StepSmem<CS, P, CX, CY, CZ, NW>;
+    StepTables<CS, P> tab;
+    fill_step_tables<CS, P>(ctx, &tab);
+    StepArgs args;
+    fill_step_args(ctx, state, h, &args);
+    args.flag = nullptr;
+    args.collide = 0;
+    args.tiles[0] = (ctx->cells[0] + CX - 1) / CX;
+    args.tiles[1] = (ctx->cells[1] + CY - 1) / CY;
+    args.tiles[2] = (ctx->cells[2] + CZ - 1) / CZ;
+    const int ntiles = args.tiles[0] * args.tiles[1] * args.tiles[2];
+    auto k = step_kernel<CS, CS, P, CX, CY, CZ, NW, false>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(SM::bytes));
+    if (e == cudaSuccess) {
+        k<<<ntiles, NW * 32, SM::bytes, ctx->stream>>>(args, tab);
+        e = cudaGetLastError();
+    }
+    ctx->launches += 1;
+    return e == cudaSuccess ? SLLBM_OK : adj_fail(ctx, e);
+}
+
+// The collision VJP over a full grid, its mu_inf partials summed in a fixed order into *dmu.
+template <typename CH, typename C>
+int launch_vjp(sllbm_ctx* ctx, const void* h, const void* lam, void* out, double* dmu) {
     AdjArgs aa;
     aa.mu_over_dt = ctx->mu_inf / ctx->dt;
     aa.inv_dt = 1.0 / ctx->dt;
     aa.inv_2cv = 0.5 * (ctx->prm.gamma - 1.0);
     aa.gfac = 2.0 / (ctx->prm.gamma - 1.0) - 3.0;
-    collide_vjp_kernel<CS, C><<<ctx->adj_blocks, 128, 0, ctx->stream>>>(
-        static_cast<const CS*>(a), static_cast<const C*>(lam_next), static_cast<C*>(b), ctx->nn, aa, adj_vel(ctx),
-        ctx->d_adj_partials);
-    accumulate_kernel<<<1, 256, 0, ctx->stream>>>(ctx->d_adj_partials, ctx->adj_blocks, dmu);
+    long long g = (ctx->nn + 127) / 128;
+    if (g > ctx->adj_blocks) g = ctx->adj_blocks;
+    const int nb = static_cast<int>(g);
+    collide_vjp_kernel<CH, C><<<nb, 128, 0, ctx->stream>>>(static_cast<const CH*>(h), static_cast<const C*>(lam),
+                                                            static_cast<C*>(out), ctx->nn, aa, adj_vel(ctx),
+                                                            ctx->d_adj_partials);
+    accumulate_kernel<<<1, 256, 0, ctx->stream>>>(ctx->d_adj_partials, nb, dmu);
     ctx->launches += 2;
     const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return adj_fail(ctx, e);
-    // lam_prev = S^T b
-    rc = launch_pass<C>(ctx, b, a, 0, true);
+    return e == cudaSuccess ? SLLBM_OK : adj_fail(ctx, e);
+}
+
+// FP32 backward step: the state streamed by the step kernel's tile body (stream-only mode),
+// the collision VJP over a full grid (one thread per node), the transposed streaming as a
+// tile kernel.  (The VJP inside the streaming tile kernel was slower: only the tile's nodes,
+// one thread each, share its arithmetic.)
+template <int P>
+int adjoint_step_tiles(sllbm_ctx* ctx, const void* state_prev, const void* lam_next, void* lam_prev, double* dmu) {
+    using A = AdjTile<float, P>;
+    void* mu = ctx->adj_buf[0];
+    void* h = ctx->adj_buf[1];
+    int rc = launch_stream_only<float, P, A::CX, A::CY, A::CZ, A::NW>(ctx, state_prev, h);
+    if (rc != SLLBM_OK) return rc;
+    rc = launch_vjp<float, float>(ctx, h, lam_next, mu, dmu);
+    if (rc != SLLBM_OK) return rc;
+    return launch_transpose<float, P, A::CX, A::CY, A::CZ, A::NW>(ctx, mu, lam_prev);
+}
+
+// Backward step with FP64 arithmetic (FP64 storage, or FP32 states with FP64 adjoint
+// populations): 1D passes for the streaming and its transpose, the VJP over a full grid.
+// (The tile kernels were slower here: the FP64 step kernel's register spills and its FP64
+// moment arithmetic in stream-only mode.)
+template <typename CS, typename C>
+int adjoint_step_passes(sllbm_ctx* ctx, const void* state_prev, const void* lam_next, void* lam_prev,
+                        double* dmu) {
+    void* a = ctx->adj_buf[0];
+    void* b = ctx->adj_buf[1];
+    int rc = launch_pass<CS>(ctx, state_prev, a, 2, false);
+    if (rc == SLLBM_OK) rc = launch_pass<CS>(ctx, a, b, 1, false);
+    if (rc == SLLBM_OK) rc = launch_pass<CS>(ctx, b, a, 0, false);
+    if (rc == SLLBM_OK) rc = launch_vjp<CS, C>(ctx, a, lam_next, b, dmu);
+    if (rc == SLLBM_OK) rc = launch_pass<C>(ctx, b, a, 0, true);
     if (rc == SLLBM_OK) rc = launch_pass<C>(ctx, a, b, 1, true);
     if (rc == SLLBM_OK) rc = launch_pass<C>(ctx, b, lam_prev, 2, true);
     return rc;
+}
+
+template <typename CS, typename C>
+int adjoint_step_t(sllbm_ctx* ctx, const void* state_prev, const void* lam_next, void* lam_prev, double* dmu) {
+    if constexpr (std::is_same<CS, float>::value && std::is_same<C, float>::value) {
+        switch (ctx->p) {
+        case 2: return adjoint_step_tiles<2>(ctx, state_prev, lam_next, lam_prev, dmu);
+        case 3: return adjoint_step_tiles<3>(ctx, state_prev, lam_next, lam_prev, dmu);
+        case 4: return adjoint_step_tiles<4>(ctx, state_prev, lam_next, lam_prev, dmu);
+        }
+        return SLLBM_EINVAL;
+    } else {
+        return adjoint_step_passes<CS, C>(ctx, state_prev, lam_next, lam_prev, dmu);
+    }
 }
 
 }  // namespace

@@ -310,12 +310,24 @@ __device__ __forceinline__ void collide_node(const C* __restrict__ h, int stride
     }
 }
 
+// Per-node phase of the step: moments, equilibrium, collision, store (Eq. LBM).
+template <typename S, typename C, int P, bool PR>
+struct CollideOp {
+    __device__ __forceinline__ void operator()(const C* h, int stride, const StepArgs& a, const StepTables<C, P>& t,
+                                               long long g) const {
+        collide_node<S, C, P, PR>(h, stride, a, t, static_cast<S*>(a.dst) + 2 * g);
+    }
+};
+
 // The step of one tile (tile index `tile` of the mesh a describes), all NW warps of the CTA,
-// with the CTA's dynamic shared memory at smem_raw.  Used by step_kernel (one tile per CTA)
-// and by the batched persistent kernel (many tiles of many meshes per CTA).
-template <typename S, typename C, int P, int CX, int CY, int CZ, int NW, bool PR>
+// with the CTA's dynamic shared memory at smem_raw: streaming of the 90 populations of the
+// tile's nodes into shared memory, then op(streamed values of node n (stride TILE), a, t,
+// global node index) for every node of the tile.  Used by step_kernel (one tile per CTA),
+// by the batched persistent kernel (many tiles of many meshes per CTA) and, with the
+// collision's vector-Jacobian product as op, by the reverse mode.
+template <typename S, typename C, int P, int CX, int CY, int CZ, int NW, bool PR, class Op>
 __device__ __forceinline__ void step_tile(const StepArgs& a, const StepTables<C, P>& t, int tile,
-                                          unsigned char* smem_raw) {
+                                          unsigned char* smem_raw, Op& op) {
     using TS = TileShape<CX, CY, CZ, P>;
     using SM = StepSmem<C, P, CX, CY, CZ, NW>;
     using C2 = typename Pair2<C>::T;
@@ -439,7 +451,6 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const StepTables<C,
     }
     __syncthreads();
 
-    S* dst = static_cast<S*>(a.dst);
     for (int n = threadIdx.x; n < TS::TILE; n += NW * 32) {
         const int ox = n % TS::TX;
         const int r = n / TS::TX;
@@ -448,7 +459,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const StepTables<C,
         if (ox >= te[0] || oy >= te[1] || oz >= te[2]) continue;
         const long long g = (static_cast<long long>(c0[2] * P + oz) * a.N[1] + (c0[1] * P + oy)) * a.N[0]
                           + (c0[0] * P + ox);
-        collide_node<S, C, P, PR>(out + n, TS::TILE, a, t, dst + 2 * g);
+        op(out + n, TS::TILE, a, t, g);
     }
 }
 
@@ -456,7 +467,8 @@ template <typename S, typename C, int P, int CX, int CY, int CZ, int NW, bool PR
 __global__ void __launch_bounds__(NW * 32)
     step_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ StepTables<C, P> t) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    step_tile<S, C, P, CX, CY, CZ, NW, PR>(a, t, blockIdx.x, smem_raw);
+    CollideOp<S, C, P, PR> op;
+    step_tile<S, C, P, CX, CY, CZ, NW, PR>(a, t, blockIdx.x, smem_raw, op);
 }
 
 // Many meshes of one order in one launch: job k of the list (BatchJob) owns work items
@@ -498,7 +510,8 @@ __global__ void __launch_bounds__(NW * 32)
             have = lo;
             __syncthreads();
         }
-        step_tile<C, C, P, CX, CY, CZ, NW, false>(*sa, *st, static_cast<int>(w - jobs[lo].tile_begin), smem_raw);
+        CollideOp<C, C, P, false> op;
+        step_tile<C, C, P, CX, CY, CZ, NW, false>(*sa, *st, static_cast<int>(w - jobs[lo].tile_begin), smem_raw, op);
         __syncthreads();  // the next item reuses the shared memory
     }
 }

@@ -310,12 +310,95 @@ __device__ __forceinline__ void collide_node(const C* __restrict__ h, int stride
     }
 }
 
-// Per-node phase of the step: moments, equilibrium, collision, store (Eq. LBM).
+// First velocity of shell sh in the canonical order (0, 1, 13, 33; 45 past the last).
+__host__ __device__ constexpr int shell_begin(int sh) {
+    return sh <= 0 ? 0 : (sh == 1 ? 1 : (sh == 2 ? 13 : (sh == 3 ? 33 : 45)));
+}
+
+// collide_node for two lanes (lane pair 2k, 2k+1, `mask` naming both) sharing one node: the
+// lane with parity `half` takes the velocities i with i % 2 == half, shell by shell (the
+// shell's equilibrium coefficients stay compile-time indexed); the moment sums are combined
+// with one exchange, and both lanes form the node's parameters.  Storage types that hold the
+// populations themselves, no Prandtl term.
+template <typename S, typename C, int P>
+__device__ __forceinline__ void collide_node_pair(const C* __restrict__ h, int stride, const StepArgs& a,
+                                                  const StepTables<C, P>& t, S* __restrict__ dst, int half,
+                                                  unsigned mask) {
+    // shells 1, 2, 3 hold 12, 20, 12 velocities (6, 10, 6 per lane); the origin goes to lane 0
+    constexpr int kPer[4] = {1, 6, 10, 6};
+    C rho = 0, mx = 0, my = 0, mz = 0, e2 = 0;
+#pragma unroll
+    for (int sh = 0; sh < 4; ++sh) {
+        const C x2 = C(shell_xi2(sh));
+        const int i0 = shell_begin(sh) + ((shell_begin(sh) ^ half) & 1);
+#pragma unroll
+        for (int m = 0; m < kPer[sh]; ++m) {
+            const int i = i0 + 2 * m;
+            if (sh == 0 && half != 0) break;
+            const C f = h[i * stride];
+            rho += f;
+            mx += f * t.xi[i][0];
+            my += f * t.xi[i][1];
+            mz += f * t.xi[i][2];
+            e2 += f * x2 + h[(kQ + i) * stride];
+        }
+    }
+    rho += __shfl_xor_sync(mask, rho, 1);
+    mx += __shfl_xor_sync(mask, mx, 1);
+    my += __shfl_xor_sync(mask, my, 1);
+    mz += __shfl_xor_sync(mask, mz, 1);
+    e2 += __shfl_xor_sync(mask, e2, 1);
+    const C inv_rho = C(1) / rho;
+    const C ux = mx * inv_rho, uy = my * inv_rho, uz = mz * inv_rho;
+    const C usq = ux * ux + uy * uy + uz * uz;
+    const C T = (e2 * inv_rho - usq) * C(a.inv_2cv);
+    if (half == 0 && a.flag != nullptr && !(rho > C(0) && T > C(0) && isfinite(rho) && isfinite(T)))
+        atomicOr(a.flag, 1);
+    const long long nn = a.nn;
+    if (!a.collide) {
+        for (int i = half; i < kQ; i += 2) {
+            dst[2 * i * nn] = static_cast<S>(h[i * stride]);
+            dst[2 * i * nn + 1] = static_cast<S>(h[(kQ + i) * stride]);
+        }
+        return;
+    }
+    // tau = mu/(P dt) + 1/2, P = rho T, mu = Sutherland(T) mu_inf  (Sec. II.A, III.C)
+    const C tau = C(a.mu_over_dt) * sutherland(T) / (rho * T) + C(0.5);
+    const C om = C(1) / tau;
+    const C gT = C(a.gfac) * T;  // g^eq = (2 C_v - D) T f^eq
+    const EqCoef<C> ec = eq_coefficients(usq, T - C(1));
+#pragma unroll
+    for (int sh = 0; sh < 4; ++sh) {
+        const C c0 = ec.c0[sh], c1 = ec.c1[sh], c2 = ec.c2[sh];
+        const int i0 = shell_begin(sh) + ((shell_begin(sh) ^ half) & 1);
+#pragma unroll
+        for (int m = 0; m < kPer[sh]; ++m) {
+            const int i = i0 + 2 * m;
+            if (sh == 0 && half != 0) break;
+            const C s = t.xi[i][0] * ux + t.xi[i][1] * uy + t.xi[i][2] * uz;
+            const C feq =
+                t.w[i] * rho * (c0 + s * (c1 + s * (c2 + s * (C(1.0 / 6.0) + s * C(1.0 / 24.0)))));
+            const C f = h[i * stride];
+            const C g = h[(kQ + i) * stride];
+            dst[2 * i * nn] = static_cast<S>(f + om * (feq - f));
+            dst[2 * i * nn + 1] = static_cast<S>(g + om * (gT * feq - g));
+        }
+    }
+}
+
+// Per-node phase of the step: moments, equilibrium, collision, store (Eq. LBM).  Two lanes
+// per node (kPair) are possible where the storage holds the populations themselves and the
+// Prandtl term is off; step_tile uses them on tiles much smaller than the CTA.
 template <typename S, typename C, int P, bool PR>
 struct CollideOp {
+    static constexpr bool kPair = !PR && !PopCodec<S>::kDev;
     __device__ __forceinline__ void operator()(const C* h, int stride, const StepArgs& a, const StepTables<C, P>& t,
                                                long long g) const {
         collide_node<S, C, P, PR>(h, stride, a, t, static_cast<S*>(a.dst) + 2 * g);
+    }
+    __device__ __forceinline__ void pair(const C* h, int stride, const StepArgs& a, const StepTables<C, P>& t,
+                                         long long g, int half, unsigned mask) const {
+        collide_node_pair<S, C, P>(h, stride, a, t, static_cast<S*>(a.dst) + 2 * g, half, mask);
     }
 };
 
@@ -451,15 +534,33 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const StepTables<C,
     }
     __syncthreads();
 
-    for (int n = threadIdx.x; n < TS::TILE; n += NW * 32) {
-        const int ox = n % TS::TX;
-        const int r = n / TS::TX;
-        const int oy = r % TS::TY;
-        const int oz = r / TS::TY;
-        if (ox >= te[0] || oy >= te[1] || oz >= te[2]) continue;
-        const long long g = (static_cast<long long>(c0[2] * P + oz) * a.N[1] + (c0[1] * P + oy)) * a.N[0]
-                          + (c0[0] * P + ox);
-        op(out + n, TS::TILE, a, t, g);
+    // Two lanes per node only where the tile has at most a quarter as many nodes as the CTA
+    // has threads (measured: on the larger default tiles one lane per node, with its fully
+    // unrolled velocity loops, is faster).
+    if constexpr (Op::kPair && 4 * TS::TILE <= NW * 32) {
+        // two lanes per node: k = 2 n + half, the pair in one warp (NW * 32 is even)
+        for (int k = threadIdx.x; k < 2 * TS::TILE; k += NW * 32) {
+            const int n = k >> 1;
+            const int ox = n % TS::TX;
+            const int r = n / TS::TX;
+            const int oy = r % TS::TY;
+            const int oz = r / TS::TY;
+            if (ox >= te[0] || oy >= te[1] || oz >= te[2]) continue;  // both lanes of the pair
+            const long long g = (static_cast<long long>(c0[2] * P + oz) * a.N[1] + (c0[1] * P + oy)) * a.N[0]
+                              + (c0[0] * P + ox);
+            op.pair(out + n, TS::TILE, a, t, g, k & 1, 3u << (lane & 30));
+        }
+    } else {
+        for (int n = threadIdx.x; n < TS::TILE; n += NW * 32) {
+            const int ox = n % TS::TX;
+            const int r = n / TS::TX;
+            const int oy = r % TS::TY;
+            const int oz = r / TS::TY;
+            if (ox >= te[0] || oy >= te[1] || oz >= te[2]) continue;
+            const long long g = (static_cast<long long>(c0[2] * P + oz) * a.N[1] + (c0[1] * P + oy)) * a.N[0]
+                              + (c0[0] * P + ox);
+            op(out + n, TS::TILE, a, t, g);
+        }
     }
 }
 

@@ -120,9 +120,11 @@ def test_batch_refuses_the_legacy_stream_and_duplicates(S):
 
 @pytest.mark.parametrize("tune", [0, 2])
 def test_persistent_batch_equals_instances_stepped_alone(S, tune):
-    """One persistent launch per order over all instances' tiles: bit for bit the generic
-    kernel's result for every instance (each node is computed from the same values with the
-    same weights in the same order, whatever the tile shape)."""
+    """One persistent launch per order over all instances' tiles.  With the default tile
+    shapes, bit for bit the generic kernel's result for every instance (same values, same
+    weights, same order).  A tuned smaller tile collides each node on two lanes (even and odd
+    velocities summed separately, then added), so there the results agree to FP32 round-off
+    (the one-step tolerance of the FP32 parity tests, 2e-6 of the population scale)."""
     insts = I.batch_instances(10, 6)
     insts = [I.Instance(cells=(min(i.cells[0], 11),) * 3, p=i.p, Ma=min(i.Ma, 0.9), Re=i.Re,
                         courant=min(i.courant, 4.0)) for i in insts]
@@ -139,7 +141,11 @@ def test_persistent_batch_equals_instances_stepped_alone(S, tune):
         assert b.step(4) == 0
     torch.cuda.synchronize()
     for a, b in zip(sims, alone):
-        assert torch.equal(a.raw_state(), b.raw_state())
+        if tune == 0:
+            assert torch.equal(a.raw_state(), b.raw_state())
+        else:
+            x, y = a.raw_state().double(), b.raw_state().double()
+            assert float((x - y).abs().max()) <= 2e-6 * 4 * float(y.abs().max())
     bt.close()
 
 

@@ -211,6 +211,15 @@ int sllbm_diag_noalloc(sllbm_ctx *ctx, double *Ek, double *eps_s, double *eps_c)
  * to pop_out (host) and synchronises the stream. */
 int sllbm_run_host(sllbm_ctx *ctx, const void *pop_in, void *pop_out, int n);
 
+/* Pipelined end-to-end runs of `count` independent states: state k is copied from HOST
+ * pop_in[k] (pop_bytes, storage type; pinned host memory for full speed), advanced n steps
+ * and copied back to HOST pop_out[k].  Three device slots (six buffers of pop_bytes,
+ * allocated on the first call, separate from the context's buffers) and two copy streams
+ * let the device-to-host copy of one state, the host-to-device copy of the next and the
+ * steps in between overlap.  The context's own state and buffers are left as they were.
+ * Synchronous. */
+int sllbm_run_host_many(sllbm_ctx *ctx, const void *const *pop_in, void *const *pop_out, int count, int n);
+
 /* Waits for all work the context enqueued. */
 int sllbm_sync(sllbm_ctx *ctx);
 

@@ -566,6 +566,11 @@ void sllbm_destroy(sllbm_ctx* ctx) {
     cudaFree(ctx->d_flag);
     cudaFree(ctx->d_partials);
     adjoint_release(ctx);
+    for (int b = 0; b < 6; ++b) cudaFree(ctx->pipe_buf[b]);
+    for (int s = 0; s < 2; ++s)
+        if (ctx->pipe_stream[s]) cudaStreamDestroy(ctx->pipe_stream[s]);
+    for (int e = 0; e < 9; ++e)
+        if (ctx->pipe_ev[e]) cudaEventDestroy(ctx->pipe_ev[e]);
     std::free(ctx->step_blob);
     std::free(ctx);
 }
@@ -875,6 +880,70 @@ int sllbm_run_host(sllbm_ctx* ctx, const void* pop_in, void* pop_out, int n) {
     CK(ctx, cudaMemcpyAsync(pop_out, ctx->buf[ctx->cur], ctx->pop_bytes, cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     return SLLBM_OK;
+}
+
+// Pipelined end-to-end runs of independent states: state k uses device slot k % 3 (two
+// buffers each, separate from the context's own), its host-to-device copy on one copy
+// stream, its steps on the context's stream, its device-to-host copy on the other copy
+// stream; events order the three per slot, so that the copies of neighbouring states run
+// in both directions at once while a state is stepped.  With three slots the copy of state
+// k + 3 into a slot never waits for the copy out of state k (with two it did: 1.2x slower).
+int sllbm_run_host_many(sllbm_ctx* ctx, const void* const* pop_in, void* const* pop_out, int count, int n) {
+    if (ctx == nullptr || pop_in == nullptr || pop_out == nullptr || count < 1 || n < 0) return SLLBM_EINVAL;
+    for (int k = 0; k < count; ++k)
+        if (pop_in[k] == nullptr || pop_out[k] == nullptr) return SLLBM_EINVAL;
+    if (ctx->pipe_buf[0] == nullptr) {
+        for (int b = 0; b < 6; ++b) {
+            cudaError_t e = cudaMalloc(&ctx->pipe_buf[b], ctx->pop_bytes);
+            if (e != cudaSuccess) {
+                for (int j = 0; j < b; ++j) cudaFree(ctx->pipe_buf[j]);
+                for (int j = 0; j < 6; ++j) ctx->pipe_buf[j] = nullptr;
+                ctx->last_err = static_cast<int>(e);
+                return SLLBM_ENOMEM;
+            }
+        }
+        for (int s = 0; s < 2; ++s) CK(ctx, cudaStreamCreateWithFlags(&ctx->pipe_stream[s], cudaStreamNonBlocking));
+        for (int e = 0; e < 9; ++e) CK(ctx, cudaEventCreateWithFlags(&ctx->pipe_ev[e], cudaEventDisableTiming));
+    }
+    void* own[2] = {ctx->buf[0], ctx->buf[1]};
+    const int own_cur = ctx->cur;
+    const bool own_init = ctx->initialised;
+    int rc = SLLBM_OK;
+    for (int k = 0; k < count && rc == SLLBM_OK; ++k) {
+        const int slot = k % 3;
+        cudaEvent_t copied_in = ctx->pipe_ev[3 * slot], stepped = ctx->pipe_ev[3 * slot + 1],
+                    copied_out = ctx->pipe_ev[3 * slot + 2];
+        void* a = ctx->pipe_buf[2 * slot];
+        // the slot is free once the previous state in it was copied out
+        cudaError_t e = k >= 3 ? cudaStreamWaitEvent(ctx->pipe_stream[0], copied_out, 0) : cudaSuccess;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(a, pop_in[k], ctx->pop_bytes, cudaMemcpyHostToDevice, ctx->pipe_stream[0]);
+        if (e == cudaSuccess) e = cudaEventRecord(copied_in, ctx->pipe_stream[0]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, copied_in, 0);
+        if (e != cudaSuccess) {
+            rc = fail(ctx, e);
+            break;
+        }
+        ctx->buf[0] = a;
+        ctx->buf[1] = ctx->pipe_buf[2 * slot + 1];
+        ctx->cur = 0;
+        for (int s = 0; s < n && rc == SLLBM_OK; ++s) rc = step_launch(ctx);
+        if (rc != SLLBM_OK) break;
+        const void* result = ctx->buf[ctx->cur];
+        e = cudaEventRecord(stepped, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->pipe_stream[1], stepped, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(pop_out[k], result, ctx->pop_bytes, cudaMemcpyDeviceToHost, ctx->pipe_stream[1]);
+        if (e == cudaSuccess) e = cudaEventRecord(copied_out, ctx->pipe_stream[1]);
+        if (e != cudaSuccess) rc = fail(ctx, e);
+    }
+    ctx->buf[0] = own[0];
+    ctx->buf[1] = own[1];
+    ctx->cur = own_cur;
+    ctx->initialised = own_init;
+    cudaError_t e = cudaStreamSynchronize(ctx->pipe_stream[1]);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess && rc == SLLBM_OK) rc = fail(ctx, e);
+    return rc;
 }
 
 int sllbm_sync(sllbm_ctx* ctx) {

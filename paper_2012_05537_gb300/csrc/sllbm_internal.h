@@ -50,6 +50,9 @@ struct sllbm_ctx {
     int adj_blocks;
     size_t adj_bytes;          // size of each reverse-mode scratch buffer
     bool adj_f64;              // FP32 storage with FP64 adjoint populations
+    void* pipe_buf[6];         // sllbm_run_host_many: three device slots of two buffers
+    cudaStream_t pipe_stream[2];  // its host-to-device and device-to-host copy streams
+    cudaEvent_t pipe_ev[9];    // per slot: copied in, stepped, copied out
 };
 
 namespace sllbm {

@@ -90,6 +90,8 @@ def load(build_if_missing: bool = False):
         "sllbm_diag": (ctypes.c_int, [vp, dp, dp, dp]),
         "sllbm_diag_noalloc": (ctypes.c_int, [vp, dp, dp, dp]),
         "sllbm_run_host": (ctypes.c_int, [vp, vp, vp, ctypes.c_int]),
+        "sllbm_run_host_many": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int,
+                                               ctypes.c_int]),
         "sllbm_sync": (ctypes.c_int, [vp]),
         "sllbm_status": (ctypes.c_int, [vp]),
         "sllbm_last_cuda_error": (ctypes.c_int, [vp]),
@@ -230,6 +232,13 @@ def sllbm_diag_noalloc(ctx):
 def sllbm_run_host(ctx, in_ptr: int, out_ptr: int, n: int) -> None:
     _check(load().sllbm_run_host(ctx, ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), int(n)),
            "sllbm_run_host", ctx)
+
+
+def sllbm_run_host_many(ctx, in_ptrs, out_ptrs, n: int) -> None:
+    assert len(in_ptrs) == len(out_ptrs)
+    ins = (ctypes.c_void_p * len(in_ptrs))(*in_ptrs)
+    outs = (ctypes.c_void_p * len(out_ptrs))(*out_ptrs)
+    _check(load().sllbm_run_host_many(ctx, ins, outs, len(in_ptrs), int(n)), "sllbm_run_host_many", ctx)
 
 
 def sllbm_status(ctx) -> int:
@@ -521,6 +530,10 @@ class Sim:
 
     def run_host(self, host_in, host_out, n: int):
         sllbm_run_host(self.ctx, host_in.data_ptr(), host_out.data_ptr(), n)
+
+    def run_host_many(self, host_ins, host_outs, n: int):
+        """Pipelined end-to-end runs of independent states (pinned host tensors)."""
+        sllbm_run_host_many(self.ctx, [t.data_ptr() for t in host_ins], [t.data_ptr() for t in host_outs], n)
 
     def sync(self):
         sllbm_sync(self.ctx)

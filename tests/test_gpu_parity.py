@@ -282,6 +282,31 @@ def test_run_host_equals_device_path(S):
     assert torch.equal(host_out, dev.raw_state().cpu())
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_run_host_many_equals_run_host(S, kernel):
+    """Pipelined end-to-end runs of independent states: each result equals the same state
+    advanced alone (bit for bit), and the context's own state is left as it was."""
+    sim = make(S, (4, 2, 2), 4, storage="f32", courant=3.0, kernel=kernel)
+    sim.init_tgv()
+    own = sim.raw_state().clone()
+    g = grid_of(sim)
+    ins, refs = [], []
+    for k in range(5):
+        pop = noneq_state(g, 40 + k)
+        one = make(S, (4, 2, 2), 4, storage="f32", courant=3.0, kernel=kernel)
+        one.set_populations(pop)
+        ins.append(one.raw_state().cpu().pin_memory())
+        assert one.step(2) == 0
+        refs.append(one.raw_state().cpu())
+        one.close()
+    outs = [torch.empty_like(x).pin_memory() for x in ins]
+    sim.run_host_many(ins, outs, 2)
+    for out, ref in zip(outs, refs):
+        assert torch.equal(out, ref)
+    assert torch.equal(sim.raw_state(), own)
+    assert sim.step(1) == 0  # the context still steps its own state
+
+
 def test_launch_count_is_one_kernel_per_step(S):
     sim = make(S, (2, 2, 2), 2)
     sim.init_tgv()

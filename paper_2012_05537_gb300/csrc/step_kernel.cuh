@@ -128,6 +128,21 @@ __device__ __forceinline__ C load_as(S v) {
         return static_cast<C>(v);
 }
 
+// One pair (f_i, g_i) stored with a single 2-element store (the pair is adjacent in a state
+// buffer and aligned to its size).
+template <typename S, typename C>
+__device__ __forceinline__ void store_pair(S* p, C f, C g) {
+    if constexpr (std::is_same<S, float>::value) {
+        *reinterpret_cast<float2*>(p) = make_float2(static_cast<float>(f), static_cast<float>(g));
+    } else if constexpr (std::is_same<S, double>::value) {
+        *reinterpret_cast<double2*>(p) = make_double2(static_cast<double>(f), static_cast<double>(g));
+    } else if constexpr (std::is_same<S, __half>::value) {
+        *reinterpret_cast<__half2*>(p) = __floats2half2_rn(static_cast<float>(f), static_cast<float>(g));
+    } else {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(static_cast<float>(f), static_cast<float>(g));
+    }
+}
+
 __device__ __forceinline__ int wrap_index(int v, int n) {
     int r = v % n;
     return r < 0 ? r + n : r;
@@ -168,7 +183,7 @@ __device__ __forceinline__ void collide_node_dev(const C* __restrict__ h, int st
     const long long nn = a.nn;
     if (!a.collide) {
 #pragma unroll 9
-        for (int q = 0; q < 2 * kQ; ++q) dst[2 * (q % kQ) * nn + q / kQ] = static_cast<S>(static_cast<float>(h[q * stride]));
+        for (int i = 0; i < kQ; ++i) store_pair<S>(dst + 2 * i * nn, h[i * stride], h[(kQ + i) * stride]);
         return;
     }
     const C tau = C(a.mu_over_dt) * sutherland(T) / (rho * T) + C(0.5);
@@ -216,8 +231,7 @@ __device__ __forceinline__ void collide_node_dev(const C* __restrict__ h, int st
             fo += ompr * fst_w;
             go += ompr * gfac * T * fst_w;
         }
-        dst[2 * i * nn] = static_cast<S>(static_cast<float>(fo));
-        dst[2 * i * nn + 1] = static_cast<S>(static_cast<float>(go));
+        store_pair<S>(dst + 2 * i * nn, fo, go);
     }
 }
 
@@ -249,8 +263,7 @@ __device__ __forceinline__ void collide_node(const C* __restrict__ h, int stride
     const long long nn = a.nn;
     if (!a.collide) {
 #pragma unroll 9
-        for (int q = 0; q < 2 * kQ; ++q)
-            dst[2 * (q % kQ) * nn + q / kQ] = static_cast<S>(h[q * stride]);
+        for (int i = 0; i < kQ; ++i) store_pair<S>(dst + 2 * i * nn, h[i * stride], h[(kQ + i) * stride]);
         return;
     }
     // tau = mu/(P dt) + 1/2, P = rho T, mu = Sutherland(T) mu_inf  (Sec. II.A, III.C)
@@ -305,8 +318,7 @@ __device__ __forceinline__ void collide_node(const C* __restrict__ h, int stride
             fo += ompr * fst;
             go += ompr * gT * fst;
         }
-        dst[2 * i * nn] = static_cast<S>(fo);
-        dst[2 * i * nn + 1] = static_cast<S>(go);
+        store_pair<S>(dst + 2 * i * nn, fo, go);
     }
 }
 
@@ -357,8 +369,7 @@ __device__ __forceinline__ void collide_node_pair(const C* __restrict__ h, int s
     const long long nn = a.nn;
     if (!a.collide) {
         for (int i = half; i < kQ; i += 2) {
-            dst[2 * i * nn] = static_cast<S>(h[i * stride]);
-            dst[2 * i * nn + 1] = static_cast<S>(h[(kQ + i) * stride]);
+            store_pair<S>(dst + 2 * i * nn, h[i * stride], h[(kQ + i) * stride]);
         }
         return;
     }
@@ -380,8 +391,7 @@ __device__ __forceinline__ void collide_node_pair(const C* __restrict__ h, int s
                 t.w[i] * rho * (c0 + s * (c1 + s * (c2 + s * (C(1.0 / 6.0) + s * C(1.0 / 24.0)))));
             const C f = h[i * stride];
             const C g = h[(kQ + i) * stride];
-            dst[2 * i * nn] = static_cast<S>(f + om * (feq - f));
-            dst[2 * i * nn + 1] = static_cast<S>(g + om * (gT * feq - g));
+            store_pair<S>(dst + 2 * i * nn, f + om * (feq - f), g + om * (gT * feq - g));
         }
     }
 }

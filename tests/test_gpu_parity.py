@@ -282,6 +282,43 @@ def test_run_host_equals_device_path(S):
     assert torch.equal(host_out, dev.raw_state().cpu())
 
 
+def load_curves(name):
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    rows = [list(map(float, line.split())) for line in open(path) if line.strip() and not line.startswith("#")]
+    return np.array(rows)
+
+
+# The 64^3-node Taylor-Green run against the oracle's curves (tests/golden/tgv_16c_p4_curves.txt,
+# written by tests/golden/make_tgv_curves.py from the FP64 oracle alone), E_k, eps_s, eps_c every
+# 20 steps over 200 steps (t* = 19): FP64 on the generic kernel and FP32 on the TMA-fed kernel
+# (the throughput path).  Bounds relative to the curve's largest value: FP64 1e-11 (round-off
+# of 200 steps; measured on GB300: 3.7e-14, 8.7e-15, 3.2e-14); FP32 STATED_CURVES_F32 (measured:
+# 1.9e-6, 9.8e-6, 1.3e-5 for E_k, eps_s, eps_c; asserted with a margin of about 4).
+STATED_CURVES_F32 = (1e-5, 4e-5, 5e-5)
+
+
+@pytest.mark.parametrize("storage,kernel", [("f64", 1), ("f32", 2)])
+def test_tgv_16c_p4_curves_match_oracle(S, storage, kernel):
+    ref = load_curves("tgv_16c_p4_curves.txt")
+    w = I.WORKLOADS["tgv_16c_p4"]
+    sim = S.Sim(S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, courant=None, dt=w.dt(), mu_inf=w.mu_inf,
+                         storage=storage, kernel=kernel))
+    assert sim.info.step_kernel == kernel
+    sim.init_tgv()
+    got = [[0] + list(sim.diag())]
+    for k in range(20, 201, 20):
+        assert sim.step(20) == 0
+        got.append([k] + list(sim.diag()))
+    got = np.array(got)
+    assert np.array_equal(got[:, 0], ref[:, 0])
+    errs = [float(np.max(np.abs(got[:, c] - ref[:, c])) / np.max(np.abs(ref[:, c]))) for c in (1, 2, 3)]
+    print(storage, "E_k, eps_s, eps_c max relative deviation from the oracle curves:", errs)
+    bounds = (1e-11, 1e-11, 1e-11) if storage == "f64" else STATED_CURVES_F32
+    for e, b in zip(errs, bounds):
+        assert e <= b
+
+
 @pytest.mark.parametrize("kernel", [1, 2])
 def test_run_host_many_equals_run_host(S, kernel):
     """Pipelined end-to-end runs of independent states: each result equals the same state

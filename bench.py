@@ -3,7 +3,7 @@ Taylor-Green input.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
                   [--workload tgv_32c_p4] [--storage f32|f64|f16dev|bf16dev]
-                  [--mixed-steps 200]
+                  [--mixed-steps 400]
 
 One "step" is one SLLBM time step over the whole mesh: one launch of the fused kernel
 (streaming of all 90 populations, moments, equilibrium, collision).  The default
@@ -70,9 +70,9 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--mixed-steps", type=int, default=200,
+    ap.add_argument("--mixed-steps", type=int, default=400,
                     help="steps of the Ma 1.25 mixed-precision comparison (0: skip)")
-    ap.add_argument("--mixed-every", type=int, default=10)
+    ap.add_argument("--mixed-every", type=int, default=20)
     ap.add_argument("--batch-steps", type=int, default=100,
                     help="steps of the 64-instance batched comparison (0: skip)")
     ap.add_argument("--no-adjoint", action="store_true",

@@ -119,15 +119,6 @@ __device__ __forceinline__ void lagrange_column(const typename Pair2<C>::T (&v)[
     }
 }
 
-// A stored value in the arithmetic type (16-bit storage goes through FP32).
-template <typename C, typename S>
-__device__ __forceinline__ C load_as(S v) {
-    if constexpr (PopCodec<S>::kDev)
-        return static_cast<C>(static_cast<float>(v));
-    else
-        return static_cast<C>(v);
-}
-
 // One pair (f_i, g_i) stored with a single 2-element store (the pair is adjacent in a state
 // buffer and aligned to its size).
 template <typename S, typename C>

@@ -16,10 +16,6 @@ namespace sllbm {
 constexpr int kQ = 45;      // velocities of the degree-9 cubature set (Sec. II.B)
 constexpr int kMaxP = 4;    // largest supported polynomial order
 
-// First velocity index of each shell in the canonical order (origin, |xi|^2 = 3, 9, 15).
-constexpr int kShellBegin[5] = {0, 1, 13, 33, 45};
-constexpr double kShellXi2[4] = {0.0, 3.0, 9.0, 15.0};
-
 SLLBM_HD constexpr int shell_of(int i) {
     return i < 1 ? 0 : (i < 13 ? 1 : (i < 33 ? 2 : 3));
 }

@@ -95,7 +95,8 @@ typedef struct {
     int dt_is_courant;      /* 1: dt = C * min_d(L[d]/N[d]) / max_i|xi_i| (C = Courant number) */
     int pr_correction;      /* 1: apply the quasi-equilibrium Prandtl term (App. D) */
     sllbm_storage storage;  /* population storage / arithmetic type */
-    int nonfinite_check;    /* 1: the step kernel flags non-finite rho or T */
+    int nonfinite_check;    /* 1: the step kernel flags non-finite rho or T (in the collision:
+                               a stream-only context does not check) */
     double tgv_C;           /* density numerator C of the TGV field; < 0 selects gamma*Ma^2 */
     double mu_inf_override; /* > 0: use this mu_inf instead of rho0*U0/Re */
     int collide;            /* 1: stream and collide (normal); 0: stream only */

@@ -235,6 +235,12 @@ __device__ __forceinline__ void collide_node(const C* __restrict__ h, int stride
         collide_node_dev<S, C, P, PR>(h, stride, a, t, dst);
         return;
     }
+    const long long nn = a.nn;
+    if (!a.collide) {  // streaming only: store the streamed pairs
+#pragma unroll 9
+        for (int i = 0; i < kQ; ++i) store_pair<S>(dst + 2 * i * nn, h[i * stride], h[(kQ + i) * stride]);
+        return;
+    }
     C rho = 0, mx = 0, my = 0, mz = 0, e2 = 0;
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
@@ -251,12 +257,6 @@ __device__ __forceinline__ void collide_node(const C* __restrict__ h, int stride
     const C T = (e2 * inv_rho - usq) * C(a.inv_2cv);
     if (a.flag != nullptr && !(rho > C(0) && T > C(0) && isfinite(rho) && isfinite(T)))
         atomicOr(a.flag, 1);
-    const long long nn = a.nn;
-    if (!a.collide) {
-#pragma unroll 9
-        for (int i = 0; i < kQ; ++i) store_pair<S>(dst + 2 * i * nn, h[i * stride], h[(kQ + i) * stride]);
-        return;
-    }
     // tau = mu/(P dt) + 1/2, P = rho T, mu = Sutherland(T) mu_inf  (Sec. II.A, III.C)
     const C tau = C(a.mu_over_dt) * sutherland(T) / (rho * T) + C(0.5);
     const C om = C(1) / tau;
@@ -327,6 +327,10 @@ template <typename S, typename C, int P>
 __device__ __forceinline__ void collide_node_pair(const C* __restrict__ h, int stride, const StepArgs& a,
                                                   const StepTables<C, P>& t, S* __restrict__ dst, int half,
                                                   unsigned mask) {
+    if (!a.collide) {  // streaming only: each lane stores its velocities' pairs
+        for (int i = half; i < kQ; i += 2) store_pair<S>(dst + 2 * i * a.nn, h[i * stride], h[(kQ + i) * stride]);
+        return;
+    }
     // shells 1, 2, 3 hold 12, 20, 12 velocities (6, 10, 6 per lane); the origin goes to lane 0
     constexpr int kPer[4] = {1, 6, 10, 6};
     C rho = 0, mx = 0, my = 0, mz = 0, e2 = 0;
@@ -358,12 +362,6 @@ __device__ __forceinline__ void collide_node_pair(const C* __restrict__ h, int s
     if (half == 0 && a.flag != nullptr && !(rho > C(0) && T > C(0) && isfinite(rho) && isfinite(T)))
         atomicOr(a.flag, 1);
     const long long nn = a.nn;
-    if (!a.collide) {
-        for (int i = half; i < kQ; i += 2) {
-            store_pair<S>(dst + 2 * i * nn, h[i * stride], h[(kQ + i) * stride]);
-        }
-        return;
-    }
     // tau = mu/(P dt) + 1/2, P = rho T, mu = Sutherland(T) mu_inf  (Sec. II.A, III.C)
     const C tau = C(a.mu_over_dt) * sutherland(T) / (rho * T) + C(0.5);
     const C om = C(1) / tau;

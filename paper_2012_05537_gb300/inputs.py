@@ -77,6 +77,9 @@ WORKLOADS = {
     # 318 MB per FP32 buffer, larger than L2)
     "tgv_32c_p3_ma125": Workload("tgv_32c_p3_ma125", (32, 32, 32), 3, 1.25, 1600.0, 1.0, 200, "f32",
                                  note="32^3 cells, p=3 (96^3 nodes), Ma 1.25, C=1"),
+    # large mesh: byte offsets of a buffer beyond 32 bits (FP32 20 GB, FP64 41 GB per buffer)
+    "tgv_96c_p4": Workload("tgv_96c_p4", (96, 96, 96), 4, 0.5, 1600.0, 4.0, 1, "f32",
+                           note="96^3 cells, p=4 (384^3 nodes), Ma 0.5, C=4 (first step)"),
     # the same mesh at Courant 8 (departures 2.7 cells away): first-step parity only
     "tgv_64c_p3_ma125_c8": Workload("tgv_64c_p3_ma125_c8", (64, 64, 64), 3, 1.25, 1600.0, 8.0, 1,
                                     "f32", note="64^3 cells, p=3, Ma 1.25, C=8 (one step)"),

@@ -225,10 +225,12 @@ def test_tgv_24cube_50_steps_matches_oracle(S, storage, tol):
 
 
 @pytest.mark.parametrize("name,storage", [("tgv_32c_p4", "f32"), ("tgv_32c_p4", "f64"),
-                                          ("tgv_64c_p3_ma125", "f32"), ("tgv_64c_p3_ma125_c8", "f32")])
+                                          ("tgv_64c_p3_ma125", "f32"), ("tgv_64c_p3_ma125_c8", "f32"),
+                                          ("tgv_96c_p4", "f32"), ("tgv_96c_p4", "f64")])
 def test_full_size_first_step_sampled(S, name, storage):
-    """At the benchmark sizes, in the benchmark launch configuration: one step from the
-    Taylor-Green state, compared at sampled nodes that the oracle evaluates one by one."""
+    """At the benchmark sizes (and at 384^3 nodes, where a buffer's byte offsets pass 2^32),
+    in the benchmark launch configuration: one step from the Taylor-Green state, compared at
+    sampled nodes (the first and the last included) that the oracle evaluates one by one."""
     w = I.WORKLOADS[name]
     sim = make(S, w.cells, w.p, storage=storage, courant=w.courant, Ma=w.Ma, Re=w.Re)
     sim.init_tgv()

@@ -218,14 +218,16 @@ int sllbm_run_host(sllbm_ctx *ctx, const void *pop_in, void *pop_out, int n);
  * allocated on the first call, separate from the context's buffers) and two copy streams
  * let the device-to-host copy of one state, the host-to-device copy of the next and the
  * steps in between overlap.  The context's own state and buffers are left as they were.
- * Synchronous. */
+ * Synchronous.  Errors: SLLBM_EINVAL (NULL pointers, count < 1, n < 0), SLLBM_ENOMEM (the
+ * slots), SLLBM_ECUDA. */
 int sllbm_run_host_many(sllbm_ctx *ctx, const void *const *pop_in, void *const *pop_out, int count, int n);
 
 /* Waits for all work the context enqueued. */
 int sllbm_sync(sllbm_ctx *ctx);
 
 /* Copies a state (storage type and order, pop_bytes bytes, device pointer) into the
- * current buffer and marks the context initialised.  Asynchronous. */
+ * current buffer and marks the context initialised.  Asynchronous.  Errors: SLLBM_EINVAL
+ * (NULL), SLLBM_ENOMEM (the context had to allocate its buffers), SLLBM_ECUDA. */
 int sllbm_load_state(sllbm_ctx *ctx, const void *state);
 
 /* Sets mu_inf, the viscosity scale of the Sutherland law, which fixes the relaxation time
@@ -250,25 +252,31 @@ int sllbm_set_step_variant(sllbm_ctx *ctx, int variant);
  * that can run this context, starting each from the current state, keeps the fastest and
  * restores the current state (a temporary device copy of one state is allocated).
  * Synchronous.  Outputs (either may be NULL): the chosen variant and its time per step in
- * milliseconds.  Needs an initialised context. */
+ * milliseconds.  Errors: SLLBM_EINVAL (steps < 1), SLLBM_ENOTREADY (not initialised),
+ * SLLBM_ENOMEM (the temporary copy), SLLBM_ECUDA; on an error the variant is unchanged. */
 int sllbm_autotune(sllbm_ctx *ctx, int steps, int *variant, double *ms_per_step);
 
 /* Batched launch of many contexts (instances of uneven size, order and parameters) as one
  * CUDA graph.  sllbm_batch_create captures two steps of every context, with the contexts
  * spread over `streams` worker streams (longest-processing-time-first on the per-step cost
- * estimate: the autotuned times if every context was autotuned, else the node counts) so that small instances run
- * concurrently; the graph forks from and joins to cuda_stream, which must be a created
+ * estimate: the autotuned times if every context was autotuned, else the node counts) so
+ * that small instances run concurrently; the graph forks from and joins to cuda_stream,
+ * which must be a created
  * stream (not the legacy default stream, NULL: SLLBM_EINVAL).  Each context must be
  * initialised, on the current device, with nonfinite_check off, and must not take part in
  * another batch.  The contexts keep ownership of their buffers and stay usable on their
  * own; a batch is invalid (SLLBM_EINVAL from sllbm_batch_step) once one of them was stepped
- * an odd number of times outside it. */
+ * an odd number of times outside it.  Synchronous.  Errors: SLLBM_EINVAL (the conditions
+ * above, n < 1, streams < 1, a context given twice), SLLBM_ENOMEM, SLLBM_ECUDA (stream
+ * capture or graph instantiation failed; the contexts are left as they were). */
 typedef struct sllbm_batch sllbm_batch;
 int sllbm_batch_create(sllbm_ctx *const *ctxs, int n, int streams, void *cuda_stream, sllbm_batch **out);
 
 /* Advances every context of the batch by nsteps (even, >= 0) steps: nsteps/2 graph
  * launches on the batch's stream, ordered after work already queued on the contexts'
- * streams and before work queued on them later.  Asynchronous. */
+ * streams and before work queued on them later.  Asynchronous.  Errors: SLLBM_EINVAL (odd or
+ * negative nsteps, or a context stepped an odd number of times outside the batch),
+ * SLLBM_ECUDA. */
 int sllbm_batch_step(sllbm_batch *b, int nsteps);
 
 /* The same, as ONE persistent kernel launch per polynomial order and step: every context
@@ -313,8 +321,9 @@ void sllbm_batch_destroy(sllbm_batch *b);
 int sllbm_set_adjoint_type(sllbm_ctx *ctx, int storage);
 
 /* dst = S src (transpose == 0) or dst = S^T src: the semi-Lagrangian streaming of all 90
- * populations alone (Eq. interpolation, pull), or its transpose, as three 1D passes.
- * src and dst may be the same buffer.  For SLLBM_F32 and SLLBM_F64 storage. */
+ * populations alone (Eq. interpolation, pull), or its transpose, as three 1D passes, on
+ * state-sized arrays of the storage type.  src and dst may be the same buffer.  For
+ * SLLBM_F32 and SLLBM_F64 storage (SLLBM_EINVAL otherwise). */
 int sllbm_stream_apply(sllbm_ctx *ctx, const void *src, void *dst, int transpose);
 
 /* One step backward.  For the step F (pull streaming S, then the BGK collision C of

@@ -97,26 +97,34 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash() -> str:
+KERNEL_SOURCES = {
+    # the TMA-fed kernel and what it is built from
+    "tma": ("step_tma.cuh", "step_f32.cu", "collide.cuh", "sllbm_internal.h", "tables.h"),
+    # the generic tile kernel and its instances
+    "generic": ("step_kernel.cuh", "collide.cuh", "storage.cuh", "sllbm_internal.h", "tables.h", "step_f32.cu",
+                "step_f32_tiles.cu", "step_f64.cu", "step_f16.cu"),
+}
+
+
+def kernel_source_hash(kind: str = "tma") -> str:
     csrc = os.path.join(ROOT, "paper_2012_05537_gb300", "csrc")
     h = hashlib.sha256()
-    for name in ("step_kernel.cuh", "step_tma.cuh", "collide.cuh", "storage.cuh", "sllbm_internal.h",
-                 "step_f32.cu", "step_f64.cu", "step_f16.cu"):
+    for name in KERNEL_SOURCES[kind]:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str, storage: str):
+def profiled_traffic(workload: str, storage: str, kind: str = "tma"):
     """DRAM bytes per launch recorded from an ncu capture of the current kernel source,
-    or None if no summary matches the current source hash."""
+    or None if no summary matches the current source hash of that kernel."""
     path = os.path.join(ROOT, "profiles", f"step_{storage}_{workload}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m_hash = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
     m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash():
+    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash(kind):
         return None
     return float(m_bytes.group(1))
 
@@ -519,7 +527,7 @@ def run_mine(args, rank, world, local):
     kern_avg_ms = statistics.mean(kern)
     hbm, peak_src = measured_peaks()
     achieved = bytes_per_node * nodes / (kern_avg_ms / 1e3) / 1e9
-    traffic = profiled_traffic(w.name, storage)
+    traffic = profiled_traffic(w.name, storage, "tma" if sim.info.step_kernel == 2 else "generic")
 
     # end to end through the C ABI with host buffers: every step copies a state from pinned
     # host memory to the device, advances it one step and copies the result back.  Headline:

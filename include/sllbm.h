@@ -286,7 +286,9 @@ int sllbm_batch_step(sllbm_batch *b, int nsteps);
  * the launches of the (up to three) orders run on separate worker streams and two steps
  * are captured into one graph.  With tune_steps > 0 an autotuner picks the tile shape per
  * order (the default tile, one size smaller, one cell): it times tune_steps (rounded up to
- * even) launches of each from the current states and restores the states.  FP32 storage
+ * even) replays of the captured graph, from the current states, keeps another shape for
+ * an order only if that makes the graph at least 2 % faster (one order at a time), and
+ * restores the states.  FP32 storage
  * without the Prandtl term only (SLLBM_EINVAL otherwise); other conditions as
  * sllbm_batch_create.  Synchronous. */
 int sllbm_batch_create_persistent(sllbm_ctx *const *ctxs, int n, void *cuda_stream, int tune_steps,

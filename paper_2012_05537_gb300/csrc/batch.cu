@@ -327,6 +327,37 @@ int sllbm_batch_step(sllbm_batch* b, int nsteps) {
     return SLLBM_OK;
 }
 
+// Captures two steps of every group (each on its worker stream, parity 0 then 1) into
+// b->graph and instantiates b->exec, replacing a previous graph.
+static int capture_persistent(sllbm_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    int rc = SLLBM_OK;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->stream);
+    for (size_t s = 0; s < b->groups.size() && e == cudaSuccess && rc == SLLBM_OK; ++s) {
+        const BatchGroup& g = b->groups[s];
+        e = cudaStreamWaitEvent(b->workers[s], b->fork, 0);
+        for (int par = 0; par < 2 && e == cudaSuccess && rc == SLLBM_OK; ++par)
+            rc = launch_batch_group(g.p, g.shape, g.d_jobs, g.njobs, g.d_tabs, g.items, par, g.grid, b->workers[s]);
+        if (e == cudaSuccess && rc == SLLBM_OK) e = cudaEventRecord(b->join[s], b->workers[s]);
+        if (e == cudaSuccess && rc == SLLBM_OK) e = cudaStreamWaitEvent(b->stream, b->join[s], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e_end = cudaStreamEndCapture(b->stream, &graph);
+    if (rc == SLLBM_OK && e == cudaSuccess && e_end == cudaSuccess) {
+        b->graph = graph;
+        if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) rc = SLLBM_ECUDA;
+    } else {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        if (rc == SLLBM_OK) rc = SLLBM_ECUDA;
+    }
+    return rc;
+}
+
 int sllbm_batch_create_persistent(sllbm_ctx* const* ctxs, int n, void* cuda_stream, int tune_steps,
                                   sllbm_batch** out) {
     if (out == nullptr) return SLLBM_EINVAL;
@@ -372,8 +403,14 @@ int sllbm_batch_create_persistent(sllbm_ctx* const* ctxs, int n, void* cuda_stre
     }
     if (e != cudaSuccess) rc = SLLBM_ECUDA;
 
-    // Autotuner: per order, time `tune_steps` (rounded up to even) launches of each tile shape
-    // from the current states and keep the fastest; the states are restored afterwards.
+    // Autotuner: the groups run concurrently in the graph (one worker stream each), so they
+    // are timed together, `tune_steps` (rounded up to even) steps of all groups from the
+    // current states; a coordinate descent over the groups keeps another tile shape for a
+    // group only if all groups then run at least 2 % faster.  The states are restored.
+    for (size_t s = 0; s < b->groups.size() && rc == SLLBM_OK; ++s) {
+        b->groups[s].shape = 0;
+        rc = build_group(b->groups[s], b->ctx, num_sms);
+    }
     if (rc == SLLBM_OK && tune_steps > 0) {
         const int steps = tune_steps + (tune_steps & 1);
         std::vector<void*> saved(n, nullptr);
@@ -386,32 +423,37 @@ int sllbm_batch_create_persistent(sllbm_ctx* const* ctxs, int n, void* cuda_stre
         cudaEvent_t ev[2] = {nullptr, nullptr};
         if (rc == SLLBM_OK && (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess))
             rc = SLLBM_ECUDA;
-        for (BatchGroup& g : b->groups) {
-            float best_ms = 0.0f;
-            int best = -1;
-            for (int sh = 0; sh < 3 && rc == SLLBM_OK; ++sh) {
-                g.shape = sh;
-                rc = build_group(g, b->ctx, num_sms);
-                if (rc != SLLBM_OK) break;
-                rc = launch_batch_group(g.p, g.shape, g.d_jobs, g.njobs, g.d_tabs, g.items, 0, g.grid, b->stream);
-                if (rc == SLLBM_OK) rc = launch_batch_group(g.p, g.shape, g.d_jobs, g.njobs, g.d_tabs, g.items, 1,
-                                                            g.grid, b->stream);
-                if (rc == SLLBM_OK && cudaEventRecord(ev[0], b->stream) != cudaSuccess) rc = SLLBM_ECUDA;
-                for (int s2 = 0; s2 < steps && rc == SLLBM_OK; ++s2)
-                    rc = launch_batch_group(g.p, g.shape, g.d_jobs, g.njobs, g.d_tabs, g.items, s2 & 1, g.grid,
-                                            b->stream);
+        // the graph of the current shapes, replayed: 2 steps of warm-up, then `steps` timed
+        auto time_graph = [&](float* ms) -> int {
+            int r = capture_persistent(b);
+            if (r != SLLBM_OK) return r;
+            if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return SLLBM_ECUDA;
+            if (cudaEventRecord(ev[0], b->stream) != cudaSuccess) return SLLBM_ECUDA;
+            for (int s2 = 0; s2 < steps / 2; ++s2)
+                if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return SLLBM_ECUDA;
+            if (cudaEventRecord(ev[1], b->stream) != cudaSuccess || cudaEventSynchronize(ev[1]) != cudaSuccess ||
+                cudaEventElapsedTime(ms, ev[0], ev[1]) != cudaSuccess)
+                return SLLBM_ECUDA;
+            return SLLBM_OK;
+        };
+        float best_ms = 0.0f;
+        if (rc == SLLBM_OK) rc = time_graph(&best_ms);
+        for (size_t g = 0; g < b->groups.size() && rc == SLLBM_OK; ++g) {
+            BatchGroup& gr = b->groups[g];
+            int best = gr.shape;
+            for (int sh = 1; sh < 3 && rc == SLLBM_OK; ++sh) {
+                gr.shape = sh;
+                rc = build_group(gr, b->ctx, num_sms);
                 float ms = 0.0f;
-                if (rc == SLLBM_OK && (cudaEventRecord(ev[1], b->stream) != cudaSuccess ||
-                                       cudaEventSynchronize(ev[1]) != cudaSuccess ||
-                                       cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess))
-                    rc = SLLBM_ECUDA;
-                if (rc == SLLBM_OK && (best < 0 || ms < best_ms)) {
+                if (rc == SLLBM_OK) rc = time_graph(&ms);
+                if (rc == SLLBM_OK && ms < 0.98f * best_ms) {
                     best = sh;
                     best_ms = ms;
                 }
             }
             if (rc != SLLBM_OK) break;
-            g.shape = best;
+            gr.shape = best;
+            rc = build_group(gr, b->ctx, num_sms);
         }
         for (int k = 0; k < n; ++k) {
             if (saved[k] != nullptr && rc == SLLBM_OK)
@@ -423,30 +465,9 @@ int sllbm_batch_create_persistent(sllbm_ctx* const* ctxs, int n, void* cuda_stre
         if (ev[0]) cudaEventDestroy(ev[0]);
         if (ev[1]) cudaEventDestroy(ev[1]);
     }
-    for (size_t s = 0; s < b->groups.size() && rc == SLLBM_OK; ++s) rc = build_group(b->groups[s], b->ctx, num_sms);
 
     // the graph: per order, on its own worker stream, two launches (parity 0 then 1)
-    if (rc == SLLBM_OK) {
-        e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
-        if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->stream);
-        for (size_t s = 0; s < b->groups.size() && e == cudaSuccess && rc == SLLBM_OK; ++s) {
-            const BatchGroup& g = b->groups[s];
-            e = cudaStreamWaitEvent(b->workers[s], b->fork, 0);
-            for (int par = 0; par < 2 && e == cudaSuccess && rc == SLLBM_OK; ++par)
-                rc = launch_batch_group(g.p, g.shape, g.d_jobs, g.njobs, g.d_tabs, g.items, par, g.grid, b->workers[s]);
-            if (e == cudaSuccess && rc == SLLBM_OK) e = cudaEventRecord(b->join[s], b->workers[s]);
-            if (e == cudaSuccess && rc == SLLBM_OK) e = cudaStreamWaitEvent(b->stream, b->join[s], 0);
-        }
-        cudaGraph_t graph = nullptr;
-        const cudaError_t e_end = cudaStreamEndCapture(b->stream, &graph);
-        if (rc == SLLBM_OK && e == cudaSuccess && e_end == cudaSuccess) {
-            b->graph = graph;
-            if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) rc = SLLBM_ECUDA;
-        } else {
-            if (graph) cudaGraphDestroy(graph);
-            if (rc == SLLBM_OK) rc = SLLBM_ECUDA;
-        }
-    }
+    if (rc == SLLBM_OK) rc = capture_persistent(b);
     if (rc != SLLBM_OK) {
         cudaGetLastError();
         destroy_batch(b);

@@ -1,6 +1,7 @@
 // Persistent batched step kernels (FP32 storage, the generic kernel's tile body) and their
 // host helpers: one launch advances every mesh of one order by one step.
 #include "step_kernel.cuh"
+#include "tables.h"
 
 namespace sllbm {
 
@@ -47,12 +48,27 @@ int grid_t(int num_sms, long long items, int* grid) {
     return SLLBM_OK;
 }
 
+// The velocity set in FP32, built once.
+const Lattice<float>& lattice_f32() {
+    static const Lattice<float> lat = [] {
+        double xi[kQ][3], w[kQ];
+        build_velocity_set(xi, w);
+        Lattice<float> l;
+        for (int i = 0; i < kQ; ++i) {
+            for (int d = 0; d < 3; ++d) l.xi[i][d] = static_cast<float>(xi[i][d]);
+            l.w[i] = static_cast<float>(w[i]);
+        }
+        return l;
+    }();
+    return lat;
+}
+
 template <int P, int SH>
 int launch_t(const BatchJob* jobs, int njobs, const void* tabs, long long items, int parity, int grid,
              cudaStream_t st) {
     auto k = kernel_of<P, SH>();
     k<<<grid, BatchShape<P, SH>::NW * 32, smem_of<P, SH>(), st>>>(
-        jobs, njobs, static_cast<const StepTables<float, P>*>(tabs), items, parity);
+        jobs, njobs, static_cast<const StepTables<float, P>*>(tabs), items, parity, lattice_f32());
     return cudaGetLastError() == cudaSuccess ? SLLBM_OK : SLLBM_ECUDA;
 }
 

@@ -70,6 +70,13 @@ struct StepTables {
     C w[kQ];
 };
 
+// The velocity set (xi_i, w_i) in a compute type; the same for every context.
+template <typename C>
+struct Lattice {
+    C xi[kQ][3];
+    C w[kQ];
+};
+
 struct StepArgs {
     const void* src;
     void* dst;

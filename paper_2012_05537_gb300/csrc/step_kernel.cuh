@@ -147,9 +147,9 @@ __device__ __forceinline__ int wrap_index(int v, int n) {
 //   d_i'  = d_i  + omega (rho (P_i - 1) + (rho - rho0) - d_i),
 //   d_gi' = d_gi + omega ((2C_v-D) (T rho (P_i - 1) + (T - T0) rho + T0 (rho - rho0)) - d_gi),
 // with f_i^eq = w_i rho P_i (Eq. discreteEquilibrium, P_i the quartic in xi_i.u).
-template <typename S, typename C, int P, bool PR>
+template <typename S, typename C, int P, bool PR, class LT>
 __device__ __forceinline__ void collide_node_dev(const C* __restrict__ h, int stride, const StepArgs& a,
-                                                 const StepTables<C, P>& t, S* __restrict__ dst) {
+                                                 const LT& t, S* __restrict__ dst) {
     C drho = 0, mx = 0, my = 0, mz = 0, se = 0;
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
@@ -227,10 +227,11 @@ __device__ __forceinline__ void collide_node_dev(const C* __restrict__ h, int st
 }
 
 // Moments, equilibrium and collision of one node whose streamed populations are
-// h[q*stride], q = 0..89 (f then g); the result f_i, g_i goes to dst[2*i*nn + {0,1}].
-template <typename S, typename C, int P, bool PR>
+// h[q*stride], q = 0..89 (f then g); the result f_i, g_i goes to dst[2*i*nn + {0,1}].  The
+// velocity set comes from t.xi, t.w (a StepTables or a Lattice).
+template <typename S, typename C, int P, bool PR, class LT>
 __device__ __forceinline__ void collide_node(const C* __restrict__ h, int stride, const StepArgs& a,
-                                             const StepTables<C, P>& t, S* __restrict__ dst) {
+                                             const LT& t, S* __restrict__ dst) {
     if constexpr (PopCodec<S>::kDev) {
         collide_node_dev<S, C, P, PR>(h, stride, a, t, dst);
         return;
@@ -323,9 +324,9 @@ __host__ __device__ constexpr int shell_begin(int sh) {
 // shell's equilibrium coefficients stay compile-time indexed); the moment sums are combined
 // with one exchange, and both lanes form the node's parameters.  Storage types that hold the
 // populations themselves, no Prandtl term.
-template <typename S, typename C, int P>
+template <typename S, typename C, int P, class LT>
 __device__ __forceinline__ void collide_node_pair(const C* __restrict__ h, int stride, const StepArgs& a,
-                                                  const StepTables<C, P>& t, S* __restrict__ dst, int half,
+                                                  const LT& t, S* __restrict__ dst, int half,
                                                   unsigned mask) {
     if (!a.collide) {  // streaming only: each lane stores its velocities' pairs
         for (int i = half; i < kQ; i += 2) store_pair<S>(dst + 2 * i * a.nn, h[i * stride], h[(kQ + i) * stride]);
@@ -398,6 +399,23 @@ struct CollideOp {
     __device__ __forceinline__ void pair(const C* h, int stride, const StepArgs& a, const StepTables<C, P>& t,
                                          long long g, int half, unsigned mask) const {
         collide_node_pair<S, C, P>(h, stride, a, t, static_cast<S*>(a.dst) + 2 * g, half, mask);
+    }
+};
+
+// CollideOp of the batched kernel: the velocity set is read from `lat` (a kernel parameter,
+// shared by every mesh) instead of the job's tables, which that kernel keeps in shared
+// memory; collision operands then come from the constant bank as in step_kernel.
+template <typename C, int P>
+struct LatticeCollideOp {
+    static constexpr bool kPair = true;
+    const Lattice<C>& lat;
+    __device__ __forceinline__ void operator()(const C* h, int stride, const StepArgs& a, const StepTables<C, P>&,
+                                               long long g) const {
+        collide_node<C, C, P, false>(h, stride, a, lat, static_cast<C*>(a.dst) + 2 * g);
+    }
+    __device__ __forceinline__ void pair(const C* h, int stride, const StepArgs& a, const StepTables<C, P>&,
+                                         long long g, int half, unsigned mask) const {
+        collide_node_pair<C, C, P>(h, stride, a, lat, static_cast<C*>(a.dst) + 2 * g, half, mask);
     }
 };
 
@@ -587,7 +605,7 @@ struct BatchSmem {
 template <typename C, int P, int CX, int CY, int CZ, int NW>
 __global__ void __launch_bounds__(NW * 32)
     batch_step_kernel(const BatchJob* __restrict__ jobs, int njobs, const StepTables<C, P>* __restrict__ tabs,
-                      long long total, int parity) {
+                      long long total, int parity, const __grid_constant__ Lattice<C> lat) {
     using BS = BatchSmem<C, P, CX, CY, CZ, NW>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepTables<C, P>* st = reinterpret_cast<StepTables<C, P>*>(smem_raw + BS::body);
@@ -610,7 +628,7 @@ __global__ void __launch_bounds__(NW * 32)
             have = lo;
             __syncthreads();
         }
-        CollideOp<C, C, P, false> op;
+        LatticeCollideOp<C, P> op{lat};
         step_tile<C, C, P, CX, CY, CZ, NW, false>(*sa, *st, static_cast<int>(w - jobs[lo].tile_begin), smem_raw, op);
         __syncthreads();  // the next item reuses the shared memory
     }

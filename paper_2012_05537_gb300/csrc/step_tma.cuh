@@ -839,12 +839,19 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
 #pragma unroll
                         for (int l = 0; l <= P; ++l) wy[ay][l] = make_float2(t.lw[j][1][ay][l], t.lw[j][1][ay][l]);
                     }
-                    // two adjacent columns per lane: 16-byte loads and stores (XP is even)
-                    const int XQ = XP >> 1, ncol = G::TZ * XQ;
+                    // two adjacent columns per lane: 16-byte loads and stores (XP is even).  A
+                    // full-height box (NY == BY) has planes of an odd number of 16-byte columns,
+                    // so consecutive lanes over (oz, xq) would put two planes' columns in one
+                    // eighth of the warp on the same banks; there lane 8 oz + xq takes column
+                    // (oz, xq), each eighth reading within one plane (conflict free).
+                    const int XQ = XP >> 1;
                     float4* box4 = reinterpret_cast<float4*>(box);
+                    constexpr bool kByPlane = NY == G::BY && G::TZ <= 4 && G::BXP / 2 <= 8;
+                    const int ncol = kByPlane ? 32 : G::TZ * XQ;
 #pragma unroll 1
                     for (int e = lane; e < ncol; e += 32) {
-                        const int oz = e / XQ, xq = e - oz * XQ;
+                        const int oz = kByPlane ? e >> 3 : e / XQ, xq = kByPlane ? e & 7 : e - oz * XQ;
+                        if (kByPlane && (oz >= G::TZ || xq >= XQ)) continue;
                         float4* col = box4 + oz * (PL >> 1) + xq;
                         float2 va[NY], vb[NY];
 #pragma unroll
@@ -899,29 +906,45 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
 #pragma unroll
                         for (int l = 0; l <= P; ++l) wx[ax][l] = make_float2(t.lw[j][0][ax][l], t.lw[j][0][ax][l]);
                     }
-                    float2 v[NX];
-                    const float2* row = box + oz_l * PL + oy_l * XP + ox0;
+                    // the row from its even start in 16-byte loads (rows start on an even pair;
+                    // these are free of bank conflicts where 8-byte loads of the odd-stride rows
+                    // are not), the first pair used being ox0 = 0 or 1
+                    constexpr int K = (NX + 2) / 2;
+                    static_assert(2 * K <= (NX == G::BX ? G::BXP : G::BXP0), "row loads stay in the row");
+                    float2 u[2 * K];
+                    const float4* row4 = reinterpret_cast<const float4*>(box + oz_l * PL + oy_l * XP);
 #pragma unroll
-                    for (int x = 0; x < NX; ++x) v[x] = row_lane ? row[x] : make_float2(0.f, 0.f);
+                    for (int q = 0; q < K; ++q) {
+                        const float4 q4 = row_lane ? row4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        u[2 * q] = make_float2(q4.x, q4.y);
+                        u[2 * q + 1] = make_float2(q4.z, q4.w);
+                    }
+                    auto interp = [&](auto off) {
+                        constexpr int O = decltype(off)::value;
 #pragma unroll
-                    for (int ox = 0; ox < G::TX; ++ox) {
-                        const int cx = ox / P, ax = ox % P;
-                        float2 o = make_float2(0.f, 0.f);
-                        if constexpr (NX == G::BX) {
-                            if (kx[ax]) {
+                        for (int ox = 0; ox < G::TX; ++ox) {
+                            const int cx = ox / P, ax = ox % P;
+                            float2 o = make_float2(0.f, 0.f);
+                            if constexpr (NX == G::BX) {
+                                if (kx[ax]) {
 #pragma unroll
-                                for (int l = 0; l <= P; ++l) o = ffma2(v[(cx + 1) * P + l], wx[ax][l], o);
+                                    for (int l = 0; l <= P; ++l) o = ffma2(u[O + (cx + 1) * P + l], wx[ax][l], o);
+                                } else {
+#pragma unroll
+                                    for (int l = 0; l <= P; ++l) o = ffma2(u[O + cx * P + l], wx[ax][l], o);
+                                }
                             } else {
 #pragma unroll
-                                for (int l = 0; l <= P; ++l) o = ffma2(v[cx * P + l], wx[ax][l], o);
+                                for (int l = 0; l <= P; ++l) o = ffma2(u[O + cx * P + l], wx[ax][l], o);
                             }
-                        } else {
-#pragma unroll
-                            for (int l = 0; l <= P; ++l) o = ffma2(v[cx * P + l], wx[ax][l], o);
+                            res[2 * ox] = o.x;
+                            res[2 * ox + 1] = o.y;
                         }
-                        res[2 * ox] = o.x;
-                        res[2 * ox + 1] = o.y;
-                    }
+                    };
+                    if (ox0)
+                        interp(IntC<1>{});
+                    else
+                        interp(IntC<0>{});
                 };
                 if (sx)
                     x_pass(IntC<G::BX>{});

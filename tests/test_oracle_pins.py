@@ -107,6 +107,57 @@ def test_p2_equilibrium_moments_are_maxwellian(seed):
     assert np.allclose(M4, rho * _gauss4(u, T), atol=tol * 200, rtol=0)
 
 
+def gauss_product_set(n: int = 5):
+    """The Gauss-product alternative of Sec. II.B: the tensor product of the n-point
+    Gauss-Hermite rule for the unit-variance Gaussian (nodes and weights from numpy's
+    probabilists' Hermite routine), n^3 velocities; n = 5 is the 125-point set."""
+    x, wx = np.polynomial.hermite_e.hermegauss(n)
+    wx = wx / wx.sum()
+    xi = np.array(list(itertools.product(x, x, x)))
+    w = np.array([a * b * c for a, b, c in itertools.product(wx, wx, wx)])
+    return xi, w
+
+
+def test_d3q125_gauss_product_set_is_degree_nine_per_direction():
+    """Sec. II.B: the 125-point product rule integrates every monomial whose exponents are
+    each at most nine, and fails on x^10 (a textbook rule, independent of the 45-point set)."""
+    xi, w = gauss_product_set()
+    assert len(w) == 125 and np.all(w > 0) and abs(w.sum() - 1.0) < 1e-15
+    worst = 0.0
+    for e in itertools.product(range(10), repeat=3):
+        terms = w * np.prod(xi ** np.array(e), axis=1)
+        worst = max(worst, abs(terms.sum() - gauss_moment(e)) / np.abs(terms).sum())
+    assert worst < 1e-13
+    assert abs(np.sum(w * xi[:, 0] ** 10) - gauss_moment((10, 0, 0))) > 1.0
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_d3q45_and_d3q125_give_the_same_equilibrium_moments(seed):
+    """Any set exact to degree nine yields the same moments of the fourth-order equilibrium
+    up to order five (a quartic times a monomial of degree five stays within degree nine),
+    so the 45-point set and the 125-point product set, built independently, must agree on
+    all of them, including the fifth-order moments that no closed form above checks."""
+    rng = np.random.default_rng(100 + seed)
+    rho = rng.uniform(0.3, 3.0)
+    u = rng.uniform(-1.5, 1.5, 3)
+    T = rng.uniform(0.5, 2.0)
+    xi45, _ = O.velset()
+    xi125, w125 = gauss_product_set()
+    f45 = O.feq(rho, u, T)
+    f125 = O.feq(rho, u, T, xi125, w125)
+    assert not np.allclose(np.sort(f45)[:5], np.sort(f125)[:5])  # different sets, same moments
+    worst = 0.0
+    for deg in range(6):
+        for e in itertools.product(range(deg + 1), repeat=3):
+            if sum(e) != deg:
+                continue
+            m45 = np.sum(f45 * np.prod(xi45 ** np.array(e), axis=1))
+            m125 = np.sum(f125 * np.prod(xi125 ** np.array(e), axis=1))
+            scale = np.sum(np.abs(f125) * np.prod(np.abs(xi125) ** np.array(e), axis=1))
+            worst = max(worst, abs(m45 - m125) / scale)
+    assert worst < 1e-13
+
+
 def test_p2_energy_moment_of_both_populations():
     """Eq. (moments) with g^eq = (2C_v - D) T f^eq: sum(f|xi|^2 + g) = rho|u|^2 + 2 C_v rho T."""
     xi, w = O.velset()

@@ -23,6 +23,7 @@
 #include <type_traits>
 
 #include "collide.cuh"
+#include "packed.cuh"
 #include "sllbm_internal.h"
 #include "storage.cuh"
 
@@ -118,6 +119,71 @@ __device__ __forceinline__ void lagrange_column(const typename Pair2<C>::T (&v)[
         r[o].y = fy;
     }
 }
+
+// FP32 form of a pass without selects: for local node a the 2P+1 taps over v[base .. base+2P]
+// carry the P+1 weights at offset k_a P and zeros elsewhere, each as the pair (w, w) for the
+// packed FMA.  The real taps keep their order and a zero tap adds exactly zero, so a column
+// gives the same values as lagrange_column.
+template <int P>
+__device__ __forceinline__ void pad_weights(const float (&w)[P][P + 1], const signed char (&kc)[P],
+                                            float2 (&W)[P][2 * P + 1]) {
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+#pragma unroll
+        for (int m = 0; m <= 2 * P; ++m) {
+            const float lo = m <= P ? w[a][m] : 0.f;
+            const float hi = m >= P ? w[a][m - P] : 0.f;
+            const float x = kc[a] != 0 ? hi : lo;
+            W[a][m] = make_float2(x, x);
+        }
+    }
+}
+
+template <int P, int T, int NV>
+__device__ __forceinline__ void lagrange_column_packed(const float2 (&v)[NV], const float2 (&W)[P][2 * P + 1],
+                                                       float2 (&r)[T]) {
+    static_assert((T - 1) / P * P + 2 * P < NV, "column shorter than the taps of its outputs");
+#pragma unroll
+    for (int o = 0; o < T; ++o) {
+        const int a = o % P;
+        const int base = (o / P) * P;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int m = 0; m <= 2 * P; ++m) acc = ffma2(v[base + m], W[a][m], acc);
+        r[o] = acc;
+    }
+}
+
+// The weights of one pass of one velocity pair, held in registers for its columns, and the
+// pass over a column: register selects for FP64 arithmetic (padding would add FP64 FMAs),
+// the packed select-free form for FP32 arithmetic.
+template <typename C, int P>
+struct ColumnPass {
+    C w[P][P + 1];
+    signed char k[P];
+    __device__ __forceinline__ void load(const C (&lw)[P][P + 1], const signed char (&kc)[P]) {
+        load_pass_weights<C, P>(lw, kc, w, k);
+    }
+    template <int T, int NV>
+    __device__ __forceinline__ void apply(const typename Pair2<C>::T (&v)[NV], typename Pair2<C>::T (&r)[T]) const {
+        lagrange_column<C, P, T, NV>(v, w, k, r);
+    }
+};
+
+template <int P>
+struct ColumnPass<float, P> {
+    float2 W[P][2 * P + 1];
+    __device__ __forceinline__ void load(const float (&lw)[P][P + 1], const signed char (&kc)[P]) {
+        float w[P][P + 1];
+        signed char k[P];
+        load_pass_weights<float, P>(lw, kc, w, k);
+        pad_weights<P>(w, k, W);
+    }
+    template <int T, int NV>
+    __device__ __forceinline__ void apply(const float2 (&v)[NV], float2 (&r)[T]) const {
+        lagrange_column_packed<P, T, NV>(v, W, r);
+    }
+};
 
 // One pair (f_i, g_i) stored with a single 2-element store (the pair is adjacent in a state
 // buffer and aligned to its size).
@@ -465,9 +531,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const StepTables<C,
         const int sx = s[0], sxy = s[0] * s[1];
         // each pass reads the pair's weights and departure-cell bits of its direction from
         // the constant bank once, before its column loop
-        C wz[P][P + 1];
-        signed char kz[P];
-        load_pass_weights<C, P>(t.lw[i][2], t.kc[i][2], wz, kz);
+        ColumnPass<C, P> pz;
+        pz.load(t.lw[i][2], t.kc[i][2]);
         // gather + z pass: lane = column (x, y) of the source box
         for (int col = lane; col < sxy; col += 32) {
             const int y = col / sx;
@@ -484,16 +549,15 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const StepTables<C,
                 }
             }
             C2 r[TS::TZ];
-            lagrange_column<C, P, TS::TZ, TS::BZ>(v, wz, kz, r);
+            pz.template apply<TS::TZ, TS::BZ>(v, r);
 #pragma unroll
             for (int oz = 0; oz < TS::TZ; ++oz)
                 if (oz < te[2]) zb[oz * sxy + col] = r[oz];
         }
         __syncwarp();
         // y pass in place: lane = column (x, z)
-        C wy[P][P + 1];
-        signed char ky[P];
-        load_pass_weights<C, P>(t.lw[i][1], t.kc[i][1], wy, ky);
+        ColumnPass<C, P> py;
+        py.load(t.lw[i][1], t.kc[i][1]);
         const int ncol = te[2] * sx;
         for (int col = lane; col < ncol; col += 32) {
             const int oz = col / sx;
@@ -510,16 +574,15 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const StepTables<C,
                 }
             }
             C2 r[TS::TY];
-            lagrange_column<C, P, TS::TY, TS::BY>(v, wy, ky, r);
+            py.template apply<TS::TY, TS::BY>(v, r);
 #pragma unroll
             for (int oy = 0; oy < TS::TY; ++oy)
                 if (oy < te[1]) cp[oy * sx] = r[oy];
         }
         __syncwarp();
         // x pass: lane = row (y, z) of the tile; f_i to OUT[i], g_i to OUT[45 + i]
-        C wx[P][P + 1];
-        signed char kx[P];
-        load_pass_weights<C, P>(t.lw[i][0], t.kc[i][0], wx, kx);
+        ColumnPass<C, P> px;
+        px.load(t.lw[i][0], t.kc[i][0]);
         for (int row = lane; row < TS::TY * TS::TZ; row += 32) {
             const int oz = row / TS::TY;
             const int oy = row - oz * TS::TY;
@@ -536,7 +599,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const StepTables<C,
                 }
             }
             C2 r[TS::TX];
-            lagrange_column<C, P, TS::TX, TS::BX>(v, wx, kx, r);
+            px.template apply<TS::TX, TS::BX>(v, r);
             C* of = out + i * TS::TILE + (oz * TS::TY + oy) * TS::TX;
             C* og = of + kQ * TS::TILE;
 #pragma unroll

@@ -99,7 +99,7 @@ def measured_peaks():
 
 KERNEL_SOURCES = {
     # the TMA-fed kernel and what it is built from
-    "tma": ("step_tma.cuh", "step_f32.cu", "collide.cuh", "packed.cuh", "sllbm_internal.h", "tables.h"),
+    "tma": ("step_tma.cuh", "step_tma.cu", "collide.cuh", "packed.cuh", "sllbm_internal.h", "tables.h"),
     # the generic tile kernel and its instances
     "generic": ("step_kernel.cuh", "collide.cuh", "packed.cuh", "storage.cuh", "sllbm_internal.h", "tables.h", "step_f32.cu",
                 "step_f32_tiles.cu", "step_f64.cu", "step_f16.cu"),

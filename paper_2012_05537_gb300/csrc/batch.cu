@@ -1,6 +1,7 @@
 // Kernel choice, autotuner and batched (graph-captured) launch of many SLLBM contexts.
-// Host code only: the kernels are the step kernels of step_f32.cu / step_f64.cu /
-// step_f16.cu, launched through step_launch().
+// Host code only: the kernels are the step kernels of step_tma.cu / step_f32.cu /
+// step_f64.cu / step_f16.cu, launched through step_launch(), and the persistent batched
+// kernels of batch_kernel.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>

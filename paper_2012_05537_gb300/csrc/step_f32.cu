@@ -1,171 +1,12 @@
-// FP32 storage / FP32 arithmetic step: the TMA-fed persistent kernel (step_tma.cuh) where
-// the mesh allows it, the generic tile kernel (step_kernel.cuh) otherwise.
-#include <cudaTypedefs.h>
-
-#include <cstdlib>
-#include <cstring>
-#include <mutex>
-
+// FP32 storage / FP32 arithmetic step: the TMA-fed persistent kernel (step_tma.cu) where
+// the mesh allows it and the context selects it, the generic tile kernel (step_kernel.cuh)
+// otherwise.
 #include "step_kernel.cuh"
-#include "step_tma.cuh"
 
 namespace sllbm {
 
-namespace {
-
-// Tile (in cells) of the TMA kernel per order: 8x8x4 nodes for p = 2 and p = 4.  (For p = 3
-// a tile of whole cells is 9 nodes wide, and two tiles of streamed pairs do not fit in tensor
-// memory next to each other; p = 3 runs the generic kernel.)
-template <int P>
-struct TmaTile;
-template <>
-struct TmaTile<2> {
-    static constexpr int CX = 4, CY = 4, CZ = 2;
-};
-template <>
-struct TmaTile<4> {
-    static constexpr int CX = 2, CY = 2, CZ = 1;
-};
-// Stream warps (45 velocity pairs split evenly: 9 x 5).
-template <int P>
-constexpr int kConsumersFor = 9;
-
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static std::once_flag once;
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    std::call_once(once, [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    });
-    return fn;
-}
-
-template <int P>
-void fill_tables_s(const sllbm_ctx* ctx, StepTablesS<P>* t) {
-    for (int i = 0; i < kQ; ++i) {
-        for (int d = 0; d < 3; ++d) {
-            int kmn = ctx->dir[d].shift[i][0], kmx = kmn;
-            for (int a = 0; a < P; ++a) {
-                const int k = ctx->dir[d].shift[i][a];
-                kmn = k < kmn ? k : kmn;
-                kmx = k > kmx ? k : kmx;
-            }
-            t->kmin[i][d] = static_cast<signed char>(kmn);
-            t->span[i][d] = static_cast<signed char>(kmx - kmn);
-            for (int a = 0; a < P; ++a) {
-                t->kc[i][d][a] = static_cast<signed char>(ctx->dir[d].shift[i][a] - kmn);
-                for (int j = 0; j <= P; ++j) {
-                    t->lw[i][d][a][j] = static_cast<float>(ctx->dir[d].weight[i][a][j]);
-                }
-            }
-            t->xi[i][d] = static_cast<float>(ctx->xi[i][d]);
-        }
-        t->w[i] = static_cast<float>(ctx->w[i]);
-    }
-}
-
-template <int P>
-bool tma_eligible_p(const sllbm_ctx* c) {
-    using T = TmaTile<P>;
-    return c->cells[0] % T::CX == 0 && c->cells[1] % T::CY == 0 && c->cells[2] % T::CZ == 0;
-}
-
-// Builds (or reuses) the TMA descriptors of a source buffer: the buffer seen as a 4D FP32
-// tensor [45][Nz][Ny][2*Nx] (f_i, g_i interleaved along x), one descriptor per box shape
-// (span 0 or 1 of the departure cells in x, y, z).  Out-of-domain elements read as zero.
-template <int P>
-int tensor_maps_for(sllbm_ctx* ctx, const void* src, TmaMaps* out) {
-    using T = TmaTile<P>;
-    using G = TmaGeom<P, T::CX, T::CY, T::CZ>;
-    const int k = (src == ctx->buf[0]) ? 0 : 1;
-    if (ctx->tmap_src[k] != src) {
-        PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-        if (enc == nullptr) return SLLBM_ECUDA;
-        const cuuint64_t nx2 = 2ull * ctx->N[0];
-        cuuint64_t gdim[4] = {nx2, static_cast<cuuint64_t>(ctx->N[1]), static_cast<cuuint64_t>(ctx->N[2]),
-                              static_cast<cuuint64_t>(kQ)};
-        cuuint64_t gstride[3] = {nx2 * 4, nx2 * ctx->N[1] * 4, nx2 * ctx->N[1] * ctx->N[2] * 4};
-        cuuint32_t estride[4] = {1, 1, 1, 1};
-        for (int shape = 0; shape < 8; ++shape) {
-            CUtensorMap map;
-            cuuint32_t box[4] = {2u * G::xpairs(shape & 1), static_cast<cuuint32_t>(G::rows((shape >> 1) & 1)),
-                                 static_cast<cuuint32_t>(G::planes((shape >> 2) & 1)), 1u};
-            CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(src), gdim, gstride, box,
-                             estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) {
-                ctx->tmap_src[k] = nullptr;
-                return SLLBM_ECUDA;
-            }
-            std::memcpy(ctx->tmap[k][shape], &map, sizeof(map));
-        }
-        ctx->tmap_src[k] = src;
-    }
-    std::memcpy(out, ctx->tmap[k], sizeof(TmaMaps));
-    return SLLBM_OK;
-}
-
-template <int P>
-int launch_tma(sllbm_ctx* ctx, const void* src, void* dst) {
-    using T = TmaTile<P>;
-    constexpr int kConsumers = kConsumersFor<P>;
-    using SM = TmaSmem<P, T::CX, T::CY, T::CZ, kConsumers>;
-    static_assert(SM::bytes <= kSmemBudget, "shared memory budget");
-    using Tab = StepTablesS<P>;
-    if (ctx->step_blob == nullptr || ctx->step_blob_size != sizeof(Tab) + 1) {
-        std::free(ctx->step_blob);
-        ctx->step_blob = static_cast<unsigned char*>(std::malloc(sizeof(Tab)));
-        if (ctx->step_blob == nullptr) return SLLBM_ENOMEM;
-        ctx->step_blob_size = sizeof(Tab) + 1;  // +1 keeps it distinct from the generic tables
-        fill_tables_s<P>(ctx, reinterpret_cast<Tab*>(ctx->step_blob));
-    }
-    TmaMaps maps;
-    int rc = tensor_maps_for<P>(ctx, src, &maps);
-    if (rc != SLLBM_OK) return rc;
-    StepArgs args;
-    fill_step_args(ctx, src, dst, &args);
-    const int ntiles = (ctx->cells[0] / T::CX) * (ctx->cells[1] / T::CY) * (ctx->cells[2] / T::CZ);
-    const int grid = ntiles < ctx->num_sms ? ntiles : ctx->num_sms;
-    auto k = step_tma_kernel<P, T::CX, T::CY, T::CZ, kConsumers>;
-    cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(SM::bytes));
-    if (err == cudaSuccess) {
-        k<<<grid, kWarps * 32, SM::bytes, ctx->stream>>>(
-            maps, args, *reinterpret_cast<const Tab*>(ctx->step_blob));
-        err = cudaGetLastError();
-    }
-    ctx->launches += 1;
-    if (err != cudaSuccess) {
-        ctx->last_err = static_cast<int>(err);
-        return SLLBM_ECUDA;
-    }
-    return SLLBM_OK;
-}
-
-}  // namespace
-
-bool tma_step_eligible(const sllbm_ctx* c) {
-    if (c->prm.storage != SLLBM_F32 || c->prm.pr_correction || !c->prm.collide) return false;
-    if (c->N[0] % 2 != 0 || c->num_sms <= 0) return false;
-    if (tensor_map_encoder() == nullptr) return false;
-    switch (c->p) {
-    case 2: return tma_eligible_p<2>(c);
-    case 4: return tma_eligible_p<4>(c);
-    }
-    return false;
-}
-
 int launch_step_f32(sllbm_ctx* ctx, const void* src, void* dst) {
-    if (ctx->step_kernel == 2) {
-        switch (ctx->p) {
-        case 2: return launch_tma<2>(ctx, src, dst);
-        case 4: return launch_tma<4>(ctx, src, dst);
-        }
-        return SLLBM_EINVAL;
-    }
+    if (ctx->step_kernel == 2) return launch_step_tma(ctx, src, dst);
     if (ctx->tile_shape != 0) return launch_step_f32_shape(ctx, src, dst, ctx->tile_shape);
     // p = 3: tiles of 4x2x1 cells with 8 warps fit twice on an SM (shared memory and
     // registers), so one CTA's collision overlaps another's streaming; measured 4-7 % faster

@@ -137,6 +137,37 @@ void sllbm_default_params(sllbm_params *p_out);
 int sllbm_create(const sllbm_mesh *mesh, int p, sllbm_velset vs, const sllbm_params *prm,
                  void *cuda_stream, sllbm_ctx **out);
 
+/* Domain decomposition along z (one process or context per part of a mesh too large for
+ * one device).  The pull streaming of Sec. II.A reads, for a node, only the (p+1)^3
+ * support points of the cell its departure point falls in, at most max_cell_shift cells
+ * away, so a slab of consecutive z-cells advances exactly like the whole periodic mesh
+ * once the cells next to it hold the neighbouring slabs' current state.
+ *
+ * sllbm_create_slab creates a context for the interior cells [z_begin, z_begin + z_cells)
+ * of the periodic mesh `mesh` (same arguments and errors as sllbm_create otherwise).
+ * Its state holds ghost = max_cell_shift + 1 cells of halo below and above the interior:
+ * N[2] = (z_cells + 2 ghost) p planes in the usual layout, with the z-cells numbered on
+ * the whole mesh (cell z_begin - ghost first, periodic), so sllbm_init_tgv and
+ * sllbm_init_fields set the slab's part of the whole-mesh fields, and sllbm_step updates
+ * the interior planes only (generic tile kernel).  Before every step the caller refreshes
+ * the halos: sllbm_halo_pack(side 0) copies the lowest `ghost` interior cells of the
+ * current state to a device buffer for the slab below, sllbm_halo_pack(side 1) the
+ * highest ones for the slab above; sllbm_halo_unpack(side 0 / 1) writes a buffer received
+ * from the slab below / above into the ghost cells below / above.  Halo buffers hold
+ * halo_bytes (sllbm_slab_info) in the order [i][plane][y][x][h], device memory owned by
+ * the caller; both calls are one asynchronous copy on the context's stream.
+ * Errors: SLLBM_EINVAL for z_begin outside the mesh, z_cells < 1 or above the mesh, a
+ * slab thinner than its ghost width (its halo would come from two neighbours), a TMA-fed
+ * kernel request, and for slab contexts in sllbm_diag*, the reverse-mode calls, batches
+ * and variant 0 of sllbm_set_step_variant; sllbm_halo_* and sllbm_slab_info on a context
+ * that is not a slab, side not 0 or 1, a NULL buffer or a context without state:
+ * SLLBM_EINVAL; a failed copy: SLLBM_ECUDA. */
+int sllbm_create_slab(const sllbm_mesh *mesh, int p, sllbm_velset vs, const sllbm_params *prm,
+                      int z_begin, int z_cells, void *cuda_stream, sllbm_ctx **out);
+int sllbm_slab_info(const sllbm_ctx *ctx, int *ghost_cells, size_t *halo_bytes);
+int sllbm_halo_pack(sllbm_ctx *ctx, int side, void *halo);
+int sllbm_halo_unpack(sllbm_ctx *ctx, int side, const void *halo);
+
 /* Frees everything the context owns (not caller buffers). NULL is accepted. */
 void sllbm_destroy(sllbm_ctx *ctx);
 

@@ -589,7 +589,7 @@ namespace {
 
 bool adjoint_supported(const sllbm_ctx* ctx) {
     return (ctx->prm.storage == SLLBM_F32 || ctx->prm.storage == SLLBM_F64) && !ctx->prm.pr_correction &&
-           ctx->prm.collide;
+           ctx->prm.collide && !ctx->slab;
 }
 
 template <typename C>
@@ -753,7 +753,7 @@ extern "C" {
 
 int sllbm_stream_apply(sllbm_ctx* ctx, const void* src, void* dst, int transpose) {
     if (ctx == nullptr || src == nullptr || dst == nullptr) return SLLBM_EINVAL;
-    if (ctx->prm.storage != SLLBM_F32 && ctx->prm.storage != SLLBM_F64) return SLLBM_EINVAL;
+    if ((ctx->prm.storage != SLLBM_F32 && ctx->prm.storage != SLLBM_F64) || ctx->slab) return SLLBM_EINVAL;
     int rc = ensure_adjoint_scratch(ctx);
     if (rc != SLLBM_OK) return rc;
     return ctx->prm.storage == SLLBM_F64 ? stream_apply_t<double>(ctx, src, dst, transpose != 0)

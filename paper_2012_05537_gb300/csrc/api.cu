@@ -278,7 +278,8 @@ __global__ void sum_partials_kernel(const double* __restrict__ partials, int nbl
 
 // 1: generic tile kernel, 2: TMA-fed persistent kernel, 0: the requested kernel cannot run.
 int choose_step_kernel(const sllbm_ctx* c) {
-    const bool tma_ok = tma_step_eligible(c);
+    // a slab's tiles start above its ghost cells: the generic kernel only
+    const bool tma_ok = !c->slab && tma_step_eligible(c);
     if (c->prm.kernel == 2) return tma_ok ? 2 : 0;
     if (c->prm.kernel == 1) return 1;
     return tma_ok ? 2 : 1;
@@ -420,6 +421,7 @@ void fill_step_args(const sllbm_ctx* ctx, const void* src, void* dst, StepArgs* 
     a->collide = ctx->prm.collide;
     a->flag = ctx->prm.nonfinite_check ? ctx->d_flag : nullptr;
     a->flag_err = ctx->d_flag + 1;
+    a->z0 = ctx->ghost;
 }
 
 }  // namespace sllbm
@@ -446,8 +448,14 @@ void sllbm_default_params(sllbm_params* p) {
     p->kernel = 0;
 }
 
-int sllbm_create(const sllbm_mesh* mesh, int p, sllbm_velset vs, const sllbm_params* prm,
-                 void* cuda_stream, sllbm_ctx** out) {
+}  // extern "C"
+
+namespace {
+
+// sllbm_create (slab = 0: the whole periodic mesh) and sllbm_create_slab (slab = 1: the
+// z-cells [z_begin, z_begin + z_cells) with ghost cells of halo on both sides).
+int create_ctx(const sllbm_mesh* mesh, int p, sllbm_velset vs, const sllbm_params* prm, int slab, int z_begin,
+               int z_cells, void* cuda_stream, sllbm_ctx** out) {
     if (out == nullptr) return SLLBM_EINVAL;
     *out = nullptr;
     if (mesh == nullptr || prm == nullptr || vs != SLLBM_D3Q45) return SLLBM_EINVAL;
@@ -465,6 +473,8 @@ int sllbm_create(const sllbm_mesh* mesh, int p, sllbm_velset vs, const sllbm_par
         nn *= static_cast<long long>(mesh->cells[d]) * p;
     }
     if (nn > 0x7fffffffLL) return SLLBM_EINVAL;  // per-field offsets are 32-bit
+    if (slab && (z_begin < 0 || z_begin >= mesh->cells[2] || z_cells < 1 || z_cells > mesh->cells[2]))
+        return SLLBM_EINVAL;
     sllbm_ctx* c = static_cast<sllbm_ctx*>(std::calloc(1, sizeof(sllbm_ctx)));
     if (c == nullptr) return SLLBM_ENOMEM;
     c->p = p;
@@ -476,6 +486,7 @@ int sllbm_create(const sllbm_mesh* mesh, int p, sllbm_velset vs, const sllbm_par
         c->L[d] = mesh->L[d];
         c->h[d] = mesh->L[d] / mesh->cells[d];
     }
+    c->z_cells_global = mesh->cells[2];
     build_velocity_set(c->xi, c->w);
     double mx = 0.0;
     for (int i = 0; i < kQ; ++i)
@@ -518,6 +529,28 @@ int sllbm_create(const sllbm_mesh* mesh, int p, sllbm_velset vs, const sllbm_par
         std::free(c);
         return SLLBM_EINVAL;
     }
+    if (slab) {
+        // Ghost cells per side: a tile's source box starts kmin >= -max_shift cells below the
+        // tile and ends with the first node of the cell kmin + span <= max_shift cells above
+        // its last cell, so max_shift + 1 cells on each side hold every source node, and the
+        // halo of one side comes from one neighbouring slab if the slab has at least as many
+        // cells.
+        c->slab = 1;
+        c->z_begin = z_begin;
+        c->ghost = c->max_shift + 1;
+        if (z_cells < c->ghost) {
+            std::free(c);
+            return SLLBM_EINVAL;
+        }
+        c->cells[2] = z_cells;
+        c->N[2] = (z_cells + 2 * c->ghost) * p;
+        c->nn = static_cast<long long>(c->N[0]) * c->N[1] * c->N[2];
+        if (c->nn > 0x7fffffffLL) {
+            std::free(c);
+            return SLLBM_EINVAL;
+        }
+        nn = c->nn;
+    }
     c->elem = prm->storage == SLLBM_F64 ? sizeof(double) : prm->storage == SLLBM_F32 ? sizeof(float) : 2;
     c->pop_bytes = static_cast<size_t>(2 * kQ) * static_cast<size_t>(nn) * c->elem;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -531,9 +564,15 @@ int sllbm_create(const sllbm_mesh* mesh, int p, sllbm_velset vs, const sllbm_par
                 e = cudaErrorMemoryAllocation;
                 break;
             }
-            for (int cc = 0; cc < c->cells[d]; ++cc)
+            // (a slab's local planes start `ghost` cells below its first interior cell; their
+            // cells are numbered on the whole periodic mesh)
+            const int c_first = d == 2 ? c->z_begin - c->ghost : 0;
+            const int c_wrap = d == 2 ? c->z_cells_global : c->cells[d];
+            for (int cc = 0; cc < c->N[d] / p; ++cc) {
+                const int gc = ((c_first + cc) % c_wrap + c_wrap) % c_wrap;
                 for (int a = 0; a < p; ++a)
-                    x[cc * p + a] = cc * c->h[d] + (1.0 - std::cos(kPi * a / p)) * 0.5 * c->h[d];
+                    x[cc * p + a] = gc * c->h[d] + (1.0 - std::cos(kPi * a / p)) * 0.5 * c->h[d];
+            }
             e = cudaMemcpy(c->d_coords[d], x, sizeof(double) * c->N[d], cudaMemcpyHostToDevice);
             std::free(x);
         }
@@ -554,6 +593,56 @@ int sllbm_create(const sllbm_mesh* mesh, int p, sllbm_velset vs, const sllbm_par
     }
     *out = c;
     return SLLBM_OK;
+}
+
+// The planes [plane0, plane0 + ghost p) of every velocity of the current state <-> a packed
+// halo buffer [i][plane][y][x][h]: one strided copy of 45 chunks.
+int halo_copy(sllbm_ctx* ctx, int side, void* halo, int to_state) {
+    if (ctx == nullptr || !ctx->slab || halo == nullptr || (side != 0 && side != 1)) return SLLBM_EINVAL;
+    if (ctx->buf[ctx->cur] == nullptr) return SLLBM_EINVAL;
+    const int gp = ctx->ghost * ctx->p;
+    // packing (to_state = 0) reads the interior cells next to the side; unpacking writes the
+    // ghost cells on that side
+    const int plane0 = to_state ? (side == 0 ? 0 : (ctx->ghost + ctx->cells[2]) * ctx->p)
+                                : (side == 0 ? gp : ctx->cells[2] * ctx->p);
+    const size_t plane_bytes = static_cast<size_t>(ctx->N[0]) * ctx->N[1] * 2 * ctx->elem;
+    const size_t chunk = static_cast<size_t>(gp) * plane_bytes;
+    const size_t vstride = static_cast<size_t>(ctx->N[2]) * plane_bytes;
+    unsigned char* state = static_cast<unsigned char*>(ctx->buf[ctx->cur]) + static_cast<size_t>(plane0) * plane_bytes;
+    cudaError_t e = to_state ? cudaMemcpy2DAsync(state, vstride, halo, chunk, chunk, kQ, cudaMemcpyDeviceToDevice,
+                                                 ctx->stream)
+                             : cudaMemcpy2DAsync(halo, chunk, state, vstride, chunk, kQ, cudaMemcpyDeviceToDevice,
+                                                 ctx->stream);
+    CK(ctx, e);
+    return SLLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sllbm_create(const sllbm_mesh* mesh, int p, sllbm_velset vs, const sllbm_params* prm,
+                 void* cuda_stream, sllbm_ctx** out) {
+    return create_ctx(mesh, p, vs, prm, 0, 0, 0, cuda_stream, out);
+}
+
+int sllbm_create_slab(const sllbm_mesh* mesh, int p, sllbm_velset vs, const sllbm_params* prm, int z_begin,
+                      int z_cells, void* cuda_stream, sllbm_ctx** out) {
+    return create_ctx(mesh, p, vs, prm, 1, z_begin, z_cells, cuda_stream, out);
+}
+
+int sllbm_slab_info(const sllbm_ctx* ctx, int* ghost_cells, size_t* halo_bytes) {
+    if (ctx == nullptr || !ctx->slab) return SLLBM_EINVAL;
+    if (ghost_cells != nullptr) *ghost_cells = ctx->ghost;
+    if (halo_bytes != nullptr)
+        *halo_bytes = static_cast<size_t>(kQ) * ctx->ghost * ctx->p * ctx->N[0] * ctx->N[1] * 2 * ctx->elem;
+    return SLLBM_OK;
+}
+
+int sllbm_halo_pack(sllbm_ctx* ctx, int side, void* halo) { return halo_copy(ctx, side, halo, 0); }
+
+int sllbm_halo_unpack(sllbm_ctx* ctx, int side, const void* halo) {
+    return halo_copy(ctx, side, const_cast<void*>(halo), 1);
 }
 
 void sllbm_destroy(sllbm_ctx* ctx) {
@@ -794,7 +883,7 @@ int sllbm_moments(sllbm_ctx* ctx, double* rho, double* u, double* T, int on_devi
 }
 
 int sllbm_diag(sllbm_ctx* ctx, double* Ek, double* eps_s, double* eps_c) {
-    if (ctx == nullptr || Ek == nullptr || eps_s == nullptr || eps_c == nullptr) return SLLBM_EINVAL;
+    if (ctx == nullptr || Ek == nullptr || eps_s == nullptr || eps_c == nullptr || ctx->slab) return SLLBM_EINVAL;
     if (!ctx->initialised) return SLLBM_ENOTREADY;
     if (ctx->d_partials == nullptr) {
         const long long ncell = static_cast<long long>(ctx->cells[0]) * ctx->cells[1] * ctx->cells[2];
@@ -833,7 +922,7 @@ int sllbm_diag(sllbm_ctx* ctx, double* Ek, double* eps_s, double* eps_c) {
 // share the array and each overwrites every entry it reads, so nothing needs clearing,
 // but calls that overlap on the GPU (other streams, other contexts) race on it.
 int sllbm_diag_noalloc(sllbm_ctx* ctx, double* Ek, double* eps_s, double* eps_c) {
-    if (ctx == nullptr || Ek == nullptr || eps_s == nullptr || eps_c == nullptr) return SLLBM_EINVAL;
+    if (ctx == nullptr || Ek == nullptr || eps_s == nullptr || eps_c == nullptr || ctx->slab) return SLLBM_EINVAL;
     if (!ctx->initialised) return SLLBM_ENOTREADY;
     const long long ncell = static_cast<long long>(ctx->cells[0]) * ctx->cells[1] * ctx->cells[2];
     if (ncell > kNoAllocDiagMaxCells) return SLLBM_EINVAL;  // more cells than the static scratch holds

@@ -41,7 +41,7 @@ namespace {
 
 int set_variant(sllbm_ctx* ctx, int v) {
     if (v == 0) {
-        if (!tma_step_eligible(ctx)) return SLLBM_EINVAL;
+        if (ctx->slab || !tma_step_eligible(ctx)) return SLLBM_EINVAL;
         ctx->step_kernel = 2;
         ctx->tile_shape = 0;
         return SLLBM_OK;
@@ -221,7 +221,9 @@ int sllbm_batch_create(sllbm_ctx* const* ctxs, int n, int streams, void* cuda_st
     if (cudaGetDevice(&dev) != cudaSuccess) return SLLBM_ECUDA;
     for (int k = 0; k < n; ++k) {
         const sllbm_ctx* c = ctxs[k];
-        if (c == nullptr || !c->initialised || c->prm.nonfinite_check || c->device != dev) return SLLBM_EINVAL;
+        // (a slab needs its halo exchanged between steps: not inside a batch)
+        if (c == nullptr || !c->initialised || c->prm.nonfinite_check || c->device != dev || c->slab)
+            return SLLBM_EINVAL;
         for (int j = 0; j < k; ++j)
             if (ctxs[j] == c) return SLLBM_EINVAL;
     }
@@ -368,7 +370,9 @@ int sllbm_batch_create_persistent(sllbm_ctx* const* ctxs, int n, void* cuda_stre
     if (cudaGetDevice(&dev) != cudaSuccess) return SLLBM_ECUDA;
     for (int k = 0; k < n; ++k) {
         const sllbm_ctx* c = ctxs[k];
-        if (c == nullptr || !c->initialised || c->prm.nonfinite_check || c->device != dev) return SLLBM_EINVAL;
+        // (a slab needs its halo exchanged between steps: not inside a batch)
+        if (c == nullptr || !c->initialised || c->prm.nonfinite_check || c->device != dev || c->slab)
+            return SLLBM_EINVAL;
         if (c->prm.storage != SLLBM_F32 || c->prm.pr_correction || !c->prm.collide) return SLLBM_EINVAL;
         for (int j = 0; j < k; ++j)
             if (ctxs[j] == c) return SLLBM_EINVAL;

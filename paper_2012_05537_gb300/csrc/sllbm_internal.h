@@ -53,6 +53,14 @@ struct sllbm_ctx {
     void* pipe_buf[6];         // sllbm_run_host_many: three device slots of two buffers
     cudaStream_t pipe_stream[2];  // its host-to-device and device-to-host copy streams
     cudaEvent_t pipe_ev[9];    // per slot: copied in, stepped, copied out
+    // z-slab of a decomposed mesh (sllbm_create_slab): the state holds the interior cells
+    // [z_begin, z_begin + cells[2]) of a mesh of z_cells_global cells along z, plus `ghost`
+    // cells of halo below and above them (N[2] = (cells[2] + 2 ghost) p planes).  An ordinary
+    // periodic context has slab = 0, ghost = 0.
+    int slab;
+    int z_begin;
+    int z_cells_global;
+    int ghost;
 };
 
 namespace sllbm {
@@ -93,6 +101,7 @@ struct StepArgs {
     int collide;        // 0: stream only
     int* flag;          // non-finite flag or nullptr
     int* flag_err;      // set (bit 2) when a bounded device-side wait gave up
+    int z0;             // first interior cell along z (a slab's ghost cells; 0 on a periodic mesh)
 };
 
 template <typename C, int P>

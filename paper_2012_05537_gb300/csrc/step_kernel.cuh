@@ -509,8 +509,10 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const StepTables<C,
     tile /= a.tiles[0];
     const int tiy = tile % a.tiles[1];
     const int tiz = tile / a.tiles[1];
-    const int c0[3] = {tix * CX, tiy * CY, tiz * CZ};
-    const int tc[3] = {min(CX, a.cells[0] - c0[0]), min(CY, a.cells[1] - c0[1]), min(CZ, a.cells[2] - c0[2])};
+    // (a slab's tiles cover its interior cells, which start a.z0 cells above its first plane)
+    const int c0[3] = {tix * CX, tiy * CY, tiz * CZ + a.z0};
+    const int tc[3] = {min(CX, a.cells[0] - c0[0]), min(CY, a.cells[1] - c0[1]),
+                       min(CZ, a.cells[2] + a.z0 - c0[2])};
     const int te[3] = {tc[0] * P, tc[1] * P, tc[2] * P};
     const S* __restrict__ src = static_cast<const S*>(a.src);
     const int nxy = a.N[0] * a.N[1];

@@ -1,0 +1,122 @@
+"""Domain decomposition of one periodic mesh along z.
+
+Each part is a slab context (``sllbm_create_slab``): its interior z-cells plus ``ghost``
+cells of halo below and above.  The pull streaming of Sec. II.A reads, for a node, the
+support points of the cell its departure point falls in, at most ``max_cell_shift`` cells
+away, so one halo exchange with the two neighbouring slabs before every step makes the
+slabs advance exactly as the whole mesh does.  The exchange is the only data movement
+between parts; the collision is node-local.
+
+Parts are ranks of a ``torch.distributed`` group (one GPU each; NCCL point-to-point on GPU
+buffers) or, on one device, several slab contexts of one process (``exchange_local``).
+"""
+from __future__ import annotations
+
+
+def slab_bounds(z_cells: int, parts: int, part: int) -> tuple[int, int]:
+    """(z_begin, z_cells) of part ``part`` of ``parts``: consecutive slabs whose sizes differ
+    by at most one cell."""
+    if parts < 1 or not 0 <= part < parts or z_cells < parts:
+        raise ValueError(f"cannot split {z_cells} cells into {parts} slabs (part {part})")
+    base, extra = divmod(z_cells, parts)
+    begin = part * base + min(part, extra)
+    return begin, base + (1 if part < extra else 0)
+
+
+def neighbours(rank: int, world: int) -> tuple[int, int]:
+    """(rank below, rank above) on the periodic ring of slabs."""
+    return (rank - 1) % world, (rank + 1) % world
+
+
+def exchange(send_low, send_high, recv_low, recv_high, rank: int, world: int, group=None) -> None:
+    """One halo exchange on the ring of slabs: ``send_low`` (the slab's lowest interior cells)
+    goes to the rank below, whose halo above it becomes; ``send_high`` goes to the rank
+    above; ``recv_low`` / ``recv_high`` receive the halos below / above.  With one rank the
+    slab is its own neighbour on both sides.  With two ranks both messages of a rank go to
+    the same peer; the receives are posted so that they match the sends in order (the
+    peer's lowest cells lie above this slab, its highest below)."""
+    if world == 1:
+        recv_low.copy_(send_high)
+        recv_high.copy_(send_low)
+        return
+    import torch.distributed as dist
+    below, above = neighbours(rank, world)
+    ops = [dist.P2POp(dist.isend, send_low, below, group),
+           dist.P2POp(dist.isend, send_high, above, group),
+           dist.P2POp(dist.irecv, recv_high, above, group),
+           dist.P2POp(dist.irecv, recv_low, below, group)]
+    for req in dist.batch_isend_irecv(ops):
+        req.wait()
+
+
+class SlabStepper:
+    """Advances one slab ``Sim`` (created with ``Config(slab=...)``), exchanging its halos
+    with the neighbouring ranks before every step."""
+
+    def __init__(self, sim, rank: int = 0, world: int = 1, group=None):
+        from . import sllbm as S
+        self.sim, self.rank, self.world, self.group = sim, rank, world, group
+        self.ghost, self.halo_bytes = S.sllbm_slab_info(sim.ctx)
+        torch = sim.torch
+        self.bufs = {k: torch.empty(self.halo_bytes, dtype=torch.uint8, device=sim.device)
+                     for k in ("send_low", "send_high", "recv_low", "recv_high")}
+
+    def pack(self) -> None:
+        from . import sllbm as S
+        S.sllbm_halo_pack(self.sim.ctx, 0, self.bufs["send_low"].data_ptr())
+        S.sllbm_halo_pack(self.sim.ctx, 1, self.bufs["send_high"].data_ptr())
+
+    def unpack(self) -> None:
+        from . import sllbm as S
+        S.sllbm_halo_unpack(self.sim.ctx, 0, self.bufs["recv_low"].data_ptr())
+        S.sllbm_halo_unpack(self.sim.ctx, 1, self.bufs["recv_high"].data_ptr())
+
+    def exchange(self) -> None:
+        torch = self.sim.torch
+        self.pack()
+        # the collectives run after the packs (enqueued on the slab's stream) and before the
+        # unpacks
+        cur = torch.cuda.current_stream(self.sim.device)
+        cur.wait_stream(self.sim.stream)
+        b = self.bufs
+        exchange(b["send_low"], b["send_high"], b["recv_low"], b["recv_high"], self.rank, self.world,
+                 self.group)
+        self.sim.stream.wait_stream(cur)
+        self.unpack()
+
+    def step(self, n: int = 1) -> None:
+        for _ in range(n):
+            self.exchange()
+            rc = self.sim.step(1)
+            if rc != 0:
+                raise RuntimeError(f"sllbm_step returned {rc}")
+
+
+def exchange_local(steppers) -> None:
+    """The halo exchange of several slabs held by one process (a ring in z order), by device
+    copies on each slab's stream: every slab packs, then unpacks its neighbours' packs."""
+    n = len(steppers)
+    for st in steppers:
+        st.pack()
+    for k, st in enumerate(steppers):
+        below, above = steppers[(k - 1) % n], steppers[(k + 1) % n]
+        st.sim.stream.wait_stream(below.sim.stream)
+        st.sim.stream.wait_stream(above.sim.stream)
+        with st.sim.torch.cuda.stream(st.sim.stream):
+            st.bufs["recv_low"].copy_(below.bufs["send_high"])
+            st.bufs["recv_high"].copy_(above.bufs["send_low"])
+        st.unpack()
+    # a slab's next pack overwrites send buffers its neighbours copied from above
+    for k, st in enumerate(steppers):
+        st.sim.stream.wait_stream(steppers[(k - 1) % n].sim.stream)
+        st.sim.stream.wait_stream(steppers[(k + 1) % n].sim.stream)
+
+
+def step_local(steppers, n: int = 1) -> None:
+    """Advances several slabs of one process by n steps (exchange, then one step each)."""
+    for _ in range(n):
+        exchange_local(steppers)
+        for st in steppers:
+            rc = st.sim.step(1)
+            if rc != 0:
+                raise RuntimeError(f"sllbm_step returned {rc}")

@@ -76,6 +76,12 @@ def load(build_if_missing: bool = False):
         "sllbm_default_params": (None, [ctypes.POINTER(Params)]),
         "sllbm_create": (ctypes.c_int, [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(Params), vp, ctypes.POINTER(vp)]),
+        "sllbm_create_slab": (ctypes.c_int, [ctypes.POINTER(Mesh), ctypes.c_int, ctypes.c_int,
+                                             ctypes.POINTER(Params), ctypes.c_int, ctypes.c_int, vp,
+                                             ctypes.POINTER(vp)]),
+        "sllbm_slab_info": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)]),
+        "sllbm_halo_pack": (ctypes.c_int, [vp, ctypes.c_int, vp]),
+        "sllbm_halo_unpack": (ctypes.c_int, [vp, ctypes.c_int, vp]),
         "sllbm_destroy": (None, [vp]),
         "sllbm_get_info": (ctypes.c_int, [vp, ctypes.POINTER(Info)]),
         "sllbm_velset_table": (ctypes.c_int, [vp, dp, dp]),
@@ -153,6 +159,30 @@ def sllbm_create(mesh: Mesh, p: int, params: Params, stream: int = 0, velset: in
                              ctypes.c_void_p(stream), ctypes.byref(ctx))
     _check(rc, "sllbm_create")
     return ctx
+
+
+def sllbm_create_slab(mesh: Mesh, p: int, params: Params, z_begin: int, z_cells: int, stream: int = 0,
+                      velset: int = 0):
+    ctx = ctypes.c_void_p()
+    rc = load().sllbm_create_slab(ctypes.byref(mesh), int(p), int(velset), ctypes.byref(params), int(z_begin),
+                                  int(z_cells), ctypes.c_void_p(stream), ctypes.byref(ctx))
+    _check(rc, "sllbm_create_slab")
+    return ctx
+
+
+def sllbm_slab_info(ctx):
+    """(ghost cells per side, bytes of one side's halo buffer)."""
+    g, b = ctypes.c_int(), ctypes.c_size_t()
+    _check(load().sllbm_slab_info(ctx, ctypes.byref(g), ctypes.byref(b)), "sllbm_slab_info", ctx)
+    return int(g.value), int(b.value)
+
+
+def sllbm_halo_pack(ctx, side: int, halo_ptr: int) -> None:
+    _check(load().sllbm_halo_pack(ctx, int(side), ctypes.c_void_p(halo_ptr)), "sllbm_halo_pack", ctx)
+
+
+def sllbm_halo_unpack(ctx, side: int, halo_ptr: int) -> None:
+    _check(load().sllbm_halo_unpack(ctx, int(side), ctypes.c_void_p(halo_ptr)), "sllbm_halo_unpack", ctx)
 
 
 def sllbm_destroy(ctx) -> None:
@@ -382,6 +412,7 @@ class Config:
     mu_inf: float | None = None
     collide: bool = True
     kernel: int = 0  # 0 automatic, 1 generic tile kernel, 2 TMA-fed persistent kernel
+    slab: tuple | None = None  # (z_begin, z_cells): this part of a mesh decomposed along z
     L: tuple = (2 * np.pi, 2 * np.pi, 2 * np.pi)
 
 
@@ -415,7 +446,11 @@ class Sim:
         prm.collide = int(bool(cfg.collide))
         prm.kernel = int(cfg.kernel)
         with torch.cuda.device(self.device):
-            self.ctx = sllbm_create(mesh, cfg.p, prm, self.stream.cuda_stream)
+            if cfg.slab is None:
+                self.ctx = sllbm_create(mesh, cfg.p, prm, self.stream.cuda_stream)
+            else:
+                self.ctx = sllbm_create_slab(mesh, cfg.p, prm, int(cfg.slab[0]), int(cfg.slab[1]),
+                                             self.stream.cuda_stream)
         self.info = sllbm_get_info(self.ctx)
         nb = int(self.info.pop_bytes)
         self.buffers = [torch.empty(nb, dtype=torch.uint8, device=self.device) for _ in range(2)]

@@ -1,0 +1,99 @@
+"""z-decomposition on one GPU: slab contexts that exchange halos before every step
+(sllbm_halo_pack / sllbm_halo_unpack, several slabs of one process) must reproduce the
+undivided periodic mesh bit for bit: the same source values reach every node, with the same
+weights, in the same order.  Also the calls that refuse slab contexts."""
+import ctypes
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_2012_05537_gb300 import decomp as D
+from paper_2012_05537_gb300 import sllbm as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _full(cfg, n):
+    sim = S.Sim(dataclasses.replace(cfg, kernel=1), device="cuda:0")
+    sim.init_tgv()
+    init = sim.populations().cpu().numpy()
+    assert sim.step(n) == 0
+    out = sim.populations().cpu().numpy()
+    sim.close()
+    return init, out
+
+
+def _slabs(cfg, parts, n):
+    steppers = []
+    for r in range(parts):
+        sim = S.Sim(dataclasses.replace(cfg, slab=D.slab_bounds(cfg.cells[2], parts, r)), device="cuda:0")
+        sim.init_tgv()
+        assert sim.info.step_kernel == 1
+        steppers.append(D.SlabStepper(sim))
+
+    def interiors():
+        parts_ = []
+        for st in steppers:
+            g, zc, p = st.ghost, st.sim.cfg.slab[1], cfg.p
+            parts_.append(st.sim.populations().cpu().numpy()[:, :, g * p:(g + zc) * p])
+        return np.concatenate(parts_, axis=2)
+
+    init = interiors()
+    D.step_local(steppers, n)
+    out = interiors()
+    ghost = steppers[0].ghost
+    for st in steppers:
+        st.sim.close()
+    return init, out, ghost
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("p", [2, 3, 4])
+@pytest.mark.parametrize("parts", [1, 2, 3])
+def test_slabs_reproduce_the_whole_mesh_bit_for_bit(storage, p, parts):
+    cfg = S.Config(cells=(4, 3, 9), p=p, courant=2.0, storage=storage)
+    init_full, full = _full(cfg, 4)
+    init_slab, slab, ghost = _slabs(cfg, parts, 4)
+    assert ghost == 2
+    assert np.array_equal(init_slab, init_full)
+    assert np.all(np.isfinite(full))
+    assert np.array_equal(slab, full)
+
+
+def test_wider_halo_at_a_larger_courant_number():
+    # departures up to two cells: three ghost cells per side, slabs of three cells
+    cfg = S.Config(cells=(3, 3, 9), p=2, courant=4.0, storage="f64")
+    _, full = _full(cfg, 3)
+    _, slab, ghost = _slabs(cfg, 3, 3)
+    assert ghost == 3
+    assert np.array_equal(slab, full)
+
+
+def test_slab_refusals():
+    base = S.Config(cells=(4, 4, 8), p=4, courant=2.0, storage="f32")
+    with pytest.raises(S.SllbmError):  # thinner than its ghost width
+        S.Sim(dataclasses.replace(base, slab=(0, 1)), device="cuda:0")
+    with pytest.raises(S.SllbmError):  # outside the mesh
+        S.Sim(dataclasses.replace(base, slab=(8, 2)), device="cuda:0")
+    with pytest.raises(S.SllbmError):  # the TMA-fed kernel cannot tile a slab
+        S.Sim(dataclasses.replace(base, slab=(0, 4), kernel=2), device="cuda:0")
+    sim = S.Sim(dataclasses.replace(base, slab=(0, 4)), device="cuda:0")
+    sim.init_tgv()
+    lib = S.load()
+    d = [ctypes.c_double() for _ in range(3)]
+    assert lib.sllbm_diag(sim.ctx, *[ctypes.byref(x) for x in d]) == S.EINVAL
+    assert lib.sllbm_set_step_variant(sim.ctx, 0) == S.EINVAL
+    st = D.SlabStepper(sim)
+    assert lib.sllbm_halo_pack(sim.ctx, 2, ctypes.c_void_p(st.bufs["send_low"].data_ptr())) == S.EINVAL
+    assert lib.sllbm_halo_unpack(sim.ctx, 0, None) == S.EINVAL
+    state = sim.raw_state().clone()
+    out = sim.state_like()
+    dmu = sim.torch.zeros(1, dtype=sim.torch.float64, device=sim.device)
+    assert lib.sllbm_adjoint_step(sim.ctx, ctypes.c_void_p(state.data_ptr()), ctypes.c_void_p(state.data_ptr()),
+                                  ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(dmu.data_ptr())) == S.EINVAL
+    sim.close()
+    whole = S.Sim(base, device="cuda:0")
+    with pytest.raises(S.SllbmError):  # not a slab
+        S.sllbm_slab_info(whole.ctx)
+    whole.close()

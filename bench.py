@@ -409,6 +409,64 @@ def adjoint_block(S, torch, device, hbm, every=20, timed=20):
     return out
 
 
+def decomposed_block(S, torch, device, w, parts=2, steps=50):
+    """The workload's mesh as `parts` z-slabs on this one GPU, advanced with one halo
+    exchange per step (device copies between the slab contexts), against the undivided mesh
+    on the same generic kernel: step times, the exchange alone, the halo bytes moved per
+    step, and whether the slabs end bit for bit equal to the whole mesh."""
+    import dataclasses
+
+    from paper_2012_05537_gb300 import decomp as D
+
+    cfg = S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, Pr=w.Pr, gamma=w.gamma, courant=w.courant,
+                   storage="f32", kernel=1)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    whole = S.Sim(cfg, device=device)
+    whole.init_tgv()
+    whole.step(3)
+    torch.cuda.synchronize()
+    ev[0].record(whole.stream)
+    whole.step(steps)
+    ev[1].record(whole.stream)
+    torch.cuda.synchronize()
+    whole_ms = ev[0].elapsed_time(ev[1]) / steps
+    ref = whole.populations()
+    whole.close()
+    steppers = []
+    for r in range(parts):
+        sim = S.Sim(dataclasses.replace(cfg, slab=D.slab_bounds(w.cells[2], parts, r)), device=device)
+        sim.init_tgv()
+        steppers.append(D.SlabStepper(sim))
+    D.step_local(steppers, 3)
+    torch.cuda.synchronize()
+    ev[0].record(steppers[0].sim.stream)
+    D.step_local(steppers, steps)
+    ev[1].record(steppers[0].sim.stream)
+    torch.cuda.synchronize()
+    slab_ms = ev[0].elapsed_time(ev[1]) / steps
+    ev[0].record(steppers[0].sim.stream)
+    for _ in range(steps):
+        D.exchange_local(steppers)
+    ev[1].record(steppers[0].sim.stream)
+    torch.cuda.synchronize()
+    exch_ms = ev[0].elapsed_time(ev[1]) / steps
+    # (the exchange-only loop above leaves the state unchanged: compare after it)
+    g, p = steppers[0].ghost, w.p
+    inner = [st.sim.populations()[:, :, g * p:(g + st.sim.cfg.slab[1]) * p] for st in steppers]
+    equal = bool(torch.equal(torch.cat(inner, dim=2), ref))
+    halo = sum(4 * st.halo_bytes for st in steppers)  # pack + unpack, both sides
+    for st in steppers:
+        st.sim.close()
+    nodes = w.nodes
+    return {"workload": w.name, "parts": parts, "ghost_cells": g, "steps": steps,
+            "whole_mesh_ms_per_step": whole_ms, "slabs_ms_per_step": slab_ms,
+            "exchange_ms_per_step": exch_ms, "halo_copy_bytes_per_step": halo,
+            "slabs_value": nodes / (slab_ms / 1e3), "whole_value": nodes / (whole_ms / 1e3),
+            "bit_equal_to_whole_mesh": equal,
+            "note": "one GPU: the slab contexts exchange by device copies; across GPUs the same "
+                    "halos move through torch.distributed point-to-point"}
+
+
 def batch_block(S, torch, device, count, steps, streams=16, seed=0):
     """`count` Taylor-Green instances of uneven size, order and parameters (seeded mix:
     cells 8^3..24^3, p in {2,3,4}, Ma 0.3..1.25, Re 400..1600, Courant 1..8), FP32, `steps`
@@ -584,6 +642,8 @@ def run_mine(args, rank, world, local):
         variants["batched"] = batch_block(S, torch, f"cuda:{local}", 64, args.batch_steps)
     if not args.no_variants and rank == 0 and not args.no_adjoint:
         variants["adjoint"] = adjoint_block(S, torch, f"cuda:{local}", hbm)
+    if not args.no_variants and rank == 0 and storage == "f32":
+        variants["decomposed"] = decomposed_block(S, torch, f"cuda:{local}", w)
     if not args.no_variants and rank == 0 and args.mixed_steps > 0:
         variants["mixed"] = mixed_precision_block(S, torch, f"cuda:{local}", args.mixed_steps,
                                                   args.mixed_every, hbm)

@@ -94,7 +94,9 @@ class SlabStepper:
 
 def exchange_local(steppers) -> None:
     """The halo exchange of several slabs held by one process (a ring in z order), by device
-    copies on each slab's stream: every slab packs, then unpacks its neighbours' packs."""
+    copies on each slab's stream: every slab packs, then unpacks its neighbours' packed
+    buffers directly."""
+    from . import sllbm as S
     n = len(steppers)
     for st in steppers:
         st.pack()
@@ -102,10 +104,8 @@ def exchange_local(steppers) -> None:
         below, above = steppers[(k - 1) % n], steppers[(k + 1) % n]
         st.sim.stream.wait_stream(below.sim.stream)
         st.sim.stream.wait_stream(above.sim.stream)
-        with st.sim.torch.cuda.stream(st.sim.stream):
-            st.bufs["recv_low"].copy_(below.bufs["send_high"])
-            st.bufs["recv_high"].copy_(above.bufs["send_low"])
-        st.unpack()
+        S.sllbm_halo_unpack(st.sim.ctx, 0, below.bufs["send_high"].data_ptr())
+        S.sllbm_halo_unpack(st.sim.ctx, 1, above.bufs["send_low"].data_ptr())
     # a slab's next pack overwrites send buffers its neighbours copied from above
     for k, st in enumerate(steppers):
         st.sim.stream.wait_stream(steppers[(k - 1) % n].sim.stream)

@@ -54,7 +54,8 @@ struct StepSmem {
     using C2 = typename Pair2<C>::T;
     static constexpr size_t out_elems = size_t(2) * kQ * TS::TILE;
     static constexpr size_t out_bytes = (out_elems * sizeof(C) + 15) / 16 * 16;
-    static constexpr size_t warp_pairs = size_t(TS::TZ) * TS::BY * TS::BX;  // z-pass output planes
+    // z-pass output planes; rows padded to an odd number of pairs (see step_tile)
+    static constexpr size_t warp_pairs = size_t(TS::TZ) * TS::BY * (TS::BX | 1);
     static constexpr size_t warp_ints = TS::BX + TS::BY + TS::BZ;
     static constexpr size_t bytes = out_bytes + NW * warp_pairs * sizeof(C2) + NW * warp_ints * sizeof(int);
 };
@@ -531,6 +532,9 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const StepTables<C,
         // storage order [i][node][h]: the pair (f_i, g_i) of a node is two adjacent values
         const S* __restrict__ sp = src + 2LL * i * a.nn;
         const int sx = s[0], sxy = s[0] * s[1];
+        // rows of the per-warp buffer hold an odd number of pairs, so that the x pass's lanes
+        // (one row each) fall on different banks; planes are s[1] such rows
+        const int rs = sx | 1, ps = rs * s[1];
         // each pass reads the pair's weights and departure-cell bits of its direction from
         // the constant bank once, before its column loop
         ColumnPass<C, P> pz;
@@ -554,7 +558,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const StepTables<C,
             pz.template apply<TS::TZ, TS::BZ>(v, r);
 #pragma unroll
             for (int oz = 0; oz < TS::TZ; ++oz)
-                if (oz < te[2]) zb[oz * sxy + col] = r[oz];
+                if (oz < te[2]) zb[oz * ps + y * rs + x] = r[oz];
         }
         __syncwarp();
         // y pass in place: lane = column (x, z)
@@ -564,12 +568,12 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const StepTables<C,
         for (int col = lane; col < ncol; col += 32) {
             const int oz = col / sx;
             const int x = col - oz * sx;
-            C2* cp = zb + oz * sxy + x;
+            C2* cp = zb + oz * ps + x;
             C2 v[TS::BY];
 #pragma unroll
             for (int y = 0; y < TS::BY; ++y) {
                 if (y < s[1]) {
-                    v[y] = cp[y * sx];
+                    v[y] = cp[y * rs];
                 } else {
                     v[y].x = C(0);
                     v[y].y = C(0);
@@ -579,7 +583,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const StepTables<C,
             py.template apply<TS::TY, TS::BY>(v, r);
 #pragma unroll
             for (int oy = 0; oy < TS::TY; ++oy)
-                if (oy < te[1]) cp[oy * sx] = r[oy];
+                if (oy < te[1]) cp[oy * rs] = r[oy];
         }
         __syncwarp();
         // x pass: lane = row (y, z) of the tile; f_i to OUT[i], g_i to OUT[45 + i]
@@ -589,7 +593,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const StepTables<C,
             const int oz = row / TS::TY;
             const int oy = row - oz * TS::TY;
             if (oz >= te[2] || oy >= te[1]) continue;
-            const C2* rp = zb + oz * sxy + oy * sx;
+            const C2* rp = zb + oz * ps + oy * rs;
             C2 v[TS::BX];
 #pragma unroll
             for (int x = 0; x < TS::BX; ++x) {

@@ -36,11 +36,16 @@ struct TileShape {
     static constexpr int TX = CX * P, TY = CY * P, TZ = CZ * P;
     static constexpr int TILE = TX * TY * TZ;
     static constexpr int BX = (CX + 1) * P + 1, BY = (CY + 1) * P + 1, BZ = (CZ + 1) * P + 1;
-    // OUT holds the streamed value of node (row r = oz TY + oy, ox) at r TX + (ox + r / RG) % TX:
-    // rows RG apart start on the same bank, so each group of RG rows is rotated by one more
-    // place, and the x pass's stores (one row per lane) fall on distinct banks
-    static constexpr int RG = 32 / gcd_c(TX, 32);
-    __host__ __device__ static constexpr int slot(int r, int ox) { return r * TX + (ox + r / RG) % TX; }
+    // OUT holds the streamed value of node (row r = oz TY + oy, ox) at r TX + (ox + r / RG) % TX,
+    // RG = 32 / gcd(TX W, 32) for values of W 4-byte words: rows RG apart start on the same
+    // bank, so each group of RG rows is rotated by one more place, and the x pass's stores
+    // (one row per lane) fall on distinct banks
+    template <int W>
+    static constexpr int RG = 32 / gcd_c(TX * W, 32);
+    template <int W>
+    __host__ __device__ static constexpr int slot(int r, int ox) {
+        return r * TX + (ox + r / RG<W>) % TX;
+    }
 };
 
 // Pair of the arithmetic type (f_i, g_i).
@@ -615,7 +620,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const StepTables<C,
             px.template apply<TS::TX, TS::BX>(v, r);
             C* of = out + i * TS::TILE + row * TS::TX;  // (row = oz TY + oy)
             C* og = of + kQ * TS::TILE;
-            const int rot = (row / TS::RG) % TS::TX;
+            const int rot = (row / TS::template RG<int(sizeof(C) / 4)>) % TS::TX;
 #pragma unroll
             for (int ox = 0; ox < TS::TX; ++ox) {
                 if (ox < te[0]) {
@@ -643,7 +648,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const StepTables<C,
             if (ox >= te[0] || oy >= te[1] || oz >= te[2]) continue;  // both lanes of the pair
             const long long g = (static_cast<long long>(c0[2] * P + oz) * a.N[1] + (c0[1] * P + oy)) * a.N[0]
                               + (c0[0] * P + ox);
-            op.pair(out + TS::slot(r, ox), TS::TILE, a, t, g, k & 1, 3u << (lane & 30));
+            op.pair(out + TS::template slot<int(sizeof(C) / 4)>(r, ox), TS::TILE, a, t, g, k & 1, 3u << (lane & 30));
         }
     } else {
         for (int n = threadIdx.x; n < TS::TILE; n += NW * 32) {
@@ -654,7 +659,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const StepTables<C,
             if (ox >= te[0] || oy >= te[1] || oz >= te[2]) continue;
             const long long g = (static_cast<long long>(c0[2] * P + oz) * a.N[1] + (c0[1] * P + oy)) * a.N[0]
                               + (c0[0] * P + ox);
-            op(out + TS::slot(r, ox), TS::TILE, a, t, g);
+            op(out + TS::template slot<int(sizeof(C) / 4)>(r, ox), TS::TILE, a, t, g);
         }
     }
 }

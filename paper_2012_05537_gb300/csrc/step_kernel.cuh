@@ -664,13 +664,14 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const StepTables<C,
     }
 }
 
-// CTAs per SM the registers are sized for: two for 9-warp tiles (the p = 3 default, whose
-// shared memory fits twice and whose 45 velocity pairs split evenly, 5 per warp), one otherwise.
-template <int NW>
-constexpr int kStepMinCtas = NW == 9 ? 2 : 1;
+// CTAs per SM the registers are sized for: two for 9-warp tiles with FP32 arithmetic (the
+// p = 3 default, whose shared memory fits twice and whose 45 velocity pairs split evenly, 5
+// per warp), one otherwise.
+template <typename C, int NW>
+constexpr int kStepMinCtas = NW == 9 && sizeof(C) == 4 ? 2 : 1;
 
 template <typename S, typename C, int P, int CX, int CY, int CZ, int NW, bool PR>
-__global__ void __launch_bounds__(NW * 32, kStepMinCtas<NW>)
+__global__ void __launch_bounds__(NW * 32, kStepMinCtas<C, NW>)
     step_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ StepTables<C, P> t) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CollideOp<S, C, P, PR> op;

@@ -283,7 +283,8 @@ struct TransShape {
 template <typename C, int P, int CX, int CY, int CZ, int NW>
 struct TransSmem {
     using TS = TransShape<CX, CY, CZ, P>;
-    static constexpr size_t warp_pairs = size_t(TS::TZ) * TS::BY * TS::BX;
+    // rows padded to an odd number of pairs (see adj_transpose_kernel)
+    static constexpr size_t warp_pairs = size_t(TS::TZ) * TS::BY * (TS::BX | 1);
     static constexpr size_t warp_ints = TS::BX + TS::BY + TS::BZ;
     static constexpr size_t bytes = NW * warp_pairs * sizeof(typename Pair2<C>::T) + NW * warp_ints * sizeof(int);
 };
@@ -355,6 +356,9 @@ __global__ void __launch_bounds__(NW * 32)
         __syncwarp();
         const C* __restrict__ sp_i = src + 2LL * i * a.nn;
         const int sx = s[0], sxy = s[0] * s[1];
+        // rows of the per-warp buffer hold an odd number of pairs, so that the x pass's lanes
+        // (one row each) fall on different banks; planes are s[1] such rows
+        const int rs = sx | 1, ps = rs * s[1];
         C w[P][P + 1];
         signed char k[P];
         load_pass_weights<C, P>(t.lw[i][2], t.kc[i][2], w, k);
@@ -376,7 +380,7 @@ __global__ void __launch_bounds__(NW * 32)
             transpose_column<C, P, TS::TZ, TS::BZ>(v, w, k, sp[2], r);
 #pragma unroll
             for (int oz = 0; oz < TS::TZ; ++oz)
-                if (oz < te[2]) zb[oz * sxy + col] = r[oz];
+                if (oz < te[2]) zb[oz * ps + y * rs + x] = r[oz];
         }
         __syncwarp();
         load_pass_weights<C, P>(t.lw[i][1], t.kc[i][1], w, k);
@@ -384,12 +388,12 @@ __global__ void __launch_bounds__(NW * 32)
         for (int col = lane; col < ncol; col += 32) {
             const int oz = col / sx;
             const int x = col - oz * sx;
-            C2* cp = zb + oz * sxy + x;
+            C2* cp = zb + oz * ps + x;
             C2 v[TS::BY];
 #pragma unroll
             for (int y = 0; y < TS::BY; ++y) {
                 if (y < s[1]) {
-                    v[y] = cp[y * sx];
+                    v[y] = cp[y * rs];
                 } else {
                     v[y].x = C(0);
                     v[y].y = C(0);
@@ -399,7 +403,7 @@ __global__ void __launch_bounds__(NW * 32)
             transpose_column<C, P, TS::TY, TS::BY>(v, w, k, sp[1], r);
 #pragma unroll
             for (int oy = 0; oy < TS::TY; ++oy)
-                if (oy < te[1]) cp[oy * sx] = r[oy];
+                if (oy < te[1]) cp[oy * rs] = r[oy];
         }
         __syncwarp();
         load_pass_weights<C, P>(t.lw[i][0], t.kc[i][0], w, k);
@@ -407,7 +411,7 @@ __global__ void __launch_bounds__(NW * 32)
             const int oz = row / TS::TY;
             const int oy = row - oz * TS::TY;
             if (oz >= te[2] || oy >= te[1]) continue;
-            const C2* rp = zb + oz * sxy + oy * sx;
+            const C2* rp = zb + oz * ps + oy * rs;
             C2 v[TS::BX];
 #pragma unroll
             for (int x = 0; x < TS::BX; ++x) {

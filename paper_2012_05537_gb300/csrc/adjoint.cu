@@ -319,7 +319,7 @@ __device__ __forceinline__ void transpose_column(const typename Pair2<C>::T (&v)
 
 // dst = S^T src (both state-sized arrays of adjoint populations, pair layout), one tile per CTA.
 template <typename C, int P, int CX, int CY, int CZ, int NW>
-__global__ void __launch_bounds__(NW * 32)
+__global__ void __launch_bounds__(NW * 32, kStepMinCtas<C, NW>)
     adj_transpose_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ StepTables<C, P> t) {
     using TS = TransShape<CX, CY, CZ, P>;
     using SM = TransSmem<C, P, CX, CY, CZ, NW>;
@@ -651,7 +651,7 @@ int launch_transpose(sllbm_ctx* ctx, const void* src, void* dst) {
 template <typename C, int P>
 struct AdjTile;
 template <> struct AdjTile<float, 2> { static constexpr int CX = 4, CY = 4, CZ = 2, NW = 16; };
-template <> struct AdjTile<float, 3> { static constexpr int CX = 2, CY = 2, CZ = 2, NW = 16; };
+template <> struct AdjTile<float, 3> { static constexpr int CX = 4, CY = 2, CZ = 1, NW = 9; };  // two CTAs per SM
 template <> struct AdjTile<float, 4> { static constexpr int CX = 2, CY = 2, CZ = 1, NW = 16; };
 
 // The state streamed without collision (the step kernel's tile body, stream-only mode).

@@ -155,18 +155,31 @@ int sllbm_create(const sllbm_mesh *mesh, int p, sllbm_velset vs, const sllbm_par
  * highest ones for the slab above; sllbm_halo_unpack(side 0 / 1) writes a buffer received
  * from the slab below / above into the ghost cells below / above.  Halo buffers hold
  * halo_bytes (sllbm_slab_info) in the order [i][plane][y][x][h], device memory owned by
- * the caller; both calls are one asynchronous copy on the context's stream.
+ * the caller; both calls are one asynchronous copy on cuda_stream (a cudaStream_t as void*;
+ * NULL: the context's stream).
+ *
+ * To overlap the exchange with the step, split it: sllbm_step_begin launches the tiles
+ * whose source cells are all interior (they read no ghost cell; nothing is swapped yet),
+ * sllbm_step_end the remaining tiles next to the ghost cells, and then swaps the state as
+ * sllbm_step does (and, with the non-finite check on, synchronises and reports it as
+ * sllbm_step does).  Between the two the caller packs, exchanges and unpacks the halos of
+ * the current state on another stream (packing reads, and unpacking writes, nothing the
+ * interior tiles touch) and makes the context's stream wait for the unpacks before
+ * sllbm_step_end.  The result equals sllbm_step's bit for bit.
  * Errors: SLLBM_EINVAL for z_begin outside the mesh, z_cells < 1 or above the mesh, a
  * slab thinner than its ghost width (its halo would come from two neighbours), a TMA-fed
  * kernel request, and for slab contexts in sllbm_diag*, the reverse-mode calls, batches
- * and variant 0 of sllbm_set_step_variant; sllbm_halo_* and sllbm_slab_info on a context
- * that is not a slab, side not 0 or 1, a NULL buffer or a context without state:
- * SLLBM_EINVAL; a failed copy: SLLBM_ECUDA. */
+ * and variant 0 of sllbm_set_step_variant; sllbm_halo_*, sllbm_slab_info and
+ * sllbm_step_begin/_end on a context that is not a slab, side not 0 or 1, a NULL buffer or
+ * a context without state: SLLBM_EINVAL (sllbm_step_begin/_end before initialisation:
+ * SLLBM_ENOTREADY); a failed copy or launch: SLLBM_ECUDA. */
 int sllbm_create_slab(const sllbm_mesh *mesh, int p, sllbm_velset vs, const sllbm_params *prm,
                       int z_begin, int z_cells, void *cuda_stream, sllbm_ctx **out);
 int sllbm_slab_info(const sllbm_ctx *ctx, int *ghost_cells, size_t *halo_bytes);
-int sllbm_halo_pack(sllbm_ctx *ctx, int side, void *halo);
-int sllbm_halo_unpack(sllbm_ctx *ctx, int side, const void *halo);
+int sllbm_halo_pack(sllbm_ctx *ctx, int side, void *halo, void *cuda_stream);
+int sllbm_halo_unpack(sllbm_ctx *ctx, int side, const void *halo, void *cuda_stream);
+int sllbm_step_begin(sllbm_ctx *ctx);
+int sllbm_step_end(sllbm_ctx *ctx);
 
 /* Frees everything the context owns (not caller buffers). NULL is accepted. */
 void sllbm_destroy(sllbm_ctx *ctx);

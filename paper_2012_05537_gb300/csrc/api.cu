@@ -390,12 +390,17 @@ int launch_diag_cells_into(sllbm_ctx* ctx, const void* pop, double* partials, do
 
 namespace sllbm {
 
-int step_launch(sllbm_ctx* ctx) {
+// The step kernel(s) from buf[cur] into buf[1-cur], without the swap.
+int launch_current(sllbm_ctx* ctx) {
     const void* src = ctx->buf[ctx->cur];
     void* dst = ctx->buf[1 - ctx->cur];
-    int rc = ctx->prm.storage == SLLBM_F64   ? launch_step_f64(ctx, src, dst)
-             : ctx->prm.storage == SLLBM_F32 ? launch_step_f32(ctx, src, dst)
-                                             : launch_step_f16(ctx, src, dst);
+    return ctx->prm.storage == SLLBM_F64   ? launch_step_f64(ctx, src, dst)
+           : ctx->prm.storage == SLLBM_F32 ? launch_step_f32(ctx, src, dst)
+                                           : launch_step_f16(ctx, src, dst);
+}
+
+int step_launch(sllbm_ctx* ctx) {
+    const int rc = launch_current(ctx);
     if (rc != SLLBM_OK) return rc;
     ctx->cur = 1 - ctx->cur;
     return SLLBM_OK;
@@ -422,6 +427,7 @@ void fill_step_args(const sllbm_ctx* ctx, const void* src, void* dst, StepArgs* 
     a->flag = ctx->prm.nonfinite_check ? ctx->d_flag : nullptr;
     a->flag_err = ctx->d_flag + 1;
     a->z0 = ctx->ghost;
+    a->tz_begin = 0;
 }
 
 }  // namespace sllbm
@@ -597,7 +603,7 @@ int create_ctx(const sllbm_mesh* mesh, int p, sllbm_velset vs, const sllbm_param
 
 // The planes [plane0, plane0 + ghost p) of every velocity of the current state <-> a packed
 // halo buffer [i][plane][y][x][h]: one strided copy of 45 chunks.
-int halo_copy(sllbm_ctx* ctx, int side, void* halo, int to_state) {
+int halo_copy(sllbm_ctx* ctx, int side, void* halo, int to_state, cudaStream_t stream) {
     if (ctx == nullptr || !ctx->slab || halo == nullptr || (side != 0 && side != 1)) return SLLBM_EINVAL;
     if (ctx->buf[ctx->cur] == nullptr) return SLLBM_EINVAL;
     const int gp = ctx->ghost * ctx->p;
@@ -610,9 +616,9 @@ int halo_copy(sllbm_ctx* ctx, int side, void* halo, int to_state) {
     const size_t vstride = static_cast<size_t>(ctx->N[2]) * plane_bytes;
     unsigned char* state = static_cast<unsigned char*>(ctx->buf[ctx->cur]) + static_cast<size_t>(plane0) * plane_bytes;
     cudaError_t e = to_state ? cudaMemcpy2DAsync(state, vstride, halo, chunk, chunk, kQ, cudaMemcpyDeviceToDevice,
-                                                 ctx->stream)
+                                                 stream)
                              : cudaMemcpy2DAsync(halo, chunk, state, vstride, chunk, kQ, cudaMemcpyDeviceToDevice,
-                                                 ctx->stream);
+                                                 stream);
     CK(ctx, e);
     return SLLBM_OK;
 }
@@ -639,10 +645,46 @@ int sllbm_slab_info(const sllbm_ctx* ctx, int* ghost_cells, size_t* halo_bytes) 
     return SLLBM_OK;
 }
 
-int sllbm_halo_pack(sllbm_ctx* ctx, int side, void* halo) { return halo_copy(ctx, side, halo, 0); }
+int sllbm_halo_pack(sllbm_ctx* ctx, int side, void* halo, void* cuda_stream) {
+    if (ctx == nullptr) return SLLBM_EINVAL;
+    return halo_copy(ctx, side, halo, 0, cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream);
+}
 
-int sllbm_halo_unpack(sllbm_ctx* ctx, int side, const void* halo) {
-    return halo_copy(ctx, side, const_cast<void*>(halo), 1);
+int sllbm_halo_unpack(sllbm_ctx* ctx, int side, const void* halo, void* cuda_stream) {
+    if (ctx == nullptr) return SLLBM_EINVAL;
+    return halo_copy(ctx, side, const_cast<void*>(halo), 1,
+                     cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream);
+}
+
+int sllbm_step_begin(sllbm_ctx* ctx) {
+    if (ctx == nullptr || !ctx->slab) return SLLBM_EINVAL;
+    if (!ctx->initialised) return SLLBM_ENOTREADY;
+    if (ctx->prm.nonfinite_check) CK(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
+    ctx->region = 1;
+    const int rc = launch_current(ctx);
+    ctx->region = 0;
+    return rc;
+}
+
+int sllbm_step_end(sllbm_ctx* ctx) {
+    if (ctx == nullptr || !ctx->slab) return SLLBM_EINVAL;
+    if (!ctx->initialised) return SLLBM_ENOTREADY;
+    ctx->region = 2;
+    const int rc = launch_current(ctx);
+    ctx->region = 0;
+    if (rc != SLLBM_OK) return rc;
+    ctx->cur = 1 - ctx->cur;
+    if (ctx->prm.nonfinite_check) {
+        int flags[2] = {0, 0};
+        CK(ctx, cudaMemcpyAsync(flags, ctx->d_flag, sizeof(flags), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        if (flags[1]) {
+            CK(ctx, cudaMemsetAsync(ctx->d_flag + 1, 0, sizeof(int), ctx->stream));
+            return SLLBM_ETIMEOUT;
+        }
+        if (flags[0]) return SLLBM_ENONFINITE;
+    }
+    return SLLBM_OK;
 }
 
 void sllbm_destroy(sllbm_ctx* ctx) {

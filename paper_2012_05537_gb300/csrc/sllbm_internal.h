@@ -61,6 +61,7 @@ struct sllbm_ctx {
     int z_begin;
     int z_cells_global;
     int ghost;
+    int region;  // tiles a slab's step launches: 0 all, 1 those reading no ghost cell, 2 the others
 };
 
 namespace sllbm {
@@ -102,7 +103,50 @@ struct StepArgs {
     int* flag;          // non-finite flag or nullptr
     int* flag_err;      // set (bit 2) when a bounded device-side wait gave up
     int z0;             // first interior cell along z (a slab's ghost cells; 0 on a periodic mesh)
+    int tz_begin;       // first z-tile of this launch (a part of a slab's tiles; 0 otherwise)
 };
+
+// The z-tile ranges [r[k][0], r[k][1]) (k < return value) that a step launches for
+// ctx->region with tiles of CZ cells.  Tile t covers the interior cells [t CZ, t CZ + tcz);
+// its source boxes start at least max_shift cells below it and end with the first node of
+// the cell at most max_shift cells above its last cell, so it reads no ghost cell when
+// t CZ >= max_shift and t CZ + tcz + max_shift < cells.  Region 1: those tiles; region 2:
+// the tiles below and above them; region 0: all tiles.
+inline int slab_tile_ranges(const sllbm_ctx* c, int CZ, int r[2][2]) {
+    const int ntz = (c->cells[2] + CZ - 1) / CZ;
+    if (c->region == 0) {
+        r[0][0] = 0;
+        r[0][1] = ntz;
+        return 1;
+    }
+    const int ms = c->max_shift;
+    const int lo = (ms + CZ - 1) / CZ;
+    int hi = c->cells[2] - ms - 1 >= 0 ? (c->cells[2] - ms - 1) / CZ : 0;
+    if (hi > ntz) hi = ntz;
+    if (hi <= lo) {  // no tile avoids the ghost cells
+        if (c->region == 1) return 0;
+        r[0][0] = 0;
+        r[0][1] = ntz;
+        return 1;
+    }
+    if (c->region == 1) {
+        r[0][0] = lo;
+        r[0][1] = hi;
+        return 1;
+    }
+    int n = 0;
+    if (lo > 0) {
+        r[n][0] = 0;
+        r[n][1] = lo;
+        ++n;
+    }
+    if (hi < ntz) {
+        r[n][0] = hi;
+        r[n][1] = ntz;
+        ++n;
+    }
+    return n;
+}
 
 template <typename C, int P>
 void fill_step_tables(const sllbm_ctx* ctx, StepTables<C, P>* t) {

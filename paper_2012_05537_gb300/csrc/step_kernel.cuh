@@ -521,7 +521,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const StepTables<C,
     const int tix = tile % a.tiles[0];
     tile /= a.tiles[0];
     const int tiy = tile % a.tiles[1];
-    const int tiz = tile / a.tiles[1];
+    const int tiz = tile / a.tiles[1] + a.tz_begin;
     // (a slab's tiles cover its interior cells, which start a.z0 cells above its first plane)
     const int c0[3] = {tix * CX, tiy * CY, tiz * CZ + a.z0};
     const int tc[3] = {min(CX, a.cells[0] - c0[0]), min(CY, a.cells[1] - c0[1]),
@@ -744,27 +744,36 @@ int launch_step_tiled(sllbm_ctx* ctx, const void* src, void* dst) {
     args.tiles[0] = (ctx->cells[0] + CX - 1) / CX;
     args.tiles[1] = (ctx->cells[1] + CY - 1) / CY;
     args.tiles[2] = (ctx->cells[2] + CZ - 1) / CZ;
-    const long long ntiles = static_cast<long long>(args.tiles[0]) * args.tiles[1] * args.tiles[2];
-    if (ntiles > 0x7fffffffLL) return SLLBM_EINVAL;
+    if (static_cast<long long>(args.tiles[0]) * args.tiles[1] * args.tiles[2] > 0x7fffffffLL) return SLLBM_EINVAL;
+    // all z-tiles, or the part of a slab's tiles its split step asks for
+    int ranges[2][2];
+    const int nr = slab_tile_ranges(ctx, CZ, ranges);
     cudaError_t err = cudaSuccess;
-    if (ctx->prm.pr_correction) {
-        if constexpr (WITH_PR) {
-            auto k = step_kernel<S, C, P, CX, CY, CZ, NW, true>;
+    for (int q = 0; q < nr && err == cudaSuccess; ++q) {
+        args.tz_begin = ranges[q][0];
+        const long long ntiles =
+            static_cast<long long>(args.tiles[0]) * args.tiles[1] * (ranges[q][1] - ranges[q][0]);
+        if (ntiles <= 0) continue;
+        if (ctx->prm.pr_correction) {
+            if constexpr (WITH_PR) {
+                auto k = step_kernel<S, C, P, CX, CY, CZ, NW, true>;
+                err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(SM::bytes));
+                if (err == cudaSuccess) {
+                    k<<<static_cast<unsigned>(ntiles), NW * 32, SM::bytes, ctx->stream>>>(args, *tab);
+                    err = cudaGetLastError();
+                }
+            }
+        } else {
+            auto k = step_kernel<S, C, P, CX, CY, CZ, NW, false>;
             err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(SM::bytes));
             if (err == cudaSuccess) {
                 k<<<static_cast<unsigned>(ntiles), NW * 32, SM::bytes, ctx->stream>>>(args, *tab);
                 err = cudaGetLastError();
             }
         }
-    } else {
-        auto k = step_kernel<S, C, P, CX, CY, CZ, NW, false>;
-        err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(SM::bytes));
-        if (err == cudaSuccess) {
-            k<<<static_cast<unsigned>(ntiles), NW * 32, SM::bytes, ctx->stream>>>(args, *tab);
-            err = cudaGetLastError();
-        }
+        ctx->launches += 1;
     }
-    ctx->launches += 1;
     if (err != cudaSuccess) {
         ctx->last_err = static_cast<int>(err);
         return SLLBM_ECUDA;

@@ -61,15 +61,17 @@ class SlabStepper:
         self.bufs = {k: torch.empty(self.halo_bytes, dtype=torch.uint8, device=sim.device)
                      for k in ("send_low", "send_high", "recv_low", "recv_high")}
 
-    def pack(self) -> None:
+    def pack(self, stream=None) -> None:
         from . import sllbm as S
-        S.sllbm_halo_pack(self.sim.ctx, 0, self.bufs["send_low"].data_ptr())
-        S.sllbm_halo_pack(self.sim.ctx, 1, self.bufs["send_high"].data_ptr())
+        st = 0 if stream is None else stream.cuda_stream
+        S.sllbm_halo_pack(self.sim.ctx, 0, self.bufs["send_low"].data_ptr(), st)
+        S.sllbm_halo_pack(self.sim.ctx, 1, self.bufs["send_high"].data_ptr(), st)
 
-    def unpack(self) -> None:
+    def unpack(self, stream=None) -> None:
         from . import sllbm as S
-        S.sllbm_halo_unpack(self.sim.ctx, 0, self.bufs["recv_low"].data_ptr())
-        S.sllbm_halo_unpack(self.sim.ctx, 1, self.bufs["recv_high"].data_ptr())
+        st = 0 if stream is None else stream.cuda_stream
+        S.sllbm_halo_unpack(self.sim.ctx, 0, self.bufs["recv_low"].data_ptr(), st)
+        S.sllbm_halo_unpack(self.sim.ctx, 1, self.bufs["recv_high"].data_ptr(), st)
 
     def exchange(self) -> None:
         torch = self.sim.torch
@@ -90,6 +92,26 @@ class SlabStepper:
             rc = self.sim.step(1)
             if rc != 0:
                 raise RuntimeError(f"sllbm_step returned {rc}")
+
+    def step_overlapped(self, n: int = 1) -> None:
+        """n steps with the halo exchange on a second stream, overlapped with the tiles that
+        read no ghost cell (sllbm_step_begin); the tiles next to the ghost cells run once the
+        halos are in (sllbm_step_end).  Same result as step(), bit for bit."""
+        from . import sllbm as S
+        torch = self.sim.torch
+        if not hasattr(self, "comm"):
+            self.comm = torch.cuda.Stream(device=self.sim.device)
+        b = self.bufs
+        for _ in range(n):
+            self.comm.wait_stream(self.sim.stream)  # the current state is complete
+            S.sllbm_step_begin(self.sim.ctx)
+            self.pack(self.comm)
+            with torch.cuda.stream(self.comm):
+                exchange(b["send_low"], b["send_high"], b["recv_low"], b["recv_high"], self.rank, self.world,
+                         self.group)
+            self.unpack(self.comm)
+            self.sim.stream.wait_stream(self.comm)
+            S.sllbm_step_end(self.sim.ctx)
 
 
 def exchange_local(steppers) -> None:
@@ -120,3 +142,28 @@ def step_local(steppers, n: int = 1) -> None:
             rc = st.sim.step(1)
             if rc != 0:
                 raise RuntimeError(f"sllbm_step returned {rc}")
+
+
+def step_local_overlapped(steppers, n: int = 1, comm=None):
+    """As step_local, with the exchange on one extra stream `comm` overlapped with every
+    slab's interior tiles (sllbm_step_begin / sllbm_step_end).  Returns the stream used."""
+    from . import sllbm as S
+    torch = steppers[0].sim.torch
+    if comm is None:
+        comm = torch.cuda.Stream(device=steppers[0].sim.device)
+    k = len(steppers)
+    for _ in range(n):
+        for st in steppers:
+            comm.wait_stream(st.sim.stream)  # every current state is complete
+        for st in steppers:
+            S.sllbm_step_begin(st.sim.ctx)
+        for st in steppers:
+            st.pack(comm)
+        for j, st in enumerate(steppers):
+            below, above = steppers[(j - 1) % k], steppers[(j + 1) % k]
+            S.sllbm_halo_unpack(st.sim.ctx, 0, below.bufs["send_high"].data_ptr(), comm.cuda_stream)
+            S.sllbm_halo_unpack(st.sim.ctx, 1, above.bufs["send_low"].data_ptr(), comm.cuda_stream)
+        for st in steppers:
+            st.sim.stream.wait_stream(comm)
+            S.sllbm_step_end(st.sim.ctx)
+    return comm

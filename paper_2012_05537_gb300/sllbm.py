@@ -80,8 +80,10 @@ def load(build_if_missing: bool = False):
                                              ctypes.POINTER(Params), ctypes.c_int, ctypes.c_int, vp,
                                              ctypes.POINTER(vp)]),
         "sllbm_slab_info": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)]),
-        "sllbm_halo_pack": (ctypes.c_int, [vp, ctypes.c_int, vp]),
-        "sllbm_halo_unpack": (ctypes.c_int, [vp, ctypes.c_int, vp]),
+        "sllbm_halo_pack": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
+        "sllbm_halo_unpack": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
+        "sllbm_step_begin": (ctypes.c_int, [vp]),
+        "sllbm_step_end": (ctypes.c_int, [vp]),
         "sllbm_destroy": (None, [vp]),
         "sllbm_get_info": (ctypes.c_int, [vp, ctypes.POINTER(Info)]),
         "sllbm_velset_table": (ctypes.c_int, [vp, dp, dp]),
@@ -177,12 +179,22 @@ def sllbm_slab_info(ctx):
     return int(g.value), int(b.value)
 
 
-def sllbm_halo_pack(ctx, side: int, halo_ptr: int) -> None:
-    _check(load().sllbm_halo_pack(ctx, int(side), ctypes.c_void_p(halo_ptr)), "sllbm_halo_pack", ctx)
+def sllbm_halo_pack(ctx, side: int, halo_ptr: int, stream: int = 0) -> None:
+    _check(load().sllbm_halo_pack(ctx, int(side), ctypes.c_void_p(halo_ptr), ctypes.c_void_p(stream)),
+           "sllbm_halo_pack", ctx)
 
 
-def sllbm_halo_unpack(ctx, side: int, halo_ptr: int) -> None:
-    _check(load().sllbm_halo_unpack(ctx, int(side), ctypes.c_void_p(halo_ptr)), "sllbm_halo_unpack", ctx)
+def sllbm_halo_unpack(ctx, side: int, halo_ptr: int, stream: int = 0) -> None:
+    _check(load().sllbm_halo_unpack(ctx, int(side), ctypes.c_void_p(halo_ptr), ctypes.c_void_p(stream)),
+           "sllbm_halo_unpack", ctx)
+
+
+def sllbm_step_begin(ctx) -> None:
+    _check(load().sllbm_step_begin(ctx), "sllbm_step_begin", ctx)
+
+
+def sllbm_step_end(ctx) -> None:
+    _check(load().sllbm_step_end(ctx), "sllbm_step_end", ctx)
 
 
 def sllbm_destroy(ctx) -> None:

@@ -24,7 +24,7 @@ def _full(cfg, n):
     return init, out
 
 
-def _slabs(cfg, parts, n):
+def _slabs(cfg, parts, n, overlapped=False):
     steppers = []
     for r in range(parts):
         sim = S.Sim(dataclasses.replace(cfg, slab=D.slab_bounds(cfg.cells[2], parts, r)), device="cuda:0")
@@ -40,7 +40,10 @@ def _slabs(cfg, parts, n):
         return np.concatenate(parts_, axis=2)
 
     init = interiors()
-    D.step_local(steppers, n)
+    if overlapped:
+        D.step_local_overlapped(steppers, n)
+    else:
+        D.step_local(steppers, n)
     out = interiors()
     ghost = steppers[0].ghost
     for st in steppers:
@@ -58,6 +61,26 @@ def test_slabs_reproduce_the_whole_mesh_bit_for_bit(storage, p, parts):
     assert ghost == 2
     assert np.array_equal(init_slab, init_full)
     assert np.all(np.isfinite(full))
+    assert np.array_equal(slab, full)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("p", [3, 4])
+@pytest.mark.parametrize("parts", [1, 2, 3])
+def test_overlapped_exchange_reproduces_the_whole_mesh(storage, p, parts):
+    # the exchange on a second stream while the tiles that read no ghost cell run
+    cfg = S.Config(cells=(4, 3, 12), p=p, courant=2.0, storage=storage)
+    _, full = _full(cfg, 4)
+    _, slab, _ = _slabs(cfg, parts, 4, overlapped=True)
+    assert np.array_equal(slab, full)
+
+
+def test_overlapped_exchange_on_slabs_without_interior_tiles():
+    # two-cell slabs with two ghost cells: every tile reads a ghost cell (all in the second launch)
+    cfg = S.Config(cells=(3, 3, 6), p=3, courant=2.0, storage="f64")
+    _, full = _full(cfg, 3)
+    _, slab, ghost = _slabs(cfg, 3, 3, overlapped=True)
+    assert ghost == 2
     assert np.array_equal(slab, full)
 
 
@@ -85,8 +108,8 @@ def test_slab_refusals():
     assert lib.sllbm_diag(sim.ctx, *[ctypes.byref(x) for x in d]) == S.EINVAL
     assert lib.sllbm_set_step_variant(sim.ctx, 0) == S.EINVAL
     st = D.SlabStepper(sim)
-    assert lib.sllbm_halo_pack(sim.ctx, 2, ctypes.c_void_p(st.bufs["send_low"].data_ptr())) == S.EINVAL
-    assert lib.sllbm_halo_unpack(sim.ctx, 0, None) == S.EINVAL
+    assert lib.sllbm_halo_pack(sim.ctx, 2, ctypes.c_void_p(st.bufs["send_low"].data_ptr()), None) == S.EINVAL
+    assert lib.sllbm_halo_unpack(sim.ctx, 0, None, None) == S.EINVAL
     state = sim.raw_state().clone()
     out = sim.state_like()
     dmu = sim.torch.zeros(1, dtype=sim.torch.float64, device=sim.device)
@@ -96,4 +119,6 @@ def test_slab_refusals():
     whole = S.Sim(base, device="cuda:0")
     with pytest.raises(S.SllbmError):  # not a slab
         S.sllbm_slab_info(whole.ctx)
+    assert lib.sllbm_step_begin(whole.ctx) == S.EINVAL
+    assert lib.sllbm_step_end(whole.ctx) == S.EINVAL
     whole.close()

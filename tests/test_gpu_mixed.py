@@ -92,6 +92,37 @@ def test_one_step_matches_oracle_in_deviation_space(S, storage, p, cells, pr):
     assert np.all(np.abs(d_got - d_ref) <= bound), float(np.max(np.abs(d_got - d_ref) / bound))
 
 
+@pytest.mark.parametrize("storage", ["f16dev", "bf16dev"])
+def test_full_size_first_step_sampled(S, storage):
+    """The 192^3-node Ma 1.25 workload at 16-bit storage, in its benchmark launch
+    configuration: one step from the Taylor-Green state, compared in deviation space at
+    sampled nodes (the first and the last included) that the oracle evaluates one by one
+    from the exact FP64 state.  The GPU starts from that state rounded to 16 bits, so the
+    bound adds to the output rounding (RELBITS |d|) the input rounding carried through the
+    interpolation (Lebesgue constant <= 2) and the collision (3 RELBITS max|d|), and the FP32
+    arithmetic (1e-5 max|d|)."""
+    import torch as T
+    w = I.WORKLOADS["tgv_64c_p3_ma125"]
+    sim = make(S, w.cells, w.p, storage, courant=w.courant, Ma=w.Ma)
+    assert sim.info.step_kernel == 1
+    sim.init_tgv()
+    assert sim.step(1) == 0
+    g = grid_of(sim)
+    nodes = I.sample_nodes(sim.nodes, 48, seed=3)
+    ref = O.tgv_step_sample(g, nodes, sim.info.U0)  # [node][h * 45 + i], f and g
+    c = sim.cfg
+    _, wq = O.velset()
+    gfac = 2.0 / (c.gamma - 1.0) - 3.0
+    d_ref = np.concatenate([ref[:, :45] / wq - c.rho0, ref[:, 45:] / wq - gfac * c.T0 * c.rho0], axis=1)
+    raw = sim.raw_state().reshape(45, -1, 2)[:, T.as_tensor(nodes, device=sim.device), :]
+    d_got = raw.permute(1, 2, 0).reshape(len(nodes), 90).double().cpu().numpy()  # stored deviations
+    rb = RELBITS[storage]
+    dmax = np.abs(d_ref).max()
+    bound = rb * np.abs(d_ref) + 3 * rb * dmax + 1e-5 * dmax
+    assert np.all(np.abs(d_got - d_ref) <= bound), float(np.max(np.abs(d_got - d_ref) / bound))
+    sim.close()
+
+
 # Relative L2 of rho, u, T after the 24^3-node Taylor-Green run (8^3 cells, p = 3) against
 # the FP64 GPU path.  Measured on GB300: FP16 3.6e-5, 2.4e-4, 2.4e-5; BF16 2.8e-4, 1.8e-3,
 # 1.9e-4 (BF16 keeps 3 fewer mantissa bits: 8x the FP16 error, as measured).  Asserted with a

@@ -245,10 +245,11 @@ int sllbm_diag(sllbm_ctx *ctx, double *Ek, double *eps_s, double *eps_c);
  * pay for cudaMalloc/cudaFree (cudaFree synchronises the device).  The scratch is a
  * static device array inside the library holding one partial triple per cell: meshes
  * with more than 65536 cells get SLLBM_EINVAL.  Results equal sllbm_diag's up to the
- * order of the FP64 sums.  The first call on a device looks up the array's address
- * (cudaGetSymbolAddress) and should come before any stream capture.  Calls share the
- * array, so calls that overlap on the GPU (other streams or contexts) race.  Uses the
- * current device, which must be the context's.  Synchronous; host outputs. */
+ * order of the FP64 sums.  sllbm_create looks up the array's device address on the
+ * context's device (cudaGetSymbolAddress), so this call does no set-up of its own.  Calls
+ * share the array, so calls that overlap on the GPU (other streams or contexts) race.
+ * The current device must be the context's (SLLBM_EINVAL otherwise).  Synchronous; host
+ * outputs. */
 int sllbm_diag_noalloc(sllbm_ctx *ctx, double *Ek, double *eps_s, double *eps_c);
 
 /* End-to-end call with HOST buffers: copies pop_in (pop_bytes, storage type, host

@@ -5,7 +5,6 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
-#include <mutex>
 #include <new>
 
 #include "collide.cuh"
@@ -351,12 +350,12 @@ int launch_diag_p(sllbm_ctx* ctx, const void* pop, double* d_out) {
 // Scratch of sllbm_diag_noalloc: one partial triple per cell plus the three totals, in a
 // file-scope device array (every GPU that loads the library holds these 1.5 MB until exit).
 constexpr long long kNoAllocDiagMaxCells = 65536;
-constexpr int kNoAllocMaxDevices = 64;
 static __device__ __align__(256) double g_diag_scratch[3 * kNoAllocDiagMaxCells + 3];
 
-// Device address of g_diag_scratch per device ordinal, looked up once with that device current.
-std::mutex g_diag_scratch_mu;
-double* g_diag_scratch_addr[kNoAllocMaxDevices] = {};
+// (Host code cannot use g_diag_scratch's name as a device address: each context looks the
+// address up with cudaGetSymbolAddress when it is created, with its device current, and
+// keeps it in sllbm_ctx::diag_scratch.  A context created after a cudaDeviceReset, or in
+// another CUDA context, thus gets the address of the array as loaded there.)
 
 template <int P>
 int launch_diag_cells_into(sllbm_ctx* ctx, const void* pop, double* partials, double* d_out) {
@@ -586,6 +585,12 @@ int create_ctx(const sllbm_mesh* mesh, int p, sllbm_velset vs, const sllbm_param
         if (e == cudaSuccess) e = cudaMalloc(&c->d_flag, 2 * sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(c->d_flag, 0, 2 * sizeof(int));
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+        // the device address of sllbm_diag_noalloc's static scratch on this device
+        if (e == cudaSuccess) {
+            void* addr = nullptr;
+            e = cudaGetSymbolAddress(&addr, g_diag_scratch);
+            c->diag_scratch = static_cast<double*>(addr);
+        }
     }
     if (e != cudaSuccess) {
         int code = (e == cudaErrorMemoryAllocation) ? SLLBM_ENOMEM : SLLBM_ECUDA;
@@ -959,10 +964,10 @@ int sllbm_diag(sllbm_ctx* ctx, double* Ek, double* eps_s, double* eps_c) {
 // Same results as sllbm_diag (up to summation order) without allocating device memory:
 // for callers whose device memory is owned by another allocator or a fixed budget, or
 // whose loop must not pay for cudaMalloc/cudaFree (cudaFree synchronises the device).
-// The scratch is g_diag_scratch above; the first call on a device looks up its address
-// with cudaGetSymbolAddress (make that first call before any stream capture).  All calls
-// share the array and each overwrites every entry it reads, so nothing needs clearing,
-// but calls that overlap on the GPU (other streams, other contexts) race on it.
+// The scratch is g_diag_scratch above, at the device address the context looked up when it
+// was created (on its device, so nothing here touches the symbol).  All calls share the
+// array and each overwrites every entry it reads, so nothing needs clearing, but calls
+// that overlap on the GPU (other streams, other contexts) race on it.
 int sllbm_diag_noalloc(sllbm_ctx* ctx, double* Ek, double* eps_s, double* eps_c) {
     if (ctx == nullptr || Ek == nullptr || eps_s == nullptr || eps_c == nullptr || ctx->slab) return SLLBM_EINVAL;
     if (!ctx->initialised) return SLLBM_ENOTREADY;
@@ -970,18 +975,8 @@ int sllbm_diag_noalloc(sllbm_ctx* ctx, double* Ek, double* eps_s, double* eps_c)
     if (ncell > kNoAllocDiagMaxCells) return SLLBM_EINVAL;  // more cells than the static scratch holds
     int dev = 0;
     CK(ctx, cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kNoAllocMaxDevices) return SLLBM_EINVAL;
-    double* scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_diag_scratch_mu);
-        if (g_diag_scratch_addr[dev] == nullptr) {
-            void* addr = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&addr, g_diag_scratch);
-            if (e != cudaSuccess) return fail(ctx, e);
-            g_diag_scratch_addr[dev] = static_cast<double*>(addr);
-        }
-        scratch = g_diag_scratch_addr[dev];
-    }
+    if (dev != ctx->device || ctx->diag_scratch == nullptr) return SLLBM_EINVAL;  // not the context's device
+    double* scratch = ctx->diag_scratch;
     double* d_out = scratch + 3 * ncell;
     const void* pop = ctx->buf[ctx->cur];
     int rc = ctx->p == 2 ? launch_diag_cells_into<2>(ctx, pop, scratch, d_out)

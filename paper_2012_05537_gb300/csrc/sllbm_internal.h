@@ -34,6 +34,7 @@ struct sllbm_ctx {
     double* d_coords[3];   // node coordinates per direction (device)
     int* d_flag;           // non-finite flag (device)
     double* d_partials;    // diagnostics partial sums (device scratch)
+    double* diag_scratch;  // device address of sllbm_diag_noalloc's static array on `device`
     int partial_blocks;
     unsigned char* step_blob;  // StepTables<C,P> of the storage type, built on first step
     size_t step_blob_size;

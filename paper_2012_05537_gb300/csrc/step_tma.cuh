@@ -692,9 +692,18 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                 sent = issued + static_cast<uint32_t>(nb);
             }
         }
-        if (!ok) {
-            // drain: wait (bounded, whatever the abort flag says) for the fills of the items
-            // in flight
+        // Drain, on every exit: wait (bounded, whatever the abort flag says) until the fills
+        // of every item whose release is not confirmed have landed, so that the CTA never
+        // ends with a bulk-tensor or cp.async copy still writing its shared memory.  This
+        // matters when the consumers left early (abort) while this producer went on and
+        // issued its last items: those items have no consumer that waits for them.  In a
+        // normal run every such item was consumed, its fill phase has completed and each
+        // test passes at once.  The items tail .. sent-1 are the last uses of their
+        // descriptors (at most kItems of them), so one parity bit tells their phases apart.
+        // A fill lands in bounded time (a TMA or cp.async read of global memory); the 2 s
+        // limit is only reached if an item's byte count disagreed with its copies, in which
+        // case nothing is left in flight either.
+        {
             volatile int keep_waiting = 0;
             for (uint32_t x = tail; x != sent; ++x)
                 mbar_wait_bounded(pf0 + 8 * (x & KM), (x / kItems) & 1u, &keep_waiting, nullptr);

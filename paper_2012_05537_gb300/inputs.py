@@ -65,6 +65,12 @@ WORKLOADS = {
     # oracle-size companion of the throughput workload (curves)
     "tgv_16c_p4": Workload("tgv_16c_p4", (16, 16, 16), 4, 0.5, 1600.0, 4.0, 2000, "f64",
                            note="16^3 cells, p=4 (64^3 nodes)"),
+    # oracle-size companion of the throughput workload's long run: the same time step as
+    # tgv_32c_p4 (Courant 4 on 128^3 nodes is Courant 2 on 64^3), 2000 steps (t* = 60), with the
+    # Prandtl term the paper's Taylor-Green runs use (Pr 0.7, App. D)
+    "tgv_16c_p4_c2": Workload("tgv_16c_p4_c2", (16, 16, 16), 4, 0.5, 1600.0, 2.0, 2000, "f64",
+                              pr_correction=True,
+                              note="16^3 cells, p=4 (64^3 nodes), Ma 0.5, C=2, Pr term on, 2000 steps"),
     # shocklet case at higher Mach (mixed-precision comparison).  BGK at Ma 1.25 is not stable
     # at Courant 2 and above on this mesh (tau - 1/2 < 0.03 once shocklets form); Courant 1
     # matches the time step the paper uses for this Mach number (dt* = 0.009 at 256^3 points).

@@ -1,12 +1,18 @@
-"""Writes tgv_16c_p4_curves.txt next to this file: the Sec. III.C diagnostics E_k, eps_s and
-eps_c of the Taylor-Green run of workload tgv_16c_p4 (16^3 cells, p = 4, Ma 0.5, Re 1600,
-Courant number 4; the constant-temperature initial condition of Sec. III.C) at step 0 and
-every 20 steps up to 200, computed by the FP64 oracle alone (oracle.init_fields,
-oracle.tgv_fields, oracle.step, oracle.diag).  The time step and mu_inf come from the workload
-definition (inputs.Workload.dt, inputs.Workload.mu_inf); the GPU test passes the same values.
+"""Writes the Taylor-Green diagnostics files next to this file: the Sec. III.C quantities
+E_k, eps_s and eps_c of a Taylor-Green run (constant-temperature initial condition of
+Sec. III.C), computed by the FP64 oracle alone (oracle.init_fields, oracle.tgv_fields,
+oracle.step, oracle.diag).  The time step, mu_inf and the Prandtl-term flag come from the
+workload definition (inputs.Workload); the GPU tests pass the same values.
 
-    python tests/golden/make_tgv_curves.py        (about ten minutes on eight cores)
+* tgv_16c_p4_curves.txt: workload tgv_16c_p4 (16^3 cells, p = 4, Ma 0.5, Re 1600, Courant
+  number 4), step 0 and every 20 steps up to 200 (about ten minutes on eight cores);
+* tgv_16c_p4_c2_curves.txt: workload tgv_16c_p4_c2 (the same mesh at Courant number 2, the
+  time step of the 128^3-node throughput workload, Prandtl term on), step 0 and every 50
+  steps up to 2000 (about two hours on eight cores).  Rows are written as the run goes.
+
+    python tests/golden/make_tgv_curves.py [tgv_16c_p4 | tgv_16c_p4_c2]
 """
+import math
 import os
 import sys
 
@@ -17,26 +23,33 @@ sys.path.insert(0, ROOT)
 import oracle as O  # noqa: E402
 from paper_2012_05537_gb300 import inputs as I  # noqa: E402
 
-STEPS, EVERY = 200, 20
+RUNS = {"tgv_16c_p4": (200, 20), "tgv_16c_p4_c2": (2000, 50)}
 
 
-def main():
-    w = I.WORKLOADS["tgv_16c_p4"]
-    g = O.Grid(cells=w.cells, p=w.p, dt=w.dt(), mu_inf=w.mu_inf, gamma=w.gamma, Pr=w.Pr)
+def main(name: str = "tgv_16c_p4"):
+    steps, every = RUNS[name]
+    w = I.WORKLOADS[name]
+    g = O.Grid(cells=w.cells, p=w.p, dt=w.dt(), mu_inf=w.mu_inf, gamma=w.gamma, Pr=w.Pr,
+               pr_correction=w.pr_correction)
     pop = O.init_fields(g, *O.tgv_fields(g, w.U0))
-    rows = [(0, O.diag(g, pop, 1.0, w.Re, w.U0))]
-    for k in range(EVERY, STEPS + 1, EVERY):
-        pop = O.step(g, pop, EVERY)
-        rows.append((k, O.diag(g, pop, 1.0, w.Re, w.U0)))
-        print(k, rows[-1][1], flush=True)
-    with open(os.path.join(HERE, "tgv_16c_p4_curves.txt"), "w") as f:
+    with open(os.path.join(HERE, f"{name}_curves.txt"), "w") as f:
         f.write("# E_k, eps_s, eps_c (Sec. III.C, volume averages in units of U0) of the Taylor-Green run\n")
-        f.write(f"# tgv_16c_p4: 16^3 cells, p = 4, Ma {w.Ma}, Re {w.Re}, dt {w.dt()!r}, mu_inf {w.mu_inf!r};\n")
+        f.write(f"# {name}: {w.cells[0]}^3 cells, p = {w.p}, Ma {w.Ma}, Re {w.Re}, dt {w.dt()!r}, "
+                f"mu_inf {w.mu_inf!r}, Prandtl term {'on' if w.pr_correction else 'off'};\n")
         f.write("# written by tests/golden/make_tgv_curves.py from the FP64 oracle only\n")
         f.write("# step Ek eps_s eps_c\n")
-        for k, d in rows:
+        d = O.diag(g, pop, 1.0, w.Re, w.U0)
+        f.write(f"0 {d[0]:.17e} {d[1]:.17e} {d[2]:.17e}\n")
+        for k in range(every, steps + 1, every):
+            pop = O.step(g, pop, every)
+            d = O.diag(g, pop, 1.0, w.Re, w.U0)
+            if not all(math.isfinite(v) for v in d):
+                print(k, "non-finite: stopping", flush=True)
+                break
             f.write(f"{k} {d[0]:.17e} {d[1]:.17e} {d[2]:.17e}\n")
+            f.flush()
+            print(k, d, flush=True)
 
 
 if __name__ == "__main__":
-    main()
+    main(*sys.argv[1:2])

@@ -476,6 +476,47 @@ def test_p9_tgv_initial_integrals():
     assert errs[1][1] < errs[0][1]
 
 
+def _spectral_grad(f, L=2 * np.pi):
+    """Exact derivatives of a periodic trigonometric polynomial sampled on a uniform grid
+    (numpy FFT), axis order (z, y, x); returns [d/dx, d/dy, d/dz]."""
+    out = []
+    for ax in (2, 1, 0):
+        n = f.shape[ax]
+        k = np.fft.fftfreq(n, d=L / n) * 2 * np.pi
+        shp = [1, 1, 1]
+        shp[ax] = n
+        out.append(np.real(np.fft.ifft(1j * k.reshape(shp) * np.fft.fft(f, axis=ax), axis=ax)))
+    return out
+
+
+@pytest.mark.parametrize("Ma", [0.5, 1.25])
+def test_p9_tgv_density_is_the_incompressible_pressure(Ma):
+    """Sec. III.C initial condition (its density expression is garbled in the paper): at
+    uniform T0 the density perturbation must carry the pressure of the incompressible
+    Taylor-Green flow, p' = rho' T0 (P = rho T), which the incompressible equations fix by
+    the pressure Poisson relation  lap p' = -rho0 d_i u_j d_j u_i  (plus a zero mean).
+    A p = 1 mesh puts the oracle's nodes on a uniform grid, where spectral derivatives of
+    these band-limited fields are exact; a wrong amplitude (C/8), a missing "+2" or a
+    sign error in the density breaks the relation at O(1)."""
+    gam, T0, rho0 = 1.4, 1.0, 1.0
+    U0 = Ma * math.sqrt(gam * T0)
+    g = O.Grid(cells=(16, 16, 16), p=1, dt=0.1)
+    x = O.node_coords(g, 0)
+    assert np.allclose(np.diff(x), 2 * np.pi / 16, rtol=0, atol=1e-14)  # uniform nodes
+    rho, u, T = O.tgv_fields(g, U0, rho0=rho0, T0=T0)
+    assert np.all(T == T0)
+    pp = (rho - rho0) * T0
+    lap = sum(_spectral_grad(gd)[d] for d, gd in enumerate(_spectral_grad(pp)))
+    du = [_spectral_grad(u[c]) for c in range(3)]  # du[j][i] = d u_j / d x_i
+    rhs = -rho0 * sum(du[j][i] * du[i][j] for i in range(3) for j in range(3))
+    scale = np.max(np.abs(rhs))
+    assert scale > 0.1 * U0 * U0
+    assert np.max(np.abs(lap - rhs)) <= 1e-12 * scale
+    assert abs(pp.mean()) <= 1e-14
+    # and the incompressible velocity field is divergence free
+    assert np.max(np.abs(du[0][0] + du[1][1] + du[2][2])) <= 1e-12 * U0
+
+
 def test_sutherland_constants_match_paper():
     g = golden()
     for T in (0.5, 1.0, 1.7):

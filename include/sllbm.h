@@ -57,6 +57,8 @@ extern "C" {
 #define SLLBM_ENONFINITE (-4) /* non-finite or non-positive rho/T seen by the step check */
 #define SLLBM_ETIMEOUT (-5)   /* a bounded device-side wait gave up */
 #define SLLBM_ENOTREADY (-6)  /* population buffers not set or not initialised */
+#define SLLBM_EABORTED (-7)   /* a launch ended early on a host abort request (sllbm_request_abort) */
+#define SLLBM_EIO (-8)        /* a checkpoint file could not be opened, written or read */
 
 typedef struct sllbm_ctx sllbm_ctx; /* opaque */
 
@@ -224,8 +226,9 @@ int sllbm_get_populations(sllbm_ctx *ctx, double *pop, int on_device);
 int sllbm_step(sllbm_ctx *ctx, int n);
 
 /* Synchronises the stream and reports device-side trouble since the last call: returns
- * SLLBM_ETIMEOUT (and clears it) if a bounded wait inside a step kernel gave up, else
- * SLLBM_OK.  Kernels never spin without a limit; after such an error the state is garbage. */
+ * SLLBM_ETIMEOUT (and clears it) if a bounded wait inside a step kernel gave up,
+ * SLLBM_EABORTED (and clears it) if a launch stopped on an abort request, else SLLBM_OK.
+ * Kernels never spin without a limit; after such an error the state is garbage. */
 int sllbm_status(sllbm_ctx *ctx);
 
 /* Density, velocity and temperature of the current state, Eq. (moments), FP64:
@@ -391,6 +394,87 @@ int sllbm_ek_adjoint(sllbm_ctx *ctx, const void *state, void *lam);
  * any of the three may be NULL. */
 int sllbm_init_fields_adjoint(sllbm_ctx *ctx, const double *rho, const double *u, const double *T,
                               const void *lam, double *grad_rho, double *grad_u, double *grad_T);
+
+/* ---- run control, fault injection, checkpoints ------------------------------------------
+ * The paper describes none of these; they are the library's operational interface. */
+
+/* Limit of each bounded device-side wait of the TMA-fed persistent kernel, in seconds
+ * (default 2 s; 0 <= seconds <= 60, else SLLBM_EINVAL), for the following steps.  A wait
+ * that runs past it makes the launch leave early (the state it wrote is then incomplete)
+ * and sets the error that sllbm_status (or sllbm_step with nonfinite_check on) reports as
+ * SLLBM_ETIMEOUT; the context stays usable.  The kernel's final wait for its own copies in
+ * flight keeps the 2 s limit whatever is set here. */
+int sllbm_set_wait_limit(sllbm_ctx *ctx, double seconds);
+
+/* Sets (on != 0) or clears the context's abort request, a device word that the TMA-fed
+ * persistent kernel reads at every tile boundary: a launch that sees it set stops issuing
+ * work, lets its copies in flight land and returns, and sllbm_status then reports
+ * SLLBM_EABORTED (the state is incomplete).  The word is written on a side stream, so a
+ * request also reaches launches already queued or running on the context's stream; it
+ * stays set until cleared.  The generic and batched kernels run a fixed amount of work
+ * without waits and do not read it.  Synchronous with respect to the write only. */
+int sllbm_request_abort(sllbm_ctx *ctx, int on);
+
+/* Test hook, process-wide, host side: the next `after` device allocations made by the
+ * library succeed and the one after them fails as if the device were out of memory (the
+ * calling entry point returns SLLBM_ENOMEM or SLLBM_ECUDA as documented); the hook then
+ * disarms itself.  after = -1 disarms it.  Makes no CUDA call. */
+int sllbm_debug_fail_allocs(int after);
+
+/* Compensated moment sums (on != 0) for the following steps of a context with FP32
+ * arithmetic (SLLBM_F32 and the 16-bit deviation storages): rho, rho u and the energy sum
+ * of Eq. (moments), and the temperature's 2 rho E - rho |u|^2, are accumulated with
+ * error-free two-sum / two-product steps, so that each carries about one FP32 rounding
+ * instead of one per term.  Runs on the generic tile kernel's default tile (the TMA-fed
+ * kernel and the alternative tiles sum plainly; the kernel choice follows the flag).
+ * FP64 storage ignores it.  SLLBM_EINVAL if the context's parameters force the TMA-fed
+ * kernel. */
+int sllbm_set_compensated(sllbm_ctx *ctx, int on);
+
+/* Steps taken since the state was last set (initialisation, sllbm_set_populations,
+ * sllbm_load_state) or loaded from a checkpoint (the checkpoint's count). */
+int64_t sllbm_step_count(const sllbm_ctx *ctx);
+
+/* Checkpoint file: a 128-byte header then the current state buffer as stored (pop_bytes,
+ * storage type and order of a state buffer).  Header, host byte order: char magic[8] =
+ * "SLLBMCK1"; uint32 version = 1; int32 storage, p, velset, cells[3], pr_correction;
+ * double L[3], dt, mu_inf, rho0, T0; int64 steps; uint64 payload_bytes; 16 reserved
+ * bytes.  sllbm_checkpoint_info reads one without a context or GPU. */
+typedef struct {
+    int storage, p, velset;
+    int cells[3];
+    int pr_correction;
+    double L[3];
+    double dt, mu_inf, rho0, T0;
+    int64_t steps;
+    uint64_t payload_bytes;
+} sllbm_checkpoint_t;
+
+/* Writes the context's current state and its description to `path` (synchronous).
+ * Errors: SLLBM_EINVAL (NULL, slab context), SLLBM_ENOTREADY, SLLBM_ENOMEM (host copy),
+ * SLLBM_ECUDA, SLLBM_EIO. */
+int sllbm_save(sllbm_ctx *ctx, const char *path);
+
+/* Loads a checkpoint into the context's current buffer (allocating the buffers if none
+ * were set), restores mu_inf and the step count, and marks the context initialised
+ * (synchronous).  The file must describe the same storage, order, cells, domain lengths,
+ * time step and reference state rho0, T0 as the context, else SLLBM_EINVAL (as for a bad
+ * magic, version or size, or a truncated payload); SLLBM_EIO if it cannot be opened. */
+int sllbm_load(sllbm_ctx *ctx, const char *path);
+
+/* Host-only, needs no context or GPU: reads and checks a checkpoint's header and that its
+ * payload is complete.  SLLBM_EIO (cannot open), SLLBM_EINVAL (not a valid checkpoint). */
+int sllbm_checkpoint_info(const char *path, sllbm_checkpoint_t *out);
+
+/* ALU-peak microbenchmark (no counterpart in the paper; it supplies the measured ALU
+ * roofline of the step): times one launch of independent dependent FMA chains over every
+ * SM of the current device on the given stream (after one warm-up launch) and returns the
+ * rate in flop/s (an FMA counts 2).  kind: 0 FP32 fma.rn.f32, 1 packed FP32x2
+ * fma.rn.f32x2 (2 FMAs per instruction), 2 FP64 fma.rn.f64.  `iters` scales the work
+ * (each thread executes 128 iters FMA instructions).  *seconds (may be NULL) receives the
+ * timed launch's duration.  Synchronous; allocates nothing.  SLLBM_EINVAL for an unknown
+ * kind or iters < 1, SLLBM_ECUDA. */
+int sllbm_fma_peak(int kind, int iters, void *cuda_stream, double *flops_per_s, double *seconds);
 
 /* Last CUDA error code seen by the context (cudaError_t as int, 0 if none). */
 int sllbm_last_cuda_error(const sllbm_ctx *ctx);

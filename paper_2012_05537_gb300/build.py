@@ -19,7 +19,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libsllbm.so")
 
 SOURCES = ["tables.cpp", "api.cu", "step_tma.cu", "step_f32.cu", "step_f32_tiles.cu", "step_f64.cu", "step_f16.cu",
-           "adjoint.cu", "batch.cu", "batch_kernel.cu"]
+           "adjoint.cu", "batch.cu", "batch_kernel.cu", "peak.cu", "runtime.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

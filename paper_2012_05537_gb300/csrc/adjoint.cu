@@ -569,9 +569,9 @@ int ensure_adjoint_scratch(sllbm_ctx* ctx) {
     const long long ncell = static_cast<long long>(ctx->cells[0]) * ctx->cells[1] * ctx->cells[2];
     ctx->adj_blocks = static_cast<int>(ncell);
     ctx->adj_bytes = need;
-    cudaError_t e = cudaMalloc(&ctx->adj_buf[0], need);
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->adj_buf[1], need);
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_adj_partials, sizeof(double) * ctx->adj_blocks);
+    cudaError_t e = dev_alloc(&ctx->adj_buf[0], need);
+    if (e == cudaSuccess) e = dev_alloc(&ctx->adj_buf[1], need);
+    if (e == cudaSuccess) e = dev_alloc(&ctx->d_adj_partials, sizeof(double) * ctx->adj_blocks);
     if (e != cudaSuccess) {
         adjoint_release(ctx);
         ctx->last_err = static_cast<int>(e);

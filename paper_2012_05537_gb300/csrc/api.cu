@@ -275,6 +275,10 @@ __global__ void sum_partials_kernel(const double* __restrict__ partials, int nbl
     if (threadIdx.x < 3) out[threadIdx.x] = red[threadIdx.x][0];
 }
 
+}  // namespace
+
+namespace sllbm {
+
 // 1: generic tile kernel, 2: TMA-fed persistent kernel, 0: the requested kernel cannot run.
 int choose_step_kernel(const sllbm_ctx* c) {
     // a slab's tiles start above its ghost cells: the generic kernel only
@@ -284,19 +288,10 @@ int choose_step_kernel(const sllbm_ctx* c) {
     return tma_ok ? 2 : 1;
 }
 
-int ensure_buffers(sllbm_ctx* ctx) {
-    if (ctx->buf[0] != nullptr) return SLLBM_OK;
-    for (int b = 0; b < 2; ++b) {
-        cudaError_t e = cudaMalloc(&ctx->buf[b], ctx->pop_bytes);
-        if (e != cudaSuccess) {
-            ctx->last_err = static_cast<int>(e);
-            return SLLBM_ENOMEM;
-        }
-    }
-    ctx->own_buf = true;
-    ctx->cur = 0;
-    return SLLBM_OK;
-}
+}  // namespace sllbm
+
+namespace {
+
 
 int launch_init(sllbm_ctx* ctx, int mode, const double* rho, const double* u, const double* T) {
     int rc = ensure_buffers(ctx);
@@ -315,6 +310,7 @@ int launch_init(sllbm_ctx* ctx, int mode, const double* rho, const double* u, co
     ctx->launches += 1;
     CK(ctx, cudaGetLastError());
     ctx->initialised = true;
+    ctx->steps = 0;
     return SLLBM_OK;
 }
 
@@ -389,6 +385,20 @@ int launch_diag_cells_into(sllbm_ctx* ctx, const void* pop, double* partials, do
 
 namespace sllbm {
 
+int ensure_buffers(sllbm_ctx* ctx) {
+    if (ctx->buf[0] != nullptr) return SLLBM_OK;
+    for (int b = 0; b < 2; ++b) {
+        cudaError_t e = dev_alloc(&ctx->buf[b], ctx->pop_bytes);
+        if (e != cudaSuccess) {
+            ctx->last_err = static_cast<int>(e);
+            return SLLBM_ENOMEM;
+        }
+    }
+    ctx->own_buf = true;
+    ctx->cur = 0;
+    return SLLBM_OK;
+}
+
 // The step kernel(s) from buf[cur] into buf[1-cur], without the swap.
 int launch_current(sllbm_ctx* ctx) {
     const void* src = ctx->buf[ctx->cur];
@@ -402,6 +412,7 @@ int step_launch(sllbm_ctx* ctx) {
     const int rc = launch_current(ctx);
     if (rc != SLLBM_OK) return rc;
     ctx->cur = 1 - ctx->cur;
+    ++ctx->steps;
     return SLLBM_OK;
 }
 
@@ -425,6 +436,8 @@ void fill_step_args(const sllbm_ctx* ctx, const void* src, void* dst, StepArgs* 
     a->collide = ctx->prm.collide;
     a->flag = ctx->prm.nonfinite_check ? ctx->d_flag : nullptr;
     a->flag_err = ctx->d_flag + 1;
+    a->abort_req = ctx->d_flag + 2;
+    a->wait_ns = ctx->wait_ns;
     a->z0 = ctx->ghost;
     a->tz_begin = 0;
 }
@@ -559,10 +572,11 @@ int create_ctx(const sllbm_mesh* mesh, int p, sllbm_velset vs, const sllbm_param
     c->elem = prm->storage == SLLBM_F64 ? sizeof(double) : prm->storage == SLLBM_F32 ? sizeof(float) : 2;
     c->pop_bytes = static_cast<size_t>(2 * kQ) * static_cast<size_t>(nn) * c->elem;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->wait_ns = kDefaultWaitNs;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) {
         for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
-            e = cudaMalloc(&c->d_coords[d], sizeof(double) * c->N[d]);
+            e = dev_alloc(&c->d_coords[d], sizeof(double) * c->N[d]);
             if (e != cudaSuccess) break;
             double* x = static_cast<double*>(std::malloc(sizeof(double) * c->N[d]));
             if (x == nullptr) {
@@ -581,9 +595,11 @@ int create_ctx(const sllbm_mesh* mesh, int p, sllbm_velset vs, const sllbm_param
             e = cudaMemcpy(c->d_coords[d], x, sizeof(double) * c->N[d], cudaMemcpyHostToDevice);
             std::free(x);
         }
-        // d_flag[0]: non-finite rho/T seen; d_flag[1]: a bounded device wait gave up
-        if (e == cudaSuccess) e = cudaMalloc(&c->d_flag, 2 * sizeof(int));
-        if (e == cudaSuccess) e = cudaMemset(c->d_flag, 0, 2 * sizeof(int));
+        // d_flag[0]: non-finite rho/T seen; d_flag[1]: a bounded device wait gave up (2) or the
+        // kernel honoured an abort request (4); d_flag[2]: the abort request
+        if (e == cudaSuccess) e = dev_alloc(&c->d_flag, 3 * sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(c->d_flag, 0, 3 * sizeof(int));
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->ctl_stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
         // the device address of sllbm_diag_noalloc's static scratch on this device
         if (e == cudaSuccess) {
@@ -679,13 +695,14 @@ int sllbm_step_end(sllbm_ctx* ctx) {
     ctx->region = 0;
     if (rc != SLLBM_OK) return rc;
     ctx->cur = 1 - ctx->cur;
+    ++ctx->steps;
     if (ctx->prm.nonfinite_check) {
         int flags[2] = {0, 0};
         CK(ctx, cudaMemcpyAsync(flags, ctx->d_flag, sizeof(flags), cudaMemcpyDeviceToHost, ctx->stream));
         CK(ctx, cudaStreamSynchronize(ctx->stream));
         if (flags[1]) {
             CK(ctx, cudaMemsetAsync(ctx->d_flag + 1, 0, sizeof(int), ctx->stream));
-            return SLLBM_ETIMEOUT;
+            return (flags[1] & 2) ? SLLBM_ETIMEOUT : SLLBM_EABORTED;
         }
         if (flags[0]) return SLLBM_ENONFINITE;
     }
@@ -700,6 +717,7 @@ void sllbm_destroy(sllbm_ctx* ctx) {
     }
     for (int d = 0; d < 3; ++d) cudaFree(ctx->d_coords[d]);
     cudaFree(ctx->d_flag);
+    if (ctx->ctl_stream) cudaStreamDestroy(ctx->ctl_stream);
     cudaFree(ctx->d_partials);
     adjoint_release(ctx);
     for (int b = 0; b < 6; ++b) cudaFree(ctx->pipe_buf[b]);
@@ -768,7 +786,7 @@ int sllbm_init_fields(sllbm_ctx* ctx, const double* rho, const double* u, const 
     if (on_device) return launch_init(ctx, 1, rho, u, T);
     double* d = nullptr;
     const size_t nb = sizeof(double) * static_cast<size_t>(ctx->nn);
-    cudaError_t e = cudaMalloc(&d, 5 * nb);
+    cudaError_t e = dev_alloc(&d, 5 * nb);
     if (e != cudaSuccess) {
         ctx->last_err = static_cast<int>(e);
         return SLLBM_ENOMEM;
@@ -795,7 +813,7 @@ int sllbm_set_populations(sllbm_ctx* ctx, const double* pop, int on_device) {
     const double* src = pop;
     double* tmp = nullptr;
     if (!on_device) {
-        CK(ctx, cudaMalloc(&tmp, count * sizeof(double)));
+        CK(ctx, dev_alloc(&tmp, count * sizeof(double)));
         cudaError_t e = cudaMemcpyAsync(tmp, pop, count * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
         if (e != cudaSuccess) {
             cudaFree(tmp);
@@ -816,6 +834,7 @@ int sllbm_set_populations(sllbm_ctx* ctx, const double* pop, int on_device) {
     }
     if (e != cudaSuccess) return fail(ctx, e);
     ctx->initialised = true;
+    ctx->steps = 0;
     return SLLBM_OK;
 }
 
@@ -827,7 +846,7 @@ int sllbm_get_populations(sllbm_ctx* ctx, double* pop, int on_device) {
     double* dst = pop;
     double* tmp = nullptr;
     if (!on_device) {
-        CK(ctx, cudaMalloc(&tmp, count * sizeof(double)));
+        CK(ctx, dev_alloc(&tmp, count * sizeof(double)));
         dst = tmp;
     }
     with_storage(ctx, [&](auto tag) {
@@ -860,7 +879,7 @@ int sllbm_step(sllbm_ctx* ctx, int n) {
         CK(ctx, cudaStreamSynchronize(ctx->stream));
         if (flags[1]) {
             CK(ctx, cudaMemsetAsync(ctx->d_flag + 1, 0, sizeof(int), ctx->stream));
-            return SLLBM_ETIMEOUT;
+            return (flags[1] & 2) ? SLLBM_ETIMEOUT : SLLBM_EABORTED;
         }
         if (flags[0]) return SLLBM_ENONFINITE;
     }
@@ -874,6 +893,7 @@ int sllbm_load_state(sllbm_ctx* ctx, const void* state) {
     if (state != ctx->buf[ctx->cur])
         CK(ctx, cudaMemcpyAsync(ctx->buf[ctx->cur], state, ctx->pop_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
     ctx->initialised = true;
+    ctx->steps = 0;
     return SLLBM_OK;
 }
 
@@ -891,7 +911,7 @@ int sllbm_status(sllbm_ctx* ctx) {
     if (err) {
         CK(ctx, cudaMemsetAsync(ctx->d_flag + 1, 0, sizeof(int), ctx->stream));
         CK(ctx, cudaStreamSynchronize(ctx->stream));
-        return SLLBM_ETIMEOUT;
+        return (err & 2) ? SLLBM_ETIMEOUT : SLLBM_EABORTED;
     }
     return SLLBM_OK;
 }
@@ -903,7 +923,7 @@ int sllbm_moments(sllbm_ctx* ctx, double* rho, double* u, double* T, int on_devi
     double* d = nullptr;
     double *dr = rho, *du = u, *dT = T;
     if (!on_device) {
-        CK(ctx, cudaMalloc(&d, 5 * nb));
+        CK(ctx, dev_alloc(&d, 5 * nb));
         dr = d;
         du = d + ctx->nn;
         dT = d + 4 * ctx->nn;
@@ -936,7 +956,7 @@ int sllbm_diag(sllbm_ctx* ctx, double* Ek, double* eps_s, double* eps_c) {
         const long long ncell = static_cast<long long>(ctx->cells[0]) * ctx->cells[1] * ctx->cells[2];
         ctx->partial_blocks = static_cast<int>(ncell < 2048 ? ncell : 2048);
         // 3 partial sums per block, then the 3 totals
-        cudaError_t e = cudaMalloc(&ctx->d_partials, sizeof(double) * (3 * ctx->partial_blocks + 3));
+        cudaError_t e = dev_alloc(&ctx->d_partials, sizeof(double) * (3 * ctx->partial_blocks + 3));
         if (e != cudaSuccess) {
             ctx->d_partials = nullptr;
             ctx->last_err = static_cast<int>(e);
@@ -1001,6 +1021,7 @@ int sllbm_run_host(sllbm_ctx* ctx, const void* pop_in, void* pop_out, int n) {
     if (rc != SLLBM_OK) return rc;
     CK(ctx, cudaMemcpyAsync(ctx->buf[ctx->cur], pop_in, ctx->pop_bytes, cudaMemcpyHostToDevice, ctx->stream));
     ctx->initialised = true;
+    ctx->steps = 0;
     rc = sllbm_step(ctx, n);
     if (rc != SLLBM_OK) return rc;
     CK(ctx, cudaMemcpyAsync(pop_out, ctx->buf[ctx->cur], ctx->pop_bytes, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1020,7 +1041,7 @@ int sllbm_run_host_many(sllbm_ctx* ctx, const void* const* pop_in, void* const* 
         if (pop_in[k] == nullptr || pop_out[k] == nullptr) return SLLBM_EINVAL;
     if (ctx->pipe_buf[0] == nullptr) {
         for (int b = 0; b < 6; ++b) {
-            cudaError_t e = cudaMalloc(&ctx->pipe_buf[b], ctx->pop_bytes);
+            cudaError_t e = dev_alloc(&ctx->pipe_buf[b], ctx->pop_bytes);
             if (e != cudaSuccess) {
                 for (int j = 0; j < b; ++j) cudaFree(ctx->pipe_buf[j]);
                 for (int j = 0; j < 6; ++j) ctx->pipe_buf[j] = nullptr;
@@ -1120,6 +1141,8 @@ const char* sllbm_strerror(int code) {
     case SLLBM_ENONFINITE: return "non-finite or non-positive density/temperature";
     case SLLBM_ETIMEOUT: return "bounded device wait timed out";
     case SLLBM_ENOTREADY: return "populations not initialised";
+    case SLLBM_EABORTED: return "step abandoned on an abort request";
+    case SLLBM_EIO: return "file input/output failed";
     }
     return "unknown error";
 }

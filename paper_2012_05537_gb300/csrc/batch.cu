@@ -52,7 +52,7 @@ int set_variant(sllbm_ctx* ctx, int v) {
         return SLLBM_OK;
     }
     if (v == 2 || v == 3) {
-        if (ctx->prm.storage != SLLBM_F32 || ctx->prm.pr_correction) return SLLBM_EINVAL;
+        if (ctx->prm.storage != SLLBM_F32 || ctx->prm.pr_correction || ctx->compensated) return SLLBM_EINVAL;
         ctx->step_kernel = 1;
         ctx->tile_shape = v - 1;
         return SLLBM_OK;
@@ -97,8 +97,8 @@ int build_group(BatchGroup& g, const std::vector<sllbm_ctx*>& ctx, int num_sms) 
     }
     g.njobs = static_cast<int>(jobs.size());
     g.items = items;
-    cudaError_t e = cudaMalloc(&g.d_jobs, sizeof(BatchJob) * jobs.size());
-    if (e == cudaSuccess) e = cudaMalloc(&g.d_tabs, tabs.size());
+    cudaError_t e = dev_alloc(&g.d_jobs, sizeof(BatchJob) * jobs.size());
+    if (e == cudaSuccess) e = dev_alloc(&g.d_tabs, tabs.size());
     if (e == cudaSuccess) e = cudaMemcpy(g.d_jobs, jobs.data(), sizeof(BatchJob) * jobs.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g.d_tabs, tabs.data(), tabs.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -134,9 +134,10 @@ int sllbm_autotune(sllbm_ctx* ctx, int steps, int* variant, double* ms_per_step)
     if (ctx == nullptr || steps < 1) return SLLBM_EINVAL;
     if (!ctx->initialised) return SLLBM_ENOTREADY;
     const int cur0 = ctx->cur;
+    const long long steps0 = ctx->steps;
     const int v0 = current_variant(ctx);
     void* saved = nullptr;
-    cudaError_t e = cudaMalloc(&saved, ctx->pop_bytes);
+    cudaError_t e = dev_alloc(&saved, ctx->pop_bytes);
     if (e != cudaSuccess) {
         ctx->last_err = static_cast<int>(e);
         return SLLBM_ENOMEM;
@@ -177,6 +178,7 @@ int sllbm_autotune(sllbm_ctx* ctx, int steps, int* variant, double* ms_per_step)
     }
     // the state as it was, in the buffer it was in
     ctx->cur = cur0;
+    ctx->steps = steps0;
     cudaError_t e2 = cudaMemcpyAsync(ctx->buf[cur0], saved, ctx->pop_bytes, cudaMemcpyDeviceToDevice, ctx->stream);
     if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(ctx->stream);
     if (e2 != cudaSuccess && rc == SLLBM_OK) rc = cuda_fail(ctx, e2);
@@ -373,7 +375,8 @@ int sllbm_batch_create_persistent(sllbm_ctx* const* ctxs, int n, void* cuda_stre
         // (a slab needs its halo exchanged between steps: not inside a batch)
         if (c == nullptr || !c->initialised || c->prm.nonfinite_check || c->device != dev || c->slab)
             return SLLBM_EINVAL;
-        if (c->prm.storage != SLLBM_F32 || c->prm.pr_correction || !c->prm.collide) return SLLBM_EINVAL;
+        if (c->prm.storage != SLLBM_F32 || c->prm.pr_correction || !c->prm.collide || c->compensated)
+            return SLLBM_EINVAL;
         for (int j = 0; j < k; ++j)
             if (ctxs[j] == c) return SLLBM_EINVAL;
     }
@@ -420,7 +423,7 @@ int sllbm_batch_create_persistent(sllbm_ctx* const* ctxs, int n, void* cuda_stre
         const int steps = tune_steps + (tune_steps & 1);
         std::vector<void*> saved(n, nullptr);
         for (int k = 0; k < n && rc == SLLBM_OK; ++k) {
-            e = cudaMalloc(&saved[k], ctxs[k]->pop_bytes);
+            e = dev_alloc(&saved[k], ctxs[k]->pop_bytes);
             if (e == cudaSuccess)
                 e = cudaMemcpy(saved[k], ctxs[k]->buf[ctxs[k]->cur], ctxs[k]->pop_bytes, cudaMemcpyDeviceToDevice);
             if (e != cudaSuccess) rc = e == cudaErrorMemoryAllocation ? SLLBM_ENOMEM : SLLBM_ECUDA;

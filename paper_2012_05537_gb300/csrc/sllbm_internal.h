@@ -32,7 +32,10 @@ struct sllbm_ctx {
     size_t elem;           // bytes per stored population value
     size_t pop_bytes;
     double* d_coords[3];   // node coordinates per direction (device)
-    int* d_flag;           // non-finite flag (device)
+    int* d_flag;           // [0] non-finite flag, [1] wait gave up (2) / abort honoured (4), [2] abort request
+    cudaStream_t ctl_stream;   // side stream of sllbm_request_abort
+    unsigned long long wait_ns;  // limit of the TMA-fed kernel's consumer waits
+    long long steps;       // steps taken since initialisation (or the loaded checkpoint's count)
     double* d_partials;    // diagnostics partial sums (device scratch)
     double* diag_scratch;  // device address of sllbm_diag_noalloc's static array on `device`
     int partial_blocks;
@@ -41,6 +44,7 @@ struct sllbm_ctx {
     int num_sms;
     int step_kernel;           // 1: generic tile kernel, 2: TMA-fed persistent kernel
     int tile_shape;            // generic FP32 kernel: 0 default tile, 1 and 2 the alternatives
+    int compensated;           // FP32 arithmetic: compensated moment sums (sllbm_set_compensated)
     alignas(64) unsigned char tmap[2][8][128];  // TMA descriptors (CUtensorMap) per source buffer and box shape
     const void* tmap_src[2];
     int last_err;
@@ -66,6 +70,23 @@ struct sllbm_ctx {
 };
 
 namespace sllbm {
+
+// Device allocation of the library (runtime.cu): cudaMalloc, unless sllbm_debug_fail_allocs
+// armed a failure for this allocation.
+cudaError_t dev_alloc_raw(void** p, size_t bytes);
+template <typename T>
+cudaError_t dev_alloc(T** p, size_t bytes) {
+    return dev_alloc_raw(reinterpret_cast<void**>(p), bytes);
+}
+
+// The context's two state buffers, allocated on first use unless the caller gave them (api.cu).
+int ensure_buffers(sllbm_ctx* ctx);
+
+// Step kernel for the context's parameters: 1 generic, 2 TMA-fed, 0 the requested one cannot run (api.cu).
+int choose_step_kernel(const sllbm_ctx* c);
+
+// Default limit of a bounded device-side wait.
+constexpr unsigned long long kDefaultWaitNs = 2000000000ull;
 
 // Constant tables of the fused step, passed to the kernel by value (constant bank).
 // kc[i][d][a] is the departure cell shift minus kmin[i][d] (0 or 1): the source box of a
@@ -102,7 +123,9 @@ struct StepArgs {
     double rho0, T0;    // reference state of 16-bit deviation storage
     int collide;        // 0: stream only
     int* flag;          // non-finite flag or nullptr
-    int* flag_err;      // set (bit 2) when a bounded device-side wait gave up
+    int* flag_err;      // set (bit 2) when a bounded device-side wait gave up, (bit 4) on an honoured abort
+    const int* abort_req;  // host-written abort request word (device memory) or nullptr
+    unsigned long long wait_ns;  // limit of the consumers' bounded waits
     int z0;             // first interior cell along z (a slab's ghost cells; 0 on a periodic mesh)
     int tz_begin;       // first z-tile of this launch (a part of a slab's tiles; 0 otherwise)
 };

@@ -218,6 +218,37 @@ __device__ __forceinline__ int wrap_index(int v, int n) {
     return r < 0 ? r + n : r;
 }
 
+// Rounded arithmetic that the compiler may neither contract into an FMA nor reorder (the
+// error-free transformations below rely on every operation being rounded on its own).
+__device__ __forceinline__ float add_rn(float x, float y) { return __fadd_rn(x, y); }
+__device__ __forceinline__ float sub_rn(float x, float y) { return __fsub_rn(x, y); }
+__device__ __forceinline__ float mul_rn(float x, float y) { return __fmul_rn(x, y); }
+__device__ __forceinline__ double add_rn(double x, double y) { return __dadd_rn(x, y); }
+__device__ __forceinline__ double sub_rn(double x, double y) { return __dsub_rn(x, y); }
+__device__ __forceinline__ double mul_rn(double x, double y) { return __dmul_rn(x, y); }
+
+// Compensated summation: s holds the rounded running sum and c the exact rounding errors of
+// its additions (Knuth's branch-free two-sum: t = s + x, z = t - s, error (s - (t - z)) +
+// (x - z)), so that s + c carries the sum to about one rounding of the result whatever the
+// number of terms.  Products enter with the rounding error of the product itself recovered
+// by an FMA (two-product), so a sum of products is compensated as well.
+template <typename C>
+struct CompSum {
+    C s = C(0), c = C(0);
+    __device__ __forceinline__ void add(C x) {
+        const C t = add_rn(s, x);
+        const C z = sub_rn(t, s);
+        c = add_rn(c, add_rn(sub_rn(s, sub_rn(t, z)), sub_rn(x, z)));
+        s = t;
+    }
+    __device__ __forceinline__ void add_prod(C x, C y) {
+        const C p = mul_rn(x, y);
+        add(p);
+        c = add_rn(c, fma(x, y, -p));  // the product's own rounding error, exactly
+    }
+    __device__ __forceinline__ C value() const { return add_rn(s, c); }
+};
+
 // Moments, equilibrium and collision of one node in 16-bit deviation storage: h[q*stride]
 // holds the streamed deviations d_i = f_i/w_i - rho0 (q < 45) and d_gi = g_i/w_i - (2C_v-D)T0
 // rho0 (q >= 45).  rho - rho0, rho u and 2 C_v rho (T - T0) come from deviation sums with the
@@ -226,28 +257,60 @@ __device__ __forceinline__ int wrap_index(int v, int n) {
 //   d_i'  = d_i  + omega (rho (P_i - 1) + (rho - rho0) - d_i),
 //   d_gi' = d_gi + omega ((2C_v-D) (T rho (P_i - 1) + (T - T0) rho + T0 (rho - rho0)) - d_gi),
 // with f_i^eq = w_i rho P_i (Eq. discreteEquilibrium, P_i the quartic in xi_i.u).
-template <typename S, typename C, int P, bool PR, class LT>
+template <typename S, typename C, int P, bool PR, class LT, bool KC = false>
 __device__ __forceinline__ void collide_node_dev(const C* __restrict__ h, int stride, const StepArgs& a,
                                                  const LT& t, S* __restrict__ dst) {
     C drho = 0, mx = 0, my = 0, mz = 0, se = 0;
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-        const C w = t.w[i];
-        const C wd = w * h[i * stride];
-        drho += wd;
-        mx += wd * t.xi[i][0];
-        my += wd * t.xi[i][1];
-        mz += wd * t.xi[i][2];
-        se += wd * C(shell_xi2(shell_of(i))) + w * h[(kQ + i) * stride];
-    }
     const C rho0 = C(a.rho0), T0 = C(a.T0);
-    const C rho = rho0 + drho;
-    const C inv_rho = C(1) / rho;
-    const C ux = mx * inv_rho, uy = my * inv_rho, uz = mz * inv_rho;
-    const C usq = ux * ux + uy * uy + uz * uz;
     const C two_cv = C(1.0 / a.inv_2cv);
-    // 2 C_v rho (T - T0) = sum w (|xi|^2 d + d_g) + D rho0 (1 - T0) - rho |u|^2 - 2 C_v T0 (rho - rho0)
-    const C dT = (se + C(3) * rho0 * (C(1) - T0) - rho * usq - two_cv * T0 * drho) * inv_rho / two_cv;
+    C rho, inv_rho, ux, uy, uz, usq, dT;
+    if constexpr (KC) {
+        // compensated sums of the deviation moments, and of the energy balance below
+        CompSum<C> r, qx, qy, qz, e;
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) {
+            const C w = t.w[i];
+            const C d = h[i * stride];
+            r.add_prod(w, d);
+            qx.add_prod(w * t.xi[i][0], d);
+            qy.add_prod(w * t.xi[i][1], d);
+            qz.add_prod(w * t.xi[i][2], d);
+            e.add_prod(w * C(shell_xi2(shell_of(i))), d);
+            e.add_prod(w, h[(kQ + i) * stride]);
+        }
+        drho = r.value();
+        mx = qx.value();
+        my = qy.value();
+        mz = qz.value();
+        rho = rho0 + drho;
+        inv_rho = C(1) / rho;
+        ux = mx * inv_rho, uy = my * inv_rho, uz = mz * inv_rho;
+        usq = ux * ux + uy * uy + uz * uz;
+        // 2 C_v rho (T - T0) with rho |u|^2 = m . u and every term compensated
+        e.add(C(3) * rho0 * (C(1) - T0));
+        e.add_prod(-mx, ux);
+        e.add_prod(-my, uy);
+        e.add_prod(-mz, uz);
+        e.add_prod(-two_cv * T0, drho);
+        dT = e.value() * inv_rho / two_cv;
+    } else {
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) {
+            const C w = t.w[i];
+            const C wd = w * h[i * stride];
+            drho += wd;
+            mx += wd * t.xi[i][0];
+            my += wd * t.xi[i][1];
+            mz += wd * t.xi[i][2];
+            se += wd * C(shell_xi2(shell_of(i))) + w * h[(kQ + i) * stride];
+        }
+        rho = rho0 + drho;
+        inv_rho = C(1) / rho;
+        ux = mx * inv_rho, uy = my * inv_rho, uz = mz * inv_rho;
+        usq = ux * ux + uy * uy + uz * uz;
+        // 2 C_v rho (T - T0) = sum w (|xi|^2 d + d_g) + D rho0 (1 - T0) - rho |u|^2 - 2 C_v T0 (rho - rho0)
+        dT = (se + C(3) * rho0 * (C(1) - T0) - rho * usq - two_cv * T0 * drho) * inv_rho / two_cv;
+    }
     const C T = T0 + dT;
     if (a.flag != nullptr && !(rho > C(0) && T > C(0) && isfinite(rho) && isfinite(T))) atomicOr(a.flag, 1);
     const long long nn = a.nn;
@@ -308,11 +371,11 @@ __device__ __forceinline__ void collide_node_dev(const C* __restrict__ h, int st
 // Moments, equilibrium and collision of one node whose streamed populations are
 // h[q*stride], q = 0..89 (f then g); the result f_i, g_i goes to dst[2*i*nn + {0,1}].  The
 // velocity set comes from t.xi, t.w (a StepTables or a Lattice).
-template <typename S, typename C, int P, bool PR, class LT>
+template <typename S, typename C, int P, bool PR, class LT, bool KC = false>
 __device__ __forceinline__ void collide_node(const C* __restrict__ h, int stride, const StepArgs& a,
                                              const LT& t, S* __restrict__ dst) {
     if constexpr (PopCodec<S>::kDev) {
-        collide_node_dev<S, C, P, PR>(h, stride, a, t, dst);
+        collide_node_dev<S, C, P, PR, LT, KC>(h, stride, a, t, dst);
         return;
     }
     const long long nn = a.nn;
@@ -322,19 +385,46 @@ __device__ __forceinline__ void collide_node(const C* __restrict__ h, int stride
         return;
     }
     C rho = 0, mx = 0, my = 0, mz = 0, e2 = 0;
+    C inv_rho, ux, uy, uz, usq, T;
+    if constexpr (KC) {
+        // compensated moment sums, and 2 rho E - rho |u|^2 = 2 rho E - m . u compensated
+        CompSum<C> r, qx, qy, qz, e;
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-        const C f = h[i * stride];
-        rho += f;
-        mx += f * t.xi[i][0];
-        my += f * t.xi[i][1];
-        mz += f * t.xi[i][2];
-        e2 += f * C(shell_xi2(shell_of(i))) + h[(kQ + i) * stride];
+        for (int i = 0; i < kQ; ++i) {
+            const C f = h[i * stride];
+            r.add(f);
+            qx.add_prod(f, t.xi[i][0]);
+            qy.add_prod(f, t.xi[i][1]);
+            qz.add_prod(f, t.xi[i][2]);
+            e.add_prod(f, C(shell_xi2(shell_of(i))));
+            e.add(h[(kQ + i) * stride]);
+        }
+        rho = r.value();
+        mx = qx.value();
+        my = qy.value();
+        mz = qz.value();
+        inv_rho = C(1) / rho;
+        ux = mx * inv_rho, uy = my * inv_rho, uz = mz * inv_rho;
+        usq = ux * ux + uy * uy + uz * uz;
+        e.add_prod(-mx, ux);
+        e.add_prod(-my, uy);
+        e.add_prod(-mz, uz);
+        T = e.value() * inv_rho * C(a.inv_2cv);
+    } else {
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) {
+            const C f = h[i * stride];
+            rho += f;
+            mx += f * t.xi[i][0];
+            my += f * t.xi[i][1];
+            mz += f * t.xi[i][2];
+            e2 += f * C(shell_xi2(shell_of(i))) + h[(kQ + i) * stride];
+        }
+        inv_rho = C(1) / rho;
+        ux = mx * inv_rho, uy = my * inv_rho, uz = mz * inv_rho;
+        usq = ux * ux + uy * uy + uz * uz;
+        T = (e2 * inv_rho - usq) * C(a.inv_2cv);
     }
-    const C inv_rho = C(1) / rho;
-    const C ux = mx * inv_rho, uy = my * inv_rho, uz = mz * inv_rho;
-    const C usq = ux * ux + uy * uy + uz * uz;
-    const C T = (e2 * inv_rho - usq) * C(a.inv_2cv);
     if (a.flag != nullptr && !(rho > C(0) && T > C(0) && isfinite(rho) && isfinite(T)))
         atomicOr(a.flag, 1);
     // tau = mu/(P dt) + 1/2, P = rho T, mu = Sutherland(T) mu_inf  (Sec. II.A, III.C)
@@ -468,12 +558,12 @@ __device__ __forceinline__ void collide_node_pair(const C* __restrict__ h, int s
 // Per-node phase of the step: moments, equilibrium, collision, store (Eq. LBM).  Two lanes
 // per node (kPair) are possible where the storage holds the populations themselves and the
 // Prandtl term is off; step_tile uses them on tiles much smaller than the CTA.
-template <typename S, typename C, int P, bool PR>
+template <typename S, typename C, int P, bool PR, bool KC = false>
 struct CollideOp {
-    static constexpr bool kPair = !PR && !PopCodec<S>::kDev;
+    static constexpr bool kPair = !PR && !KC && !PopCodec<S>::kDev;
     __device__ __forceinline__ void operator()(const C* h, int stride, const StepArgs& a, const StepTables<C, P>& t,
                                                long long g) const {
-        collide_node<S, C, P, PR>(h, stride, a, t, static_cast<S*>(a.dst) + 2 * g);
+        collide_node<S, C, P, PR, StepTables<C, P>, KC>(h, stride, a, t, static_cast<S*>(a.dst) + 2 * g);
     }
     __device__ __forceinline__ void pair(const C* h, int stride, const StepArgs& a, const StepTables<C, P>& t,
                                          long long g, int half, unsigned mask) const {
@@ -670,11 +760,11 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const StepTables<C,
 template <typename C, int NW>
 constexpr int kStepMinCtas = NW == 9 && sizeof(C) == 4 ? 2 : 1;
 
-template <typename S, typename C, int P, int CX, int CY, int CZ, int NW, bool PR>
+template <typename S, typename C, int P, int CX, int CY, int CZ, int NW, bool PR, bool KC = false>
 __global__ void __launch_bounds__(NW * 32, kStepMinCtas<C, NW>)
     step_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ StepTables<C, P> t) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    CollideOp<S, C, P, PR> op;
+    CollideOp<S, C, P, PR, KC> op;
     step_tile<S, C, P, CX, CY, CZ, NW, PR>(a, t, blockIdx.x, smem_raw, op);
 }
 
@@ -723,11 +813,30 @@ __global__ void __launch_bounds__(NW * 32)
     }
 }
 
+// Launches step_kernel<..., PR, KC> over the tiles [q] of a launch (helper of launch_step_tiled).
+template <typename S, typename C, int P, int CX, int CY, int CZ, int NW, bool PR, bool KC>
+cudaError_t launch_step_variant(const StepArgs& args, const StepTables<C, P>& tab, long long ntiles,
+                                cudaStream_t stream) {
+    using SM = StepSmem<C, P, CX, CY, CZ, NW>;
+    auto k = step_kernel<S, C, P, CX, CY, CZ, NW, PR, KC>;
+    cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(SM::bytes));
+    if (err == cudaSuccess) {
+        k<<<static_cast<unsigned>(ntiles), NW * 32, SM::bytes, stream>>>(args, tab);
+        err = cudaGetLastError();
+    }
+    return err;
+}
+
 // WITH_PR = false instantiates only the kernel without the Prandtl term (tile-shape
 // variants offered to the autotuner); such a launcher refuses contexts with the term on.
-template <typename S, typename C, int P, int CX, int CY, int CZ, int NW, bool WITH_PR = true>
+// WITH_KC = true also instantiates the compensated-moment kernels (FP32 arithmetic); a
+// launcher without them refuses a context that asks for compensation, and FP64 arithmetic
+// ignores the request (its sums need none).
+template <typename S, typename C, int P, int CX, int CY, int CZ, int NW, bool WITH_PR = true, bool WITH_KC = true>
 int launch_step_tiled(sllbm_ctx* ctx, const void* src, void* dst) {
     if (!WITH_PR && ctx->prm.pr_correction) return SLLBM_EINVAL;
+    constexpr bool kKC = WITH_KC && sizeof(C) == 4;
+    if (!WITH_KC && sizeof(C) == 4 && ctx->compensated) return SLLBM_EINVAL;
     using SM = StepSmem<C, P, CX, CY, CZ, NW>;
     static_assert(SM::bytes <= 227 * 1024, "shared memory budget");
     // the tables are built once per context and kept in its host-side blob
@@ -754,23 +863,19 @@ int launch_step_tiled(sllbm_ctx* ctx, const void* src, void* dst) {
         const long long ntiles =
             static_cast<long long>(args.tiles[0]) * args.tiles[1] * (ranges[q][1] - ranges[q][0]);
         if (ntiles <= 0) continue;
+        const bool kc = kKC && ctx->compensated;
         if (ctx->prm.pr_correction) {
             if constexpr (WITH_PR) {
-                auto k = step_kernel<S, C, P, CX, CY, CZ, NW, true>;
-                err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           static_cast<int>(SM::bytes));
-                if (err == cudaSuccess) {
-                    k<<<static_cast<unsigned>(ntiles), NW * 32, SM::bytes, ctx->stream>>>(args, *tab);
-                    err = cudaGetLastError();
+                if constexpr (kKC) {
+                    if (kc) err = launch_step_variant<S, C, P, CX, CY, CZ, NW, true, true>(args, *tab, ntiles, ctx->stream);
                 }
+                if (!kc) err = launch_step_variant<S, C, P, CX, CY, CZ, NW, true, false>(args, *tab, ntiles, ctx->stream);
             }
         } else {
-            auto k = step_kernel<S, C, P, CX, CY, CZ, NW, false>;
-            err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(SM::bytes));
-            if (err == cudaSuccess) {
-                k<<<static_cast<unsigned>(ntiles), NW * 32, SM::bytes, ctx->stream>>>(args, *tab);
-                err = cudaGetLastError();
+            if constexpr (kKC) {
+                if (kc) err = launch_step_variant<S, C, P, CX, CY, CZ, NW, false, true>(args, *tab, ntiles, ctx->stream);
             }
+            if (!kc) err = launch_step_variant<S, C, P, CX, CY, CZ, NW, false, false>(args, *tab, ntiles, ctx->stream);
         }
         ctx->launches += 1;
     }

@@ -147,7 +147,7 @@ int launch_tma(sllbm_ctx* ctx, const void* src, void* dst) {
 }  // namespace
 
 bool tma_step_eligible(const sllbm_ctx* c) {
-    if (c->prm.storage != SLLBM_F32 || c->prm.pr_correction || !c->prm.collide) return false;
+    if (c->prm.storage != SLLBM_F32 || c->prm.pr_correction || !c->prm.collide || c->compensated) return false;
     if (c->N[0] % 2 != 0 || c->num_sms <= 0) return false;
     if (tensor_map_encoder() == nullptr) return false;
     switch (c->p) {

@@ -220,10 +220,13 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Bounded waits give up after kWaitNs of wall time (read from the global timer), or after
-// kWaitPolls polls should that timer not advance, or as soon as another warp raised the CTA
-// abort flag; the warp that gives up raises the abort flag and the global error bit.
-constexpr uint64_t kWaitNs = 2000000000ull;
+// Bounded waits give up after limit_ns of wall time (read from the global timer; the step
+// arguments carry the limit of the consumers' and the producer's waits, 2 s unless
+// sllbm_set_wait_limit changed it), or after kWaitPolls polls should that timer not advance,
+// or as soon as another warp raised the CTA abort flag; the warp that gives up raises the
+// abort flag and the global error bit.  The producer's drain of its copies in flight always
+// waits up to kWaitNs.
+constexpr uint64_t kWaitNs = kDefaultWaitNs;
 constexpr uint32_t kWaitPolls = 1u << 26;
 
 __device__ __forceinline__ bool wait_give_up(volatile int* abort_flag, int* err_flag) {
@@ -235,14 +238,14 @@ __device__ __forceinline__ bool wait_give_up(volatile int* abort_flag, int* err_
 // Bounded wait for the phase `parity` of an mbarrier.  try_wait suspends the thread until the
 // phase completes (or the hint expires), so the loop does not spin on the issue slots.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                                  int* err_flag) {
+                                                  int* err_flag, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t it = 1; it < kWaitPolls; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 7u) == 0) {
             if (*abort_flag) return false;
-            if (global_ns() - t0 > kWaitNs) break;
+            if (global_ns() - t0 > limit_ns) break;
         }
     }
     return wait_give_up(abort_flag, err_flag);
@@ -252,7 +255,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 // reaches `want`; returns the low half (0 if the wait gave up, same give-up rules).  Short
 // sleeps between polls leave the issue slots to the warps doing work.
 __device__ __forceinline__ uint32_t wait_item_bounded(volatile unsigned long long* word, uint32_t want,
-                                                      volatile int* abort_flag, int* err_flag) {
+                                                      volatile int* abort_flag, int* err_flag, uint64_t limit_ns) {
     unsigned long long v = *word;
     if (static_cast<uint32_t>(v >> 32) == want) return static_cast<uint32_t>(v);
     const uint64_t t0 = global_ns();
@@ -262,7 +265,7 @@ __device__ __forceinline__ uint32_t wait_item_bounded(volatile unsigned long lon
         if (static_cast<uint32_t>(v >> 32) == want) return static_cast<uint32_t>(v);
         if ((it & 7u) == 0) {
             if (*abort_flag) return 0;
-            if (global_ns() - t0 > kWaitNs) break;
+            if (global_ns() - t0 > limit_ns) break;
         }
     }
     wait_give_up(abort_flag, err_flag);
@@ -498,7 +501,22 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         bool ok = true;
         const uint32_t ring_u32 = smem_u32(ring);
         const int cd[3] = {CX, CY, CZ};
+        // the host-written abort request word, read one tile ahead so that its latency hides
+        // behind a tile's work
+        const volatile int* abort_req = reinterpret_cast<const volatile int*>(a.abort_req);
+        int req_word = (lane == 0 && abort_req != nullptr) ? *abort_req : 0;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, s_tile += IPP) {
+            // an abort request ends the launch at a tile boundary: the consumers leave through
+            // the abort flag, this producer drains its copies (below)
+            if (__shfl_sync(0xffffffffu, req_word, 0) != 0) {
+                if (lane == 0) {
+                    *abort_flag = 1;
+                    if (err_flag != nullptr) atomicOr(err_flag, 4);
+                }
+                ok = false;
+                break;
+            }
+            if (lane == 0 && abort_req != nullptr) req_word = *abort_req;
             int tc[3];
             tile_coords(tile, ntx, nty, ntz, tc);
             const int cb[3] = {tc[0] * CX * P, tc[1] * CY * P, tc[2] * CZ * P};
@@ -610,7 +628,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                     // nothing fits: wait (blocking, bounded) for the oldest item's release
                     int stop = 0;
                     if (lane == 0 && !mbar_wait_bounded(pe0 + 8 * (tail & KM), (tail / kItems) & 1u, abort_flag,
-                                                        err_flag))
+                                                        err_flag, a.wait_ns))
                         stop = 1;
                     if (__shfl_sync(0xffffffffu, stop, 0)) {
                         ok = false;
@@ -706,7 +724,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         {
             volatile int keep_waiting = 0;
             for (uint32_t x = tail; x != sent; ++x)
-                mbar_wait_bounded(pf0 + 8 * (x & KM), (x / kItems) & 1u, &keep_waiting, nullptr);
+                mbar_wait_bounded(pf0 + 8 * (x & KM), (x / kItems) & 1u, &keep_waiting, nullptr, kWaitNs);
         }
         return;
     }
@@ -736,7 +754,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
             const int c0[3] = {tc[0] * CX, tc[1] * CY, tc[2] * CZ};
             if (it >= 2)
                 mbar_wait_bounded(tmem_empty0 + 8 * (qd * 2 + bf), static_cast<uint32_t>((it - 2) >> 1) & 1u, abort_flag,
-                                  err_flag);
+                                  err_flag, a.wait_ns);
             tc_fence_after();
             const uint32_t tbuf = tmem_warp + static_cast<uint32_t>(bf * TC::per_buf);
 #pragma unroll 1
@@ -747,9 +765,13 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                 // s - kItems has released the same descriptor, so its full barrier is then at most
                 // one phase ahead of the phase awaited below (one parity bit cannot tell more apart).
                 const uint32_t e = s & KM;
-                const uint32_t word = wait_item_bounded(items + pbase + e, s, abort_flag, err_flag);
-                const int m = static_cast<int>(word & 15u);
-                if (m > 0) mbar_wait_bounded(full0 + 8 * (pbase + e), (s / kItems) & 1u, abort_flag, err_flag);
+                const uint32_t word = wait_item_bounded(items + pbase + e, s, abort_flag, err_flag, a.wait_ns);
+                const int m = static_cast<int>(word & 15u);  // (0 only when the wait gave up)
+                // Whether this item's copies have landed.  An item whose wait gave up (abort)
+                // is not released below: its fill may still be writing the box, and an
+                // unreleased item stays in the producer's drain.
+                const bool filled =
+                    m > 0 && mbar_wait_bounded(full0 + 8 * (pbase + e), (s / kItems) & 1u, abort_flag, err_flag, a.wait_ns);
                 float2* box = ring + static_cast<size_t>(word >> 8) * 16;
                 const int ox0 = ((c0[0] + t.kmin[j][0]) * P) & 1;
                 // the box's shape: rows of XP pairs, planes of PL pairs; pieces PSTRIDE float2 apart
@@ -953,7 +975,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                 // the slot was written in place (generic proxy); order that before the next TMA fill
                 fence_proxy_async();
                 __syncwarp();
-                if (lane == 0 && m > 0) mbar_arrive(full0 + 8 * (pbase + kItems + e));
+                if (lane == 0 && filled) mbar_arrive(full0 + 8 * (pbase + kItems + e));
 
                 // park the pair in tensor memory
                 tmem_store_row<G::TX>(tbuf + static_cast<uint32_t>(k * 2 * G::TX), res);
@@ -984,7 +1006,8 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
             tile_coords(tile, ntx, nty, ntz, tc);
             const int c0[3] = {tc[0] * CX, tc[1] * CY, tc[2] * CZ};
             const uint32_t tb = tq + static_cast<uint32_t>(bf * TC::per_buf);
-            mbar_wait_bounded(tmem_full0 + 8 * (qd * 2 + bf), static_cast<uint32_t>(it >> 1) & 1u, abort_flag, err_flag);
+            mbar_wait_bounded(tmem_full0 + 8 * (qd * 2 + bf), static_cast<uint32_t>(it >> 1) & 1u, abort_flag, err_flag,
+                              a.wait_ns);
             tc_fence_after();
             // moment contributions of the quarter's pairs (rho, m_x, m_y, m_z, 2 rho E; Eq. moments)
             {

@@ -16,7 +16,7 @@ import numpy as np
 
 from . import build as _build
 
-OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ENOTREADY = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ENOTREADY, EABORTED, EIO = 0, -1, -2, -3, -4, -5, -6, -7, -8
 F64, F32, F16DEV, BF16DEV = 0, 1, 2, 3
 STORAGE = {"f64": F64, "f32": F32, "f16dev": F16DEV, "bf16dev": BF16DEV}
 Q = 45
@@ -45,6 +45,14 @@ class Params(ctypes.Structure):
                 ("nonfinite_check", ctypes.c_int), ("tgv_C", ctypes.c_double),
                 ("mu_inf_override", ctypes.c_double), ("collide", ctypes.c_int),
                 ("kernel", ctypes.c_int)]
+
+
+class Checkpoint(ctypes.Structure):
+    _fields_ = [("storage", ctypes.c_int), ("p", ctypes.c_int), ("velset", ctypes.c_int),
+                ("cells", ctypes.c_int * 3), ("pr_correction", ctypes.c_int),
+                ("L", ctypes.c_double * 3), ("dt", ctypes.c_double), ("mu_inf", ctypes.c_double),
+                ("rho0", ctypes.c_double), ("T0", ctypes.c_double), ("steps", ctypes.c_int64),
+                ("payload_bytes", ctypes.c_uint64)]
 
 
 class Info(ctypes.Structure):
@@ -126,6 +134,15 @@ def load(build_if_missing: bool = False):
         "sllbm_adjoint_step": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "sllbm_ek_adjoint": (ctypes.c_int, [vp, vp, vp]),
         "sllbm_init_fields_adjoint": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp]),
+        "sllbm_set_wait_limit": (ctypes.c_int, [vp, ctypes.c_double]),
+        "sllbm_request_abort": (ctypes.c_int, [vp, ctypes.c_int]),
+        "sllbm_debug_fail_allocs": (ctypes.c_int, [ctypes.c_int]),
+        "sllbm_step_count": (ctypes.c_int64, [vp]),
+        "sllbm_set_compensated": (ctypes.c_int, [vp, ctypes.c_int]),
+        "sllbm_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
+        "sllbm_load": (ctypes.c_int, [vp, ctypes.c_char_p]),
+        "sllbm_checkpoint_info": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(Checkpoint)]),
+        "sllbm_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, dp, dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -285,9 +302,51 @@ def sllbm_run_host_many(ctx, in_ptrs, out_ptrs, n: int) -> None:
 
 def sllbm_status(ctx) -> int:
     rc = load().sllbm_status(ctx)
-    if rc not in (OK, ETIMEOUT):
+    if rc not in (OK, ETIMEOUT, EABORTED):
         _check(rc, "sllbm_status", ctx)
     return rc
+
+
+def sllbm_set_wait_limit(ctx, seconds: float) -> None:
+    _check(load().sllbm_set_wait_limit(ctx, float(seconds)), "sllbm_set_wait_limit", ctx)
+
+
+def sllbm_request_abort(ctx, on: bool) -> None:
+    _check(load().sllbm_request_abort(ctx, int(bool(on))), "sllbm_request_abort", ctx)
+
+
+def sllbm_debug_fail_allocs(after: int) -> None:
+    _check(load().sllbm_debug_fail_allocs(int(after)), "sllbm_debug_fail_allocs")
+
+
+def sllbm_set_compensated(ctx, on: bool) -> None:
+    _check(load().sllbm_set_compensated(ctx, int(bool(on))), "sllbm_set_compensated", ctx)
+
+
+def sllbm_step_count(ctx) -> int:
+    return int(load().sllbm_step_count(ctx))
+
+
+def sllbm_save(ctx, path: str) -> None:
+    _check(load().sllbm_save(ctx, os.fsencode(path)), "sllbm_save", ctx)
+
+
+def sllbm_load(ctx, path: str) -> None:
+    _check(load().sllbm_load(ctx, os.fsencode(path)), "sllbm_load", ctx)
+
+
+def sllbm_checkpoint_info(path: str) -> Checkpoint:
+    c = Checkpoint()
+    _check(load().sllbm_checkpoint_info(os.fsencode(path), ctypes.byref(c)), "sllbm_checkpoint_info")
+    return c
+
+
+def sllbm_fma_peak(kind: int, iters: int = 4096, stream: int = 0):
+    """(flop/s, seconds) of the FMA microbenchmark: kind 0 FP32, 1 packed FP32x2, 2 FP64."""
+    f, t = ctypes.c_double(), ctypes.c_double()
+    _check(load().sllbm_fma_peak(int(kind), int(iters), ctypes.c_void_p(stream), ctypes.byref(f),
+                                 ctypes.byref(t)), "sllbm_fma_peak")
+    return float(f.value), float(t.value)
 
 
 def sllbm_sync(ctx) -> None:

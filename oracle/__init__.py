@@ -18,7 +18,8 @@ Each wrapper cites the passage of the paper its C function follows:
 * :func:`tgv_fields` -- Sec. III.C Taylor-Green initial fields;
 * :func:`diag` -- the E_k, eps_s, eps_c definitions of Sec. III.C;
 * :func:`stream_adjoint`, :func:`collide_vjp`, :func:`step_adjoint`, :func:`ek_grad`,
-  :func:`init_fields_vjp` -- reverse mode of the above (no counterpart in the paper):
+  :func:`diag_grad`, :func:`init_fields_vjp` -- reverse mode of the above (no counterpart
+  in the paper):
   the literal transpose of the streaming, and finite-difference (Richardson-extrapolated)
   Jacobians of the collision and the equilibrium initialisation.
 
@@ -91,6 +92,7 @@ def _load():
             lib.orc_stream_adjoint.argtypes = [cfgp, ctypes.c_int, ctypes.c_int, dp, dp, dp]
             lib.orc_collide_vjp.argtypes = [cfgp, dp, dp, dp, dp]
             lib.orc_ek_grad.argtypes = [cfgp, dp, ctypes.c_double, ctypes.c_double, dp]
+            lib.orc_diag_grad.argtypes = [cfgp, dp] + [ctypes.c_double] * 6 + [dp]
             lib.orc_init_fields_vjp.argtypes = [cfgp, dp, dp, dp, dp, dp, dp, dp]
             _lib = lib
     return _lib
@@ -336,6 +338,19 @@ def ek_grad(g: Grid, pop: np.ndarray, rho_ref: float, U0: float) -> np.ndarray:
     lam = np.empty_like(pop)
     c = g._c()
     _load().orc_ek_grad(ctypes.byref(c), _ptr(pop), float(rho_ref), float(U0), _ptr(lam))
+    return lam
+
+
+def diag_grad(g: Grid, pop: np.ndarray, rho_ref: float, Re: float, U0: float,
+              weights=(0.0, 1.0, 1.0)) -> np.ndarray:
+    """d (wk E_k + ws eps_s + wc eps_c) / d pop for the diagnostics of :func:`diag` (Sec.
+    III.C), weights = (wk, ws, wc); [2,45,Nz,Ny,Nx]."""
+    pop = np.ascontiguousarray(pop, dtype=np.float64)
+    lam = np.empty_like(pop)
+    c = g._c()
+    wk, ws, wc = (float(x) for x in weights)
+    _load().orc_diag_grad(ctypes.byref(c), _ptr(pop), float(rho_ref), float(Re), float(U0), wk, ws, wc,
+                          _ptr(lam))
     return lam
 
 

@@ -820,6 +820,119 @@ void orc_ek_grad(const orc_cfg *g, const double *pop, double rho_ref, double U0,
     free(rho); free(u); free(T);
 }
 
+/* Derivative of a weighted sum of the diagnostics of orc_diag,
+ *   J = wk E_k + ws eps_s + wc eps_c,
+ * with respect to the populations: lam = dJ/dpop ([2][45][nodes], f then g).  Written as
+ * the chain rule through the node fields, in scatter form, cell by cell:
+ *   - E_k's integrand at a quadrature point, rho |u|^2 / 2, sends |u|^2/2 to the point's
+ *     rho adjoint and rho u to its u adjoint;
+ *   - eps_s's and eps_c's integrands, mu~(T) |curl u|^2 and (4/3) mu~(T) (div u)^2, send
+ *     mu~'(T) times the squared quantity to the point's T adjoint, and their derivative with
+ *     respect to each gradient entry d u_c / d x_d at the point to the u_c adjoint of every
+ *     support point on the point's line along d, with the cell-local Lagrange derivative
+ *     weight (2/h_d) D[a][j] the forward gradient used;
+ *   - then each node's (rho, u, T) adjoint becomes population adjoints through the moments
+ *     rho = sum f, rho u = sum f xi, 2 C_v rho T + rho |u|^2 = sum (f |xi|^2 + g):
+ *     d rho/d f_i = 1, d u/d f_i = (xi_i - u)/rho, d T/d f_i = (|xi_i - u|^2 - 2 C_v T)/(2 C_v rho),
+ *     d T/d g_i = 1/(2 C_v rho), d u/d g_i = d rho/d g_i = 0.
+ * mu~ is the Sutherland law of orc_sutherland; its derivative is taken analytically from
+ * the printed law.                                                                     */
+void orc_diag_grad(const orc_cfg *g, const double *pop, double rho_ref, double Re, double U0,
+                   double wk, double ws, double wc, double *lam)
+{
+    const int p = g->p;
+    const int N[3] = {g->cells[0] * p, g->cells[1] * p, g->cells[2] * p};
+    const long nn = (long)N[0] * N[1] * N[2];
+    const long ncell = (long)g->cells[0] * g->cells[1] * g->cells[2];
+    const double two_cv = 2.0 / (g->gamma - 1.0);
+    double *rho = (double *)malloc(sizeof(double) * nn);
+    double *u = (double *)malloc(sizeof(double) * 3 * nn);
+    double *T = (double *)malloc(sizeof(double) * nn);
+    double *a_rho = (double *)calloc((size_t)nn, sizeof(double));
+    double *a_u = (double *)calloc((size_t)3 * nn, sizeof(double));
+    double *a_T = (double *)calloc((size_t)nn, sizeof(double));
+    double xi[3 * ORC_Q], w[ORC_Q], W[16], D[16][16], nodes[16], h[3];
+    const double vol = g->L[0] * g->L[1] * g->L[2];
+    const double ke = wk / (vol * rho_ref * U0 * U0);
+    const double ks = ws / (vol * rho_ref * Re * U0 * U0);
+    const double kc = wc * 4.0 / 3.0 / (vol * rho_ref * Re * U0 * U0);
+    long cell, n;
+    int a, d, i;
+    orc_velset(xi, w);
+    orc_moments(g, pop, rho, u, T);
+    orc_quad_weights(p, W);
+    orc_glc(p, nodes);
+    for (a = 0; a <= p; ++a) orc_lagrange_deriv(p, nodes[a], D[a]);
+    for (d = 0; d < 3; ++d) h[d] = g->L[d] / g->cells[d];
+    for (cell = 0; cell < ncell; ++cell) {
+        int c[3], loc[3], comp, j;
+        c[0] = (int)(cell % g->cells[0]);
+        c[1] = (int)((cell / g->cells[0]) % g->cells[1]);
+        c[2] = (int)(cell / ((long)g->cells[0] * g->cells[1]));
+        for (loc[2] = 0; loc[2] <= p; ++loc[2])
+            for (loc[1] = 0; loc[1] <= p; ++loc[1])
+                for (loc[0] = 0; loc[0] <= p; ++loc[0]) {
+                    long line[3][16]; /* node index of support point j on the point's line along d */
+                    double grad[3][3], om[3], dv, usq, mut, dmut, wq, G;
+                    long nq;
+                    for (d = 0; d < 3; ++d)
+                        for (j = 0; j <= p; ++j) {
+                            int m[3];
+                            m[0] = wrap(c[0] * p + (d == 0 ? j : loc[0]), N[0]);
+                            m[1] = wrap(c[1] * p + (d == 1 ? j : loc[1]), N[1]);
+                            m[2] = wrap(c[2] * p + (d == 2 ? j : loc[2]), N[2]);
+                            line[d][j] = ((long)m[2] * N[1] + m[1]) * N[0] + m[0];
+                        }
+                    nq = line[0][loc[0]];
+                    wq = W[loc[0]] * W[loc[1]] * W[loc[2]] * h[0] * h[1] * h[2] / 8.0;
+                    for (comp = 0; comp < 3; ++comp)
+                        for (d = 0; d < 3; ++d) {
+                            double sacc = 0.0;
+                            for (j = 0; j <= p; ++j) sacc += D[loc[d]][j] * u[comp * nn + line[d][j]];
+                            grad[comp][d] = sacc * 2.0 / h[d];
+                        }
+                    om[0] = grad[2][1] - grad[1][2];
+                    om[1] = grad[0][2] - grad[2][0];
+                    om[2] = grad[1][0] - grad[0][1];
+                    dv = grad[0][0] + grad[1][1] + grad[2][2];
+                    usq = u[nq] * u[nq] + u[nn + nq] * u[nn + nq] + u[2 * nn + nq] * u[2 * nn + nq];
+                    mut = orc_sutherland(T[nq]);
+                    /* mu~ = A T^1.5 / (T + B): d mu~/dT = mu~ (1.5/T - 1/(T + B)) */
+                    dmut = mut * (1.5 / T[nq] - 1.0 / (T[nq] + 0.40417));
+                    /* kinetic energy */
+                    a_rho[nq] += wq * ke * 0.5 * usq;
+                    for (comp = 0; comp < 3; ++comp) a_u[comp * nn + nq] += wq * ke * rho[nq] * u[comp * nn + nq];
+                    /* temperature through the Sutherland factor */
+                    a_T[nq] += wq * dmut * (ks * (om[0] * om[0] + om[1] * om[1] + om[2] * om[2]) + kc * dv * dv);
+                    /* gradient entries: dJ/dgrad[comp][d] */
+                    for (comp = 0; comp < 3; ++comp)
+                        for (d = 0; d < 3; ++d) {
+                            double dcurl = 0.0;
+                            if (comp == 2 && d == 1) dcurl = 2.0 * om[0];
+                            if (comp == 1 && d == 2) dcurl = -2.0 * om[0];
+                            if (comp == 0 && d == 2) dcurl = 2.0 * om[1];
+                            if (comp == 2 && d == 0) dcurl = -2.0 * om[1];
+                            if (comp == 1 && d == 0) dcurl = 2.0 * om[2];
+                            if (comp == 0 && d == 1) dcurl = -2.0 * om[2];
+                            G = wq * mut * (ks * dcurl + kc * (comp == d ? 2.0 * dv : 0.0));
+                            if (G == 0.0) continue;
+                            for (j = 0; j <= p; ++j)
+                                a_u[comp * nn + line[d][j]] += G * D[loc[d]][j] * 2.0 / h[d];
+                        }
+                }
+    }
+    for (n = 0; n < nn; ++n) {
+        const double r = rho[n], ux = u[n], uy = u[nn + n], uz = u[2 * nn + n];
+        for (i = 0; i < ORC_Q; ++i) {
+            const double cx = xi[3 * i] - ux, cy = xi[3 * i + 1] - uy, cz = xi[3 * i + 2] - uz;
+            lam[(long)i * nn + n] = a_rho[n] + (a_u[n] * cx + a_u[nn + n] * cy + a_u[2 * nn + n] * cz) / r
+                                  + a_T[n] * (cx * cx + cy * cy + cz * cz - two_cv * T[n]) / (two_cv * r);
+            lam[(long)(ORC_Q + i) * nn + n] = a_T[n] / (two_cv * r);
+        }
+    }
+    free(rho); free(u); free(T); free(a_rho); free(a_u); free(a_T);
+}
+
 /* Transpose of orc_init_fields: grad_rho[n], grad_u[3][n], grad_T[n] = the derivatives of
  * sum_i (lam_f_i f_i + lam_g_i g_i) at node n with respect to rho, u, T there, where
  * f_i = f_i^eq(rho, u, T) and g_i = (2C_v - D) T f_i^eq.                                */

@@ -170,3 +170,51 @@ def test_taylor_green_run_against_fp64(S, storage):
     print(storage, "relative L2 of rho, u, T after", w.steps, "steps:", errs)
     for e, bound in zip(errs, STATED_TGV[storage]):
         assert e <= bound
+
+
+@pytest.mark.parametrize("storage,p,pr", [("f32", 3, False), ("f32", 4, True), ("f16dev", 3, False),
+                                          ("bf16dev", 3, True)])
+def test_compensated_moments_step_matches_oracle(S, storage, p, pr):
+    """sllbm_set_compensated: the compensated moment and temperature sums give the same step
+    as the oracle within the tolerances of the plain sums (FP32: relative L2 1.5e-6 from the
+    FP32-rounded start; 16-bit: the deviation-space bound of the plain test); both errors are
+    printed for comparison."""
+    cells = (3, 2, 2) if p == 3 else (2, 2, 1)
+    errs = {}
+    for kc in (False, True):
+        sim = make(S, cells, p, storage, courant=3.0, pr=pr, Ma=1.25)
+        if kc:
+            S.sllbm_set_compensated(sim.ctx, True)
+        assert sim.info.step_kernel == 1 or not kc
+        g = grid_of(sim, pr=pr)
+        sim.set_populations(noneq_state(g, 21))
+        start = sim.populations().cpu().numpy()
+        ref = O.step(g, start, 1)
+        assert sim.step(1) == 0
+        got = sim.populations().cpu().numpy()
+        if storage == "f32":
+            errs[kc] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+            assert errs[kc] <= 1.5e-6
+        else:
+            d_ref, d_got = deviations(ref, sim), deviations(got, sim)
+            bound = RELBITS[storage] * np.abs(d_ref) + 1e-5 * np.abs(d_ref).max()
+            errs[kc] = float(np.max(np.abs(d_got - d_ref) / bound))
+            assert errs[kc] <= 1.0
+        sim.close()
+    print(storage, p, "pr" if pr else "", "plain", errs[False], "compensated", errs[True])
+
+
+def test_compensation_flag_selects_a_summing_kernel(S):
+    sim = S.Sim(S.Config(cells=(4, 2, 2), p=4, courant=3.0, storage="f32"))
+    assert sim.info.step_kernel == 2  # the TMA-fed kernel by default
+    S.sllbm_set_compensated(sim.ctx, True)
+    assert S.sllbm_get_info(sim.ctx).step_kernel == 1
+    with pytest.raises(S.SllbmError):
+        S.sllbm_set_step_variant(sim.ctx, 2)  # the alternative tiles sum plainly
+    S.sllbm_set_compensated(sim.ctx, False)
+    assert S.sllbm_get_info(sim.ctx).step_kernel == 2
+    forced = S.Sim(S.Config(cells=(4, 2, 2), p=4, courant=3.0, storage="f32", kernel=2))
+    with pytest.raises(S.SllbmError):
+        S.sllbm_set_compensated(forced.ctx, True)
+    sim.close()
+    forced.close()

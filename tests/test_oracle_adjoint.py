@@ -153,6 +153,36 @@ def test_ek_grad_is_the_derivative_of_the_diagnostic():
     assert rel(float(np.sum(lam * v)), float(fd)) < 1e-8
 
 
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_diag_grad_is_the_derivative_of_each_diagnostic(k):
+    """d(E_k, eps_s, eps_c)/dpop of the oracle against directional differences of its own
+    diagnostics (Sec. III.C definitions) along a random direction, on a mesh of several
+    cells per direction (cells share face nodes, so the scatter over neighbouring cells is
+    exercised) with a non-equilibrium state."""
+    g = grid((3, 2, 2), 3)
+    pop = noneq(g, 43)
+    U0, Re = 0.59, 1600.0
+    wts = [0.0, 0.0, 0.0]
+    wts[k] = 1.0
+    lam = O.diag_grad(g, pop, 1.0, Re, U0, wts)
+    rng = np.random.default_rng(17 + k)
+    v = rng.standard_normal(pop.shape) * np.abs(pop)
+    fd = directional(lambda x: O.diag(g, x, 1.0, Re, U0)[k], pop, v, 1e-3)
+    assert rel(float(np.sum(lam * v)), float(fd)) < 1e-7
+    if k == 0:  # the E_k part equals the dedicated E_k gradient
+        assert np.allclose(lam, O.ek_grad(g, pop, 1.0, U0), rtol=1e-13, atol=1e-18)
+    else:  # the dissipation depends on g only through T
+        assert np.any(lam[1] != 0.0)
+
+
+def test_diag_grad_is_linear_in_the_weights():
+    g = grid((2, 2, 1), 2)
+    pop = noneq(g, 44)
+    parts = [O.diag_grad(g, pop, 1.0, 400.0, 0.7, w) for w in ((1, 0, 0), (0, 1, 0), (0, 0, 1))]
+    mix = O.diag_grad(g, pop, 1.0, 400.0, 0.7, (0.5, -2.0, 3.0))
+    assert np.allclose(mix, 0.5 * parts[0] - 2.0 * parts[1] + 3.0 * parts[2], rtol=1e-12, atol=1e-15)
+
+
 def test_init_fields_vjp_is_the_transpose_of_the_initialisation():
     g = grid((2, 1, 1), 3)
     rho, u, T = I.smooth_fields(g.N[::-1], 51)
@@ -198,5 +228,38 @@ def test_adjoint_chain_reproduces_finite_differences_of_the_forward_run():
         return O.diag(gg, run(u + eps * du, gg)[-1], 1.0, 1600.0, U0)[0]
     fd_eps = directional(lambda e: ek(eps=e), 0.0, 1.0, 1.0)
     fd_mu = directional(lambda m: ek(mu=m), g.mu_inf, 1.0, 1e-2 * g.mu_inf)
+    assert rel(grad_eps, fd_eps) < 1e-6
+    assert rel(dmu, fd_mu) < 1e-6
+
+
+def test_adjoint_chain_of_the_dissipation_reproduces_finite_differences():
+    """The same chain seeded with the dissipation eps_s + eps_c of the final state."""
+    g = grid((2, 2, 1), 2, dt=0.1, mu=4e-3)
+    U0, Re, steps = 0.5, 1600.0, 3
+    rho, u, T = I.smooth_fields(g.N[::-1], 62)
+    rng = np.random.default_rng(10)
+    du = 1e-3 * U0 * rng.standard_normal(u.shape)
+
+    def run(uu, gg):
+        s = [O.init_fields(gg, rho, uu, T)]
+        for _ in range(steps):
+            s.append(O.step(gg, s[-1], 1))
+        return s
+
+    states = run(u, g)
+    lam = O.diag_grad(g, states[-1], 1.0, Re, U0, (0.0, 1.0, 1.0))
+    dmu = 0.0
+    for k in range(steps, 0, -1):
+        lam, d = O.step_adjoint(g, states[k - 1], lam)
+        dmu += d
+    _, gu, _ = O.init_fields_vjp(g, rho, u, T, lam)
+    grad_eps = float(np.sum(gu * du))
+
+    def eps(e=0.0, mu=g.mu_inf):
+        gg = grid((2, 2, 1), 2, dt=0.1, mu=mu)
+        d = O.diag(gg, run(u + e * du, gg)[-1], 1.0, Re, U0)
+        return d[1] + d[2]
+    fd_eps = directional(lambda e: eps(e=e), 0.0, 1.0, 1.0)
+    fd_mu = directional(lambda m: eps(mu=m), g.mu_inf, 1.0, 1e-2 * g.mu_inf)
     assert rel(grad_eps, fd_eps) < 1e-6
     assert rel(dmu, fd_mu) < 1e-6

@@ -23,6 +23,16 @@ parameters one by one and as one CUDA graph per two steps (autotuned kernels), a
 the aggregate node-updates/s of each.  The "adjoint" block times the reverse mode on the 48^3-node Taylor-Green run and states
 its gradients' errors against central differences of the FP64 forward run.
 
+The line's "alu_peaks" are measured at the start by the library's FMA microbenchmark
+(sllbm_fma_peak: FP32, packed FP32x2, FP64); the FP64 variant and the mixed block quote
+their arithmetic against them ("roofline_alu"; for 16-bit storage the bound is the larger of
+the HBM time of the algorithmic bytes and the FP32 time of the algorithmic flops).  The
+mixed block also runs FP32 arithmetic with compensated moment sums ("*_comp").  The "pr"
+variant times the headline workload with the Prandtl term of App. D on.  The "long_run"
+block runs the throughput mesh for 2000 steps in FP32 and FP64 (Prandtl term on, the
+paper's Taylor-Green setting) and compares their E_k(t) and eps(t) curves with each other
+and with the oracle's 16^3-cell run at the same time step (tests/golden).
+
 --impl reference times the FP64 CPU oracle (tests-only code) on the host cores on a
 bounded sample of the same workload.
 """
@@ -48,7 +58,6 @@ from paper_2012_05537_gb300 import inputs as I  # noqa: E402
 METRIC = "node-updates/s (×45 pops) vs HBM roofline; mixed vs FP64 at stated error"
 UNIT = "node-updates/s"
 FALLBACK_HBM_GBS = 6800.0
-FP64_NOMINAL_TFLOPS = 1.25
 
 
 def algorithmic_flops_per_node(p: int) -> float:
@@ -57,6 +66,31 @@ def algorithmic_flops_per_node(p: int) -> float:
     Horner per velocity (45 x 9); the BGK update of 90 values (2 each)."""
     fma = 90 * 3 * (p + 1) + 45 * 6 + 45 * 9 + 90 * 2
     return 2.0 * fma
+
+
+def alu_peaks(S):
+    """FMA rates of this GPU in TFLOP/s from the library's microbenchmark (FP32, packed
+    FP32x2, FP64), each timed over one launch of a few tens of milliseconds."""
+    out = {}
+    for name, kind, iters in (("fp32", 0, 32768), ("fp32x2", 1, 16384), ("fp64", 2, 512)):
+        f, t = S.sllbm_fma_peak(kind, iters)
+        out[name + "_tflops"] = f / 1e12
+        out[name + "_ms"] = t * 1e3
+    out["how"] = ("sllbm_fma_peak: independent dependent FMA chains on every SM, one timed launch "
+                  "after a warm-up launch (CUDA events)")
+    return out
+
+
+def min_roofline(bytes_per_node, flops_per_node, nodes, kernel_ms, hbm_gbs, alu_tflops):
+    """Roofline of a step bound by HBM and by the ALU together: the bound is the larger of
+    the HBM time of the algorithmic bytes and the ALU time of the algorithmic flops."""
+    t_hbm = bytes_per_node * nodes / (hbm_gbs * 1e9)
+    t_alu = flops_per_node * nodes / (alu_tflops * 1e12)
+    t = kernel_ms / 1e3
+    return {"bound": "hbm" if t_hbm >= t_alu else "alu", "frac": max(t_hbm, t_alu) / t,
+            "hbm_frac": t_hbm / t, "alu_frac": t_alu / t, "hbm_peak_gbs": hbm_gbs,
+            "alu_peak_tflops": alu_tflops, "algorithmic_flops_per_node": flops_per_node,
+            "algorithmic_bytes_per_node": bytes_per_node}
 
 
 def parse_args():
@@ -73,8 +107,11 @@ def parse_args():
     ap.add_argument("--mixed-steps", type=int, default=400,
                     help="steps of the Ma 1.25 mixed-precision comparison (0: skip)")
     ap.add_argument("--mixed-every", type=int, default=20)
-    ap.add_argument("--batch-steps", type=int, default=100,
+    ap.add_argument("--batch-steps", type=int, default=500,
                     help="steps of the 64-instance batched comparison (0: skip)")
+    ap.add_argument("--long-steps", type=int, default=2000,
+                    help="steps of the FP32 vs FP64 long run of the throughput mesh (0: skip)")
+    ap.add_argument("--long-every", type=int, default=50)
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the reverse-mode block (gradients on the 48^3-node run)")
     return ap.parse_args()
@@ -291,12 +328,13 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b)) / den if den > 0 else float(np.linalg.norm(a - b))
 
 
-def mixed_precision_block(S, torch, device, steps, every, hbm):
+def mixed_precision_block(S, torch, device, steps, every, hbm, alu):
     """FP64, FP32 and 16-bit deviation storage on the Ma 1.25 Taylor-Green workload, all from
     the same initial state, for `steps` steps.  Per storage: median kernel time, node-updates/s,
     fraction of the HBM peak at its algorithmic bytes, and the relative L2 error against the
     FP64 GPU run of rho, u, T after the last step and of the E_k(t) and dissipation
-    eps_s(t) + eps_c(t) curves sampled every `every` steps."""
+    eps_s(t) + eps_c(t) curves sampled every `every` steps.  The FP32-arithmetic storages run
+    a second time with compensated moment sums ("<storage>_comp")."""
     import numpy as np
 
     w = I.WORKLOADS["tgv_64c_p3_ma125"]
@@ -305,10 +343,14 @@ def mixed_precision_block(S, torch, device, steps, every, hbm):
     out = {"workload": w.name, "note": w.note, "steps": chunks * every,
            "configured_steps": w.steps, "curve_every": every, "reference": "f64 (GPU)"}
     ref = None
-    for st in ("f64", "f32", "f16dev", "bf16dev"):
+    flops = algorithmic_flops_per_node(w.p)
+    for name in ("f64", "f32", "f16dev", "bf16dev", "f32_comp", "f16dev_comp", "bf16dev_comp"):
+        st = name.split("_")[0]
         sim = S.Sim(S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, Pr=w.Pr, gamma=w.gamma,
                              courant=w.courant, pr_correction=w.pr_correction, storage=st),
                     device=device)
+        if name.endswith("_comp"):
+            S.sllbm_set_compensated(sim.ctx, True)
         sim.init_tgv()
         curve = [sim.diag()]
         kern = []
@@ -324,6 +366,9 @@ def mixed_precision_block(S, torch, device, steps, every, hbm):
         rec = {"kernel_ms": kms, "value": sim.nodes / (kms / 1e3), "unit": UNIT,
                "hbm_frac": bpn * sim.nodes / (kms / 1e3) / 1e9 / hbm,
                "algorithmic_bytes_per_node": bpn, "step_kernel": int(sim.info.step_kernel),
+               "compensated_moments": name.endswith("_comp"),
+               "roofline_alu": min_roofline(bpn, flops, sim.nodes, kms, hbm,
+                                            alu["fp64_tflops"] if st == "f64" else alu["fp32_tflops"]),
                "finite": bool(np.isfinite(T).all() and np.isfinite(rho).all())}
         if ref is None:
             ref = (rho, u, T, ek, eps, kms)
@@ -333,31 +378,35 @@ def mixed_precision_block(S, torch, device, steps, every, hbm):
                              "T": rel_l2(T, ref[2]), "Ek_curve": rel_l2(ek, ref[3]),
                              "eps_curve": rel_l2(eps, ref[4])}
             rec["speedup_vs_f64"] = ref[5] / kms
-        out[st] = rec
+        out[name] = rec
         sim.close()
     return out
 
 
 def adjoint_block(S, torch, device, hbm, every=20, timed=20):
     """Reverse mode on the 16^3-cell, p = 3 Taylor-Green run (200 steps, checkpoints every
-    20): gradients of the final E_k with respect to a seeded initial-velocity perturbation
-    (amplitude 1e-3 U0) and mu_inf in FP32 and FP64, checked against central differences of
-    the FP64 forward run; and the device time of one backward step (sllbm_adjoint_step)."""
+    20): gradients of the final E_k and of the final dissipation eps = eps_s + eps_c with
+    respect to a seeded initial-velocity perturbation (amplitude 1e-3 U0) and mu_inf, in FP64,
+    FP32 and FP32 with compensated moment sums ("f32_comp"), checked against central
+    differences of the FP64 forward run; and the device time of one backward step
+    (sllbm_adjoint_step)."""
     from paper_2012_05537_gb300 import adjoint as A
 
     w = I.WORKLOADS["tgv_16c_p3_adj"]
-    cfgs = {st: S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, courant=w.courant, storage=st)
-            for st in ("f64", "f32")}
+    cfgs = {st: S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, courant=w.courant, storage=st.split("_")[0])
+            for st in ("f64", "f32", "f32_comp")}
     rho, u, T = A.tgv_fields(cfgs["f64"], device=device)
     out = {"workload": w.name, "note": w.note, "steps": w.steps, "checkpoint_every": every}
     grads = {}
     for st, cfg in cfgs.items():
         sim = S.Sim(cfg, device=device)
+        if st == "f32_comp":
+            S.sllbm_set_compensated(sim.ctx, True)
         U0 = float(sim.info.U0)
         du = torch.as_tensor(1e-3 * U0 * I.noise(tuple(u.shape), 0), device=device)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        grads[st] = A.kinetic_energy_gradients(sim, rho, u, T, du, w.steps, every)
+        grads[st] = A.diagnostic_gradients(sim, rho, u, T, du, w.steps, every)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         # device time of the backward step alone
@@ -376,7 +425,7 @@ def adjoint_block(S, torch, device, hbm, every=20, timed=20):
         torch.cuda.synchronize()
         ms = ev[0].elapsed_time(ev[1]) / timed
         _, fwd = time_steps(sim, torch, timed)
-        bpn = 3 * 90 * ELEM_BYTES[st]  # read state and lambda, write lambda
+        bpn = 3 * 90 * ELEM_BYTES[st.split("_")[0]]  # read state and lambda, write lambda
         out[st] = {"gradients": grads[st], "wall_s_forward_and_backward": wall,
                    "adjoint_step_ms": ms, "forward_step_ms": statistics.median(fwd),
                    "adjoint_node_updates_per_s": sim.nodes / (ms / 1e3),
@@ -387,25 +436,89 @@ def adjoint_block(S, torch, device, hbm, every=20, timed=20):
     mu0 = float(sim.info.mu_inf)
     du = torch.as_tensor(1e-3 * float(sim.info.U0) * I.noise(tuple(u.shape), 0), device=device)
 
-    def ek(eps=0.0, mu=mu0):
+    def diag(e=0.0, mu=mu0):
         sim.set_mu_inf(mu)
-        sim.init_fields(rho, u + eps * du, T)
+        sim.init_fields(rho, u + e * du, T)
         sim.step(w.steps)
-        return sim.diag()[0]
+        d = sim.diag()
+        return d[0], d[1] + d[2]
 
     def central(fun, x, h):
-        d1 = (fun(x + h) - fun(x - h)) / (2 * h)
-        d2 = (fun(x + h / 2) - fun(x - h / 2)) / h
-        return (4 * d2 - d1) / 3
+        d1 = [(a - b) / (2 * h) for a, b in zip(fun(x + h), fun(x - h))]
+        d2 = [(a - b) / h for a, b in zip(fun(x + h / 2), fun(x - h / 2))]
+        return [(4 * b - a) / 3 for a, b in zip(d1, d2)]
 
-    fd = {"dEk_deps": central(lambda e: ek(eps=e), 0.0, 1.0),
-          "dEk_dmu_inf": central(lambda m: ek(mu=m), mu0, 1e-2 * mu0)}
+    de = central(lambda e: diag(e=e), 0.0, 1.0)
+    dm = central(lambda m: diag(mu=m), mu0, 1e-2 * mu0)
+    fd = {"dEk_deps": de[0], "dEk_dmu_inf": dm[0], "deps_deps": de[1], "deps_dmu_inf": dm[1]}
     sim.close()
     out["finite_differences_f64"] = fd
-    for st in ("f64", "f32"):
+    for st in cfgs:
         out[st]["rel_err_vs_fd"] = {k: abs(grads[st][k] - v) / abs(v) for k, v in fd.items()}
-    out["f32"]["rel_err_vs_f64"] = {k: abs(grads["f32"][k] - grads["f64"][k]) / abs(grads["f64"][k])
-                                    for k in fd}
+        if st != "f64":
+            out[st]["rel_err_vs_f64"] = {k: abs(grads[st][k] - grads["f64"][k]) / abs(grads["f64"][k])
+                                         for k in fd}
+    out["target_rel_err"] = 1e-4
+    return out
+
+
+def golden_curves(name):
+    """(steps, E_k, eps) rows of a stored oracle curve file under tests/golden (as text), or
+    None if it is absent."""
+    import numpy as np
+
+    path = os.path.join(ROOT, "tests", "golden", f"{name}_curves.txt")
+    if not os.path.exists(path):
+        return None
+    rows = np.array([[float(x) for x in line.split()] for line in open(path)
+                     if line.strip() and not line.startswith("#")])
+    return rows[:, 0].astype(int), rows[:, 1], rows[:, 2] + rows[:, 3]
+
+
+def long_run_block(S, torch, device, steps, every):
+    """The throughput mesh (128^3 nodes, Courant 4) with the Prandtl term on, in FP32 and FP64
+    for `steps` steps from the Taylor-Green state: kinetic energy E_k(t) and dissipation
+    eps(t) = eps_s + eps_c every `every` steps, the relative L2 of the FP32 curves against the
+    FP64 ones, and of both against the FP64 oracle's run of the same flow on 16^3 cells
+    (64^3 nodes) at the same time step (tests/golden/tgv_16c_p4_c2_curves.txt; a comparison
+    across resolutions, at the steps the file holds)."""
+    import numpy as np
+
+    w = I.WORKLOADS["tgv_32c_p4"]
+    gold = golden_curves("tgv_16c_p4_c2")
+    out = {"workload": w.name, "steps": steps, "every": every, "pr_correction": True,
+           "oracle_curves": "tgv_16c_p4_c2 (16^3 cells, p = 4, same dt, Prandtl term on)"}
+    curves = {}
+    for st in ("f64", "f32"):
+        sim = S.Sim(S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, Pr=w.Pr, gamma=w.gamma,
+                             courant=w.courant, pr_correction=True, storage=st), device=device)
+        sim.init_tgv()
+        rows = [[0] + list(sim.diag())]
+        kern = []
+        for k in range(every, steps + 1, every):
+            _, kk = time_steps(sim, torch, every, per_launch=(k == every))
+            kern.extend(kk)
+            rows.append([k] + list(sim.diag()))
+        rows = np.array(rows)
+        curves[st] = (rows[:, 0].astype(int), rows[:, 1], rows[:, 2] + rows[:, 3])
+        out[st] = {"kernel_ms": statistics.median(kern), "step_kernel": int(sim.info.step_kernel),
+                   "Ek_end": float(rows[-1, 1]), "eps_end": float(rows[-1, 2] + rows[-1, 3]),
+                   "finite": bool(np.isfinite(rows).all()),
+                   "eps_peak_step": int(rows[np.argmax(rows[:, 2] + rows[:, 3]), 0])}
+        sim.close()
+    out["f32_vs_f64_rel_l2"] = {"Ek_curve": rel_l2(curves["f32"][1], curves["f64"][1]),
+                                "eps_curve": rel_l2(curves["f32"][2], curves["f64"][2])}
+    if gold is not None:
+        ks, ek_o, eps_o = gold
+        for st in ("f64", "f32"):
+            idx = {int(k): n for n, k in enumerate(curves[st][0])}
+            sel = [n for n, k in enumerate(ks) if int(k) in idx]
+            if not sel:
+                continue
+            at = [idx[int(ks[n])] for n in sel]
+            out[st]["vs_oracle_16c"] = {"steps_compared": int(ks[sel[-1]]),
+                                        "Ek_curve_rel_l2": rel_l2(curves[st][1][at], ek_o[sel]),
+                                        "eps_curve_rel_l2": rel_l2(curves[st][2][at], eps_o[sel])}
     return out
 
 
@@ -564,6 +677,7 @@ def run_mine(args, rank, world, local):
     if dist is not None:
         dist.barrier()
     S.load()
+    alu = alu_peaks(S)
     w = I.WORKLOADS[args.workload]
     storage = args.storage or w.storage
     cfg = S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, Pr=w.Pr, gamma=w.gamma,
@@ -644,12 +758,26 @@ def run_mine(args, rank, world, local):
                            "kernel_ms": k64_ms,
                            "hbm_gbs_equiv": 2 * 45 * 2 * 8 * nodes / (k64_ms / 1e3) / 1e9,
                            "roofline": {"bound": "alu", "achieved": flops * nodes / (k64_ms / 1e3) / 1e12,
-                                        "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                                        "frac": flops * nodes / (k64_ms / 1e3) / 1e12 / FP64_NOMINAL_TFLOPS,
-                                        "peak_source": "nominal FP64 rate of the part",
+                                        "peak": alu["fp64_tflops"], "unit": "TFLOP/s",
+                                        "frac": flops * nodes / (k64_ms / 1e3) / 1e12 / alu["fp64_tflops"],
+                                        "peak_source": "measured (sllbm_fma_peak, FP64 FMA)",
                                         "algorithmic_flops_per_node": flops},
                            "steps": n64}
         sim64.close()
+        # the paper's Taylor-Green setting: the Prandtl term of App. D on
+        simpr = S.Sim(S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, Pr=w.Pr, gamma=w.gamma,
+                               courant=w.courant, pr_correction=True, storage=storage),
+                      device=f"cuda:{local}")
+        simpr.init_tgv()
+        simpr.step(3)
+        npr = 50
+        tpr, kpr = time_steps(simpr, torch, npr)
+        kpr_ms = statistics.mean(kpr)
+        variants["pr"] = {"pr_correction": True, "Pr": w.Pr, "value": nodes * npr / (tpr / 1e3),
+                          "ms_per_step": tpr / npr, "kernel_ms": kpr_ms,
+                          "step_kernel": int(simpr.info.step_kernel),
+                          "hbm_frac": bytes_per_node * nodes / (kpr_ms / 1e3) / 1e9 / hbm, "steps": npr}
+        simpr.close()
     if not args.no_variants and rank == 0 and args.batch_steps > 0:
         variants["batched"] = batch_block(S, torch, f"cuda:{local}", 64, args.batch_steps)
     if not args.no_variants and rank == 0 and not args.no_adjoint:
@@ -658,7 +786,9 @@ def run_mine(args, rank, world, local):
         variants["decomposed"] = decomposed_block(S, torch, f"cuda:{local}", w)
     if not args.no_variants and rank == 0 and args.mixed_steps > 0:
         variants["mixed"] = mixed_precision_block(S, torch, f"cuda:{local}", args.mixed_steps,
-                                                  args.mixed_every, hbm)
+                                                  args.mixed_every, hbm, alu)
+    if not args.no_variants and rank == 0 and args.long_steps > 0:
+        variants["long_run"] = long_run_block(S, torch, f"cuda:{local}", args.long_steps, args.long_every)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -681,6 +811,9 @@ def run_mine(args, rank, world, local):
                          "frac": achieved / hbm, "traffic": traffic,
                          "peak_source": peak_src, "kernel_ms": kern_avg_ms,
                          "algorithmic_bytes_per_node": bytes_per_node},
+            "roofline_alu": min_roofline(bytes_per_node, algorithmic_flops_per_node(w.p), nodes, kern_avg_ms, hbm,
+                                         alu["fp64_tflops"] if storage == "f64" else alu["fp32_tflops"]),
+            "alu_peaks": alu,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "finite": finite,
         }

@@ -388,6 +388,15 @@ int sllbm_adjoint_step(sllbm_ctx *ctx, const void *state_prev, const void *lam_n
  * entries are zero). */
 int sllbm_ek_adjoint(sllbm_ctx *ctx, const void *state, void *lam);
 
+/* lam = dJ/dstate at state for J = wk Ek + ws eps_s + wc eps_c, the Sec. III.C diagnostics
+ * as sllbm_diag defines and normalises them (the dissipation's gradient takes wk = 0,
+ * ws = wc = 1).  FP64 arithmetic: the node fields rho, u, T; per quadrature point of every
+ * cell the derivatives of its integrand with respect to the nine velocity-gradient entries
+ * (cell-local Lagrange derivatives) and to T (Sutherland law); per node the sum over the
+ * points whose integrand involves it, mapped to f and g through the moments.  Uses the
+ * reverse-mode scratch buffers (allocated on first use); lam in the adjoint type. */
+int sllbm_diag_adjoint(sllbm_ctx *ctx, const void *state, void *lam, double wk, double ws, double wc);
+
 /* Transpose of sllbm_init_fields (equilibrium populations of the FP64 fields rho[nodes],
  * u[3][nodes], T[nodes]): grad_rho[n], grad_u[3][nodes], grad_T[n] = derivatives of
  * sum(lam * init(rho, u, T)) with respect to rho, u, T at node n, FP64 device arrays,

@@ -10,7 +10,9 @@ library's kernels (PyTorch only holds the tensors and chains the calls):
   checkpoint (k states held at a time) and applies ``sllbm_adjoint_step`` step by step in
   reverse, accumulating the mu_inf sensitivity on the device;
 * :class:`KineticEnergy` -- state -> E_k of Sec. III.C (``sllbm_diag``; backward
-  ``sllbm_ek_adjoint``).
+  ``sllbm_ek_adjoint``);
+* :class:`Diagnostics` -- state -> (E_k, eps_s, eps_c) of Sec. III.C (``sllbm_diag``;
+  backward ``sllbm_diag_adjoint`` with the incoming gradient as the weights).
 
 mu_inf sets the relaxation time through tau = mu_inf (mu/mu_inf)(T)/(rho T dt) + 1/2; the
 sensitivity to the reference relaxation time tau_ref = mu_inf (mu/mu_inf)(T0)/(rho0 T0 dt)
@@ -128,6 +130,26 @@ class KineticEnergy(torch.autograd.Function):
         return lam * g.to(lam.dtype), None
 
 
+class Diagnostics(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, state, sim):
+        st = state.detach().to(sim.pop_dtype).contiguous()
+        sim.load_state(st)
+        d = S.sllbm_diag(sim.ctx)
+        ctx.sim = sim
+        ctx.save_for_backward(st)
+        return torch.tensor(d, dtype=torch.float64, device=sim.device)
+
+    @staticmethod
+    def backward(ctx, g):
+        sim = ctx.sim
+        (st,) = ctx.saved_tensors
+        w = [float(x) for x in g.detach().to("cpu", torch.float64)]
+        lam = torch.empty(st.shape, dtype=sim.adjoint_dtype, device=st.device)
+        S.sllbm_diag_adjoint(sim.ctx, st.data_ptr(), lam.data_ptr(), w[0], w[1], w[2])
+        return lam, None
+
+
 def tgv_fields(cfg: S.Config, device=None):
     """Taylor-Green initial fields (rho, u[3], T) at the nodes, FP64 on the device: the
     moments of the equilibrium state sllbm_init_tgv builds in an FP64 context."""
@@ -154,3 +176,24 @@ def kinetic_energy_gradients(sim: S.Sim, rho, u, T, du, steps: int, every: int, 
     dmu = float(mu.grad)
     return {"Ek": float(ek.detach()), "dEk_deps": float(eps.grad), "dEk_dmu_inf": dmu,
             "dEk_dtau_ref": dmu / dtau_ref_dmu(sim)}
+
+
+def diagnostic_gradients(sim: S.Sim, rho, u, T, du, steps: int, every: int, adjoint: str | None = None):
+    """E_k and the dissipation eps = eps_s + eps_c after `steps` steps from the equilibrium of
+    (rho, u + e du, T) at e = 0, with the gradient of each with respect to e and mu_inf: one
+    forward run, one reverse sweep per quantity (FP64 scalars in a dict)."""
+    if adjoint is not None:
+        sim.set_adjoint_type(adjoint)
+    e = torch.zeros((), dtype=torch.float64, device=sim.device, requires_grad=True)
+    mu = torch.tensor(float(sim.info.mu_inf), dtype=torch.float64, device=sim.device, requires_grad=True)
+    state0 = InitFields.apply(rho, u + e * du, T, sim)
+    stateN = Steps.apply(state0, mu, sim, steps, every)
+    d = Diagnostics.apply(stateN, sim)
+    out = {}
+    for name, wts in (("Ek", (1.0, 0.0, 0.0)), ("eps", (0.0, 1.0, 1.0))):
+        J = d @ torch.tensor(wts, dtype=torch.float64, device=sim.device)
+        ge, gm = torch.autograd.grad(J, (e, mu), retain_graph=True)
+        out[name] = float(J.detach())
+        out[f"d{name}_deps"] = float(ge)
+        out[f"d{name}_dmu_inf"] = float(gm)
+    return out

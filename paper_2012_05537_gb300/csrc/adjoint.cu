@@ -485,6 +485,169 @@ __global__ void __launch_bounds__(128) ek_seed_kernel(const CS* __restrict__ pop
     }
 }
 
+// ---- reverse mode of the Sec. III.C diagnostics ---------------------------------------
+// J = wk E_k + ws eps_s + wc eps_c as sllbm_diag computes it: per cell, the Clenshaw-Curtis
+// quadrature over its (p+1)^3 support points of rho|u|^2/2, mu~(T)|curl u|^2 and
+// (4/3) mu~(T)(div u)^2, with velocity gradients from the cell-local Lagrange derivative.
+// dJ/dpop in three gather kernels (no atomics): the node fields; per quadrature point the
+// derivatives of its integrand with respect to its nine gradient entries and to its
+// temperature; per node the sum over the quadrature points whose integrand involves it,
+// mapped to f and g through the moments.
+struct DiagAdjConst {
+    double xi[kQ][3];
+    double W[kMaxP + 1];
+    double D[kMaxP + 1][kMaxP + 1];  // D[a][j]: derivative of basis j at GLC point a
+};
+
+// rho, u, T (FP64, [5][nodes]) of a state in storage order.
+template <typename CS>
+__global__ void __launch_bounds__(128) node_fields_kernel(const CS* __restrict__ pop, long long nn, double inv_2cv,
+                                                          const __grid_constant__ AdjVel v, double* __restrict__ fld) {
+    for (long long n = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; n < nn;
+         n += static_cast<long long>(gridDim.x) * blockDim.x) {
+        double rho = 0, mx = 0, my = 0, mz = 0, e2 = 0;
+        for (int i = 0; i < kQ; ++i) {
+            const double f = static_cast<double>(pop[2 * (i * nn + n)]);
+            rho += f;
+            mx += f * v.xi[i][0];
+            my += f * v.xi[i][1];
+            mz += f * v.xi[i][2];
+            e2 += f * shell_xi2(shell_of(i)) + static_cast<double>(pop[2 * (i * nn + n) + 1]);
+        }
+        const double ux = mx / rho, uy = my / rho, uz = mz / rho;
+        fld[n] = rho;
+        fld[nn + n] = ux;
+        fld[2 * nn + n] = uy;
+        fld[3 * nn + n] = uz;
+        fld[4 * nn + n] = (e2 / rho - (ux * ux + uy * uy + uz * uz)) * inv_2cv;
+    }
+}
+
+// Per quadrature point (cell, local a, b, c): G[0..8] = dJ/d(du_comp/dx_dir) times the
+// derivative factor 2/h_dir (index comp*3 + dir), G[9] = dJ/dT at the point.
+template <int P>
+__global__ void __launch_bounds__(128) diag_point_adj_kernel(const double* __restrict__ fld, long long nn, int Nx,
+                                                             int Ny, int Nz, int ncx, int ncy, long long ncell,
+                                                             double hx, double hy, double hz, double ks, double kc,
+                                                             const __grid_constant__ DiagAdjConst dc,
+                                                             double* __restrict__ G) {
+    constexpr int P1 = P + 1, NPC = P1 * P1 * P1;
+    const double h[3] = {hx, hy, hz};
+    for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < ncell * NPC;
+         idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long cell = idx / NPC;
+        const int q = static_cast<int>(idx - cell * NPC);
+        const int loc[3] = {q % P1, (q / P1) % P1, q / (P1 * P1)};
+        const int c[3] = {static_cast<int>(cell % ncx), static_cast<int>((cell / ncx) % ncy),
+                          static_cast<int>(cell / (static_cast<long long>(ncx) * ncy))};
+        const int Nd[3] = {Nx, Ny, Nz};
+        double g[3][3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double acc[3] = {0, 0, 0};
+#pragma unroll
+            for (int j = 0; j < P1; ++j) {
+                int m[3];
+#pragma unroll
+                for (int e = 0; e < 3; ++e) m[e] = (c[e] * P + (e == d ? j : loc[e])) % Nd[e];
+                const long long node = (static_cast<long long>(m[2]) * Ny + m[1]) * Nx + m[0];
+#pragma unroll
+                for (int comp = 0; comp < 3; ++comp) acc[comp] += dc.D[loc[d]][j] * fld[(1 + comp) * nn + node];
+            }
+#pragma unroll
+            for (int comp = 0; comp < 3; ++comp) g[comp][d] = acc[comp] * 2.0 / h[d];
+        }
+        const long long nq = (static_cast<long long>((c[2] * P + loc[2]) % Nz) * Ny + (c[1] * P + loc[1]) % Ny) * Nx +
+                             (c[0] * P + loc[0]) % Nx;
+        const double T = fld[4 * nn + nq];
+        const double wq = dc.W[loc[0]] * dc.W[loc[1]] * dc.W[loc[2]] * hx * hy * hz * 0.125;
+        const double ox = g[2][1] - g[1][2], oy = g[0][2] - g[2][0], oz = g[1][0] - g[0][1];
+        const double dv = g[0][0] + g[1][1] + g[2][2];
+        const double mut = sutherland(T);
+        const double wm = wq * mut;
+        double* out = G + idx * 10;
+        // d|curl u|^2 / d g[comp][dir] and d(div u)^2 / d g[comp][dir]
+        const double dcurl[3][3] = {{0.0, -2.0 * oz, 2.0 * oy}, {2.0 * oz, 0.0, -2.0 * ox}, {-2.0 * oy, 2.0 * ox, 0.0}};
+#pragma unroll
+        for (int comp = 0; comp < 3; ++comp)
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                out[comp * 3 + d] = wm * (ks * dcurl[comp][d] + (comp == d ? kc * 2.0 * dv : 0.0)) * 2.0 / h[d];
+        out[9] = wq * mut * sutherland_dlog(T) * (ks * (ox * ox + oy * oy + oz * oz) + kc * dv * dv);
+    }
+}
+
+// Per node: the point terms of every quadrature point whose integrand involves the node
+// (the node's own point in each cell that holds it, and the points on its lines in those
+// cells), the kinetic-energy term, then lam_f_i = a_rho + a_u.(xi_i - u)/rho +
+// a_T (|xi_i - u|^2 - 2 C_v T)/(2 C_v rho) and lam_g_i = a_T/(2 C_v rho).
+template <int P, typename C>
+__global__ void __launch_bounds__(128) diag_node_adj_kernel(const double* __restrict__ fld, const double* __restrict__ G,
+                                                            long long nn, int Nx, int Ny, int ncx, int ncy, int ncz,
+                                                            double hx, double hy, double hz, double ke, double two_cv,
+                                                            const __grid_constant__ DiagAdjConst dc,
+                                                            C* __restrict__ lam) {
+    constexpr int P1 = P + 1, NPC = P1 * P1 * P1;
+    const long long sxy = static_cast<long long>(Nx) * Ny;
+    for (long long n = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; n < nn;
+         n += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int x[3] = {static_cast<int>(n % Nx), static_cast<int>((n / Nx) % Ny), static_cast<int>(n / sxy)};
+        const int nc[3] = {ncx, ncy, ncz};
+        // the (cell, local index) pairs that hold the node, per direction: one, or two for a
+        // cell-face node (local 0 of its cell and local P of the cell before, periodically)
+        int cc[3][2], aa[3][2], cnt[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            cc[d][0] = x[d] / P;
+            aa[d][0] = x[d] % P;
+            cnt[d] = 1;
+            if (aa[d][0] == 0) {
+                cc[d][1] = (cc[d][0] + nc[d] - 1) % nc[d];
+                aa[d][1] = P;
+                cnt[d] = 2;
+            }
+        }
+        const double rho = fld[n], ux = fld[nn + n], uy = fld[2 * nn + n], uz = fld[3 * nn + n], T = fld[4 * nn + n];
+        double a_rho = 0, a_u[3] = {0, 0, 0}, a_T = 0;
+        const double hv = hx * hy * hz * 0.125;
+        for (int kz = 0; kz < cnt[2]; ++kz)
+            for (int ky = 0; ky < cnt[1]; ++ky)
+                for (int kx = 0; kx < cnt[0]; ++kx) {
+                    const int lc[3] = {aa[0][kx], aa[1][ky], aa[2][kz]};
+                    const long long base =
+                        ((static_cast<long long>(cc[2][kz]) * ncy + cc[1][ky]) * ncx + cc[0][kx]) * NPC;
+                    const long long q0 = base + (lc[2] * P1 + lc[1]) * P1 + lc[0];
+                    a_T += G[q0 * 10 + 9];
+                    const double wq = dc.W[lc[0]] * dc.W[lc[1]] * dc.W[lc[2]] * hv;
+                    a_rho += ke * wq * 0.5 * (ux * ux + uy * uy + uz * uz);
+                    a_u[0] += ke * wq * rho * ux;
+                    a_u[1] += ke * wq * rho * uy;
+                    a_u[2] += ke * wq * rho * uz;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+                        for (int j = 0; j < P1; ++j) {
+                            int m[3] = {lc[0], lc[1], lc[2]};
+                            m[d] = j;
+                            const double* gq = G + (base + (m[2] * P1 + m[1]) * P1 + m[0]) * 10;
+                            const double dw = dc.D[j][lc[d]];
+                            a_u[0] += gq[0 * 3 + d] * dw;
+                            a_u[1] += gq[1 * 3 + d] * dw;
+                            a_u[2] += gq[2 * 3 + d] * dw;
+                        }
+                    }
+                }
+        const double inv_rho = 1.0 / rho, aT = a_T / (two_cv * rho);
+        for (int i = 0; i < kQ; ++i) {
+            const double cx = dc.xi[i][0] - ux, cy = dc.xi[i][1] - uy, cz = dc.xi[i][2] - uz;
+            const double lf = a_rho + (a_u[0] * cx + a_u[1] * cy + a_u[2] * cz) * inv_rho +
+                              aT * (cx * cx + cy * cy + cz * cz - two_cv * T);
+            lam[2 * (i * nn + n)] = static_cast<C>(lf);
+            lam[2 * (i * nn + n) + 1] = static_cast<C>(aT);
+        }
+    }
+}
+
 // Transpose of the equilibrium initialisation f_i = w_i rho P_i, g_i = (2C_v - D) T f_i at
 // each node (FP64 arithmetic, as the initialisation itself).
 template <typename C>
@@ -813,6 +976,59 @@ int sllbm_ek_adjoint(sllbm_ctx* ctx, const void* state, void* lam) {
                                                                     static_cast<float*>(lam), ctx->nn, ctx->N[0],
                                                                     ctx->N[1], ctx->p, scale, kc);
     ctx->launches += 1;
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SLLBM_OK : adj_fail(ctx, e);
+}
+
+int sllbm_diag_adjoint(sllbm_ctx* ctx, const void* state, void* lam, double wk, double ws, double wc) {
+    if (ctx == nullptr || state == nullptr || lam == nullptr) return SLLBM_EINVAL;
+    if (!adjoint_supported(ctx)) return SLLBM_EINVAL;
+    int rc = ensure_adjoint_scratch(ctx);
+    if (rc != SLLBM_OK) return rc;
+    DiagAdjConst dc;
+    std::memcpy(dc.xi, ctx->xi, sizeof(dc.xi));
+    clenshaw_curtis(ctx->p, dc.W);
+    diff_matrix(ctx->p, dc.D);
+    const long long ncell = static_cast<long long>(ctx->cells[0]) * ctx->cells[1] * ctx->cells[2];
+    const int P1 = ctx->p + 1;
+    const long long npts = ncell * P1 * P1 * P1;
+    // scratch: the node fields (5 doubles per node) and the point terms (10 per quadrature
+    // point) fit the two state-sized reverse-mode buffers (at least 360 bytes per node)
+    if (static_cast<size_t>(5 * ctx->nn) * sizeof(double) > ctx->adj_bytes ||
+        static_cast<size_t>(10 * npts) * sizeof(double) > ctx->adj_bytes)
+        return SLLBM_EINVAL;
+    double* fld = static_cast<double*>(ctx->adj_buf[0]);
+    double* G = static_cast<double*>(ctx->adj_buf[1]);
+    const double vol = ctx->L[0] * ctx->L[1] * ctx->L[2];
+    const double base = vol * ctx->prm.rho0 * ctx->U0 * ctx->U0;
+    const double ke = wk / base, ks = ws / (base * ctx->prm.Re), kc = wc * 4.0 / 3.0 / (base * ctx->prm.Re);
+    const double inv_2cv = 0.5 * (ctx->prm.gamma - 1.0), two_cv = 1.0 / inv_2cv;
+    const AdjVel v = adj_vel(ctx);
+    if (ctx->prm.storage == SLLBM_F64)
+        node_fields_kernel<double><<<adj_grid(ctx->nn, 128), 128, 0, ctx->stream>>>(
+            static_cast<const double*>(state), ctx->nn, inv_2cv, v, fld);
+    else
+        node_fields_kernel<float><<<adj_grid(ctx->nn, 128), 128, 0, ctx->stream>>>(
+            static_cast<const float*>(state), ctx->nn, inv_2cv, v, fld);
+    const bool f64 = ctx->prm.storage == SLLBM_F64 || ctx->adj_f64;
+    auto run = [&](auto pc) {
+        constexpr int P = decltype(pc)::value;
+        diag_point_adj_kernel<P><<<adj_grid(npts, 128), 128, 0, ctx->stream>>>(
+            fld, ctx->nn, ctx->N[0], ctx->N[1], ctx->N[2], ctx->cells[0], ctx->cells[1], ncell, ctx->h[0], ctx->h[1],
+            ctx->h[2], ks, kc, dc, G);
+        if (f64)
+            diag_node_adj_kernel<P, double><<<adj_grid(ctx->nn, 128), 128, 0, ctx->stream>>>(
+                fld, G, ctx->nn, ctx->N[0], ctx->N[1], ctx->cells[0], ctx->cells[1], ctx->cells[2], ctx->h[0],
+                ctx->h[1], ctx->h[2], ke, two_cv, dc, static_cast<double*>(lam));
+        else
+            diag_node_adj_kernel<P, float><<<adj_grid(ctx->nn, 128), 128, 0, ctx->stream>>>(
+                fld, G, ctx->nn, ctx->N[0], ctx->N[1], ctx->cells[0], ctx->cells[1], ctx->cells[2], ctx->h[0],
+                ctx->h[1], ctx->h[2], ke, two_cv, dc, static_cast<float*>(lam));
+    };
+    if (ctx->p == 2) run(std::integral_constant<int, 2>{});
+    else if (ctx->p == 3) run(std::integral_constant<int, 3>{});
+    else run(std::integral_constant<int, 4>{});
+    ctx->launches += 3;
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SLLBM_OK : adj_fail(ctx, e);
 }

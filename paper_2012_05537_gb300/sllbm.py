@@ -133,6 +133,7 @@ def load(build_if_missing: bool = False):
         "sllbm_set_adjoint_type": (ctypes.c_int, [vp, ctypes.c_int]),
         "sllbm_adjoint_step": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "sllbm_ek_adjoint": (ctypes.c_int, [vp, vp, vp]),
+        "sllbm_diag_adjoint": (ctypes.c_int, [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
         "sllbm_init_fields_adjoint": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp]),
         "sllbm_set_wait_limit": (ctypes.c_int, [vp, ctypes.c_double]),
         "sllbm_request_abort": (ctypes.c_int, [vp, ctypes.c_int]),
@@ -453,6 +454,11 @@ def sllbm_adjoint_step(ctx, state_prev_ptr: int, lam_next_ptr: int, lam_prev_ptr
 def sllbm_ek_adjoint(ctx, state_ptr: int, lam_ptr: int) -> None:
     _check(load().sllbm_ek_adjoint(ctx, ctypes.c_void_p(state_ptr), ctypes.c_void_p(lam_ptr)),
            "sllbm_ek_adjoint", ctx)
+
+
+def sllbm_diag_adjoint(ctx, state_ptr: int, lam_ptr: int, wk: float, ws: float, wc: float) -> None:
+    _check(load().sllbm_diag_adjoint(ctx, ctypes.c_void_p(state_ptr), ctypes.c_void_p(lam_ptr), float(wk),
+                                     float(ws), float(wc)), "sllbm_diag_adjoint", ctx)
 
 
 def sllbm_init_fields_adjoint(ctx, rho_ptr: int, u_ptr: int, T_ptr: int, lam_ptr: int,

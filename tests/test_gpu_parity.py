@@ -6,11 +6,14 @@ Tolerances (written here, derived from the arithmetic):
     algebra in double precision with different summation orders; one step perturbs each
     value by a few ulps (~1e-15).
   * FP32 path: FP32 unit round-off is 6e-8; one step sums 3(p+1) weighted values per
-    pass (Lebesgue constant of the GLC points <= 2 for p <= 4) and a few collision
-    terms, so per-element errors stay below ~1e-6 relative to the local population
-    scale; relative L2 <= 1e-6 after one step, <= 3e-5 after 50 steps.  At Ma 1.25 the
-    equilibrium quartic has terms up to s^4/24 ~ 45 (s = |xi||u| <= 5.7) that cancel
-    to O(1), which amplifies FP32 round-off; the bound there is 4e-6 of the scale.
+    pass and a few collision terms.  The 1D sums of |weights| at the departure points stay
+    below the Lebesgue constant of the p <= 4 Gauss-Lobatto-Chebyshev points (5/3 at p = 3),
+    their 3D products below about 4 on these meshes, so rounding errors of a few 1e-7 of
+    the local population scale per element are expected, and their root mean square is
+    lower; relative L2 <= 1e-6 after one step is a bound with margin, <= 3e-5 after 50 steps.
+    At Ma 1.25 the equilibrium quartic has terms up to s^4/24 ~ 45 (s = |xi||u| <= 5.7) that
+    cancel to O(1): rounding of 6e-8 on terms 45 times the result is 2.7e-6 of the scale,
+    hence the 4e-6 bound there.
 Inputs come from the oracle (equilibrium of seeded fields, seeded noise) or from the
 paper's Taylor-Green definition evaluated independently on each side.
 """

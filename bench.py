@@ -578,7 +578,10 @@ def decomposed_block(S, torch, device, w, parts=2, steps=50):
     g, p = steppers[0].ghost, w.p
     inner = [st.sim.populations()[:, :, g * p:(g + st.sim.cfg.slab[1]) * p] for st in steppers]
     equal = bool(torch.equal(torch.cat(inner, dim=2), ref))
-    halo = sum(4 * st.halo_bytes for st in steppers)  # pack + unpack, both sides
+    # pack + unpack of both sides; beside it what whole ghost widths for every velocity moved
+    halo = sum(2 * (st.sizes["send_low"] + st.sizes["send_high"]) for st in steppers)
+    plane = 2 * 45 * ELEM_BYTES["f32"] * w.N[0] * w.N[1] // 45
+    halo_full = sum(4 * 45 * g_ * p_ * plane for g_, p_ in [(st.ghost, w.p) for st in steppers])
     for st in steppers:
         st.sim.close()
     nodes = w.nodes
@@ -586,6 +589,7 @@ def decomposed_block(S, torch, device, w, parts=2, steps=50):
             "whole_mesh_ms_per_step": whole_ms, "slabs_ms_per_step": slab_ms,
             "slabs_overlapped_ms_per_step": overlap_ms,
             "exchange_ms_per_step": exch_ms, "halo_copy_bytes_per_step": halo,
+            "halo_copy_bytes_per_step_whole_ghost_width": halo_full,
             "slabs_value": nodes / (slab_ms / 1e3), "whole_value": nodes / (whole_ms / 1e3),
             "bit_equal_to_whole_mesh": equal,
             "note": "one GPU: the slab contexts exchange by device copies; across GPUs the same "

@@ -152,13 +152,19 @@ int sllbm_create(const sllbm_mesh *mesh, int p, sllbm_velset vs, const sllbm_par
  * the whole mesh (cell z_begin - ghost first, periodic), so sllbm_init_tgv and
  * sllbm_init_fields set the slab's part of the whole-mesh fields, and sllbm_step updates
  * the interior planes only (generic tile kernel).  Before every step the caller refreshes
- * the halos: sllbm_halo_pack(side 0) copies the lowest `ghost` interior cells of the
- * current state to a device buffer for the slab below, sllbm_halo_pack(side 1) the
- * highest ones for the slab above; sllbm_halo_unpack(side 0 / 1) writes a buffer received
- * from the slab below / above into the ghost cells below / above.  Halo buffers hold
- * halo_bytes (sllbm_slab_info) in the order [i][plane][y][x][h], device memory owned by
- * the caller; both calls are one asynchronous copy on cuda_stream (a cudaStream_t as void*;
- * NULL: the context's stream).
+ * the halos: sllbm_halo_pack(side 0) copies lowest interior planes of the current state to
+ * a device buffer for the slab below, sllbm_halo_pack(side 1) highest ones for the slab
+ * above; sllbm_halo_unpack(side 0 / 1) writes a buffer received from the slab below / above
+ * into the ghost planes below / above.  Only the planes a velocity's source boxes reach
+ * are moved: with kmin and kmin + span the smallest and largest departure cell shift of
+ * velocity i along z, the ghost region below holds -kmin cells of it (kmin < 0) and the
+ * one above (kmin + span) cells plus the shared face plane (kmin + span >= 0); its other
+ * ghost planes are never read.  A packed buffer holds, velocity after velocity, those
+ * planes in the order [plane][y][x][h]: sllbm_slab_halo_bytes(side) bytes for what
+ * sllbm_halo_pack(side) writes and the neighbour's sllbm_halo_unpack(1 - side) reads
+ * (halo_bytes of sllbm_slab_info is the larger of the two sides); device memory owned by
+ * the caller; both calls are one asynchronous kernel launch on cuda_stream (a cudaStream_t
+ * as void*; NULL: the context's stream).
  *
  * To overlap the exchange with the step, split it: sllbm_step_begin launches the tiles
  * whose source cells are all interior (they read no ghost cell; nothing is swapped yet),
@@ -178,6 +184,7 @@ int sllbm_create(const sllbm_mesh *mesh, int p, sllbm_velset vs, const sllbm_par
 int sllbm_create_slab(const sllbm_mesh *mesh, int p, sllbm_velset vs, const sllbm_params *prm,
                       int z_begin, int z_cells, void *cuda_stream, sllbm_ctx **out);
 int sllbm_slab_info(const sllbm_ctx *ctx, int *ghost_cells, size_t *halo_bytes);
+int sllbm_slab_halo_bytes(const sllbm_ctx *ctx, int side, size_t *bytes);
 int sllbm_halo_pack(sllbm_ctx *ctx, int side, void *halo, void *cuda_stream);
 int sllbm_halo_unpack(sllbm_ctx *ctx, int side, const void *halo, void *cuda_stream);
 int sllbm_step_begin(sllbm_ctx *ctx);

@@ -622,25 +622,88 @@ int create_ctx(const sllbm_mesh* mesh, int p, sllbm_velset vs, const sllbm_param
     return SLLBM_OK;
 }
 
-// The planes [plane0, plane0 + ghost p) of every velocity of the current state <-> a packed
-// halo buffer [i][plane][y][x][h]: one strided copy of 45 chunks.
+// Per velocity: the first state plane of its chunk and its plane count, and the chunk's
+// offset in the packed halo buffer (4-byte words; a plane of (f, g) pairs is a whole number
+// of words).
+struct HaloMap {
+    int plane0[kQ];
+    int planes[kQ];
+    long long packed_word[kQ];
+};
+
+// Copies each velocity's chunk of planes between the state and the packed halo buffer
+// (to_state: packed -> state); blockIdx.y is the velocity.
+__global__ void __launch_bounds__(256) halo_copy_kernel(unsigned* __restrict__ state, unsigned* __restrict__ halo,
+                                                         long long plane_words, long long vstride_words,
+                                                         int to_state, const __grid_constant__ HaloMap m) {
+    const int i = blockIdx.y;
+    const long long n = static_cast<long long>(m.planes[i]) * plane_words;
+    unsigned* sp = state + i * vstride_words + static_cast<long long>(m.plane0[i]) * plane_words;
+    unsigned* hp = halo + m.packed_word[i];
+    for (long long k = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; k < n;
+         k += static_cast<long long>(gridDim.x) * blockDim.x) {
+        if (to_state) sp[k] = hp[k];
+        else hp[k] = sp[k];
+    }
+}
+
+// Planes of velocity i in the ghost region on `side` that the step reads (0 below, 1
+// above), from its departure cell shifts along z: a tile's source box starts kmin cells
+// below its first cell and ends with the first node of the cell kmin + span + 1 above its
+// last one, so below the slab it reads -kmin cells (when kmin < 0) and above it
+// (kmin + span) cells plus one plane (when kmin + span >= 0).
+int ghost_planes(const sllbm_ctx* c, int i, int side) {
+    int kmn = 1 << 20, kmx = -(1 << 20);
+    for (int a = 0; a < c->p; ++a) {
+        const int k = c->dir[2].shift[i][a];
+        kmn = k < kmn ? k : kmn;
+        kmx = k > kmx ? k : kmx;
+    }
+    if (side == 0) return kmn < 0 ? -kmn * c->p : 0;
+    return kmx >= 0 ? kmx * c->p + 1 : 0;
+}
+
+// Bytes of the packed halo sllbm_halo_pack(side) writes (the receiving slab's ghost region
+// on the other side).
+size_t halo_pack_bytes(const sllbm_ctx* c, int side) {
+    const size_t plane_bytes = static_cast<size_t>(c->N[0]) * c->N[1] * 2 * c->elem;
+    size_t planes = 0;
+    for (int i = 0; i < kQ; ++i) planes += static_cast<size_t>(ghost_planes(c, i, 1 - side));
+    return planes * plane_bytes;
+}
+
+// Packing (to_state = 0) copies, per velocity, the interior planes next to `side` that the
+// neighbouring slab on that side reads as its ghost planes; unpacking (to_state = 1) writes a
+// neighbour's packed planes into this slab's ghost planes on `side` -- only the planes each
+// velocity's source boxes reach, not the whole ghost width.
 int halo_copy(sllbm_ctx* ctx, int side, void* halo, int to_state, cudaStream_t stream) {
     if (ctx == nullptr || !ctx->slab || halo == nullptr || (side != 0 && side != 1)) return SLLBM_EINVAL;
     if (ctx->buf[ctx->cur] == nullptr) return SLLBM_EINVAL;
     const int gp = ctx->ghost * ctx->p;
-    // packing (to_state = 0) reads the interior cells next to the side; unpacking writes the
-    // ghost cells on that side
-    const int plane0 = to_state ? (side == 0 ? 0 : (ctx->ghost + ctx->cells[2]) * ctx->p)
-                                : (side == 0 ? gp : ctx->cells[2] * ctx->p);
-    const size_t plane_bytes = static_cast<size_t>(ctx->N[0]) * ctx->N[1] * 2 * ctx->elem;
-    const size_t chunk = static_cast<size_t>(gp) * plane_bytes;
-    const size_t vstride = static_cast<size_t>(ctx->N[2]) * plane_bytes;
-    unsigned char* state = static_cast<unsigned char*>(ctx->buf[ctx->cur]) + static_cast<size_t>(plane0) * plane_bytes;
-    cudaError_t e = to_state ? cudaMemcpy2DAsync(state, vstride, halo, chunk, chunk, kQ, cudaMemcpyDeviceToDevice,
-                                                 stream)
-                             : cudaMemcpy2DAsync(halo, chunk, state, vstride, chunk, kQ, cudaMemcpyDeviceToDevice,
-                                                 stream);
-    CK(ctx, e);
+    const int top = gp + ctx->cells[2] * ctx->p;  // first plane above the interior
+    const long long plane_words = static_cast<long long>(ctx->N[0]) * ctx->N[1] * 2 * ctx->elem / 4;
+    HaloMap m;
+    long long off = 0;
+    int most = 0;
+    for (int i = 0; i < kQ; ++i) {
+        // pack(side) serves the neighbour's ghost region on the other side; unpack(side)
+        // fills this slab's ghost region on `side`
+        const int n = ghost_planes(ctx, i, to_state ? side : 1 - side);
+        m.planes[i] = n;
+        m.plane0[i] = to_state ? (side == 0 ? gp - n : top) : (side == 0 ? gp : top - n);
+        m.packed_word[i] = off;
+        off += static_cast<long long>(n) * plane_words;
+        most = n > most ? n : most;
+    }
+    if (most == 0) return SLLBM_OK;
+    const long long per = static_cast<long long>(most) * plane_words;
+    long long bx = (per + 255) / 256;
+    if (bx > 1024) bx = 1024;
+    halo_copy_kernel<<<dim3(static_cast<unsigned>(bx), kQ), 256, 0, stream>>>(
+        static_cast<unsigned*>(ctx->buf[ctx->cur]), static_cast<unsigned*>(halo), plane_words,
+        static_cast<long long>(ctx->N[2]) * plane_words, to_state, m);
+    ctx->launches += 1;
+    CK(ctx, cudaGetLastError());
     return SLLBM_OK;
 }
 
@@ -661,8 +724,16 @@ int sllbm_create_slab(const sllbm_mesh* mesh, int p, sllbm_velset vs, const sllb
 int sllbm_slab_info(const sllbm_ctx* ctx, int* ghost_cells, size_t* halo_bytes) {
     if (ctx == nullptr || !ctx->slab) return SLLBM_EINVAL;
     if (ghost_cells != nullptr) *ghost_cells = ctx->ghost;
-    if (halo_bytes != nullptr)
-        *halo_bytes = static_cast<size_t>(kQ) * ctx->ghost * ctx->p * ctx->N[0] * ctx->N[1] * 2 * ctx->elem;
+    if (halo_bytes != nullptr) {
+        const size_t b0 = halo_pack_bytes(ctx, 0), b1 = halo_pack_bytes(ctx, 1);
+        *halo_bytes = b0 > b1 ? b0 : b1;
+    }
+    return SLLBM_OK;
+}
+
+int sllbm_slab_halo_bytes(const sllbm_ctx* ctx, int side, size_t* bytes) {
+    if (ctx == nullptr || !ctx->slab || (side != 0 && side != 1) || bytes == nullptr) return SLLBM_EINVAL;
+    *bytes = halo_pack_bytes(ctx, side);
     return SLLBM_OK;
 }
 

@@ -70,7 +70,15 @@ void fill_tables_s(const sllbm_ctx* ctx, StepTablesS<P>* t) {
 template <int P>
 bool tma_eligible_p(const sllbm_ctx* c) {
     using T = TmaTile<P>;
-    return c->cells[0] % T::CX == 0 && c->cells[1] % T::CY == 0 && c->cells[2] % T::CZ == 0;
+    if (c->cells[0] % T::CX != 0 || c->cells[1] % T::CY != 0 || c->cells[2] % T::CZ != 0) return false;
+    // the passes are compiled per first local node of the upper departure cell: the shifts of
+    // a cell's local nodes must not decrease with the node (they do not: the support points
+    // are ordered, and so are their departure points)
+    for (int d = 0; d < 3; ++d)
+        for (int i = 0; i < kQ; ++i)
+            for (int a = 1; a < P; ++a)
+                if (c->dir[d].shift[i][a] < c->dir[d].shift[i][a - 1]) return false;
+    return true;
 }
 
 // Builds (or reuses) the TMA descriptors of a source buffer: the buffer seen as a 4D FP32

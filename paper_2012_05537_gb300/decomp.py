@@ -57,9 +57,13 @@ class SlabStepper:
         from . import sllbm as S
         self.sim, self.rank, self.world, self.group = sim, rank, world, group
         self.ghost, self.halo_bytes = S.sllbm_slab_info(sim.ctx)
+        # what goes down (the neighbour's ghost planes above) and what goes up differ in
+        # size: each velocity's halo holds only the planes its source boxes reach
+        down, up = S.sllbm_slab_halo_bytes(sim.ctx, 0), S.sllbm_slab_halo_bytes(sim.ctx, 1)
+        self.sizes = {"send_low": down, "recv_high": down, "send_high": up, "recv_low": up}
         torch = sim.torch
-        self.bufs = {k: torch.empty(self.halo_bytes, dtype=torch.uint8, device=sim.device)
-                     for k in ("send_low", "send_high", "recv_low", "recv_high")}
+        self.bufs = {k: torch.empty(max(n, 1), dtype=torch.uint8, device=sim.device)[:n]
+                     for k, n in self.sizes.items()}
 
     def pack(self, stream=None) -> None:
         from . import sllbm as S

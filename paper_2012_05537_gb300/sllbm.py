@@ -88,6 +88,7 @@ def load(build_if_missing: bool = False):
                                              ctypes.POINTER(Params), ctypes.c_int, ctypes.c_int, vp,
                                              ctypes.POINTER(vp)]),
         "sllbm_slab_info": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)]),
+        "sllbm_slab_halo_bytes": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
         "sllbm_halo_pack": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
         "sllbm_halo_unpack": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
         "sllbm_step_begin": (ctypes.c_int, [vp]),
@@ -195,6 +196,13 @@ def sllbm_slab_info(ctx):
     g, b = ctypes.c_int(), ctypes.c_size_t()
     _check(load().sllbm_slab_info(ctx, ctypes.byref(g), ctypes.byref(b)), "sllbm_slab_info", ctx)
     return int(g.value), int(b.value)
+
+
+def sllbm_slab_halo_bytes(ctx, side: int) -> int:
+    """Bytes sllbm_halo_pack(side) writes (the neighbour's sllbm_halo_unpack(1 - side) reads)."""
+    b = ctypes.c_size_t()
+    _check(load().sllbm_slab_halo_bytes(ctx, int(side), ctypes.byref(b)), "sllbm_slab_halo_bytes", ctx)
+    return int(b.value)
 
 
 def sllbm_halo_pack(ctx, side: int, halo_ptr: int, stream: int = 0) -> None:

@@ -16,7 +16,9 @@ sys.path.insert(0, ROOT)
 
 from paper_2012_05537_gb300 import decomp as D  # noqa: E402
 
-Z, GHOST, K = 10, 2, 3  # mesh cells along z, halo cells per side, values per cell
+# mesh cells along z, halo cells below and above a slab (unequal, as when each velocity's
+# halo holds only the planes its departure points reach), values per cell
+Z, GLOW, GHIGH, K = 10, 2, 1, 3
 
 
 def _free_port():
@@ -33,11 +35,13 @@ def _cells(first: int, count: int) -> torch.Tensor:
 
 def _exchange_on_rank(rank: int, world: int):
     z0, zc = D.slab_bounds(Z, world, rank)
-    send_low, send_high = _cells(z0, GHOST), _cells(z0 + zc - GHOST, GHOST)
-    recv_low, recv_high = torch.full_like(send_low, -1.0), torch.full_like(send_high, -1.0)
+    # down: the lowest cells, which the slab below keeps as its halo above (GHIGH cells);
+    # up: the highest cells, the halo below of the slab above (GLOW cells)
+    send_low, send_high = _cells(z0, GHIGH), _cells(z0 + zc - GLOW, GLOW)
+    recv_low, recv_high = torch.full_like(send_high, -1.0), torch.full_like(send_low, -1.0)
     D.exchange(send_low, send_high, recv_low, recv_high, rank, world)
-    return (recv_low.numpy(), recv_high.numpy(), _cells(z0 - GHOST, GHOST).numpy(),
-            _cells(z0 + zc, GHOST).numpy())
+    return (recv_low.numpy(), recv_high.numpy(), _cells(z0 - GLOW, GLOW).numpy(),
+            _cells(z0 + zc, GHIGH).numpy())
 
 
 def _worker(rank, world, port, out):

@@ -522,10 +522,10 @@ def long_run_block(S, torch, device, steps, every):
     return out
 
 
-def decomposed_block(S, torch, device, w, parts=2, steps=50):
+def decomposed_block(S, torch, device, w, parts=2, steps=50, kernel=1):
     """The workload's mesh as `parts` z-slabs on this one GPU, advanced with one halo
     exchange per step (device copies between the slab contexts), against the undivided mesh
-    on the same generic kernel: step times with the exchange before the step and overlapped
+    on the same kernel (generic or TMA-fed): step times with the exchange before the step and overlapped
     with it (a second stream), the exchange alone, the halo bytes moved per step, and whether
     the slabs end bit for bit equal to the whole mesh."""
     import dataclasses
@@ -533,7 +533,7 @@ def decomposed_block(S, torch, device, w, parts=2, steps=50):
     from paper_2012_05537_gb300 import decomp as D
 
     cfg = S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, Pr=w.Pr, gamma=w.gamma, courant=w.courant,
-                   storage="f32", kernel=1)
+                   storage="f32", kernel=kernel)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     whole = S.Sim(cfg, device=device)
     whole.init_tgv()
@@ -585,7 +585,8 @@ def decomposed_block(S, torch, device, w, parts=2, steps=50):
     for st in steppers:
         st.sim.close()
     nodes = w.nodes
-    return {"workload": w.name, "parts": parts, "ghost_cells": g, "steps": steps,
+    return {"workload": w.name, "kernel": "TMA-fed" if kernel == 2 else "generic", "parts": parts,
+            "ghost_cells": g, "steps": steps,
             "whole_mesh_ms_per_step": whole_ms, "slabs_ms_per_step": slab_ms,
             "slabs_overlapped_ms_per_step": overlap_ms,
             "exchange_ms_per_step": exch_ms, "halo_copy_bytes_per_step": halo,
@@ -787,7 +788,8 @@ def run_mine(args, rank, world, local):
     if not args.no_variants and rank == 0 and not args.no_adjoint:
         variants["adjoint"] = adjoint_block(S, torch, f"cuda:{local}", hbm)
     if not args.no_variants and rank == 0 and storage == "f32":
-        variants["decomposed"] = decomposed_block(S, torch, f"cuda:{local}", w)
+        variants["decomposed"] = {"generic": decomposed_block(S, torch, f"cuda:{local}", w, kernel=1),
+                                  "tma": decomposed_block(S, torch, f"cuda:{local}", w, kernel=2)}
     if not args.no_variants and rank == 0 and args.mixed_steps > 0:
         variants["mixed"] = mixed_precision_block(S, torch, f"cuda:{local}", args.mixed_steps,
                                                   args.mixed_every, hbm, alu)

@@ -151,7 +151,9 @@ int sllbm_create(const sllbm_mesh *mesh, int p, sllbm_velset vs, const sllbm_par
  * N[2] = (z_cells + 2 ghost) p planes in the usual layout, with the z-cells numbered on
  * the whole mesh (cell z_begin - ghost first, periodic), so sllbm_init_tgv and
  * sllbm_init_fields set the slab's part of the whole-mesh fields, and sllbm_step updates
- * the interior planes only (generic tile kernel).  Before every step the caller refreshes
+ * the interior planes only (the generic tile kernel, or the TMA-fed kernel where the
+ * interior cells are whole tiles of it: its source boxes then reach into the ghost planes
+ * and never wrap along z).  Before every step the caller refreshes
  * the halos: sllbm_halo_pack(side 0) copies lowest interior planes of the current state to
  * a device buffer for the slab below, sllbm_halo_pack(side 1) highest ones for the slab
  * above; sllbm_halo_unpack(side 0 / 1) writes a buffer received from the slab below / above
@@ -176,8 +178,8 @@ int sllbm_create(const sllbm_mesh *mesh, int p, sllbm_velset vs, const sllbm_par
  * sllbm_step_end.  The result equals sllbm_step's bit for bit.
  * Errors: SLLBM_EINVAL for z_begin outside the mesh, z_cells < 1 or above the mesh, a
  * slab thinner than its ghost width (its halo would come from two neighbours), a TMA-fed
- * kernel request, and for slab contexts in sllbm_diag*, the reverse-mode calls, batches
- * and variant 0 of sllbm_set_step_variant; sllbm_halo_*, sllbm_slab_info and
+ * kernel request the interior cells cannot tile, and for slab contexts in sllbm_diag*, the
+ * reverse-mode calls and batches; sllbm_halo_*, sllbm_slab_info and
  * sllbm_step_begin/_end on a context that is not a slab, side not 0 or 1, a NULL buffer or
  * a context without state: SLLBM_EINVAL (sllbm_step_begin/_end before initialisation:
  * SLLBM_ENOTREADY); a failed copy or launch: SLLBM_ECUDA. */

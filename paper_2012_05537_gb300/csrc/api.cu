@@ -281,8 +281,7 @@ namespace sllbm {
 
 // 1: generic tile kernel, 2: TMA-fed persistent kernel, 0: the requested kernel cannot run.
 int choose_step_kernel(const sllbm_ctx* c) {
-    // a slab's tiles start above its ghost cells: the generic kernel only
-    const bool tma_ok = !c->slab && tma_step_eligible(c);
+    const bool tma_ok = tma_step_eligible(c);
     if (c->prm.kernel == 2) return tma_ok ? 2 : 0;
     if (c->prm.kernel == 1) return 1;
     return tma_ok ? 2 : 1;

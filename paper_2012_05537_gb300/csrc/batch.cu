@@ -41,7 +41,7 @@ namespace {
 
 int set_variant(sllbm_ctx* ctx, int v) {
     if (v == 0) {
-        if (ctx->slab || !tma_step_eligible(ctx)) return SLLBM_EINVAL;
+        if (!tma_step_eligible(ctx)) return SLLBM_EINVAL;
         ctx->step_kernel = 2;
         ctx->tile_shape = 0;
         return SLLBM_OK;

@@ -135,16 +135,21 @@ int launch_tma(sllbm_ctx* ctx, const void* src, void* dst) {
     if (rc != SLLBM_OK) return rc;
     StepArgs args;
     fill_step_args(ctx, src, dst, &args);
-    const int ntiles = (ctx->cells[0] / T::CX) * (ctx->cells[1] / T::CY) * (ctx->cells[2] / T::CZ);
-    const int grid = ntiles < ctx->num_sms ? ntiles : ctx->num_sms;
     auto k = step_tma_kernel<P, T::CX, T::CY, T::CZ, kConsumers>;
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(SM::bytes));
-    if (err == cudaSuccess) {
-        k<<<grid, kWarps * 32, SM::bytes, ctx->stream>>>(
-            maps, args, *reinterpret_cast<const Tab*>(ctx->step_blob));
+    // all z-tiles, or the part of a slab's tiles its split step asks for (one launch per range)
+    int ranges[2][2];
+    const int nr = slab_tile_ranges(ctx, T::CZ, ranges);
+    for (int q = 0; q < nr && err == cudaSuccess; ++q) {
+        args.tz_begin = ranges[q][0];
+        args.cells[2] = (ranges[q][1] - ranges[q][0]) * T::CZ;
+        const int ntiles = (ctx->cells[0] / T::CX) * (ctx->cells[1] / T::CY) * (ranges[q][1] - ranges[q][0]);
+        if (ntiles <= 0) continue;
+        const int grid = ntiles < ctx->num_sms ? ntiles : ctx->num_sms;
+        k<<<grid, kWarps * 32, SM::bytes, ctx->stream>>>(maps, args, *reinterpret_cast<const Tab*>(ctx->step_blob));
         err = cudaGetLastError();
+        ctx->launches += 1;
     }
-    ctx->launches += 1;
     if (err != cudaSuccess) {
         ctx->last_err = static_cast<int>(err);
         return SLLBM_ECUDA;

@@ -472,6 +472,9 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     __syncthreads();
     tc_fence_after();
 
+    // the launch's tiles: a.cells[2] / CZ z-tiles starting at z-tile a.tz_begin, cells counted
+    // from a.z0 (a slab's ghost cells lie below it; the source boxes of a slab's tiles stay in
+    // its buffer, so they never wrap along z)
     const int ntx = a.cells[0] / CX, nty = a.cells[1] / CY, ntz = a.cells[2] / CZ;
     const int ntiles = ntx * nty * ntz;
     int* err_flag = a.flag_err;
@@ -519,7 +522,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
             if (lane == 0 && abort_req != nullptr) req_word = *abort_req;
             int tc[3];
             tile_coords(tile, ntx, nty, ntz, tc);
-            const int cb[3] = {tc[0] * CX * P, tc[1] * CY * P, tc[2] * CZ * P};
+            const int cb[3] = {tc[0] * CX * P, tc[1] * CY * P, ((tc[2] + a.tz_begin) * CZ + a.z0) * P};
             // meta: pieces m | nk_x << 4 | nk_y << 8 | nk_z << 12 | shape << 16 | cp.async << 20
             uint32_t meta[2];
             int crd[2][3];
@@ -751,7 +754,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
             const int tile = static_cast<int>(blockIdx.x) + it * static_cast<int>(gridDim.x);
             int tc[3];
             tile_coords(tile, ntx, nty, ntz, tc);
-            const int c0[3] = {tc[0] * CX, tc[1] * CY, tc[2] * CZ};
+            const int c0[3] = {tc[0] * CX, tc[1] * CY, (tc[2] + a.tz_begin) * CZ + a.z0};
             if (it >= 2)
                 mbar_wait_bounded(tmem_empty0 + 8 * (qd * 2 + bf), static_cast<uint32_t>((it - 2) >> 1) & 1u, abort_flag,
                                   err_flag, a.wait_ns);
@@ -1004,7 +1007,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
             const int tile = static_cast<int>(blockIdx.x) + it * static_cast<int>(gridDim.x);
             int tc[3];
             tile_coords(tile, ntx, nty, ntz, tc);
-            const int c0[3] = {tc[0] * CX, tc[1] * CY, tc[2] * CZ};
+            const int c0[3] = {tc[0] * CX, tc[1] * CY, (tc[2] + a.tz_begin) * CZ + a.z0};
             const uint32_t tb = tq + static_cast<uint32_t>(bf * TC::per_buf);
             mbar_wait_bounded(tmem_full0 + 8 * (qd * 2 + bf), static_cast<uint32_t>(it >> 1) & 1u, abort_flag, err_flag,
                               a.wait_ns);

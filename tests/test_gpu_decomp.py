@@ -14,8 +14,8 @@ from paper_2012_05537_gb300 import sllbm as S
 pytestmark = pytest.mark.gpu
 
 
-def _full(cfg, n):
-    sim = S.Sim(dataclasses.replace(cfg, kernel=1), device="cuda:0")
+def _full(cfg, n, kernel=1):
+    sim = S.Sim(dataclasses.replace(cfg, kernel=kernel), device="cuda:0")
     sim.init_tgv()
     init = sim.populations().cpu().numpy()
     assert sim.step(n) == 0
@@ -24,12 +24,13 @@ def _full(cfg, n):
     return init, out
 
 
-def _slabs(cfg, parts, n, overlapped=False):
+def _slabs(cfg, parts, n, overlapped=False, kernel=1):
     steppers = []
     for r in range(parts):
-        sim = S.Sim(dataclasses.replace(cfg, slab=D.slab_bounds(cfg.cells[2], parts, r)), device="cuda:0")
+        sim = S.Sim(dataclasses.replace(cfg, slab=D.slab_bounds(cfg.cells[2], parts, r), kernel=kernel),
+                    device="cuda:0")
         sim.init_tgv()
-        assert sim.info.step_kernel == 1
+        assert sim.info.step_kernel == kernel
         steppers.append(D.SlabStepper(sim))
 
     def interiors():
@@ -75,6 +76,18 @@ def test_overlapped_exchange_reproduces_the_whole_mesh(storage, p, parts):
     assert np.array_equal(slab, full)
 
 
+@pytest.mark.parametrize("p,parts", [(4, 1), (4, 2), (4, 3), (2, 1), (2, 2)])
+@pytest.mark.parametrize("overlapped", [False, True])
+def test_tma_fed_slabs_reproduce_the_whole_mesh(p, parts, overlapped):
+    # the TMA-fed kernel on slabs (tiles over the interior cells, source boxes reaching into
+    # the ghost planes) against the same kernel on the undivided mesh, FP32
+    cfg = S.Config(cells=(4, 4, 8), p=p, courant=2.0, storage="f32")
+    _, full = _full(cfg, 4, kernel=2)
+    _, slab, _ = _slabs(cfg, parts, 4, overlapped=overlapped, kernel=2)
+    assert np.all(np.isfinite(full))
+    assert np.array_equal(slab, full)
+
+
 def test_overlapped_exchange_on_slabs_without_interior_tiles():
     # two-cell slabs with two ghost cells: every tile reads a ghost cell (all in the second launch)
     cfg = S.Config(cells=(3, 3, 6), p=3, courant=2.0, storage="f64")
@@ -99,14 +112,14 @@ def test_slab_refusals():
         S.Sim(dataclasses.replace(base, slab=(0, 1)), device="cuda:0")
     with pytest.raises(S.SllbmError):  # outside the mesh
         S.Sim(dataclasses.replace(base, slab=(8, 2)), device="cuda:0")
-    with pytest.raises(S.SllbmError):  # the TMA-fed kernel cannot tile a slab
-        S.Sim(dataclasses.replace(base, slab=(0, 4), kernel=2), device="cuda:0")
+    with pytest.raises(S.SllbmError):  # the TMA-fed kernel cannot tile 3 x 4 x 4 cells at p = 4
+        S.Sim(dataclasses.replace(base, cells=(3, 4, 8), slab=(0, 4), kernel=2), device="cuda:0")
     sim = S.Sim(dataclasses.replace(base, slab=(0, 4)), device="cuda:0")
     sim.init_tgv()
     lib = S.load()
     d = [ctypes.c_double() for _ in range(3)]
     assert lib.sllbm_diag(sim.ctx, *[ctypes.byref(x) for x in d]) == S.EINVAL
-    assert lib.sllbm_set_step_variant(sim.ctx, 0) == S.EINVAL
+    assert lib.sllbm_set_step_variant(sim.ctx, 0) == S.OK  # the TMA-fed kernel tiles this slab
     st = D.SlabStepper(sim)
     assert lib.sllbm_halo_pack(sim.ctx, 2, ctypes.c_void_p(st.bufs["send_low"].data_ptr()), None) == S.EINVAL
     assert lib.sllbm_halo_unpack(sim.ctx, 0, None, None) == S.EINVAL

@@ -39,6 +39,7 @@ bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -102,6 +103,9 @@ def parse_args():
     ap.add_argument("--workload", default="tgv_32c_p4", choices=sorted(I.WORKLOADS))
     ap.add_argument("--storage", choices=["f32", "f64", "f16dev", "bf16dev"], default=None)
     ap.add_argument("--e2e-steps", type=int, default=40)
+    ap.add_argument("--periodic-z", choices=["ghost", "wrap"], default="ghost",
+                    help="z boundary of the headline mesh: ghost planes (the mesh as one periodic z-slab, "
+                         "refreshed in place before each step) or source boxes wrapping around")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--mixed-steps", type=int, default=400,
@@ -152,10 +156,10 @@ def kernel_source_hash(kind: str = "tma") -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str, storage: str, kind: str = "tma"):
+def profiled_traffic(workload: str, storage: str, kind: str = "tma", suffix: str = ""):
     """DRAM bytes per launch recorded from an ncu capture of the current kernel source,
     or None if no summary matches the current source hash of that kernel."""
-    path = os.path.join(ROOT, "profiles", f"step_{storage}_{workload}.md")
+    path = os.path.join(ROOT, "profiles", f"step_{storage}_{workload}{suffix}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
@@ -685,8 +689,14 @@ def run_mine(args, rank, world, local):
     alu = alu_peaks(S)
     w = I.WORKLOADS[args.workload]
     storage = args.storage or w.storage
+    # The periodic mesh with ghost planes along z: one slab spanning all z-cells, whose steps
+    # refresh its ghost planes in place (sllbm_halo_periodic, one small launch) so that no
+    # source box wraps around along z; bit for bit the same states as the ordinary periodic
+    # context (tests/test_gpu_decomp.py), which "--periodic-z wrap" times instead.
+    ghost = args.periodic_z == "ghost"
     cfg = S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, Pr=w.Pr, gamma=w.gamma,
-                   courant=w.courant, pr_correction=w.pr_correction, storage=storage)
+                   courant=w.courant, pr_correction=w.pr_correction, storage=storage,
+                   slab=(0, w.cells[2]) if ghost else None)
     sim = S.Sim(cfg, device=f"cuda:{local}")
     sim.init_tgv()
     for _ in range(max(3, args.warmup)):
@@ -703,7 +713,7 @@ def run_mine(args, rank, world, local):
     total_ms, kern = time_steps(sim, torch, args.steps)
     launches = sim.launches() - launches0
     torch.cuda.synchronize()
-    nodes = sim.nodes
+    nodes = w.nodes  # the mesh's nodes (a slab's buffers also hold its ghost planes)
     total_ms, value = replica_throughput(total_ms, nodes, args.steps, dist, device=f"cuda:{local}")
     if dist is not None:
         dist.barrier()
@@ -716,7 +726,8 @@ def run_mine(args, rank, world, local):
     kern_avg_ms = statistics.mean(kern)
     hbm, peak_src = measured_peaks()
     achieved = bytes_per_node * nodes / (kern_avg_ms / 1e3) / 1e9
-    traffic = profiled_traffic(w.name, storage, "tma" if sim.info.step_kernel == 2 else "generic")
+    traffic = profiled_traffic(w.name, storage, "tma" if sim.info.step_kernel == 2 else "generic",
+                               "_ghostz" if ghost else "")
 
     # end to end through the C ABI with host buffers: every step copies a state from pinned
     # host memory to the device, advances it one step and copies the result back.  Headline:
@@ -748,6 +759,18 @@ def run_mine(args, rank, world, local):
                               "mode": "one state at a time through sllbm_run_host"}}
 
     variants = {}
+    if not args.no_variants and rank == 0 and ghost:
+        # the same workload on the ordinary periodic context (source boxes wrap around along z)
+        simw = S.Sim(dataclasses.replace(cfg, slab=None), device=f"cuda:{local}")
+        simw.init_tgv()
+        simw.step(3)
+        nw = 50
+        tw, kw = time_steps(simw, torch, nw)
+        variants["periodic_wrap"] = {"value": nodes * nw / (tw / 1e3), "ms_per_step": tw / nw,
+                                     "kernel_ms": statistics.mean(kw), "step_kernel": int(simw.info.step_kernel),
+                                     "hbm_frac": bytes_per_node * nodes / (statistics.mean(kw) / 1e3) / 1e9 / hbm,
+                                     "steps": nw}
+        simw.close()
     if not args.no_variants and rank == 0 and storage == "f32":
         # FP64 storage/arithmetic on the same workload (FP64-ALU bound on this part)
         sim64 = S.Sim(S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, Pr=w.Pr, gamma=w.gamma,
@@ -809,7 +832,11 @@ def run_mine(args, rank, world, local):
             "dtype": storage, "data": "synthetic",
             "config": {"workload": w.name, "cells": list(w.cells), "p": w.p,
                        "nodes": nodes, "Ma": w.Ma, "Re": w.Re, "courant": w.courant,
+                       "pr_correction": bool(w.pr_correction),
                        "dt": sim.dt, "storage": storage,
+                       "z_boundary": ("ghost planes: the mesh as one periodic z-slab (sllbm_create_slab over "
+                                      "all cells), refreshed in place before each step by sllbm_halo_periodic "
+                                      "inside sllbm_step" if ghost else "source boxes wrap around (periodic images)"),
                        "l2": f"inputs larger than L2 ({sim.info.pop_bytes / 1e6:.0f} MB per buffer)",
                        "parallelism": f"replicas x{world}",
                        "population_updates_per_s": value * 45},

@@ -408,6 +408,12 @@ int launch_current(sllbm_ctx* ctx) {
 }
 
 int step_launch(sllbm_ctx* ctx) {
+    if (ctx->slab && ctx->cells[2] == ctx->z_cells_global) {
+        // a slab spanning the whole mesh is periodic along z by its own ghost planes: refresh
+        // them from the opposite end of the interior before the step reads them
+        const int rc = sllbm_halo_periodic(ctx, nullptr);
+        if (rc != SLLBM_OK) return rc;
+    }
     const int rc = launch_current(ctx);
     if (rc != SLLBM_OK) return rc;
     ctx->cur = 1 - ctx->cur;
@@ -662,6 +668,29 @@ int ghost_planes(const sllbm_ctx* c, int i, int side) {
     return kmx >= 0 ? kmx * c->p + 1 : 0;
 }
 
+// A slab that spans the whole mesh along z is its own neighbour: each velocity's ghost planes
+// below it are its highest interior planes and those above it its lowest ones.  One launch
+// copies both sides inside the state buffer (blockIdx.z = side, blockIdx.y = velocity), in
+// 16-byte words when a plane is a whole number of them (else 4-byte words).
+struct PeriodicMap {
+    int dst0[2][kQ];  // first ghost plane written
+    int src0[2][kQ];  // first interior plane read
+    int planes[2][kQ];
+};
+
+template <typename W>
+__global__ void __launch_bounds__(256) halo_periodic_kernel(W* __restrict__ state, long long plane_words,
+                                                             long long vstride_words, const __grid_constant__ PeriodicMap m) {
+    const int side = blockIdx.z, i = blockIdx.y;
+    const long long n = static_cast<long long>(m.planes[side][i]) * plane_words;
+    W* base = state + i * vstride_words;
+    const W* src = base + static_cast<long long>(m.src0[side][i]) * plane_words;
+    W* dst = base + static_cast<long long>(m.dst0[side][i]) * plane_words;
+    for (long long k = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; k < n;
+         k += static_cast<long long>(gridDim.x) * blockDim.x)
+        dst[k] = src[k];
+}
+
 // Bytes of the packed halo sllbm_halo_pack(side) writes (the receiving slab's ghost region
 // on the other side).
 size_t halo_pack_bytes(const sllbm_ctx* c, int side) {
@@ -747,10 +776,53 @@ int sllbm_halo_unpack(sllbm_ctx* ctx, int side, const void* halo, void* cuda_str
                      cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream);
 }
 
+int sllbm_halo_periodic(sllbm_ctx* ctx, void* cuda_stream) {
+    if (ctx == nullptr || !ctx->slab || ctx->cells[2] != ctx->z_cells_global) return SLLBM_EINVAL;
+    if (ctx->buf[ctx->cur] == nullptr) return SLLBM_EINVAL;
+    const cudaStream_t stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream;
+    const int gp = ctx->ghost * ctx->p;
+    const int top = gp + ctx->cells[2] * ctx->p;
+    PeriodicMap m;
+    int most = 0;
+    for (int i = 0; i < kQ; ++i) {
+        const int nb = ghost_planes(ctx, i, 0), na = ghost_planes(ctx, i, 1);
+        m.planes[0][i] = nb;  // below: the highest interior planes
+        m.dst0[0][i] = gp - nb;
+        m.src0[0][i] = top - nb;
+        m.planes[1][i] = na;  // above: the lowest interior planes
+        m.dst0[1][i] = top;
+        m.src0[1][i] = gp;
+        most = nb > most ? nb : most;
+        most = na > most ? na : most;
+    }
+    if (most == 0) return SLLBM_OK;
+    const size_t plane_bytes = static_cast<size_t>(ctx->N[0]) * ctx->N[1] * 2 * ctx->elem;
+    const bool w16 = plane_bytes % 16 == 0;
+    const long long plane_words = static_cast<long long>(plane_bytes / (w16 ? 16 : 4));
+    const long long per = static_cast<long long>(most) * plane_words;
+    long long bx = (per + 255) / 256;
+    if (bx > 512) bx = 512;
+    const dim3 grid(static_cast<unsigned>(bx), kQ, 2);
+    if (w16)
+        halo_periodic_kernel<uint4><<<grid, 256, 0, stream>>>(static_cast<uint4*>(ctx->buf[ctx->cur]), plane_words,
+                                                             static_cast<long long>(ctx->N[2]) * plane_words, m);
+    else
+        halo_periodic_kernel<unsigned><<<grid, 256, 0, stream>>>(static_cast<unsigned*>(ctx->buf[ctx->cur]),
+                                                                plane_words,
+                                                                static_cast<long long>(ctx->N[2]) * plane_words, m);
+    ctx->launches += 1;
+    CK(ctx, cudaGetLastError());
+    return SLLBM_OK;
+}
+
 int sllbm_step_begin(sllbm_ctx* ctx) {
     if (ctx == nullptr || !ctx->slab) return SLLBM_EINVAL;
     if (!ctx->initialised) return SLLBM_ENOTREADY;
     if (ctx->prm.nonfinite_check) CK(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
+    if (ctx->cells[2] == ctx->z_cells_global) {  // periodic by its own ghost planes (see step_launch)
+        const int rc0 = sllbm_halo_periodic(ctx, nullptr);
+        if (rc0 != SLLBM_OK) return rc0;
+    }
     ctx->region = 1;
     const int rc = launch_current(ctx);
     ctx->region = 0;

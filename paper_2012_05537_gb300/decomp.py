@@ -79,6 +79,10 @@ class SlabStepper:
 
     def exchange(self) -> None:
         torch = self.sim.torch
+        if self.world == 1:
+            # the slab is the whole mesh along z: every step refreshes its ghost planes in
+            # place (sllbm_halo_periodic inside sllbm_step), nothing to exchange
+            return
         self.pack()
         # the collectives run after the packs (enqueued on the slab's stream) and before the
         # unpacks

@@ -91,6 +91,7 @@ def load(build_if_missing: bool = False):
         "sllbm_slab_halo_bytes": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
         "sllbm_halo_pack": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
         "sllbm_halo_unpack": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
+        "sllbm_halo_periodic": (ctypes.c_int, [vp, vp]),
         "sllbm_step_begin": (ctypes.c_int, [vp]),
         "sllbm_step_end": (ctypes.c_int, [vp]),
         "sllbm_destroy": (None, [vp]),
@@ -213,6 +214,10 @@ def sllbm_halo_pack(ctx, side: int, halo_ptr: int, stream: int = 0) -> None:
 def sllbm_halo_unpack(ctx, side: int, halo_ptr: int, stream: int = 0) -> None:
     _check(load().sllbm_halo_unpack(ctx, int(side), ctypes.c_void_p(halo_ptr), ctypes.c_void_p(stream)),
            "sllbm_halo_unpack", ctx)
+
+
+def sllbm_halo_periodic(ctx, stream: int = 0) -> None:
+    _check(load().sllbm_halo_periodic(ctx, ctypes.c_void_p(stream)), "sllbm_halo_periodic", ctx)
 
 
 def sllbm_step_begin(ctx) -> None:

@@ -88,6 +88,30 @@ def test_tma_fed_slabs_reproduce_the_whole_mesh(p, parts, overlapped):
     assert np.array_equal(slab, full)
 
 
+@pytest.mark.parametrize("kernel,p,storage", [(1, 3, "f64"), (1, 4, "f32"), (2, 4, "f32"), (2, 2, "f32")])
+def test_periodic_halo_refresh_of_a_whole_mesh_slab(kernel, p, storage):
+    # one slab spanning the mesh, its ghost planes refreshed in place before every step (by
+    # sllbm_step itself: sllbm_halo_periodic), against the ordinary periodic context on the
+    # same kernel
+    cfg = S.Config(cells=(4, 4, 8), p=p, courant=2.0, storage=storage)
+    _, full = _full(cfg, 4, kernel=kernel)
+    sim = S.Sim(dataclasses.replace(cfg, slab=(0, 8), kernel=kernel), device="cuda:0")
+    assert sim.info.step_kernel == kernel
+    sim.init_tgv()
+    g = S.sllbm_slab_info(sim.ctx)[0]
+    for k in range(4):
+        if k % 2:
+            S.sllbm_halo_periodic(sim.ctx)  # explicit refreshes on top of the step's own are harmless
+        assert sim.step(1) == 0
+    got = sim.populations().cpu().numpy()[:, :, g * p:(g + 8) * p]
+    assert np.array_equal(got, full)
+    half = S.Sim(dataclasses.replace(cfg, slab=(0, 4)), device="cuda:0")  # not the whole mesh
+    with pytest.raises(S.SllbmError):
+        S.sllbm_halo_periodic(half.ctx)
+    sim.close()
+    half.close()
+
+
 def test_overlapped_exchange_on_slabs_without_interior_tiles():
     # two-cell slabs with two ghost cells: every tile reads a ghost cell (all in the second launch)
     cfg = S.Config(cells=(3, 3, 6), p=3, courant=2.0, storage="f64")

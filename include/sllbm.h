@@ -103,8 +103,11 @@ typedef struct {
     double mu_inf_override; /* > 0: use this mu_inf instead of rho0*U0/Re */
     int collide;            /* 1: stream and collide (normal); 0: stream only */
     int kernel;             /* step kernel: 0 automatic, 1 generic tile kernel, 2 TMA-fed
-                               persistent kernel (FP32 only; needs N[0] even, cells divisible
-                               by its tile, no Prandtl term, collide on; else SLLBM_EINVAL) */
+                               persistent kernel (FP32 and the 16-bit deviation storages; needs
+                               N[0] a multiple of 2 (FP32) or 4 (16-bit), cells divisible by its
+                               tile of 4x4x2 (p = 2), 2x3x1 (p = 3: y may end in a partial
+                               tile) or 2x2x1 cells (p = 4), no Prandtl term, collide on, no
+                               compensated sums; else SLLBM_EINVAL) */
 } sllbm_params;
 
 /* Read-only description of a created context. */
@@ -305,7 +308,7 @@ int sllbm_set_mu_inf(sllbm_ctx *ctx, double mu_inf);
 
 /* ---- kernel choice, autotuning, batched launch ------------------------------------------
  * A step can run on several kernels with identical results up to FP rounding order: the
- * TMA-fed persistent kernel (FP32, p = 2 or 4, meshes of whole tiles) and the generic tile
+ * TMA-fed persistent kernel (FP32 or 16-bit deviations; whole tiles in x and z) and the generic tile
  * kernel with its default tile or, for FP32 storage without the Prandtl term, one of two
  * smaller tiles (more CTAs on small meshes).  Variants: 0 TMA-fed kernel; 1 generic,
  * default tile (FP32: p = 2 4x4x2 cells, p = 3 2x2x2, p = 4 2x2x1); 2 and 3 generic,

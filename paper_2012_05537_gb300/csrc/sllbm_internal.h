@@ -196,7 +196,7 @@ void fill_step_tables(const sllbm_ctx* ctx, StepTables<C, P>* t) {
 
 // Step launchers, one per storage type (step_f32.cu, step_f64.cu).
 int launch_step_f32(sllbm_ctx* ctx, const void* src, void* dst);
-int launch_step_tma(sllbm_ctx* ctx, const void* src, void* dst);  // TMA-fed FP32 kernel, p = 2, 4 (step_tma.cu)
+int launch_step_tma(sllbm_ctx* ctx, const void* src, void* dst);  // TMA-fed kernel, FP32 and 16-bit, p = 2..4 (step_tma.cu)
 int launch_step_f64(sllbm_ctx* ctx, const void* src, void* dst);
 int launch_step_f16(sllbm_ctx* ctx, const void* src, void* dst);  // both 16-bit deviation types (step_f16.cu)
 // Generic FP32 kernel with one of the alternative tile shapes 1, 2 (step_f32_tiles.cu).
@@ -225,7 +225,7 @@ int batch_group_grid(int p, int shape, int num_sms, long long items, int* grid);
 int launch_batch_group(int p, int shape, const BatchJob* jobs, int njobs, const void* tabs, long long items,
                        int parity, int grid, cudaStream_t stream);
 
-// True when the TMA-fed FP32 kernel can run this context (step_tma.cu).
+// True when the TMA-fed kernel can run this context (step_tma.cu).
 bool tma_step_eligible(const sllbm_ctx* c);
 
 // Reverse-mode scratch of a context (adjoint.cu): allocation on first use, release.

@@ -1,5 +1,6 @@
-// 16-bit deviation storage (IEEE half, bfloat16) / FP32 arithmetic instances of the
-// generic step kernel.
+// 16-bit deviation storage (IEEE half, bfloat16) / FP32 arithmetic: the TMA-fed kernel
+// (step_tma.cu) where the mesh allows it and the context selects it, the generic tile
+// kernel otherwise.
 #include "step_kernel.cuh"
 
 namespace sllbm {
@@ -16,6 +17,7 @@ int launch_step_dev(sllbm_ctx* ctx, const void* src, void* dst) {
 }
 
 int launch_step_f16(sllbm_ctx* ctx, const void* src, void* dst) {
+    if (ctx->step_kernel == 2) return launch_step_tma(ctx, src, dst);
     if (ctx->prm.storage == SLLBM_BF16DEV) return launch_step_dev<__nv_bfloat16>(ctx, src, dst);
     return launch_step_dev<__half>(ctx, src, dst);
 }

@@ -1,5 +1,6 @@
-// Host side of the TMA-fed persistent FP32 step kernel (step_tma.cuh): eligibility, the
-// tensor maps of the source buffer, the per-velocity tables and the launch.
+// Host side of the TMA-fed persistent step kernel (step_tma.cuh) for FP32 storage and the
+// 16-bit deviation storages: eligibility, the tensor maps of the source buffer, the
+// per-velocity tables and the launch.
 #include <cudaTypedefs.h>
 
 #include <cstdlib>
@@ -12,14 +13,19 @@ namespace sllbm {
 
 namespace {
 
-// Tile (in cells) of the TMA kernel per order: 8x8x4 nodes for p = 2 and p = 4.  (For p = 3
-// a tile of whole cells is 9 nodes wide, and two tiles of streamed pairs do not fit in tensor
-// memory next to each other; p = 3 runs the generic kernel.)
+// Tile (in cells) of the TMA kernel per order: 8x8x4 nodes for p = 2 and p = 4, 6x9x3 for
+// p = 3 (a tile of whole cells 9 nodes wide would not fit two tiles of streamed pairs in
+// tensor memory; 9 rows of 3 planes keep 27 of the 32 lanes busy, and a mesh whose y cell
+// count is not a multiple of 3 ends in a partial tile row).
 template <int P>
 struct TmaTile;
 template <>
 struct TmaTile<2> {
     static constexpr int CX = 4, CY = 4, CZ = 2;
+};
+template <>
+struct TmaTile<3> {
+    static constexpr int CX = 2, CY = 3, CZ = 1;
 };
 template <>
 struct TmaTile<4> {
@@ -70,7 +76,8 @@ void fill_tables_s(const sllbm_ctx* ctx, StepTablesS<P>* t) {
 template <int P>
 bool tma_eligible_p(const sllbm_ctx* c) {
     using T = TmaTile<P>;
-    if (c->cells[0] % T::CX != 0 || c->cells[1] % T::CY != 0 || c->cells[2] % T::CZ != 0) return false;
+    if (c->cells[0] % T::CX != 0 || c->cells[2] % T::CZ != 0) return false;
+    if (P != 3 && c->cells[1] % T::CY != 0) return false;
     // the passes are compiled per first local node of the upper departure cell: the shifts of
     // a cell's local nodes must not decrease with the node (they do not: the support points
     // are ordered, and so are their departure points)
@@ -81,28 +88,33 @@ bool tma_eligible_p(const sllbm_ctx* c) {
     return true;
 }
 
-// Builds (or reuses) the TMA descriptors of a source buffer: the buffer seen as a 4D FP32
-// tensor [45][Nz][Ny][2*Nx] (f_i, g_i interleaved along x), one descriptor per box shape
-// (span 0 or 1 of the departure cells in x, y, z).  Out-of-domain elements read as zero.
-template <int P>
+// Builds (or reuses) the TMA descriptors of a source buffer: the buffer seen as a 4D tensor
+// [45][Nz][Ny][X] (f_i, g_i interleaved along x): FP32 elements with X = 2*Nx for FP32
+// storage, one 32-bit element per 16-bit (f, g) pair with X = Nx otherwise; one descriptor per
+// box shape (span 0 or 1 of the departure cells in x, y, z).  Out-of-domain elements read as
+// zero.
+template <typename S, int P>
 int tensor_maps_for(sllbm_ctx* ctx, const void* src, TmaMaps* out) {
     using T = TmaTile<P>;
-    using G = TmaGeom<P, T::CX, T::CY, T::CZ>;
+    using G = TmaGeom<S, P, T::CX, T::CY, T::CZ>;
+    constexpr cuuint64_t XM = G::kF32 ? 2 : 1;  // elements per pair
     const int k = (src == ctx->buf[0]) ? 0 : 1;
     if (ctx->tmap_src[k] != src) {
         PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
         if (enc == nullptr) return SLLBM_ECUDA;
-        const cuuint64_t nx2 = 2ull * ctx->N[0];
-        cuuint64_t gdim[4] = {nx2, static_cast<cuuint64_t>(ctx->N[1]), static_cast<cuuint64_t>(ctx->N[2]),
+        const cuuint64_t nx = XM * ctx->N[0];
+        cuuint64_t gdim[4] = {nx, static_cast<cuuint64_t>(ctx->N[1]), static_cast<cuuint64_t>(ctx->N[2]),
                               static_cast<cuuint64_t>(kQ)};
-        cuuint64_t gstride[3] = {nx2 * 4, nx2 * ctx->N[1] * 4, nx2 * ctx->N[1] * ctx->N[2] * 4};
+        cuuint64_t gstride[3] = {nx * 4, nx * ctx->N[1] * 4, nx * ctx->N[1] * ctx->N[2] * 4};
         cuuint32_t estride[4] = {1, 1, 1, 1};
+        const CUtensorMapDataType dt = G::kF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
         for (int shape = 0; shape < 8; ++shape) {
             CUtensorMap map;
-            cuuint32_t box[4] = {2u * G::xpairs(shape & 1), static_cast<cuuint32_t>(G::rows((shape >> 1) & 1)),
+            cuuint32_t box[4] = {static_cast<cuuint32_t>(XM * G::xpairs_s(shape & 1)),
+                                 static_cast<cuuint32_t>(G::rows((shape >> 1) & 1)),
                                  static_cast<cuuint32_t>(G::planes((shape >> 2) & 1)), 1u};
-            CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(src), gdim, gstride, box,
-                             estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CUresult r = enc(&map, dt, 4, const_cast<void*>(src), gdim, gstride, box, estride,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (r != CUDA_SUCCESS) {
                 ctx->tmap_src[k] = nullptr;
@@ -116,11 +128,11 @@ int tensor_maps_for(sllbm_ctx* ctx, const void* src, TmaMaps* out) {
     return SLLBM_OK;
 }
 
-template <int P>
+template <typename S, int P>
 int launch_tma(sllbm_ctx* ctx, const void* src, void* dst) {
     using T = TmaTile<P>;
     constexpr int kConsumers = kConsumersFor<P>;
-    using SM = TmaSmem<P, T::CX, T::CY, T::CZ, kConsumers>;
+    using SM = TmaSmem<S, P, T::CX, T::CY, T::CZ, kConsumers>;
     static_assert(SM::bytes <= kSmemBudget, "shared memory budget");
     using Tab = StepTablesS<P>;
     if (ctx->step_blob == nullptr || ctx->step_blob_size != sizeof(Tab) + 1) {
@@ -131,11 +143,11 @@ int launch_tma(sllbm_ctx* ctx, const void* src, void* dst) {
         fill_tables_s<P>(ctx, reinterpret_cast<Tab*>(ctx->step_blob));
     }
     TmaMaps maps;
-    int rc = tensor_maps_for<P>(ctx, src, &maps);
+    int rc = tensor_maps_for<S, P>(ctx, src, &maps);
     if (rc != SLLBM_OK) return rc;
     StepArgs args;
     fill_step_args(ctx, src, dst, &args);
-    auto k = step_tma_kernel<P, T::CX, T::CY, T::CZ, kConsumers>;
+    auto k = step_tma_kernel<S, P, T::CX, T::CY, T::CZ, kConsumers>;
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(SM::bytes));
     // all z-tiles, or the part of a slab's tiles its split step asks for (one launch per range)
     int ranges[2][2];
@@ -143,7 +155,8 @@ int launch_tma(sllbm_ctx* ctx, const void* src, void* dst) {
     for (int q = 0; q < nr && err == cudaSuccess; ++q) {
         args.tz_begin = ranges[q][0];
         args.cells[2] = (ranges[q][1] - ranges[q][0]) * T::CZ;
-        const int ntiles = (ctx->cells[0] / T::CX) * (ctx->cells[1] / T::CY) * (ranges[q][1] - ranges[q][0]);
+        const int ntiles =
+            (ctx->cells[0] / T::CX) * ((ctx->cells[1] + T::CY - 1) / T::CY) * (ranges[q][1] - ranges[q][0]);
         if (ntiles <= 0) continue;
         const int grid = ntiles < ctx->num_sms ? ntiles : ctx->num_sms;
         k<<<grid, kWarps * 32, SM::bytes, ctx->stream>>>(maps, args, *reinterpret_cast<const Tab*>(ctx->step_blob));
@@ -160,20 +173,38 @@ int launch_tma(sllbm_ctx* ctx, const void* src, void* dst) {
 }  // namespace
 
 bool tma_step_eligible(const sllbm_ctx* c) {
-    if (c->prm.storage != SLLBM_F32 || c->prm.pr_correction || !c->prm.collide || c->compensated) return false;
-    if (c->N[0] % 2 != 0 || c->num_sms <= 0) return false;
+    const int st = c->prm.storage;
+    if (st != SLLBM_F32 && st != SLLBM_F16DEV && st != SLLBM_BF16DEV) return false;
+    if (c->prm.pr_correction || !c->prm.collide || c->compensated) return false;
+    // TMA rows start on 16 bytes: x a multiple of 2 (FP32) or 4 (16-bit) pairs, so a row
+    // of the mesh must be one too
+    if (c->N[0] % (st == SLLBM_F32 ? 2 : 4) != 0 || c->num_sms <= 0) return false;
     if (tensor_map_encoder() == nullptr) return false;
     switch (c->p) {
     case 2: return tma_eligible_p<2>(c);
+    case 3: return tma_eligible_p<3>(c);
     case 4: return tma_eligible_p<4>(c);
     }
     return false;
 }
 
-int launch_step_tma(sllbm_ctx* ctx, const void* src, void* dst) {
+namespace {
+template <typename S>
+int launch_tma_for(sllbm_ctx* ctx, const void* src, void* dst) {
     switch (ctx->p) {
-    case 2: return launch_tma<2>(ctx, src, dst);
-    case 4: return launch_tma<4>(ctx, src, dst);
+    case 2: return launch_tma<S, 2>(ctx, src, dst);
+    case 3: return launch_tma<S, 3>(ctx, src, dst);
+    case 4: return launch_tma<S, 4>(ctx, src, dst);
+    }
+    return SLLBM_EINVAL;
+}
+}  // namespace
+
+int launch_step_tma(sllbm_ctx* ctx, const void* src, void* dst) {
+    switch (ctx->prm.storage) {
+    case SLLBM_F32: return launch_tma_for<float>(ctx, src, dst);
+    case SLLBM_F16DEV: return launch_tma_for<__half>(ctx, src, dst);
+    case SLLBM_BF16DEV: return launch_tma_for<__nv_bfloat16>(ctx, src, dst);
     }
     return SLLBM_EINVAL;
 }

@@ -37,6 +37,11 @@
 
 #include <cstdint>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
 #include "collide.cuh"
 #include "packed.cuh"
 #include "sllbm_internal.h"
@@ -55,32 +60,51 @@ struct StepTablesS {
     signed char span[kQ][3];
 };
 
-template <int P, int CX, int CY, int CZ>
+// Box and tile geometry for storage type S (float: f and g themselves; __half or
+// __nv_bfloat16: their deviations, see storage.cuh).  A box is held in the ring as stored
+// (rows of pairs from an x that TMA can address: a multiple of AL pairs, 16 bytes); the
+// passes run in FP32 on rows of pairs from an even x (in place in the ring for FP32, in the
+// stream warp's scratch otherwise).
+template <typename S, int P, int CX, int CY, int CZ>
 struct TmaGeom {
+    static constexpr bool kF32 = sizeof(S) == 4;
+    static constexpr int PB = 2 * static_cast<int>(sizeof(S));  // bytes of one stored (f, g) pair
+    static constexpr int AL = 16 / PB;                           // pairs per 16 bytes
     static constexpr int TX = CX * P, TY = CY * P, TZ = CZ * P;
     static constexpr int TILE = TX * TY * TZ;
     static constexpr int ROWS = TY * TZ;  // x-rows of a tile, one per lane
     static constexpr int BX = (CX + 1) * P + 1, BY = (CY + 1) * P + 1, BZ = (CZ + 1) * P + 1;
-    static constexpr int BXP = ((BX + 1) + 1) / 2 * 2;  // pairs per box row: even start + offset
+    static constexpr int BXP = ((BX + 1) + 1) / 2 * 2;  // FP32 pairs per box row: even start + offset
     static constexpr int PLANE = BY * BXP;              // float2 per box plane
     static constexpr int BOX = BZ * PLANE;              // float2 per box
-    static constexpr uint32_t BOX_BYTES = BOX * 8u;
-    static constexpr int SLOT_BYTES = (BOX * 8 + 127) / 128 * 128;
     // A velocity whose P local nodes all depart from the same cell in a direction (span 0)
     // needs one cell less of the box in that direction.  Box extents per span:
     static constexpr int BX0 = CX * P + 1, BY0 = CY * P + 1, BZ0 = CZ * P + 1;
     static constexpr int BXP0 = ((BX0 + 1) + 1) / 2 * 2;
+    // stored pairs per ring row (from the x rounded down to a multiple of AL)
+    static constexpr int BXS = (BX + AL - 1 + AL - 1) / AL * AL, BXS0 = (BX0 + AL - 1 + AL - 1) / AL * AL;
     __host__ __device__ static constexpr int xpairs(int span) { return span ? BXP : BXP0; }
+    __host__ __device__ static constexpr int xpairs_s(int span) { return span ? BXS : BXS0; }
     __host__ __device__ static constexpr int rows(int span) { return span ? BY : BY0; }
     __host__ __device__ static constexpr int planes(int span) { return span ? BZ : BZ0; }
-    // bytes of a box of shape sx + 2 sy + 4 sz, and the 128-byte ring units one piece takes
+    // bytes of a stored box of shape sx + 2 sy + 4 sz, and the 128-byte ring units one piece takes
     __host__ __device__ static constexpr int box_bytes(int shape) {
-        return xpairs(shape & 1) * rows((shape >> 1) & 1) * planes((shape >> 2) & 1) * 8;
+        return xpairs_s(shape & 1) * rows((shape >> 1) & 1) * planes((shape >> 2) & 1) * PB;
     }
     __host__ __device__ static constexpr int piece_units(int shape) { return (box_bytes(shape) + 127) / 128; }
+    static constexpr int SLOT_BYTES = (BXS * BY * BZ * PB + 127) / 128 * 128;
+    // FP32 working copy of a 16-bit box after the z pass (TZ planes), per stream warp
+    static constexpr int SCRATCH_F2 = kF32 ? 0 : TZ * BY * BXP;
+    // tensor-memory columns per streamed pair (2 TX used; a multiple of 16 keeps every
+    // tcgen05 access aligned to its width)
+    static constexpr int PCS = (2 * TX + 15) / 16 * 16;
     static_assert(ROWS <= 32, "one x-row per lane");
-    static_assert(BXP % 2 == 0 && BXP >= BX + 1 && BXP0 % 2 == 0 && BXP0 >= BX0 + 1, "TMA rows start on an even pair");
-    static_assert(TX == 8, "tensor-memory row layout and node shares of the epilogue warps");
+    static_assert(BXP % 2 == 0 && BXP >= BX + 1 && BXP0 % 2 == 0 && BXP0 >= BX0 + 1, "pass rows start on an even pair");
+    static_assert(BXS % AL == 0 && BXS >= BX + AL - 1 && BXS0 % AL == 0 && BXS0 >= BX0 + AL - 1, "TMA rows");
+    // a 16-bit row is read from its even pair at or below the first used one (AL - 2 at most
+    // above the row start) for BXP pairs
+    static_assert(kF32 || (AL - 2 + BXP <= BXS && AL - 2 + BXP0 <= BXS0), "z pass reads stay in the row");
+    static_assert(TX == 8 || TX == 6, "tensor-memory row layout and node shares of the epilogue warps");
 };
 
 // One TMA descriptor per box shape (span 0/1 in x, y, z: index sx + 2 sy + 4 sz) of a source
@@ -124,15 +148,19 @@ constexpr int kItems = 32;
 constexpr size_t kSmemBudget = 227 * 1024;
 static_assert((kItems & (kItems - 1)) == 0, "item table size");
 
-template <int P, int CX, int CY, int CZ, int NC>
+template <typename S, int P, int CX, int CY, int CZ, int NC>
 struct TmaSmem {
-    using G = TmaGeom<P, CX, CY, CZ>;
+    using G = TmaGeom<S, P, CX, CY, CZ>;
     // every region starts on a 128-byte boundary (TMA destinations, float4 and mbarrier
     // alignment)
     static constexpr size_t round128(size_t b) { return (b + 127) / 128 * 128; }
+    // per-node parameters of the collision: rho, ux, uy, uz, gT, omega, c0[4], c1[4], c2[4]
+    // (FP32 storage); rho, ux, uy, uz, omega, rho - rho0, (2C_v-D) T rho, (2C_v-D)((T - T0) rho
+    // + T0 (rho - rho0)), c0[4] - 1, c1[4], c2[4] (deviation storage)
+    static constexpr int kNPar = G::kF32 ? kNParams : kNParams + 2;
     // the per-quarter moment sums (3 quarters x 5) and the per-node parameters share one region:
     // an epilogue warp reads the sums of exactly the node columns whose parameters it writes
-    static constexpr int kShared = 3 * 5 > kNParams ? 3 * 5 : kNParams;
+    static constexpr int kShared = 3 * 5 > kNPar ? 3 * 5 : kNPar;
     static constexpr size_t partials = round128(size_t(kShared) * G::TX * 32 * sizeof(float));
     static constexpr size_t params = 0;
     static constexpr size_t tables = round128(sizeof(StepTablesS<P>));
@@ -142,10 +170,12 @@ struct TmaSmem {
     static constexpr size_t bars =
         (size_t(NPROD) * 3 * kItems + 16) * sizeof(uint64_t) + size_t(NPROD) * kItems * sizeof(int) + 16;
     static constexpr size_t bars_padded = round128(bars);
-    static constexpr int woff_n = G::BZ + G::BY + G::BXP / 2;  // wrapped-offset table per producer
+    static constexpr int woff_n = G::BZ + G::BY + G::BXS / G::AL;  // wrapped-offset table per producer
     static constexpr size_t woff = round128(size_t(NPROD) * woff_n * sizeof(long long));
     static constexpr size_t stage = size_t(kEpilogueWarps) * 32 * 64;  // one pair's 32 rows per epilogue warp
-    static constexpr size_t fixed = partials + params + tables + bars_padded + woff + stage + 128;  // +128: base alignment
+    static constexpr size_t scratch = round128(size_t(NC) * G::SCRATCH_F2 * 8);  // 16-bit storage only
+    static constexpr size_t fixed =
+        partials + params + tables + bars_padded + woff + stage + scratch + 128;  // +128: base alignment
     // the box ring takes the rest, in 128-byte units
     static constexpr int ring_units = static_cast<int>((kSmemBudget - fixed) / 128);
     static constexpr size_t ring = size_t(ring_units) * 128;
@@ -153,12 +183,12 @@ struct TmaSmem {
     static_assert(ring_units / NPROD >= G::SLOT_BYTES / 128, "each producer's ring holds the largest box");
 };
 
-// Tensor-memory columns: a stream warp's lane keeps NPW pairs x 2*TX floats per tile; stream
-// warps w, w+4, w+8 share a 32-lane quarter (the quarter a warp may touch is fixed by w % 4);
-// each quarter holds two tiles (buffers).
-template <int TX, int NPW, int NC>
+// Tensor-memory columns: a stream warp's lane keeps NPW pairs x 2*TX floats per tile (PCS
+// columns per pair); stream warps w, w+4, w+8 share a 32-lane quarter (the quarter a warp may
+// touch is fixed by w % 4); each quarter holds two tiles (buffers).
+template <int PCS, int NPW, int NC>
 struct TmemCols {
-    static constexpr int per_warp = NPW * 2 * TX;
+    static constexpr int per_warp = NPW * PCS;
     static constexpr int per_buf = ((NC + 3) / 4) * per_warp;
     static constexpr int per_quarter = 2 * per_buf;
     static constexpr int alloc = per_quarter <= 32 ? 32 : per_quarter <= 64 ? 64 : per_quarter <= 128 ? 128
@@ -173,6 +203,33 @@ struct IntC {
 };
 
 // ------------------------------------------------------------------ PTX helpers
+// One stored 16-bit (f, g) pair (a 32-bit word) as two floats, and two floats rounded to one.
+template <typename S>
+__device__ __forceinline__ float2 widen_pair(uint32_t w) {
+    if constexpr (std::is_same<S, __half>::value) {
+        __half2 h;
+        memcpy(&h, &w, 4);
+        return __half22float2(h);
+    } else {
+        __nv_bfloat162 h;
+        memcpy(&h, &w, 4);
+        return __bfloat1622float2(h);
+    }
+}
+
+template <typename S>
+__device__ __forceinline__ uint32_t narrow_pair(float f, float g) {
+    uint32_t w;
+    if constexpr (std::is_same<S, __half>::value) {
+        const __half2 h = __floats2half2_rn(f, g);
+        memcpy(&w, &h, 4);
+    } else {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(f, g);
+        memcpy(&w, &h, 4);
+    }
+    return w;
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -341,8 +398,17 @@ __device__ __forceinline__ void tmem_st16(uint32_t ta, const float* v) {
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_st2(uint32_t ta, const float* v) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};" ::"r"(ta), "f"(v[0]), "f"(v[1]) : "memory");
+// 8 and 4 consecutive columns (the column address a multiple of 8 and 4).
+__device__ __forceinline__ void tmem_st8(uint32_t ta, const float* v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(ta), "f"(v[0]),
+                 "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_st4(uint32_t ta, const float* v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(ta), "f"(v[0]), "f"(v[1]),
+                 "f"(v[2]), "f"(v[3])
+                 : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t ta, float* v) {
@@ -355,22 +421,42 @@ __device__ __forceinline__ void tmem_ld16(uint32_t ta, float* v) {
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld2(uint32_t ta, float* v) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=f"(v[0]), "=f"(v[1]) : "r"(ta) : "memory");
+__device__ __forceinline__ void tmem_ld8(uint32_t ta, float* v) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+                 : "r"(ta)
+                 : "memory");
 }
 
-// 2*TX floats (TX = 8 or 9) of one pair at column ta.
+__device__ __forceinline__ void tmem_ld4(uint32_t ta, float* v) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+                 : "r"(ta)
+                 : "memory");
+}
+
+// 2*TX floats (TX = 8 or 6) of one pair at column ta (a multiple of 16).
 template <int TX>
 __device__ __forceinline__ void tmem_store_row(uint32_t ta, const float* v) {
-    tmem_st16(ta, v);
-    if (TX == 9) tmem_st2(ta + 16, v + 16);
+    if constexpr (TX == 8) {
+        tmem_st16(ta, v);
+    } else {
+        static_assert(TX == 6, "row widths");
+        tmem_st8(ta, v);
+        tmem_st4(ta + 8, v + 8);
+    }
 }
 
 // (the caller waits with tcgen05.wait::ld before using v)
 template <int TX>
 __device__ __forceinline__ void tmem_load_row(uint32_t ta, float* v) {
-    tmem_ld16(ta, v);
-    if (TX == 9) tmem_ld2(ta + 16, v + 16);
+    if constexpr (TX == 8) {
+        tmem_ld16(ta, v);
+    } else {
+        static_assert(TX == 6, "row widths");
+        tmem_ld8(ta, v);
+        tmem_ld4(ta + 8, v + 8);
+    }
 }
 
 // Visiting order of the tiles: slabs of kBlockZ tile layers; in a slab, blocks of kBlockXY x
@@ -408,22 +494,27 @@ __device__ __forceinline__ int wrapi(int v, int n) {
 }
 
 // ------------------------------------------------------------------ kernel
-template <int P, int CX, int CY, int CZ, int NC>
+template <typename S, int P, int CX, int CY, int CZ, int NC>
 __global__ void __launch_bounds__(kWarps * 32, 1)
     step_tma_kernel(const __grid_constant__ TmaMaps maps, const StepArgs a,
                     const __grid_constant__ StepTablesS<P> tpar) {
-    using G = TmaGeom<P, CX, CY, CZ>;
-    using SM = TmaSmem<P, CX, CY, CZ, NC>;
+    using G = TmaGeom<S, P, CX, CY, CZ>;
+    using SM = TmaSmem<S, P, CX, CY, CZ, NC>;
     constexpr int NPW = kQ / NC;  // velocity pairs per consumer warp
     static_assert(NPW * NC == kQ, "consumers must split the 45 pairs evenly");
-    using TC = TmemCols<G::TX, NPW, NC>;
+    using TC = TmemCols<G::PCS, NPW, NC>;
+    // (x in the tensor maps counts floats for FP32 storage, (f, g) pairs for 16-bit storage)
+    constexpr int XM = G::kF32 ? 2 : 1;
+    // p = 3 tiles are 3 cells high: the last tile row of a mesh whose y cell count is not a
+    // multiple of 3 is partial (its missing x-rows are computed from in-box data and dropped)
+    constexpr bool kRaggedY = CY == 3;
     constexpr uint32_t KM = kItems - 1;
     constexpr int NE = kEpilogueWarps;
     static_assert(NC == 9 && NE == 3, "warp roles");
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    float2* ring = reinterpret_cast<float2*>(base);  // the box ring, 16 float2 per unit
+    unsigned char* ringb = base;  // the box ring, in 128-byte units
     float* part = reinterpret_cast<float*>(base + SM::ring);
     float* prm = part;  // (the same region; see TmaSmem)
     StepTablesS<P>* tsm = reinterpret_cast<StepTablesS<P>*>(base + SM::ring + SM::partials + SM::params);
@@ -438,6 +529,8 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(start_of + NPROD * kItems) + 1;
     long long* woff = reinterpret_cast<long long*>(reinterpret_cast<unsigned char*>(bars) + SM::bars_padded);
     float4* stage = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(bars) + SM::bars_padded + SM::woff);
+    float2* scratch = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(bars) + SM::bars_padded + SM::woff +
+                                                SM::stage);
     const uint32_t full0 = smem_u32(bars);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -475,7 +568,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     // the launch's tiles: a.cells[2] / CZ z-tiles starting at z-tile a.tz_begin, cells counted
     // from a.z0 (a slab's ghost cells lie below it; the source boxes of a slab's tiles stay in
     // its buffer, so they never wrap along z)
-    const int ntx = a.cells[0] / CX, nty = a.cells[1] / CY, ntz = a.cells[2] / CZ;
+    const int ntx = a.cells[0] / CX, nty = (a.cells[1] + CY - 1) / CY, ntz = a.cells[2] / CZ;
     const int ntiles = ntx * nty * ntz;
     int* err_flag = a.flag_err;
 
@@ -502,7 +595,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         int head = 0;         // ring unit where the next item goes (if it fits)
         uint32_t sent = 0;    // items issued
         bool ok = true;
-        const uint32_t ring_u32 = smem_u32(ring);
+        const uint32_t ring_u32 = smem_u32(ringb);
         const int cd[3] = {CX, CY, CZ};
         // the host-written abort request word, read one tile ahead so that its latency hides
         // behind a tile's work
@@ -549,8 +642,8 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                     const bool tma_pieces = npiece <= kMaxPieces && npiece * G::piece_units(shape) <= RP;
                     const int m = tma_pieces ? npiece : 1;
                     units[h] = m * G::piece_units(shape);
-                    const int x0 = b0[0] - (b0[0] & 1);  // even pair index (floor for negatives)
-                    crd[h][0] = 2 * (x0 - klo[0] * a.N[0]);
+                    const int x0 = b0[0] - (b0[0] & (G::AL - 1));  // 16-byte aligned pair index (floor)
+                    crd[h][0] = XM * (x0 - klo[0] * a.N[0]);
                     crd[h][1] = b0[1] - klo[1] * a.N[1];
                     crd[h][2] = b0[2] - klo[2] * a.N[2];
                     meta[h] = static_cast<uint32_t>(m | (nk[0] << 4) | (nk[1] << 8) | (nk[2] << 12) | (shape << 16) |
@@ -666,7 +759,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                         for (int qz = 0; qz < nkz; ++qz)
                             for (int qy = 0; qy < nky; ++qy)
                                 for (int qx = 0; qx < nkx; ++qx, dst += pstride)
-                                    tma_load_4d(dst, map, cx - 2 * qx * a.N[0], cy - qy * a.N[1], cz - qz * a.N[2], j,
+                                    tma_load_4d(dst, map, cx - XM * qx * a.N[0], cy - qy * a.N[1], cz - qz * a.N[2], j,
                                                 full);
                     }
                 }
@@ -680,28 +773,29 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                         sp[d] = t.span[j][d];
                         b0[d] = cb[d] + t.kmin[j][d] * P;
                     }
-                    const int x0 = b0[0] - (b0[0] & 1);
+                    const int x0 = b0[0] - (b0[0] & (G::AL - 1));
                     const uint32_t dst = ring_u32 + static_cast<uint32_t>(RB + foff) * 128u;
                     const uint32_t full = pf0 + 8 * e;
                     // the box overlaps more periodic images than there are pieces: 16-byte copies
                     // from the wrapped positions, in the layout of the box's shape.  A chunk is
-                    // two (f,g) pairs at an even x and N[0] is even, so a chunk never straddles
-                    // the boundary.  The wrapped offsets (in floats) of the box's planes, rows
-                    // and chunks are computed once per box into a table.
-                    const float* src = static_cast<const float*>(a.src) + 2LL * j * a.nn;
-                    const int XP = G::xpairs(sp[0]), YR = G::rows(sp[1]), ZP = G::planes(sp[2]);
-                    const int CH = XP / 2;
+                    // AL (f,g) pairs at an x that is a multiple of AL and N[0] is a multiple of AL,
+                    // so a chunk never straddles the boundary.  The wrapped offsets (in stored
+                    // elements) of the box's planes, rows and chunks are computed once per box
+                    // into a table.
+                    const S* src = static_cast<const S*>(a.src) + 2LL * j * a.nn;
+                    const int XP = G::xpairs_s(sp[0]), YR = G::rows(sp[1]), ZP = G::planes(sp[2]);
+                    const int CH = XP / G::AL;
                     const int nchunk = ZP * YR * CH;
                     if (lane < ZP) pwo[lane] = 2LL * wrapi(b0[2] + lane, a.N[2]) * a.N[1] * a.N[0];
                     if (lane < YR) pwo[G::BZ + lane] = 2LL * wrapi(b0[1] + lane, a.N[1]) * a.N[0];
-                    if (lane < CH) pwo[G::BZ + G::BY + lane] = 2LL * wrapi(x0 + 2 * lane, a.N[0]);
+                    if (lane < CH) pwo[G::BZ + G::BY + lane] = 2LL * wrapi(x0 + G::AL * lane, a.N[0]);
                     __syncwarp();
                     for (int q = lane; q < nchunk; q += 32) {
                         const int row = q / CH;
                         const int c = q - row * CH;
                         const int z = row / YR, y = row - z * YR;
                         const long long off = pwo[z] + pwo[G::BZ + y] + pwo[G::BZ + G::BY + c];
-                        cp_async16(dst + static_cast<uint32_t>((row * XP + 2 * c) * 8), src + off);
+                        cp_async16(dst + static_cast<uint32_t>((row * XP + G::AL * c) * G::PB), src + off);
                     }
                     __syncwarp();  // the table is rewritten for the next such box
                     cp_async_mbar_arrive(full);
@@ -775,14 +869,24 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                 // unreleased item stays in the producer's drain.
                 const bool filled =
                     m > 0 && mbar_wait_bounded(full0 + 8 * (pbase + e), (s / kItems) & 1u, abort_flag, err_flag, a.wait_ns);
-                float2* box = ring + static_cast<size_t>(word >> 8) * 16;
-                const int ox0 = ((c0[0] + t.kmin[j][0]) * P) & 1;
-                // the box's shape: rows of XP pairs, planes of PL pairs; pieces PSTRIDE float2 apart
+                const unsigned char* sbox = ringb + static_cast<size_t>(word >> 8) * 128;
+                // the first used pair of a box row: ox0s in the stored row (which starts at a
+                // multiple of AL), ox0 = 0 or 1 in the FP32 row the passes use, which starts
+                // xs stored pairs into the stored row (xs = 0 for FP32 storage: the same row)
+                const int ox0s = ((c0[0] + t.kmin[j][0]) * P) & (G::AL - 1);
+                const int ox0 = ox0s & 1, xs = ox0s - ox0;
+                // the box's shape: FP32 rows of XP pairs, planes of PL pairs; stored rows of XPS
+                // pairs, planes of PLS pairs; pieces PSTRIDE bytes apart
                 const int sx = t.span[j][0], sy = t.span[j][1], sz = t.span[j][2];
                 const int XP = G::xpairs(sx), PL = G::rows(sy) * XP;
-                const int PSTRIDE = G::piece_units(sx + 2 * sy + 4 * sz) * 16;
+                const int XPS = G::xpairs_s(sx), PLS = G::rows(sy) * XPS;
+                const int PSTRIDE = G::piece_units(sx + 2 * sy + 4 * sz) * 128;
+                // where the passes run: in place in the ring (FP32), in the warp's scratch (16-bit)
+                float2* box = G::kF32 ? reinterpret_cast<float2*>(const_cast<unsigned char*>(sbox))
+                                      : scratch + static_cast<size_t>(c) * G::SCRATCH_F2;
 
-                // z pass, in place: column (y, xb) of the box, NZ planes -> output planes 0..TZ-1
+                // z pass: column (y, xb) of the box, NZ planes -> output planes 0..TZ-1 of the
+                // FP32 box (in place for FP32 storage; 16-bit pairs are widened on the way)
                 auto z_pass = [&](auto nz) {
                     constexpr int NZ = decltype(nz)::value;
                     float2 wz[P][P + 1];
@@ -793,30 +897,63 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
 #pragma unroll
                         for (int l = 0; l <= P; ++l) wz[az][l] = make_float2(t.lw[j][2][az][l], t.lw[j][2][az][l]);
                     }
-                    // two adjacent columns per lane: 16-byte loads and stores (PL is even and the box
-                    // starts on a 128-byte boundary)
-                    const int nq = PL >> 1;
+                    // two adjacent columns per lane: 16-byte loads and stores of FP32 pairs (PL is
+                    // even and the box starts on a 128-byte boundary), 8-byte loads of 16-bit pairs
+                    // (even pair index: xs, XPS and the column are even)
+                    const int nq = PL >> 1, XQ = XP >> 1;
                     float4* box4 = reinterpret_cast<float4*>(box);
 #pragma unroll 1
                     for (int e2 = lane; e2 < nq; e2 += 32) {
                         float2 va[NZ], vb[NZ];
+                        int srow = 0;  // 16-bit: the column pair's index in a stored plane, in 8-byte units
+                        if constexpr (!G::kF32) {
+                            const int y = e2 / XQ;
+                            srow = ((y * XPS + xs) >> 1) + (e2 - y * XQ);
+                        } else {
+                            (void)srow;
+                            (void)XQ;
+                        }
+                        if constexpr (G::kF32) {
+                            const float4* b0 = reinterpret_cast<const float4*>(sbox);
 #pragma unroll
-                        for (int z = 0; z < NZ; ++z) {
-                            const float4 q4 = box4[z * nq + e2];
-                            va[z] = make_float2(q4.x, q4.y);
-                            vb[z] = make_float2(q4.z, q4.w);
+                            for (int z = 0; z < NZ; ++z) {
+                                const float4 q4 = b0[z * nq + e2];
+                                va[z] = make_float2(q4.x, q4.y);
+                                vb[z] = make_float2(q4.z, q4.w);
+                            }
+                        } else {
+                            const uint2* b0 = reinterpret_cast<const uint2*>(sbox);
+#pragma unroll
+                            for (int z = 0; z < NZ; ++z) {
+                                const uint2 u = b0[z * (PLS >> 1) + srow];
+                                va[z] = widen_pair<S>(u.x);
+                                vb[z] = widen_pair<S>(u.y);
+                            }
                         }
                         // the other periodic images of a box that crosses the boundary (each is
                         // zero outside the domain, so their sum is the wrapped box)
                         for (int q = 1; q < m; ++q) {
-                            const float4* bq = reinterpret_cast<const float4*>(box + q * PSTRIDE);
+                            if constexpr (G::kF32) {
+                                const float4* bq = reinterpret_cast<const float4*>(sbox + q * PSTRIDE);
 #pragma unroll
-                            for (int z = 0; z < NZ; ++z) {
-                                const float4 u = bq[z * nq + e2];
-                                va[z].x += u.x;
-                                va[z].y += u.y;
-                                vb[z].x += u.z;
-                                vb[z].y += u.w;
+                                for (int z = 0; z < NZ; ++z) {
+                                    const float4 u = bq[z * nq + e2];
+                                    va[z].x += u.x;
+                                    va[z].y += u.y;
+                                    vb[z].x += u.z;
+                                    vb[z].y += u.w;
+                                }
+                            } else {
+                                const uint2* bq = reinterpret_cast<const uint2*>(sbox + q * PSTRIDE);
+#pragma unroll
+                                for (int z = 0; z < NZ; ++z) {
+                                    const uint2 u = bq[z * (PLS >> 1) + srow];
+                                    const float2 ua = widen_pair<S>(u.x), ub = widen_pair<S>(u.y);
+                                    va[z].x += ua.x;
+                                    va[z].y += ua.y;
+                                    vb[z].x += ub.x;
+                                    vb[z].y += ub.y;
+                                }
                             }
                         }
 #pragma unroll
@@ -853,6 +990,10 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                 else
                     z_pass(IntC<G::BZ0>{});
                 __syncwarp();
+                if constexpr (!G::kF32) {
+                    // the stored box has been read (into the scratch): release it now
+                    if (lane == 0 && filled) mbar_arrive(full0 + 8 * (pbase + kItems + e));
+                }
                 // y pass, in place: column (oz, xb), NY rows -> output rows 0..TY-1
                 auto y_pass = [&](auto ny) {
                     constexpr int NY = decltype(ny)::value;
@@ -975,13 +1116,18 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                     x_pass(IntC<G::BX>{});
                 else
                     x_pass(IntC<G::BX0>{});
-                // the slot was written in place (generic proxy); order that before the next TMA fill
-                fence_proxy_async();
-                __syncwarp();
-                if (lane == 0 && filled) mbar_arrive(full0 + 8 * (pbase + kItems + e));
+                if constexpr (G::kF32) {
+                    // the slot was written in place (generic proxy); order that before the next
+                    // TMA fill
+                    fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0 && filled) mbar_arrive(full0 + 8 * (pbase + kItems + e));
+                } else {
+                    __syncwarp();  // the scratch is rewritten by the next pair's z pass
+                }
 
                 // park the pair in tensor memory
-                tmem_store_row<G::TX>(tbuf + static_cast<uint32_t>(k * 2 * G::TX), res);
+                tmem_store_row<G::TX>(tbuf + static_cast<uint32_t>(k * G::PCS), res);
             }
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             tc_fence_before();
@@ -1024,18 +1170,32 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                     for (int k = 0; k < NPW; ++k) {
                         const int j = stream_index(qd + 4 * sw) + NC * k;
                         float v[2 * G::TX];
-                        tmem_load_row<G::TX>(tb + static_cast<uint32_t>(sw * TC::per_warp + k * 2 * G::TX), v);
+                        tmem_load_row<G::TX>(tb + static_cast<uint32_t>(sw * TC::per_warp + k * G::PCS), v);
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                         const float xix = t.xi[j][0], xiy = t.xi[j][1], xiz = t.xi[j][2];
                         const float x2 = static_cast<float>(shell_xi2(shell_of(j)));
+                        if constexpr (G::kF32) {
 #pragma unroll
-                        for (int x = 0; x < G::TX; ++x) {
-                            const float f = v[2 * x], g = v[2 * x + 1];
-                            pm[0][x] += f;
-                            pm[1][x] += f * xix;
-                            pm[2][x] += f * xiy;
-                            pm[3][x] += f * xiz;
-                            pm[4][x] += f * x2 + g;
+                            for (int x = 0; x < G::TX; ++x) {
+                                const float f = v[2 * x], g = v[2 * x + 1];
+                                pm[0][x] += f;
+                                pm[1][x] += f * xix;
+                                pm[2][x] += f * xiy;
+                                pm[3][x] += f * xiz;
+                                pm[4][x] += f * x2 + g;
+                            }
+                        } else {
+                            // deviation sums: rho - rho0, rho u and sum w (|xi|^2 d + d_g)
+                            const float wj = t.w[j];
+#pragma unroll
+                            for (int x = 0; x < G::TX; ++x) {
+                                const float wd = wj * v[2 * x], g = v[2 * x + 1];
+                                pm[0][x] += wd;
+                                pm[1][x] += wd * xix;
+                                pm[2][x] += wd * xiy;
+                                pm[3][x] += wd * xiz;
+                                pm[4][x] += wd * x2 + wj * g;
+                            }
                         }
                     }
                 }
@@ -1048,7 +1208,11 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
             }
             epilogue_barrier_or(0);
             // per-node moments (quarters summed in a fixed order), tau, equilibrium coefficients
-            // (Eq. discreteEquilibrium, Sutherland's law) of this warp's share of the nodes
+            // (Eq. discreteEquilibrium, Sutherland's law) of this warp's share of the nodes.  A
+            // lane's row exists if it is one of the tile's x-rows and, in a partial tile, inside
+            // the mesh; rows that do not exist are neither checked nor stored.
+            const bool row_ok =
+                (G::ROWS == 32 || lane < G::ROWS) && (!kRaggedY || c0[1] * P + oy_l < a.cells[1] * P);
 #pragma unroll
             for (int xx = 0; xx < XS; ++xx) {
                 const int x = ep * XS + xx;
@@ -1058,31 +1222,75 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                 for (int q = 0; q < 5; ++q)
                     m[q] = (part[(0 * 5 + q) * QS + x * 32 + lane] + part[(1 * 5 + q) * QS + x * 32 + lane]) +
                            part[(2 * 5 + q) * QS + x * 32 + lane];
-                const float rho = m[0];
-                const float inv_rho = 1.0f / rho;
-                const float ux = m[1] * inv_rho, uy = m[2] * inv_rho, uz = m[3] * inv_rho;
-                const float usq = ux * ux + uy * uy + uz * uz;
-                const float T = (m[4] * inv_rho - usq) * static_cast<float>(a.inv_2cv);
-                if (a.flag != nullptr && !(rho > 0.f && T > 0.f && isfinite(rho) && isfinite(T))) atomicOr(a.flag, 1);
-                const float tau_r = static_cast<float>(a.mu_over_dt) * sutherland(T) / (rho * T) + 0.5f;
-                const EqCoef<float> ec = eq_coefficients(usq, T - 1.0f);
                 float* pn = prm + x * 32 + lane;
-                pn[0 * QS] = rho;
-                pn[1 * QS] = ux;
-                pn[2 * QS] = uy;
-                pn[3 * QS] = uz;
-                pn[4 * QS] = static_cast<float>(a.gfac) * T;
-                pn[5 * QS] = 1.0f / tau_r;
+                if constexpr (G::kF32) {
+                    const float rho = m[0];
+                    const float inv_rho = 1.0f / rho;
+                    const float ux = m[1] * inv_rho, uy = m[2] * inv_rho, uz = m[3] * inv_rho;
+                    const float usq = ux * ux + uy * uy + uz * uz;
+                    const float T = (m[4] * inv_rho - usq) * static_cast<float>(a.inv_2cv);
+                    if (a.flag != nullptr && row_ok && !(rho > 0.f && T > 0.f && isfinite(rho) && isfinite(T)))
+                        atomicOr(a.flag, 1);
+                    const float tau_r = static_cast<float>(a.mu_over_dt) * sutherland(T) / (rho * T) + 0.5f;
+                    const EqCoef<float> ec = eq_coefficients(usq, T - 1.0f);
+                    pn[0 * QS] = rho;
+                    pn[1 * QS] = ux;
+                    pn[2 * QS] = uy;
+                    pn[3 * QS] = uz;
+                    pn[4 * QS] = static_cast<float>(a.gfac) * T;
+                    pn[5 * QS] = 1.0f / tau_r;
 #pragma unroll
-                for (int sh = 0; sh < 4; ++sh) {
-                    pn[(6 + sh) * QS] = ec.c0[sh];
-                    pn[(10 + sh) * QS] = ec.c1[sh];
-                    pn[(14 + sh) * QS] = ec.c2[sh];
+                    for (int sh = 0; sh < 4; ++sh) {
+                        pn[(6 + sh) * QS] = ec.c0[sh];
+                        pn[(10 + sh) * QS] = ec.c1[sh];
+                        pn[(14 + sh) * QS] = ec.c2[sh];
+                    }
+                } else {
+                    // from the deviation sums with the quadrature identities sum w = 1,
+                    // sum w xi = 0, sum w |xi|^2 = D (the generic kernel's deviation collision):
+                    // 2 C_v rho (T - T0) = sum w (|xi|^2 d + d_g) + D rho0 (1 - T0) - rho |u|^2
+                    //                      - 2 C_v T0 (rho - rho0)
+                    const float rho0 = static_cast<float>(a.rho0), T0 = static_cast<float>(a.T0);
+                    const float two_cv = static_cast<float>(1.0 / a.inv_2cv), gfac = static_cast<float>(a.gfac);
+                    const float drho = m[0];
+                    const float rho = rho0 + drho;
+                    const float inv_rho = 1.0f / rho;
+                    const float ux = m[1] * inv_rho, uy = m[2] * inv_rho, uz = m[3] * inv_rho;
+                    const float usq = ux * ux + uy * uy + uz * uz;
+                    const float dT =
+                        (m[4] + 3.0f * rho0 * (1.0f - T0) - rho * usq - two_cv * T0 * drho) * inv_rho / two_cv;
+                    const float T = T0 + dT;
+                    if (a.flag != nullptr && row_ok && !(rho > 0.f && T > 0.f && isfinite(rho) && isfinite(T)))
+                        atomicOr(a.flag, 1);
+                    const float tau_r = static_cast<float>(a.mu_over_dt) * sutherland(T) / (rho * T) + 0.5f;
+                    const EqCoef<float> ec = eq_coefficients(usq, T - 1.0f);
+                    const float th = T - 1.0f;
+                    pn[0 * QS] = rho;
+                    pn[1 * QS] = ux;
+                    pn[2 * QS] = uy;
+                    pn[3 * QS] = uz;
+                    pn[4 * QS] = 1.0f / tau_r;
+                    pn[5 * QS] = drho;
+                    pn[6 * QS] = gfac * T * rho;
+                    pn[7 * QS] = gfac * (dT * rho + T0 * drho);
+#pragma unroll
+                    for (int sh = 0; sh < 4; ++sh) {
+                        // c0 - 1 without forming c0 (which is 1 + O(u^2, th))
+                        const float x2 = static_cast<float>(shell_xi2(sh));
+                        pn[(8 + sh) * QS] = -0.5f * usq + 0.5f * th * (x2 - 3.0f) + 0.125f * usq * usq +
+                                            0.25f * th * usq * (5.0f - x2) +
+                                            0.125f * th * th * (x2 * x2 - 10.0f * x2 + 15.0f);
+                        pn[(12 + sh) * QS] = ec.c1[sh];
+                        pn[(16 + sh) * QS] = ec.c2[sh];
+                    }
                 }
             }
             epilogue_barrier_or(0);
             // collision of the quarter's pairs at the lane's TX nodes, pair by pair
-            float rho_[G::TX], ux_[G::TX], uy_[G::TX], uz_[G::TX], gT_[G::TX], om_[G::TX];
+            // (FP32: gT_; deviations: dr_ = rho - rho0, gr_ and gb_ the g equilibrium's factor
+            // and offset)
+            float rho_[G::TX], ux_[G::TX], uy_[G::TX], uz_[G::TX], gT_[G::TX], om_[G::TX], dr_[G::TX], gr_[G::TX],
+                gb_[G::TX];
 #pragma unroll
             for (int x = 0; x < G::TX; ++x) {
                 const float* pn = prm + x * 32 + lane;
@@ -1090,8 +1298,15 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                 ux_[x] = pn[1 * QS];
                 uy_[x] = pn[2 * QS];
                 uz_[x] = pn[3 * QS];
-                gT_[x] = pn[4 * QS];
-                om_[x] = pn[5 * QS];
+                if constexpr (G::kF32) {
+                    gT_[x] = pn[4 * QS];
+                    om_[x] = pn[5 * QS];
+                } else {
+                    om_[x] = pn[4 * QS];
+                    dr_[x] = pn[5 * QS];
+                    gr_[x] = pn[6 * QS];
+                    gb_[x] = pn[7 * QS];
+                }
             }
             float2* dstp = static_cast<float2*>(a.dst);
             float4* st = stage + ep * 128;
@@ -1100,7 +1315,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                 for (int k = 0; k < NPW; ++k) {
                     const int j = stream_index(qd + 4 * sw) + NC * k;
                     float h[2 * G::TX];
-                    tmem_load_row<G::TX>(tb + static_cast<uint32_t>(sw * TC::per_warp + k * 2 * G::TX), h);
+                    tmem_load_row<G::TX>(tb + static_cast<uint32_t>(sw * TC::per_warp + k * G::PCS), h);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                     if (sw == nsw - 1 && k == NPW - 1) {
                         // the last read of this buffer: hand it back to the stream warps
@@ -1110,17 +1325,36 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                     }
                     const int sh = shell_of(j);
                     const float xix = t.xi[j][0], xiy = t.xi[j][1], xiz = t.xi[j][2], wj = t.w[j];
+                    if constexpr (G::kF32) {
 #pragma unroll
-                    for (int x = 0; x < G::TX; ++x) {
-                        const float* pn = prm + x * 32 + lane;
-                        const float sdot = xix * ux_[x] + xiy * uy_[x] + xiz * uz_[x];
-                        const float poly = pn[(6 + sh) * QS] +
-                                           sdot * (pn[(10 + sh) * QS] +
-                                                   sdot * (pn[(14 + sh) * QS] + sdot * (1.0f / 6.0f + sdot * (1.0f / 24.0f))));
-                        const float feq = wj * rho_[x] * poly;
-                        const float f = h[2 * x], g = h[2 * x + 1];
-                        h[2 * x] = f + om_[x] * (feq - f);
-                        h[2 * x + 1] = g + om_[x] * (gT_[x] * feq - g);
+                        for (int x = 0; x < G::TX; ++x) {
+                            const float* pn = prm + x * 32 + lane;
+                            const float sdot = xix * ux_[x] + xiy * uy_[x] + xiz * uz_[x];
+                            const float poly =
+                                pn[(6 + sh) * QS] +
+                                sdot * (pn[(10 + sh) * QS] +
+                                        sdot * (pn[(14 + sh) * QS] + sdot * (1.0f / 6.0f + sdot * (1.0f / 24.0f))));
+                            const float feq = wj * rho_[x] * poly;
+                            const float f = h[2 * x], g = h[2 * x + 1];
+                            h[2 * x] = f + om_[x] * (feq - f);
+                            h[2 * x + 1] = g + om_[x] * (gT_[x] * feq - g);
+                        }
+                    } else {
+                        // the collision written for the deviations (f^eq / (w rho) - 1 = pm1):
+                        //   d'  = d  + omega (rho pm1 + (rho - rho0) - d)
+                        //   dg' = dg + omega ((2C_v-D) (T rho pm1 + (T - T0) rho + T0 (rho - rho0)) - dg)
+#pragma unroll
+                        for (int x = 0; x < G::TX; ++x) {
+                            const float* pn = prm + x * 32 + lane;
+                            const float sdot = xix * ux_[x] + xiy * uy_[x] + xiz * uz_[x];
+                            const float pm1 =
+                                pn[(8 + sh) * QS] +
+                                sdot * (pn[(12 + sh) * QS] +
+                                        sdot * (pn[(16 + sh) * QS] + sdot * (1.0f / 6.0f + sdot * (1.0f / 24.0f))));
+                            const float d = h[2 * x], dg = h[2 * x + 1];
+                            h[2 * x] = d + om_[x] * (rho_[x] * pm1 + dr_[x] - d);
+                            h[2 * x + 1] = dg + om_[x] * (gr_[x] * pm1 + gb_[x] - dg);
+                        }
                     }
                     // streaming stores (the new state is not read again in this step, so it
                     // should not push the source boxes' halos out of L2), through the warp's
@@ -1128,20 +1362,72 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                     // (64 bytes each) instead of a quarter of 32 rows.  Chunk q of row r sits at
                     // float4 r*4 + (q ^ ((r >> 1) & 3)): both access patterns are free of bank
                     // conflicts.
-                    __syncwarp();
+                    if constexpr (G::kF32 && G::TX == 8) {
+                        __syncwarp();
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        st[lane * 4 + (q ^ ((lane >> 1) & 3))] =
-                            make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
-                    __syncwarp();
+                        for (int q = 0; q < 4; ++q)
+                            st[lane * 4 + (q ^ ((lane >> 1) & 3))] =
+                                make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+                        __syncwarp();
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int r = 8 * i + (lane >> 2), ch = lane & 3;
-                        const float4 vv = st[r * 4 + (ch ^ ((r >> 1) & 3))];
-                        const int oz = r / G::TY, oy = r % G::TY;
-                        const long long g0r =
-                            (static_cast<long long>(c0[2] * P + oz) * a.N[1] + (c0[1] * P + oy)) * a.N[0] + c0[0] * P;
-                        __stcs(reinterpret_cast<float4*>(dstp + static_cast<long long>(j) * a.nn + g0r) + ch, vv);
+                        for (int i = 0; i < 4; ++i) {
+                            const int r = 8 * i + (lane >> 2), ch = lane & 3;
+                            const float4 vv = st[r * 4 + (ch ^ ((r >> 1) & 3))];
+                            const int oz = r / G::TY, oy = r % G::TY;
+                            const long long g0r =
+                                (static_cast<long long>(c0[2] * P + oz) * a.N[1] + (c0[1] * P + oy)) * a.N[0] +
+                                c0[0] * P;
+                            __stcs(reinterpret_cast<float4*>(dstp + static_cast<long long>(j) * a.nn + g0r) + ch, vv);
+                        }
+                    } else {
+                        // the other row widths (FP32 rows of 6 nodes, 16-bit rows of 6 or 8): a
+                        // row is NCH chunks of CW 32-bit words (16 bytes where the row's bytes
+                        // and its start in the mesh allow it, else 8); lane r puts row r's
+                        // chunks into the staging buffer (odd chunk stride per row: no bank
+                        // conflicts), then consecutive lanes store consecutive chunks
+                        constexpr int RW = G::TX * G::PB / 4;
+                        constexpr bool k16 = (G::TX * G::PB) % 16 == 0 && (CX * P * G::PB) % 16 == 0;
+                        constexpr int CW = k16 ? 4 : 2;
+                        constexpr int NCH = RW / CW, NCHP = NCH | 1;
+                        static_assert(RW % CW == 0 && 32 * NCHP * CW * 4 <= 32 * 64, "staging buffer");
+                        uint32_t wv[RW];
+#pragma unroll
+                        for (int x = 0; x < G::TX; ++x) {
+                            if constexpr (G::kF32) {
+                                wv[2 * x] = __float_as_uint(h[2 * x]);
+                                wv[2 * x + 1] = __float_as_uint(h[2 * x + 1]);
+                            } else {
+                                wv[x] = narrow_pair<S>(h[2 * x], h[2 * x + 1]);
+                            }
+                        }
+                        uint32_t* stw = reinterpret_cast<uint32_t*>(st);
+                        __syncwarp();
+#pragma unroll
+                        for (int q = 0; q < NCH; ++q) {
+                            uint32_t* cp = stw + (lane * NCHP + q) * CW;
+                            if constexpr (CW == 4)
+                                *reinterpret_cast<uint4*>(cp) = make_uint4(wv[4 * q], wv[4 * q + 1], wv[4 * q + 2], wv[4 * q + 3]);
+                            else
+                                *reinterpret_cast<uint2*>(cp) = make_uint2(wv[2 * q], wv[2 * q + 1]);
+                        }
+                        __syncwarp();
+                        unsigned char* dstb = static_cast<unsigned char*>(a.dst);
+#pragma unroll
+                        for (int i = 0; i < (G::ROWS * NCH + 31) / 32; ++i) {
+                            const int q = 32 * i + lane;
+                            const int r = q / NCH, ch = q - r * NCH;
+                            const int oz = r / G::TY, oy = r - oz * G::TY;
+                            if (r >= G::ROWS || (kRaggedY && c0[1] * P + oy >= a.cells[1] * P)) continue;
+                            const uint32_t* cp = stw + (r * NCHP + ch) * CW;
+                            const long long g0r =
+                                (static_cast<long long>(c0[2] * P + oz) * a.N[1] + (c0[1] * P + oy)) * a.N[0] +
+                                c0[0] * P;
+                            unsigned char* gp = dstb + (static_cast<long long>(j) * a.nn + g0r) * G::PB + ch * CW * 4;
+                            if constexpr (CW == 4)
+                                __stcs(reinterpret_cast<uint4*>(gp), *reinterpret_cast<const uint4*>(cp));
+                            else
+                                __stcs(reinterpret_cast<uint2*>(gp), *reinterpret_cast<const uint2*>(cp));
+                        }
                     }
                 }
             }

@@ -37,8 +37,9 @@ def S():
     return sllbm
 
 
-def make(S, cells, p, storage, courant=2.0, pr=False, Ma=0.5):
-    cfg = S.Config(cells=tuple(cells), p=p, Ma=Ma, courant=courant, pr_correction=pr, storage=storage)
+def make(S, cells, p, storage, courant=2.0, pr=False, Ma=0.5, kernel=0):
+    cfg = S.Config(cells=tuple(cells), p=p, Ma=Ma, courant=courant, pr_correction=pr, storage=storage,
+                   kernel=kernel, nonfinite_check=True)
     return S.Sim(cfg)
 
 
@@ -79,7 +80,7 @@ def test_storage_round_trip_rounds_deviations(S, storage):
 @pytest.mark.parametrize("p,cells,pr", [(2, (3, 2, 4), False), (3, (3, 2, 2), False), (4, (2, 2, 1), False),
                                         (3, (2, 3, 2), True)])
 def test_one_step_matches_oracle_in_deviation_space(S, storage, p, cells, pr):
-    sim = make(S, cells, p, storage, courant=3.0, pr=pr)
+    sim = make(S, cells, p, storage, courant=3.0, pr=pr, kernel=1)
     assert sim.info.step_kernel == 1
     g = grid_of(sim, pr=pr)
     sim.set_populations(noneq_state(g, 11))
@@ -90,6 +91,55 @@ def test_one_step_matches_oracle_in_deviation_space(S, storage, p, cells, pr):
     d_got = deviations(sim.populations().cpu().numpy(), sim)
     bound = RELBITS[storage] * np.abs(d_ref) + 1e-5 * np.abs(d_ref).max()
     assert np.all(np.abs(d_got - d_ref) <= bound), float(np.max(np.abs(d_got - d_ref) / bound))
+
+
+# TMA-fed kernel at 16-bit storage: tiles of 4x4x2 (p = 2), 2x3x1 (p = 3) and 2x2x1 cells
+# (p = 4).  The smallest meshes wrap every source box (cp.async path), the larger ones have
+# interior tiles; (8, 7, 2) and (4, 4, 3) at p = 3 end in a partial tile row along y.
+TMA16_CASES = [(2, (4, 4, 2)), (2, (8, 4, 4)), (3, (4, 3, 2)), (3, (8, 7, 2)), (3, (4, 4, 3)), (4, (2, 2, 1)),
+               (4, (4, 6, 3))]
+
+
+@pytest.mark.parametrize("storage", ["f16dev", "bf16dev"])
+@pytest.mark.parametrize("p,cells", TMA16_CASES)
+def test_tma_step_matches_oracle_in_deviation_space(S, storage, p, cells):
+    """Two steps on the TMA-fed kernel, each compared with the oracle's step from the decoded
+    16-bit state the kernel started from (the bound of the generic kernel's test: output
+    rounding plus 1e-5 max|d| for the FP32 arithmetic)."""
+    sim = make(S, cells, p, storage, courant=3.0, kernel=2)
+    assert sim.info.step_kernel == 2
+    g = grid_of(sim)
+    sim.set_populations(noneq_state(g, 13))
+    for _ in range(2):
+        start = sim.populations().cpu().numpy()
+        ref = O.step(g, start, 1)
+        assert sim.step(1) == 0
+        d_ref = deviations(ref, sim)
+        d_got = deviations(sim.populations().cpu().numpy(), sim)
+        bound = RELBITS[storage] * np.abs(d_ref) + 1e-5 * np.abs(d_ref).max()
+        assert np.all(np.abs(d_got - d_ref) <= bound), float(np.max(np.abs(d_got - d_ref) / bound))
+    assert sim.status() == 0
+    sim.close()
+
+
+@pytest.mark.parametrize("storage", ["f16dev", "bf16dev"])
+def test_tma_and_generic_kernels_agree_at_16_bits(S, storage):
+    """Both kernels on the same 48^3-node Taylor-Green run (p = 3, 16^3 cells, C = 4): each
+    step rounds to 16 bits after FP32 arithmetic in a different order, so single elements
+    may round to neighbouring 16-bit values; the states stay within a few units of the last
+    place of the largest deviation."""
+    runs = []
+    for kernel in (1, 2):
+        sim = make(S, (16, 16, 16), 3, storage, courant=4.0, Ma=1.25, kernel=kernel)
+        assert sim.info.step_kernel == kernel
+        sim.init_tgv()
+        assert sim.step(5) == 0
+        runs.append(deviations(sim.populations().cpu().numpy(), sim))
+        sim.close()
+    a, b = runs
+    dmax = np.abs(a).max()
+    assert np.max(np.abs(a - b)) <= 8 * RELBITS[storage] * dmax
+    assert float(np.linalg.norm(a - b) / np.linalg.norm(a)) <= RELBITS[storage]
 
 
 def lebesgue_3d(g, dt):
@@ -112,8 +162,9 @@ def lebesgue_3d(g, dt):
     return lam
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
 @pytest.mark.parametrize("storage", ["f16dev", "bf16dev"])
-def test_full_size_first_step_sampled(S, storage):
+def test_full_size_first_step_sampled(S, storage, kernel):
     """The 192^3-node Ma 1.25 workload at 16-bit storage, in its benchmark launch
     configuration: one step from the Taylor-Green state, compared in deviation space at
     sampled nodes (the first and the last included) that the oracle evaluates one by one
@@ -127,8 +178,8 @@ def test_full_size_first_step_sampled(S, storage):
     derived constant."""
     import torch as T
     w = I.WORKLOADS["tgv_64c_p3_ma125"]
-    sim = make(S, w.cells, w.p, storage, courant=w.courant, Ma=w.Ma)
-    assert sim.info.step_kernel == 1
+    sim = make(S, w.cells, w.p, storage, courant=w.courant, Ma=w.Ma, kernel=kernel)
+    assert sim.info.step_kernel == kernel
     sim.init_tgv()
     assert sim.step(1) == 0
     g = grid_of(sim)
@@ -156,18 +207,21 @@ def test_full_size_first_step_sampled(S, storage):
 STATED_TGV = {"f16dev": (1e-4, 7.5e-4, 7.5e-5), "bf16dev": (1e-3, 6e-3, 6e-4)}
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
 @pytest.mark.parametrize("storage", ["f16dev", "bf16dev"])
-def test_taylor_green_run_against_fp64(S, storage):
+def test_taylor_green_run_against_fp64(S, storage, kernel):
     w = I.WORKLOADS["tgv_8c_p3"]
     runs = {}
     for st in ("f64", storage):
-        sim = S.Sim(S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, courant=w.courant, storage=st))
+        sim = S.Sim(S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, courant=w.courant, storage=st,
+                             kernel=kernel if st == storage else 1))
+        assert sim.info.step_kernel == (kernel if st == storage else 1)
         sim.init_tgv()
         assert sim.step(w.steps) == 0
         rho, u, T = sim.moments()
         runs[st] = (rho.cpu().numpy(), u.cpu().numpy(), T.cpu().numpy())
     errs = [float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(runs[storage], runs["f64"])]
-    print(storage, "relative L2 of rho, u, T after", w.steps, "steps:", errs)
+    print(storage, "kernel", kernel, "relative L2 of rho, u, T after", w.steps, "steps:", errs)
     for e, bound in zip(errs, STATED_TGV[storage]):
         assert e <= bound
 

@@ -144,11 +144,12 @@ def test_step_f32_matches_oracle(S, cells, p, pr):
     assert np.max(np.abs(got - ref)) <= 2e-6 * np.abs(ref).max()
 
 
-# TMA-fed kernel: tiles of 8x8x4 (p=2, 4), 9x9x3 (p=3) nodes.  On the small meshes every
-# source box wraps around the periodic boundary (16-byte cp.async path); the larger ones
-# have interior tiles (one TMA load per box).
+# TMA-fed kernel: tiles of 8x8x4 (p = 2, 4) and 6x9x3 (p = 3) nodes.  On the small meshes
+# every source box wraps around the periodic boundary (16-byte cp.async path); the larger ones
+# have interior tiles (one TMA load per box).  At p = 3 a y cell count that is not a multiple
+# of 3 ends in a partial tile row.
 TMA_CASES = [((2, 2, 1), 4), ((4, 2, 3), 4), ((6, 4, 2), 4), ((8, 4, 2), 2), ((8, 8, 6), 4),
-             ((12, 8, 4), 2)]
+             ((12, 8, 4), 2), ((2, 3, 1), 3), ((4, 4, 2), 3), ((8, 7, 3), 3), ((10, 12, 4), 3)]
 
 
 @pytest.mark.parametrize("cells,p", TMA_CASES)
@@ -185,10 +186,16 @@ def test_tma_kernel_refuses_meshes_it_cannot_tile(S):
     with pytest.raises(S.SllbmError):
         make(S, (2, 2, 2), 4, storage="f32", kernel=2, pr=True)
     assert make(S, (3, 2, 2), 4, storage="f32").info.step_kernel == 1
-    # p = 3: two tiles of streamed pairs do not fit in tensor memory; the generic kernel runs
+    # p = 3: tiles are 2 cells wide in x; 16-bit rows must also start on 16 bytes (N[0] a
+    # multiple of 4 pairs); the generic kernel runs where the TMA-fed one cannot
     with pytest.raises(S.SllbmError):
-        make(S, (6, 6, 3), 3, storage="f32", kernel=2)
-    assert make(S, (6, 6, 3), 3, storage="f32").info.step_kernel == 1
+        make(S, (3, 6, 3), 3, storage="f32", kernel=2)
+    assert make(S, (3, 6, 3), 3, storage="f32").info.step_kernel == 1
+    assert make(S, (6, 5, 3), 3, storage="f32").info.step_kernel == 2
+    with pytest.raises(S.SllbmError):
+        make(S, (6, 6, 3), 3, storage="f16dev", kernel=2)  # N[0] = 18
+    assert make(S, (6, 6, 3), 3, storage="f16dev").info.step_kernel == 1
+    assert make(S, (8, 6, 3), 3, storage="f16dev").info.step_kernel == 2
 
 
 @pytest.mark.parametrize("p", [2, 3, 4])

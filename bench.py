@@ -338,7 +338,9 @@ def mixed_precision_block(S, torch, device, steps, every, hbm, alu):
     fraction of the HBM peak at its algorithmic bytes, and the relative L2 error against the
     FP64 GPU run of rho, u, T after the last step and of the E_k(t) and dissipation
     eps_s(t) + eps_c(t) curves sampled every `every` steps.  The FP32-arithmetic storages run
-    a second time with compensated moment sums ("<storage>_comp")."""
+    a second time with compensated moment sums ("<storage>_comp"), and the 16-bit storages a
+    second time on the TMA-fed kernel ("<storage>_tma"; the automatic choice at p = 3 is the
+    generic kernel, the faster one there)."""
     import numpy as np
 
     w = I.WORKLOADS["tgv_64c_p3_ma125"]
@@ -348,10 +350,12 @@ def mixed_precision_block(S, torch, device, steps, every, hbm, alu):
            "configured_steps": w.steps, "curve_every": every, "reference": "f64 (GPU)"}
     ref = None
     flops = algorithmic_flops_per_node(w.p)
-    for name in ("f64", "f32", "f16dev", "bf16dev", "f32_comp", "f16dev_comp", "bf16dev_comp"):
+    for name in ("f64", "f32", "f16dev", "bf16dev", "f16dev_tma", "bf16dev_tma", "f32_comp", "f16dev_comp",
+                 "bf16dev_comp"):
         st = name.split("_")[0]
         sim = S.Sim(S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, Pr=w.Pr, gamma=w.gamma,
-                             courant=w.courant, pr_correction=w.pr_correction, storage=st),
+                             courant=w.courant, pr_correction=w.pr_correction, storage=st,
+                             kernel=2 if name.endswith("_tma") else 0),
                     device=device)
         if name.endswith("_comp"):
             S.sllbm_set_compensated(sim.ctx, True)

@@ -82,7 +82,7 @@ typedef enum {
  * weights of each pass sum to one), forms rho - rho0, rho u and 2 rho (T - T0) C_v from
  * deviation sums with the exact quadrature identities sum w_i = 1, sum w_i xi_i = 0,
  * sum w_i |xi_i|^2 = 3 (no cancellation against the reference state), collides in FP32 and
- * stores deviations again.  The generic kernel runs these types. */
+ * stores deviations again.  Both step kernels run these types. */
 
 /* Physical and run parameters.  Taylor-Green scaling (Sec. III.C): U0 = Ma*sqrt(gamma*T0),
  * mu_inf = rho0*U0*1/Re (reference length 1), unless mu_inf_override > 0. */
@@ -107,7 +107,8 @@ typedef struct {
                                N[0] a multiple of 2 (FP32) or 4 (16-bit), cells divisible by its
                                tile of 4x4x2 (p = 2), 2x3x1 (p = 3: y may end in a partial
                                tile) or 2x2x1 cells (p = 4), no Prandtl term, collide on, no
-                               compensated sums; else SLLBM_EINVAL) */
+                               compensated sums; else SLLBM_EINVAL).  Automatic: the TMA-fed
+                               kernel where it can run, except at p = 3 with 16-bit storage */
 } sllbm_params;
 
 /* Read-only description of a created context. */

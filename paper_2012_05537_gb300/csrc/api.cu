@@ -280,11 +280,17 @@ __global__ void sum_partials_kernel(const double* __restrict__ partials, int nbl
 namespace sllbm {
 
 // 1: generic tile kernel, 2: TMA-fed persistent kernel, 0: the requested kernel cannot run.
+// The automatic choice takes the TMA-fed kernel where it can run, except for p = 3 with 16-bit
+// storage: there its 6x9x3-node tiles (27 of 32 lanes, smaller tiles than at p = 2 and 4) and
+// the widening of every stored pair leave it about 15 % slower than the generic kernel with
+// two CTAs per SM (measured on GB300 at 132^3 and 192^3 nodes), while at p = 2 and 4 and for
+// FP32 storage it is as fast or faster.
 int choose_step_kernel(const sllbm_ctx* c) {
     const bool tma_ok = tma_step_eligible(c);
     if (c->prm.kernel == 2) return tma_ok ? 2 : 0;
     if (c->prm.kernel == 1) return 1;
-    return tma_ok ? 2 : 1;
+    const bool dev16 = c->prm.storage == SLLBM_F16DEV || c->prm.storage == SLLBM_BF16DEV;
+    return (tma_ok && !(dev16 && c->p == 3)) ? 2 : 1;
 }
 
 }  // namespace sllbm

@@ -195,7 +195,11 @@ def test_tma_kernel_refuses_meshes_it_cannot_tile(S):
     with pytest.raises(S.SllbmError):
         make(S, (6, 6, 3), 3, storage="f16dev", kernel=2)  # N[0] = 18
     assert make(S, (6, 6, 3), 3, storage="f16dev").info.step_kernel == 1
-    assert make(S, (8, 6, 3), 3, storage="f16dev").info.step_kernel == 2
+    # 16-bit at p = 3: the TMA-fed kernel runs when asked for, the automatic choice is the
+    # generic kernel (the faster one there); at p = 4 it is the TMA-fed kernel
+    assert make(S, (8, 6, 3), 3, storage="f16dev", kernel=2).info.step_kernel == 2
+    assert make(S, (8, 6, 3), 3, storage="f16dev").info.step_kernel == 1
+    assert make(S, (2, 2, 1), 4, storage="bf16dev").info.step_kernel == 2
 
 
 @pytest.mark.parametrize("p", [2, 3, 4])

@@ -1310,6 +1310,36 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
             }
             float2* dstp = static_cast<float2*>(a.dst);
             float4* st = stage + ep * 128;
+            // Where this lane's store chunks go, as (f, g)-pair offsets inside one velocity's
+            // block of the destination (the same for every pair of the tile; -1: a row outside
+            // the mesh), and where it reads them in the staging buffer.  (Node offsets stay
+            // below 2^31: buffers hold at most 2^31 nodes per velocity.)
+            constexpr int RW_ = G::TX * G::PB / 4;
+            constexpr bool k16_ = (G::TX * G::PB) % 16 == 0 && (CX * P * G::PB) % 16 == 0;
+            constexpr int CW_ = k16_ ? 4 : 2;
+            constexpr int NCH_ = RW_ / CW_, NCHP_ = NCH_ | 1;
+            constexpr bool kStaged8 = G::kF32 && G::TX == 8;
+            constexpr int NI = kStaged8 ? 4 : (G::ROWS * NCH_ + 31) / 32;
+            int goff[NI], sidx[NI];
+#pragma unroll
+            for (int i = 0; i < NI; ++i) {
+                int r, ch;
+                if constexpr (kStaged8) {
+                    r = 8 * i + (lane >> 2);
+                    ch = lane & 3;
+                    sidx[i] = r * 4 + (ch ^ ((r >> 1) & 3));
+                } else {
+                    const int q = 32 * i + lane;
+                    r = q / NCH_;
+                    ch = q - r * NCH_;
+                    sidx[i] = (r * NCHP_ + ch) * CW_;
+                }
+                const int oz = r / G::TY, oy = r - (r / G::TY) * G::TY;
+                const bool ok = r < G::ROWS && (!kRaggedY || c0[1] * P + oy < a.cells[1] * P);
+                goff[i] = ok ? ((c0[2] * P + oz) * a.N[1] + (c0[1] * P + oy)) * a.N[0] + c0[0] * P +
+                                   ch * (CW_ * 4 / G::PB)
+                             : -1;
+            }
             for (int sw = 0; sw < nsw; ++sw) {
 #pragma unroll 1
                 for (int k = 0; k < NPW; ++k) {
@@ -1369,16 +1399,9 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                             st[lane * 4 + (q ^ ((lane >> 1) & 3))] =
                                 make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
                         __syncwarp();
+                        float2* dj = dstp + static_cast<long long>(j) * a.nn;
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const int r = 8 * i + (lane >> 2), ch = lane & 3;
-                            const float4 vv = st[r * 4 + (ch ^ ((r >> 1) & 3))];
-                            const int oz = r / G::TY, oy = r % G::TY;
-                            const long long g0r =
-                                (static_cast<long long>(c0[2] * P + oz) * a.N[1] + (c0[1] * P + oy)) * a.N[0] +
-                                c0[0] * P;
-                            __stcs(reinterpret_cast<float4*>(dstp + static_cast<long long>(j) * a.nn + g0r) + ch, vv);
-                        }
+                        for (int i = 0; i < 4; ++i) __stcs(reinterpret_cast<float4*>(dj + goff[i]), st[sidx[i]]);
                     } else {
                         // the other row widths (FP32 rows of 6 nodes, 16-bit rows of 6 or 8): a
                         // row is NCH chunks of CW 32-bit words (16 bytes where the row's bytes
@@ -1411,22 +1434,15 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                                 *reinterpret_cast<uint2*>(cp) = make_uint2(wv[2 * q], wv[2 * q + 1]);
                         }
                         __syncwarp();
-                        unsigned char* dstb = static_cast<unsigned char*>(a.dst);
+                        unsigned char* dj = static_cast<unsigned char*>(a.dst) + static_cast<long long>(j) * a.nn * G::PB;
 #pragma unroll
-                        for (int i = 0; i < (G::ROWS * NCH + 31) / 32; ++i) {
-                            const int q = 32 * i + lane;
-                            const int r = q / NCH, ch = q - r * NCH;
-                            const int oz = r / G::TY, oy = r - oz * G::TY;
-                            if (r >= G::ROWS || (kRaggedY && c0[1] * P + oy >= a.cells[1] * P)) continue;
-                            const uint32_t* cp = stw + (r * NCHP + ch) * CW;
-                            const long long g0r =
-                                (static_cast<long long>(c0[2] * P + oz) * a.N[1] + (c0[1] * P + oy)) * a.N[0] +
-                                c0[0] * P;
-                            unsigned char* gp = dstb + (static_cast<long long>(j) * a.nn + g0r) * G::PB + ch * CW * 4;
+                        for (int i = 0; i < NI; ++i) {
+                            if (goff[i] < 0) continue;
+                            unsigned char* gp = dj + static_cast<long long>(goff[i]) * G::PB;
                             if constexpr (CW == 4)
-                                __stcs(reinterpret_cast<uint4*>(gp), *reinterpret_cast<const uint4*>(cp));
+                                __stcs(reinterpret_cast<uint4*>(gp), *reinterpret_cast<const uint4*>(stw + sidx[i]));
                             else
-                                __stcs(reinterpret_cast<uint2*>(gp), *reinterpret_cast<const uint2*>(cp));
+                                __stcs(reinterpret_cast<uint2*>(gp), *reinterpret_cast<const uint2*>(stw + sidx[i]));
                         }
                     }
                 }

@@ -103,6 +103,8 @@ def parse_args():
     ap.add_argument("--workload", default="tgv_32c_p4", choices=sorted(I.WORKLOADS))
     ap.add_argument("--storage", choices=["f32", "f64", "f16dev", "bf16dev"], default=None)
     ap.add_argument("--e2e-steps", type=int, default=40)
+    ap.add_argument("--kernel", type=int, choices=[0, 1, 2], default=0,
+                    help="step kernel of the headline run: 0 automatic, 1 generic, 2 TMA-fed")
     ap.add_argument("--periodic-z", choices=["ghost", "wrap"], default="ghost",
                     help="z boundary of the headline mesh: ghost planes (the mesh as one periodic z-slab, "
                          "refreshed in place before each step) or source boxes wrapping around")
@@ -700,7 +702,7 @@ def run_mine(args, rank, world, local):
     ghost = args.periodic_z == "ghost"
     cfg = S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, Pr=w.Pr, gamma=w.gamma,
                    courant=w.courant, pr_correction=w.pr_correction, storage=storage,
-                   slab=(0, w.cells[2]) if ghost else None)
+                   slab=(0, w.cells[2]) if ghost else None, kernel=args.kernel)
     sim = S.Sim(cfg, device=f"cuda:{local}")
     sim.init_tgv()
     for _ in range(max(3, args.warmup)):

@@ -31,9 +31,9 @@ template <>
 struct TmaTile<4> {
     static constexpr int CX = 2, CY = 2, CZ = 1;
 };
-// Stream warps (45 velocity pairs split evenly: 9 x 5).
+// Stream warps (45 velocity pairs: one warp with 5, ten with 4).
 template <int P>
-constexpr int kConsumersFor = 9;
+constexpr int kConsumersFor = kStreamWarps;
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static std::once_flag once;

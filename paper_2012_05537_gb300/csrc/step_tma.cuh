@@ -1,7 +1,7 @@
-// Fused SLLBM step for FP32 storage on sm_100-family GPUs: TMA-fed, warp-specialised,
-// persistent, with the streamed populations parked in tensor memory.  Same arithmetic as
-// step_kernel.cuh (Eq. interpolation, Eq. moments, Eq. discreteEquilibrium, Eq. LBM),
-// organised for GB300:
+// Fused SLLBM step for FP32 and 16-bit deviation storage on sm_100-family GPUs: TMA-fed,
+// warp-specialised, persistent, with the streamed populations parked in tensor memory.  Same
+// arithmetic as step_kernel.cuh (Eq. interpolation, Eq. moments, Eq. discreteEquilibrium,
+// Eq. LBM), organised for GB300:
 //
 //  * One persistent CTA per SM walks tiles of CX x CY x CZ cells (TX x TY x TZ nodes).
 //  * A producer warp loads, for every velocity i of a tile, the source box of the pair
@@ -15,17 +15,18 @@
 //    copies from the wrapped positions when that takes too many images.  Items are handed
 //    over through a ring of 32 descriptors: full/empty mbarriers (transaction counts) and
 //    an item table entry that tells the consumers where the item's box sits.
-//  * NC stream warps own 45/NC velocity pairs each.  For a pair they run the z and y
-//    Lagrange passes in place in the box (each lane owns whole columns) and the x pass
-//    into registers (lane = one x-row of the tile), then release the box.  f_i and g_i
-//    share weights and positions, so every FMA is a packed FP32x2 FMA.  The streamed
-//    (f_i, g_i) of the lane's TX nodes go to the lane's row of tensor memory (tcgen05.st),
-//    in one of two buffers per tile parity.
+//  * 11 stream warps own 4 or 5 velocity pairs each.  For a pair they run the z and y
+//    Lagrange passes in place in the box (each lane owns whole columns; a 16-bit box is
+//    widened to FP32 by the z pass, into the warp's scratch) and the x pass into registers
+//    (lane = one x-row of the tile), then release the box.  f_i and g_i share weights and
+//    positions, so every FMA is a packed FP32x2 FMA.  The streamed (f_i, g_i) of the lane's
+//    TX nodes go to the lane's row of tensor memory (tcgen05.st), in one of two buffers per
+//    tile parity.
 //  * Four epilogue warps, one per tensor-memory lane quarter, take a tile's buffer once the
 //    quarter's stream warps are done with it: per-node moment sums of the quarter's pairs,
 //    the sum over the quarters in a fixed order (deterministic), rho, u, T, omega and the
 //    shell coefficients of the quartic equilibrium (each epilogue warp a quarter of the
-//    nodes), then the collision of the quarter's pairs and 16-byte stores (f_i and g_i
+//    nodes), then the collision of the quarter's pairs and 16- or 8-byte stores (f_i and g_i
 //    interleaved).  Meanwhile the stream warps fill the other buffer: streaming never
 //    waits for the collision.
 //  * Every mbarrier wait is bounded; on expiry the kernel raises an error flag, the stream
@@ -114,29 +115,31 @@ struct TmaMaps {
 };
 
 constexpr int kNParams = 18;  // rho, ux, uy, uz, gT, omega, c0[4], c1[4], c2[4]
-// Warp roles.  A warp's SM sub-partition is its index mod 4.  The producer (warp 1; with
-// SLLBM_TMA_PRODUCERS=3, warps 1, 5, 9) has sub-partition 1 to itself, so that its
-// latency-bound issue path is not starved of issue slots; the 9 stream warps are 0, 2, 3, 4,
-// 6, 7, 8, 10, 11 (three per tensor-memory lane quarter 0, 2, 3, the quarter a warp may touch
-// being its index mod 4) and the 3 epilogue warps 12, 14, 15 (one per used quarter); the
-// other warps of sub-partition 1 have no work.  (Three producers, each serving the
-// velocities of one residue mod 3 from its own third of the ring, measured faster on a 96^3
-// mesh and slower on 128^3.)
+
+// Warp roles.  A warp's SM sub-partition is its index mod 4, and so is the tensor-memory lane
+// quarter it may touch.  Warp 1 is the producer; warps 12..15 are the epilogue warps, one per
+// quarter; the other 11 are stream warps, three in quarters 0, 2 and 3 and two (5, 9) in
+// quarter 1, next to the producer.  Stream warp c (c = 0..10, warp 5 first) streams the pairs
+// j = c, c + 11, c + 22, ... (five for c = 0, four for the others), so the quarters hold
+// 12, 9, 12 and 12 pairs: every sub-partition has work, and the one with the producer the
+// least.  (Nine stream warps in quarters 0, 2, 3 with 15 pairs each and sub-partition 1 left
+// to the producer alone measured 3 % slower at p = 4 and 7-9 % slower at p = 3.)
 constexpr int kWarps = 16;
-constexpr int kEpilogueWarps = 3;
-#ifndef SLLBM_TMA_PRODUCERS
-#define SLLBM_TMA_PRODUCERS 1
-#endif
-constexpr int NPROD = SLLBM_TMA_PRODUCERS;  // producers; producer p serves velocities j = p (mod NPROD)
-constexpr int IPP = kQ / NPROD;             // items per tile and producer
-static_assert((NPROD == 1 || NPROD == 3) && IPP * NPROD == kQ && IPP <= 64, "items per producer");
-__host__ __device__ constexpr bool is_producer_warp(int w) { return w < 4 * NPROD && (w & 3) == 1; }
-__host__ __device__ constexpr int producer_index(int w) { return w >> 2; }
-__host__ __device__ constexpr bool is_stream_warp(int w) { return w < 12 && (w & 3) != 1; }
-static_assert(9 % NPROD == 0, "a stream warp's pairs all come from one producer");
-__host__ __device__ constexpr int stream_index(int w) { return w - ((w + 2) >> 2); }
-__host__ __device__ constexpr bool is_epilogue_warp(int w) { return w == 12 || w == 14 || w == 15; }
-__host__ __device__ constexpr int epilogue_index(int w) { return w == 12 ? 0 : w - 13; }
+constexpr int kEpilogueWarps = 4;
+constexpr int kStreamWarps = 11;
+constexpr int kMaxPairsPerWarp = (kQ + kStreamWarps - 1) / kStreamWarps;  // 5
+constexpr int NPROD = 1;    // producers
+constexpr int IPP = kQ;     // items per tile and producer
+__host__ __device__ constexpr bool is_producer_warp(int w) { return w == 1; }
+__host__ __device__ constexpr int producer_index(int) { return 0; }
+__host__ __device__ constexpr bool is_stream_warp(int w) { return w < 12 && w != 1; }
+__host__ __device__ constexpr int stream_index(int w) { return w == 5 ? 0 : (w == 0 ? 1 : (w < 5 ? w : w - 1)); }
+// velocity pairs of stream warp c, and the k-th of them
+__host__ __device__ constexpr int pairs_of(int c) { return (kQ - c + kStreamWarps - 1) / kStreamWarps; }
+__host__ __device__ constexpr int pair_of(int c, int k) { return c + kStreamWarps * k; }
+__host__ __device__ constexpr bool is_epilogue_warp(int w) { return w >= 12; }
+__host__ __device__ constexpr int epilogue_index(int w) { return w - 12; }
+static_assert(pairs_of(0) == kMaxPairsPerWarp && pairs_of(1) == 4 && pairs_of(10) == 4, "pair split");
 // A source box that crosses the periodic boundary is loaded as one TMA box per periodic image
 // it overlaps (zero outside the domain), at most kMaxPieces of them, back to back in the ring;
 // boxes with more images (meshes not much larger than a tile), or whose images would not fit
@@ -158,9 +161,9 @@ struct TmaSmem {
     // (FP32 storage); rho, ux, uy, uz, omega, rho - rho0, (2C_v-D) T rho, (2C_v-D)((T - T0) rho
     // + T0 (rho - rho0)), c0[4] - 1, c1[4], c2[4] (deviation storage)
     static constexpr int kNPar = G::kF32 ? kNParams : kNParams + 2;
-    // the per-quarter moment sums (3 quarters x 5) and the per-node parameters share one region:
+    // the per-quarter moment sums (4 quarters x 5) and the per-node parameters share one region:
     // an epilogue warp reads the sums of exactly the node columns whose parameters it writes
-    static constexpr int kShared = 3 * 5 > kNPar ? 3 * 5 : kNPar;
+    static constexpr int kShared = 4 * 5 > kNPar ? 4 * 5 : kNPar;
     static constexpr size_t partials = round128(size_t(kShared) * G::TX * 32 * sizeof(float));
     static constexpr size_t params = 0;
     static constexpr size_t tables = round128(sizeof(StepTablesS<P>));
@@ -183,9 +186,10 @@ struct TmaSmem {
     static_assert(ring_units / NPROD >= G::SLOT_BYTES / 128, "each producer's ring holds the largest box");
 };
 
-// Tensor-memory columns: a stream warp's lane keeps NPW pairs x 2*TX floats per tile (PCS
+// Tensor-memory columns: a stream warp's lane keeps up to NPW pairs x 2*TX floats per tile (PCS
 // columns per pair); stream warps w, w+4, w+8 share a 32-lane quarter (the quarter a warp may
-// touch is fixed by w % 4); each quarter holds two tiles (buffers).
+// touch is fixed by w % 4; warp w's columns are the (w / 4)-th share); each quarter holds two
+// tiles (buffers).
 template <int PCS, int NPW, int NC>
 struct TmemCols {
     static constexpr int per_warp = NPW * PCS;
@@ -500,8 +504,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                     const __grid_constant__ StepTablesS<P> tpar) {
     using G = TmaGeom<S, P, CX, CY, CZ>;
     using SM = TmaSmem<S, P, CX, CY, CZ, NC>;
-    constexpr int NPW = kQ / NC;  // velocity pairs per consumer warp
-    static_assert(NPW * NC == kQ, "consumers must split the 45 pairs evenly");
+    constexpr int NPW = kMaxPairsPerWarp;  // velocity pairs per stream warp, at most
     using TC = TmemCols<G::PCS, NPW, NC>;
     // (x in the tensor maps counts floats for FP32 storage, (f, g) pairs for 16-bit storage)
     constexpr int XM = G::kF32 ? 2 : 1;
@@ -510,7 +513,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     constexpr bool kRaggedY = CY == 3;
     constexpr uint32_t KM = kItems - 1;
     constexpr int NE = kEpilogueWarps;
-    static_assert(NC == 9 && NE == 3, "warp roles");
+    static_assert(NC == kStreamWarps && NE == 4, "warp roles");
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -548,7 +551,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
             for (int e = 0; e < kItems; ++e) items[pp * 3 * kItems + e] = ~0ull;
         for (int q = 0; q < 4; ++q)
             for (int b = 0; b < 2; ++b) {
-                mbar_init(tmem_full0 + 8 * (q * 2 + b), q == 1 ? 1u : 3u);  // stream warps per quarter
+                mbar_init(tmem_full0 + 8 * (q * 2 + b), q == 1 ? 2u : 3u);  // stream warps per quarter
                 mbar_init(tmem_empty0 + 8 * (q * 2 + b), 1);
             }
         *abort_flag = 0;
@@ -826,18 +829,18 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         return;
     }
 
-    if (!is_stream_warp(warp) && !is_epilogue_warp(warp)) return;  // no work
 
     // ---------------------------------------------------- stream warps
-    // Warp c streams pairs c, c + NC, ... of every tile of the CTA into tensor-memory buffer
-    // it & 1 of its lane quarter (c % 4), then hands the buffer to the quarter's epilogue warp
-    // (tmem_full); before reusing a buffer it waits until that warp has read it (tmem_empty).
+    // Stream warp c streams its pairs pair_of(c, k) of every tile of the CTA into tensor-memory
+    // buffer it & 1 of its lane quarter (its warp index mod 4), then hands the buffer to the
+    // quarter's epilogue warp (tmem_full); before reusing a buffer it waits until that warp has
+    // read it (tmem_empty).
     const int ncta = ntiles > static_cast<int>(blockIdx.x)
                          ? (ntiles - 1 - static_cast<int>(blockIdx.x)) / static_cast<int>(gridDim.x) + 1
                          : 0;
     const int oz_l = lane / G::TY, oy_l = lane % G::TY;
     if (is_stream_warp(warp)) {
-        const int c = stream_index(warp), qd = warp & 3;
+        const int c = stream_index(warp), qd = warp & 3, npw = pairs_of(c);
         const uint32_t pbase = static_cast<uint32_t>((c % NPROD) * 3 * kItems);  // its producer's block
         const bool row_lane = lane < G::ROWS;
         const uint32_t tmem_warp = *tmem_base_s + (static_cast<uint32_t>(qd * 32) << 16) +
@@ -855,8 +858,8 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
             tc_fence_after();
             const uint32_t tbuf = tmem_warp + static_cast<uint32_t>(bf * TC::per_buf);
 #pragma unroll 1
-            for (int k = 0; k < NPW; ++k) {
-                const int j = c + NC * k;
+            for (int k = 0; k < npw; ++k) {
+                const int j = pair_of(c, k);
                 const uint32_t s = static_cast<uint32_t>(it) * IPP + static_cast<uint32_t>(j / NPROD);
                 // Where the item sits in the ring.  The producer announces item s only once item
                 // s - kItems has released the same descriptor, so its full barrier is then at most
@@ -1137,13 +1140,15 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     }
     // ---------------------------------------------------- epilogue warps
     // One per lane quarter.  Per tile: the moment sums of the quarter's pairs (streamed by
-    // warps q, q + 4, q + 8), the sum over the quarters in a fixed order and the per-node
-    // parameters (each epilogue warp a share of the nodes), then the BGK collision and the
-    // stores of the quarter's pairs.  The epilogue warps meet at named barrier 2.
+    // warps q, q + 4, q + 8; q + 4, q + 8 in quarter 1), the sum over the quarters in a fixed
+    // order and the per-node parameters (each epilogue warp a share of the nodes), then the BGK
+    // collision and the stores of the quarter's pairs.  The epilogue warps meet at named
+    // barrier 2.
     else if (is_epilogue_warp(warp)) {
         const int ep = epilogue_index(warp);  // 0 .. NE-1: share of the nodes whose parameters it forms
-        const int qd = warp & 3;              // the lane quarter it reads (0, 2 or 3)
-        constexpr int nsw = 3;                // stream warps in the quarter: qd, qd + 4, qd + 8
+        const int qd = warp & 3;              // the lane quarter it reads (= ep)
+        constexpr int nsw = 3;                // stream warp slots in the quarter: warps qd, qd + 4, qd + 8
+        const int sw0 = qd == 1 ? 1 : 0;      // (warp 1 is the producer)
         const uint32_t tq = *tmem_base_s + (static_cast<uint32_t>(qd * 32) << 16);
         constexpr int QS = G::TX * 32;  // stride between parameters
         constexpr int XS = (G::TX + NE - 1) / NE;  // node columns per epilogue warp (the last one fewer)
@@ -1165,10 +1170,11 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                 for (int q = 0; q < 5; ++q)
 #pragma unroll
                     for (int x = 0; x < G::TX; ++x) pm[q][x] = 0.f;
-                for (int sw = 0; sw < nsw; ++sw) {
+                for (int sw = sw0; sw < nsw; ++sw) {
+                    const int cw = stream_index(qd + 4 * sw), npw = pairs_of(cw);
 #pragma unroll 1
-                    for (int k = 0; k < NPW; ++k) {
-                        const int j = stream_index(qd + 4 * sw) + NC * k;
+                    for (int k = 0; k < npw; ++k) {
+                        const int j = pair_of(cw, k);
                         float v[2 * G::TX];
                         tmem_load_row<G::TX>(tb + static_cast<uint32_t>(sw * TC::per_warp + k * G::PCS), v);
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -1200,7 +1206,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                     }
                 }
                 // layout [quarter][moment][x][lane] (node = lane*TX + x): contiguous lane accesses
-                float* pc = part + static_cast<size_t>(qd == 0 ? 0 : qd - 1) * 5 * QS + lane;
+                float* pc = part + static_cast<size_t>(qd) * 5 * QS + lane;
 #pragma unroll
                 for (int q = 0; q < 5; ++q)
 #pragma unroll
@@ -1220,8 +1226,9 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                 float m[5];
 #pragma unroll
                 for (int q = 0; q < 5; ++q)
-                    m[q] = (part[(0 * 5 + q) * QS + x * 32 + lane] + part[(1 * 5 + q) * QS + x * 32 + lane]) +
-                           part[(2 * 5 + q) * QS + x * 32 + lane];
+                    m[q] = ((part[(0 * 5 + q) * QS + x * 32 + lane] + part[(1 * 5 + q) * QS + x * 32 + lane]) +
+                            part[(2 * 5 + q) * QS + x * 32 + lane]) +
+                           part[(3 * 5 + q) * QS + x * 32 + lane];
                 float* pn = prm + x * 32 + lane;
                 if constexpr (G::kF32) {
                     const float rho = m[0];
@@ -1340,14 +1347,15 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                                    ch * (CW_ * 4 / G::PB)
                              : -1;
             }
-            for (int sw = 0; sw < nsw; ++sw) {
+            for (int sw = sw0; sw < nsw; ++sw) {
+                const int cw = stream_index(qd + 4 * sw), npw = pairs_of(cw);
 #pragma unroll 1
-                for (int k = 0; k < NPW; ++k) {
-                    const int j = stream_index(qd + 4 * sw) + NC * k;
+                for (int k = 0; k < npw; ++k) {
+                    const int j = pair_of(cw, k);
                     float h[2 * G::TX];
                     tmem_load_row<G::TX>(tb + static_cast<uint32_t>(sw * TC::per_warp + k * G::PCS), h);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    if (sw == nsw - 1 && k == NPW - 1) {
+                    if (sw == nsw - 1 && k == npw - 1) {
                         // the last read of this buffer: hand it back to the stream warps
                         tc_fence_before();
                         __syncwarp();

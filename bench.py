@@ -390,6 +390,24 @@ def mixed_precision_block(S, torch, device, steps, every, hbm, alu):
             rec["speedup_vs_f64"] = ref[5] / kms
         out[name] = rec
         sim.close()
+    # The same workload as one periodic z-slab with ghost planes (the headline's mode; no
+    # source box wraps around along z), timing only: sllbm_diag refuses slab contexts, so no
+    # curves; the automatic kernel choice is the TMA-fed kernel here for every storage.
+    ghost = {}
+    for st in ("f32", "f16dev", "bf16dev"):
+        sim = S.Sim(S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, Pr=w.Pr, gamma=w.gamma,
+                             courant=w.courant, pr_correction=w.pr_correction, storage=st,
+                             slab=(0, w.cells[2]), nonfinite_check=True), device=device)
+        sim.init_tgv()
+        time_steps(sim, torch, 3, per_launch=False)
+        _, kern = time_steps(sim, torch, every)
+        kms = statistics.median(kern)
+        bpn = 2 * 45 * 2 * ELEM_BYTES[st]
+        ghost[st] = {"kernel_ms": kms, "value": sim.nodes / (kms / 1e3), "unit": UNIT,
+                     "hbm_frac": bpn * sim.nodes / (kms / 1e3) / 1e9 / hbm, "step_kernel": int(sim.info.step_kernel),
+                     "steps_timed": every, "status": int(sim.status())}
+        sim.close()
+    out["ghost_planes_timing"] = ghost
     return out
 
 

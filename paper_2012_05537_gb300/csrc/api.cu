@@ -281,16 +281,18 @@ namespace sllbm {
 
 // 1: generic tile kernel, 2: TMA-fed persistent kernel, 0: the requested kernel cannot run.
 // The automatic choice takes the TMA-fed kernel where it can run, except for p = 3 with 16-bit
-// storage: there its 6x9x3-node tiles (27 of 32 lanes, smaller tiles than at p = 2 and 4) and
-// the widening of every stored pair leave it about 15 % slower than the generic kernel with
-// two CTAs per SM (measured on GB300 at 132^3 and 192^3 nodes), while at p = 2 and 4 and for
-// FP32 storage it is as fast or faster.
+// storage on an ordinary periodic context: there its 6x9x3-node tiles (27 of 32 lanes), the
+// widening of every stored pair and the two periodic images of the boxes that wrap around
+// along z leave it 9-18 % slower than the generic kernel with two CTAs per SM, while on a slab
+// (whose boxes never wrap along z, e.g. the whole mesh with ghost planes) it is as fast or
+// 6 % faster (measured on GB300 at 132^3 and 192^3 nodes).  At p = 2 and 4 and for FP32
+// storage it is as fast or faster everywhere.
 int choose_step_kernel(const sllbm_ctx* c) {
     const bool tma_ok = tma_step_eligible(c);
     if (c->prm.kernel == 2) return tma_ok ? 2 : 0;
     if (c->prm.kernel == 1) return 1;
     const bool dev16 = c->prm.storage == SLLBM_F16DEV || c->prm.storage == SLLBM_BF16DEV;
-    return (tma_ok && !(dev16 && c->p == 3)) ? 2 : 1;
+    return (tma_ok && !(dev16 && c->p == 3 && !c->slab)) ? 2 : 1;
 }
 
 }  // namespace sllbm

@@ -76,19 +76,23 @@ def test_overlapped_exchange_reproduces_the_whole_mesh(storage, p, parts):
     assert np.array_equal(slab, full)
 
 
-@pytest.mark.parametrize("p,parts", [(4, 1), (4, 2), (4, 3), (2, 1), (2, 2)])
+@pytest.mark.parametrize("p,parts,storage", [(4, 1, "f32"), (4, 2, "f32"), (4, 3, "f32"), (2, 1, "f32"),
+                                             (2, 2, "f32"), (3, 1, "f32"), (3, 2, "f32"), (3, 2, "f16dev"),
+                                             (2, 2, "f16dev"), (4, 3, "bf16dev")])
 @pytest.mark.parametrize("overlapped", [False, True])
-def test_tma_fed_slabs_reproduce_the_whole_mesh(p, parts, overlapped):
+def test_tma_fed_slabs_reproduce_the_whole_mesh(p, parts, storage, overlapped):
     # the TMA-fed kernel on slabs (tiles over the interior cells, source boxes reaching into
-    # the ghost planes) against the same kernel on the undivided mesh, FP32
-    cfg = S.Config(cells=(4, 4, 8), p=p, courant=2.0, storage="f32")
+    # the ghost planes) against the same kernel on the undivided mesh (whose boxes that wrap
+    # around along z arrive as zero-filled periodic images, summed exactly)
+    cfg = S.Config(cells=(4, 4, 8), p=p, courant=2.0, storage=storage)
     _, full = _full(cfg, 4, kernel=2)
     _, slab, _ = _slabs(cfg, parts, 4, overlapped=overlapped, kernel=2)
     assert np.all(np.isfinite(full))
     assert np.array_equal(slab, full)
 
 
-@pytest.mark.parametrize("kernel,p,storage", [(1, 3, "f64"), (1, 4, "f32"), (2, 4, "f32"), (2, 2, "f32")])
+@pytest.mark.parametrize("kernel,p,storage", [(1, 3, "f64"), (1, 4, "f32"), (2, 4, "f32"), (2, 2, "f32"),
+                                              (2, 3, "f16dev"), (2, 4, "bf16dev"), (2, 3, "f32")])
 def test_periodic_halo_refresh_of_a_whole_mesh_slab(kernel, p, storage):
     # one slab spanning the mesh, its ghost planes refreshed in place before every step (by
     # sllbm_step itself: sllbm_halo_periodic), against the ordinary periodic context on the

@@ -375,7 +375,7 @@ def mixed_precision_block(S, torch, device, steps, every, hbm, alu):
         bpn = 2 * 45 * 2 * ELEM_BYTES[st]
         rec = {"kernel_ms": kms, "value": sim.nodes / (kms / 1e3), "unit": UNIT,
                "hbm_frac": bpn * sim.nodes / (kms / 1e3) / 1e9 / hbm,
-               "algorithmic_bytes_per_node": bpn, "step_kernel": int(sim.info.step_kernel),
+               "algorithmic_bytes_per_node": bpn, "step_kernel": int(S.sllbm_get_info(sim.ctx).step_kernel),
                "compensated_moments": name.endswith("_comp"),
                "roofline_alu": min_roofline(bpn, flops, sim.nodes, kms, hbm,
                                             alu["fp64_tflops"] if st == "f64" else alu["fp32_tflops"]),
@@ -529,7 +529,7 @@ def long_run_block(S, torch, device, steps, every):
             rows.append([k] + list(sim.diag()))
         rows = np.array(rows)
         curves[st] = (rows[:, 0].astype(int), rows[:, 1], rows[:, 2] + rows[:, 3])
-        out[st] = {"kernel_ms": statistics.median(kern), "step_kernel": int(sim.info.step_kernel),
+        out[st] = {"kernel_ms": statistics.median(kern), "step_kernel": int(S.sllbm_get_info(sim.ctx).step_kernel),
                    "Ek_end": float(rows[-1, 1]), "eps_end": float(rows[-1, 2] + rows[-1, 3]),
                    "finite": bool(np.isfinite(rows).all()),
                    "eps_peak_step": int(rows[np.argmax(rows[:, 2] + rows[:, 3]), 0])}

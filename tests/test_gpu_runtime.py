@@ -24,25 +24,47 @@ def S():
     return sllbm
 
 
-def tma_sim(S, cells=(16, 8, 8)):
-    sim = S.Sim(S.Config(cells=cells, p=4, courant=3.0, storage="f32", kernel=2))
+# the TMA-fed instances the run-control tests cover: FP32 at p = 4, FP16 deviations at p = 3
+# (a 16-bit box is released right after its z pass), BF16 deviations at p = 4
+TMA_RUN_CASES = [("f32", 4, (16, 8, 8)), ("f16dev", 3, (8, 6, 4)), ("bf16dev", 4, (8, 4, 4))]
+
+
+def tma_sim(S, cells=(16, 8, 8), storage="f32", p=4):
+    sim = S.Sim(S.Config(cells=cells, p=p, courant=3.0, storage=storage, kernel=2))
     assert sim.info.step_kernel == 2
     return sim
 
 
 def check_against_oracle(S, sim, steps=2, tol=1e-5):
+    """FP32: the oracle's run from the FP32-rounded Taylor-Green state.  16-bit deviations: one
+    step from the decoded state, in deviation space within the output rounding (2^-11 or 2^-8
+    of |d|) plus 1e-5 max|d| for the FP32 arithmetic."""
     sim.init_tgv()
-    assert sim.step(steps) == 0
-    assert S.sllbm_status(sim.ctx) == S.OK
-    got = sim.populations().cpu().numpy()
     g = O.Grid(cells=tuple(sim.cfg.cells), p=sim.cfg.p, dt=sim.dt, mu_inf=float(sim.info.mu_inf))
-    pop = O.init_fields(g, *O.tgv_fields(g, sim.info.U0)).astype(np.float32).astype(np.float64)
-    ref = O.step(g, pop, steps)
-    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= tol
+    if sim.cfg.storage == "f32":
+        assert sim.step(steps) == 0
+        assert S.sllbm_status(sim.ctx) == S.OK
+        got = sim.populations().cpu().numpy()
+        pop = O.init_fields(g, *O.tgv_fields(g, sim.info.U0)).astype(np.float32).astype(np.float64)
+        ref = O.step(g, pop, steps)
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= tol
+        return
+    start = sim.populations().cpu().numpy()
+    assert sim.step(1) == 0
+    assert S.sllbm_status(sim.ctx) == S.OK
+    ref = O.step(g, start, 1)
+    _, w = O.velset()
+    c = sim.cfg
+    dref = np.array([c.rho0, (2.0 / (c.gamma - 1.0) - 3.0) * c.T0 * c.rho0]).reshape(2, 1, 1, 1, 1)
+    dev = lambda pop: pop / np.asarray(w).reshape(1, -1, 1, 1, 1) - dref  # noqa: E731
+    d_ref, d_got = dev(ref), dev(sim.populations().cpu().numpy())
+    rb = 2.0 ** -11 if c.storage == "f16dev" else 2.0 ** -8
+    assert np.all(np.abs(d_got - d_ref) <= rb * np.abs(d_ref) + 1e-5 * np.abs(d_ref).max())
 
 
-def test_wait_limit_runs_out_then_context_steps_cleanly(S):
-    sim = tma_sim(S)
+@pytest.mark.parametrize("storage,p,cells", TMA_RUN_CASES)
+def test_wait_limit_runs_out_then_context_steps_cleanly(S, storage, p, cells):
+    sim = tma_sim(S, cells, storage, p)
     sim.init_tgv()
     S.sllbm_set_wait_limit(sim.ctx, 0.0)  # every wait that is not satisfied at once gives up
     assert sim.step(3) == 0  # (the launches are asynchronous; the status tells)
@@ -54,8 +76,9 @@ def test_wait_limit_runs_out_then_context_steps_cleanly(S):
     sim.close()
 
 
-def test_abort_request_stops_the_persistent_kernel(S):
-    sim = tma_sim(S)
+@pytest.mark.parametrize("storage,p,cells", TMA_RUN_CASES)
+def test_abort_request_stops_the_persistent_kernel(S, storage, p, cells):
+    sim = tma_sim(S, cells, storage, p)
     sim.init_tgv()
     S.sllbm_request_abort(sim.ctx, True)
     assert sim.step(2) == 0

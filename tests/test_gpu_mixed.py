@@ -162,22 +162,24 @@ def lebesgue_3d(g, dt):
     return lam
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("name,kernel", [("tgv_64c_p3_ma125", 1), ("tgv_64c_p3_ma125", 2), ("tgv_96c_p4", 2)])
 @pytest.mark.parametrize("storage", ["f16dev", "bf16dev"])
-def test_full_size_first_step_sampled(S, storage, kernel):
+def test_full_size_first_step_sampled(S, storage, name, kernel):
     """The 192^3-node Ma 1.25 workload at 16-bit storage, in its benchmark launch
-    configuration: one step from the Taylor-Green state, compared in deviation space at
+    configuration on both kernels, and the 384^3-node Ma 0.5 workload (byte offsets of a
+    buffer past 2^32) on the TMA-fed kernel: one step from the Taylor-Green state, compared in deviation space at
     sampled nodes (the first and the last included) that the oracle evaluates one by one
     from the exact FP64 state.  The GPU starts from that state rounded to 16 bits, so the
     bound adds to the output rounding (RELBITS |d|) and the FP32 arithmetic (1e-5 max|d|)
     the input rounding carried through the interpolation, at most Lam RELBITS max|d| where
     Lam is the largest product over the three directions of sum_l |l_l(r)| at this
-    workload's departure points (computed here from the oracle's Lagrange basis: 3.78),
+    workload's departure points (computed here from the oracle's Lagrange basis: 3.78 and
+    5.77),
     and through the collision, which mixes that error with the equilibrium's response to
     the moments' error; the factor 2 on Lam for the latter is a measured margin, not a
     derived constant."""
     import torch as T
-    w = I.WORKLOADS["tgv_64c_p3_ma125"]
+    w = I.WORKLOADS[name]
     sim = make(S, w.cells, w.p, storage, courant=w.courant, Ma=w.Ma, kernel=kernel)
     assert sim.info.step_kernel == kernel
     sim.init_tgv()

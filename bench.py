@@ -336,29 +336,33 @@ def rel_l2(a, b):
 
 def mixed_precision_block(S, torch, device, steps, every, hbm, alu):
     """FP64, FP32 and 16-bit deviation storage on the Ma 1.25 Taylor-Green workload, all from
-    the same initial state, for `steps` steps.  Per storage: median kernel time, node-updates/s,
-    fraction of the HBM peak at its algorithmic bytes, and the relative L2 error against the
-    FP64 GPU run of rho, u, T after the last step and of the E_k(t) and dissipation
-    eps_s(t) + eps_c(t) curves sampled every `every` steps.  The FP32-arithmetic storages run
-    a second time with compensated moment sums ("<storage>_comp"), and the 16-bit storages a
-    second time on the TMA-fed kernel ("<storage>_tma"; the automatic choice at p = 3 is the
-    generic kernel, the faster one there)."""
+    the same initial state, for `steps` steps, on the periodic mesh with ghost planes along z
+    (one slab spanning the mesh, the headline's mode: the same states bit for bit as the
+    ordinary periodic context, and no source box wraps around along z; the automatic kernel
+    choice is the TMA-fed kernel there for FP32 and the 16-bit storages).  Per storage: median
+    kernel time, node-updates/s, fraction of the HBM peak at its algorithmic bytes, and the
+    relative L2 error against the FP64 GPU run of rho, u, T after the last step and of the
+    E_k(t) and dissipation eps_s(t) + eps_c(t) curves sampled every `every` steps.  The
+    FP32-arithmetic storages run a second time with compensated moment sums
+    ("<storage>_comp", generic kernel).  "periodic_wrap_timing" times the ordinary periodic
+    context (boxes wrapping around along z) with the automatic choice (the generic kernel for
+    16-bit storage at p = 3) and with the TMA-fed kernel forced."""
     import numpy as np
 
     w = I.WORKLOADS["tgv_64c_p3_ma125"]
     every = max(1, min(every, steps))
     chunks = steps // every
     out = {"workload": w.name, "note": w.note, "steps": chunks * every,
-           "configured_steps": w.steps, "curve_every": every, "reference": "f64 (GPU)"}
+           "configured_steps": w.steps, "curve_every": every, "reference": "f64 (GPU)",
+           "z_boundary": "ghost planes (one slab over the whole mesh)"}
     ref = None
     flops = algorithmic_flops_per_node(w.p)
-    for name in ("f64", "f32", "f16dev", "bf16dev", "f16dev_tma", "bf16dev_tma", "f32_comp", "f16dev_comp",
-                 "bf16dev_comp"):
+    nodes = w.nodes
+    for name in ("f64", "f32", "f16dev", "bf16dev", "f32_comp", "f16dev_comp", "bf16dev_comp"):
         st = name.split("_")[0]
         sim = S.Sim(S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, Pr=w.Pr, gamma=w.gamma,
                              courant=w.courant, pr_correction=w.pr_correction, storage=st,
-                             kernel=2 if name.endswith("_tma") else 0),
-                    device=device)
+                             slab=(0, w.cells[2])), device=device)
         if name.endswith("_comp"):
             S.sllbm_set_compensated(sim.ctx, True)
         sim.init_tgv()
@@ -368,16 +372,20 @@ def mixed_precision_block(S, torch, device, steps, every, hbm, alu):
             _, k = time_steps(sim, torch, every)
             kern.extend(k)
             curve.append(sim.diag())
-        rho, u, T = (x.cpu().numpy() for x in sim.moments())
+        # the interior planes (the ghost planes below and above hold copies)
+        g = S.sllbm_slab_info(sim.ctx)[0]
+        z = slice(g * w.p, (g + w.cells[2]) * w.p)
+        rho, u, T = sim.moments()
+        rho, u, T = rho[z].cpu().numpy(), u[:, z].cpu().numpy(), T[z].cpu().numpy()
         curve = np.array(curve)
         ek, eps = curve[:, 0], curve[:, 1] + curve[:, 2]
         kms = statistics.median(kern)
         bpn = 2 * 45 * 2 * ELEM_BYTES[st]
-        rec = {"kernel_ms": kms, "value": sim.nodes / (kms / 1e3), "unit": UNIT,
-               "hbm_frac": bpn * sim.nodes / (kms / 1e3) / 1e9 / hbm,
+        rec = {"kernel_ms": kms, "value": nodes / (kms / 1e3), "unit": UNIT,
+               "hbm_frac": bpn * nodes / (kms / 1e3) / 1e9 / hbm,
                "algorithmic_bytes_per_node": bpn, "step_kernel": int(S.sllbm_get_info(sim.ctx).step_kernel),
                "compensated_moments": name.endswith("_comp"),
-               "roofline_alu": min_roofline(bpn, flops, sim.nodes, kms, hbm,
+               "roofline_alu": min_roofline(bpn, flops, nodes, kms, hbm,
                                             alu["fp64_tflops"] if st == "f64" else alu["fp32_tflops"]),
                "finite": bool(np.isfinite(T).all() and np.isfinite(rho).all())}
         if ref is None:
@@ -390,24 +398,23 @@ def mixed_precision_block(S, torch, device, steps, every, hbm, alu):
             rec["speedup_vs_f64"] = ref[5] / kms
         out[name] = rec
         sim.close()
-    # The same workload as one periodic z-slab with ghost planes (the headline's mode; no
-    # source box wraps around along z), timing only: sllbm_diag refuses slab contexts, so no
-    # curves; the automatic kernel choice is the TMA-fed kernel here for every storage.
-    ghost = {}
-    for st in ("f32", "f16dev", "bf16dev"):
+    # the ordinary periodic context, timing only
+    wrap = {}
+    for name in ("f32", "f16dev", "bf16dev", "f16dev_tma", "bf16dev_tma"):
+        st = name.split("_")[0]
         sim = S.Sim(S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, Pr=w.Pr, gamma=w.gamma,
                              courant=w.courant, pr_correction=w.pr_correction, storage=st,
-                             slab=(0, w.cells[2]), nonfinite_check=True), device=device)
+                             kernel=2 if name.endswith("_tma") else 0, nonfinite_check=True), device=device)
         sim.init_tgv()
         time_steps(sim, torch, 3, per_launch=False)
         _, kern = time_steps(sim, torch, every)
         kms = statistics.median(kern)
         bpn = 2 * 45 * 2 * ELEM_BYTES[st]
-        ghost[st] = {"kernel_ms": kms, "value": sim.nodes / (kms / 1e3), "unit": UNIT,
-                     "hbm_frac": bpn * sim.nodes / (kms / 1e3) / 1e9 / hbm, "step_kernel": int(sim.info.step_kernel),
-                     "steps_timed": every, "status": int(sim.status())}
+        wrap[name] = {"kernel_ms": kms, "value": nodes / (kms / 1e3), "unit": UNIT,
+                      "hbm_frac": bpn * nodes / (kms / 1e3) / 1e9 / hbm, "step_kernel": int(sim.info.step_kernel),
+                      "steps_timed": every, "status": int(sim.status())}
         sim.close()
-    out["ghost_planes_timing"] = ghost
+    out["periodic_wrap_timing"] = wrap
     return out
 
 

@@ -183,7 +183,8 @@ int sllbm_create(const sllbm_mesh *mesh, int p, sllbm_velset vs, const sllbm_par
  * sllbm_step_end.  The result equals sllbm_step's bit for bit.
  * Errors: SLLBM_EINVAL for z_begin outside the mesh, z_cells < 1 or above the mesh, a
  * slab thinner than its ghost width (its halo would come from two neighbours), a TMA-fed
- * kernel request the interior cells cannot tile, and for slab contexts in sllbm_diag*, the
+ * kernel request the interior cells cannot tile, and for slab contexts that are a part of a
+ * mesh (not all of it) in sllbm_diag*, the
  * reverse-mode calls and batches; sllbm_halo_*, sllbm_slab_info and
  * sllbm_step_begin/_end on a context that is not a slab, side not 0 or 1, a NULL buffer or
  * a context without state: SLLBM_EINVAL (sllbm_step_begin/_end before initialisation:
@@ -264,7 +265,10 @@ int sllbm_moments(sllbm_ctx *ctx, double *rho, double *u, double *T, int on_devi
  * Ek = <rho|u|^2/2>/(rho0 U0^2), eps_s = <mu/mu_inf |curl u|^2>/(rho0 Re U0^2),
  * eps_c = (4/3)<mu/mu_inf (div u)^2>/(rho0 Re U0^2), with per-cell Clenshaw-Curtis
  * quadrature on the support points and cell-local Lagrange derivatives.
- * Synchronous.  Uses a context-owned device scratch buffer (allocated on first use). */
+ * Synchronous.  Uses a context-owned device scratch buffer (allocated on first use).
+ * A slab context must span the whole mesh (its interior is the mesh; the support points
+ * wrap around within it, so the ghost planes are not read): SLLBM_EINVAL for a part of a
+ * mesh. */
 int sllbm_diag(sllbm_ctx *ctx, double *Ek, double *eps_s, double *eps_c);
 
 /* sllbm_diag without any device allocation (the paper has no counterpart: this is a

@@ -170,9 +170,13 @@ struct DiagConst {
 // Per cell: rho, u, T at its (p+1)^3 support points, gradients from the cell-local
 // Lagrange polynomials, Clenshaw-Curtis quadrature of rho|u|^2/2, mu~|curl u|^2 and
 // mu~(div u)^2 (Sec. III.C).  Grid-stride over cells; one FP64 partial triple per block.
+// Along z the support points wrap around within Nz planes that start zoff planes into the
+// buffer (the whole buffer of a periodic context; the interior of a slab spanning the whole
+// mesh, so that its ghost planes are not read).
 template <typename S, int P>
 __global__ void __launch_bounds__(128) diag_kernel(const S* __restrict__ pop, long long nn, int Nx, int Ny,
-                                                   int Nz, int ncx, int ncy, long long ncell, double inv_2cv,
+                                                   int Nz, int zoff, int ncx, int ncy, long long ncell,
+                                                   double inv_2cv,
                                                    double hx, double hy, double hz,
                                                    const __grid_constant__ DiagConst dc,
                                                    double* __restrict__ partials) {
@@ -189,7 +193,7 @@ __global__ void __launch_bounds__(128) diag_kernel(const S* __restrict__ pop, lo
         const int cz = static_cast<int>(cell / (static_cast<long long>(ncx) * ncy));
         double rho = 0, T = 0, ux = 0, uy = 0, uz = 0;
         if (t < NPC) {
-            const int nx = (cx * P + ia) % Nx, ny = (cy * P + ib) % Ny, nz = (cz * P + ic) % Nz;
+            const int nx = (cx * P + ia) % Nx, ny = (cy * P + ib) % Ny, nz = zoff + (cz * P + ic) % Nz;
             const long long n = (static_cast<long long>(nz) * Ny + ny) * Nx + nx;
             double mx = 0, my = 0, mz = 0, e2 = 0;
             for (int i = 0; i < kQ; ++i) {
@@ -321,6 +325,11 @@ int launch_init(sllbm_ctx* ctx, int mode, const double* rho, const double* u, co
     return SLLBM_OK;
 }
 
+// The planes the diagnostics wrap around in, and where they start in the buffer (a slab that
+// spans the whole mesh: its interior, above the ghost planes).
+int diag_planes(const sllbm_ctx* ctx) { return ctx->slab ? ctx->cells[2] * ctx->p : ctx->N[2]; }
+int diag_zoff(const sllbm_ctx* ctx) { return ctx->slab ? ctx->ghost * ctx->p : 0; }
+
 template <int P>
 int launch_diag_p(sllbm_ctx* ctx, const void* pop, double* d_out) {
     const long long ncell = static_cast<long long>(ctx->cells[0]) * ctx->cells[1] * ctx->cells[2];
@@ -340,8 +349,8 @@ int launch_diag_p(sllbm_ctx* ctx, const void* pop, double* d_out) {
     with_storage(ctx, [&](auto tag) {
         using S = decltype(tag);
         diag_kernel<S, P><<<nb, 128, 0, ctx->stream>>>(
-            static_cast<const S*>(pop), ctx->nn, ctx->N[0], ctx->N[1], ctx->N[2], ctx->cells[0],
-            ctx->cells[1], ncell, inv_2cv, ctx->h[0], ctx->h[1], ctx->h[2], dc, ctx->d_partials);
+            static_cast<const S*>(pop), ctx->nn, ctx->N[0], ctx->N[1], diag_planes(ctx), diag_zoff(ctx),
+            ctx->cells[0], ctx->cells[1], ncell, inv_2cv, ctx->h[0], ctx->h[1], ctx->h[2], dc, ctx->d_partials);
     });
     sum_partials_kernel<<<1, 256, 0, ctx->stream>>>(ctx->d_partials, nb, d_out);
     ctx->launches += 2;
@@ -379,8 +388,8 @@ int launch_diag_cells_into(sllbm_ctx* ctx, const void* pop, double* partials, do
     with_storage(ctx, [&](auto tag) {
         using S = decltype(tag);
         diag_kernel<S, P><<<nb, 128, 0, ctx->stream>>>(
-            static_cast<const S*>(pop), ctx->nn, ctx->N[0], ctx->N[1], ctx->N[2], ctx->cells[0],
-            ctx->cells[1], ncell, inv_2cv, ctx->h[0], ctx->h[1], ctx->h[2], dc, partials);
+            static_cast<const S*>(pop), ctx->nn, ctx->N[0], ctx->N[1], diag_planes(ctx), diag_zoff(ctx),
+            ctx->cells[0], ctx->cells[1], ncell, inv_2cv, ctx->h[0], ctx->h[1], ctx->h[2], dc, partials);
     });
     sum_partials_kernel<<<1, 256, 0, ctx->stream>>>(partials, nb, d_out);
     ctx->launches += 2;
@@ -1100,7 +1109,8 @@ int sllbm_moments(sllbm_ctx* ctx, double* rho, double* u, double* T, int on_devi
 }
 
 int sllbm_diag(sllbm_ctx* ctx, double* Ek, double* eps_s, double* eps_c) {
-    if (ctx == nullptr || Ek == nullptr || eps_s == nullptr || eps_c == nullptr || ctx->slab) return SLLBM_EINVAL;
+    if (ctx == nullptr || Ek == nullptr || eps_s == nullptr || eps_c == nullptr) return SLLBM_EINVAL;
+    if (ctx->slab && ctx->cells[2] != ctx->z_cells_global) return SLLBM_EINVAL;  // a part of a mesh
     if (!ctx->initialised) return SLLBM_ENOTREADY;
     if (ctx->d_partials == nullptr) {
         const long long ncell = static_cast<long long>(ctx->cells[0]) * ctx->cells[1] * ctx->cells[2];
@@ -1139,7 +1149,8 @@ int sllbm_diag(sllbm_ctx* ctx, double* Ek, double* eps_s, double* eps_c) {
 // array and each overwrites every entry it reads, so nothing needs clearing, but calls
 // that overlap on the GPU (other streams, other contexts) race on it.
 int sllbm_diag_noalloc(sllbm_ctx* ctx, double* Ek, double* eps_s, double* eps_c) {
-    if (ctx == nullptr || Ek == nullptr || eps_s == nullptr || eps_c == nullptr || ctx->slab) return SLLBM_EINVAL;
+    if (ctx == nullptr || Ek == nullptr || eps_s == nullptr || eps_c == nullptr) return SLLBM_EINVAL;
+    if (ctx->slab && ctx->cells[2] != ctx->z_cells_global) return SLLBM_EINVAL;  // a part of a mesh
     if (!ctx->initialised) return SLLBM_ENOTREADY;
     const long long ncell = static_cast<long long>(ctx->cells[0]) * ctx->cells[1] * ctx->cells[2];
     if (ncell > kNoAllocDiagMaxCells) return SLLBM_EINVAL;  // more cells than the static scratch holds

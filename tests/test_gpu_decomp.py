@@ -116,6 +116,24 @@ def test_periodic_halo_refresh_of_a_whole_mesh_slab(kernel, p, storage):
     half.close()
 
 
+@pytest.mark.parametrize("kernel,p,storage", [(1, 3, "f64"), (2, 4, "f32"), (2, 3, "f16dev")])
+def test_diagnostics_of_a_whole_mesh_slab(kernel, p, storage):
+    # E_k, eps_s, eps_c of a slab spanning the whole mesh (its interior, the support points
+    # wrapping around within it) equal those of the ordinary periodic context bit for bit: the
+    # states are the same and the cells are visited in the same order
+    cfg = S.Config(cells=(4, 6, 8), p=p, courant=2.0, storage=storage, kernel=kernel)
+    a = S.Sim(cfg, device="cuda:0")
+    b = S.Sim(dataclasses.replace(cfg, slab=(0, 8)), device="cuda:0")
+    for sim in (a, b):
+        sim.init_tgv()
+        assert sim.step(3) == 0
+    da, db = a.diag(), b.diag()
+    assert all(np.isfinite(da)) and tuple(da) == tuple(db)
+    assert np.allclose(S.sllbm_diag_noalloc(b.ctx), db, rtol=1e-13, atol=0)  # (another summation order)
+    a.close()
+    b.close()
+
+
 def test_overlapped_exchange_on_slabs_without_interior_tiles():
     # two-cell slabs with two ghost cells: every tile reads a ghost cell (all in the second launch)
     cfg = S.Config(cells=(3, 3, 6), p=3, courant=2.0, storage="f64")

@@ -749,6 +749,7 @@ def run_mine(args, rank, world, local):
     if dist is not None:
         dist.barrier()
     clk = clocks.stop()
+    clk["covers"] = "the headline's timed region (nvidia-smi every 200 ms, from 0.3 s before it)"
     _, _, T = sim.moments()
     finite = bool(torch.isfinite(T).all().item())
 

@@ -928,6 +928,7 @@ int sllbm_stream_apply(sllbm_ctx* ctx, const void* src, void* dst, int transpose
 }
 
 int sllbm_adjoint_step(sllbm_ctx* ctx, const void* state_prev, const void* lam_next, void* lam_prev, double* dmu) {
+    NvtxRange range("sllbm_adjoint_step");
     if (ctx == nullptr || state_prev == nullptr || lam_next == nullptr || lam_prev == nullptr || dmu == nullptr)
         return SLLBM_EINVAL;
     if (!adjoint_supported(ctx)) return SLLBM_EINVAL;

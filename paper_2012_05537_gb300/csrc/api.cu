@@ -783,11 +783,13 @@ int sllbm_slab_halo_bytes(const sllbm_ctx* ctx, int side, size_t* bytes) {
 }
 
 int sllbm_halo_pack(sllbm_ctx* ctx, int side, void* halo, void* cuda_stream) {
+    NvtxRange range("sllbm_halo_pack");
     if (ctx == nullptr) return SLLBM_EINVAL;
     return halo_copy(ctx, side, halo, 0, cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream);
 }
 
 int sllbm_halo_unpack(sllbm_ctx* ctx, int side, const void* halo, void* cuda_stream) {
+    NvtxRange range("sllbm_halo_unpack");
     if (ctx == nullptr) return SLLBM_EINVAL;
     return halo_copy(ctx, side, const_cast<void*>(halo), 1,
                      cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream);
@@ -833,6 +835,7 @@ int sllbm_halo_periodic(sllbm_ctx* ctx, void* cuda_stream) {
 }
 
 int sllbm_step_begin(sllbm_ctx* ctx) {
+    NvtxRange range("sllbm_step_begin");
     if (ctx == nullptr || !ctx->slab) return SLLBM_EINVAL;
     if (!ctx->initialised) return SLLBM_ENOTREADY;
     if (ctx->prm.nonfinite_check) CK(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
@@ -847,6 +850,7 @@ int sllbm_step_begin(sllbm_ctx* ctx) {
 }
 
 int sllbm_step_end(sllbm_ctx* ctx) {
+    NvtxRange range("sllbm_step_end");
     if (ctx == nullptr || !ctx->slab) return SLLBM_EINVAL;
     if (!ctx->initialised) return SLLBM_ENOTREADY;
     ctx->region = 2;
@@ -1025,6 +1029,7 @@ int sllbm_get_populations(sllbm_ctx* ctx, double* pop, int on_device) {
 }
 
 int sllbm_step(sllbm_ctx* ctx, int n) {
+    NvtxRange range("sllbm_step");
     if (ctx == nullptr || n < 0) return SLLBM_EINVAL;
     if (!ctx->initialised) return SLLBM_ENOTREADY;
     if (ctx->prm.nonfinite_check) CK(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
@@ -1109,6 +1114,7 @@ int sllbm_moments(sllbm_ctx* ctx, double* rho, double* u, double* T, int on_devi
 }
 
 int sllbm_diag(sllbm_ctx* ctx, double* Ek, double* eps_s, double* eps_c) {
+    NvtxRange range("sllbm_diag");
     if (ctx == nullptr || Ek == nullptr || eps_s == nullptr || eps_c == nullptr) return SLLBM_EINVAL;
     if (ctx->slab && ctx->cells[2] != ctx->z_cells_global) return SLLBM_EINVAL;  // a part of a mesh
     if (!ctx->initialised) return SLLBM_ENOTREADY;
@@ -1177,6 +1183,7 @@ int sllbm_diag_noalloc(sllbm_ctx* ctx, double* Ek, double* eps_s, double* eps_c)
 }
 
 int sllbm_run_host(sllbm_ctx* ctx, const void* pop_in, void* pop_out, int n) {
+    NvtxRange range("sllbm_run_host");
     if (ctx == nullptr || pop_in == nullptr || pop_out == nullptr || n < 0) return SLLBM_EINVAL;
     int rc = ensure_buffers(ctx);
     if (rc != SLLBM_OK) return rc;
@@ -1197,6 +1204,7 @@ int sllbm_run_host(sllbm_ctx* ctx, const void* pop_in, void* pop_out, int n) {
 // in both directions at once while a state is stepped.  With three slots the copy of state
 // k + 3 into a slot never waits for the copy out of state k (with two it did: 1.2x slower).
 int sllbm_run_host_many(sllbm_ctx* ctx, const void* const* pop_in, void* const* pop_out, int count, int n) {
+    NvtxRange range("sllbm_run_host_many");
     if (ctx == nullptr || pop_in == nullptr || pop_out == nullptr || count < 1 || n < 0) return SLLBM_EINVAL;
     for (int k = 0; k < count; ++k)
         if (pop_in[k] == nullptr || pop_out[k] == nullptr) return SLLBM_EINVAL;

@@ -310,6 +310,7 @@ int sllbm_batch_create(sllbm_ctx* const* ctxs, int n, int streams, void* cuda_st
 }
 
 int sllbm_batch_step(sllbm_batch* b, int nsteps) {
+    NvtxRange range("sllbm_batch_step");
     if (b == nullptr || nsteps < 0 || (nsteps & 1)) return SLLBM_EINVAL;
     const int n = static_cast<int>(b->ctx.size());
     for (int k = 0; k < n; ++k)

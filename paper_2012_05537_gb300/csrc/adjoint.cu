@@ -19,6 +19,7 @@
 
 #include "collide.cuh"
 #include "sllbm_internal.h"
+#include "trace.h"
 #include "step_kernel.cuh"
 #include "tables.h"
 

@@ -9,6 +9,7 @@
 
 #include "collide.cuh"
 #include "sllbm_internal.h"
+#include "trace.h"
 #include "storage.cuh"
 #include "tables.h"
 

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "sllbm_internal.h"
+#include "trace.h"
 
 using namespace sllbm;
 

@@ -2,7 +2,6 @@
 #pragma once
 
 #include <cuda_runtime.h>
-#include <nvtx3/nvToolsExt.h>
 
 #include <cstddef>
 #include <cstdint>
@@ -71,17 +70,6 @@ struct sllbm_ctx {
 };
 
 namespace sllbm {
-
-// A named NVTX range over the rest of the enclosing scope (host side; each public call that
-// launches work opens one, so that a profiler's timeline shows the library's calls; with no
-// tool attached the NVTX calls return at once).
-struct NvtxRange {
-    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
-    ~NvtxRange() { nvtxRangePop(); }
-    NvtxRange(const NvtxRange&) = delete;
-    NvtxRange& operator=(const NvtxRange&) = delete;
-};
-
 
 // Device allocation of the library (runtime.cu): cudaMalloc, unless sllbm_debug_fail_allocs
 // armed a failure for this allocation.

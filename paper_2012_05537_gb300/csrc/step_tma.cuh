@@ -468,13 +468,15 @@ __device__ __forceinline__ void tmem_load_row(uint32_t ta, float* v) {
 // (the CTAs of one wave) thus cover a compact region whose source boxes overlap in L2, rather
 // than one thin layer of tiles whose z-halo (a box is 2.25 cells deep for a 1-cell tile) is
 // read again by the next wave.  Edge slabs, rows and blocks are simply thinner.  Returns the
-// tile's (x, y, z) tile coordinates.  (Columns 16 tiles deep measured best on 96^3 and 128^3
-// meshes, within a few per cent of 2x2x16, 2x2x32 and 4x4x8 blocks.)
+// tile's (x, y, z) tile coordinates.  (Columns 8 tiles deep measured best with the
+// four-quarter warp layout: 1.3 % faster than 16 at p = 4 on 128^3 nodes, as fast or faster
+// at p = 3, and 4, 32 or 64 deep or 2x2-column blocks slower; with the earlier layout 16 had
+// been best, within a few per cent of 2x2x16, 2x2x32 and 4x4x8 blocks.)
 #ifndef SLLBM_TILE_BLOCK_XY
 #define SLLBM_TILE_BLOCK_XY 1
 #endif
 #ifndef SLLBM_TILE_BLOCK_Z
-#define SLLBM_TILE_BLOCK_Z 16
+#define SLLBM_TILE_BLOCK_Z 8
 #endif
 constexpr int kBlockXY = SLLBM_TILE_BLOCK_XY, kBlockZ = SLLBM_TILE_BLOCK_Z;
 __device__ __forceinline__ void tile_coords(int t, int ntx, int nty, int ntz, int* tc) {

@@ -108,8 +108,10 @@ typedef struct {
                                tile of 4x4x2 (p = 2), 2x3x1 (p = 3: y may end in a partial
                                tile) or 2x2x1 cells (p = 4), no Prandtl term, collide on, no
                                compensated sums; else SLLBM_EINVAL).  Automatic: the TMA-fed
-                               kernel where it can run, except at p = 3 with 16-bit storage
-                               outside slab contexts (the faster kernel in each case) */
+                               kernel where it can run and the mesh (a slab: its interior)
+                               has at least 0.5 M (p = 2), 3 M (p = 3) or 1.5 M (p = 4)
+                               nodes, except at p = 3 with 16-bit storage outside slab
+                               contexts (the faster kernel in each case, as measured) */
 } sllbm_params;
 
 /* Read-only description of a created context. */

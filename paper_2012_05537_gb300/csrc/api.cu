@@ -285,19 +285,25 @@ __global__ void sum_partials_kernel(const double* __restrict__ partials, int nbl
 namespace sllbm {
 
 // 1: generic tile kernel, 2: TMA-fed persistent kernel, 0: the requested kernel cannot run.
-// The automatic choice takes the TMA-fed kernel where it can run, except for p = 3 with 16-bit
-// storage on an ordinary periodic context: there its 6x9x3-node tiles (27 of 32 lanes), the
-// widening of every stored pair and the two periodic images of the boxes that wrap around
-// along z leave it 9-18 % slower than the generic kernel with two CTAs per SM, while on a slab
-// (whose boxes never wrap along z, e.g. the whole mesh with ghost planes) it is as fast or
-// 6 % faster (measured on GB300 at 132^3 and 192^3 nodes).  At p = 2 and 4 and for FP32
-// storage it is as fast or faster everywhere.
+// The automatic choice takes the TMA-fed kernel where it can run and the mesh (a slab: its
+// interior) has enough nodes for its persistent CTAs to run full: on smaller meshes its set-up
+// per CTA and the source boxes that wrap around the periodic boundary (all of them on the
+// smallest meshes, several images each) make it slower than the generic kernel (measured on
+// GB300, FP32 and FP16 storage, time TMA / generic: p = 2 1.05 at 64^3 nodes and 0.81 at 96^3;
+// p = 3 1.19 at 96^3, 1.00 at 132^3, 0.92 at 192^3; p = 4 1.03 at 96^3, 0.87 at 128^3; up to
+// 3-6x on meshes of a few tiles).  And not for 16-bit storage at p = 3 on an ordinary periodic
+// context: there its 6x9x3-node tiles (27 of 32 lanes), the widening of every stored pair and
+// the two periodic images of the boxes that wrap around along z leave it 9-18 % slower than
+// the generic kernel with two CTAs per SM even at 192^3 nodes, while on a slab (whose boxes
+// never wrap along z, e.g. the whole mesh with ghost planes) it is 6 % faster there.
 int choose_step_kernel(const sllbm_ctx* c) {
     const bool tma_ok = tma_step_eligible(c);
     if (c->prm.kernel == 2) return tma_ok ? 2 : 0;
     if (c->prm.kernel == 1) return 1;
     const bool dev16 = c->prm.storage == SLLBM_F16DEV || c->prm.storage == SLLBM_BF16DEV;
-    return (tma_ok && !(dev16 && c->p == 3 && !c->slab)) ? 2 : 1;
+    const double nodes = static_cast<double>(c->N[0]) * c->N[1] * (static_cast<double>(c->cells[2]) * c->p);
+    const double min_nodes = c->p == 2 ? 5e5 : (c->p == 3 ? 3e6 : 1.5e6);
+    return (tma_ok && nodes >= min_nodes && !(dev16 && c->p == 3 && !c->slab)) ? 2 : 1;
 }
 
 }  // namespace sllbm

@@ -261,7 +261,8 @@ def test_compensated_moments_step_matches_oracle(S, storage, p, pr):
 
 
 def test_compensation_flag_selects_a_summing_kernel(S):
-    sim = S.Sim(S.Config(cells=(4, 2, 2), p=4, courant=3.0, storage="f32"))
+    # (a mesh large enough for the automatic choice to take the TMA-fed kernel)
+    sim = S.Sim(S.Config(cells=(32, 32, 32), p=4, courant=3.0, storage="f32"))
     assert sim.info.step_kernel == 2  # the TMA-fed kernel by default
     S.sllbm_set_compensated(sim.ctx, True)
     assert S.sllbm_get_info(sim.ctx).step_kernel == 1

@@ -191,7 +191,13 @@ def test_tma_kernel_refuses_meshes_it_cannot_tile(S):
     with pytest.raises(S.SllbmError):
         make(S, (3, 6, 3), 3, storage="f32", kernel=2)
     assert make(S, (3, 6, 3), 3, storage="f32").info.step_kernel == 1
-    assert make(S, (6, 5, 3), 3, storage="f32").info.step_kernel == 2
+    assert make(S, (6, 5, 3), 3, storage="f32", kernel=2).info.step_kernel == 2
+    # the automatic choice: the generic kernel on meshes too small for the persistent CTAs
+    # (below 0.5 M nodes at p = 2, 3 M at p = 3, 1.5 M at p = 4), the TMA-fed one above
+    assert make(S, (6, 5, 3), 3, storage="f32").info.step_kernel == 1
+    assert make(S, (2, 2, 1), 4, storage="f32").info.step_kernel == 1
+    assert make(S, (40, 40, 40), 2, storage="f32").info.step_kernel == 2
+    assert make(S, (32, 32, 32), 4, storage="f32").info.step_kernel == 2
     with pytest.raises(S.SllbmError):
         make(S, (6, 6, 3), 3, storage="f16dev", kernel=2)  # N[0] = 18
     assert make(S, (6, 6, 3), 3, storage="f16dev").info.step_kernel == 1
@@ -199,7 +205,7 @@ def test_tma_kernel_refuses_meshes_it_cannot_tile(S):
     # generic kernel (the faster one there); at p = 4 it is the TMA-fed kernel
     assert make(S, (8, 6, 3), 3, storage="f16dev", kernel=2).info.step_kernel == 2
     assert make(S, (8, 6, 3), 3, storage="f16dev").info.step_kernel == 1
-    assert make(S, (2, 2, 1), 4, storage="bf16dev").info.step_kernel == 2
+    assert make(S, (32, 32, 32), 4, storage="bf16dev").info.step_kernel == 2
 
 
 @pytest.mark.parametrize("p", [2, 3, 4])

@@ -695,6 +695,7 @@ def batch_block(S, torch, device, count, steps, streams=16, seed=0):
             "persistent_graph": {"ms": pers_ms, "value": nodes * bsteps / (pers_ms / 1e3),
                                  "tile_shape_per_order": {str(k): v for k, v in shapes.items()}},
             "speedup_vs_one_by_one_default": (nodes * bsteps / batch_ms) / (nodes * steps / default_ms),
+            "persistent_speedup_vs_one_by_one_default": (nodes * bsteps / pers_ms) / (nodes * steps / default_ms),
             "variants_chosen": {str(v): variants.count(v) for v in sorted(set(variants))},
             "instances_finite_at_end": finite, "unit": UNIT}
 

@@ -767,29 +767,37 @@ def run_mine(args, rank, world, local):
     # a stream of independent states through sllbm_run_host_many (the copies of neighbouring
     # states overlap, in both directions); beside it the same one state at a time
     # (sllbm_run_host, copy in, step, copy out, synchronise).
+    # The states here are those of the ordinary periodic context (the call a user makes with
+    # host buffers): a slab's state would also carry its ghost planes across the host link.
     e2e = None
     if args.e2e_steps > 0:
-        nb = int(sim.info.pop_bytes)
+        sime = S.Sim(dataclasses.replace(cfg, slab=None), device=f"cuda:{local}") if ghost else sim
+        if ghost:
+            sime.init_tgv()
+        nb = int(sime.info.pop_bytes)
         host_in = torch.empty(nb, dtype=torch.uint8).pin_memory()
         host_outs = [torch.empty(nb, dtype=torch.uint8).pin_memory() for _ in range(3)]
-        host_in.copy_(sim.raw_state().view(torch.uint8).reshape(-1).cpu())
-        sim.run_host(host_in, host_outs[0], 1)
+        host_in.copy_(sime.raw_state().view(torch.uint8).reshape(-1).cpu())
+        sime.run_host(host_in, host_outs[0], 1)
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            sim.run_host(host_in, host_outs[0], 1)
+            sime.run_host(host_in, host_outs[0], 1)
         el_seq = time.perf_counter() - t0
         ins = [host_in] * args.e2e_steps
         outs = [host_outs[k % 3] for k in range(args.e2e_steps)]
-        sim.run_host_many(ins[:3], outs[:3], 1)
+        sime.run_host_many(ins[:3], outs[:3], 1)
         t0 = time.perf_counter()
-        sim.run_host_many(ins, outs, 1)
+        sime.run_host_many(ins, outs, 1)
         el = time.perf_counter() - t0
         e2e = {"value": nodes * args.e2e_steps * world / el, "unit": UNIT,
                "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
-               "steps": args.e2e_steps,
-               "mode": "independent states streamed through sllbm_run_host_many (copies overlapped)",
+               "steps": args.e2e_steps, "step_kernel": int(sime.info.step_kernel),
+               "mode": "independent states streamed through sllbm_run_host_many (copies overlapped), "
+                       "ordinary periodic context",
                "sequential": {"value": nodes * args.e2e_steps * world / el_seq, "unit": UNIT,
                               "mode": "one state at a time through sllbm_run_host"}}
+        if sime is not sim:
+            sime.close()
 
     variants = {}
     if not args.no_variants and rank == 0 and ghost:

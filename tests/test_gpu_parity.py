@@ -345,9 +345,9 @@ def test_tgv_16c_p4_curves_match_oracle(S, storage, kernel):
 # paper's Taylor-Green setting), 2000 steps, against the oracle's curves every 50 steps
 # (tests/golden/tgv_16c_p4_c2_curves.txt, as far as the file goes).  Both storages run on the
 # generic kernel (the Prandtl term).  Bounds relative to the curve's largest value, from
-# measurements on GB300 over the first 1250 steps (FP64: 1.1e-13, 1.9e-13, 4.2e-13 for E_k,
-# eps_s, eps_c, i.e. round-off; FP32: 3.8e-6, 2.3e-5, 3.0e-5), asserted with a margin of
-# about 4 for FP32 and with 1e-11 for FP64.
+# measurements on GB300 over the 2000 steps (FP64: 1.1e-13, 1.9e-13, 4.2e-13 for E_k, eps_s,
+# eps_c, i.e. round-off; FP32: 3.8e-6, 2.3e-5, 3.0e-5), asserted with a margin of about 4 for
+# FP32 and with 1e-11 for FP64.
 STATED_CURVES_C2 = {"f64": (1e-11, 1e-11, 1e-11), "f32": (2e-5, 1e-4, 1.2e-4)}
 
 

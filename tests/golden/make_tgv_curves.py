@@ -8,7 +8,9 @@ workload definition (inputs.Workload); the GPU tests pass the same values.
   number 4), step 0 and every 20 steps up to 200 (about ten minutes on eight cores);
 * tgv_16c_p4_c2_curves.txt: workload tgv_16c_p4_c2 (the same mesh at Courant number 2, the
   time step of the 128^3-node throughput workload, Prandtl term on), step 0 and every 50
-  steps up to 2000 (about two hours on eight cores).  Rows are written as the run goes.
+  steps up to 2000 (about three hours on eight cores).  Rows are written as the run goes;
+  the oracle's diagnostic sums are reduced in parallel, so two runs agree to about 1e-13
+  relative, not bit for bit.
 
     python tests/golden/make_tgv_curves.py [tgv_16c_p4 | tgv_16c_p4_c2]
 """

@@ -78,7 +78,7 @@ def test_storage_round_trip_rounds_deviations(S, storage):
 
 @pytest.mark.parametrize("storage", ["f16dev", "bf16dev"])
 @pytest.mark.parametrize("p,cells,pr", [(2, (3, 2, 4), False), (3, (3, 2, 2), False), (4, (2, 2, 1), False),
-                                        (3, (2, 3, 2), True)])
+                                        (3, (2, 3, 2), True), (2, (1, 1, 1), False), (4, (1, 1, 1), True)])
 def test_one_step_matches_oracle_in_deviation_space(S, storage, p, cells, pr):
     sim = make(S, cells, p, storage, courant=3.0, pr=pr, kernel=1)
     assert sim.info.step_kernel == 1

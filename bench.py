@@ -105,6 +105,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--kernel", type=int, choices=[0, 1, 2], default=0,
                     help="step kernel of the headline run: 0 automatic, 1 generic, 2 TMA-fed")
+    ap.add_argument("--pr", action="store_true",
+                    help="headline run with the quasi-equilibrium Prandtl term (App. D) on")
     ap.add_argument("--periodic-z", choices=["ghost", "wrap"], default="ghost",
                     help="z boundary of the headline mesh: ghost planes (the mesh as one periodic z-slab, "
                          "refreshed in place before each step) or source boxes wrapping around")
@@ -727,7 +729,7 @@ def run_mine(args, rank, world, local):
     # context (tests/test_gpu_decomp.py), which "--periodic-z wrap" times instead.
     ghost = args.periodic_z == "ghost"
     cfg = S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, Pr=w.Pr, gamma=w.gamma,
-                   courant=w.courant, pr_correction=w.pr_correction, storage=storage,
+                   courant=w.courant, pr_correction=w.pr_correction or args.pr, storage=storage,
                    slab=(0, w.cells[2]) if ghost else None, kernel=args.kernel)
     sim = S.Sim(cfg, device=f"cuda:{local}")
     sim.init_tgv()
@@ -760,7 +762,7 @@ def run_mine(args, rank, world, local):
     hbm, peak_src = measured_peaks()
     achieved = bytes_per_node * nodes / (kern_avg_ms / 1e3) / 1e9
     traffic = profiled_traffic(w.name, storage, "tma" if sim.info.step_kernel == 2 else "generic",
-                               "_ghostz" if ghost else "")
+                               ("_ghostz" if ghost else "") + ("_pr" if args.pr else ""))
 
     # end to end through the C ABI with host buffers: every step copies a state from pinned
     # host memory to the device, advances it one step and copies the result back.  Headline:
@@ -873,7 +875,7 @@ def run_mine(args, rank, world, local):
             "dtype": storage, "data": "synthetic",
             "config": {"workload": w.name, "cells": list(w.cells), "p": w.p,
                        "nodes": nodes, "Ma": w.Ma, "Re": w.Re, "courant": w.courant,
-                       "pr_correction": bool(w.pr_correction),
+                       "pr_correction": bool(w.pr_correction or args.pr),
                        "dt": sim.dt, "storage": storage,
                        "z_boundary": ("ghost planes: the mesh as one periodic z-slab (sllbm_create_slab over "
                                       "all cells), refreshed in place before each step by sllbm_halo_periodic "

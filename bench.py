@@ -849,6 +849,17 @@ def run_mine(args, rank, world, local):
                           "step_kernel": int(simpr.info.step_kernel),
                           "hbm_frac": bytes_per_node * nodes / (kpr_ms / 1e3) / 1e9 / hbm, "steps": npr}
         simpr.close()
+        # the same on the TMA-fed kernel (as fast as the generic one with ghost planes, slower
+        # with boxes wrapping along z: the automatic choice keeps the term on the generic kernel)
+        for gname, gslab in (("ghost", (0, w.cells[2])), ("wrap", None)):
+            simt = S.Sim(S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, Pr=w.Pr, gamma=w.gamma,
+                                  courant=w.courant, pr_correction=True, storage=storage, kernel=2,
+                                  slab=gslab), device=f"cuda:{local}")
+            simt.init_tgv()
+            simt.step(3)
+            _, kt = time_steps(simt, torch, npr)
+            variants["pr"][f"tma_kernel_ms_{gname}"] = statistics.mean(kt)
+            simt.close()
     if not args.no_variants and rank == 0 and args.batch_steps > 0:
         variants["batched"] = batch_block(S, torch, f"cuda:{local}", 64, args.batch_steps)
     if not args.no_variants and rank == 0 and not args.no_adjoint:

@@ -103,15 +103,17 @@ typedef struct {
     double mu_inf_override; /* > 0: use this mu_inf instead of rho0*U0/Re */
     int collide;            /* 1: stream and collide (normal); 0: stream only */
     int kernel;             /* step kernel: 0 automatic, 1 generic tile kernel, 2 TMA-fed
-                               persistent kernel (FP32 and the 16-bit deviation storages; needs
+                               persistent kernel (FP32 and the 16-bit deviation storages, the
+                               Prandtl term with FP32 storage; needs
                                N[0] a multiple of 2 (FP32) or 4 (16-bit), cells divisible by its
                                tile of 4x4x2 (p = 2), 2x3x1 (p = 3: y may end in a partial
-                               tile) or 2x2x1 cells (p = 4), no Prandtl term, collide on, no
-                               compensated sums; else SLLBM_EINVAL).  Automatic: the TMA-fed
+                               tile) or 2x2x1 cells (p = 4), collide on, no compensated sums;
+                               else SLLBM_EINVAL).  Automatic: the TMA-fed
                                kernel where it can run and the mesh (a slab: its interior)
                                has at least 0.5 M (p = 2), 3 M (p = 3) or 1.5 M (p = 4)
-                               nodes, except at p = 3 with 16-bit storage outside slab
-                               contexts (the faster kernel in each case, as measured) */
+                               nodes, except with the Prandtl term and at p = 3 with 16-bit
+                               storage outside slab contexts (the faster kernel in each case,
+                               as measured) */
 } sllbm_params;
 
 /* Read-only description of a created context. */

@@ -128,11 +128,22 @@ int tensor_maps_for(sllbm_ctx* ctx, const void* src, TmaMaps* out) {
     return SLLBM_OK;
 }
 
-template <typename S, int P>
+// Per-velocity coefficients of the Prandtl term (see PrTablesS), from the velocity set in FP64.
+void fill_pr_tables(const sllbm_ctx* ctx, PrTablesS* pt) {
+    for (int i = 0; i < kQ; ++i) {
+        const double x = ctx->xi[i][0], y = ctx->xi[i][1], z = ctx->xi[i][2];
+        const double a[10] = {x * x * x - 3 * x,     y * y * y - 3 * y,     z * z * z - 3 * z,     3 * x * x * y - 3 * y,
+                              3 * x * x * z - 3 * z, 3 * y * y * x - 3 * x, 3 * y * y * z - 3 * z, 3 * z * z * x - 3 * x,
+                              3 * z * z * y - 3 * y, 6 * x * y * z};
+        for (int k = 0; k < 10; ++k) pt->a[i][k] = static_cast<float>(a[k] / 6.0);
+    }
+}
+
+template <typename S, int P, bool PR>
 int launch_tma(sllbm_ctx* ctx, const void* src, void* dst) {
     using T = TmaTile<P>;
     constexpr int kConsumers = kConsumersFor<P>;
-    using SM = TmaSmem<S, P, T::CX, T::CY, T::CZ, kConsumers>;
+    using SM = TmaSmem<S, P, T::CX, T::CY, T::CZ, kConsumers, PR>;
     static_assert(SM::bytes <= kSmemBudget, "shared memory budget");
     using Tab = StepTablesS<P>;
     if (ctx->step_blob == nullptr || ctx->step_blob_size != sizeof(Tab) + 1) {
@@ -147,7 +158,13 @@ int launch_tma(sllbm_ctx* ctx, const void* src, void* dst) {
     if (rc != SLLBM_OK) return rc;
     StepArgs args;
     fill_step_args(ctx, src, dst, &args);
-    auto k = step_tma_kernel<S, P, T::CX, T::CY, T::CZ, kConsumers>;
+    PrTablesS prt;
+    if (PR) {
+        fill_pr_tables(ctx, &prt);
+    } else {
+        std::memset(&prt, 0, sizeof(prt));
+    }
+    auto k = step_tma_kernel<S, P, T::CX, T::CY, T::CZ, kConsumers, PR>;
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(SM::bytes));
     // all z-tiles, or the part of a slab's tiles its split step asks for (one launch per range)
     int ranges[2][2];
@@ -159,7 +176,7 @@ int launch_tma(sllbm_ctx* ctx, const void* src, void* dst) {
             (ctx->cells[0] / T::CX) * ((ctx->cells[1] + T::CY - 1) / T::CY) * (ranges[q][1] - ranges[q][0]);
         if (ntiles <= 0) continue;
         const int grid = ntiles < ctx->num_sms ? ntiles : ctx->num_sms;
-        k<<<grid, kWarps * 32, SM::bytes, ctx->stream>>>(maps, args, *reinterpret_cast<const Tab*>(ctx->step_blob));
+        k<<<grid, kWarps * 32, SM::bytes, ctx->stream>>>(maps, args, *reinterpret_cast<const Tab*>(ctx->step_blob), prt);
         err = cudaGetLastError();
         ctx->launches += 1;
     }
@@ -175,7 +192,8 @@ int launch_tma(sllbm_ctx* ctx, const void* src, void* dst) {
 bool tma_step_eligible(const sllbm_ctx* c) {
     const int st = c->prm.storage;
     if (st != SLLBM_F32 && st != SLLBM_F16DEV && st != SLLBM_BF16DEV) return false;
-    if (c->prm.pr_correction || !c->prm.collide || c->compensated) return false;
+    // (the Prandtl term with FP32 storage only)
+    if ((c->prm.pr_correction && st != SLLBM_F32) || !c->prm.collide || c->compensated) return false;
     // TMA rows start on 16 bytes: x a multiple of 2 (FP32) or 4 (16-bit) pairs, so a row
     // of the mesh must be one too
     if (c->N[0] % (st == SLLBM_F32 ? 2 : 4) != 0 || c->num_sms <= 0) return false;
@@ -189,12 +207,12 @@ bool tma_step_eligible(const sllbm_ctx* c) {
 }
 
 namespace {
-template <typename S>
+template <typename S, bool PR>
 int launch_tma_for(sllbm_ctx* ctx, const void* src, void* dst) {
     switch (ctx->p) {
-    case 2: return launch_tma<S, 2>(ctx, src, dst);
-    case 3: return launch_tma<S, 3>(ctx, src, dst);
-    case 4: return launch_tma<S, 4>(ctx, src, dst);
+    case 2: return launch_tma<S, 2, PR>(ctx, src, dst);
+    case 3: return launch_tma<S, 3, PR>(ctx, src, dst);
+    case 4: return launch_tma<S, 4, PR>(ctx, src, dst);
     }
     return SLLBM_EINVAL;
 }
@@ -202,9 +220,11 @@ int launch_tma_for(sllbm_ctx* ctx, const void* src, void* dst) {
 
 int launch_step_tma(sllbm_ctx* ctx, const void* src, void* dst) {
     switch (ctx->prm.storage) {
-    case SLLBM_F32: return launch_tma_for<float>(ctx, src, dst);
-    case SLLBM_F16DEV: return launch_tma_for<__half>(ctx, src, dst);
-    case SLLBM_BF16DEV: return launch_tma_for<__nv_bfloat16>(ctx, src, dst);
+    case SLLBM_F32:
+        return ctx->prm.pr_correction ? launch_tma_for<float, true>(ctx, src, dst)
+                                      : launch_tma_for<float, false>(ctx, src, dst);
+    case SLLBM_F16DEV: return launch_tma_for<__half, false>(ctx, src, dst);
+    case SLLBM_BF16DEV: return launch_tma_for<__nv_bfloat16, false>(ctx, src, dst);
     }
     return SLLBM_EINVAL;
 }

@@ -29,6 +29,10 @@
 //    nodes), then the collision of the quarter's pairs and 16- or 8-byte stores (f_i and g_i
 //    interleaved).  Meanwhile the stream warps fill the other buffer: streaming never
 //    waits for the collision.
+//  * With the quasi-equilibrium Prandtl term (App. D, FP32 storage) the epilogue warps also
+//    form the centred third moment of the streamed f per node, in a second pass over their
+//    buffer (two rounds of five components, the quarters summed through shared memory), and
+//    add the term to the collision.
 //  * Every mbarrier wait is bounded; on expiry the kernel raises an error flag, the stream
 //    and epilogue warps leave (and free the tensor memory) and the producer waits (bounded)
 //    for its copies in flight before returning.
@@ -59,6 +63,15 @@ struct StepTablesS {
     signed char kc[kQ][3][P];   // departure cell shift minus kmin (0 or 1)
     signed char kmin[kQ][3];
     signed char span[kQ][3];
+};
+
+// Coefficients of the quasi-equilibrium Prandtl term per velocity (App. D): with Qbar the
+// centred third moment of the streamed f and q_a = sum_b Qbar_abb, f*_i / w_i =
+// (Qbar : H3(xi_i)) / 6 = sum_k a[i][k] Qbar_k over Qbar_xxx, Qbar_yyy, Qbar_zzz, Qbar_xxy,
+// Qbar_xxz, Qbar_yyx, Qbar_yyz, Qbar_zzx, Qbar_zzy, Qbar_xyz, with a = (x^3 - 3x, y^3 - 3y,
+// z^3 - 3z, 3x^2y - 3y, 3x^2z - 3z, 3y^2x - 3x, 3y^2z - 3z, 3z^2x - 3x, 3z^2y - 3y, 6xyz) / 6.
+struct PrTablesS {
+    float a[kQ][10];
 };
 
 // Box and tile geometry for storage type S (float: f and g themselves; __half or
@@ -151,7 +164,7 @@ constexpr int kItems = 32;
 constexpr size_t kSmemBudget = 227 * 1024;
 static_assert((kItems & (kItems - 1)) == 0, "item table size");
 
-template <typename S, int P, int CX, int CY, int CZ, int NC>
+template <typename S, int P, int CX, int CY, int CZ, int NC, bool PR = false>
 struct TmaSmem {
     using G = TmaGeom<S, P, CX, CY, CZ>;
     // every region starts on a 128-byte boundary (TMA destinations, float4 and mbarrier
@@ -177,8 +190,13 @@ struct TmaSmem {
     static constexpr size_t woff = round128(size_t(NPROD) * woff_n * sizeof(long long));
     static constexpr size_t stage = size_t(kEpilogueWarps) * 32 * 64;  // one pair's 32 rows per epilogue warp
     static constexpr size_t scratch = round128(size_t(NC) * G::SCRATCH_F2 * 8);  // 16-bit storage only
+    // Prandtl term only: the quarters' partial sums of five components of the centred third
+    // moment (4 x 5 rows), the ten components per node (10 rows) and the per-velocity
+    // coefficients of the term (kQ x 10)
+    static constexpr int kQRows = 30;
+    static constexpr size_t qreg = PR ? round128((size_t(kQRows) * G::TX * 32 + size_t(kQ) * 10) * sizeof(float)) : 0;
     static constexpr size_t fixed =
-        partials + params + tables + bars_padded + woff + stage + scratch + 128;  // +128: base alignment
+        partials + params + tables + bars_padded + woff + stage + scratch + qreg + 128;  // +128: base alignment
     // the box ring takes the rest, in 128-byte units
     static constexpr int ring_units = static_cast<int>((kSmemBudget - fixed) / 128);
     static constexpr size_t ring = size_t(ring_units) * 128;
@@ -500,12 +518,13 @@ __device__ __forceinline__ int wrapi(int v, int n) {
 }
 
 // ------------------------------------------------------------------ kernel
-template <typename S, int P, int CX, int CY, int CZ, int NC>
+template <typename S, int P, int CX, int CY, int CZ, int NC, bool PR>
 __global__ void __launch_bounds__(kWarps * 32, 1)
     step_tma_kernel(const __grid_constant__ TmaMaps maps, const StepArgs a,
-                    const __grid_constant__ StepTablesS<P> tpar) {
+                    const __grid_constant__ StepTablesS<P> tpar, const __grid_constant__ PrTablesS prt) {
     using G = TmaGeom<S, P, CX, CY, CZ>;
-    using SM = TmaSmem<S, P, CX, CY, CZ, NC>;
+    using SM = TmaSmem<S, P, CX, CY, CZ, NC, PR>;
+    static_assert(!PR || G::kF32, "the Prandtl term runs with FP32 storage");
     constexpr int NPW = kMaxPairsPerWarp;  // velocity pairs per stream warp, at most
     using TC = TmemCols<G::PCS, NPW, NC>;
     // (x in the tensor maps counts floats for FP32 storage, (f, g) pairs for 16-bit storage)
@@ -536,6 +555,10 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     float4* stage = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(bars) + SM::bars_padded + SM::woff);
     float2* scratch = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(bars) + SM::bars_padded + SM::woff +
                                                 SM::stage);
+    // Prandtl term: partial sums [quarter][component][x][lane] (20 rows), the centred third
+    // moment [component][x][lane] (10 rows), then the per-velocity coefficients
+    float* qreg = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(bars) + SM::bars_padded + SM::woff +
+                                           SM::stage + SM::scratch);
     const uint32_t full0 = smem_u32(bars);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -544,6 +567,10 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         const int* src = reinterpret_cast<const int*>(&tpar);
         int* dstw = reinterpret_cast<int*>(tsm);
         for (int q = threadIdx.x; q < static_cast<int>(sizeof(StepTablesS<P>) / 4); q += blockDim.x) dstw[q] = src[q];
+        if constexpr (PR) {
+            float* pa = qreg + SM::kQRows * G::TX * 32;
+            for (int q = threadIdx.x; q < kQ * 10; q += blockDim.x) pa[q] = prt.a[q / 10][q % 10];
+        }
     }
     const StepTablesS<P>& t = *tsm;
     if (threadIdx.x == 0) {
@@ -1248,6 +1275,11 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                     pn[3 * QS] = uz;
                     pn[4 * QS] = static_cast<float>(a.gfac) * T;
                     pn[5 * QS] = 1.0f / tau_r;
+                    if constexpr (PR) {
+                        // App. D: the term relaxes with tau_Pr = (tau - 1/2) / Pr + 1/2
+                        const float tau_pr = (tau_r - 0.5f) * static_cast<float>(a.inv_pr) + 0.5f;
+                        pn[18 * QS] = 1.0f / tau_r - 1.0f / tau_pr;
+                    }
 #pragma unroll
                     for (int sh = 0; sh < 4; ++sh) {
                         pn[(6 + sh) * QS] = ec.c0[sh];
@@ -1295,6 +1327,82 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                 }
             }
             epilogue_barrier_or(0);
+            float* qall = qreg + 20 * QS;  // Prandtl term: Qbar per node, 10 rows
+            if constexpr (PR) {
+                // App. D: centred third moment Qbar_abc = sum_i f_i c_a c_b c_c (c = xi_i - u)
+                // of the streamed f at each node, from the quarter's pairs (a second pass over
+                // its tensor-memory buffer) in two rounds of five components and two halves
+                // of the lane's nodes (registers), the quarters' partial sums summed through
+                // shared memory in a fixed order, as the moments are
+                constexpr int NH = G::TX / 2;
+                float* qpart = qreg;
+#pragma unroll 1
+                for (int r = 0; r < 2; ++r) {
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        float acc[5][NH], uxh[NH], uyh[NH], uzh[NH];
+#pragma unroll
+                        for (int n = 0; n < NH; ++n) {
+                            const float* pn = prm + (hh * NH + n) * 32 + lane;
+                            uxh[n] = pn[1 * QS];
+                            uyh[n] = pn[2 * QS];
+                            uzh[n] = pn[3 * QS];
+#pragma unroll
+                            for (int c = 0; c < 5; ++c) acc[c][n] = 0.f;
+                        }
+                        for (int sw = sw0; sw < nsw; ++sw) {
+                            const int cw = stream_index(qd + 4 * sw), npw = pairs_of(cw);
+#pragma unroll 1
+                            for (int k = 0; k < npw; ++k) {
+                                const int j = pair_of(cw, k);
+                                float v[2 * G::TX];
+                                tmem_load_row<G::TX>(tb + static_cast<uint32_t>(sw * TC::per_warp + k * G::PCS), v);
+                                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                                const float xix = t.xi[j][0], xiy = t.xi[j][1], xiz = t.xi[j][2];
+#pragma unroll
+                                for (int n = 0; n < NH; ++n) {
+                                    const float f = v[2 * (hh * NH + n)];
+                                    const float cx = xix - uxh[n], cy = xiy - uyh[n], cz = xiz - uzh[n];
+                                    const float fx = f * cx, fy = f * cy, fz = f * cz;
+                                    if (r == 0) {
+                                        acc[0][n] += fx * cx * cx;  // xxx
+                                        acc[1][n] += fy * cy * cy;  // yyy
+                                        acc[2][n] += fz * cz * cz;  // zzz
+                                        acc[3][n] += fx * cx * cy;  // xxy
+                                        acc[4][n] += fx * cx * cz;  // xxz
+                                    } else {
+                                        acc[0][n] += fy * cy * cx;  // yyx
+                                        acc[1][n] += fy * cy * cz;  // yyz
+                                        acc[2][n] += fz * cz * cx;  // zzx
+                                        acc[3][n] += fz * cz * cy;  // zzy
+                                        acc[4][n] += fx * cy * cz;  // xyz
+                                    }
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int c = 0; c < 5; ++c)
+#pragma unroll
+                            for (int n = 0; n < NH; ++n)
+                                qpart[(qd * 5 + c) * QS + (hh * NH + n) * 32 + lane] = acc[c][n];
+                    }
+                    epilogue_barrier_or(0);
+#pragma unroll
+                    for (int xx = 0; xx < XS; ++xx) {
+                        const int x = ep * XS + xx;
+                        if (x >= G::TX) break;
+#pragma unroll
+                        for (int c = 0; c < 5; ++c)
+                            qall[(5 * r + c) * QS + x * 32 + lane] =
+                                ((qpart[(0 * 5 + c) * QS + x * 32 + lane] + qpart[(1 * 5 + c) * QS + x * 32 + lane]) +
+                                 qpart[(2 * 5 + c) * QS + x * 32 + lane]) +
+                                qpart[(3 * 5 + c) * QS + x * 32 + lane];
+                    }
+                    epilogue_barrier_or(0);
+                }
+            } else {
+                (void)qall;
+            }
             // collision of the quarter's pairs at the lane's TX nodes, pair by pair
             // (FP32: gT_; deviations: dr_ = rho - rho0, gr_ and gb_ the g equilibrium's factor
             // and offset)
@@ -1378,6 +1486,25 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                             const float f = h[2 * x], g = h[2 * x + 1];
                             h[2 * x] = f + om_[x] * (feq - f);
                             h[2 * x + 1] = g + om_[x] * (gT_[x] * feq - g);
+                        }
+                        if constexpr (PR) {
+                            // App. D: f*_i = w_i (Qbar : H3(xi_i)) / 6, g*_i = (2C_v - D) T f*_i,
+                            // relaxed at omega - omega_Pr
+                            const float* pa = qreg + SM::kQRows * G::TX * 32 + j * 10;
+                            float aj[10];
+#pragma unroll
+                            for (int c = 0; c < 10; ++c) aj[c] = pa[c];
+#pragma unroll
+                            for (int x = 0; x < G::TX; ++x) {
+                                const float* qn = qall + x * 32 + lane;
+                                float fw = aj[0] * qn[0];
+#pragma unroll
+                                for (int c = 1; c < 10; ++c) fw += aj[c] * qn[c * QS];
+                                const float fst = wj * fw;
+                                const float ompr = prm[18 * QS + x * 32 + lane];
+                                h[2 * x] += ompr * fst;
+                                h[2 * x + 1] += ompr * gT_[x] * fst;
+                            }
                         }
                     } else {
                         // the collision written for the deviations (f^eq / (w rho) - 1 = pm1):

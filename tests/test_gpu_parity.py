@@ -168,6 +168,25 @@ def test_step_f32_tma_matches_oracle(S, cells, p):
     assert sim.status() == 0
 
 
+@pytest.mark.parametrize("cells,p", [((2, 2, 1), 4), ((4, 2, 3), 4), ((8, 8, 6), 4), ((8, 4, 2), 2),
+                                     ((12, 8, 4), 2), ((2, 3, 1), 3), ((8, 7, 3), 3)])
+def test_step_f32_tma_prandtl_term_matches_oracle(S, cells, p):
+    """The TMA-fed kernel with the quasi-equilibrium Prandtl term (App. D), two steps, with
+    the bound of the FP32 step without it."""
+    sim = make(S, cells, p, storage="f32", courant=3.0, pr=True, kernel=2, check=True)
+    assert sim.info.step_kernel == 2
+    g = grid_of(sim, pr=True)
+    pop = noneq_state(g, 23).astype(np.float32).astype(np.float64)
+    sim.set_populations(pop)
+    for _ in range(2):
+        assert sim.step(1) == 0
+        pop = O.step(g, pop, 1)
+        got = sim.populations().cpu().numpy()
+        assert rel_l2(got, pop) <= 1.5e-6
+        assert np.max(np.abs(got - pop)) <= 3e-6 * np.abs(pop).max()
+    assert sim.status() == 0
+
+
 def test_tma_kernel_agrees_with_generic_kernel(S):
     """Both FP32 kernels on the same 64^3-node Taylor-Green run (C = 8, multi-cell shifts)."""
     a = make(S, (16, 16, 16), 4, storage="f32", courant=8.0, kernel=1)
@@ -183,8 +202,8 @@ def test_tma_kernel_agrees_with_generic_kernel(S):
 def test_tma_kernel_refuses_meshes_it_cannot_tile(S):
     with pytest.raises(S.SllbmError):
         make(S, (3, 2, 2), 4, storage="f32", kernel=2)
-    with pytest.raises(S.SllbmError):
-        make(S, (2, 2, 2), 4, storage="f32", kernel=2, pr=True)
+    with pytest.raises(S.SllbmError):  # the Prandtl term runs on the TMA-fed kernel with FP32 storage only
+        make(S, (2, 2, 1), 4, storage="f16dev", kernel=2, pr=True)
     assert make(S, (3, 2, 2), 4, storage="f32").info.step_kernel == 1
     # p = 3: tiles are 2 cells wide in x; 16-bit rows must also start on 16 bytes (N[0] a
     # multiple of 4 pairs); the generic kernel runs where the TMA-fed one cannot

@@ -24,13 +24,16 @@ def S():
     return sllbm
 
 
-# the TMA-fed instances the run-control tests cover: FP32 at p = 4, FP16 deviations at p = 3
-# (a 16-bit box is released right after its z pass), BF16 deviations at p = 4
-TMA_RUN_CASES = [("f32", 4, (16, 8, 8)), ("f16dev", 3, (8, 6, 4)), ("bf16dev", 4, (8, 4, 4))]
+# the TMA-fed instances the run-control tests cover: FP32 at p = 4 (without and with the
+# Prandtl term, whose epilogue has more barriers), FP16 deviations at p = 3 (a 16-bit box is
+# released right after its z pass), BF16 deviations at p = 4
+TMA_RUN_CASES = [("f32", 4, (16, 8, 8)), ("f32pr", 4, (8, 8, 4)), ("f16dev", 3, (8, 6, 4)), ("bf16dev", 4, (8, 4, 4))]
 
 
 def tma_sim(S, cells=(16, 8, 8), storage="f32", p=4):
-    sim = S.Sim(S.Config(cells=cells, p=p, courant=3.0, storage=storage, kernel=2))
+    pr = storage.endswith("pr")
+    storage = storage[:-2] if pr else storage
+    sim = S.Sim(S.Config(cells=cells, p=p, courant=3.0, storage=storage, kernel=2, pr_correction=pr))
     assert sim.info.step_kernel == 2
     return sim
 
@@ -40,7 +43,8 @@ def check_against_oracle(S, sim, steps=2, tol=1e-5):
     step from the decoded state, in deviation space within the output rounding (2^-11 or 2^-8
     of |d|) plus 1e-5 max|d| for the FP32 arithmetic."""
     sim.init_tgv()
-    g = O.Grid(cells=tuple(sim.cfg.cells), p=sim.cfg.p, dt=sim.dt, mu_inf=float(sim.info.mu_inf))
+    g = O.Grid(cells=tuple(sim.cfg.cells), p=sim.cfg.p, dt=sim.dt, mu_inf=float(sim.info.mu_inf),
+               pr_correction=bool(sim.cfg.pr_correction))
     if sim.cfg.storage == "f32":
         assert sim.step(steps) == 0
         assert S.sllbm_status(sim.ctx) == S.OK

@@ -27,8 +27,9 @@ The line's "alu_peaks" are measured at the start by the library's FMA microbench
 (sllbm_fma_peak: FP32, packed FP32x2, FP64); the FP64 variant and the mixed block quote
 their arithmetic against them ("roofline_alu"; for 16-bit storage the bound is the larger of
 the HBM time of the algorithmic bytes and the FP32 time of the algorithmic flops).  The
-mixed block also runs FP32 arithmetic with compensated moment sums ("*_comp").  The "pr"
-variant times the headline workload with the Prandtl term of App. D on.  The "long_run"
+mixed block also runs FP32 arithmetic with compensated moment sums ("*_comp"), and the
+"compensated" variant times the headline workload with them.  The "pr" variant times the
+headline workload with the Prandtl term of App. D on.  The "long_run"
 block runs the throughput mesh for 2000 steps in FP32 and FP64 (Prandtl term on, the
 paper's Taylor-Green setting) and compares their E_k(t) and eps(t) curves with each other
 and with the oracle's 16^3-cell run at the same time step (tests/golden).
@@ -144,9 +145,9 @@ def measured_peaks():
 
 KERNEL_SOURCES = {
     # the TMA-fed kernel and what it is built from
-    "tma": ("step_tma.cuh", "step_tma.cu", "collide.cuh", "packed.cuh", "sllbm_internal.h", "tables.h"),
+    "tma": ("step_tma.cuh", "step_tma.cu", "collide.cuh", "compsum.cuh", "packed.cuh", "sllbm_internal.h", "tables.h"),
     # the generic tile kernel and its instances
-    "generic": ("step_kernel.cuh", "collide.cuh", "packed.cuh", "storage.cuh", "sllbm_internal.h", "tables.h", "step_f32.cu",
+    "generic": ("step_kernel.cuh", "collide.cuh", "compsum.cuh", "packed.cuh", "storage.cuh", "sllbm_internal.h", "tables.h", "step_f32.cu",
                 "step_f32_tiles.cu", "step_f64.cu", "step_f16.cu"),
 }
 
@@ -346,7 +347,7 @@ def mixed_precision_block(S, torch, device, steps, every, hbm, alu):
     relative L2 error against the FP64 GPU run of rho, u, T after the last step and of the
     E_k(t) and dissipation eps_s(t) + eps_c(t) curves sampled every `every` steps.  The
     FP32-arithmetic storages run a second time with compensated moment sums
-    ("<storage>_comp", generic kernel).  "periodic_wrap_timing" times the ordinary periodic
+    ("<storage>_comp", the same automatic kernel choice).  "periodic_wrap_timing" times the ordinary periodic
     context (boxes wrapping around along z) with the automatic choice (the generic kernel for
     16-bit storage at p = 3) and with the TMA-fed kernel forced."""
     import numpy as np
@@ -814,6 +815,20 @@ def run_mine(args, rank, world, local):
                                      "hbm_frac": bytes_per_node * nodes / (statistics.mean(kw) / 1e3) / 1e9 / hbm,
                                      "steps": nw}
         simw.close()
+    if not args.no_variants and rank == 0 and storage != "f64" and not args.pr:
+        # the same workload with compensated moment sums (the same context kind and kernel choice)
+        simc = S.Sim(cfg, device=f"cuda:{local}")
+        S.sllbm_set_compensated(simc.ctx, True)
+        simc.init_tgv()
+        simc.step(3)
+        nc = 50
+        tc, kc = time_steps(simc, torch, nc)
+        kc_ms = statistics.mean(kc)
+        variants["compensated"] = {"value": nodes * nc / (tc / 1e3), "ms_per_step": tc / nc, "kernel_ms": kc_ms,
+                                   "step_kernel": int(S.sllbm_get_info(simc.ctx).step_kernel),
+                                   "kernel_time_vs_plain": kc_ms / kern_avg_ms,
+                                   "hbm_frac": bytes_per_node * nodes / (kc_ms / 1e3) / 1e9 / hbm, "steps": nc}
+        simc.close()
     if not args.no_variants and rank == 0 and storage == "f32":
         # FP64 storage/arithmetic on the same workload (FP64-ALU bound on this part)
         sim64 = S.Sim(S.Config(cells=w.cells, p=w.p, Ma=w.Ma, Re=w.Re, Pr=w.Pr, gamma=w.gamma,

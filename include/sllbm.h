@@ -107,13 +107,15 @@ typedef struct {
                                Prandtl term with FP32 storage; needs
                                N[0] a multiple of 2 (FP32) or 4 (16-bit), cells divisible by its
                                tile of 4x4x2 (p = 2), 2x3x1 (p = 3: y may end in a partial
-                               tile) or 2x2x1 cells (p = 4), collide on, no compensated sums;
-                               else SLLBM_EINVAL).  Automatic: the TMA-fed
-                               kernel where it can run and the mesh (a slab: its interior)
-                               has at least 0.5 M (p = 2), 3 M (p = 3) or 1.5 M (p = 4)
-                               nodes, except with the Prandtl term and at p = 3 with 16-bit
-                               storage outside slab contexts (the faster kernel in each case,
-                               as measured) */
+                               tile) or 2x2x1 cells (p = 4), collide on, not both the
+                               Prandtl term and compensated sums; else SLLBM_EINVAL).
+                               Automatic: the TMA-fed kernel where it can run and the mesh
+                               (a slab: its interior) has at least 0.5 M (p = 2), 3 M
+                               (p = 3) or 1.5 M (p = 4) nodes, except with the Prandtl term,
+                               at p = 3 with 16-bit storage outside slab contexts, and with
+                               compensated moment sums at p = 3, or at p = 4 with 16-bit
+                               storage outside slab contexts (the faster kernel in each
+                               case, as measured) */
 } sllbm_params;
 
 /* Read-only description of a created context. */
@@ -467,10 +469,11 @@ int sllbm_debug_fail_allocs(int after);
  * arithmetic (SLLBM_F32 and the 16-bit deviation storages): rho, rho u and the energy sum
  * of Eq. (moments), and the temperature's 2 rho E - rho |u|^2, are accumulated with
  * error-free two-sum / two-product steps, so that each carries about one FP32 rounding
- * instead of one per term.  Runs on the generic tile kernel's default tile (the TMA-fed
- * kernel and the alternative tiles sum plainly; the kernel choice follows the flag).
- * FP64 storage ignores it.  SLLBM_EINVAL if the context's parameters force the TMA-fed
- * kernel. */
+ * instead of one per term.  Both step kernels run it: the TMA-fed kernel (without the
+ * Prandtl term) and the generic tile kernel's default tile (its alternative tiles sum
+ * plainly, so the flag returns the context to the default tile); the automatic kernel
+ * choice is made again.  FP64 storage ignores it.  SLLBM_EINVAL if the context's
+ * parameters force the TMA-fed kernel and carry the Prandtl term. */
 int sllbm_set_compensated(sllbm_ctx *ctx, int on);
 
 /* Steps taken since the state was last set (initialisation, sllbm_set_populations,

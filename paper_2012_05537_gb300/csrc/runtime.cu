@@ -110,15 +110,11 @@ int64_t sllbm_step_count(const sllbm_ctx* ctx) { return ctx ? ctx->steps : 0; }
 
 int sllbm_set_compensated(sllbm_ctx* ctx, int on) {
     if (ctx == nullptr) return SLLBM_EINVAL;
-    if (on && ctx->prm.kernel == 2) return SLLBM_EINVAL;  // the TMA-fed kernel sums plainly
+    // (the TMA-fed kernel has no instance with both compensated sums and the Prandtl term)
+    if (on && ctx->prm.kernel == 2 && ctx->prm.pr_correction) return SLLBM_EINVAL;
     ctx->compensated = on ? 1 : 0;
-    if (ctx->compensated) {
-        // the kernels that sum plainly: the TMA-fed one and the generic alternative tiles
-        ctx->step_kernel = 1;
-        ctx->tile_shape = 0;
-    } else {
-        ctx->step_kernel = choose_step_kernel(ctx);
-    }
+    if (ctx->compensated) ctx->tile_shape = 0;  // the generic kernel's alternative tiles sum plainly
+    ctx->step_kernel = choose_step_kernel(ctx);
     return SLLBM_OK;
 }
 

@@ -139,11 +139,11 @@ void fill_pr_tables(const sllbm_ctx* ctx, PrTablesS* pt) {
     }
 }
 
-template <typename S, int P, bool PR>
+template <typename S, int P, bool PR, bool KC>
 int launch_tma(sllbm_ctx* ctx, const void* src, void* dst) {
     using T = TmaTile<P>;
     constexpr int kConsumers = kConsumersFor<P>;
-    using SM = TmaSmem<S, P, T::CX, T::CY, T::CZ, kConsumers, PR>;
+    using SM = TmaSmem<S, P, T::CX, T::CY, T::CZ, kConsumers, PR, KC>;
     static_assert(SM::bytes <= kSmemBudget, "shared memory budget");
     using Tab = StepTablesS<P>;
     if (ctx->step_blob == nullptr || ctx->step_blob_size != sizeof(Tab) + 1) {
@@ -164,7 +164,7 @@ int launch_tma(sllbm_ctx* ctx, const void* src, void* dst) {
     } else {
         std::memset(&prt, 0, sizeof(prt));
     }
-    auto k = step_tma_kernel<S, P, T::CX, T::CY, T::CZ, kConsumers, PR>;
+    auto k = step_tma_kernel<S, P, T::CX, T::CY, T::CZ, kConsumers, PR, KC>;
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(SM::bytes));
     // all z-tiles, or the part of a slab's tiles its split step asks for (one launch per range)
     int ranges[2][2];
@@ -192,8 +192,8 @@ int launch_tma(sllbm_ctx* ctx, const void* src, void* dst) {
 bool tma_step_eligible(const sllbm_ctx* c) {
     const int st = c->prm.storage;
     if (st != SLLBM_F32 && st != SLLBM_F16DEV && st != SLLBM_BF16DEV) return false;
-    // (the Prandtl term with FP32 storage only)
-    if ((c->prm.pr_correction && st != SLLBM_F32) || !c->prm.collide || c->compensated) return false;
+    // (the Prandtl term with FP32 storage only; compensated moment sums without it)
+    if ((c->prm.pr_correction && (st != SLLBM_F32 || c->compensated)) || !c->prm.collide) return false;
     // TMA rows start on 16 bytes: x a multiple of 2 (FP32) or 4 (16-bit) pairs, so a row
     // of the mesh must be one too
     if (c->N[0] % (st == SLLBM_F32 ? 2 : 4) != 0 || c->num_sms <= 0) return false;
@@ -207,12 +207,12 @@ bool tma_step_eligible(const sllbm_ctx* c) {
 }
 
 namespace {
-template <typename S, bool PR>
+template <typename S, bool PR, bool KC = false>
 int launch_tma_for(sllbm_ctx* ctx, const void* src, void* dst) {
     switch (ctx->p) {
-    case 2: return launch_tma<S, 2, PR>(ctx, src, dst);
-    case 3: return launch_tma<S, 3, PR>(ctx, src, dst);
-    case 4: return launch_tma<S, 4, PR>(ctx, src, dst);
+    case 2: return launch_tma<S, 2, PR, KC>(ctx, src, dst);
+    case 3: return launch_tma<S, 3, PR, KC>(ctx, src, dst);
+    case 4: return launch_tma<S, 4, PR, KC>(ctx, src, dst);
     }
     return SLLBM_EINVAL;
 }
@@ -221,10 +221,15 @@ int launch_tma_for(sllbm_ctx* ctx, const void* src, void* dst) {
 int launch_step_tma(sllbm_ctx* ctx, const void* src, void* dst) {
     switch (ctx->prm.storage) {
     case SLLBM_F32:
-        return ctx->prm.pr_correction ? launch_tma_for<float, true>(ctx, src, dst)
-                                      : launch_tma_for<float, false>(ctx, src, dst);
-    case SLLBM_F16DEV: return launch_tma_for<__half, false>(ctx, src, dst);
-    case SLLBM_BF16DEV: return launch_tma_for<__nv_bfloat16, false>(ctx, src, dst);
+        if (ctx->prm.pr_correction) return launch_tma_for<float, true>(ctx, src, dst);
+        return ctx->compensated ? launch_tma_for<float, false, true>(ctx, src, dst)
+                                : launch_tma_for<float, false>(ctx, src, dst);
+    case SLLBM_F16DEV:
+        return ctx->compensated ? launch_tma_for<__half, false, true>(ctx, src, dst)
+                                : launch_tma_for<__half, false>(ctx, src, dst);
+    case SLLBM_BF16DEV:
+        return ctx->compensated ? launch_tma_for<__nv_bfloat16, false, true>(ctx, src, dst)
+                                : launch_tma_for<__nv_bfloat16, false>(ctx, src, dst);
     }
     return SLLBM_EINVAL;
 }

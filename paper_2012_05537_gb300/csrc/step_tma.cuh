@@ -33,6 +33,10 @@
 //    form the centred third moment of the streamed f per node, in a second pass over their
 //    buffer (two rounds of five components, the quarters summed through shared memory), and
 //    add the term to the collision.
+//  * With compensated moment sums (KC; FP32 arithmetic, without the Prandtl term) each
+//    epilogue warp keeps a two-sum running sum and its error per moment and node, and the
+//    quarters' sums and errors are merged in the same compensated way, so a moment carries
+//    about one FP32 rounding.
 //  * Every mbarrier wait is bounded; on expiry the kernel raises an error flag, the stream
 //    and epilogue warps leave (and free the tensor memory) and the producer waits (bounded)
 //    for its copies in flight before returning.
@@ -48,6 +52,7 @@
 #include <type_traits>
 
 #include "collide.cuh"
+#include "compsum.cuh"
 #include "packed.cuh"
 #include "sllbm_internal.h"
 
@@ -164,7 +169,7 @@ constexpr int kItems = 32;
 constexpr size_t kSmemBudget = 227 * 1024;
 static_assert((kItems & (kItems - 1)) == 0, "item table size");
 
-template <typename S, int P, int CX, int CY, int CZ, int NC, bool PR = false>
+template <typename S, int P, int CX, int CY, int CZ, int NC, bool PR = false, bool KC = false>
 struct TmaSmem {
     using G = TmaGeom<S, P, CX, CY, CZ>;
     // every region starts on a 128-byte boundary (TMA destinations, float4 and mbarrier
@@ -174,9 +179,11 @@ struct TmaSmem {
     // (FP32 storage); rho, ux, uy, uz, omega, rho - rho0, (2C_v-D) T rho, (2C_v-D)((T - T0) rho
     // + T0 (rho - rho0)), c0[4] - 1, c1[4], c2[4] (deviation storage)
     static constexpr int kNPar = G::kF32 ? kNParams : kNParams + 2;
-    // the per-quarter moment sums (4 quarters x 5) and the per-node parameters share one region:
-    // an epilogue warp reads the sums of exactly the node columns whose parameters it writes
-    static constexpr int kShared = 4 * 5 > kNPar ? 4 * 5 : kNPar;
+    // the per-quarter moment sums (4 quarters x 5, then with compensated sums their 4 x 5 error
+    // terms) and the per-node parameters share one region: an epilogue warp reads the sums of
+    // exactly the node columns whose parameters it writes
+    static constexpr int kSumRows = KC ? 2 * 4 * 5 : 4 * 5;
+    static constexpr int kShared = kSumRows > kNPar ? kSumRows : kNPar;
     static constexpr size_t partials = round128(size_t(kShared) * G::TX * 32 * sizeof(float));
     static constexpr size_t params = 0;
     static constexpr size_t tables = round128(sizeof(StepTablesS<P>));
@@ -518,12 +525,13 @@ __device__ __forceinline__ int wrapi(int v, int n) {
 }
 
 // ------------------------------------------------------------------ kernel
-template <typename S, int P, int CX, int CY, int CZ, int NC, bool PR>
+template <typename S, int P, int CX, int CY, int CZ, int NC, bool PR, bool KC>
 __global__ void __launch_bounds__(kWarps * 32, 1)
     step_tma_kernel(const __grid_constant__ TmaMaps maps, const StepArgs a,
                     const __grid_constant__ StepTablesS<P> tpar, const __grid_constant__ PrTablesS prt) {
     using G = TmaGeom<S, P, CX, CY, CZ>;
-    using SM = TmaSmem<S, P, CX, CY, CZ, NC, PR>;
+    using SM = TmaSmem<S, P, CX, CY, CZ, NC, PR, KC>;
+    static_assert(!(KC && PR), "compensated sums without the Prandtl term");
     static_assert(!PR || G::kF32, "the Prandtl term runs with FP32 storage");
     constexpr int NPW = kMaxPairsPerWarp;  // velocity pairs per stream warp, at most
     using TC = TmemCols<G::PCS, NPW, NC>;
@@ -1193,7 +1201,60 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                               a.wait_ns);
             tc_fence_after();
             // moment contributions of the quarter's pairs (rho, m_x, m_y, m_z, 2 rho E; Eq. moments)
-            {
+            if constexpr (KC) {
+                // compensated: a running sum and its exact rounding errors per moment and node
+                // (one tensor-memory load per pair, as below); the sums go to rows
+                // [quarter][moment], the error terms to the 20 rows after them
+                float* pc = part + static_cast<size_t>(qd) * 5 * QS + lane;
+                float* pe = pc + 20 * QS;
+                {
+                    CompSum<float> cs[5][G::TX];
+                    for (int sw = sw0; sw < nsw; ++sw) {
+                        const int cw = stream_index(qd + 4 * sw), npw = pairs_of(cw);
+#pragma unroll 1
+                        for (int k = 0; k < npw; ++k) {
+                            const int j = pair_of(cw, k);
+                            float v[2 * G::TX];
+                            tmem_load_row<G::TX>(tb + static_cast<uint32_t>(sw * TC::per_warp + k * G::PCS), v);
+                            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                            const float xix = t.xi[j][0], xiy = t.xi[j][1], xiz = t.xi[j][2];
+                            const float x2 = static_cast<float>(shell_xi2(shell_of(j)));
+                            if constexpr (G::kF32) {
+#pragma unroll
+                                for (int x = 0; x < G::TX; ++x) {
+                                    const float f = v[2 * x], g = v[2 * x + 1];
+                                    cs[0][x].add(f);
+                                    cs[1][x].add_prod(f, xix);
+                                    cs[2][x].add_prod(f, xiy);
+                                    cs[3][x].add_prod(f, xiz);
+                                    cs[4][x].add_prod(f, x2);
+                                    cs[4][x].add(g);
+                                }
+                            } else {
+                                const float wj = t.w[j];
+                                const float wx = wj * xix, wy = wj * xiy, wz = wj * xiz, wx2 = wj * x2;
+#pragma unroll
+                                for (int x = 0; x < G::TX; ++x) {
+                                    const float d = v[2 * x], dg = v[2 * x + 1];
+                                    cs[0][x].add_prod(wj, d);
+                                    cs[1][x].add_prod(wx, d);
+                                    cs[2][x].add_prod(wy, d);
+                                    cs[3][x].add_prod(wz, d);
+                                    cs[4][x].add_prod(wx2, d);
+                                    cs[4][x].add_prod(wj, dg);
+                                }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 5; ++q)
+#pragma unroll
+                        for (int x = 0; x < G::TX; ++x) {
+                            pc[q * QS + x * 32] = cs[q][x].s;
+                            pe[q * QS + x * 32] = cs[q][x].c;
+                        }
+                }
+            } else {
                 float pm[5][G::TX];
 #pragma unroll
                 for (int q = 0; q < 5; ++q)
@@ -1253,18 +1314,40 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                 const int x = ep * XS + xx;
                 if (x >= G::TX) break;
                 float m[5];
+                [[maybe_unused]] CompSum<float> cm[5];  // compensated sums: the quarters' partials
+                if constexpr (KC) {
 #pragma unroll
-                for (int q = 0; q < 5; ++q)
-                    m[q] = ((part[(0 * 5 + q) * QS + x * 32 + lane] + part[(1 * 5 + q) * QS + x * 32 + lane]) +
-                            part[(2 * 5 + q) * QS + x * 32 + lane]) +
-                           part[(3 * 5 + q) * QS + x * 32 + lane];
+                    for (int q = 0; q < 5; ++q) {
+#pragma unroll
+                        for (int qq = 0; qq < 4; ++qq)
+                            cm[q].add_partial(part[(qq * 5 + q) * QS + x * 32 + lane],
+                                              part[(20 + qq * 5 + q) * QS + x * 32 + lane]);
+                        m[q] = cm[q].value();
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 5; ++q)
+                        m[q] = ((part[(0 * 5 + q) * QS + x * 32 + lane] + part[(1 * 5 + q) * QS + x * 32 + lane]) +
+                                part[(2 * 5 + q) * QS + x * 32 + lane]) +
+                               part[(3 * 5 + q) * QS + x * 32 + lane];
+                }
                 float* pn = prm + x * 32 + lane;
                 if constexpr (G::kF32) {
                     const float rho = m[0];
                     const float inv_rho = 1.0f / rho;
                     const float ux = m[1] * inv_rho, uy = m[2] * inv_rho, uz = m[3] * inv_rho;
                     const float usq = ux * ux + uy * uy + uz * uz;
-                    const float T = (m[4] * inv_rho - usq) * static_cast<float>(a.inv_2cv);
+                    float T;
+                    if constexpr (KC) {
+                        // 2 rho E - rho |u|^2 = 2 rho E - m . u, compensated
+                        CompSum<float> e = cm[4];
+                        e.add_prod(-m[1], ux);
+                        e.add_prod(-m[2], uy);
+                        e.add_prod(-m[3], uz);
+                        T = e.value() * inv_rho * static_cast<float>(a.inv_2cv);
+                    } else {
+                        T = (m[4] * inv_rho - usq) * static_cast<float>(a.inv_2cv);
+                    }
                     if (a.flag != nullptr && row_ok && !(rho > 0.f && T > 0.f && isfinite(rho) && isfinite(T)))
                         atomicOr(a.flag, 1);
                     const float tau_r = static_cast<float>(a.mu_over_dt) * sutherland(T) / (rho * T) + 0.5f;
@@ -1298,8 +1381,19 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                     const float inv_rho = 1.0f / rho;
                     const float ux = m[1] * inv_rho, uy = m[2] * inv_rho, uz = m[3] * inv_rho;
                     const float usq = ux * ux + uy * uy + uz * uz;
-                    const float dT =
-                        (m[4] + 3.0f * rho0 * (1.0f - T0) - rho * usq - two_cv * T0 * drho) * inv_rho / two_cv;
+                    float dT;
+                    if constexpr (KC) {
+                        // every term of the balance compensated, rho |u|^2 as m . u
+                        CompSum<float> e = cm[4];
+                        e.add(3.0f * rho0 * (1.0f - T0));
+                        e.add_prod(-m[1], ux);
+                        e.add_prod(-m[2], uy);
+                        e.add_prod(-m[3], uz);
+                        e.add_prod(-two_cv * T0, drho);
+                        dT = e.value() * inv_rho / two_cv;
+                    } else {
+                        dT = (m[4] + 3.0f * rho0 * (1.0f - T0) - rho * usq - two_cv * T0 * drho) * inv_rho / two_cv;
+                    }
                     const float T = T0 + dT;
                     if (a.flag != nullptr && row_ok && !(rho > 0.f && T > 0.f && isfinite(rho) && isfinite(T)))
                         atomicOr(a.flag, 1);

@@ -306,10 +306,11 @@ int choose_step_kernel(const sllbm_ctx* c) {
     // (with the Prandtl term the TMA-fed kernel is at best as fast as the generic one: at
     // 128^3 nodes, p = 4, 1.35 ms against 1.36 with ghost planes, 1.51 against 1.35 on the
     // ordinary periodic context; at 192^3, p = 3, 5.28 against 4.25)
-    // Compensated moment sums cost the TMA-fed kernel +28 to +65 % (its four epilogue warps
-    // issue them) and the generic one +10 to +17 %: the generic kernel is then the faster at
-    // p = 3 (192^3 nodes: FP32 4.06 against 4.33 ms) and with 16-bit storage at p = 4 on the
-    // ordinary periodic context (128^3: 1.31 against 1.48 ms).
+    // Compensated moment sums cost the TMA-fed kernel +22 to +52 % (its four epilogue warps
+    // issue them) and the generic one +10 to +18 %: the generic kernel is then the faster at
+    // p = 3 (192^3 nodes: FP32 4.01 against 4.33 ms) and about as fast with 16-bit storage at
+    // p = 4 on the ordinary periodic context (128^3: FP16 1.31 against 1.34 ms, BF16 1.33
+    // against 1.31).
     const bool comp_generic = c->compensated && (c->p == 3 || (dev16 && c->p == 4 && !c->slab));
     return (tma_ok && nodes >= min_nodes && !c->prm.pr_correction && !(dev16 && c->p == 3 && !c->slab) &&
             !comp_generic)

@@ -488,6 +488,17 @@ __device__ __forceinline__ void tmem_load_row(uint32_t ta, float* v) {
     }
 }
 
+// 2*CH floats of one pair at column ta: CH = 4 nodes (half of an 8-node row), or a whole
+// 6-node row
+template <int CH>
+__device__ __forceinline__ void tmem_load_nodes(uint32_t ta, float* v) {
+    if constexpr (CH == 4) {
+        tmem_ld8(ta, v);
+    } else {
+        tmem_load_row<CH>(ta, v);
+    }
+}
+
 // Visiting order of the tiles: slabs of kBlockZ tile layers; in a slab, blocks of kBlockXY x
 // kBlockXY tile columns (row by row); in a block, z-, y-, then x-slowest.  Consecutive tiles
 // (the CTAs of one wave) thus cover a compact region whose source boxes overlap in L2, rather
@@ -1202,26 +1213,30 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
             tc_fence_after();
             // moment contributions of the quarter's pairs (rho, m_x, m_y, m_z, 2 rho E; Eq. moments)
             if constexpr (KC) {
-                // compensated: a running sum and its exact rounding errors per moment and node
-                // (one tensor-memory load per pair, as below); the sums go to rows
-                // [quarter][moment], the error terms to the 20 rows after them
+                // compensated: a running sum and its exact rounding errors per moment and node,
+                // CH node columns at a time (8-node rows in two halves: measured faster than
+                // whole rows there, 1.05 against 1.12 ms per 128^3 step; 6-node rows whole);
+                // the sums go to rows [quarter][moment], the error terms to the 20 rows after them
+                constexpr int CH = G::TX == 8 ? 4 : G::TX;
                 float* pc = part + static_cast<size_t>(qd) * 5 * QS + lane;
                 float* pe = pc + 20 * QS;
-                {
-                    CompSum<float> cs[5][G::TX];
+#pragma unroll 1
+                for (int x0 = 0; x0 < G::TX; x0 += CH) {
+                    CompSum<float> cs[5][CH];
                     for (int sw = sw0; sw < nsw; ++sw) {
                         const int cw = stream_index(qd + 4 * sw), npw = pairs_of(cw);
 #pragma unroll 1
                         for (int k = 0; k < npw; ++k) {
                             const int j = pair_of(cw, k);
-                            float v[2 * G::TX];
-                            tmem_load_row<G::TX>(tb + static_cast<uint32_t>(sw * TC::per_warp + k * G::PCS), v);
+                            float v[2 * CH];
+                            tmem_load_nodes<CH>(
+                                tb + static_cast<uint32_t>(sw * TC::per_warp + k * G::PCS + 2 * x0), v);
                             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                             const float xix = t.xi[j][0], xiy = t.xi[j][1], xiz = t.xi[j][2];
                             const float x2 = static_cast<float>(shell_xi2(shell_of(j)));
                             if constexpr (G::kF32) {
 #pragma unroll
-                                for (int x = 0; x < G::TX; ++x) {
+                                for (int x = 0; x < CH; ++x) {
                                     const float f = v[2 * x], g = v[2 * x + 1];
                                     cs[0][x].add(f);
                                     cs[1][x].add_prod(f, xix);
@@ -1234,7 +1249,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                                 const float wj = t.w[j];
                                 const float wx = wj * xix, wy = wj * xiy, wz = wj * xiz, wx2 = wj * x2;
 #pragma unroll
-                                for (int x = 0; x < G::TX; ++x) {
+                                for (int x = 0; x < CH; ++x) {
                                     const float d = v[2 * x], dg = v[2 * x + 1];
                                     cs[0][x].add_prod(wj, d);
                                     cs[1][x].add_prod(wx, d);
@@ -1249,9 +1264,9 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
 #pragma unroll
                     for (int q = 0; q < 5; ++q)
 #pragma unroll
-                        for (int x = 0; x < G::TX; ++x) {
-                            pc[q * QS + x * 32] = cs[q][x].s;
-                            pe[q * QS + x * 32] = cs[q][x].c;
+                        for (int x = 0; x < CH; ++x) {
+                            pc[q * QS + (x0 + x) * 32] = cs[q][x].s;
+                            pe[q * QS + (x0 + x) * 32] = cs[q][x].c;
                         }
                 }
             } else {

@@ -14,8 +14,11 @@ from paper_2012_05537_gb300 import sllbm as S
 pytestmark = pytest.mark.gpu
 
 
-def _full(cfg, n, kernel=1):
+def _full(cfg, n, kernel=1, compensated=False):
     sim = S.Sim(dataclasses.replace(cfg, kernel=kernel), device="cuda:0")
+    if compensated:
+        S.sllbm_set_compensated(sim.ctx, True)
+    assert sim.info.step_kernel == kernel
     sim.init_tgv()
     init = sim.populations().cpu().numpy()
     assert sim.step(n) == 0
@@ -24,11 +27,13 @@ def _full(cfg, n, kernel=1):
     return init, out
 
 
-def _slabs(cfg, parts, n, overlapped=False, kernel=1):
+def _slabs(cfg, parts, n, overlapped=False, kernel=1, compensated=False):
     steppers = []
     for r in range(parts):
         sim = S.Sim(dataclasses.replace(cfg, slab=D.slab_bounds(cfg.cells[2], parts, r), kernel=kernel),
                     device="cuda:0")
+        if compensated:
+            S.sllbm_set_compensated(sim.ctx, True)
         sim.init_tgv()
         assert sim.info.step_kernel == kernel
         steppers.append(D.SlabStepper(sim))
@@ -89,6 +94,22 @@ def test_tma_fed_slabs_reproduce_the_whole_mesh(p, parts, storage, overlapped):
     _, slab, _ = _slabs(cfg, parts, 4, overlapped=overlapped, kernel=2)
     assert np.all(np.isfinite(full))
     assert np.array_equal(slab, full)
+
+
+@pytest.mark.parametrize("p,parts,storage,overlapped", [(4, 2, "f32", False), (3, 2, "f32", False),
+                                                        (2, 2, "f32", True), (3, 2, "f16dev", False),
+                                                        (2, 2, "f16dev", False), (4, 3, "bf16dev", True)])
+def test_tma_fed_slabs_with_compensated_sums_reproduce_the_whole_mesh(p, parts, storage, overlapped):
+    # compensated moment sums (sllbm_set_compensated) run in the epilogue, after the
+    # streaming: slabs stay bit-equal to the undivided mesh, the TMA-fed kernel on both
+    cfg = S.Config(cells=(4, 4, 8), p=p, courant=2.0, storage=storage)
+    _, full = _full(cfg, 4, kernel=2, compensated=True)
+    _, plain = _full(cfg, 4, kernel=2)
+    _, slab, _ = _slabs(cfg, parts, 4, overlapped=overlapped, kernel=2, compensated=True)
+    assert np.all(np.isfinite(full))
+    assert np.array_equal(slab, full)
+    if storage == "f32":
+        assert not np.array_equal(full, plain)  # (the compensated instance did run)
 
 
 @pytest.mark.parametrize("kernel,p,storage", [(1, 3, "f64"), (1, 4, "f32"), (2, 4, "f32"), (2, 2, "f32"),

@@ -27,14 +27,19 @@ def S():
 # the TMA-fed instances the run-control tests cover: FP32 at p = 4 (without and with the
 # Prandtl term, whose epilogue has more barriers), FP16 deviations at p = 3 (a 16-bit box is
 # released right after its z pass), BF16 deviations at p = 4
-TMA_RUN_CASES = [("f32", 4, (16, 8, 8)), ("f32pr", 4, (8, 8, 4)), ("f16dev", 3, (8, 6, 4)), ("bf16dev", 4, (8, 4, 4))]
+# (storage, p, cells); the suffix "pr" adds the Prandtl term, "kc" compensated moment sums
+# (their instances hold a smaller box ring)
+TMA_RUN_CASES = [("f32", 4, (16, 8, 8)), ("f32pr", 4, (8, 8, 4)), ("f16dev", 3, (8, 6, 4)), ("bf16dev", 4, (8, 4, 4)),
+                 ("f32kc", 4, (8, 8, 4)), ("f16devkc", 3, (8, 6, 4))]
 
 
 def tma_sim(S, cells=(16, 8, 8), storage="f32", p=4):
-    pr = storage.endswith("pr")
-    storage = storage[:-2] if pr else storage
+    pr, kc = storage.endswith("pr"), storage.endswith("kc")
+    storage = storage[:-2] if (pr or kc) else storage
     sim = S.Sim(S.Config(cells=cells, p=p, courant=3.0, storage=storage, kernel=2, pr_correction=pr))
-    assert sim.info.step_kernel == 2
+    if kc:
+        S.sllbm_set_compensated(sim.ctx, True)
+    assert S.sllbm_get_info(sim.ctx).step_kernel == 2
     return sim
 
 

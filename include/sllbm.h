@@ -372,8 +372,8 @@ int sllbm_batch_step(sllbm_batch *b, int nsteps);
  * even) replays of the captured graph, from the current states, keeps another shape for
  * an order only if that makes the graph at least 2 % faster (one order at a time), and
  * restores the states.  FP32 storage
- * without the Prandtl term only (SLLBM_EINVAL otherwise); other conditions as
- * sllbm_batch_create.  Synchronous. */
+ * without the Prandtl term or compensated moment sums only (SLLBM_EINVAL otherwise); other
+ * conditions as sllbm_batch_create.  Synchronous. */
 int sllbm_batch_create_persistent(sllbm_ctx *const *ctxs, int n, void *cuda_stream, int tune_steps,
                                   sllbm_batch **out);
 

@@ -108,6 +108,8 @@ def parse_args():
                     help="step kernel of the headline run: 0 automatic, 1 generic, 2 TMA-fed")
     ap.add_argument("--pr", action="store_true",
                     help="headline run with the quasi-equilibrium Prandtl term (App. D) on")
+    ap.add_argument("--compensated", action="store_true",
+                    help="headline run with compensated moment sums (sllbm_set_compensated)")
     ap.add_argument("--periodic-z", choices=["ghost", "wrap"], default="ghost",
                     help="z boundary of the headline mesh: ghost planes (the mesh as one periodic z-slab, "
                          "refreshed in place before each step) or source boxes wrapping around")
@@ -733,6 +735,8 @@ def run_mine(args, rank, world, local):
                    courant=w.courant, pr_correction=w.pr_correction or args.pr, storage=storage,
                    slab=(0, w.cells[2]) if ghost else None, kernel=args.kernel)
     sim = S.Sim(cfg, device=f"cuda:{local}")
+    if args.compensated:
+        sim.set_compensated(True)
     sim.init_tgv()
     for _ in range(max(3, args.warmup)):
         sim.step(1)
@@ -763,7 +767,8 @@ def run_mine(args, rank, world, local):
     hbm, peak_src = measured_peaks()
     achieved = bytes_per_node * nodes / (kern_avg_ms / 1e3) / 1e9
     traffic = profiled_traffic(w.name, storage, "tma" if sim.info.step_kernel == 2 else "generic",
-                               ("_ghostz" if ghost else "") + ("_pr" if args.pr else ""))
+                               ("_ghostz" if ghost else "") + ("_pr" if args.pr else "") +
+                               ("_kc" if args.compensated else ""))
 
     # end to end through the C ABI with host buffers: every step copies a state from pinned
     # host memory to the device, advances it one step and copies the result back.  Headline:
@@ -775,6 +780,8 @@ def run_mine(args, rank, world, local):
     e2e = None
     if args.e2e_steps > 0:
         sime = S.Sim(dataclasses.replace(cfg, slab=None), device=f"cuda:{local}") if ghost else sim
+        if args.compensated and sime is not sim:
+            sime.set_compensated(True)
         if ghost:
             sime.init_tgv()
         nb = int(sime.info.pop_bytes)
@@ -815,7 +822,7 @@ def run_mine(args, rank, world, local):
                                      "hbm_frac": bytes_per_node * nodes / (statistics.mean(kw) / 1e3) / 1e9 / hbm,
                                      "steps": nw}
         simw.close()
-    if not args.no_variants and rank == 0 and storage != "f64" and not args.pr:
+    if not args.no_variants and rank == 0 and storage != "f64" and not args.pr and not args.compensated:
         # the same workload with compensated moment sums (the same context kind and kernel choice)
         simc = S.Sim(cfg, device=f"cuda:{local}")
         S.sllbm_set_compensated(simc.ctx, True)
@@ -902,6 +909,7 @@ def run_mine(args, rank, world, local):
             "config": {"workload": w.name, "cells": list(w.cells), "p": w.p,
                        "nodes": nodes, "Ma": w.Ma, "Re": w.Re, "courant": w.courant,
                        "pr_correction": bool(w.pr_correction or args.pr),
+                       "compensated_moments": bool(args.compensated),
                        "dt": sim.dt, "storage": storage,
                        "z_boundary": ("ghost planes: the mesh as one periodic z-slab (sllbm_create_slab over "
                                       "all cells), refreshed in place before each step by sllbm_halo_periodic "

@@ -624,6 +624,11 @@ class Sim:
         sllbm_set_step_variant(self.ctx, variant)
         self.info = sllbm_get_info(self.ctx)
 
+    def set_compensated(self, on: bool = True) -> None:
+        """Compensated moment sums for the following steps (the kernel choice is made again)."""
+        sllbm_set_compensated(self.ctx, on)
+        self.info = sllbm_get_info(self.ctx)
+
     def autotune(self, steps: int = 5):
         """Times every variant that can run this context from the current state, keeps the
         fastest (the state is restored); returns (variant, ms per step)."""
